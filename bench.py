@@ -1,0 +1,414 @@
+"""Benchmark: ms per topology-optimisation iteration on the 3D H8 128^3
+heat-sink workload (2,146,689 nodal temperatures), mixed-precision MGAR
+against plain FP64 MGCG on the same GPU, with the dominant kernel's roofline.
+
+One step = one whole optimisation run of the workload (50 design cycles from
+rho = 0.3: filter, MGCG or MGAR with fallback, sensitivities, OC), inputs
+resident in HBM; value = mean device time per design cycle.  The e2e figure
+runs the same through mgar_run from pinned host memory (design in, design and
+per-cycle reports out).  --impl reference times the FP64 CPU oracle on a
+bounded sample of the same workload instead.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mgar|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ms per TO iteration, 3D H8 128^3, MGAR vs FP64 MGCG @1e-6 rel err; HBM %"
+UNIT = "ms/iteration"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mgar", choices=["mgar", "reference"])
+    ap.add_argument("--workload", default="heat3d_128")
+    ap.add_argument("--cycles", type=int, default=0, help="design cycles per step (0 = workload's)")
+    ap.add_argument("--guess", default="previous", choices=["previous", "zero"])
+    ap.add_argument("--eps1", type=float, default=None)
+    ap.add_argument("--kernel", default="apply64",
+                    choices=["apply64", "smooth0", "resid0", "oc", "galerkin0", "filter", "sens"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 MGCG comparison run")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-check", action="store_true", help="skip the equal-compliance check")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------ distributed
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------- roofline
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return {}
+
+
+def fp64_peak_tflops(sm_mhz):
+    """FP64 peak of GB300 from its unit count and clock: the nominal
+    1.25 TFLOP/s at the 2070 MHz maximum SM clock is 604 FLOP per clock for
+    the chip (152 SMs x 2 FP64 FMA per clock x 2 FLOP); scaled to the clock
+    seen under load."""
+    mhz = sm_mhz or 2070.0
+    return 152 * 2 * 2 * mhz * 1e6 / 1e12
+
+
+def kernel_model(kernel, w):
+    """Algorithmic work per launch of a kernel class on workload w:
+    (bytes, fp64 flops, bound).  Per-unit figures are stated in the design doc."""
+    n = w.n_nodes
+    e = w.n_elems
+    if kernel == "apply64":
+        # 3D H8 y = A x in FP64, node-centred: read x (8 B) and one k_e per
+        # node (8 B, each element read once) and the fixed-node mask (1 B),
+        # write y (8 B); 62 FP64 FLOP per node (7 adds for sum k, 12 pair
+        # sums, 20 FMA, 3 multiplies), + 2 for the fused p.Ap dot.
+        return 25 * n, 64 * n, "alu"
+    if kernel == "smooth0":
+        # FP32 level-0 Jacobi: read x, b, dinv (12 B), k_e (4 B), mask (1 B), write x (4 B)
+        return 21 * n, 0, "hbm"
+    if kernel == "resid0":
+        return 21 * n, 0, "hbm"
+    if kernel == "oc":
+        # read s, lo, hi, dv (32 B per element)
+        return 32 * e, 5 * e, "alu"
+    if kernel == "filter":
+        return 24 * e, 40 * e, "alu"
+    if kernel == "sens":
+        return 8 * n + 16 * e, 50 * e, "alu"
+    if kernel == "galerkin0":
+        return 8 * e + 64 * 4 * e // 8, 0, "hbm"
+    raise ValueError(kernel)
+
+
+KC = {"apply64": 1, "smooth0": 2, "resid0": 3, "oc": 4, "galerkin0": 5, "filter": 6, "sens": 7}
+
+
+# ------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2210_00947_gb300 import mgar, workloads
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workloads.WORKLOADS[args.workload]
+    cycles = args.cycles or w.iters
+    fixed = w.fixed()
+    q = w.q()
+    rho0 = w.density()
+    guess = mgar.MGAR_GUESS_PREVIOUS if args.guess == "previous" else mgar.MGAR_GUESS_ZERO
+    overrides = {} if args.eps1 is None else {"eps1": args.eps1}
+    stream = torch.cuda.current_stream(dev)
+
+    p_mix = mgar.params_for(w, precision=mgar.MGAR_MIXED, basis_guess=guess, **overrides)
+    solver = mgar.Solver(p_mix, fixed, q, stream=stream)
+    rho0_d = torch.tensor(rho0, device=dev)
+    rho = torch.empty_like(rho0_d)
+    T = torch.zeros(solver.n_nodes, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def one_run(s, rho_t, T_t):
+        rho_t.copy_(rho0_d)
+        T_t.zero_()
+        infos = []
+        for k in range(1, cycles + 1):
+            infos.append(s.step(rho_t, T_t, k))
+        return infos
+
+    for _ in range(args.warmup):
+        one_run(solver, rho, T)
+    torch.cuda.synchronize()
+
+    # timed region: K whole runs, L2 flushed between them (outside the events)
+    sampler = ClockSampler(local)
+    kc = KC[args.kernel]
+    times = []
+    infos = []
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler.start()
+    launches0 = mgar.kernel_launches()
+    solver.profile_start(kc)
+    for _ in range(args.steps):
+        flush.zero_()
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        infos = one_run(solver, rho, T)
+        end.record(stream)
+        end.synchronize()
+        times.append(start.elapsed_time(end))
+    kern_ms, kern_launches = solver.profile_stop()
+    launches = mgar.kernel_launches() - launches0
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    step_ms = max_over_ranks(statistics.mean(times), world)
+    value = step_ms / (cycles * world)
+
+    # e2e: mgar_run from pinned host memory, copies inside the timed region
+    rho_h = torch.from_numpy(rho0.copy()).pin_memory()
+    rho_out = torch.empty_like(rho_h).pin_memory()
+    solver.run(rho_h, cycles, rho_out)
+    e2e_times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        solver.run(rho_h, cycles, rho_out)
+        e2e_times.append((time.perf_counter() - t0) * 1e3)
+    e2e_ms = max_over_ranks(statistics.mean(e2e_times), world)
+
+    # plain FP64 MGCG on the same workload (MGCG every cycle)
+    fp64 = None
+    if not args.no_fp64:
+        p64 = mgar.params_for(w, precision=mgar.MGAR_FP64, n_on=cycles + 1)
+        s64 = mgar.Solver(p64, fixed, q, stream=stream)
+        rho64 = torch.empty_like(rho0_d)
+        T64 = torch.zeros_like(T)
+        one_run(s64, rho64, T64)
+        t64 = []
+        for _ in range(max(1, min(args.steps, 2))):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            inf64 = one_run(s64, rho64, T64)
+            b.record(stream)
+            b.synchronize()
+            t64.append(a.elapsed_time(b))
+        fp64 = {"ms_per_iteration": statistics.mean(t64) / cycles,
+                "cg_iters_mean": statistics.mean(i["cg_iters"] for i in inf64),
+                "final_compliance": inf64[-1]["compliance"]}
+
+    # equal-compliance check: replay the mixed trajectory; at every cycle solve
+    # the same design with FP64 MGCG to eps2 = 1e-10 and compare compliances
+    check = None
+    if not args.no_check:
+        pc = mgar.params_for(w, precision=mgar.MGAR_FP64, n_on=cycles + 1, eps2=1e-10)
+        sc = mgar.Solver(pc, fixed, q, stream=stream)
+        rho.copy_(rho0_d)
+        T.zero_()
+        Tc = torch.zeros_like(T)
+        worst, worst_acc = 0.0, 0.0
+        for k in range(1, cycles + 1):
+            sc.set_density(rho)
+            Tc.zero_()
+            sc.solve_mgcg(Tc)
+            c_ref = sc.sensitivity(Tc)
+            inf = solver.step(rho, T, k)
+            rel = abs(inf["compliance"] - c_ref) / abs(c_ref)
+            worst = max(worst, rel)
+            if inf["accepted"]:
+                worst_acc = max(worst_acc, rel)
+        check = {"max_rel_err_all_cycles": worst, "max_rel_err_accepted_mgar": worst_acc,
+                 "reference": "FP64 MGCG (eps2 1e-10) on the same design each cycle"}
+
+    peaks = load_peaks()
+    bytes_, flops, bound = kernel_model(args.kernel, w)
+    avg_ms = kern_ms / max(kern_launches, 1)
+    if bound == "alu":
+        achieved = flops / (avg_ms * 1e-3) / 1e12
+        peak = fp64_peak_tflops(clocks.get("sm_mhz"))
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s (fp64)",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "FP64 unit count x SM clock under load (derived, see DESIGN.md)",
+                "hbm_gbs": bytes_ / (avg_ms * 1e-3) / 1e9}
+    else:
+        achieved = bytes_ / (avg_ms * 1e-3) / 1e9
+        peak = peaks.get("hbm_gbs", 6800.0)
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
+    roof.update({"kernel": args.kernel, "launches": kern_launches, "avg_launch_us": avg_ms * 1e3,
+                 "share_of_step": kern_ms / sum(times)})
+
+    n_mgcg = sum(1 for i in infos if i["used_mgcg"])
+    n_acc = sum(1 for i in infos if i["accepted"])
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": args.workload, "grid": f"{w.nx}x{w.ny}x{w.nz} H8" if w.nz else
+                   f"{w.nx}x{w.ny} Q4", "dofs": w.n_nodes, "cycles_per_step": cycles,
+                   "nl": w.nl, "m": w.m, "eps1": p_mix.eps1, "eps2": w.eps2,
+                   "basis_guess": args.guess, "precision": "mixed (FP32 V-cycle, FP64 CG/GS/reduced)",
+                   "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) between steps"},
+        "cycles": {"mgcg": n_mgcg, "mgar_accepted": n_acc,
+                   "cg_iters_mean": statistics.mean([i["cg_iters"] for i in infos if i["used_mgcg"]] or [0]),
+                   "final_compliance": infos[-1]["compliance"]},
+        "fp64_mgcg": fp64, "compliance_check": check,
+        "e2e": {"value": e2e_ms / (cycles * world), "unit": UNIT,
+                "h2d_bytes_per_step": 8 * w.n_elems,
+                "d2h_bytes_per_step": 8 * w.n_elems + 48 * cycles},
+        "gpu_launches": launches, "roofline": roof, "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(args.workload, cycles=1)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------ CPU oracle
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+from oracle import loop
+from paper_2210_00947_gb300 import workloads
+w = workloads.WORKLOADS[{name!r}]
+s = loop.LoopSettings(nx=w.nx, ny=w.ny, nz=w.nz, volfrac=w.volfrac, iters=w.iters, n_on=w.n_on,
+                      nl=w.nl, eps2=w.eps2, cg_max=w.cg_max, eps1=w.eps1, m=w.m)
+an = loop.Analysis(s, w.fixed(), w.q())
+rho = w.density(); t = np.zeros(an.grid.n_nodes)
+out = []
+for k in range(1, {cycles} + 1):
+    t0 = time.perf_counter()
+    rho, t, info = an.cycle(k, rho, t)
+    out.append(dict(seconds=time.perf_counter() - t0, mgcg=bool(info["mgcg"]),
+                    compliance=float(info["compliance"])))
+print(json.dumps(out))
+"""
+
+
+def cpu_baseline(name, cycles=1):
+    """The FP64 oracle as it stands, on the host cores, one process with BLAS
+    and OpenMP pinned to one thread: design cycles 1..cycles of the workload."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ORACLE_SNIPPET.format(root=ROOT, name=name, cycles=cycles)
+    res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if res.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": "failed: " + res.stderr.strip().splitlines()[-1][:200]}
+    cyc = json.loads(res.stdout.strip().splitlines()[-1])
+    ms = 1e3 * statistics.mean(c["seconds"] for c in cyc)
+    return {"value": ms, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"design cycles 1..{cycles} of {name} (MGCG cycles incl. assembly and "
+                      f"hierarchy), mean per cycle, numpy/scipy FP64, one thread"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and rank != 0:
+        return
+    times = []
+    for i in range(args.warmup + args.steps):
+        b = cpu_baseline(args.workload, cycles=1)
+        if b["value"] is None:
+            print(json.dumps({"impl": "reference", "unavailable": b["sample"]}))
+            return
+        if i >= args.warmup:
+            times.append(b["value"])
+    value = statistics.mean(times)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": value, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": args.workload, "sample": "design cycle 1 per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "design cycle 1 (MGCG) of the workload per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gpu(a)

@@ -1,0 +1,223 @@
+/*
+ * mgar.h - C ABI of the GB300 (sm_103a) library for multigrid-assisted
+ * reanalysis (MGAR) heat-transfer topology optimisation.
+ *
+ * The operations follow Yin, Wang, Guo, Li, "An efficient topology
+ * optimization based on multigrid assisted reanalysis for heat transfer
+ * problem" (arXiv 2210.00947).  Each entry point cites the passage that
+ * defines what it computes.
+ *
+ * Conventions shared by every call
+ *   - Grid: nx x ny (x nz) unit elements; nz = 0 selects 2D bilinear (Q4)
+ *     elements, nz > 0 3D trilinear (H8) elements.  Nodes and elements are
+ *     numbered x-fastest: node(i,j,k) = i + (nx+1)*(j + (ny+1)*k),
+ *     elem(i,j,k) = i + nx*(j + ny*k).  n = number of nodes, E = number of
+ *     elements.
+ *   - Arrays named "device" are CUDA device pointers owned by the caller;
+ *     the library never frees them and keeps no reference after the call
+ *     returns.  Arrays named "host" are plain host memory, read during the
+ *     call only.
+ *   - Every call is ordered on the CUDA stream given to mgar_create (or
+ *     mgar_set_stream).  A call that returns a scalar through a host
+ *     pointer synchronises that stream before returning.
+ *   - Return value: MGAR_OK (0) or a negative MGAR_ERR_* code;
+ *     mgar_last_error() then describes the failure.  A handle is not
+ *     thread-safe: use one handle per host thread.
+ *   - Fixed (Dirichlet, T = 0) nodes are eliminated: the operator is
+ *     A = Z K Z + (I - Z), Z = diag(free nodes).
+ */
+#ifndef MGAR_H_
+#define MGAR_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MGAR_OK 0
+#define MGAR_ERR_ARG (-1)       /* invalid argument or size */
+#define MGAR_ERR_CUDA (-2)      /* a CUDA runtime call failed */
+#define MGAR_ERR_NOT_SPD (-3)   /* a Cholesky factorisation met a non-positive pivot */
+#define MGAR_ERR_MAXIT (-4)     /* MGCG stopped at cg_max without reaching eps2 */
+#define MGAR_ERR_NONFINITE (-5) /* a NaN/Inf appeared in a solver scalar */
+#define MGAR_ERR_STATE (-6)     /* call out of order (e.g. MGAR before any MGCG) */
+
+#define MGAR_FP64 0  /* every step in FP64 */
+#define MGAR_MIXED 1 /* FP32 multigrid preconditioner, FP64 elsewhere */
+
+#define MGAR_GUESS_PREVIOUS 0 /* Eq. 17 as printed: V-cycle initial guess r_{i-1} */
+#define MGAR_GUESS_ZERO 1     /* V-cycle from a zero initial guess */
+
+typedef struct mgar_ctx* mgar_t;
+
+/* Problem and solver parameters (Sections 2.1-2.2, 3.2).  All fields are
+ * read at mgar_create. */
+typedef struct mgar_params {
+  int32_t nx, ny, nz;   /* elements per axis; nz = 0 for 2D */
+  double k0, kmin;      /* solid / void conductivity (Eq. 4) */
+  double penal;         /* SIMP exponent p (Eq. 4) */
+  double rmin;          /* density-filter radius in element lengths (Eq. 6-8) */
+  int32_t nl;           /* multigrid levels incl. the finest, >= 2 (Section 3.2) */
+  int32_t m;            /* MGAR basis size, 1..8 (Eq. 14) */
+  double eps1;          /* MGAR acceptance threshold on Res (Eq. 28) */
+  double eps2;          /* MGCG relative residual tolerance (Section 3.2) */
+  int32_t cg_max;       /* MGCG iteration cap (Section 3.2) */
+  double omega;         /* damped-Jacobi weight (Section 2.2) */
+  int32_t nu_pre, nu_post; /* smoothing sweeps before / after the coarse correction */
+  int32_t precision;    /* MGAR_FP64 or MGAR_MIXED */
+  int32_t basis_guess;  /* MGAR_GUESS_PREVIOUS or MGAR_GUESS_ZERO (Eq. 17) */
+  int32_t n_on;         /* MGAR activation cycle N_on (Section 3.1) */
+  double volfrac;       /* volume fraction of the OC update */
+  double move;          /* OC move limit */
+} mgar_params;
+
+/* Per-cycle report of mgar_step. */
+typedef struct mgar_step_info {
+  double compliance;  /* f = q^T t (Eq. 5) */
+  double res;         /* MGAR residual Res (Eq. 28), NaN when MGAR did not run */
+  double relres;      /* MGCG final relative residual, NaN when MGCG did not run */
+  double lambda;      /* OC multiplier */
+  int32_t used_mgcg;  /* 1 when MGCG produced t (N_on or Eq. 28 rejection) */
+  int32_t accepted;   /* 1 when the MGAR solution was accepted */
+  int32_t cg_iters;   /* MGCG iterations of this cycle */
+  int32_t status;     /* MGAR_OK, or MGAR_ERR_MAXIT when MGCG hit cg_max */
+} mgar_step_info;
+
+/* Fill *p with the defaults of the paper's experiments (Section 3.2): k0 1,
+ * kmin 1e-3, p 3, rmin 1.5, nl 4, m 2, eps1 0.5, eps2 1e-8, cg_max 200,
+ * omega 0.6, one pre- and post-sweep, FP64, Eq. 17 as printed, n_on 0,
+ * volfrac 0.4, move 0.2.  The grid size is left zero. */
+void mgar_default_params(mgar_params* p);
+
+/* Create a handle for one design domain (Eq. 3-5).
+ *   fixed_mask: host, n bytes, non-zero marks a T = 0 node.
+ *   q:          host, n doubles, nodal heat load (entries on fixed nodes
+ *               are ignored and treated as zero).
+ *   stream:     cudaStream_t to order all work on (NULL = legacy default).
+ * Allocates all device workspaces; the caller's arrays are copied.
+ * Errors: MGAR_ERR_ARG on bad sizes/parameters (nl too deep for the grid,
+ * m out of range), MGAR_ERR_CUDA on allocation failure. */
+int mgar_create(mgar_t* out, const mgar_params* p, const uint8_t* fixed_mask, const double* q,
+                void* stream);
+
+/* Release every device allocation of the handle.  h may be NULL. */
+int mgar_destroy(mgar_t h);
+
+/* Change the stream later calls are ordered on. */
+int mgar_set_stream(mgar_t h, void* stream);
+
+/* Text of the last error on this handle (never NULL). */
+const char* mgar_last_error(mgar_t h);
+
+/* Density filter, Eq. 6-8 (transpose = 0): out_e = sum_i w_ei in_i /
+ * sum_i w_ei with w_ei = max(0, rmin - |c_e - c_i|) over in-domain
+ * elements.  transpose = 1 applies the adjoint used by the chain rule of
+ * Eq. 9 and 11: out_j = sum_e w_ej in_e / sum_i w_ei.
+ *   in, out: device, E doubles, must not overlap. */
+int mgar_filter(mgar_t h, const double* in, double* out, int transpose);
+
+/* Set the current design.  rho: device, E doubles.  is_physical = 0
+ * filters rho first (Eq. 6); 1 takes rho as the physical density rho~.
+ * The element conductivities k_e = kmin + (k0-kmin) rho~^p (Eq. 4) are
+ * derived here; the multigrid hierarchy is not touched. */
+int mgar_set_density(mgar_t h, const double* rho, int is_physical);
+
+/* y = A(rho~) x for the current design (Eq. 3, fixed nodes eliminated).
+ *   x, y: device, n doubles, must not overlap. */
+int mgar_apply_K(mgar_t h, const double* x, double* y);
+
+/* Build the multigrid hierarchy of the current design and make it the
+ * reference ("factorised") matrix K0 of Eq. 12 (Table 1 operators, Galerkin
+ * coarse levels A_{l+1} = P^T A_l P, coarsest level factorised). */
+int mgar_build_hierarchy(mgar_t h);
+
+/* One V-cycle x <- MG(K0, b, x, P) on the reference hierarchy (Table 1).
+ *   b: device, n doubles; x: device, n doubles, initial guess in, result
+ *   out.  Errors: MGAR_ERR_STATE if no hierarchy was built yet. */
+int mgar_vcycle(mgar_t h, const double* b, double* x);
+
+/* MGCG solve of A(rho~) T = q for the current design (Section 3.2): the
+ * hierarchy is rebuilt from the current design (K0 <- K), then CG
+ * preconditioned by one V-cycle runs until ||r||/||q|| <= eps2 or cg_max
+ * iterations.
+ *   T: device, n doubles, warm start in, solution out.
+ *   iters, relres: host, may be NULL.
+ * Returns MGAR_ERR_MAXIT (T still written) when cg_max was reached,
+ * MGAR_ERR_NONFINITE on breakdown. */
+int mgar_solve_mgcg(mgar_t h, double* T, int* iters, double* relres);
+
+/* MGAR reanalysis (Eq. 17-21 and 28) of the current design on the reference
+ * hierarchy K0: basis from t_prev by V-cycles, Gram-Schmidt, reduced
+ * m x m Cholesky solve, Res = ||K R~ y - q|| / ||q||.
+ *   T_prev: device, n doubles (r_1 of Eq. 15); T: device, n doubles, the
+ *   reduced solution t~ = R~ y.  T may alias T_prev.
+ *   res, accepted: host, may be NULL; accepted = (Res <= eps1).
+ * No fallback inside: the caller decides what to do on rejection.
+ * Errors: MGAR_ERR_STATE if no hierarchy exists. */
+int mgar_solve_mgar(mgar_t h, const double* T_prev, double* T, double* res, int* accepted);
+
+/* Compliance and design sensitivities (Eq. 5, 9-11) for the current design
+ * and temperatures T:
+ *   dc_j = sum_e w_ej/sum_i w_ei * (-p (k0-kmin) rho~_e^(p-1) t_e^T k0 t_e).
+ *   T: device n doubles; dc: device E doubles (may be NULL);
+ *   dv: device E doubles (may be NULL), gradient of mean(rho~);
+ *   compliance: host (may be NULL), q^T T. */
+int mgar_sensitivity(mgar_t h, const double* T, double* dc, double* dv, double* compliance);
+
+/* Optimality-criteria update (not in the paper; the classical SIMP
+ * framework it names): rho <- clamp(rho sqrt(-dc/(lambda dv)), rho-move,
+ * rho+move, [0,1]) with lambda by bisection so that mean(F rho) = volfrac.
+ *   rho: device E doubles, updated in place; dc: device E doubles.
+ *   lambda, change: host (may be NULL); change = max |rho_new - rho|. */
+int mgar_oc_update(mgar_t h, double* rho, const double* dc, double volfrac, double move,
+                   double* lambda, double* change);
+
+/* One design cycle of the MGAR-based loop (Section 3.1, Figure 5): filter,
+ * then MGCG when cycle < n_on or no reference exists, else MGAR with MGCG
+ * fallback when Res > eps1; then compliance, sensitivities and the OC
+ * update of rho.
+ *   rho: device E doubles (design, updated in place); T: device n doubles
+ *   (previous temperatures in, this cycle's out); cycle: 1-based.
+ *   info: host, may be NULL. */
+int mgar_step(mgar_t h, double* rho, double* T, int cycle, mgar_step_info* info);
+
+/* Sizes of the handle's grid: nodes, elements. */
+int mgar_sizes(mgar_t h, int64_t* n_nodes, int64_t* n_elems);
+
+/* A whole optimisation run from host memory (Section 3.1, Figure 5): copy
+ * rho_host (E doubles, pinned or pageable) to the device, start from zero
+ * temperatures and no reference matrix, run design cycles 1..cycles of
+ * mgar_step, then copy the final design to rho_out_host (E doubles) and one
+ * mgar_step_info per cycle to info_host (cycles entries, may be NULL).
+ * Device work buffers are allocated on the first call and kept. */
+int mgar_run(mgar_t h, const double* rho_host, int cycles, double* rho_out_host,
+             mgar_step_info* info_host);
+
+/* Instrumentation (no counterpart in the paper).  Kernel classes whose
+ * launches can be timed with CUDA events on the handle's stream: */
+#define MGAR_KC_APPLY64 1 /* FP64 finest-level K x (CG matvec, MGAR projection) */
+#define MGAR_KC_SMOOTH0 2 /* finest-level damped-Jacobi sweep (any precision) */
+#define MGAR_KC_RESID0 3  /* finest-level residual inside the V-cycle */
+#define MGAR_KC_OC 4      /* OC bisection pass */
+#define MGAR_KC_GALERKIN0 5 /* Galerkin element matrices of level 1 */
+#define MGAR_KC_FILTER 6  /* density filter / its transpose */
+#define MGAR_KC_SENS 7    /* element sensitivities (Eq. 10) */
+
+/* Start timing every launch of one kernel class (0 stops).  Each launch
+ * is bracketed by two CUDA events; at most 65536 launches are recorded. */
+int mgar_profile_start(mgar_t h, int kernel_class);
+/* Stop, synchronise the stream, and return the summed duration (ms) and
+ * the number of timed launches. */
+int mgar_profile_stop(mgar_t h, double* total_ms, int64_t* launches);
+
+/* Number of kernels this library has launched in this process (all
+ * handles), for accounting in benchmarks. */
+int64_t mgar_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MGAR_H_ */

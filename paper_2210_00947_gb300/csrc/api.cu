@@ -1,0 +1,413 @@
+// C ABI of libmgar (declared in include/mgar.h).
+#include "common.cuh"
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include <atomic>
+
+using namespace mgar;
+
+namespace {
+std::atomic<int64_t> g_launches{0};
+}  // namespace
+
+namespace mgar {
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace mgar
+
+namespace {
+
+thread_local std::string g_create_error = "no error";
+
+template <class F>
+int guarded(mgar_t h, F&& f) {
+  Ctx* c = reinterpret_cast<Ctx*>(h);
+  if (!c) return MGAR_ERR_ARG;
+  try {
+    return f(*c);
+  } catch (const Error& e) {
+    c->err = e.msg;
+    return e.code;
+  } catch (const std::exception& e) {
+    c->err = e.what();
+    return MGAR_ERR_CUDA;
+  }
+}
+
+void free_ctx(Ctx& c) {
+  free_hierarchy(c);
+  if (c.prof_ev) {
+    for (int i = 0; i < 2 * kProfMax; ++i)
+      if (c.prof_ev[i]) cudaEventDestroy(c.prof_ev[i]);
+    delete[] c.prof_ev;
+    c.prof_ev = nullptr;
+  }
+  cudaFree(c.run_rho);
+  cudaFree(c.run_T);
+  void* ptrs[] = {c.fixed, c.q, c.rho_phys, c.ke, c.ke0, c.ke_f, c.ke0_f, c.inv_hs, c.f_offs, c.f_w,
+                  c.dv, c.r, c.z, c.pv, c.Ap, c.tm, c.tmp_dc, c.R, c.W, c.b32, c.x32, c.tmp_e, c.oc_s, c.oc_lo,
+                  c.oc_hi, c.partials, c.counter, c.dsc, c.derr};
+  for (void* p : ptrs) cudaFree(p);
+  if (c.hsc) cudaFreeHost(c.hsc);
+}
+
+// One design cycle of Figure 5 on device arrays rho (design) and T.
+mgar_step_info design_cycle(Ctx& c, double* rho, double* T, int cycle) {
+  mgar_step_info inf{};
+  inf.res = NAN;
+  inf.relres = NAN;
+  int status = MGAR_OK;
+  set_density(c, rho, false);
+  bool need_mgcg = cycle < c.p.n_on || !c.have_ref;
+  if (!need_mgcg) {
+    double res = 0.0;
+    int acc = 0;
+    solve_mgar(c, T, c.tm, &res, &acc);  // t_prev in T, t~ in tm
+    inf.res = res;
+    inf.accepted = acc;
+    if (acc)
+      MGAR_CUDA(cudaMemcpyAsync(T, c.tm, c.n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    else
+      need_mgcg = true;  // Eq. 28 rejected: MGCG from t_prev, new reference
+  }
+  if (need_mgcg) {
+    int it = 0;
+    double rr = 0.0;
+    status = solve_mgcg(c, T, &it, &rr);
+    inf.used_mgcg = 1;
+    inf.cg_iters = it;
+    inf.relres = rr;
+  }
+  double comp = 0.0;
+  sensitivity(c, T, c.tmp_dc, nullptr, &comp);
+  inf.compliance = comp;
+  double lam = 0.0, change = 0.0;
+  oc_update(c, rho, c.tmp_dc, c.p.volfrac, c.p.move, &lam, &change);
+  inf.lambda = lam;
+  inf.status = status;
+  return inf;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mgar_default_params(mgar_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->k0 = 1.0;
+  p->kmin = 1e-3;
+  p->penal = 3.0;
+  p->rmin = 1.5;
+  p->nl = 4;
+  p->m = 2;
+  p->eps1 = 0.5;
+  p->eps2 = 1e-8;
+  p->cg_max = 200;
+  p->omega = 0.6;
+  p->nu_pre = 1;
+  p->nu_post = 1;
+  p->precision = MGAR_FP64;
+  p->basis_guess = MGAR_GUESS_PREVIOUS;
+  p->n_on = 0;
+  p->volfrac = 0.4;
+  p->move = 0.2;
+}
+
+const char* mgar_last_error(mgar_t h) {
+  if (!h) return g_create_error.c_str();
+  return reinterpret_cast<Ctx*>(h)->err.c_str();
+}
+
+int mgar_create(mgar_t* out, const mgar_params* p, const uint8_t* fixed_mask, const double* q,
+                void* stream) {
+  if (!out || !p || !fixed_mask || !q) {
+    g_create_error = "mgar_create: null argument";
+    return MGAR_ERR_ARG;
+  }
+  *out = nullptr;
+  Ctx* c = new Ctx();
+  try {
+    c->p = *p;
+    c->stream = reinterpret_cast<cudaStream_t>(stream);
+    const mgar_params& P = c->p;
+    require(P.nx >= 1 && P.ny >= 1 && P.nz >= 0, MGAR_ERR_ARG, "grid size must be positive");
+    require(P.nl >= 2 && P.nl <= kMaxLevels, MGAR_ERR_ARG, "nl must be in [2, 14]");
+    require(P.m >= 1 && P.m <= kMaxM, MGAR_ERR_ARG, "m must be in [1, 8]");
+    require(P.cg_max >= 0 && P.nu_pre >= 0 && P.nu_post >= 0, MGAR_ERR_ARG, "negative count");
+    require(P.precision == MGAR_FP64 || P.precision == MGAR_MIXED, MGAR_ERR_ARG, "bad precision");
+    require(P.basis_guess == MGAR_GUESS_PREVIOUS || P.basis_guess == MGAR_GUESS_ZERO, MGAR_ERR_ARG,
+            "bad basis_guess");
+    require(P.rmin > 0.0 && P.k0 > P.kmin && P.kmin > 0.0, MGAR_ERR_ARG, "bad material/filter");
+    c->dim = P.nz == 0 ? 2 : 3;
+    c->nen = 1 << c->dim;
+    c->S = c->dim == 2 ? 9 : 27;
+    c->nl = P.nl;
+    int ex = P.nx, ey = P.ny, ez = c->dim == 3 ? P.nz : 1;
+    for (int l = 0; l < c->nl; ++l) {
+      Dims& d = c->L[l];
+      d.ex = ex;
+      d.ey = ey;
+      d.ez = ez;
+      d.NX = ex + 1;
+      d.NY = ey + 1;
+      d.NZ = c->dim == 3 ? ez + 1 : 1;
+      d.n = (int64_t)d.NX * d.NY * d.NZ;
+      d.ne = (int64_t)ex * ey * ez;
+      ex = (ex + 1) / 2;
+      ey = (ey + 1) / 2;
+      if (c->dim == 3) ez = (ez + 1) / 2;
+    }
+    const Dims& coarsest = c->L[c->nl - 1];
+    require(coarsest.n <= 8192, MGAR_ERR_ARG,
+            "coarsest grid too large for the direct solve (use more levels)");
+    c->n = c->L[0].n;
+    c->ne = c->L[0].ne;
+    const int64_t n = c->n, ne = c->ne;
+    const int64_t maxb = blocks_for(n > ne ? n : ne);
+    c->grid_blocks = (int)std::min<int64_t>(blocks_for(n), 152 * 8);
+    c->grid_blocks_e = (int)std::min<int64_t>(blocks_for(ne), 152 * 8);
+
+    MGAR_CUDA(cudaMalloc(&c->fixed, n));
+    MGAR_CUDA(cudaMalloc(&c->q, n * sizeof(double)));
+    MGAR_CUDA(cudaMalloc(&c->rho_phys, ne * sizeof(double)));
+    MGAR_CUDA(cudaMalloc(&c->ke, ne * sizeof(double)));
+    MGAR_CUDA(cudaMalloc(&c->ke0, ne * sizeof(double)));
+    MGAR_CUDA(cudaMalloc(&c->inv_hs, ne * sizeof(double)));
+    MGAR_CUDA(cudaMalloc(&c->dv, ne * sizeof(double)));
+    MGAR_CUDA(cudaMalloc(&c->tmp_e, ne * sizeof(double)));
+    MGAR_CUDA(cudaMalloc(&c->oc_s, ne * sizeof(double)));
+    MGAR_CUDA(cudaMalloc(&c->oc_lo, ne * sizeof(double)));
+    MGAR_CUDA(cudaMalloc(&c->oc_hi, ne * sizeof(double)));
+    MGAR_CUDA(cudaMalloc(&c->r, n * sizeof(double)));
+    MGAR_CUDA(cudaMalloc(&c->z, n * sizeof(double)));
+    MGAR_CUDA(cudaMalloc(&c->pv, n * sizeof(double)));
+    MGAR_CUDA(cudaMalloc(&c->Ap, n * sizeof(double)));
+    MGAR_CUDA(cudaMalloc(&c->tm, n * sizeof(double)));
+    MGAR_CUDA(cudaMalloc(&c->tmp_dc, ne * sizeof(double)));
+    MGAR_CUDA(cudaMalloc(&c->R, (size_t)P.m * n * sizeof(double)));
+    MGAR_CUDA(cudaMalloc(&c->W, (size_t)P.m * n * sizeof(double)));
+    if (P.precision == MGAR_MIXED) {
+      MGAR_CUDA(cudaMalloc(&c->ke_f, ne * sizeof(float)));
+      MGAR_CUDA(cudaMalloc(&c->ke0_f, ne * sizeof(float)));
+      MGAR_CUDA(cudaMalloc(&c->b32, n * sizeof(float)));
+      MGAR_CUDA(cudaMalloc(&c->x32, n * sizeof(float)));
+    }
+    MGAR_CUDA(cudaMalloc(&c->partials, (size_t)8 * maxb * sizeof(double)));
+    MGAR_CUDA(cudaMalloc(&c->counter, 8 * sizeof(unsigned int)));
+    MGAR_CUDA(cudaMemset(c->counter, 0, 8 * sizeof(unsigned int)));
+    MGAR_CUDA(cudaMalloc(&c->dsc, S_COUNT * sizeof(double)));
+    MGAR_CUDA(cudaMemset(c->dsc, 0, S_COUNT * sizeof(double)));
+    MGAR_CUDA(cudaMallocHost(&c->hsc, S_COUNT * sizeof(double)));
+    MGAR_CUDA(cudaMalloc(&c->derr, sizeof(int)));
+    MGAR_CUDA(cudaMemset(c->derr, 0, sizeof(int)));
+
+    // problem data: q is zeroed on fixed nodes
+    std::vector<double> qh(q, q + n);
+    double qq = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+      if (fixed_mask[i]) qh[i] = 0.0;
+      qq += qh[i] * qh[i];
+    }
+    c->qnorm = std::sqrt(qq);
+    require(c->qnorm > 0.0 && std::isfinite(c->qnorm), MGAR_ERR_ARG, "load vector is zero");
+    std::vector<uint8_t> fh(fixed_mask, fixed_mask + n);
+    for (auto& v : fh) v = v ? 1 : 0;
+    MGAR_CUDA(cudaMemcpy(c->fixed, fh.data(), n, cudaMemcpyHostToDevice));
+    MGAR_CUDA(cudaMemcpy(c->q, qh.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+    alloc_hierarchy(*c);
+    setup_filter(*c);
+  } catch (const Error& e) {
+    g_create_error = e.msg;
+    free_ctx(*c);
+    delete c;
+    return e.code;
+  }
+  *out = reinterpret_cast<mgar_t>(c);
+  return MGAR_OK;
+}
+
+int mgar_destroy(mgar_t h) {
+  if (!h) return MGAR_OK;
+  Ctx* c = reinterpret_cast<Ctx*>(h);
+  free_ctx(*c);
+  delete c;
+  return MGAR_OK;
+}
+
+int mgar_set_stream(mgar_t h, void* stream) {
+  return guarded(h, [&](Ctx& c) {
+    c.stream = reinterpret_cast<cudaStream_t>(stream);
+    return MGAR_OK;
+  });
+}
+
+int mgar_sizes(mgar_t h, int64_t* n_nodes, int64_t* n_elems) {
+  return guarded(h, [&](Ctx& c) {
+    if (n_nodes) *n_nodes = c.n;
+    if (n_elems) *n_elems = c.ne;
+    return MGAR_OK;
+  });
+}
+
+int mgar_filter(mgar_t h, const double* in, double* out, int transpose) {
+  return guarded(h, [&](Ctx& c) {
+    require(in && out && in != out, MGAR_ERR_ARG, "filter: bad pointers");
+    filter(c, in, out, transpose != 0);
+    return MGAR_OK;
+  });
+}
+
+int mgar_set_density(mgar_t h, const double* rho, int is_physical) {
+  return guarded(h, [&](Ctx& c) {
+    require(rho != nullptr, MGAR_ERR_ARG, "set_density: null rho");
+    set_density(c, rho, is_physical != 0);
+    return MGAR_OK;
+  });
+}
+
+int mgar_apply_K(mgar_t h, const double* x, double* y) {
+  return guarded(h, [&](Ctx& c) {
+    require(x && y && x != y, MGAR_ERR_ARG, "apply_K: bad pointers");
+    apply_fine64(c, c.ke, x, y, nullptr);
+    return MGAR_OK;
+  });
+}
+
+int mgar_build_hierarchy(mgar_t h) {
+  return guarded(h, [&](Ctx& c) {
+    build_hierarchy(c);
+    MGAR_CUDA(cudaStreamSynchronize(c.stream));
+    int e = 0;
+    MGAR_CUDA(cudaMemcpy(&e, c.derr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+      MGAR_CUDA(cudaMemset(c.derr, 0, sizeof(int)));
+      c.have_ref = false;
+      throw Error{e, "coarsest factorisation met a non-positive pivot"};
+    }
+    return MGAR_OK;
+  });
+}
+
+int mgar_vcycle(mgar_t h, const double* b, double* x) {
+  return guarded(h, [&](Ctx& c) {
+    require(c.have_ref, MGAR_ERR_STATE, "no hierarchy built");
+    require(b && x && b != x, MGAR_ERR_ARG, "vcycle: bad pointers");
+    if (c.p.precision == MGAR_FP64) {
+      vcycle<double>(c, b, x, false);
+    } else {
+      convert_d2f(c, b, c.b32, c.n);
+      convert_d2f(c, x, c.x32, c.n);
+      vcycle<float>(c, c.b32, c.x32, false);
+      convert_f2d(c, c.x32, x, c.n);
+    }
+    return MGAR_OK;
+  });
+}
+
+int mgar_solve_mgcg(mgar_t h, double* T, int* iters, double* relres) {
+  return guarded(h, [&](Ctx& c) {
+    require(T != nullptr, MGAR_ERR_ARG, "solve_mgcg: null T");
+    int it = 0;
+    double rr = 0.0;
+    const int rc = solve_mgcg(c, T, &it, &rr);
+    if (iters) *iters = it;
+    if (relres) *relres = rr;
+    if (rc == MGAR_ERR_MAXIT) c.err = "MGCG reached cg_max";
+    return rc;
+  });
+}
+
+int mgar_solve_mgar(mgar_t h, const double* T_prev, double* T, double* res, int* accepted) {
+  return guarded(h, [&](Ctx& c) {
+    require(T_prev && T, MGAR_ERR_ARG, "solve_mgar: null pointer");
+    solve_mgar(c, T_prev, T, res, accepted);
+    return MGAR_OK;
+  });
+}
+
+int mgar_sensitivity(mgar_t h, const double* T, double* dc, double* dv, double* compliance) {
+  return guarded(h, [&](Ctx& c) {
+    require(T != nullptr, MGAR_ERR_ARG, "sensitivity: null T");
+    sensitivity(c, T, dc, dv, compliance);
+    return MGAR_OK;
+  });
+}
+
+int mgar_oc_update(mgar_t h, double* rho, const double* dc, double volfrac, double move,
+                   double* lambda, double* change) {
+  return guarded(h, [&](Ctx& c) {
+    require(rho && dc, MGAR_ERR_ARG, "oc_update: null pointer");
+    require(volfrac > 0.0 && volfrac < 1.0 && move > 0.0, MGAR_ERR_ARG, "oc_update: bad volfrac/move");
+    oc_update(c, rho, dc, volfrac, move, lambda, change);
+    return MGAR_OK;
+  });
+}
+
+int mgar_step(mgar_t h, double* rho, double* T, int cycle, mgar_step_info* info) {
+  return guarded(h, [&](Ctx& c) {
+    require(rho && T, MGAR_ERR_ARG, "step: null pointer");
+    mgar_step_info inf = design_cycle(c, rho, T, cycle);
+    if (info) *info = inf;
+    if (inf.status == MGAR_ERR_MAXIT) c.err = "MGCG reached cg_max";
+    return MGAR_OK;
+  });
+}
+
+int mgar_run(mgar_t h, const double* rho_host, int cycles, double* rho_out_host,
+             mgar_step_info* info_host) {
+  return guarded(h, [&](Ctx& c) {
+    require(rho_host && rho_out_host && cycles >= 0, MGAR_ERR_ARG, "run: bad arguments");
+    if (!c.run_rho) {
+      MGAR_CUDA(cudaMalloc(&c.run_rho, c.ne * sizeof(double)));
+      MGAR_CUDA(cudaMalloc(&c.run_T, c.n * sizeof(double)));
+    }
+    MGAR_CUDA(cudaMemcpyAsync(c.run_rho, rho_host, c.ne * sizeof(double), cudaMemcpyHostToDevice,
+                              c.stream));
+    MGAR_CUDA(cudaMemsetAsync(c.run_T, 0, c.n * sizeof(double), c.stream));
+    c.have_ref = false;
+    for (int k = 1; k <= cycles; ++k) {
+      mgar_step_info inf = design_cycle(c, c.run_rho, c.run_T, k);
+      if (info_host) info_host[k - 1] = inf;
+    }
+    MGAR_CUDA(cudaMemcpyAsync(rho_out_host, c.run_rho, c.ne * sizeof(double),
+                              cudaMemcpyDeviceToHost, c.stream));
+    MGAR_CUDA(cudaStreamSynchronize(c.stream));
+    return MGAR_OK;
+  });
+}
+
+int mgar_profile_start(mgar_t h, int kernel_class) {
+  return guarded(h, [&](Ctx& c) {
+    if (!c.prof_ev) {
+      c.prof_ev = new cudaEvent_t[2 * kProfMax]();
+      for (int i = 0; i < 2 * kProfMax; ++i) MGAR_CUDA(cudaEventCreate(&c.prof_ev[i]));
+    }
+    c.prof_class = kernel_class;
+    c.prof_used = 0;
+    return MGAR_OK;
+  });
+}
+
+int mgar_profile_stop(mgar_t h, double* total_ms, int64_t* launches) {
+  return guarded(h, [&](Ctx& c) {
+    MGAR_CUDA(cudaStreamSynchronize(c.stream));
+    double tot = 0.0;
+    for (int i = 0; i < c.prof_used; ++i) {
+      float ms = 0.f;
+      MGAR_CUDA(cudaEventElapsedTime(&ms, c.prof_ev[2 * i], c.prof_ev[2 * i + 1]));
+      tot += ms;
+    }
+    if (total_ms) *total_ms = tot;
+    if (launches) *launches = c.prof_used;
+    c.prof_class = 0;
+    c.prof_used = 0;
+    return MGAR_OK;
+  });
+}
+
+int64_t mgar_kernel_launches(void) { return g_launches.load(); }
+
+}  // extern "C"

@@ -1,0 +1,482 @@
+// Internal definitions shared by the CUDA translation units of libmgar.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include "../../include/mgar.h"
+
+namespace mgar {
+
+constexpr int kMaxLevels = 14;
+constexpr int kThreads = 256;
+constexpr int kMaxFilterOffsets = 1024;
+constexpr int kMaxM = 8;
+
+// Slots of the device scalar array.
+enum Slot : int {
+  S_RZ0 = 0, S_RZ1 = 1, S_PAP = 2, S_RR = 3, S_TMP = 4, S_NORM = 5,
+  S_OC_LO = 8, S_OC_HI = 9, S_OC_DONE = 10, S_OC_LAM = 11, S_OC_VOL = 12, S_OC_CHANGE = 13,
+  S_OC_STEPS = 14, S_COMPL = 15,
+  S_GS = 16,      // 16..31 Gram-Schmidt coefficients
+  S_KR = 32,      // 32..95 reduced matrix (8x8)
+  S_QR = 96,      // 96..103 reduced right-hand side
+  S_Y = 104,      // 104..111 reduced solution
+  S_RES2 = 112, S_FLAG = 113, S_QQ = 114,
+  S_COUNT = 128
+};
+
+// Element/node counts of one multigrid level.
+struct Dims {
+  int ex, ey, ez;  // elements per axis (ez = 1 in 2D)
+  int NX, NY, NZ;  // nodes per axis (NZ = 1 in 2D)
+  int64_t n, ne;
+};
+
+template <typename Real>
+struct LevelBuf {
+  Real* st = nullptr;    // [S][n] assembled stencil, levels >= 1
+  Real* dinv = nullptr;  // [n] 1/diag, levels >= 1
+  Real* elem = nullptr;  // [ne][nen*nen] Galerkin element matrices, levels >= 1
+  Real* x = nullptr;     // V-cycle iterate (levels >= 1; level 0 uses caller arrays)
+  Real* b = nullptr;     // right-hand side (levels >= 1)
+  Real* t = nullptr;     // smoothing double buffer
+  Real* r = nullptr;     // residual
+};
+
+struct Ctx {
+  mgar_params p{};
+  int dim = 2, nen = 4, S = 9;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int nl = 0;
+  Dims L[kMaxLevels]{};
+  int64_t n = 0, ne = 0;
+  int grid_blocks = 0;    // blocks of grid-stride reduction kernels over nodes
+  int grid_blocks_e = 0;  // ... over elements
+
+  // fine level, problem data
+  uint8_t* fixed = nullptr;
+  double* q = nullptr;
+  double qnorm = 0.0;
+  double* rho_phys = nullptr;
+  double* ke = nullptr;     // current conductivities k_e(rho~)
+  double* ke0 = nullptr;    // reference conductivities (K0)
+  float* ke_f = nullptr;    // FP32 copies (mixed mode)
+  float* ke0_f = nullptr;
+  double* inv_hs = nullptr; // 1 / sum of filter weights
+  int4* f_offs = nullptr;   // filter offsets (dx, dy, dz)
+  double* f_w = nullptr;    // filter weights max(0, r - |d|)
+  double* dv = nullptr;     // F^T (1/E)
+  int n_filter = 0;
+
+  // hierarchy
+  LevelBuf<double> h64[kMaxLevels];
+  LevelBuf<float> h32[kMaxLevels];
+  bool have_ref = false;
+  int nc = 0, bw = 0;
+  double* band = nullptr;   // [nc][bw+1] Cholesky factor (lower band)
+  double* cinv = nullptr;   // [nc][nc] inverse of the coarsest operator
+  float* cinv_f = nullptr;
+  double* tables = nullptr;  // k0 (nen^2) then Galerkin sub-element tables G
+
+  // Krylov / reanalysis vectors
+  double *r = nullptr, *z = nullptr, *pv = nullptr, *Ap = nullptr, *tm = nullptr;
+  double* tmp_dc = nullptr;
+  double *R = nullptr, *W = nullptr;    // [m][n]
+  float *b32 = nullptr, *x32 = nullptr; // mixed-mode level-0 buffers
+  double *tmp_e = nullptr, *oc_s = nullptr, *oc_lo = nullptr, *oc_hi = nullptr;
+
+  // reductions
+  double* partials = nullptr;        // [8][max blocks]
+  unsigned int* counter = nullptr;   // ticket counters [8]
+  double* dsc = nullptr;             // device scalars [S_COUNT]
+  double* hsc = nullptr;             // pinned host mirror [S_COUNT]
+  int* derr = nullptr;               // device error flag
+
+  // whole-run buffers (mgar_run)
+  double *run_rho = nullptr, *run_T = nullptr;
+
+  // instrumentation: CUDA-event timing of one kernel class
+  int prof_class = 0;
+  int prof_used = 0;
+  cudaEvent_t* prof_ev = nullptr;  // [2 * kProfMax]
+};
+
+constexpr int kProfMax = 65536;
+
+// Brackets the launches issued in its scope with two events when the
+// handle is timing kernel class `kc`.
+struct ProfScope {
+  Ctx& c;
+  bool on;
+  ProfScope(Ctx& ctx, int kc) : c(ctx), on(ctx.prof_class == kc && ctx.prof_used < kProfMax) {
+    if (on) cudaEventRecord(c.prof_ev[2 * c.prof_used], c.stream);
+  }
+  ~ProfScope() {
+    if (on) {
+      cudaEventRecord(c.prof_ev[2 * c.prof_used + 1], c.stream);
+      ++c.prof_used;
+    }
+  }
+};
+
+// ---------------------------------------------------------------- errors
+struct Error {
+  int code;
+  std::string msg;
+};
+
+#define MGAR_CUDA(call)                                                              \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess)                                                           \
+      throw ::mgar::Error{MGAR_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+
+// Every kernel launch is followed by MGAR_LAUNCH_CHECK(), which also counts it.
+void count_launch();
+#define MGAR_LAUNCH_CHECK()            \
+  do {                                 \
+    ::mgar::count_launch();            \
+    MGAR_CUDA(cudaGetLastError());     \
+  } while (0)
+
+inline void require(bool ok, int code, const std::string& msg) {
+  if (!ok) throw Error{code, msg};
+}
+
+inline int blocks_for(int64_t n, int threads = kThreads) {
+  int64_t b = (n + threads - 1) / threads;
+  return (int)(b < 1 ? 1 : b);
+}
+
+// ------------------------------------------------------------ reductions
+// Deterministic block sum of N values: each block's partial sums go to
+// partials[k*gridDim.x + blockIdx.x]; the last block to arrive (ticket on
+// *counter) adds them up in block order, resets the ticket, and returns true
+// with the totals in every thread.  Other blocks return false.  Every thread
+// of every block must call it.
+template <int N>
+__device__ __forceinline__ bool block_sum_last(double (&v)[N], double* partials,
+                                               unsigned int* counter, double (&total)[N]) {
+  __shared__ double sh[N][kThreads / 32];
+  __shared__ double tot[N];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    double s = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) sh[k][warp] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += sh[k][w];
+      partials[k * gridDim.x + blockIdx.x] = s;
+    }
+    __threadfence();
+    unsigned int t = atomicAdd(counter, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+      s += ((volatile double*)partials)[k * gridDim.x + b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    __syncthreads();
+    if (lane == 0) sh[k][warp] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) s += sh[k][w];
+      tot[k] = s;
+    }
+    *counter = 0u;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < N; ++k) total[k] = tot[k];
+  return true;
+}
+
+// As block_sum_last, storing the totals to out[0..N) from the last block.
+template <int N>
+__device__ __forceinline__ void block_sum_finish(double (&v)[N], double* partials,
+                                                 unsigned int* counter, double* out) {
+  double t[N];
+  if (block_sum_last<N>(v, partials, counter, t) && threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) out[k] = t[k];
+  }
+}
+
+// Deterministic block max (values >= 0) with the same last-block scheme.
+__device__ __forceinline__ void block_max_finish(double v, double* partials, unsigned int* counter,
+                                                 double* out) {
+  __shared__ double sh[kThreads / 32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s = fmax(s, sh[w]);
+    partials[blockIdx.x] = s;
+    __threadfence();
+    unsigned int t = atomicAdd(counter, 1u);
+    last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double s = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+    s = fmax(s, ((volatile double*)partials)[b]);
+  for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_down_sync(0xffffffffu, s, o));
+  if (lane == 0) sh[warp] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < nw; ++w) m = fmax(m, sh[w]);
+    *out = m;
+    *counter = 0u;
+  }
+}
+
+// ------------------------------------------------------------- operators
+// Matrix-free fine-level operator A = Z K Z + (I - Z) with element
+// conductivities k_e (Eq. 3-4).  With ksub set, the coefficient is
+// k_e - ksub_e and fixed rows give 0 (the operator dK = A - A0).
+//
+// Unit-element conductivity matrices (Galerkin integrals of the shape
+// function gradients):
+//   Q4: k0 = 1/6 * (4 on the diagonal, -1 between edge neighbours, -2
+//       between opposite corners)
+//   H8: k0 = 1/12 * (4 on the diagonal, 0 between edge neighbours, -1
+//       between face- and body-diagonal corners)
+// so the node-centred stencil of K at node i, with the (up to) 2^d
+// elements e around it, is
+//   2D: 4 sum k_e x_i - sum_edges (k_a + k_b) x_j - 2 sum_diag k_e x_j, / 6
+//   3D: 4 sum k_e x_i - sum_facediag (k_a + k_b) x_j - sum_bodydiag k_e x_j, / 12
+template <typename Real>
+struct FineOp {
+  const Real* ke;
+  const Real* ksub;   // nullptr, or reference conductivities for dK
+  const uint8_t* fixed;
+  int ex, ey, ez, NX, NY, NZ;
+  int64_t n;
+};
+
+template <typename Real>
+__device__ __forceinline__ Real ld_x(const Real* x, const uint8_t* fixed, int64_t idx, bool ok) {
+  return (ok && !fixed[idx]) ? x[idx] : Real(0);
+}
+
+template <typename Real>
+__device__ __forceinline__ Real ld_k(const FineOp<Real>& op, int64_t e, bool ok) {
+  if (!ok) return Real(0);
+  Real k = op.ke[e];
+  if (op.ksub) k -= op.ksub[e];
+  return k;
+}
+
+// (A x)_i and diag(A)_i for a 2D node (i, j).
+template <typename Real>
+__device__ __forceinline__ Real fine_row2(const FineOp<Real>& op, const Real* __restrict__ x,
+                                          int i, int j, Real& diag) {
+  const int64_t idx = (int64_t)i + (int64_t)op.NX * j;
+  if (op.fixed[idx]) {
+    diag = Real(1);
+    return op.ksub ? Real(0) : x[idx];
+  }
+  const bool xm = i > 0, xp = i < op.ex, ym = j > 0, yp = j < op.ey;
+  // elements around the node: k[oy][ox], o = 0 -> element at -1, 1 -> at 0
+  const int64_t e00 = (int64_t)(i - 1) + (int64_t)op.ex * (j - 1);
+  const Real k00 = ld_k(op, e00, xm && ym);
+  const Real k01 = ld_k(op, e00 + 1, xp && ym);
+  const Real k10 = ld_k(op, e00 + op.ex, xm && yp);
+  const Real k11 = ld_k(op, e00 + op.ex + 1, xp && yp);
+  const Real ksum = (k00 + k01) + (k10 + k11);
+  const int NX = op.NX;
+  const Real* xr = x;
+  const uint8_t* fx = op.fixed;
+  Real acc = Real(4) * ksum * xr[idx];
+  acc -= (k00 + k10) * ld_x(xr, fx, idx - 1, xm);
+  acc -= (k01 + k11) * ld_x(xr, fx, idx + 1, xp);
+  acc -= (k00 + k01) * ld_x(xr, fx, idx - NX, ym);
+  acc -= (k10 + k11) * ld_x(xr, fx, idx + NX, yp);
+  acc -= Real(2) * k00 * ld_x(xr, fx, idx - NX - 1, xm && ym);
+  acc -= Real(2) * k01 * ld_x(xr, fx, idx - NX + 1, xp && ym);
+  acc -= Real(2) * k10 * ld_x(xr, fx, idx + NX - 1, xm && yp);
+  acc -= Real(2) * k11 * ld_x(xr, fx, idx + NX + 1, xp && yp);
+  diag = ksum * Real(4.0 / 6.0);
+  return acc * Real(1.0 / 6.0);
+}
+
+// (A x)_i and diag(A)_i for a 3D node (i, j, k).
+template <typename Real>
+__device__ __forceinline__ Real fine_row3(const FineOp<Real>& op, const Real* __restrict__ x,
+                                          int i, int j, int k, Real& diag) {
+  const int64_t NX = op.NX, NXY = (int64_t)op.NX * op.NY;
+  const int64_t idx = i + NX * j + NXY * k;
+  if (op.fixed[idx]) {
+    diag = Real(1);
+    return op.ksub ? Real(0) : x[idx];
+  }
+  const bool xm = i > 0, xp = i < op.ex, ym = j > 0, yp = j < op.ey, zm = k > 0, zp = k < op.ez;
+  const int64_t EX = op.ex, EXY = (int64_t)op.ex * op.ey;
+  const int64_t e000 = (i - 1) + EX * (j - 1) + EXY * (k - 1);
+  // kz y x ; index 0 = element on the minus side, 1 = plus side
+  const Real k000 = ld_k(op, e000, xm && ym && zm);
+  const Real k001 = ld_k(op, e000 + 1, xp && ym && zm);
+  const Real k010 = ld_k(op, e000 + EX, xm && yp && zm);
+  const Real k011 = ld_k(op, e000 + EX + 1, xp && yp && zm);
+  const Real k100 = ld_k(op, e000 + EXY, xm && ym && zp);
+  const Real k101 = ld_k(op, e000 + EXY + 1, xp && ym && zp);
+  const Real k110 = ld_k(op, e000 + EXY + EX, xm && yp && zp);
+  const Real k111 = ld_k(op, e000 + EXY + EX + 1, xp && yp && zp);
+  const Real ksum = ((k000 + k001) + (k010 + k011)) + ((k100 + k101) + (k110 + k111));
+  const Real* xr = x;
+  const uint8_t* fx = op.fixed;
+  Real acc = Real(4) * ksum * xr[idx];
+  // face diagonals in the xy plane (dz = 0): shared by the two z-layers
+  acc -= (k000 + k100) * ld_x(xr, fx, idx - 1 - NX, xm && ym);
+  acc -= (k001 + k101) * ld_x(xr, fx, idx + 1 - NX, xp && ym);
+  acc -= (k010 + k110) * ld_x(xr, fx, idx - 1 + NX, xm && yp);
+  acc -= (k011 + k111) * ld_x(xr, fx, idx + 1 + NX, xp && yp);
+  // xz plane (dy = 0)
+  acc -= (k000 + k010) * ld_x(xr, fx, idx - 1 - NXY, xm && zm);
+  acc -= (k001 + k011) * ld_x(xr, fx, idx + 1 - NXY, xp && zm);
+  acc -= (k100 + k110) * ld_x(xr, fx, idx - 1 + NXY, xm && zp);
+  acc -= (k101 + k111) * ld_x(xr, fx, idx + 1 + NXY, xp && zp);
+  // yz plane (dx = 0)
+  acc -= (k000 + k001) * ld_x(xr, fx, idx - NX - NXY, ym && zm);
+  acc -= (k010 + k011) * ld_x(xr, fx, idx + NX - NXY, yp && zm);
+  acc -= (k100 + k101) * ld_x(xr, fx, idx - NX + NXY, ym && zp);
+  acc -= (k110 + k111) * ld_x(xr, fx, idx + NX + NXY, yp && zp);
+  // body diagonals: one element each
+  acc -= k000 * ld_x(xr, fx, idx - 1 - NX - NXY, xm && ym && zm);
+  acc -= k001 * ld_x(xr, fx, idx + 1 - NX - NXY, xp && ym && zm);
+  acc -= k010 * ld_x(xr, fx, idx - 1 + NX - NXY, xm && yp && zm);
+  acc -= k011 * ld_x(xr, fx, idx + 1 + NX - NXY, xp && yp && zm);
+  acc -= k100 * ld_x(xr, fx, idx - 1 - NX + NXY, xm && ym && zp);
+  acc -= k101 * ld_x(xr, fx, idx + 1 - NX + NXY, xp && ym && zp);
+  acc -= k110 * ld_x(xr, fx, idx - 1 + NX + NXY, xm && yp && zp);
+  acc -= k111 * ld_x(xr, fx, idx + 1 + NX + NXY, xp && yp && zp);
+  diag = ksum * Real(4.0 / 12.0);
+  return acc * Real(1.0 / 12.0);
+}
+
+// Assembled (Galerkin) coarse operator: S = 3^d coefficients per node,
+// stored as st[s*n + i] with s = (dx+1) + 3(dy+1) [+ 9(dz+1)].
+template <typename Real>
+struct StencilOp {
+  const Real* st;
+  const Real* dinv;
+  int NX, NY, NZ;
+  int64_t n;
+};
+
+template <typename Real>
+__device__ __forceinline__ Real stencil_row2(const StencilOp<Real>& op, const Real* __restrict__ x,
+                                             int i, int j) {
+  const int64_t idx = (int64_t)i + (int64_t)op.NX * j;
+  Real acc = Real(0);
+#pragma unroll
+  for (int dy = -1; dy <= 1; ++dy) {
+    const int jj = j + dy;
+    if (jj < 0 || jj >= op.NY) continue;
+#pragma unroll
+    for (int dx = -1; dx <= 1; ++dx) {
+      const int ii = i + dx;
+      if (ii < 0 || ii >= op.NX) continue;
+      const int s = (dx + 1) + 3 * (dy + 1);
+      acc += op.st[s * op.n + idx] * x[idx + dx + (int64_t)op.NX * dy];
+    }
+  }
+  return acc;
+}
+
+template <typename Real>
+__device__ __forceinline__ Real stencil_row3(const StencilOp<Real>& op, const Real* __restrict__ x,
+                                             int i, int j, int k) {
+  const int64_t NX = op.NX, NXY = (int64_t)op.NX * op.NY;
+  const int64_t idx = i + NX * j + NXY * k;
+  Real acc = Real(0);
+#pragma unroll
+  for (int dz = -1; dz <= 1; ++dz) {
+    const int kk = k + dz;
+    if (kk < 0 || kk >= op.NZ) continue;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int jj = j + dy;
+      if (jj < 0 || jj >= op.NY) continue;
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int ii = i + dx;
+        if (ii < 0 || ii >= op.NX) continue;
+        const int s = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
+        acc += op.st[s * op.n + idx] * x[idx + dx + NX * dy + NXY * dz];
+      }
+    }
+  }
+  return acc;
+}
+
+// Node coordinates from a flat index.
+__device__ __forceinline__ void node_ijk(int64_t idx, int NX, int NY, int& i, int& j, int& k) {
+  const int64_t plane = (int64_t)NX * NY;
+  k = (int)(idx / plane);
+  const int64_t rem = idx - (int64_t)k * plane;
+  j = (int)(rem / NX);
+  i = (int)(rem - (int64_t)j * NX);
+}
+
+// ------------------------------------------------------- host interfaces
+// hierarchy.cu
+void alloc_hierarchy(Ctx& c);
+void free_hierarchy(Ctx& c);
+void build_hierarchy(Ctx& c);      // K0 <- K, all levels, coarsest factor
+// vcycle.cu
+template <typename Real>
+void vcycle(Ctx& c, const Real* b, Real* x, bool zero_guess);
+void apply_fine64(Ctx& c, const double* ke, const double* x, double* y, double* dot_out);
+void apply_fine32(Ctx& c, const float* ke, const float* x, float* y);
+void apply_dK64(Ctx& c, const double* x, double* y);
+void apply_dK32(Ctx& c, const float* x, float* y);
+void convert_d2f(Ctx& c, const double* a, float* b, int64_t n);
+void convert_f2d(Ctx& c, const float* a, double* b, int64_t n);
+// solvers.cu
+int solve_mgcg(Ctx& c, double* T, int* iters, double* relres);
+void solve_mgar(Ctx& c, const double* T_prev, double* T, double* res, int* accepted);
+void precondition(Ctx& c, const double* r, double* z);
+// reductions
+void dot(Ctx& c, const double* a, const double* b, int64_t n, double* out_dev);
+void fetch_scalars(Ctx& c, int first, int count);
+// design.cu
+void setup_filter(Ctx& c);
+void filter(Ctx& c, const double* in, double* out, bool transpose);
+void set_density(Ctx& c, const double* rho, bool physical);
+void sensitivity(Ctx& c, const double* T, double* dc, double* dv, double* compliance);
+void oc_update(Ctx& c, double* rho, const double* dc, double volfrac, double move, double* lambda,
+               double* change);
+
+}  // namespace mgar

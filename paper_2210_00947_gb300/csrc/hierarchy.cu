@@ -1,0 +1,439 @@
+// Multigrid hierarchy of the reference matrix K0 (Section 2.2, Table 1).
+//
+// Coarse operators are Galerkin products A_{l+1} = P_l^T A_l P_l with
+// P_0 = Z P (no coarse correction reaches a fixed fine node).  They are
+// built element by element: every fine element lies inside exactly one
+// coarse element, and the interpolation onto its nodes uses only that coarse
+// element's nodes, so each coarse element matrix is
+//   sum over its sub-elements s of  P_s^T M_s P_s,
+// with M_s = k_s Z k0 Z on the finest level and the stored element matrix
+// below it.  P_s is the tensor product of 1D 2x2 weights chosen by the
+// position of s inside the coarse element (first half, second half, or the
+// single fine element of a truncated coarse element on an odd axis).
+// Node stencils are then assembled from the element matrices.  The coarsest
+// operator is factorised by a banded Cholesky and inverted explicitly, so the
+// coarse solve of every V-cycle is one small dense product.
+#include "common.cuh"
+
+#include <vector>
+
+namespace mgar {
+
+// 1D interpolation weight of coarse local node c onto fine local node f of a
+// sub-element of position type t (0: first half, 1: second half, 2: the
+// single fine element of a truncated coarse element).
+__host__ __device__ __forceinline__ double w1(int t, int f, int c) {
+  if (t == 0) return f == 0 ? (c == 0 ? 1.0 : 0.0) : 0.5;
+  if (t == 1) return f == 1 ? (c == 1 ? 1.0 : 0.0) : 0.5;
+  return f == c ? 1.0 : 0.0;
+}
+
+template <int DIM>
+__device__ __forceinline__ double pw(const int (&t)[3], int a, int I) {
+  double w = w1(t[0], a & 1, I & 1) * w1(t[1], (a >> 1) & 1, (I >> 1) & 1);
+  if (DIM == 3) w *= w1(t[2], (a >> 2) & 1, (I >> 2) & 1);
+  return w;
+}
+
+// Unit element matrix k0 (Galerkin integral of grad N_a . grad N_b).
+static void unit_element(int dim, double* k) {
+  const int nen = 1 << dim;
+  for (int a = 0; a < nen; ++a)
+    for (int b = 0; b < nen; ++b) {
+      const int d = __builtin_popcount(a ^ b);
+      if (dim == 2) k[a * nen + b] = (d == 0 ? 4.0 : d == 1 ? -1.0 : -2.0) / 6.0;
+      else k[a * nen + b] = (d == 0 ? 4.0 : d == 1 ? 0.0 : -1.0) / 12.0;
+    }
+}
+
+// ------------------------------------------------------------------ kernels
+// Level 0 -> 1: element matrices of A_1 from k_e, one thread per (coarse
+// element, row I).
+template <typename Real, int DIM>
+__global__ void k_galerkin_fine(const Real* __restrict__ ke, const uint8_t* __restrict__ fixed,
+                                Dims f, Dims cd, const double* __restrict__ G,
+                                const double* __restrict__ k0, Real* __restrict__ elem) {
+  constexpr int nen = 1 << DIM;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= cd.ne * nen) return;
+  const int64_t E = tid / nen;
+  const int I = (int)(tid - E * nen);
+  const int cx = (int)(E % cd.ex);
+  const int cy = (int)((E / cd.ex) % cd.ey);
+  const int cz = DIM == 3 ? (int)(E / ((int64_t)cd.ex * cd.ey)) : 0;
+  double out[nen];
+#pragma unroll
+  for (int J = 0; J < nen; ++J) out[J] = 0.0;
+  const int nsub = 1 << DIM;
+  for (int s = 0; s < nsub; ++s) {
+    const int sx = s & 1, sy = (s >> 1) & 1, sz = (s >> 2) & 1;
+    const int fx = 2 * cx + sx, fy = 2 * cy + sy, fz = 2 * cz + sz;
+    if (fx >= f.ex || fy >= f.ey || (DIM == 3 && fz >= f.ez)) continue;
+    int t[3];
+    t[0] = (2 * cx + 1 < f.ex) ? sx : 2;
+    t[1] = (2 * cy + 1 < f.ey) ? sy : 2;
+    t[2] = DIM == 3 ? ((2 * cz + 1 < f.ez) ? sz : 2) : 0;
+    const int64_t e = fx + (int64_t)f.ex * (fy + (int64_t)f.ey * fz);
+    const double k = (double)ke[e];
+    // fixed nodes of the sub-element
+    unsigned fmask = 0;
+#pragma unroll
+    for (int a = 0; a < nen; ++a) {
+      const int64_t nd = (fx + (a & 1)) + (int64_t)f.NX * ((fy + ((a >> 1) & 1)) +
+                                                           (int64_t)f.NY * (fz + ((a >> 2) & 1)));
+      if (fixed[nd]) fmask |= 1u << a;
+    }
+    if (fmask == 0) {
+      const int type = t[0] + 3 * t[1] + 9 * t[2];
+      const double* g = G + (size_t)type * nen * nen + I * nen;
+#pragma unroll
+      for (int J = 0; J < nen; ++J) out[J] += k * g[J];
+    } else {
+      // (Z P_s)^T (k k0) (Z P_s), row I
+      for (int a = 0; a < nen; ++a) {
+        if (fmask & (1u << a)) continue;
+        const double pa = pw<DIM>(t, a, I);
+        if (pa == 0.0) continue;
+        for (int b = 0; b < nen; ++b) {
+          if (fmask & (1u << b)) continue;
+          const double m = k * k0[a * nen + b] * pa;
+#pragma unroll
+          for (int J = 0; J < nen; ++J) out[J] += m * pw<DIM>(t, b, J);
+        }
+      }
+    }
+  }
+  Real* dst = elem + E * nen * nen + I * nen;
+#pragma unroll
+  for (int J = 0; J < nen; ++J) dst[J] = (Real)out[J];
+}
+
+// Level l -> l+1 (l >= 1) from stored element matrices.
+template <typename Real, int DIM>
+__global__ void k_galerkin_coarse(const Real* __restrict__ elem_f, Dims f, Dims cd,
+                                  Real* __restrict__ elem_c) {
+  constexpr int nen = 1 << DIM;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= cd.ne * nen) return;
+  const int64_t E = tid / nen;
+  const int I = (int)(tid - E * nen);
+  const int cx = (int)(E % cd.ex);
+  const int cy = (int)((E / cd.ex) % cd.ey);
+  const int cz = DIM == 3 ? (int)(E / ((int64_t)cd.ex * cd.ey)) : 0;
+  Real out[nen];
+#pragma unroll
+  for (int J = 0; J < nen; ++J) out[J] = Real(0);
+  for (int s = 0; s < nen; ++s) {
+    const int sx = s & 1, sy = (s >> 1) & 1, sz = (s >> 2) & 1;
+    const int fx = 2 * cx + sx, fy = 2 * cy + sy, fz = 2 * cz + sz;
+    if (fx >= f.ex || fy >= f.ey || (DIM == 3 && fz >= f.ez)) continue;
+    int t[3];
+    t[0] = (2 * cx + 1 < f.ex) ? sx : 2;
+    t[1] = (2 * cy + 1 < f.ey) ? sy : 2;
+    t[2] = DIM == 3 ? ((2 * cz + 1 < f.ez) ? sz : 2) : 0;
+    const int64_t e = fx + (int64_t)f.ex * (fy + (int64_t)f.ey * fz);
+    const Real* M = elem_f + e * nen * nen;
+    Real v[nen];
+#pragma unroll
+    for (int b = 0; b < nen; ++b) v[b] = Real(0);
+#pragma unroll
+    for (int a = 0; a < nen; ++a) {
+      const Real pa = (Real)pw<DIM>(t, a, I);
+      if (pa == Real(0)) continue;
+#pragma unroll
+      for (int b = 0; b < nen; ++b) v[b] += pa * M[a * nen + b];
+    }
+#pragma unroll
+    for (int b = 0; b < nen; ++b) {
+#pragma unroll
+      for (int J = 0; J < nen; ++J) {
+        const Real pb = (Real)pw<DIM>(t, b, J);
+        if (pb != Real(0)) out[J] += v[b] * pb;
+      }
+    }
+  }
+  Real* dst = elem_c + E * nen * nen + I * nen;
+#pragma unroll
+  for (int J = 0; J < nen; ++J) dst[J] = out[J];
+}
+
+// Node stencils and inverse diagonal of a level from its element matrices.
+template <typename Real, int DIM>
+__global__ void k_assemble(const Real* __restrict__ elem, Dims d, Real* __restrict__ st,
+                           Real* __restrict__ dinv) {
+  constexpr int nen = 1 << DIM;
+  constexpr int S = DIM == 2 ? 9 : 27;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= d.n) return;
+  int i, j, k;
+  node_ijk(idx, d.NX, d.NY, i, j, k);
+  Real acc[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) acc[s] = Real(0);
+#pragma unroll
+  for (int o = 0; o < nen; ++o) {
+    const int ox = -(o & 1), oy = -((o >> 1) & 1), oz = DIM == 3 ? -((o >> 2) & 1) : 0;
+    const int exi = i + ox, eyi = j + oy, ezi = k + oz;
+    if (exi < 0 || exi >= d.ex || eyi < 0 || eyi >= d.ey) continue;
+    if (DIM == 3 && (ezi < 0 || ezi >= d.ez)) continue;
+    const int64_t e = exi + (int64_t)d.ex * (eyi + (int64_t)d.ey * ezi);
+    const int Iloc = o;  // node position inside the element equals -offset
+    const Real* row = elem + e * nen * nen + Iloc * nen;
+#pragma unroll
+    for (int J = 0; J < nen; ++J) {
+      const int dx = (J & 1) + ox, dy = ((J >> 1) & 1) + oy;
+      const int dz = DIM == 3 ? ((J >> 2) & 1) + oz : 0;
+      const int s = (dx + 1) + 3 * (dy + 1) + (DIM == 3 ? 9 * (dz + 1) : 0);
+      acc[s] += row[J];
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < S; ++s) st[s * d.n + idx] = acc[s];
+  dinv[idx] = Real(1) / acc[S / 2];
+}
+
+// Inverse diagonal of the matrix-free finest operator (1 on fixed nodes).
+template <typename Real, int DIM>
+__global__ void k_fine_dinv(const Real* __restrict__ ke, const uint8_t* __restrict__ fixed, Dims d,
+                            Real* __restrict__ dinv) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= d.n) return;
+  if (fixed[idx]) {
+    dinv[idx] = Real(1);
+    return;
+  }
+  int i, j, k;
+  node_ijk(idx, d.NX, d.NY, i, j, k);
+  Real ks = Real(0);
+  constexpr int nen = 1 << DIM;
+#pragma unroll
+  for (int o = 0; o < nen; ++o) {
+    const int exi = i - (o & 1), eyi = j - ((o >> 1) & 1), ezi = DIM == 3 ? k - ((o >> 2) & 1) : 0;
+    if (exi < 0 || exi >= d.ex || eyi < 0 || eyi >= d.ey) continue;
+    if (DIM == 3 && (ezi < 0 || ezi >= d.ez)) continue;
+    ks += ke[exi + (int64_t)d.ex * (eyi + (int64_t)d.ey * ezi)];
+  }
+  dinv[idx] = Real(1) / (ks * Real(DIM == 2 ? 4.0 / 6.0 : 4.0 / 12.0));
+}
+
+// Lower band of the coarsest operator: band[i*(bw+1) + (j - i + bw)].
+template <typename Real, int DIM>
+__global__ void k_band_fill(const Real* __restrict__ st, Dims d, int bw, double* __restrict__ band) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= d.n) return;
+  int i, j, k;
+  node_ijk(idx, d.NX, d.NY, i, j, k);
+  const int S = DIM == 2 ? 9 : 27;
+  for (int s = 0; s < S; ++s) {
+    const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = DIM == 3 ? s / 9 - 1 : 0;
+    const int ii = i + dx, jj = j + dy, kk = k + dz;
+    if (ii < 0 || ii >= d.NX || jj < 0 || jj >= d.NY || kk < 0 || kk >= d.NZ) continue;
+    const int64_t col = ii + (int64_t)d.NX * (jj + (int64_t)d.NY * kk);
+    if (col > idx) continue;
+    band[idx * (bw + 1) + (col - idx + bw)] = (double)st[s * d.n + idx];
+  }
+}
+
+// Right-looking banded Cholesky in one block.
+__global__ void k_band_cholesky(double* __restrict__ band, int n, int bw, int* __restrict__ err) {
+  __shared__ double piv;
+  __shared__ int bad;
+  const int ld = bw + 1;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) {
+      const double a = band[(int64_t)k * ld + bw];
+      if (!(a > 0.0) || !isfinite(a)) bad = 1;
+      piv = sqrt(a);
+      band[(int64_t)k * ld + bw] = piv;
+    }
+    __syncthreads();
+    if (bad) break;
+    const int last = min(k + bw, n - 1);
+    for (int i = k + 1 + threadIdx.x; i <= last; i += blockDim.x)
+      band[(int64_t)i * ld + (k - i + bw)] /= piv;
+    __syncthreads();
+    const int m = last - k;
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+      const int ii = t / m, jj = t - (t / m) * m;
+      if (jj > ii) continue;
+      const int i = k + 1 + ii, j = k + 1 + jj;
+      band[(int64_t)i * ld + (j - i + bw)] -=
+          band[(int64_t)i * ld + (k - i + bw)] * band[(int64_t)j * ld + (k - j + bw)];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && bad) *err = MGAR_ERR_NOT_SPD;
+}
+
+// Column j of the inverse, one warp per column: forward then backward
+// substitution with the band factor; inv is row-major n x n.
+__global__ void k_band_inverse(const double* __restrict__ band, int n, int bw, double* inv) {
+  const int warps = blockDim.x >> 5;
+  const int col = blockIdx.x * warps + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (col >= n) return;
+  const int ld = bw + 1;
+  for (int i = col; i < n; ++i) {
+    double s = 0.0;
+    for (int p = max(col, i - bw) + lane; p < i; p += 32)
+      s += band[(int64_t)i * ld + (p - i + bw)] * inv[(int64_t)p * n + col];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0)
+      inv[(int64_t)i * n + col] = ((i == col ? 1.0 : 0.0) - s) / band[(int64_t)i * ld + bw];
+    __syncwarp();
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    double s = 0.0;
+    const int last = min(n - 1, i + bw);
+    for (int p = i + 1 + lane; p <= last; p += 32)
+      s += band[(int64_t)p * ld + (i - p + bw)] * inv[(int64_t)p * n + col];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) inv[(int64_t)i * n + col] = (inv[(int64_t)i * n + col] - s) / band[(int64_t)i * ld + bw];
+    __syncwarp();
+  }
+}
+
+__global__ void k_d2f(const double* a, float* b, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+// ------------------------------------------------------------------- host
+template <typename Real>
+static void alloc_levels(Ctx& c, LevelBuf<Real>* h) {
+  const int nen = c.nen;
+  for (int l = 0; l < c.nl; ++l) {
+    const Dims& d = c.L[l];
+    MGAR_CUDA(cudaMalloc(&h[l].dinv, d.n * sizeof(Real)));
+    MGAR_CUDA(cudaMalloc(&h[l].t, d.n * sizeof(Real)));
+    MGAR_CUDA(cudaMalloc(&h[l].r, d.n * sizeof(Real)));
+    if (l >= 1) {
+      MGAR_CUDA(cudaMalloc(&h[l].st, (size_t)c.S * d.n * sizeof(Real)));
+      MGAR_CUDA(cudaMalloc(&h[l].elem, (size_t)d.ne * nen * nen * sizeof(Real)));
+      MGAR_CUDA(cudaMalloc(&h[l].x, d.n * sizeof(Real)));
+      MGAR_CUDA(cudaMalloc(&h[l].b, d.n * sizeof(Real)));
+    }
+  }
+}
+
+template <typename Real>
+static void free_levels(LevelBuf<Real>* h) {
+  for (int l = 0; l < kMaxLevels; ++l) {
+    cudaFree(h[l].dinv);
+    cudaFree(h[l].t);
+    cudaFree(h[l].r);
+    cudaFree(h[l].st);
+    cudaFree(h[l].elem);
+    cudaFree(h[l].x);
+    cudaFree(h[l].b);
+    h[l] = LevelBuf<Real>{};
+  }
+}
+
+void alloc_hierarchy(Ctx& c) {
+  if (c.p.precision == MGAR_FP64) alloc_levels(c, c.h64);
+  else alloc_levels(c, c.h32);
+  const Dims& dc = c.L[c.nl - 1];
+  c.nc = (int)dc.n;
+  c.bw = (c.dim == 2) ? dc.NX + 1 : dc.NX * dc.NY + dc.NX + 1;
+  if (c.bw > c.nc - 1) c.bw = c.nc - 1 > 0 ? c.nc - 1 : 0;
+  MGAR_CUDA(cudaMalloc(&c.band, (size_t)c.nc * (c.bw + 1) * sizeof(double)));
+  MGAR_CUDA(cudaMalloc(&c.cinv, (size_t)c.nc * c.nc * sizeof(double)));
+  if (c.p.precision != MGAR_FP64) MGAR_CUDA(cudaMalloc(&c.cinv_f, (size_t)c.nc * c.nc * sizeof(float)));
+  // constant tables: k0 (nen^2) then G (3^dim * nen^2)
+  const int nen = c.nen, ntypes = c.dim == 2 ? 9 : 27;
+  std::vector<double> k0(nen * nen), G((size_t)ntypes * nen * nen, 0.0);
+  unit_element(c.dim, k0.data());
+  for (int type = 0; type < ntypes; ++type) {
+    const int t[3] = {type % 3, (type / 3) % 3, type / 9};
+    std::vector<double> P(nen * nen);
+    for (int a = 0; a < nen; ++a)
+      for (int I = 0; I < nen; ++I) {
+        double w = w1(t[0], a & 1, I & 1) * w1(t[1], (a >> 1) & 1, (I >> 1) & 1);
+        if (c.dim == 3) w *= w1(t[2], (a >> 2) & 1, (I >> 2) & 1);
+        P[a * nen + I] = w;
+      }
+    for (int I = 0; I < nen; ++I)
+      for (int J = 0; J < nen; ++J) {
+        double s = 0.0;
+        for (int a = 0; a < nen; ++a)
+          for (int b = 0; b < nen; ++b) s += P[a * nen + I] * k0[a * nen + b] * P[b * nen + J];
+        G[(size_t)type * nen * nen + I * nen + J] = s;
+      }
+  }
+  MGAR_CUDA(cudaMalloc(&c.tables, (k0.size() + G.size()) * sizeof(double)));
+  MGAR_CUDA(cudaMemcpy(c.tables, k0.data(), k0.size() * sizeof(double), cudaMemcpyHostToDevice));
+  MGAR_CUDA(cudaMemcpy(c.tables + k0.size(), G.data(), G.size() * sizeof(double),
+                       cudaMemcpyHostToDevice));
+}
+
+void free_hierarchy(Ctx& c) {
+  free_levels(c.h64);
+  free_levels(c.h32);
+  cudaFree(c.band);
+  cudaFree(c.cinv);
+  cudaFree(c.cinv_f);
+  cudaFree(c.tables);
+  c.band = nullptr;
+  c.cinv = nullptr;
+  c.cinv_f = nullptr;
+  c.tables = nullptr;
+}
+
+template <typename Real, int DIM>
+static void build_levels(Ctx& c, const Real* ke0, LevelBuf<Real>* h) {
+  cudaStream_t s = c.stream;
+  const int nen = 1 << DIM;
+  const double* k0 = c.tables;
+  const double* G = c.tables + nen * nen;
+  k_fine_dinv<Real, DIM><<<blocks_for(c.L[0].n), kThreads, 0, s>>>(ke0, c.fixed, c.L[0], h[0].dinv);
+  MGAR_LAUNCH_CHECK();
+  for (int l = 0; l + 1 < c.nl; ++l) {
+    const Dims& f = c.L[l];
+    const Dims& cd = c.L[l + 1];
+    const int64_t work = cd.ne * nen;
+    ProfScope ps(c, l == 0 ? MGAR_KC_GALERKIN0 : -1);
+    if (l == 0)
+      k_galerkin_fine<Real, DIM><<<blocks_for(work), kThreads, 0, s>>>(ke0, c.fixed, f, cd, G, k0,
+                                                                         h[1].elem);
+    else
+      k_galerkin_coarse<Real, DIM><<<blocks_for(work), kThreads, 0, s>>>(h[l].elem, f, cd,
+                                                                           h[l + 1].elem);
+    MGAR_LAUNCH_CHECK();
+    k_assemble<Real, DIM><<<blocks_for(cd.n), kThreads, 0, s>>>(h[l + 1].elem, cd, h[l + 1].st,
+                                                                 h[l + 1].dinv);
+    MGAR_LAUNCH_CHECK();
+  }
+  const Dims& dcst = c.L[c.nl - 1];
+  MGAR_CUDA(cudaMemsetAsync(c.band, 0, (size_t)c.nc * (c.bw + 1) * sizeof(double), s));
+  k_band_fill<Real, DIM><<<blocks_for(dcst.n), kThreads, 0, s>>>(h[c.nl - 1].st, dcst, c.bw, c.band);
+  MGAR_LAUNCH_CHECK();
+  k_band_cholesky<<<1, 512, 0, s>>>(c.band, c.nc, c.bw, c.derr);
+  MGAR_LAUNCH_CHECK();
+  MGAR_CUDA(cudaMemsetAsync(c.cinv, 0, (size_t)c.nc * c.nc * sizeof(double), s));
+  k_band_inverse<<<(c.nc + 3) / 4, 128, 0, s>>>(c.band, c.nc, c.bw, c.cinv);
+  MGAR_LAUNCH_CHECK();
+  if (c.cinv_f) {
+    k_d2f<<<blocks_for((int64_t)c.nc * c.nc), kThreads, 0, s>>>(c.cinv, c.cinv_f, (int64_t)c.nc * c.nc);
+    MGAR_LAUNCH_CHECK();
+  }
+}
+
+void build_hierarchy(Ctx& c) {
+  cudaStream_t s = c.stream;
+  MGAR_CUDA(cudaMemcpyAsync(c.ke0, c.ke, c.ne * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  if (c.p.precision == MGAR_FP64) {
+    if (c.dim == 2) build_levels<double, 2>(c, c.ke0, c.h64);
+    else build_levels<double, 3>(c, c.ke0, c.h64);
+  } else {
+    k_d2f<<<blocks_for(c.ne), kThreads, 0, s>>>(c.ke0, c.ke0_f, c.ne);
+    MGAR_LAUNCH_CHECK();
+    if (c.dim == 2) build_levels<float, 2>(c, c.ke0_f, c.h32);
+    else build_levels<float, 3>(c, c.ke0_f, c.h32);
+  }
+  c.have_ref = true;
+}
+
+}  // namespace mgar

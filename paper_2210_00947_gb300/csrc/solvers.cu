@@ -1,0 +1,304 @@
+// MGCG and MGAR solves of A(rho~) t = q.
+//
+// MGCG (Sections 1 and 3.2): conjugate gradients in FP64 preconditioned by
+// one V-cycle; stop when ||r|| / ||q|| <= eps2 (recursively updated residual)
+// or after cg_max iterations.  The CG scalars stay in device memory; the host
+// reads ||r||^2 once per iteration to decide convergence.
+//
+// MGAR (Eq. 17-21 and 28): r_1 = t_prev; r_i = one V-cycle on the reference
+// hierarchy K0 with right-hand side -dK r_{i-1} and initial guess r_{i-1}
+// (or zero); modified Gram-Schmidt twice in FP64 (vectors below 1e-12 ||r_1||
+// are dropped); W = A R~; K_R = R~^T W, q_R = R~^T q; m x m Cholesky on the
+// device; t~ = R~ y; Res = ||W y - q|| / ||q||.
+#include "common.cuh"
+
+namespace mgar {
+
+// ----------------------------------------------------------------- kernels
+__global__ void k_dot(const double* __restrict__ a, const double* __restrict__ b, int64_t n,
+                      double* partials, unsigned int* counter, double* out) {
+  double v[1] = {0.0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    v[0] += a[i] * b[i];
+  block_sum_finish<1>(v, partials, counter, out);
+}
+
+// r = q - A x with ||r||^2 (A from the current conductivities).
+template <int DIM>
+__global__ void k_residual_norm(FineOp<double> op, const double* __restrict__ q,
+                                const double* __restrict__ x, double* __restrict__ r,
+                                double* partials, unsigned int* counter, double* out) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double v[1] = {0.0};
+  if (idx < op.n) {
+    int i, j, k;
+    node_ijk(idx, op.NX, op.NY, i, j, k);
+    double d;
+    const double ax = DIM == 2 ? fine_row2(op, x, i, j, d) : fine_row3(op, x, i, j, k, d);
+    const double ri = q[idx] - ax;
+    r[idx] = ri;
+    v[0] = ri * ri;
+  }
+  block_sum_finish<1>(v, partials, counter, out);
+}
+
+// alpha = rz / pAp; x += alpha p; r -= alpha Ap; ||r||^2.
+__global__ void k_cg_xr(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+                        const double* __restrict__ Ap, int64_t n, const double* __restrict__ rz,
+                        const double* __restrict__ pap, double* partials, unsigned int* counter,
+                        double* out) {
+  const double alpha = *rz / *pap;
+  double v[1] = {0.0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    const double ri = r[i] - alpha * Ap[i];
+    r[i] = ri;
+    v[0] += ri * ri;
+  }
+  block_sum_finish<1>(v, partials, counter, out);
+}
+
+// p = z + (rz_new / rz_old) p
+__global__ void k_cg_p(double* __restrict__ p, const double* __restrict__ z, int64_t n,
+                       const double* __restrict__ rz_new, const double* __restrict__ rz_old) {
+  const double beta = *rz_new / *rz_old;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = z[i] + beta * p[i];
+}
+
+// v -= coef * u, coef read from device memory
+__global__ void k_axpy_dev(double* __restrict__ v, const double* __restrict__ u, int64_t n,
+                           const double* __restrict__ coef) {
+  const double a = *coef;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    v[i] -= a * u[i];
+}
+
+__global__ void k_scale(double* __restrict__ v, int64_t n, double s) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    v[i] *= s;
+}
+
+__global__ void k_neg_copy(const double* __restrict__ a, double* __restrict__ b, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = a[i];
+}
+
+// Reduced m x m solve (Eq. 19-21): K_R y = q_R by Cholesky, one thread.
+__global__ void k_reduced_solve(double* dsc, int m, int* err) {
+  double L[kMaxM * kMaxM];
+  const double* KR = dsc + S_KR;
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double s = KR[i * kMaxM + j];
+      for (int k = 0; k < j; ++k) s -= L[i * kMaxM + k] * L[j * kMaxM + k];
+      if (i == j) {
+        if (!(s > 0.0)) {
+          *err = MGAR_ERR_NOT_SPD;
+          return;
+        }
+        L[i * kMaxM + i] = sqrt(s);
+      } else {
+        L[i * kMaxM + j] = s / L[j * kMaxM + j];
+      }
+    }
+  double y[kMaxM];
+  for (int i = 0; i < m; ++i) {
+    double s = dsc[S_QR + i];
+    for (int k = 0; k < i; ++k) s -= L[i * kMaxM + k] * y[k];
+    y[i] = s / L[i * kMaxM + i];
+  }
+  for (int i = m - 1; i >= 0; --i) {
+    double s = y[i];
+    for (int k = i + 1; k < m; ++k) s -= L[k * kMaxM + i] * y[k];
+    y[i] = s / L[i * kMaxM + i];
+  }
+  for (int i = 0; i < m; ++i) dsc[S_Y + i] = y[i];
+}
+
+// t = sum_j y_j Q_j ; ||sum_j y_j W_j - q||^2
+__global__ void k_reduced_combine(const double* __restrict__ Q, const double* __restrict__ W,
+                                  const double* __restrict__ q, int64_t n, int m,
+                                  const double* __restrict__ dsc, double* __restrict__ t,
+                                  double* partials, unsigned int* counter, double* out) {
+  double y[kMaxM];
+  for (int j = 0; j < m; ++j) y[j] = dsc[S_Y + j];
+  double v[1] = {0.0};
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double ti = 0.0, wi = 0.0;
+    for (int j = 0; j < m; ++j) {
+      ti += y[j] * Q[(int64_t)j * n + i];
+      wi += y[j] * W[(int64_t)j * n + i];
+    }
+    t[i] = ti;
+    const double d = wi - q[i];
+    v[0] += d * d;
+  }
+  block_sum_finish<1>(v, partials, counter, out);
+}
+
+// -------------------------------------------------------------------- host
+static int red_blocks(Ctx& c) { return c.grid_blocks; }
+
+void dot(Ctx& c, const double* a, const double* b, int64_t n, double* out_dev) {
+  k_dot<<<red_blocks(c), kThreads, 0, c.stream>>>(a, b, n, c.partials, c.counter, out_dev);
+  MGAR_LAUNCH_CHECK();
+}
+
+void fetch_scalars(Ctx& c, int first, int count) {
+  MGAR_CUDA(cudaMemcpyAsync(c.hsc + first, c.dsc + first, count * sizeof(double),
+                            cudaMemcpyDeviceToHost, c.stream));
+  MGAR_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+static void check_device_error(Ctx& c) {
+  int e = 0;
+  MGAR_CUDA(cudaMemcpyAsync(&e, c.derr, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+  MGAR_CUDA(cudaStreamSynchronize(c.stream));
+  if (e != 0) {
+    MGAR_CUDA(cudaMemsetAsync(c.derr, 0, sizeof(int), c.stream));
+    throw Error{e, e == MGAR_ERR_NOT_SPD ? "factorisation met a non-positive pivot"
+                                         : "device error"};
+  }
+}
+
+// z = M r (one V-cycle, zero initial guess) in the handle's precision.
+void precondition(Ctx& c, const double* r, double* z) {
+  if (c.p.precision == MGAR_FP64) {
+    vcycle<double>(c, r, z, true);
+  } else {
+    convert_d2f(c, r, c.b32, c.n);
+    vcycle<float>(c, c.b32, c.x32, true);
+    convert_f2d(c, c.x32, z, c.n);
+  }
+}
+
+template <int DIM>
+static void residual_norm(Ctx& c, const double* x, double* r, double* out) {
+  const Dims& d = c.L[0];
+  FineOp<double> op{c.ke, nullptr, c.fixed, d.ex, d.ey, d.ez, d.NX, d.NY, d.NZ, d.n};
+  k_residual_norm<DIM><<<blocks_for(d.n), kThreads, 0, c.stream>>>(op, c.q, x, r, c.partials,
+                                                                    c.counter, out);
+  MGAR_LAUNCH_CHECK();
+}
+
+int solve_mgcg(Ctx& c, double* T, int* iters, double* relres) {
+  build_hierarchy(c);
+  check_device_error(c);
+  const int64_t n = c.n;
+  if (c.dim == 2) residual_norm<2>(c, T, c.r, c.dsc + S_RR);
+  else residual_norm<3>(c, T, c.r, c.dsc + S_RR);
+  fetch_scalars(c, S_RR, 1);
+  double rel = std::sqrt(c.hsc[S_RR]) / c.qnorm;
+  int it = 0;
+  if (!(rel <= c.p.eps2)) {
+    require(std::isfinite(rel), MGAR_ERR_NONFINITE, "non-finite initial residual");
+    precondition(c, c.r, c.z);
+    int a = S_RZ0, b = S_RZ1;
+    dot(c, c.r, c.z, n, c.dsc + a);
+    MGAR_CUDA(cudaMemcpyAsync(c.pv, c.z, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+    while (it < c.p.cg_max) {
+      apply_fine64(c, c.ke, c.pv, c.Ap, c.dsc + S_PAP);
+      k_cg_xr<<<red_blocks(c), kThreads, 0, c.stream>>>(T, c.r, c.pv, c.Ap, n, c.dsc + a,
+                                                        c.dsc + S_PAP, c.partials, c.counter,
+                                                        c.dsc + S_RR);
+      MGAR_LAUNCH_CHECK();
+      ++it;
+      fetch_scalars(c, S_RR, 1);
+      rel = std::sqrt(c.hsc[S_RR]) / c.qnorm;
+      require(std::isfinite(rel), MGAR_ERR_NONFINITE, "CG breakdown (non-finite residual)");
+      if (rel <= c.p.eps2) break;
+      precondition(c, c.r, c.z);
+      dot(c, c.r, c.z, n, c.dsc + b);
+      k_cg_p<<<red_blocks(c), kThreads, 0, c.stream>>>(c.pv, c.z, n, c.dsc + b, c.dsc + a);
+      MGAR_LAUNCH_CHECK();
+      std::swap(a, b);
+    }
+  }
+  if (iters) *iters = it;
+  if (relres) *relres = rel;
+  return rel <= c.p.eps2 ? MGAR_OK : MGAR_ERR_MAXIT;
+}
+
+void solve_mgar(Ctx& c, const double* T_prev, double* T, double* res, int* accepted) {
+  require(c.have_ref, MGAR_ERR_STATE, "MGAR needs a reference hierarchy (run MGCG first)");
+  const int64_t n = c.n;
+  const int m = c.p.m;
+  const bool zero = c.p.basis_guess == MGAR_GUESS_ZERO;
+  const int rb = red_blocks(c);
+  MGAR_CUDA(cudaMemcpyAsync(c.R, T_prev, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+  // Eq. 17: basis vectors by V-cycles on K0
+  for (int i = 1; i < m; ++i) {
+    const double* prev = c.R + (int64_t)(i - 1) * n;
+    double* ri = c.R + (int64_t)i * n;
+    if (c.p.precision == MGAR_FP64) {
+      apply_dK64(c, prev, c.r);  // c.r = -dK r_{i-1}
+      if (!zero)
+        MGAR_CUDA(cudaMemcpyAsync(ri, prev, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+      vcycle<double>(c, c.r, ri, zero);
+    } else {
+      convert_d2f(c, prev, c.x32, n);
+      apply_dK32(c, c.x32, c.b32);  // b32 = -dK r_{i-1}; x32 keeps r_{i-1} as the guess
+      vcycle<float>(c, c.b32, c.x32, zero);
+      convert_f2d(c, c.x32, ri, n);
+    }
+  }
+  // Eq. 18: orthonormal basis (modified Gram-Schmidt, twice)
+  dot(c, c.R, c.R, n, c.dsc + S_NORM);
+  fetch_scalars(c, S_NORM, 1);
+  const double ref = std::sqrt(c.hsc[S_NORM]);
+  require(std::isfinite(ref), MGAR_ERR_NONFINITE, "non-finite MGAR basis");
+  int kept = 0;
+  for (int i = 0; i < m; ++i) {
+    double* v = c.R + (int64_t)i * n;
+    for (int pass = 0; pass < 2; ++pass)
+      for (int j = 0; j < kept; ++j) {
+        const double* qj = c.R + (int64_t)j * n;
+        dot(c, qj, v, n, c.dsc + S_GS);
+        k_axpy_dev<<<rb, kThreads, 0, c.stream>>>(v, qj, n, c.dsc + S_GS);
+        MGAR_LAUNCH_CHECK();
+      }
+    dot(c, v, v, n, c.dsc + S_NORM);
+    fetch_scalars(c, S_NORM, 1);
+    const double nv = std::sqrt(c.hsc[S_NORM]);
+    require(std::isfinite(nv), MGAR_ERR_NONFINITE, "non-finite MGAR basis");
+    if (nv > 1e-12 * ref && nv > 0.0) {
+      double* dst = c.R + (int64_t)kept * n;
+      if (dst != v)
+        MGAR_CUDA(cudaMemcpyAsync(dst, v, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+      k_scale<<<rb, kThreads, 0, c.stream>>>(dst, n, 1.0 / nv);
+      MGAR_LAUNCH_CHECK();
+      ++kept;
+    }
+  }
+  require(kept > 0, MGAR_ERR_NONFINITE, "MGAR basis vanished");
+  // Eq. 19-21: reduced system
+  for (int j = 0; j < kept; ++j)
+    apply_fine64(c, c.ke, c.R + (int64_t)j * n, c.W + (int64_t)j * n, nullptr);
+  for (int i = 0; i < kept; ++i) {
+    for (int j = 0; j <= i; ++j) {
+      dot(c, c.R + (int64_t)i * n, c.W + (int64_t)j * n, n, c.dsc + S_KR + i * kMaxM + j);
+    }
+    dot(c, c.R + (int64_t)i * n, c.q, n, c.dsc + S_QR + i);
+  }
+  k_reduced_solve<<<1, 1, 0, c.stream>>>(c.dsc, kept, c.derr);
+  MGAR_LAUNCH_CHECK();
+  k_reduced_combine<<<rb, kThreads, 0, c.stream>>>(c.R, c.W, c.q, n, kept, c.dsc, T, c.partials,
+                                                   c.counter, c.dsc + S_RES2);
+  MGAR_LAUNCH_CHECK();
+  check_device_error(c);
+  fetch_scalars(c, S_RES2, 1);
+  const double r = std::sqrt(c.hsc[S_RES2]) / c.qnorm;
+  require(std::isfinite(r), MGAR_ERR_NONFINITE, "non-finite MGAR residual");
+  if (res) *res = r;
+  if (accepted) *accepted = (r <= c.p.eps1) ? 1 : 0;
+}
+
+}  // namespace mgar

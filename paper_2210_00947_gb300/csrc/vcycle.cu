@@ -1,0 +1,352 @@
+// V-cycle x <- MG(A, b, x, P) of Table 1 on the reference hierarchy, plus the
+// fine-level operator applications used by the solvers.
+//
+// Per level (Table 1): pre-smooth with damped Jacobi
+// x <- x + omega D^-1 (b - A x), residual restricted by P^T, coarse
+// correction (recursively one V-cycle with zero initial guess, the coarsest
+// level by its explicit inverse), interpolation x <- x + P x^c, post-smooth.
+// The finest operator is matrix-free from the element conductivities; the
+// coarse ones are assembled 3^d-point stencils.  Every kernel is templated on
+// the working precision (FP64, or FP32 for the mixed preconditioner).
+#include "common.cuh"
+
+namespace mgar {
+
+// ------------------------------------------------------------ row functors
+template <typename Real, int DIM>
+struct FineRow {
+  FineOp<Real> op;
+  __device__ __forceinline__ Real operator()(const Real* __restrict__ x, int64_t idx) const {
+    int i, j, k;
+    node_ijk(idx, op.NX, op.NY, i, j, k);
+    Real d;
+    if (DIM == 2) return fine_row2(op, x, i, j, d);
+    return fine_row3(op, x, i, j, k, d);
+  }
+  __device__ __forceinline__ int64_t size() const { return op.n; }
+};
+
+template <typename Real, int DIM>
+struct StencilRow {
+  StencilOp<Real> op;
+  __device__ __forceinline__ Real operator()(const Real* __restrict__ x, int64_t idx) const {
+    int i, j, k;
+    node_ijk(idx, op.NX, op.NY, i, j, k);
+    if (DIM == 2) return stencil_row2(op, x, i, j);
+    return stencil_row3(op, x, i, j, k);
+  }
+  __device__ __forceinline__ int64_t size() const { return op.n; }
+};
+
+// ----------------------------------------------------------------- kernels
+template <class Row, typename Real>
+__global__ void k_jacobi(Row row, const Real* __restrict__ b, const Real* __restrict__ xin,
+                         Real* __restrict__ xout, const Real* __restrict__ dinv, Real omega) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= row.size()) return;
+  const Real ax = row(xin, idx);
+  xout[idx] = xin[idx] + omega * dinv[idx] * (b[idx] - ax);
+}
+
+template <typename Real>
+__global__ void k_jacobi_zero(const Real* __restrict__ b, Real* __restrict__ x,
+                              const Real* __restrict__ dinv, Real omega, int64_t n) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < n) x[idx] = omega * dinv[idx] * b[idx];
+}
+
+template <class Row, typename Real>
+__global__ void k_residual(Row row, const Real* __restrict__ b, const Real* __restrict__ x,
+                           Real* __restrict__ r) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= row.size()) return;
+  r[idx] = b[idx] - row(x, idx);
+}
+
+// y = A x, optionally with the deterministic sum of x.y into out[0].
+template <class Row, typename Real, bool DOT>
+__global__ void k_apply(Row row, const Real* __restrict__ x, Real* __restrict__ y, Real scale,
+                        double* partials, unsigned int* counter, double* out) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double v[1] = {0.0};
+  if (idx < row.size()) {
+    const Real ax = scale * row(x, idx);
+    y[idx] = ax;
+    if (DOT) v[0] = (double)x[idx] * (double)ax;
+  }
+  if (DOT) block_sum_finish<1>(v, partials, counter, out);
+}
+
+// 1D interpolation taps.  Coarse node I sits at fine node min(2I, nf).
+// Restriction (P^T) gathers from fine nodes 2I (weight 1), 2I-1 and 2I+1
+// (weight 1/2, or 1 for the injected last node nf of an odd axis).
+__device__ __forceinline__ int restrict_taps(int I, int nf, int* idx, float* w) {
+  int c = 0;
+  if (2 * I <= nf) { idx[c] = 2 * I; w[c++] = 1.f; }
+  if (2 * I - 1 >= 1 && 2 * I - 1 <= nf) { idx[c] = 2 * I - 1; w[c++] = (2 * I - 1 < nf) ? 0.5f : 1.f; }
+  if (2 * I + 1 < nf) { idx[c] = 2 * I + 1; w[c++] = 0.5f; }
+  return c;
+}
+
+// Interpolation (P) onto fine node i from coarse nodes.
+__device__ __forceinline__ int prolong_taps(int i, int nf, int* idx, float* w) {
+  if ((i & 1) == 0) { idx[0] = i >> 1; w[0] = 1.f; return 1; }
+  if (i < nf) { idx[0] = (i - 1) >> 1; w[0] = 0.5f; idx[1] = (i + 1) >> 1; w[1] = 0.5f; return 2; }
+  idx[0] = (i + 1) >> 1; w[0] = 1.f; return 1;
+}
+
+template <typename Real, int DIM>
+__global__ void k_restrict(const Real* __restrict__ r, Real* __restrict__ bc, Dims f, Dims cd,
+                           const uint8_t* __restrict__ fixed) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= cd.n) return;
+  int I, J, K;
+  node_ijk(idx, cd.NX, cd.NY, I, J, K);
+  int ix[3], iy[3], iz[3];
+  float wx[3], wy[3], wz[3];
+  const int nx = restrict_taps(I, f.ex, ix, wx);
+  const int ny = restrict_taps(J, f.ey, iy, wy);
+  int nz = 1;
+  iz[0] = 0;
+  wz[0] = 1.f;
+  if (DIM == 3) nz = restrict_taps(K, f.ez, iz, wz);
+  Real acc = Real(0);
+  for (int c = 0; c < nz; ++c)
+    for (int b = 0; b < ny; ++b) {
+      const int64_t base = (int64_t)f.NX * (iy[b] + (int64_t)f.NY * iz[c]);
+      const Real wyz = (Real)(wy[b] * wz[c]);
+      for (int a = 0; a < nx; ++a) {
+        const int64_t fi = base + ix[a];
+        if (fixed && fixed[fi]) continue;
+        acc += (wyz * (Real)wx[a]) * r[fi];
+      }
+    }
+  bc[idx] = acc;
+}
+
+// dst = cur + P xc (fixed fine nodes keep cur); dst may equal cur.
+template <typename Real, int DIM>
+__global__ void k_prolong(const Real* __restrict__ xc, const Real* cur, Real* dst, Dims f, Dims cd,
+                          const uint8_t* __restrict__ fixed) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= f.n) return;
+  if (fixed && fixed[idx]) {
+    dst[idx] = cur[idx];
+    return;
+  }
+  int i, j, k;
+  node_ijk(idx, f.NX, f.NY, i, j, k);
+  int ix[2], iy[2], iz[2];
+  float wx[2], wy[2], wz[2];
+  const int nx = prolong_taps(i, f.ex, ix, wx);
+  const int ny = prolong_taps(j, f.ey, iy, wy);
+  int nz = 1;
+  iz[0] = 0;
+  wz[0] = 1.f;
+  if (DIM == 3) nz = prolong_taps(k, f.ez, iz, wz);
+  Real acc = Real(0);
+  for (int c = 0; c < nz; ++c)
+    for (int b = 0; b < ny; ++b) {
+      const int64_t base = (int64_t)cd.NX * (iy[b] + (int64_t)cd.NY * iz[c]);
+      const Real wyz = (Real)(wy[b] * wz[c]);
+      for (int a = 0; a < nx; ++a) acc += (wyz * (Real)wx[a]) * xc[base + ix[a]];
+    }
+  dst[idx] = cur[idx] + acc;
+}
+
+// x = C b with the explicit inverse of the coarsest operator (FP64 sums).
+template <typename Real>
+__global__ void k_coarse_solve(const double* __restrict__ cinv, const Real* __restrict__ b,
+                               Real* __restrict__ x, int n) {
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  double s = 0.0;
+  for (int j = lane; j < n; j += 32) s += cinv[(int64_t)row * n + j] * (double)b[j];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) x[row] = (Real)s;
+}
+
+__global__ void k_convert_d2f(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+__global__ void k_convert_f2d(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (double)a[i];
+}
+
+// -------------------------------------------------------------------- host
+template <typename Real>
+static LevelBuf<Real>* levels(Ctx& c);
+template <>
+LevelBuf<double>* levels<double>(Ctx& c) { return c.h64; }
+template <>
+LevelBuf<float>* levels<float>(Ctx& c) { return c.h32; }
+
+template <typename Real>
+static const Real* ref_ke(Ctx& c);
+template <>
+const double* ref_ke<double>(Ctx& c) { return c.ke0; }
+template <>
+const float* ref_ke<float>(Ctx& c) { return c.ke0_f; }
+
+template <typename Real, int DIM>
+static FineRow<Real, DIM> fine_row(Ctx& c, const Real* ke, const Real* ksub) {
+  FineRow<Real, DIM> r;
+  const Dims& d = c.L[0];
+  r.op = FineOp<Real>{ke, ksub, c.fixed, d.ex, d.ey, d.ez, d.NX, d.NY, d.NZ, d.n};
+  return r;
+}
+
+template <typename Real, int DIM>
+static StencilRow<Real, DIM> stencil_row(Ctx& c, int l) {
+  StencilRow<Real, DIM> r;
+  const Dims& d = c.L[l];
+  r.op = StencilOp<Real>{levels<Real>(c)[l].st, levels<Real>(c)[l].dinv, d.NX, d.NY, d.NZ, d.n};
+  return r;
+}
+
+// One damped-Jacobi sweep xout = xin + omega D^-1 (b - A xin) on level l.
+template <typename Real, int DIM>
+static void sweep(Ctx& c, int l, const Real* b, const Real* xin, Real* xout) {
+  const Dims& d = c.L[l];
+  LevelBuf<Real>* h = levels<Real>(c);
+  const Real om = (Real)c.p.omega;
+  ProfScope ps(c, l == 0 ? MGAR_KC_SMOOTH0 : -1);
+  if (l == 0)
+    k_jacobi<<<blocks_for(d.n), kThreads, 0, c.stream>>>(fine_row<Real, DIM>(c, ref_ke<Real>(c), nullptr),
+                                                         b, xin, xout, h[0].dinv, om);
+  else
+    k_jacobi<<<blocks_for(d.n), kThreads, 0, c.stream>>>(stencil_row<Real, DIM>(c, l), b, xin, xout,
+                                                         h[l].dinv, om);
+  MGAR_LAUNCH_CHECK();
+}
+
+template <typename Real, int DIM>
+static void residual(Ctx& c, int l, const Real* b, const Real* x, Real* r) {
+  const Dims& d = c.L[l];
+  ProfScope ps(c, l == 0 ? MGAR_KC_RESID0 : -1);
+  if (l == 0)
+    k_residual<<<blocks_for(d.n), kThreads, 0, c.stream>>>(fine_row<Real, DIM>(c, ref_ke<Real>(c), nullptr),
+                                                           b, x, r);
+  else
+    k_residual<<<blocks_for(d.n), kThreads, 0, c.stream>>>(stencil_row<Real, DIM>(c, l), b, x, r);
+  MGAR_LAUNCH_CHECK();
+}
+
+template <typename Real, int DIM>
+static void vcycle_dim(Ctx& c, const Real* b0, Real* x0, bool zero_guess) {
+  LevelBuf<Real>* h = levels<Real>(c);
+  const int nl = c.nl;
+  const Real om = (Real)c.p.omega;
+  Real* cur[kMaxLevels];
+  // downward leg
+  for (int l = 0; l + 1 < nl; ++l) {
+    const Dims& d = c.L[l];
+    const Real* b = l == 0 ? b0 : h[l].b;
+    Real* x = l == 0 ? x0 : h[l].x;
+    Real* other = h[l].t;
+    Real* cu = x;
+    int sweeps = c.p.nu_pre;
+    if (l > 0 || zero_guess) {
+      if (sweeps > 0) {
+        ProfScope ps(c, l == 0 ? MGAR_KC_SMOOTH0 : -1);
+        k_jacobi_zero<<<blocks_for(d.n), kThreads, 0, c.stream>>>(b, x, h[l].dinv, om, d.n);
+        MGAR_LAUNCH_CHECK();
+        --sweeps;
+      } else {
+        MGAR_CUDA(cudaMemsetAsync(x, 0, d.n * sizeof(Real), c.stream));
+      }
+    }
+    for (; sweeps > 0; --sweeps) {
+      Real* dst = (cu == x) ? other : x;
+      sweep<Real, DIM>(c, l, b, cu, dst);
+      cu = dst;
+    }
+    cur[l] = cu;
+    residual<Real, DIM>(c, l, b, cu, h[l].r);
+    k_restrict<Real, DIM><<<blocks_for(c.L[l + 1].n), kThreads, 0, c.stream>>>(
+        h[l].r, h[l + 1].b, d, c.L[l + 1], l == 0 ? c.fixed : nullptr);
+    MGAR_LAUNCH_CHECK();
+  }
+  // coarsest level
+  {
+    const int l = nl - 1;
+    const int rows_per_block = kThreads / 32;
+    k_coarse_solve<Real><<<(c.nc + rows_per_block - 1) / rows_per_block, kThreads, 0, c.stream>>>(
+        c.cinv, h[l].b, h[l].x, c.nc);
+    MGAR_LAUNCH_CHECK();
+  }
+  // upward leg
+  for (int l = nl - 2; l >= 0; --l) {
+    const Dims& d = c.L[l];
+    const Real* b = l == 0 ? b0 : h[l].b;
+    Real* x = l == 0 ? x0 : h[l].x;
+    Real* other = h[l].t;
+    const int post = c.p.nu_post;
+    Real* dst = (post % 2 == 0) ? x : other;
+    k_prolong<Real, DIM><<<blocks_for(d.n), kThreads, 0, c.stream>>>(h[l + 1].x, cur[l], dst, d,
+                                                                      c.L[l + 1],
+                                                                      l == 0 ? c.fixed : nullptr);
+    MGAR_LAUNCH_CHECK();
+    Real* cu = dst;
+    for (int s = 0; s < post; ++s) {
+      Real* nxt = (cu == x) ? other : x;
+      sweep<Real, DIM>(c, l, b, cu, nxt);
+      cu = nxt;
+    }
+  }
+}
+
+template <typename Real>
+void vcycle(Ctx& c, const Real* b, Real* x, bool zero_guess) {
+  if (c.dim == 2) vcycle_dim<Real, 2>(c, b, x, zero_guess);
+  else vcycle_dim<Real, 3>(c, b, x, zero_guess);
+}
+template void vcycle<double>(Ctx&, const double*, double*, bool);
+template void vcycle<float>(Ctx&, const float*, float*, bool);
+
+template <typename Real, int DIM>
+static void apply_dim(Ctx& c, const Real* ke, const Real* ksub, const Real* x, Real* y, Real scale,
+                      double* dot_out) {
+  const Dims& d = c.L[0];
+  auto row = fine_row<Real, DIM>(c, ke, ksub);
+  if (dot_out)
+    k_apply<FineRow<Real, DIM>, Real, true><<<blocks_for(d.n), kThreads, 0, c.stream>>>(
+        row, x, y, scale, c.partials, c.counter, dot_out);
+  else
+    k_apply<FineRow<Real, DIM>, Real, false><<<blocks_for(d.n), kThreads, 0, c.stream>>>(
+        row, x, y, scale, nullptr, nullptr, nullptr);
+  MGAR_LAUNCH_CHECK();
+}
+
+void apply_fine64(Ctx& c, const double* ke, const double* x, double* y, double* dot_out) {
+  ProfScope ps(c, MGAR_KC_APPLY64);
+  if (c.dim == 2) apply_dim<double, 2>(c, ke, nullptr, x, y, 1.0, dot_out);
+  else apply_dim<double, 3>(c, ke, nullptr, x, y, 1.0, dot_out);
+}
+void apply_fine32(Ctx& c, const float* ke, const float* x, float* y) {
+  if (c.dim == 2) apply_dim<float, 2>(c, ke, nullptr, x, y, 1.f, nullptr);
+  else apply_dim<float, 3>(c, ke, nullptr, x, y, 1.f, nullptr);
+}
+// y = -(A - A0) x
+void apply_dK64(Ctx& c, const double* x, double* y) {
+  if (c.dim == 2) apply_dim<double, 2>(c, c.ke, c.ke0, x, y, -1.0, nullptr);
+  else apply_dim<double, 3>(c, c.ke, c.ke0, x, y, -1.0, nullptr);
+}
+void apply_dK32(Ctx& c, const float* x, float* y) {
+  if (c.dim == 2) apply_dim<float, 2>(c, c.ke_f, c.ke0_f, x, y, -1.f, nullptr);
+  else apply_dim<float, 3>(c, c.ke_f, c.ke0_f, x, y, -1.f, nullptr);
+}
+
+void convert_d2f(Ctx& c, const double* a, float* b, int64_t n) {
+  k_convert_d2f<<<blocks_for(n), kThreads, 0, c.stream>>>(a, b, n);
+  MGAR_LAUNCH_CHECK();
+}
+void convert_f2d(Ctx& c, const float* a, double* b, int64_t n) {
+  k_convert_f2d<<<blocks_for(n), kThreads, 0, c.stream>>>(a, b, n);
+  MGAR_LAUNCH_CHECK();
+}
+
+}  // namespace mgar
