@@ -18,6 +18,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIB_DIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIB_DIR, "libmgar.so")
+# Debug build with bounds checks on computed indices (MGAR_CHECKED): every
+# unit compiled as one, so the fault record is a single device variable.
+LIB_CHECKED = os.path.join(LIB_DIR, "libmgar_checked.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
@@ -76,5 +79,25 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return LIB
 
 
+def build_checked() -> str:
+    """Compile the bounds-checked debug library libmgar_checked.so."""
+    nvcc = _nvcc()
+    os.makedirs(BUILD_DIR, exist_ok=True)
+    os.makedirs(LIB_DIR, exist_ok=True)
+    unity = os.path.join(BUILD_DIR, "unity_checked.cu")
+    with open(unity, "w") as f:
+        for src in _sources():
+            f.write(f'#include "{src}"\n')
+    cmd = [nvcc, *ARCH, *FLAGS, "-DMGAR_CHECKED", "-I", CSRC, "-shared", "-o", LIB_CHECKED, unity]
+    res = subprocess.run(cmd, capture_output=True, text=True)
+    if res.returncode != 0:
+        raise RuntimeError(f"checked build failed:\n{res.stdout}\n{res.stderr}")
+    return LIB_CHECKED
+
+
 if __name__ == "__main__":
-    print(build(force=True, verbose=True))
+    import sys
+    if len(sys.argv) > 1 and sys.argv[1] == "checked":
+        print(build_checked())
+    else:
+        print(build(force=True, verbose=True))

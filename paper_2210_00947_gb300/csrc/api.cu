@@ -15,18 +15,44 @@ std::atomic<int64_t> g_launches{0};
 
 namespace mgar {
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(int64_t delta) { g_launches.fetch_add(delta, std::memory_order_relaxed); }
+int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace mgar
 
 namespace {
 
 thread_local std::string g_create_error = "no error";
 
+#ifdef MGAR_CHECKED
+// Checked build: report the first out-of-bounds access recorded by CK().
+int ck_report(Ctx& c) {
+  cudaDeviceSynchronize();
+  unsigned long long f[4] = {0, 0, 0, 0};
+  cudaMemcpyFromSymbol(f, g_ck_fault, sizeof(f));
+  if (f[0] == 0) return MGAR_OK;
+  char buf[256];
+  snprintf(buf, sizeof(buf), "bounds check failed at source line %llu: index %lld, bound %lld",
+           f[0], (long long)f[1], (long long)f[2]);
+  fprintf(stderr, "[libmgar checked] %s\n", buf);
+  c.err = buf;
+  const unsigned long long z[4] = {0, 0, 0, 0};
+  cudaMemcpyToSymbol(g_ck_fault, z, sizeof(z));
+  return MGAR_ERR_ARG;
+}
+#endif
+
 template <class F>
 int guarded(mgar_t h, F&& f) {
   Ctx* c = reinterpret_cast<Ctx*>(h);
   if (!c) return MGAR_ERR_ARG;
   try {
+#ifdef MGAR_CHECKED
+    const int rc = f(*c);
+    const int ck = ck_report(*c);
+    return ck != MGAR_OK ? ck : rc;
+#else
     return f(*c);
+#endif
   } catch (const Error& e) {
     c->err = e.msg;
     return e.code;
@@ -37,6 +63,9 @@ int guarded(mgar_t h, F&& f) {
 }
 
 void free_ctx(Ctx& c) {
+  for (auto& g : c.graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
   free_hierarchy(c);
   if (c.prof_ev) {
     for (int i = 0; i < 2 * kProfMax; ++i)
@@ -48,7 +77,7 @@ void free_ctx(Ctx& c) {
   cudaFree(c.run_T);
   void* ptrs[] = {c.fixed, c.q, c.rho_phys, c.ke, c.ke0, c.ke_f, c.ke0_f, c.inv_hs, c.f_offs, c.f_w,
                   c.dv, c.r, c.z, c.pv, c.Ap, c.tm, c.tmp_dc, c.R, c.W, c.b32, c.x32, c.tmp_e, c.oc_s, c.oc_lo,
-                  c.oc_hi, c.partials, c.counter, c.dsc, c.derr};
+                  c.oc_hi, c.oc_s32, c.oc_lo32, c.oc_hi32, c.dv32, c.oc_amb, c.oc_namb, c.partials, c.counter, c.dsc, c.derr};
   for (void* p : ptrs) cudaFree(p);
   if (c.hsc) cudaFreeHost(c.hsc);
 }
@@ -156,6 +185,11 @@ int mgar_create(mgar_t* out, const mgar_params* p, const uint8_t* fixed_mask, co
       d.NZ = c->dim == 3 ? ez + 1 : 1;
       d.n = (int64_t)d.NX * d.NY * d.NZ;
       d.ne = (int64_t)ex * ey * ez;
+      require(d.n < (int64_t(1) << 31) / 32, MGAR_ERR_ARG, "grid too large for 32-bit indexing");
+      d.fNX = FastDiv((uint32_t)d.NX);
+      d.fNXY = FastDiv((uint32_t)(d.NX * d.NY));
+      d.fEX = FastDiv((uint32_t)ex);
+      d.fEXY = FastDiv((uint32_t)(ex * ey));
       ex = (ex + 1) / 2;
       ey = (ey + 1) / 2;
       if (c->dim == 3) ez = (ez + 1) / 2;
@@ -170,6 +204,7 @@ int mgar_create(mgar_t* out, const mgar_params* p, const uint8_t* fixed_mask, co
     c->grid_blocks = (int)std::min<int64_t>(blocks_for(n), 152 * 8);
     c->grid_blocks_e = (int)std::min<int64_t>(blocks_for(ne), 152 * 8);
 
+    MGAR_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
     MGAR_CUDA(cudaMalloc(&c->fixed, n));
     MGAR_CUDA(cudaMalloc(&c->q, n * sizeof(double)));
     MGAR_CUDA(cudaMalloc(&c->rho_phys, ne * sizeof(double)));
@@ -181,6 +216,12 @@ int mgar_create(mgar_t* out, const mgar_params* p, const uint8_t* fixed_mask, co
     MGAR_CUDA(cudaMalloc(&c->oc_s, ne * sizeof(double)));
     MGAR_CUDA(cudaMalloc(&c->oc_lo, ne * sizeof(double)));
     MGAR_CUDA(cudaMalloc(&c->oc_hi, ne * sizeof(double)));
+    MGAR_CUDA(cudaMalloc(&c->oc_s32, ne * sizeof(float)));
+    MGAR_CUDA(cudaMalloc(&c->oc_lo32, ne * sizeof(float)));
+    MGAR_CUDA(cudaMalloc(&c->oc_hi32, ne * sizeof(float)));
+    MGAR_CUDA(cudaMalloc(&c->dv32, ne * sizeof(float)));
+    MGAR_CUDA(cudaMalloc(&c->oc_amb, kOcAmbMax * sizeof(int)));
+    MGAR_CUDA(cudaMalloc(&c->oc_namb, sizeof(int)));
     MGAR_CUDA(cudaMalloc(&c->r, n * sizeof(double)));
     MGAR_CUDA(cudaMalloc(&c->z, n * sizeof(double)));
     MGAR_CUDA(cudaMalloc(&c->pv, n * sizeof(double)));
@@ -195,7 +236,13 @@ int mgar_create(mgar_t* out, const mgar_params* p, const uint8_t* fixed_mask, co
       MGAR_CUDA(cudaMalloc(&c->b32, n * sizeof(float)));
       MGAR_CUDA(cudaMalloc(&c->x32, n * sizeof(float)));
     }
-    MGAR_CUDA(cudaMalloc(&c->partials, (size_t)8 * maxb * sizeof(double)));
+    MGAR_CUDA(cudaMalloc(&c->partials, (size_t)32 * maxb * sizeof(double)));
+#ifdef MGAR_CHECKED
+    {
+      const long long plen = (long long)32 * maxb;
+      MGAR_CUDA(cudaMemcpyToSymbol(g_partials_len, &plen, sizeof(plen)));
+    }
+#endif
     MGAR_CUDA(cudaMalloc(&c->counter, 8 * sizeof(unsigned int)));
     MGAR_CUDA(cudaMemset(c->counter, 0, 8 * sizeof(unsigned int)));
     MGAR_CUDA(cudaMalloc(&c->dsc, S_COUNT * sizeof(double)));

@@ -12,10 +12,39 @@
 
 namespace mgar {
 
+// Bounds checks of computed indices.  In the checked build (MGAR_CHECKED,
+// all units compiled as one) CK(i, n) verifies 0 <= i < n; a failure records
+// the source line, index and bound of the first bad access, which is then
+// skipped, and the API reports it.  In the normal build CK is `true`.
+#ifdef MGAR_CHECKED
+__device__ unsigned long long g_ck_fault[4];
+__device__ __forceinline__ bool ck_fail(long long i, long long n, int line) {
+  if (atomicCAS(&g_ck_fault[0], 0ull, (unsigned long long)line) == 0ull) {
+    g_ck_fault[1] = (unsigned long long)i;
+    g_ck_fault[2] = (unsigned long long)n;
+  }
+  return false;
+}
+#define CK(i, n) (((long long)(i) >= 0 && (long long)(i) < (long long)(n)) ? true : ::mgar::ck_fail((long long)(i), (long long)(n), __LINE__))
+#else
+#define CK(i, n) true
+#endif
+// length of the reduction scratch (checked build)
+#ifdef MGAR_CHECKED
+__device__ long long g_partials_len;
+#else
+constexpr long long g_partials_len = 0;
+#endif
+
 constexpr int kMaxLevels = 14;
 constexpr int kThreads = 256;
 constexpr int kMaxFilterOffsets = 1024;
 constexpr int kMaxM = 8;
+constexpr int kOcCand = 31;      // multisection candidates per pass (5 bits)
+constexpr int kOcPasses = 5;     // FP32 passes: ln-bracket 92 -> 3e-6
+constexpr int kOcAmbMax = 4096;  // ambiguous elements handled by the FP64 finish
+constexpr double kOcMargin = 1e-3;  // ln-bracket widening that absorbs FP32 volume rounding
+constexpr size_t kBandSmemMax = 160 * 1024;  // band factorised in shared memory up to this size
 
 // Slots of the device scalar array.
 enum Slot : int {
@@ -27,14 +56,40 @@ enum Slot : int {
   S_QR = 96,      // 96..103 reduced right-hand side
   S_Y = 104,      // 104..111 reduced solution
   S_RES2 = 112, S_FLAG = 113, S_QQ = 114,
-  S_COUNT = 128
+  S_OC_LA = 116, S_OC_LB = 117, S_OC_MUA = 118, S_OC_MUB = 119, S_OC_C = 120, S_OC_B = 121,
+  S_OC_MU = 122, S_OC_FAIL = 123,
+  S_OC_CAND = 128,  // 128..158 multisection candidates
+  S_COUNT = 160
 };
 
-// Element/node counts of one multigrid level.
+// Unsigned division by an invariant divisor d >= 1 for numerators below
+// 2^31, by multiply-high and shift (Granlund and Montgomery, "Division by
+// invariant integers using multiplication", 1994): with l = ceil(log2 d)
+// and m = floor(2^32 (2^l - d) / d) + 1, n / d = (umulhi(m, n) + n) >> l.
+struct FastDiv {
+  uint32_t d = 1, m = 1, l = 0;
+  FastDiv() = default;
+  explicit FastDiv(uint32_t div) : d(div) {
+    l = 0;
+    while ((1ull << l) < div) ++l;
+    m = (uint32_t)((((1ull << 32) * ((1ull << l) - div)) / div) + 1);
+  }
+  __host__ __device__ __forceinline__ uint32_t div(uint32_t n) const {
+#ifdef __CUDA_ARCH__
+    return (__umulhi(m, n) + n) >> l;
+#else
+    return (uint32_t)((((uint64_t)m * n) >> 32) + n) >> l;
+#endif
+  }
+};
+
+// Element/node counts of one multigrid level.  Indices are 32-bit: the
+// library refuses grids with 2^31 / 32 nodes or more.
 struct Dims {
   int ex, ey, ez;  // elements per axis (ez = 1 in 2D)
   int NX, NY, NZ;  // nodes per axis (NZ = 1 in 2D)
   int64_t n, ne;
+  FastDiv fNX, fNXY, fEX, fEXY;  // node row / plane, element row / plane
 };
 
 template <typename Real>
@@ -80,6 +135,7 @@ struct Ctx {
   bool have_ref = false;
   int nc = 0, bw = 0;
   double* band = nullptr;   // [nc][bw+1] Cholesky factor (lower band)
+  double* rdiag = nullptr;  // [nc] reciprocals of the factor's diagonal
   double* cinv = nullptr;   // [nc][nc] inverse of the coarsest operator
   float* cinv_f = nullptr;
   double* tables = nullptr;  // k0 (nen^2) then Galerkin sub-element tables G
@@ -90,6 +146,9 @@ struct Ctx {
   double *R = nullptr, *W = nullptr;    // [m][n]
   float *b32 = nullptr, *x32 = nullptr; // mixed-mode level-0 buffers
   double *tmp_e = nullptr, *oc_s = nullptr, *oc_lo = nullptr, *oc_hi = nullptr;
+  float *oc_s32 = nullptr, *oc_lo32 = nullptr, *oc_hi32 = nullptr, *dv32 = nullptr;
+  int *oc_amb = nullptr, *oc_namb = nullptr;
+  int64_t oc_fallbacks = 0;
 
   // reductions
   double* partials = nullptr;        // [8][max blocks]
@@ -100,6 +159,21 @@ struct Ctx {
 
   // whole-run buffers (mgar_run)
   double *run_rho = nullptr, *run_T = nullptr;
+
+  // CUDA graphs of fixed launch sequences (V-cycles), captured on cap_stream
+  // once and replayed on stream; all buffers they touch live as long as the
+  // handle, so a graph stays valid across hierarchy rebuilds.
+  struct GraphEntry {
+    int kind = -1;
+    const void* a = nullptr;
+    const void* b = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;
+  };
+  static constexpr int kGraphs = 16;
+  GraphEntry graphs[kGraphs];
+  bool use_graphs = true;
+  cudaStream_t cap_stream = nullptr;
 
   // instrumentation: CUDA-event timing of one kernel class
   int prof_class = 0;
@@ -140,6 +214,8 @@ struct Error {
 
 // Every kernel launch is followed by MGAR_LAUNCH_CHECK(), which also counts it.
 void count_launch();
+void count_launches(int64_t delta);
+int64_t launches_so_far();
 #define MGAR_LAUNCH_CHECK()            \
   do {                                 \
     ::mgar::count_launch();            \
@@ -181,7 +257,7 @@ __device__ __forceinline__ bool block_sum_last(double (&v)[N], double* partials,
     for (int k = 0; k < N; ++k) {
       double s = 0.0;
       for (int w = 0; w < nw; ++w) s += sh[k][w];
-      partials[k * gridDim.x + blockIdx.x] = s;
+      if (CK(k * gridDim.x + blockIdx.x, g_partials_len)) partials[k * gridDim.x + blockIdx.x] = s;
     }
     __threadfence();
     unsigned int t = atomicAdd(counter, 1u);
@@ -239,7 +315,7 @@ __device__ __forceinline__ void block_max_finish(double v, double* partials, uns
   if (threadIdx.x == 0) {
     double s = 0.0;
     for (int w = 0; w < nw; ++w) s = fmax(s, sh[w]);
-    partials[blockIdx.x] = s;
+    if (CK(blockIdx.x, g_partials_len)) partials[blockIdx.x] = s;
     __threadfence();
     unsigned int t = atomicAdd(counter, 1u);
     last = (t == gridDim.x - 1);
@@ -282,34 +358,41 @@ struct FineOp {
   const Real* ksub;   // nullptr, or reference conductivities for dK
   const uint8_t* fixed;
   int ex, ey, ez, NX, NY, NZ;
-  int64_t n;
+  int n;
+  FastDiv fNX, fNXY;
 };
 
+// Neighbour loads never form an out-of-range address, even speculatively:
+// a neighbour outside the grid is read at a clamped valid index and its
+// value discarded.
 template <typename Real>
-__device__ __forceinline__ Real ld_x(const Real* x, const uint8_t* fixed, int64_t idx, bool ok) {
-  return (ok && !fixed[idx]) ? x[idx] : Real(0);
+__device__ __forceinline__ Real ld_x(const Real* x, const uint8_t* fixed, int idx, bool ok, int n) {
+  const int j = (ok && CK(idx, n)) ? idx : 0;
+  const Real v = x[j];
+  return (ok && !fixed[j]) ? v : Real(0);
 }
 
 template <typename Real>
-__device__ __forceinline__ Real ld_k(const FineOp<Real>& op, int64_t e, bool ok) {
-  if (!ok) return Real(0);
-  Real k = op.ke[e];
-  if (op.ksub) k -= op.ksub[e];
-  return k;
+__device__ __forceinline__ Real ld_k(const FineOp<Real>& op, int e, bool ok) {
+  const int ee = (ok && CK(e, op.ex * op.ey * op.ez)) ? e : 0;
+  Real k = op.ke[ee];
+  if (op.ksub) k -= op.ksub[ee];
+  return ok ? k : Real(0);
 }
 
 // (A x)_i and diag(A)_i for a 2D node (i, j).
 template <typename Real>
 __device__ __forceinline__ Real fine_row2(const FineOp<Real>& op, const Real* __restrict__ x,
                                           int i, int j, Real& diag) {
-  const int64_t idx = (int64_t)i + (int64_t)op.NX * j;
+  const int idx = i + op.NX * j;
+  if (!CK(idx, op.n)) return Real(0);
   if (op.fixed[idx]) {
     diag = Real(1);
     return op.ksub ? Real(0) : x[idx];
   }
   const bool xm = i > 0, xp = i < op.ex, ym = j > 0, yp = j < op.ey;
   // elements around the node: k[oy][ox], o = 0 -> element at -1, 1 -> at 0
-  const int64_t e00 = (int64_t)(i - 1) + (int64_t)op.ex * (j - 1);
+  const int e00 = (i - 1) + op.ex * (j - 1);
   const Real k00 = ld_k(op, e00, xm && ym);
   const Real k01 = ld_k(op, e00 + 1, xp && ym);
   const Real k10 = ld_k(op, e00 + op.ex, xm && yp);
@@ -319,14 +402,14 @@ __device__ __forceinline__ Real fine_row2(const FineOp<Real>& op, const Real* __
   const Real* xr = x;
   const uint8_t* fx = op.fixed;
   Real acc = Real(4) * ksum * xr[idx];
-  acc -= (k00 + k10) * ld_x(xr, fx, idx - 1, xm);
-  acc -= (k01 + k11) * ld_x(xr, fx, idx + 1, xp);
-  acc -= (k00 + k01) * ld_x(xr, fx, idx - NX, ym);
-  acc -= (k10 + k11) * ld_x(xr, fx, idx + NX, yp);
-  acc -= Real(2) * k00 * ld_x(xr, fx, idx - NX - 1, xm && ym);
-  acc -= Real(2) * k01 * ld_x(xr, fx, idx - NX + 1, xp && ym);
-  acc -= Real(2) * k10 * ld_x(xr, fx, idx + NX - 1, xm && yp);
-  acc -= Real(2) * k11 * ld_x(xr, fx, idx + NX + 1, xp && yp);
+  acc -= (k00 + k10) * ld_x(xr, fx, idx - 1, xm, op.n);
+  acc -= (k01 + k11) * ld_x(xr, fx, idx + 1, xp, op.n);
+  acc -= (k00 + k01) * ld_x(xr, fx, idx - NX, ym, op.n);
+  acc -= (k10 + k11) * ld_x(xr, fx, idx + NX, yp, op.n);
+  acc -= Real(2) * k00 * ld_x(xr, fx, idx - NX - 1, xm && ym, op.n);
+  acc -= Real(2) * k01 * ld_x(xr, fx, idx - NX + 1, xp && ym, op.n);
+  acc -= Real(2) * k10 * ld_x(xr, fx, idx + NX - 1, xm && yp, op.n);
+  acc -= Real(2) * k11 * ld_x(xr, fx, idx + NX + 1, xp && yp, op.n);
   diag = ksum * Real(4.0 / 6.0);
   return acc * Real(1.0 / 6.0);
 }
@@ -335,15 +418,16 @@ __device__ __forceinline__ Real fine_row2(const FineOp<Real>& op, const Real* __
 template <typename Real>
 __device__ __forceinline__ Real fine_row3(const FineOp<Real>& op, const Real* __restrict__ x,
                                           int i, int j, int k, Real& diag) {
-  const int64_t NX = op.NX, NXY = (int64_t)op.NX * op.NY;
-  const int64_t idx = i + NX * j + NXY * k;
+  const int NX = op.NX, NXY = op.NX * op.NY;
+  const int idx = i + NX * j + NXY * k;
+  if (!CK(idx, op.n)) return Real(0);
   if (op.fixed[idx]) {
     diag = Real(1);
     return op.ksub ? Real(0) : x[idx];
   }
   const bool xm = i > 0, xp = i < op.ex, ym = j > 0, yp = j < op.ey, zm = k > 0, zp = k < op.ez;
-  const int64_t EX = op.ex, EXY = (int64_t)op.ex * op.ey;
-  const int64_t e000 = (i - 1) + EX * (j - 1) + EXY * (k - 1);
+  const int EX = op.ex, EXY = op.ex * op.ey;
+  const int e000 = (i - 1) + EX * (j - 1) + EXY * (k - 1);
   // kz y x ; index 0 = element on the minus side, 1 = plus side
   const Real k000 = ld_k(op, e000, xm && ym && zm);
   const Real k001 = ld_k(op, e000 + 1, xp && ym && zm);
@@ -358,29 +442,29 @@ __device__ __forceinline__ Real fine_row3(const FineOp<Real>& op, const Real* __
   const uint8_t* fx = op.fixed;
   Real acc = Real(4) * ksum * xr[idx];
   // face diagonals in the xy plane (dz = 0): shared by the two z-layers
-  acc -= (k000 + k100) * ld_x(xr, fx, idx - 1 - NX, xm && ym);
-  acc -= (k001 + k101) * ld_x(xr, fx, idx + 1 - NX, xp && ym);
-  acc -= (k010 + k110) * ld_x(xr, fx, idx - 1 + NX, xm && yp);
-  acc -= (k011 + k111) * ld_x(xr, fx, idx + 1 + NX, xp && yp);
+  acc -= (k000 + k100) * ld_x(xr, fx, idx - 1 - NX, xm && ym, op.n);
+  acc -= (k001 + k101) * ld_x(xr, fx, idx + 1 - NX, xp && ym, op.n);
+  acc -= (k010 + k110) * ld_x(xr, fx, idx - 1 + NX, xm && yp, op.n);
+  acc -= (k011 + k111) * ld_x(xr, fx, idx + 1 + NX, xp && yp, op.n);
   // xz plane (dy = 0)
-  acc -= (k000 + k010) * ld_x(xr, fx, idx - 1 - NXY, xm && zm);
-  acc -= (k001 + k011) * ld_x(xr, fx, idx + 1 - NXY, xp && zm);
-  acc -= (k100 + k110) * ld_x(xr, fx, idx - 1 + NXY, xm && zp);
-  acc -= (k101 + k111) * ld_x(xr, fx, idx + 1 + NXY, xp && zp);
+  acc -= (k000 + k010) * ld_x(xr, fx, idx - 1 - NXY, xm && zm, op.n);
+  acc -= (k001 + k011) * ld_x(xr, fx, idx + 1 - NXY, xp && zm, op.n);
+  acc -= (k100 + k110) * ld_x(xr, fx, idx - 1 + NXY, xm && zp, op.n);
+  acc -= (k101 + k111) * ld_x(xr, fx, idx + 1 + NXY, xp && zp, op.n);
   // yz plane (dx = 0)
-  acc -= (k000 + k001) * ld_x(xr, fx, idx - NX - NXY, ym && zm);
-  acc -= (k010 + k011) * ld_x(xr, fx, idx + NX - NXY, yp && zm);
-  acc -= (k100 + k101) * ld_x(xr, fx, idx - NX + NXY, ym && zp);
-  acc -= (k110 + k111) * ld_x(xr, fx, idx + NX + NXY, yp && zp);
+  acc -= (k000 + k001) * ld_x(xr, fx, idx - NX - NXY, ym && zm, op.n);
+  acc -= (k010 + k011) * ld_x(xr, fx, idx + NX - NXY, yp && zm, op.n);
+  acc -= (k100 + k101) * ld_x(xr, fx, idx - NX + NXY, ym && zp, op.n);
+  acc -= (k110 + k111) * ld_x(xr, fx, idx + NX + NXY, yp && zp, op.n);
   // body diagonals: one element each
-  acc -= k000 * ld_x(xr, fx, idx - 1 - NX - NXY, xm && ym && zm);
-  acc -= k001 * ld_x(xr, fx, idx + 1 - NX - NXY, xp && ym && zm);
-  acc -= k010 * ld_x(xr, fx, idx - 1 + NX - NXY, xm && yp && zm);
-  acc -= k011 * ld_x(xr, fx, idx + 1 + NX - NXY, xp && yp && zm);
-  acc -= k100 * ld_x(xr, fx, idx - 1 - NX + NXY, xm && ym && zp);
-  acc -= k101 * ld_x(xr, fx, idx + 1 - NX + NXY, xp && ym && zp);
-  acc -= k110 * ld_x(xr, fx, idx - 1 + NX + NXY, xm && yp && zp);
-  acc -= k111 * ld_x(xr, fx, idx + 1 + NX + NXY, xp && yp && zp);
+  acc -= k000 * ld_x(xr, fx, idx - 1 - NX - NXY, xm && ym && zm, op.n);
+  acc -= k001 * ld_x(xr, fx, idx + 1 - NX - NXY, xp && ym && zm, op.n);
+  acc -= k010 * ld_x(xr, fx, idx - 1 + NX - NXY, xm && yp && zm, op.n);
+  acc -= k011 * ld_x(xr, fx, idx + 1 + NX - NXY, xp && yp && zm, op.n);
+  acc -= k100 * ld_x(xr, fx, idx - 1 - NX + NXY, xm && ym && zp, op.n);
+  acc -= k101 * ld_x(xr, fx, idx + 1 - NX + NXY, xp && ym && zp, op.n);
+  acc -= k110 * ld_x(xr, fx, idx - 1 + NX + NXY, xm && yp && zp, op.n);
+  acc -= k111 * ld_x(xr, fx, idx + 1 + NX + NXY, xp && yp && zp, op.n);
   diag = ksum * Real(4.0 / 12.0);
   return acc * Real(1.0 / 12.0);
 }
@@ -392,24 +476,27 @@ struct StencilOp {
   const Real* st;
   const Real* dinv;
   int NX, NY, NZ;
-  int64_t n;
+  int n;
+  FastDiv fNX, fNXY;
 };
 
 template <typename Real>
 __device__ __forceinline__ Real stencil_row2(const StencilOp<Real>& op, const Real* __restrict__ x,
                                              int i, int j) {
-  const int64_t idx = (int64_t)i + (int64_t)op.NX * j;
+  const int idx = i + op.NX * j;
+  // the assembled coefficient of a neighbour outside the grid is zero, so
+  // clamped coordinates give the same sum without branches
   Real acc = Real(0);
 #pragma unroll
   for (int dy = -1; dy <= 1; ++dy) {
-    const int jj = j + dy;
-    if (jj < 0 || jj >= op.NY) continue;
+    const int jj = min(max(j + dy, 0), op.NY - 1);
 #pragma unroll
     for (int dx = -1; dx <= 1; ++dx) {
-      const int ii = i + dx;
-      if (ii < 0 || ii >= op.NX) continue;
+      const int ii = min(max(i + dx, 0), op.NX - 1);
       const int s = (dx + 1) + 3 * (dy + 1);
-      acc += op.st[s * op.n + idx] * x[idx + dx + (int64_t)op.NX * dy];
+      const int nb = ii + op.NX * jj;
+      if (!CK(nb, op.n) || !CK(idx, op.n)) continue;
+      acc += op.st[s * op.n + idx] * x[nb];
     }
   }
   return acc;
@@ -418,36 +505,36 @@ __device__ __forceinline__ Real stencil_row2(const StencilOp<Real>& op, const Re
 template <typename Real>
 __device__ __forceinline__ Real stencil_row3(const StencilOp<Real>& op, const Real* __restrict__ x,
                                              int i, int j, int k) {
-  const int64_t NX = op.NX, NXY = (int64_t)op.NX * op.NY;
-  const int64_t idx = i + NX * j + NXY * k;
+  const int NX = op.NX, NXY = op.NX * op.NY;
+  const int idx = i + NX * j + NXY * k;
   Real acc = Real(0);
 #pragma unroll
   for (int dz = -1; dz <= 1; ++dz) {
-    const int kk = k + dz;
-    if (kk < 0 || kk >= op.NZ) continue;
+    const int kk = min(max(k + dz, 0), op.NZ - 1);
 #pragma unroll
     for (int dy = -1; dy <= 1; ++dy) {
-      const int jj = j + dy;
-      if (jj < 0 || jj >= op.NY) continue;
+      const int jj = min(max(j + dy, 0), op.NY - 1);
 #pragma unroll
       for (int dx = -1; dx <= 1; ++dx) {
-        const int ii = i + dx;
-        if (ii < 0 || ii >= op.NX) continue;
+        const int ii = min(max(i + dx, 0), op.NX - 1);
         const int s = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
-        acc += op.st[s * op.n + idx] * x[idx + dx + NX * dy + NXY * dz];
+        const int nb = ii + NX * jj + NXY * kk;
+        if (!CK(nb, op.n) || !CK(idx, op.n)) continue;
+        acc += op.st[s * op.n + idx] * x[nb];
       }
     }
   }
   return acc;
 }
 
-// Node coordinates from a flat index.
-__device__ __forceinline__ void node_ijk(int64_t idx, int NX, int NY, int& i, int& j, int& k) {
-  const int64_t plane = (int64_t)NX * NY;
-  k = (int)(idx / plane);
-  const int64_t rem = idx - (int64_t)k * plane;
-  j = (int)(rem / NX);
-  i = (int)(rem - (int64_t)j * NX);
+// Coordinates of flat index idx on a row-major (x fastest) box whose rows
+// and planes have the sizes behind fr (row) and fp (plane).
+__device__ __forceinline__ void coords(int idx, const FastDiv& fr, const FastDiv& fp, int& i, int& j,
+                                       int& k) {
+  k = (int)fp.div((uint32_t)idx);
+  const int rem = idx - k * (int)fp.d;
+  j = (int)fr.div((uint32_t)rem);
+  i = rem - j * (int)fr.d;
 }
 
 // ------------------------------------------------------- host interfaces
@@ -479,4 +566,61 @@ void sensitivity(Ctx& c, const double* T, double* dc, double* dv, double* compli
 void oc_update(Ctx& c, double* rho, const double* dc, double volfrac, double move, double* lambda,
                double* change);
 
+}  // namespace mgar
+
+namespace mgar {
+// Run `issue` (a fixed sequence of launches on c.stream) through a cached
+// CUDA graph keyed by (kind, a, b); falls back to direct launches while a
+// kernel class inside it is being timed.
+template <class F>
+void run_graph(Ctx& c, int kind, const void* a, const void* b, bool profiled_inside, F&& issue) {
+  if (!c.use_graphs || profiled_inside) {
+    issue();
+    return;
+  }
+  Ctx::GraphEntry* hit = nullptr;
+  for (auto& g : c.graphs)
+    if (g.exec && g.kind == kind && g.a == a && g.b == b) hit = &g;
+  if (!hit) {
+    Ctx::GraphEntry* slot = nullptr;
+    for (auto& g : c.graphs)
+      if (!g.exec) {
+        slot = &g;
+        break;
+      }
+    if (!slot) {  // cache full: run directly
+      issue();
+      return;
+    }
+    const int64_t before = launches_so_far();
+    MGAR_CUDA(cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaStream_t saved = c.stream;
+    c.stream = c.cap_stream;
+    try {
+      issue();
+    } catch (...) {
+      c.stream = saved;
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(c.cap_stream, &g);
+      if (g) cudaGraphDestroy(g);
+      throw;
+    }
+    c.stream = saved;
+    cudaGraph_t g = nullptr;
+    MGAR_CUDA(cudaStreamEndCapture(c.cap_stream, &g));
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    MGAR_CUDA(e);
+    slot->kind = kind;
+    slot->a = a;
+    slot->b = b;
+    slot->exec = exec;
+    slot->kernels = launches_so_far() - before;
+    count_launches(-slot->kernels);  // captured, not executed
+    hit = slot;
+  }
+  MGAR_CUDA(cudaGraphLaunch(hit->exec, c.stream));
+  count_launches(hit->kernels);
+}
 }  // namespace mgar

@@ -13,29 +13,33 @@ namespace mgar {
 template <bool TRANSPOSE>
 __global__ void k_filter(const double* __restrict__ in, double* __restrict__ out,
                          const double* __restrict__ inv_hs, const int4* __restrict__ offs,
-                         const double* __restrict__ w, int noff, int ex, int ey, int ez) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t ne = (int64_t)ex * ey * ez;
-  if (e >= ne) return;
-  const int i = (int)(e % ex), j = (int)((e / ex) % ey), k = (int)(e / ((int64_t)ex * ey));
+                         const double* __restrict__ w, int noff, Dims d) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int)d.ne) return;
+  const int ex = d.ex, ey = d.ey, ez = d.ez;
+  int i, j, k;
+  coords(e, d.fEX, d.fEXY, i, j, k);
   double acc = 0.0;
   for (int o = 0; o < noff; ++o) {
     const int4 d = offs[o];
     const int ii = i + d.x, jj = j + d.y, kk = k + d.z;
-    if (ii < 0 || ii >= ex || jj < 0 || jj >= ey || kk < 0 || kk >= ez) continue;
-    const int64_t nb = ii + (int64_t)ex * (jj + (int64_t)ey * kk);
-    if (TRANSPOSE) acc += w[o] * (in[nb] * inv_hs[nb]);
-    else acc += w[o] * in[nb];
+    const bool ok = !(ii < 0 || ii >= ex || jj < 0 || jj >= ey || kk < 0 || kk >= ez);
+    const int nb = ok ? ii + ex * (jj + ey * kk) : e;  // valid address either way
+    if (!CK(nb, ex * ey * ez)) continue;
+    const double wo = ok ? w[o] : 0.0;
+    if (TRANSPOSE) acc += wo * (in[nb] * inv_hs[nb]);
+    else acc += wo * in[nb];
   }
   out[e] = TRANSPOSE ? acc : acc * inv_hs[e];
 }
 
 __global__ void k_filter_norm(double* __restrict__ inv_hs, const int4* __restrict__ offs,
-                              const double* __restrict__ w, int noff, int ex, int ey, int ez) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t ne = (int64_t)ex * ey * ez;
-  if (e >= ne) return;
-  const int i = (int)(e % ex), j = (int)((e / ex) % ey), k = (int)(e / ((int64_t)ex * ey));
+                              const double* __restrict__ w, int noff, Dims d) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int)d.ne) return;
+  const int ex = d.ex, ey = d.ey, ez = d.ez;
+  int i, j, k;
+  coords(e, d.fEX, d.fEXY, i, j, k);
   double hs = 0.0;
   for (int o = 0; o < noff; ++o) {
     const int4 d = offs[o];
@@ -63,14 +67,16 @@ template <int DIM>
 __global__ void k_elem_sens(const double* __restrict__ T, const double* __restrict__ rho,
                             double* __restrict__ out, Dims d, double coef, double p) {
   constexpr int nen = 1 << DIM;
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= d.ne) return;
-  const int i = (int)(e % d.ex), j = (int)((e / d.ex) % d.ey);
-  const int k = DIM == 3 ? (int)(e / ((int64_t)d.ex * d.ey)) : 0;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int)d.ne) return;
+  int i, j, k;
+  coords(e, d.fEX, d.fEXY, i, j, k);
   double t[nen];
 #pragma unroll
-  for (int a = 0; a < nen; ++a)
-    t[a] = T[(i + (a & 1)) + (int64_t)d.NX * ((j + ((a >> 1) & 1)) + (int64_t)d.NY * (k + ((a >> 2) & 1)))];
+  for (int a = 0; a < nen; ++a) {
+    const int nd = (i + (a & 1)) + d.NX * ((j + ((a >> 1) & 1)) + d.NY * (k + ((a >> 2) & 1)));
+    t[a] = CK(nd, d.n) ? T[nd] : 0.0;
+  }
   // k0 has zero row sums, so t^T k0 t = -sum_{a<b} k0_ab (t_a - t_b)^2:
   // differences first, no cancellation between large temperatures.
   double energy = 0.0;
@@ -156,11 +162,206 @@ __global__ void k_oc_final(double* __restrict__ rho, const double* __restrict__ 
   if (blockIdx.x == 0 && threadIdx.x == 0) dsc[S_OC_LAM] = lam;
 }
 
+__global__ void k_oc_mu_from_bracket(double* dsc) {
+  const double lam = sqrt(dsc[S_OC_LO] * dsc[S_OC_HI]);
+  dsc[S_OC_MU] = 1.0 / sqrt(lam);
+}
+
 __global__ void k_oc_init(double* dsc, double lo, double hi) {
   dsc[S_OC_LO] = lo;
   dsc[S_OC_HI] = hi;
   dsc[S_OC_DONE] = 0.0;
   dsc[S_OC_STEPS] = 0.0;
+}
+
+// ---- OC solve for mu = 1/sqrt(lambda) without 50 FP64 passes ----------
+// g(mu) = sum_e dv_e clamp(s_e mu, lo_e, hi_e) is continuous, monotone and
+// piecewise linear.  (1) FP32 multisection on ln(mu) narrows the bracket by
+// 32x per pass; (2) one FP64 pass splits the elements into constant
+// (clamped over the whole bracket), linear, and ambiguous (a breakpoint
+// inside the bracket) and sums the first two; (3) one warp bisects in FP64
+// over the few ambiguous elements.  Any failed check falls back to the plain
+// bisection of k_oc_pass.
+
+// candidates mu_k, k = 0..kOcCand-1, at fractions (k+1)/(kOcCand+1) of [La, Lb]
+__device__ __forceinline__ void oc_candidates(double* dsc) {
+  const double La = dsc[S_OC_LA], Lb = dsc[S_OC_LB];
+  for (int k = threadIdx.x; k < kOcCand; k += blockDim.x)
+    dsc[S_OC_CAND + k] = exp(La + (Lb - La) * (double)(k + 1) / (double)(kOcCand + 1));
+}
+
+__global__ void k_oc_start(double* dsc, double La, double Lb) {
+  if (threadIdx.x == 0) {
+    dsc[S_OC_LA] = La;
+    dsc[S_OC_LB] = Lb;
+    dsc[S_OC_FAIL] = 0.0;
+  }
+  __syncthreads();
+  oc_candidates(dsc);
+}
+
+__global__ void k_oc_multisect(const float* __restrict__ s, const float* __restrict__ lo,
+                               const float* __restrict__ hi, const float* __restrict__ dv, int ne,
+                               double volfrac, double* dsc, double* partials,
+                               unsigned int* counter) {
+  __shared__ float mu[kOcCand];
+  if (threadIdx.x < kOcCand) mu[threadIdx.x] = (float)dsc[S_OC_CAND + threadIdx.x];
+  __syncthreads();
+  float acc[kOcCand];
+#pragma unroll
+  for (int k = 0; k < kOcCand; ++k) acc[k] = 0.f;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
+    const float se = s[e], l = lo[e], h = hi[e], d = dv[e];
+#pragma unroll
+    for (int k = 0; k < kOcCand; ++k) acc[k] += d * fminf(fmaxf(se * mu[k], l), h);
+  }
+  double v[kOcCand], tot[kOcCand];
+#pragma unroll
+  for (int k = 0; k < kOcCand; ++k) v[k] = (double)acc[k];
+  const bool last = block_sum_last<kOcCand>(v, partials, counter, tot);
+  if (!last) return;
+  if (threadIdx.x == 0) {
+    int ks = kOcCand;
+    for (int k = 0; k < kOcCand; ++k)
+      if (tot[k] >= volfrac) {
+        ks = k;
+        break;
+      }
+    const double La = dsc[S_OC_LA], Lb = dsc[S_OC_LB];
+    dsc[S_OC_LA] = La + (Lb - La) * (double)ks / (double)(kOcCand + 1);
+    dsc[S_OC_LB] = La + (Lb - La) * (double)(ks + 1) / (double)(kOcCand + 1);
+  }
+  __syncthreads();
+  oc_candidates(dsc);
+}
+
+// Split elements for the bracket [mu_a, mu_b] (ln bracket widened by
+// margin): constant part C, slope B, and the ambiguous list.
+__global__ void k_oc_classify(const double* __restrict__ s, const double* __restrict__ lo,
+                              const double* __restrict__ hi, const double* __restrict__ dv, int ne,
+                              double margin, double Lmin, double Lmax, double* dsc, int* amb,
+                              int* namb, double* partials, unsigned int* counter) {
+  __shared__ double mua, mub;
+  if (threadIdx.x == 0) {
+    const double La = fmax(dsc[S_OC_LA] - margin, Lmin), Lb = fmin(dsc[S_OC_LB] + margin, Lmax);
+    mua = exp(La);
+    mub = exp(Lb);
+    if (blockIdx.x == 0) {
+      dsc[S_OC_MUA] = mua;
+      dsc[S_OC_MUB] = mub;
+    }
+  }
+  __syncthreads();
+  const double a = mua, b = mub;
+  double v[2] = {0.0, 0.0};
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
+    const double se = s[e], l = lo[e], h = hi[e];
+    const double ta = se * a, tb = se * b;
+    if (tb <= l) v[0] += dv[e] * l;
+    else if (ta >= h) v[0] += dv[e] * h;
+    else if (ta >= l && tb <= h) v[1] += dv[e] * se;
+    else {
+      const int slot = atomicAdd(namb, 1);
+      if (slot < kOcAmbMax && CK(slot, kOcAmbMax)) amb[slot] = e;
+    }
+  }
+  double tot[2];
+  if (block_sum_last<2>(v, partials, counter, tot) && threadIdx.x == 0) {
+    dsc[S_OC_C] = tot[0];
+    dsc[S_OC_B] = tot[1];
+  }
+}
+
+// Sort the ambiguous list (bitonic, shared memory), then one warp bisects
+// g(mu) = C + B mu + sum_amb dv clamp(s mu, lo, hi) = volfrac on [mu_a, mu_b].
+__global__ void k_oc_finish(const double* __restrict__ s, const double* __restrict__ lo,
+                            const double* __restrict__ hi, const double* __restrict__ dv, int ne,
+                            double volfrac, double* dsc, int* amb, int* namb_p) {
+  __shared__ int key[kOcAmbMax];
+  const int namb = *namb_p;
+  if (namb > kOcAmbMax) {
+    if (threadIdx.x == 0) dsc[S_OC_FAIL] = 1.0;
+    return;
+  }
+  int size = 1;
+  while (size < namb) size <<= 1;
+  for (int i = threadIdx.x; i < size; i += blockDim.x)
+    if (CK(i, kOcAmbMax)) key[i] = i < namb ? amb[i] : 0x7fffffff;
+  __syncthreads();
+  for (int k = 2; k <= size; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < size; i += blockDim.x) {
+        const int ixj = i ^ j;
+        if (ixj > i && CK(ixj, kOcAmbMax) && CK(i, kOcAmbMax)) {
+          const bool up = (i & k) == 0;
+          const int a = key[i], b = key[ixj];
+          if ((a > b) == up) {
+            key[i] = b;
+            key[ixj] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  const double C = dsc[S_OC_C], B = dsc[S_OC_B];
+  double a = dsc[S_OC_MUA], b = dsc[S_OC_MUB];
+  auto g = [&](double mu) {
+    double acc = 0.0;
+    for (int i = lane; i < namb; i += 32) {
+      if (!CK(i, kOcAmbMax)) continue;
+      const int e = key[i];
+      if (!CK(e, ne)) continue;
+      acc += dv[e] * fmin(fmax(s[e] * mu, lo[e]), hi[e]);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    return C + B * mu + acc;
+  };
+  const double ga = g(a), gb = g(b);
+  if (!(ga <= volfrac && volfrac <= gb)) {
+    if (lane == 0) dsc[S_OC_FAIL] = 1.0;
+    return;
+  }
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (a + b);
+    if (!(mid > a && mid < b)) break;
+    if ((b - a) <= 1e-15 * b) break;
+    if (g(mid) >= volfrac) b = mid;
+    else a = mid;
+  }
+  if (lane == 0) dsc[S_OC_MU] = 0.5 * (a + b);
+}
+
+// rho <- clamp(s mu) for mu = dsc[S_OC_MU]; max |change| into dsc.
+__global__ void k_oc_apply(double* __restrict__ rho, const double* __restrict__ s,
+                           const double* __restrict__ lo, const double* __restrict__ hi, int ne,
+                           double* dsc, double* partials, unsigned int* counter) {
+  const double mu = dsc[S_OC_MU];
+  double ch = 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
+    const double rn = fmin(fmax(s[e] * mu, lo[e]), hi[e]);
+    ch = fmax(ch, fabs(rn - rho[e]));
+    rho[e] = rn;
+  }
+  block_max_finish(ch, partials, counter, dsc + S_OC_CHANGE);
+  if (blockIdx.x == 0 && threadIdx.x == 0) dsc[S_OC_LAM] = 1.0 / (mu * mu);
+}
+
+__global__ void k_d2f_e(const double* __restrict__ a, float* __restrict__ b, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+// FP32 copies of the OC inputs for the multisection.
+__global__ void k_oc_prep32(const double* __restrict__ s, const double* __restrict__ lo,
+                            const double* __restrict__ hi, float* __restrict__ s32,
+                            float* __restrict__ lo32, float* __restrict__ hi32, int ne) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  s32[e] = (float)s[e];
+  lo32[e] = (float)lo[e];
+  hi32[e] = (float)hi[e];
 }
 
 // ------------------------------------------------------------------- host
@@ -187,13 +388,15 @@ void setup_filter(Ctx& c) {
   MGAR_CUDA(cudaMemcpy(c.f_w, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice));
   const Dims& d = c.L[0];
   k_filter_norm<<<blocks_for(c.ne), kThreads, 0, c.stream>>>(c.inv_hs, c.f_offs, c.f_w, c.n_filter,
-                                                             d.ex, d.ey, d.ez);
+                                                             d);
   MGAR_LAUNCH_CHECK();
   // dv = F^T (1/E)
   std::vector<double> ones(c.ne, 1.0 / (double)c.ne);
   MGAR_CUDA(cudaMemcpyAsync(c.tmp_e, ones.data(), c.ne * sizeof(double), cudaMemcpyHostToDevice,
                             c.stream));
   filter(c, c.tmp_e, c.dv, true);
+  k_d2f_e<<<blocks_for(c.ne), kThreads, 0, c.stream>>>(c.dv, c.dv32, (int)c.ne);
+  MGAR_LAUNCH_CHECK();
   MGAR_CUDA(cudaStreamSynchronize(c.stream));
 }
 
@@ -202,10 +405,10 @@ void filter(Ctx& c, const double* in, double* out, bool transpose) {
   ProfScope ps(c, MGAR_KC_FILTER);
   if (transpose)
     k_filter<true><<<blocks_for(c.ne), kThreads, 0, c.stream>>>(in, out, c.inv_hs, c.f_offs, c.f_w,
-                                                                c.n_filter, d.ex, d.ey, d.ez);
+                                                                c.n_filter, d);
   else
     k_filter<false><<<blocks_for(c.ne), kThreads, 0, c.stream>>>(in, out, c.inv_hs, c.f_offs, c.f_w,
-                                                                 c.n_filter, d.ex, d.ey, d.ez);
+                                                                 c.n_filter, d);
   MGAR_LAUNCH_CHECK();
 }
 
@@ -250,25 +453,55 @@ namespace mgar {
 
 void oc_update(Ctx& c, double* rho, const double* dc, double volfrac, double move, double* lambda,
                double* change) {
-  const int64_t ne = c.ne;
+  const int ne = (int)c.ne;
   const int rb = c.grid_blocks_e;
   k_oc_prep<<<blocks_for(ne), kThreads, 0, c.stream>>>(rho, dc, c.dv, c.oc_s, c.oc_lo, c.oc_hi, ne,
                                                        move);
   MGAR_LAUNCH_CHECK();
-  k_oc_init<<<1, 1, 0, c.stream>>>(c.dsc, 1e-40, 1e40);
-  MGAR_LAUNCH_CHECK();
-  const int max_steps = 200, batch = 16;
-  for (int done = 0; done < max_steps; done += batch) {
-    for (int b = 0; b < batch; ++b) {
-      ProfScope ps(c, MGAR_KC_OC);
-      k_oc_pass<<<rb, kThreads, 0, c.stream>>>(c.oc_s, c.oc_lo, c.oc_hi, c.dv, ne, volfrac, 1e-13,
-                                               c.dsc, c.partials, c.counter);
+  // lambda in [1e-40, 1e40]  <=>  ln(mu) in [-20 ln 10, 20 ln 10]
+  const double Lmax = 20.0 * std::log(10.0), Lmin = -Lmax;
+  bool fast_ok = false;
+  {
+    ProfScope ps(c, MGAR_KC_OC);
+    k_oc_prep32<<<blocks_for(ne), kThreads, 0, c.stream>>>(c.oc_s, c.oc_lo, c.oc_hi, c.oc_s32,
+                                                           c.oc_lo32, c.oc_hi32, ne);
+    MGAR_LAUNCH_CHECK();
+    k_oc_start<<<1, 32, 0, c.stream>>>(c.dsc, Lmin, Lmax);
+    MGAR_LAUNCH_CHECK();
+    for (int pass = 0; pass < kOcPasses; ++pass) {
+      k_oc_multisect<<<rb, kThreads, 0, c.stream>>>(c.oc_s32, c.oc_lo32, c.oc_hi32, c.dv32, ne,
+                                                    volfrac, c.dsc, c.partials, c.counter);
       MGAR_LAUNCH_CHECK();
     }
-    fetch_scalars(c, S_OC_DONE, 1);
-    if (c.hsc[S_OC_DONE] != 0.0) break;
+    MGAR_CUDA(cudaMemsetAsync(c.oc_namb, 0, sizeof(int), c.stream));
+    k_oc_classify<<<rb, kThreads, 0, c.stream>>>(c.oc_s, c.oc_lo, c.oc_hi, c.dv, ne, kOcMargin, Lmin,
+                                                 Lmax, c.dsc, c.oc_amb, c.oc_namb, c.partials,
+                                                 c.counter);
+    MGAR_LAUNCH_CHECK();
+    k_oc_finish<<<1, 1024, 0, c.stream>>>(c.oc_s, c.oc_lo, c.oc_hi, c.dv, ne, volfrac, c.dsc,
+                                          c.oc_amb, c.oc_namb);
+    MGAR_LAUNCH_CHECK();
+    fetch_scalars(c, S_OC_FAIL, 1);
+    fast_ok = c.hsc[S_OC_FAIL] == 0.0;
   }
-  k_oc_final<<<rb, kThreads, 0, c.stream>>>(rho, c.oc_s, c.oc_lo, c.oc_hi, ne, c.dsc, c.partials,
+  if (!fast_ok) {
+    // plain bisection on lambda over the whole range
+    k_oc_init<<<1, 1, 0, c.stream>>>(c.dsc, 1e-40, 1e40);
+    MGAR_LAUNCH_CHECK();
+    const int max_steps = 200, batch = 16;
+    for (int done = 0; done < max_steps; done += batch) {
+      for (int b = 0; b < batch; ++b) {
+        k_oc_pass<<<rb, kThreads, 0, c.stream>>>(c.oc_s, c.oc_lo, c.oc_hi, c.dv, ne, volfrac, 1e-13,
+                                                 c.dsc, c.partials, c.counter);
+        MGAR_LAUNCH_CHECK();
+      }
+      fetch_scalars(c, S_OC_DONE, 1);
+      if (c.hsc[S_OC_DONE] != 0.0) break;
+    }
+    k_oc_mu_from_bracket<<<1, 1, 0, c.stream>>>(c.dsc);
+    MGAR_LAUNCH_CHECK();
+  }
+  k_oc_apply<<<rb, kThreads, 0, c.stream>>>(rho, c.oc_s, c.oc_lo, c.oc_hi, ne, c.dsc, c.partials,
                                             c.counter);
   MGAR_LAUNCH_CHECK();
   if (lambda || change) {
@@ -276,6 +509,7 @@ void oc_update(Ctx& c, double* rho, const double* dc, double volfrac, double mov
     if (lambda) *lambda = c.hsc[S_OC_LAM];
     if (change) *change = c.hsc[S_OC_CHANGE];
   }
+  c.oc_fallbacks += fast_ok ? 0 : 1;
 }
 
 }  // namespace mgar

@@ -54,13 +54,12 @@ __global__ void k_galerkin_fine(const Real* __restrict__ ke, const uint8_t* __re
                                 Dims f, Dims cd, const double* __restrict__ G,
                                 const double* __restrict__ k0, Real* __restrict__ elem) {
   constexpr int nen = 1 << DIM;
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= cd.ne * nen) return;
-  const int64_t E = tid / nen;
-  const int I = (int)(tid - E * nen);
-  const int cx = (int)(E % cd.ex);
-  const int cy = (int)((E / cd.ex) % cd.ey);
-  const int cz = DIM == 3 ? (int)(E / ((int64_t)cd.ex * cd.ey)) : 0;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= (int)cd.ne * nen) return;
+  const int E = tid / nen;
+  const int I = tid - E * nen;
+  int cx, cy, cz;
+  coords(E, cd.fEX, cd.fEXY, cx, cy, cz);
   double out[nen];
 #pragma unroll
   for (int J = 0; J < nen; ++J) out[J] = 0.0;
@@ -68,26 +67,27 @@ __global__ void k_galerkin_fine(const Real* __restrict__ ke, const uint8_t* __re
   for (int s = 0; s < nsub; ++s) {
     const int sx = s & 1, sy = (s >> 1) & 1, sz = (s >> 2) & 1;
     const int fx = 2 * cx + sx, fy = 2 * cy + sy, fz = 2 * cz + sz;
-    if (fx >= f.ex || fy >= f.ey || (DIM == 3 && fz >= f.ez)) continue;
+    const bool ok = !(fx >= f.ex || fy >= f.ey || (DIM == 3 && fz >= f.ez));
+    const int e = ok ? fx + f.ex * (fy + f.ey * fz) : 0;  // valid address either way
+    if (!ok || !CK(e, f.ne)) continue;
     int t[3];
     t[0] = (2 * cx + 1 < f.ex) ? sx : 2;
     t[1] = (2 * cy + 1 < f.ey) ? sy : 2;
     t[2] = DIM == 3 ? ((2 * cz + 1 < f.ez) ? sz : 2) : 0;
-    const int64_t e = fx + (int64_t)f.ex * (fy + (int64_t)f.ey * fz);
     const double k = (double)ke[e];
     // fixed nodes of the sub-element
     unsigned fmask = 0;
 #pragma unroll
     for (int a = 0; a < nen; ++a) {
-      const int64_t nd = (fx + (a & 1)) + (int64_t)f.NX * ((fy + ((a >> 1) & 1)) +
-                                                           (int64_t)f.NY * (fz + ((a >> 2) & 1)));
-      if (fixed[nd]) fmask |= 1u << a;
+      const int nd = (fx + (a & 1)) + f.NX * ((fy + ((a >> 1) & 1)) + f.NY * (fz + ((a >> 2) & 1)));
+      if (CK(nd, f.n) && fixed[nd]) fmask |= 1u << a;
     }
     if (fmask == 0) {
       const int type = t[0] + 3 * t[1] + 9 * t[2];
       const double* g = G + (size_t)type * nen * nen + I * nen;
 #pragma unroll
-      for (int J = 0; J < nen; ++J) out[J] += k * g[J];
+      for (int J = 0; J < nen; ++J)
+        if (CK((size_t)type * nen * nen + I * nen + J, (DIM == 2 ? 9 : 27) * nen * nen)) out[J] += k * g[J];
     } else {
       // (Z P_s)^T (k k0) (Z P_s), row I
       for (int a = 0; a < nen; ++a) {
@@ -103,9 +103,10 @@ __global__ void k_galerkin_fine(const Real* __restrict__ ke, const uint8_t* __re
       }
     }
   }
-  Real* dst = elem + E * nen * nen + I * nen;
+  Real* dst = elem + (size_t)E * nen * nen + I * nen;
 #pragma unroll
-  for (int J = 0; J < nen; ++J) dst[J] = (Real)out[J];
+  for (int J = 0; J < nen; ++J)
+    if (CK((size_t)E * nen * nen + I * nen + J, cd.ne * nen * nen)) dst[J] = (Real)out[J];
 }
 
 // Level l -> l+1 (l >= 1) from stored element matrices.
@@ -113,26 +114,26 @@ template <typename Real, int DIM>
 __global__ void k_galerkin_coarse(const Real* __restrict__ elem_f, Dims f, Dims cd,
                                   Real* __restrict__ elem_c) {
   constexpr int nen = 1 << DIM;
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= cd.ne * nen) return;
-  const int64_t E = tid / nen;
-  const int I = (int)(tid - E * nen);
-  const int cx = (int)(E % cd.ex);
-  const int cy = (int)((E / cd.ex) % cd.ey);
-  const int cz = DIM == 3 ? (int)(E / ((int64_t)cd.ex * cd.ey)) : 0;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= (int)cd.ne * nen) return;
+  const int E = tid / nen;
+  const int I = tid - E * nen;
+  int cx, cy, cz;
+  coords(E, cd.fEX, cd.fEXY, cx, cy, cz);
   Real out[nen];
 #pragma unroll
   for (int J = 0; J < nen; ++J) out[J] = Real(0);
   for (int s = 0; s < nen; ++s) {
     const int sx = s & 1, sy = (s >> 1) & 1, sz = (s >> 2) & 1;
     const int fx = 2 * cx + sx, fy = 2 * cy + sy, fz = 2 * cz + sz;
-    if (fx >= f.ex || fy >= f.ey || (DIM == 3 && fz >= f.ez)) continue;
+    const bool ok = !(fx >= f.ex || fy >= f.ey || (DIM == 3 && fz >= f.ez));
+    const int e = ok ? fx + f.ex * (fy + f.ey * fz) : 0;  // valid address either way
+    if (!ok || !CK(e, f.ne)) continue;
     int t[3];
     t[0] = (2 * cx + 1 < f.ex) ? sx : 2;
     t[1] = (2 * cy + 1 < f.ey) ? sy : 2;
     t[2] = DIM == 3 ? ((2 * cz + 1 < f.ez) ? sz : 2) : 0;
-    const int64_t e = fx + (int64_t)f.ex * (fy + (int64_t)f.ey * fz);
-    const Real* M = elem_f + e * nen * nen;
+    const Real* M = elem_f + (size_t)e * nen * nen;
     Real v[nen];
 #pragma unroll
     for (int b = 0; b < nen; ++b) v[b] = Real(0);
@@ -152,9 +153,10 @@ __global__ void k_galerkin_coarse(const Real* __restrict__ elem_f, Dims f, Dims 
       }
     }
   }
-  Real* dst = elem_c + E * nen * nen + I * nen;
+  Real* dst = elem_c + (size_t)E * nen * nen + I * nen;
 #pragma unroll
-  for (int J = 0; J < nen; ++J) dst[J] = out[J];
+  for (int J = 0; J < nen; ++J)
+    if (CK((size_t)E * nen * nen + I * nen + J, cd.ne * nen * nen)) dst[J] = out[J];
 }
 
 // Node stencils and inverse diagonal of a level from its element matrices.
@@ -163,10 +165,10 @@ __global__ void k_assemble(const Real* __restrict__ elem, Dims d, Real* __restri
                            Real* __restrict__ dinv) {
   constexpr int nen = 1 << DIM;
   constexpr int S = DIM == 2 ? 9 : 27;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= d.n) return;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int)d.n) return;
   int i, j, k;
-  node_ijk(idx, d.NX, d.NY, i, j, k);
+  coords(idx, d.fNX, d.fNXY, i, j, k);
   Real acc[S];
 #pragma unroll
   for (int s = 0; s < S; ++s) acc[s] = Real(0);
@@ -174,11 +176,12 @@ __global__ void k_assemble(const Real* __restrict__ elem, Dims d, Real* __restri
   for (int o = 0; o < nen; ++o) {
     const int ox = -(o & 1), oy = -((o >> 1) & 1), oz = DIM == 3 ? -((o >> 2) & 1) : 0;
     const int exi = i + ox, eyi = j + oy, ezi = k + oz;
-    if (exi < 0 || exi >= d.ex || eyi < 0 || eyi >= d.ey) continue;
-    if (DIM == 3 && (ezi < 0 || ezi >= d.ez)) continue;
-    const int64_t e = exi + (int64_t)d.ex * (eyi + (int64_t)d.ey * ezi);
+    const bool ok = !(exi < 0 || exi >= d.ex || eyi < 0 || eyi >= d.ey) &&
+                    !(DIM == 3 && (ezi < 0 || ezi >= d.ez));
+    const int e = ok ? exi + d.ex * (eyi + d.ey * ezi) : 0;  // valid address either way
+    if (!ok || !CK(e, d.ne)) continue;
     const int Iloc = o;  // node position inside the element equals -offset
-    const Real* row = elem + e * nen * nen + Iloc * nen;
+    const Real* row = elem + (size_t)e * nen * nen + Iloc * nen;
 #pragma unroll
     for (int J = 0; J < nen; ++J) {
       const int dx = (J & 1) + ox, dy = ((J >> 1) & 1) + oy;
@@ -188,7 +191,7 @@ __global__ void k_assemble(const Real* __restrict__ elem, Dims d, Real* __restri
     }
   }
 #pragma unroll
-  for (int s = 0; s < S; ++s) st[s * d.n + idx] = acc[s];
+  for (int s = 0; s < S; ++s) st[s * (int)d.n + idx] = acc[s];
   dinv[idx] = Real(1) / acc[S / 2];
 }
 
@@ -196,22 +199,24 @@ __global__ void k_assemble(const Real* __restrict__ elem, Dims d, Real* __restri
 template <typename Real, int DIM>
 __global__ void k_fine_dinv(const Real* __restrict__ ke, const uint8_t* __restrict__ fixed, Dims d,
                             Real* __restrict__ dinv) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= d.n) return;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int)d.n) return;
   if (fixed[idx]) {
     dinv[idx] = Real(1);
     return;
   }
   int i, j, k;
-  node_ijk(idx, d.NX, d.NY, i, j, k);
+  coords(idx, d.fNX, d.fNXY, i, j, k);
   Real ks = Real(0);
   constexpr int nen = 1 << DIM;
 #pragma unroll
   for (int o = 0; o < nen; ++o) {
     const int exi = i - (o & 1), eyi = j - ((o >> 1) & 1), ezi = DIM == 3 ? k - ((o >> 2) & 1) : 0;
-    if (exi < 0 || exi >= d.ex || eyi < 0 || eyi >= d.ey) continue;
-    if (DIM == 3 && (ezi < 0 || ezi >= d.ez)) continue;
-    ks += ke[exi + (int64_t)d.ex * (eyi + (int64_t)d.ey * ezi)];
+    const bool ok = !(exi < 0 || exi >= d.ex || eyi < 0 || eyi >= d.ey) &&
+                    !(DIM == 3 && (ezi < 0 || ezi >= d.ez));
+    const int e = ok ? exi + d.ex * (eyi + d.ey * ezi) : 0;  // valid address either way
+    const Real kv = CK(e, d.ne) ? ke[e] : Real(0);
+    if (ok) ks += kv;
   }
   dinv[idx] = Real(1) / (ks * Real(DIM == 2 ? 4.0 / 6.0 : 4.0 / 12.0));
 }
@@ -219,26 +224,36 @@ __global__ void k_fine_dinv(const Real* __restrict__ ke, const uint8_t* __restri
 // Lower band of the coarsest operator: band[i*(bw+1) + (j - i + bw)].
 template <typename Real, int DIM>
 __global__ void k_band_fill(const Real* __restrict__ st, Dims d, int bw, double* __restrict__ band) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= d.n) return;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int)d.n) return;
   int i, j, k;
-  node_ijk(idx, d.NX, d.NY, i, j, k);
+  coords(idx, d.fNX, d.fNXY, i, j, k);
   const int S = DIM == 2 ? 9 : 27;
   for (int s = 0; s < S; ++s) {
     const int dx = s % 3 - 1, dy = (s / 3) % 3 - 1, dz = DIM == 3 ? s / 9 - 1 : 0;
     const int ii = i + dx, jj = j + dy, kk = k + dz;
     if (ii < 0 || ii >= d.NX || jj < 0 || jj >= d.NY || kk < 0 || kk >= d.NZ) continue;
-    const int64_t col = ii + (int64_t)d.NX * (jj + (int64_t)d.NY * kk);
+    const int col = ii + d.NX * (jj + d.NY * kk);  // no load depends on it before the check
     if (col > idx) continue;
-    band[idx * (bw + 1) + (col - idx + bw)] = (double)st[s * d.n + idx];
+    if (CK((int64_t)idx * (bw + 1) + (col - idx + bw), d.n * (bw + 1)) && CK(col - idx + bw, bw + 1))
+      band[(int64_t)idx * (bw + 1) + (col - idx + bw)] = (double)st[s * (int)d.n + idx];
   }
 }
 
-// Right-looking banded Cholesky in one block.
-__global__ void k_band_cholesky(double* __restrict__ band, int n, int bw, int* __restrict__ err) {
-  __shared__ double piv;
+// Right-looking banded Cholesky in one block, on a shared-memory copy of
+// the band when it fits (SMEM) or in place in global memory.  Stores the
+// factor and the reciprocals of its diagonal (rdiag).
+template <bool SMEM>
+__global__ void k_band_cholesky(double* __restrict__ gband, double* __restrict__ rdiag, int n,
+                                int bw, int* __restrict__ err) {
+  extern __shared__ double sband[];
+  __shared__ double piv, rpiv;
   __shared__ int bad;
   const int ld = bw + 1;
+  const int64_t size = (int64_t)n * ld;
+  double* band = SMEM ? sband : gband;
+  if (SMEM)
+    for (int64_t t = threadIdx.x; t < size; t += blockDim.x) band[t] = gband[t];
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
   for (int k = 0; k < n; ++k) {
@@ -246,51 +261,73 @@ __global__ void k_band_cholesky(double* __restrict__ band, int n, int bw, int* _
       const double a = band[(int64_t)k * ld + bw];
       if (!(a > 0.0) || !isfinite(a)) bad = 1;
       piv = sqrt(a);
+      rpiv = 1.0 / piv;
       band[(int64_t)k * ld + bw] = piv;
+      rdiag[k] = rpiv;
     }
     __syncthreads();
     if (bad) break;
     const int last = min(k + bw, n - 1);
     for (int i = k + 1 + threadIdx.x; i <= last; i += blockDim.x)
-      band[(int64_t)i * ld + (k - i + bw)] /= piv;
+      if (CK((int64_t)i * ld + (k - i + bw), size) && CK(k - i + bw, ld))
+        band[(int64_t)i * ld + (k - i + bw)] *= rpiv;
     __syncthreads();
     const int m = last - k;
     for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
       const int ii = t / m, jj = t - (t / m) * m;
       if (jj > ii) continue;
       const int i = k + 1 + ii, j = k + 1 + jj;
+      if (!CK((int64_t)i * ld + (j - i + bw), size) || !CK((int64_t)j * ld + (k - j + bw), size) ||
+          !CK(k - i + bw, ld) || !CK(k - j + bw, ld) || !CK(j - i + bw, ld))
+        continue;
       band[(int64_t)i * ld + (j - i + bw)] -=
           band[(int64_t)i * ld + (k - i + bw)] * band[(int64_t)j * ld + (k - j + bw)];
     }
     __syncthreads();
   }
+  if (SMEM)
+    for (int64_t t = threadIdx.x; t < size; t += blockDim.x) gband[t] = band[t];
   if (threadIdx.x == 0 && bad) *err = MGAR_ERR_NOT_SPD;
 }
 
-// Column j of the inverse, one warp per column: forward then backward
-// substitution with the band factor; inv is row-major n x n.
-__global__ void k_band_inverse(const double* __restrict__ band, int n, int bw, double* inv) {
+// Columns of the inverse, one warp per column: forward then backward
+// substitution with the band factor; inv is row-major n x n.  With SMEM the
+// band is staged in shared memory once per block.
+template <bool SMEM>
+__global__ void k_band_inverse(const double* __restrict__ gband, const double* __restrict__ rdiag,
+                               int n, int bw, double* inv) {
+  extern __shared__ double sband[];
+  const int ld = bw + 1;
+  const double* band = gband;
+  if (SMEM) {
+    const int64_t size = (int64_t)n * ld;
+    for (int64_t t = threadIdx.x; t < size; t += blockDim.x) sband[t] = gband[t];
+    __syncthreads();
+    band = sband;
+  }
   const int warps = blockDim.x >> 5;
   const int col = blockIdx.x * warps + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (col >= n) return;
-  const int ld = bw + 1;
   for (int i = col; i < n; ++i) {
     double s = 0.0;
     for (int p = max(col, i - bw) + lane; p < i; p += 32)
-      s += band[(int64_t)i * ld + (p - i + bw)] * inv[(int64_t)p * n + col];
+      if (CK((int64_t)i * ld + (p - i + bw), (int64_t)n * ld) && CK(p - i + bw, ld) &&
+          CK((int64_t)p * n + col, (int64_t)n * n))
+        s += band[(int64_t)i * ld + (p - i + bw)] * inv[(int64_t)p * n + col];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0)
-      inv[(int64_t)i * n + col] = ((i == col ? 1.0 : 0.0) - s) / band[(int64_t)i * ld + bw];
+    if (lane == 0) inv[(int64_t)i * n + col] = ((i == col ? 1.0 : 0.0) - s) * rdiag[i];
     __syncwarp();
   }
   for (int i = n - 1; i >= 0; --i) {
     double s = 0.0;
     const int last = min(n - 1, i + bw);
     for (int p = i + 1 + lane; p <= last; p += 32)
-      s += band[(int64_t)p * ld + (i - p + bw)] * inv[(int64_t)p * n + col];
+      if (CK((int64_t)p * ld + (i - p + bw), (int64_t)n * ld) && CK(i - p + bw, ld) &&
+          CK((int64_t)p * n + col, (int64_t)n * n))
+        s += band[(int64_t)p * ld + (i - p + bw)] * inv[(int64_t)p * n + col];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) inv[(int64_t)i * n + col] = (inv[(int64_t)i * n + col] - s) / band[(int64_t)i * ld + bw];
+    if (lane == 0) inv[(int64_t)i * n + col] = (inv[(int64_t)i * n + col] - s) * rdiag[i];
     __syncwarp();
   }
 }
@@ -340,6 +377,14 @@ void alloc_hierarchy(Ctx& c) {
   c.bw = (c.dim == 2) ? dc.NX + 1 : dc.NX * dc.NY + dc.NX + 1;
   if (c.bw > c.nc - 1) c.bw = c.nc - 1 > 0 ? c.nc - 1 : 0;
   MGAR_CUDA(cudaMalloc(&c.band, (size_t)c.nc * (c.bw + 1) * sizeof(double)));
+  MGAR_CUDA(cudaMalloc(&c.rdiag, (size_t)c.nc * sizeof(double)));
+  const size_t band_bytes = (size_t)c.nc * (c.bw + 1) * sizeof(double);
+  if (band_bytes <= kBandSmemMax) {
+    MGAR_CUDA(cudaFuncSetAttribute(k_band_cholesky<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kBandSmemMax));
+    MGAR_CUDA(cudaFuncSetAttribute(k_band_inverse<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kBandSmemMax));
+  }
   MGAR_CUDA(cudaMalloc(&c.cinv, (size_t)c.nc * c.nc * sizeof(double)));
   if (c.p.precision != MGAR_FP64) MGAR_CUDA(cudaMalloc(&c.cinv_f, (size_t)c.nc * c.nc * sizeof(float)));
   // constant tables: k0 (nen^2) then G (3^dim * nen^2)
@@ -373,10 +418,12 @@ void free_hierarchy(Ctx& c) {
   free_levels(c.h64);
   free_levels(c.h32);
   cudaFree(c.band);
+  cudaFree(c.rdiag);
   cudaFree(c.cinv);
   cudaFree(c.cinv_f);
   cudaFree(c.tables);
   c.band = nullptr;
+  c.rdiag = nullptr;
   c.cinv = nullptr;
   c.cinv_f = nullptr;
   c.tables = nullptr;
@@ -410,10 +457,19 @@ static void build_levels(Ctx& c, const Real* ke0, LevelBuf<Real>* h) {
   MGAR_CUDA(cudaMemsetAsync(c.band, 0, (size_t)c.nc * (c.bw + 1) * sizeof(double), s));
   k_band_fill<Real, DIM><<<blocks_for(dcst.n), kThreads, 0, s>>>(h[c.nl - 1].st, dcst, c.bw, c.band);
   MGAR_LAUNCH_CHECK();
-  k_band_cholesky<<<1, 512, 0, s>>>(c.band, c.nc, c.bw, c.derr);
+  const size_t band_bytes = (size_t)c.nc * (c.bw + 1) * sizeof(double);
+  const bool smem = band_bytes <= kBandSmemMax;
+  if (smem) {
+    k_band_cholesky<true><<<1, 1024, band_bytes, s>>>(c.band, c.rdiag, c.nc, c.bw, c.derr);
+  } else {
+    k_band_cholesky<false><<<1, 1024, 0, s>>>(c.band, c.rdiag, c.nc, c.bw, c.derr);
+  }
   MGAR_LAUNCH_CHECK();
   MGAR_CUDA(cudaMemsetAsync(c.cinv, 0, (size_t)c.nc * c.nc * sizeof(double), s));
-  k_band_inverse<<<(c.nc + 3) / 4, 128, 0, s>>>(c.band, c.nc, c.bw, c.cinv);
+  if (smem)
+    k_band_inverse<true><<<(c.nc + 7) / 8, 256, band_bytes, s>>>(c.band, c.rdiag, c.nc, c.bw, c.cinv);
+  else
+    k_band_inverse<false><<<(c.nc + 7) / 8, 256, 0, s>>>(c.band, c.rdiag, c.nc, c.bw, c.cinv);
   MGAR_LAUNCH_CHECK();
   if (c.cinv_f) {
     k_d2f<<<blocks_for((int64_t)c.nc * c.nc), kThreads, 0, s>>>(c.cinv, c.cinv_f, (int64_t)c.nc * c.nc);

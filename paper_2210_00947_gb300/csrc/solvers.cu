@@ -29,11 +29,11 @@ template <int DIM>
 __global__ void k_residual_norm(FineOp<double> op, const double* __restrict__ q,
                                 const double* __restrict__ x, double* __restrict__ r,
                                 double* partials, unsigned int* counter, double* out) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   double v[1] = {0.0};
   if (idx < op.n) {
     int i, j, k;
-    node_ijk(idx, op.NX, op.NY, i, j, k);
+    coords(idx, op.fNX, op.fNXY, i, j, k);
     double d;
     const double ax = DIM == 2 ? fine_row2(op, x, i, j, d) : fine_row3(op, x, i, j, k, d);
     const double ri = q[idx] - ax;
@@ -170,20 +170,27 @@ static void check_device_error(Ctx& c) {
 }
 
 // z = M r (one V-cycle, zero initial guess) in the handle's precision.
+static bool vcycle_profiled(Ctx& c) {
+  return c.prof_class == MGAR_KC_SMOOTH0 || c.prof_class == MGAR_KC_RESID0;
+}
+
 void precondition(Ctx& c, const double* r, double* z) {
-  if (c.p.precision == MGAR_FP64) {
-    vcycle<double>(c, r, z, true);
-  } else {
-    convert_d2f(c, r, c.b32, c.n);
-    vcycle<float>(c, c.b32, c.x32, true);
-    convert_f2d(c, c.x32, z, c.n);
-  }
+  run_graph(c, 1, r, z, vcycle_profiled(c), [&] {
+    if (c.p.precision == MGAR_FP64) {
+      vcycle<double>(c, r, z, true);
+    } else {
+      convert_d2f(c, r, c.b32, c.n);
+      vcycle<float>(c, c.b32, c.x32, true);
+      convert_f2d(c, c.x32, z, c.n);
+    }
+  });
 }
 
 template <int DIM>
 static void residual_norm(Ctx& c, const double* x, double* r, double* out) {
   const Dims& d = c.L[0];
-  FineOp<double> op{c.ke, nullptr, c.fixed, d.ex, d.ey, d.ez, d.NX, d.NY, d.NZ, d.n};
+  FineOp<double> op{c.ke, nullptr, c.fixed, d.ex, d.ey, d.ez, d.NX, d.NY, d.NZ, (int)d.n,
+                    d.fNX, d.fNXY};
   k_residual_norm<DIM><<<blocks_for(d.n), kThreads, 0, c.stream>>>(op, c.q, x, r, c.partials,
                                                                     c.counter, out);
   MGAR_LAUNCH_CHECK();
@@ -242,12 +249,15 @@ void solve_mgar(Ctx& c, const double* T_prev, double* T, double* res, int* accep
       apply_dK64(c, prev, c.r);  // c.r = -dK r_{i-1}
       if (!zero)
         MGAR_CUDA(cudaMemcpyAsync(ri, prev, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
-      vcycle<double>(c, c.r, ri, zero);
+      run_graph(c, zero ? 2 : 3, c.r, ri, vcycle_profiled(c),
+                [&] { vcycle<double>(c, c.r, ri, zero); });
     } else {
-      convert_d2f(c, prev, c.x32, n);
-      apply_dK32(c, c.x32, c.b32);  // b32 = -dK r_{i-1}; x32 keeps r_{i-1} as the guess
-      vcycle<float>(c, c.b32, c.x32, zero);
-      convert_f2d(c, c.x32, ri, n);
+      run_graph(c, zero ? 4 : 5, prev, ri, vcycle_profiled(c), [&] {
+        convert_d2f(c, prev, c.x32, n);
+        apply_dK32(c, c.x32, c.b32);  // b32 = -dK r_{i-1}; x32 keeps r_{i-1} as the guess
+        vcycle<float>(c, c.b32, c.x32, zero);
+        convert_f2d(c, c.x32, ri, n);
+      });
     }
   }
   // Eq. 18: orthonormal basis (modified Gram-Schmidt, twice)

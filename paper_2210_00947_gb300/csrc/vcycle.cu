@@ -16,33 +16,33 @@ namespace mgar {
 template <typename Real, int DIM>
 struct FineRow {
   FineOp<Real> op;
-  __device__ __forceinline__ Real operator()(const Real* __restrict__ x, int64_t idx) const {
+  __device__ __forceinline__ Real operator()(const Real* __restrict__ x, int idx) const {
     int i, j, k;
-    node_ijk(idx, op.NX, op.NY, i, j, k);
+    coords(idx, op.fNX, op.fNXY, i, j, k);
     Real d;
     if (DIM == 2) return fine_row2(op, x, i, j, d);
     return fine_row3(op, x, i, j, k, d);
   }
-  __device__ __forceinline__ int64_t size() const { return op.n; }
+  __device__ __forceinline__ int size() const { return op.n; }
 };
 
 template <typename Real, int DIM>
 struct StencilRow {
   StencilOp<Real> op;
-  __device__ __forceinline__ Real operator()(const Real* __restrict__ x, int64_t idx) const {
+  __device__ __forceinline__ Real operator()(const Real* __restrict__ x, int idx) const {
     int i, j, k;
-    node_ijk(idx, op.NX, op.NY, i, j, k);
+    coords(idx, op.fNX, op.fNXY, i, j, k);
     if (DIM == 2) return stencil_row2(op, x, i, j);
     return stencil_row3(op, x, i, j, k);
   }
-  __device__ __forceinline__ int64_t size() const { return op.n; }
+  __device__ __forceinline__ int size() const { return op.n; }
 };
 
 // ----------------------------------------------------------------- kernels
 template <class Row, typename Real>
 __global__ void k_jacobi(Row row, const Real* __restrict__ b, const Real* __restrict__ xin,
                          Real* __restrict__ xout, const Real* __restrict__ dinv, Real omega) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= row.size()) return;
   const Real ax = row(xin, idx);
   xout[idx] = xin[idx] + omega * dinv[idx] * (b[idx] - ax);
@@ -50,15 +50,15 @@ __global__ void k_jacobi(Row row, const Real* __restrict__ b, const Real* __rest
 
 template <typename Real>
 __global__ void k_jacobi_zero(const Real* __restrict__ b, Real* __restrict__ x,
-                              const Real* __restrict__ dinv, Real omega, int64_t n) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                              const Real* __restrict__ dinv, Real omega, int n) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx < n) x[idx] = omega * dinv[idx] * b[idx];
 }
 
 template <class Row, typename Real>
 __global__ void k_residual(Row row, const Real* __restrict__ b, const Real* __restrict__ x,
                            Real* __restrict__ r) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= row.size()) return;
   r[idx] = b[idx] - row(x, idx);
 }
@@ -67,7 +67,7 @@ __global__ void k_residual(Row row, const Real* __restrict__ b, const Real* __re
 template <class Row, typename Real, bool DOT>
 __global__ void k_apply(Row row, const Real* __restrict__ x, Real* __restrict__ y, Real scale,
                         double* partials, unsigned int* counter, double* out) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   double v[1] = {0.0};
   if (idx < row.size()) {
     const Real ax = scale * row(x, idx);
@@ -80,7 +80,11 @@ __global__ void k_apply(Row row, const Real* __restrict__ x, Real* __restrict__ 
 // 1D interpolation taps.  Coarse node I sits at fine node min(2I, nf).
 // Restriction (P^T) gathers from fine nodes 2I (weight 1), 2I-1 and 2I+1
 // (weight 1/2, or 1 for the injected last node nf of an odd axis).
+// Unused tap slots point at a valid node with weight 0.
 __device__ __forceinline__ int restrict_taps(int I, int nf, int* idx, float* w) {
+  const int home = min(2 * I, nf);
+  idx[0] = idx[1] = idx[2] = home;
+  w[0] = w[1] = w[2] = 0.f;
   int c = 0;
   if (2 * I <= nf) { idx[c] = 2 * I; w[c++] = 1.f; }
   if (2 * I - 1 >= 1 && 2 * I - 1 <= nf) { idx[c] = 2 * I - 1; w[c++] = (2 * I - 1 < nf) ? 0.5f : 1.f; }
@@ -90,33 +94,35 @@ __device__ __forceinline__ int restrict_taps(int I, int nf, int* idx, float* w) 
 
 // Interpolation (P) onto fine node i from coarse nodes.
 __device__ __forceinline__ int prolong_taps(int i, int nf, int* idx, float* w) {
-  if ((i & 1) == 0) { idx[0] = i >> 1; w[0] = 1.f; return 1; }
+  if ((i & 1) == 0) { idx[0] = idx[1] = i >> 1; w[0] = 1.f; w[1] = 0.f; return 1; }
   if (i < nf) { idx[0] = (i - 1) >> 1; w[0] = 0.5f; idx[1] = (i + 1) >> 1; w[1] = 0.5f; return 2; }
-  idx[0] = (i + 1) >> 1; w[0] = 1.f; return 1;
+  idx[0] = idx[1] = (i + 1) >> 1; w[0] = 1.f; w[1] = 0.f; return 1;
 }
 
 template <typename Real, int DIM>
 __global__ void k_restrict(const Real* __restrict__ r, Real* __restrict__ bc, Dims f, Dims cd,
                            const uint8_t* __restrict__ fixed) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= cd.n) return;
   int I, J, K;
-  node_ijk(idx, cd.NX, cd.NY, I, J, K);
+  coords(idx, cd.fNX, cd.fNXY, I, J, K);
   int ix[3], iy[3], iz[3];
   float wx[3], wy[3], wz[3];
   const int nx = restrict_taps(I, f.ex, ix, wx);
   const int ny = restrict_taps(J, f.ey, iy, wy);
   int nz = 1;
-  iz[0] = 0;
+  iz[0] = iz[1] = iz[2] = 0;
   wz[0] = 1.f;
+  wz[1] = wz[2] = 0.f;
   if (DIM == 3) nz = restrict_taps(K, f.ez, iz, wz);
   Real acc = Real(0);
   for (int c = 0; c < nz; ++c)
     for (int b = 0; b < ny; ++b) {
-      const int64_t base = (int64_t)f.NX * (iy[b] + (int64_t)f.NY * iz[c]);
+      const int base = f.NX * (iy[b] + f.NY * iz[c]);
       const Real wyz = (Real)(wy[b] * wz[c]);
       for (int a = 0; a < nx; ++a) {
-        const int64_t fi = base + ix[a];
+        const int fi = base + ix[a];
+        if (!CK(fi, f.n)) continue;
         if (fixed && fixed[fi]) continue;
         acc += (wyz * (Real)wx[a]) * r[fi];
       }
@@ -128,28 +134,30 @@ __global__ void k_restrict(const Real* __restrict__ r, Real* __restrict__ bc, Di
 template <typename Real, int DIM>
 __global__ void k_prolong(const Real* __restrict__ xc, const Real* cur, Real* dst, Dims f, Dims cd,
                           const uint8_t* __restrict__ fixed) {
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= f.n) return;
   if (fixed && fixed[idx]) {
     dst[idx] = cur[idx];
     return;
   }
   int i, j, k;
-  node_ijk(idx, f.NX, f.NY, i, j, k);
+  coords(idx, f.fNX, f.fNXY, i, j, k);
   int ix[2], iy[2], iz[2];
   float wx[2], wy[2], wz[2];
   const int nx = prolong_taps(i, f.ex, ix, wx);
   const int ny = prolong_taps(j, f.ey, iy, wy);
   int nz = 1;
-  iz[0] = 0;
+  iz[0] = iz[1] = 0;
   wz[0] = 1.f;
+  wz[1] = 0.f;
   if (DIM == 3) nz = prolong_taps(k, f.ez, iz, wz);
   Real acc = Real(0);
   for (int c = 0; c < nz; ++c)
     for (int b = 0; b < ny; ++b) {
-      const int64_t base = (int64_t)cd.NX * (iy[b] + (int64_t)cd.NY * iz[c]);
+      const int base = cd.NX * (iy[b] + cd.NY * iz[c]);
       const Real wyz = (Real)(wy[b] * wz[c]);
-      for (int a = 0; a < nx; ++a) acc += (wyz * (Real)wx[a]) * xc[base + ix[a]];
+      for (int a = 0; a < nx; ++a)
+        if (CK(base + ix[a], cd.n)) acc += (wyz * (Real)wx[a]) * xc[base + ix[a]];
     }
   dst[idx] = cur[idx] + acc;
 }
@@ -162,7 +170,8 @@ __global__ void k_coarse_solve(const double* __restrict__ cinv, const Real* __re
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
   double s = 0.0;
-  for (int j = lane; j < n; j += 32) s += cinv[(int64_t)row * n + j] * (double)b[j];
+  for (int j = lane; j < n; j += 32)
+    if (CK((int64_t)row * n + j, (int64_t)n * n)) s += cinv[(int64_t)row * n + j] * (double)b[j];
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   if (lane == 0) x[row] = (Real)s;
 }
@@ -195,7 +204,7 @@ template <typename Real, int DIM>
 static FineRow<Real, DIM> fine_row(Ctx& c, const Real* ke, const Real* ksub) {
   FineRow<Real, DIM> r;
   const Dims& d = c.L[0];
-  r.op = FineOp<Real>{ke, ksub, c.fixed, d.ex, d.ey, d.ez, d.NX, d.NY, d.NZ, d.n};
+  r.op = FineOp<Real>{ke, ksub, c.fixed, d.ex, d.ey, d.ez, d.NX, d.NY, d.NZ, (int)d.n, d.fNX, d.fNXY};
   return r;
 }
 
@@ -203,7 +212,8 @@ template <typename Real, int DIM>
 static StencilRow<Real, DIM> stencil_row(Ctx& c, int l) {
   StencilRow<Real, DIM> r;
   const Dims& d = c.L[l];
-  r.op = StencilOp<Real>{levels<Real>(c)[l].st, levels<Real>(c)[l].dinv, d.NX, d.NY, d.NZ, d.n};
+  r.op = StencilOp<Real>{levels<Real>(c)[l].st, levels<Real>(c)[l].dinv, d.NX, d.NY, d.NZ, (int)d.n,
+                         d.fNX, d.fNXY};
   return r;
 }
 
@@ -252,7 +262,7 @@ static void vcycle_dim(Ctx& c, const Real* b0, Real* x0, bool zero_guess) {
     if (l > 0 || zero_guess) {
       if (sweeps > 0) {
         ProfScope ps(c, l == 0 ? MGAR_KC_SMOOTH0 : -1);
-        k_jacobi_zero<<<blocks_for(d.n), kThreads, 0, c.stream>>>(b, x, h[l].dinv, om, d.n);
+        k_jacobi_zero<<<blocks_for(d.n), kThreads, 0, c.stream>>>(b, x, h[l].dinv, om, (int)d.n);
         MGAR_LAUNCH_CHECK();
         --sweeps;
       } else {

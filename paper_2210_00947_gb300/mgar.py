@@ -77,9 +77,14 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
     global _LIB
     if _LIB is not None:
         return _LIB
-    if build_if_missing and not _build.up_to_date():
-        _build.build()
-    path = _build.LIB
+    if os.environ.get("MGAR_CHECKED") == "1":
+        path = _build.LIB_CHECKED  # bounds-checked debug build
+        if not os.path.exists(path):
+            _build.build_checked()
+    else:
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        path = _build.LIB
     if not os.path.exists(path):
         raise RuntimeError(f"libmgar.so not found at {path}; run paper_2210_00947_gb300/build.py")
     lib = ctypes.CDLL(path)

@@ -219,3 +219,36 @@ def test_oc_matches_oracle(dims):
         np.testing.assert_allclose(out, ref, rtol=1e-11, atol=1e-12)
         assert abs(change - np.max(np.abs(ref - rho))) < 1e-11
         assert abs(dv @ out - 0.4) < 1e-11
+
+
+def test_oc_unreachable_volume_matches_oracle():
+    """Volume out of reach of the move limits: the bracket collapses to its
+    end (lambda -> 1e-40, every element at its upper move limit)."""
+    dims = (30, 20, 0)
+    g, rho, fixed, q = make_problem(dims, mask="sink")
+    rho = np.full(g.n_elems, 0.1)
+    dc = -np.random.default_rng(10).uniform(0.1, 1.0, g.n_elems)
+    H, Hs = design.filter_matrix(g, 1.5)
+    dv = design.filter_transpose(H, Hs, np.full(g.n_elems, 1.0 / g.n_elems))
+    ref, lam_ref = design.oc_update(rho, dc, dv, 0.5, 0.2)
+    with solver_for(dims, fixed, q, nl=2) as s:
+        r = dev(rho)
+        lam, change = s.oc_update(r, dev(dc), 0.5, 0.2)
+        np.testing.assert_allclose(host(r), ref, rtol=1e-12, atol=1e-13)
+        np.testing.assert_allclose(host(r), 0.3, rtol=1e-12)
+        assert lam < 1e-30 and lam_ref < 1e-30
+
+
+@pytest.mark.parametrize("dims", [(128, 96, 0), (40, 36, 30)])
+def test_oc_large_matches_oracle(dims):
+    g, rho, fixed, q = make_problem(dims, mask="sink", seed=11)
+    rng = np.random.default_rng(12)
+    dc = -(10.0 ** rng.uniform(-4, 2, g.n_elems))
+    H, Hs = design.filter_matrix(g, 1.5)
+    dv = design.filter_transpose(H, Hs, np.full(g.n_elems, 1.0 / g.n_elems))
+    ref, lam_ref = design.oc_update(rho, dc, dv, 0.35, 0.2)
+    with solver_for(dims, fixed, q, nl=3) as s:
+        r = dev(rho)
+        lam, change = s.oc_update(r, dev(dc), 0.35, 0.2)
+        assert abs(lam - lam_ref) / lam_ref < 1e-12
+        np.testing.assert_allclose(host(r), ref, rtol=1e-11, atol=1e-12)
