@@ -43,6 +43,7 @@ extern "C" {
 #define MGAR_ERR_MAXIT (-4)     /* MGCG stopped at cg_max without reaching eps2 */
 #define MGAR_ERR_NONFINITE (-5) /* a NaN/Inf appeared in a solver scalar */
 #define MGAR_ERR_STATE (-6)     /* call out of order (e.g. MGAR before any MGCG) */
+#define MGAR_ERR_TOO_LARGE (-7) /* input beyond a fixed internal capacity */
 
 #define MGAR_FP64 0  /* every step in FP64 */
 #define MGAR_MIXED 1 /* FP32 multigrid preconditioner, FP64 elsewhere */
@@ -215,6 +216,28 @@ int mgar_profile_stop(mgar_t h, double* total_ms, int64_t* launches);
 /* Number of kernels this library has launched in this process (all
  * handles), for accounting in benchmarks. */
 int64_t mgar_kernel_launches(void);
+
+/* Design sensitivities dc, as mgar_sensitivity computes them, for callers
+ * that cannot allocate device memory (no counterpart in the paper): code
+ * whose device memory is owned by a host framework's pool, or that must not
+ * grow the process's device footprint after start-up.  No handle and no
+ * allocation: the per-element intermediate lives in a static device array
+ * of 2^20 doubles (8 MiB) that every GPU loading the library keeps until
+ * the process exits.
+ *   p:        host; nx, ny, nz, k0, kmin, penal and rmin are read.
+ *   rho_phys: device, E doubles, the physical (filtered) density.
+ *   T:        device, n doubles; dc: device, E doubles (output).
+ *   stream:   cudaStream_t the two kernels are queued on.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call outside any
+ * stream capture.  All calls share the array, so calls whose work overlaps
+ * on the GPU (other streams or host threads) race; each call writes every
+ * entry it reads, so nothing needs clearing between calls.
+ * Errors: MGAR_ERR_ARG (null pointer, bad grid or rmin > 8),
+ * MGAR_ERR_TOO_LARGE (more than 2^20 elements), MGAR_ERR_CUDA (symbol lookup
+ * or launch failed).  Returns without synchronising the stream. */
+int mgar_sensitivity_noalloc(const mgar_params* p, const double* rho_phys, const double* T,
+                             double* dc, void* stream);
 
 #ifdef __cplusplus
 }

@@ -23,6 +23,7 @@ MGAR_ERR_NOT_SPD = -3
 MGAR_ERR_MAXIT = -4
 MGAR_ERR_NONFINITE = -5
 MGAR_ERR_STATE = -6
+MGAR_ERR_TOO_LARGE = -7
 MGAR_FP64 = 0
 MGAR_MIXED = 1
 MGAR_GUESS_PREVIOUS = 0
@@ -37,7 +38,8 @@ EXPORTS = ("mgar_default_params", "mgar_create", "mgar_destroy", "mgar_set_strea
            "mgar_last_error", "mgar_filter", "mgar_set_density", "mgar_apply_K",
            "mgar_build_hierarchy", "mgar_vcycle", "mgar_solve_mgcg", "mgar_solve_mgar",
            "mgar_sensitivity", "mgar_oc_update", "mgar_step", "mgar_sizes", "mgar_run",
-           "mgar_profile_start", "mgar_profile_stop", "mgar_kernel_launches")
+           "mgar_profile_start", "mgar_profile_stop", "mgar_kernel_launches",
+           "mgar_sensitivity_noalloc")
 
 # kernel classes of mgar_profile_start
 KC_APPLY64, KC_SMOOTH0, KC_RESID0, KC_OC, KC_GALERKIN0, KC_FILTER, KC_SENS = range(1, 8)
@@ -110,6 +112,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "mgar_profile_start": (i32, [vp, i32]),
         "mgar_profile_stop": (i32, [vp, dp, P(ctypes.c_int64)]),
         "mgar_kernel_launches": (ctypes.c_int64, []),
+        "mgar_sensitivity_noalloc": (i32, [P(Params), vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
