@@ -44,6 +44,10 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 MGCG comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-check", action="store_true", help="skip the equal-compliance check")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end leg")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--timeline", action="store_true",
+                    help="after timing, print a per-launch-site device-time table to stderr")
     return ap.parse_args()
 
 
@@ -189,7 +193,8 @@ def run_gpu(args):
     overrides = {} if args.eps1 is None else {"eps1": args.eps1}
     stream = torch.cuda.current_stream(dev)
 
-    p_mix = mgar.params_for(w, precision=mgar.MGAR_MIXED, basis_guess=guess, **overrides)
+    prec = mgar.MGAR_MIXED if args.precision == "mixed" else mgar.MGAR_FP64
+    p_mix = mgar.params_for(w, precision=prec, basis_guess=guess, **overrides)
     solver = mgar.Solver(p_mix, fixed, q, stream=stream)
     rho0_d = torch.tensor(rho0, device=dev)
     rho = torch.empty_like(rho0_d)
@@ -235,18 +240,27 @@ def run_gpu(args):
     step_ms = max_over_ranks(statistics.mean(times), world)
     value = step_ms / (cycles * world)
 
+    if args.timeline:
+        solver.profile_start(mgar.KC_TIMELINE)
+        one_run(solver, rho, T)
+        tl_ms, tl_n = solver.profile_stop()
+        print(f"[timeline] one run: {tl_ms:.2f} ms over {tl_n} marks\n" + solver.profile_report(),
+              file=sys.stderr, flush=True)
+
     # e2e: mgar_run from pinned host memory, copies inside the timed region
-    rho_h = torch.from_numpy(rho0.copy()).pin_memory()
-    rho_out = torch.empty_like(rho_h).pin_memory()
-    solver.run(rho_h, cycles, rho_out)
-    e2e_times = []
-    for _ in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
+    e2e_ms = float("nan")
+    if not args.no_e2e:
+        rho_h = torch.from_numpy(rho0.copy()).pin_memory()
+        rho_out = torch.empty_like(rho_h).pin_memory()
         solver.run(rho_h, cycles, rho_out)
-        e2e_times.append((time.perf_counter() - t0) * 1e3)
-    e2e_ms = max_over_ranks(statistics.mean(e2e_times), world)
+        e2e_times = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            solver.run(rho_h, cycles, rho_out)
+            e2e_times.append((time.perf_counter() - t0) * 1e3)
+        e2e_ms = max_over_ranks(statistics.mean(e2e_times), world)
 
     # plain FP64 MGCG on the same workload (MGCG every cycle)
     fp64 = None
@@ -321,7 +335,8 @@ def run_gpu(args):
         "config": {"workload": args.workload, "grid": f"{w.nx}x{w.ny}x{w.nz} H8" if w.nz else
                    f"{w.nx}x{w.ny} Q4", "dofs": w.n_nodes, "cycles_per_step": cycles,
                    "nl": w.nl, "m": w.m, "eps1": p_mix.eps1, "eps2": w.eps2,
-                   "basis_guess": args.guess, "precision": "mixed (FP32 V-cycle, FP64 CG/GS/reduced)",
+                   "basis_guess": args.guess, "precision": "mixed (FP32 V-cycle, FP64 CG/GS/reduced)" if prec == mgar.MGAR_MIXED
+                   else "fp64",
                    "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) between steps"},
         "cycles": {"mgcg": n_mgcg, "mgar_accepted": n_acc,
                    "cg_iters_mean": statistics.mean([i["cg_iters"] for i in infos if i["used_mgcg"]] or [0]),

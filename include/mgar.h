@@ -205,13 +205,21 @@ int mgar_run(mgar_t h, const double* rho_host, int cycles, double* rho_out_host,
 #define MGAR_KC_GALERKIN0 5 /* Galerkin element matrices of level 1 */
 #define MGAR_KC_FILTER 6  /* density filter / its transpose */
 #define MGAR_KC_SENS 7    /* element sensitivities (Eq. 10) */
+#define MGAR_KC_TIMELINE 100 /* every launch site: device time between consecutive launches */
 
 /* Start timing every launch of one kernel class (0 stops).  Each launch
  * is bracketed by two CUDA events; at most 65536 launches are recorded. */
 int mgar_profile_start(mgar_t h, int kernel_class);
 /* Stop, synchronise the stream, and return the summed duration (ms) and
- * the number of timed launches. */
+ * the number of timed launches.  With MGAR_KC_TIMELINE an event follows
+ * every launch site (and graph replay); the device time between two
+ * consecutive events is charged to the later site, and the per-site totals
+ * become available through mgar_profile_report. */
 int mgar_profile_stop(mgar_t h, double* total_ms, int64_t* launches);
+
+/* Text table (site, launches, ms, share) of the last MGAR_KC_TIMELINE
+ * session, written to buf (host, len bytes, NUL-terminated). */
+int mgar_profile_report(mgar_t h, char* buf, int64_t len);
 
 /* Number of kernels this library has launched in this process (all
  * handles), for accounting in benchmarks. */

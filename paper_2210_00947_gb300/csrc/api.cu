@@ -2,6 +2,7 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -14,6 +15,18 @@ std::atomic<int64_t> g_launches{0};
 }  // namespace
 
 namespace mgar {
+Ctx*& current_ctx() {
+  static thread_local Ctx* cur = nullptr;
+  return cur;
+}
+void prof_mark(const char* site) {
+  Ctx* c = current_ctx();
+  if (!c || c->prof_class != MGAR_KC_TIMELINE || c->stream == c->cap_stream) return;
+  if (c->prof_used >= 2 * kProfMax) return;
+  cudaEventRecord(c->prof_ev[c->prof_used], c->stream);
+  c->prof_sites[c->prof_used] = site;
+  ++c->prof_used;
+}
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void count_launches(int64_t delta) { g_launches.fetch_add(delta, std::memory_order_relaxed); }
 int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
@@ -45,6 +58,11 @@ template <class F>
 int guarded(mgar_t h, F&& f) {
   Ctx* c = reinterpret_cast<Ctx*>(h);
   if (!c) return MGAR_ERR_ARG;
+  struct CurGuard {
+    Ctx* prev;
+    explicit CurGuard(Ctx* c) : prev(current_ctx()) { current_ctx() = c; }
+    ~CurGuard() { current_ctx() = prev; }
+  } cur_guard(c);
   try {
 #ifdef MGAR_CHECKED
     const int rc = f(*c);
@@ -72,11 +90,13 @@ void free_ctx(Ctx& c) {
       if (c.prof_ev[i]) cudaEventDestroy(c.prof_ev[i]);
     delete[] c.prof_ev;
     c.prof_ev = nullptr;
+    delete[] c.prof_sites;
+    c.prof_sites = nullptr;
   }
   cudaFree(c.run_rho);
   cudaFree(c.run_T);
-  void* ptrs[] = {c.fixed, c.q, c.rho_phys, c.ke, c.ke0, c.ke_f, c.ke0_f, c.inv_hs, c.f_offs, c.f_w,
-                  c.dv, c.r, c.z, c.pv, c.Ap, c.tm, c.tmp_dc, c.R, c.W, c.b32, c.x32, c.tmp_e, c.oc_s, c.oc_lo,
+  void* ptrs[] = {c.fixed, c.efix, c.q, c.rho_phys, c.ke, c.ke0, c.ke_f, c.ke0_f, c.inv_hs, c.f_offs, c.f_w,
+                  c.dv, c.rsdv, c.r, c.z, c.pv, c.Ap, c.tm, c.tmp_dc, c.R, c.W, c.b32, c.x32, c.ke_df, c.df_q, c.df_x, c.df_r, c.df_p, c.df_Ap, c.tmp_e, c.oc_s, c.oc_lo,
                   c.oc_hi, c.oc_s32, c.oc_lo32, c.oc_hi32, c.dv32, c.oc_amb, c.oc_namb, c.partials, c.counter, c.dsc, c.derr};
   for (void* p : ptrs) cudaFree(p);
   if (c.hsc) cudaFreeHost(c.hsc);
@@ -212,6 +232,7 @@ int mgar_create(mgar_t* out, const mgar_params* p, const uint8_t* fixed_mask, co
     MGAR_CUDA(cudaMalloc(&c->ke0, ne * sizeof(double)));
     MGAR_CUDA(cudaMalloc(&c->inv_hs, ne * sizeof(double)));
     MGAR_CUDA(cudaMalloc(&c->dv, ne * sizeof(double)));
+    MGAR_CUDA(cudaMalloc(&c->rsdv, ne * sizeof(double)));
     MGAR_CUDA(cudaMalloc(&c->tmp_e, ne * sizeof(double)));
     MGAR_CUDA(cudaMalloc(&c->oc_s, ne * sizeof(double)));
     MGAR_CUDA(cudaMalloc(&c->oc_lo, ne * sizeof(double)));
@@ -235,6 +256,9 @@ int mgar_create(mgar_t* out, const mgar_params* p, const uint8_t* fixed_mask, co
       MGAR_CUDA(cudaMalloc(&c->ke0_f, ne * sizeof(float)));
       MGAR_CUDA(cudaMalloc(&c->b32, n * sizeof(float)));
       MGAR_CUDA(cudaMalloc(&c->x32, n * sizeof(float)));
+      MGAR_CUDA(cudaMalloc(&c->ke_df, ne * sizeof(float2)));
+      for (float2** v : {&c->df_q, &c->df_x, &c->df_r, &c->df_p, &c->df_Ap})
+        MGAR_CUDA(cudaMalloc(v, n * sizeof(float2)));
     }
     MGAR_CUDA(cudaMalloc(&c->partials, (size_t)32 * maxb * sizeof(double)));
 #ifdef MGAR_CHECKED
@@ -263,9 +287,33 @@ int mgar_create(mgar_t* out, const mgar_params* p, const uint8_t* fixed_mask, co
     std::vector<uint8_t> fh(fixed_mask, fixed_mask + n);
     for (auto& v : fh) v = v ? 1 : 0;
     MGAR_CUDA(cudaMemcpy(c->fixed, fh.data(), n, cudaMemcpyHostToDevice));
+    {
+      // per fine element: does any of its nodes carry T = 0?
+      const Dims& d = c->L[0];
+      std::vector<uint8_t> ef((size_t)ne, 0);
+      for (int k = 0; k < d.ez; ++k)
+        for (int j = 0; j < d.ey; ++j)
+          for (int i = 0; i < d.ex; ++i) {
+            uint8_t any = 0;
+            for (int a = 0; a < c->nen; ++a) {
+              const int64_t nd = (i + (a & 1)) + (int64_t)d.NX * ((j + ((a >> 1) & 1)) +
+                                                                  (int64_t)d.NY * (k + ((a >> 2) & 1)));
+              any |= fh[nd];
+            }
+            ef[i + (int64_t)d.ex * (j + (int64_t)d.ey * k)] = any;
+          }
+      MGAR_CUDA(cudaMalloc(&c->efix, ne));
+      MGAR_CUDA(cudaMemcpy(c->efix, ef.data(), ne, cudaMemcpyHostToDevice));
+    }
     MGAR_CUDA(cudaMemcpy(c->q, qh.data(), n * sizeof(double), cudaMemcpyHostToDevice));
     alloc_hierarchy(*c);
     setup_filter(*c);
+    if (P.precision == MGAR_MIXED) {
+      q_to_df(*c);
+      MGAR_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    // debugging aid: MGAR_NO_GRAPHS=1 issues every V-cycle launch directly
+    if (const char* ng = std::getenv("MGAR_NO_GRAPHS")) c->use_graphs = !(ng[0] == '1');
   } catch (const Error& e) {
     g_create_error = e.msg;
     free_ctx(*c);
@@ -430,10 +478,17 @@ int mgar_profile_start(mgar_t h, int kernel_class) {
   return guarded(h, [&](Ctx& c) {
     if (!c.prof_ev) {
       c.prof_ev = new cudaEvent_t[2 * kProfMax]();
+      c.prof_sites = new const char*[2 * kProfMax]();
       for (int i = 0; i < 2 * kProfMax; ++i) MGAR_CUDA(cudaEventCreate(&c.prof_ev[i]));
     }
     c.prof_class = kernel_class;
     c.prof_used = 0;
+    c.prof_report.clear();
+    if (kernel_class == MGAR_KC_TIMELINE) {
+      MGAR_CUDA(cudaEventRecord(c.prof_ev[0], c.stream));
+      c.prof_sites[0] = "start";
+      c.prof_used = 1;
+    }
     return MGAR_OK;
   });
 }
@@ -442,15 +497,56 @@ int mgar_profile_stop(mgar_t h, double* total_ms, int64_t* launches) {
   return guarded(h, [&](Ctx& c) {
     MGAR_CUDA(cudaStreamSynchronize(c.stream));
     double tot = 0.0;
-    for (int i = 0; i < c.prof_used; ++i) {
-      float ms = 0.f;
-      MGAR_CUDA(cudaEventElapsedTime(&ms, c.prof_ev[2 * i], c.prof_ev[2 * i + 1]));
-      tot += ms;
+    int64_t count = 0;
+    if (c.prof_class == MGAR_KC_TIMELINE) {
+      std::vector<std::pair<std::string, std::pair<int64_t, double>>> acc;
+      for (int i = 1; i < c.prof_used; ++i) {
+        float ms = 0.f;
+        MGAR_CUDA(cudaEventElapsedTime(&ms, c.prof_ev[i - 1], c.prof_ev[i]));
+        tot += ms;
+        std::string site = c.prof_sites[i];
+        const size_t slash = site.rfind('/');
+        if (slash != std::string::npos) site = site.substr(slash + 1);
+        bool found = false;
+        for (auto& a : acc)
+          if (a.first == site) {
+            a.second.first += 1;
+            a.second.second += ms;
+            found = true;
+          }
+        if (!found) acc.push_back({site, {1, (double)ms}});
+      }
+      count = c.prof_used - 1;
+      std::sort(acc.begin(), acc.end(),
+                [](const auto& x, const auto& y) { return x.second.second > y.second.second; });
+      char line[256];
+      for (auto& a : acc) {
+        snprintf(line, sizeof(line), "%-40s %8lld %10.3f ms %6.2f%%\n", a.first.c_str(),
+                 (long long)a.second.first, a.second.second, 100.0 * a.second.second / tot);
+        c.prof_report += line;
+      }
+    } else {
+      for (int i = 0; i < c.prof_used; ++i) {
+        float ms = 0.f;
+        MGAR_CUDA(cudaEventElapsedTime(&ms, c.prof_ev[2 * i], c.prof_ev[2 * i + 1]));
+        tot += ms;
+      }
+      count = c.prof_used;
     }
     if (total_ms) *total_ms = tot;
-    if (launches) *launches = c.prof_used;
+    if (launches) *launches = count;
     c.prof_class = 0;
     c.prof_used = 0;
+    return MGAR_OK;
+  });
+}
+
+int mgar_profile_report(mgar_t h, char* buf, int64_t len) {
+  return guarded(h, [&](Ctx& c) {
+    require(buf && len > 0, MGAR_ERR_ARG, "profile_report: bad buffer");
+    const size_t n = std::min<size_t>((size_t)len - 1, c.prof_report.size());
+    std::memcpy(buf, c.prof_report.data(), n);
+    buf[n] = 0;
     return MGAR_OK;
   });
 }

@@ -1,0 +1,331 @@
+// MGCG of the mixed-precision path in double-float arithmetic.
+//
+// The outer conjugate-gradient iteration (Sections 1 and 3.2) keeps its
+// vectors as df64 pairs (about 48 bits) and runs every operation on the FP32
+// pipe; only the CG scalars are FP64.  The preconditioner is the FP32
+// V-cycle.  The finest-level product uses the difference form of the
+// conductivity stencil: K has zero row sums, so
+//   (A x)_i = c * sum_j w_ij (x_i - x^_j),   x^_j = 0 on a fixed node,
+// with w_ij = k_a + k_b for the face diagonals and k_e for the body diagonals
+// of an H8 node (c = 1/12), w_ij = k_a + k_b along the edges and 2 k_e across
+// the diagonals of a Q4 node (c = 1/6); a fixed row is the identity.  Each
+// term is then rounded relative to its own size, not relative to |x|.
+#include "common.cuh"
+#include "df64.cuh"
+
+namespace mgar {
+
+namespace {
+
+struct DfOp {
+  const float2* ke;
+  const uint8_t* fixed;
+  int ex, ey, ez, NX, NY, NZ, n;
+  FastDiv fNX, fNXY;
+  df scale;  // 1/6 (2D) or 1/12 (3D)
+};
+
+__device__ __forceinline__ df ld_kdf(const DfOp& op, int e, bool ok) {
+  const int ee = (ok && CK(e, op.ex * op.ey * op.ez)) ? e : 0;
+  const float2 v = op.ke[ee];
+  return ok ? df{v.x, v.y} : df{0.f, 0.f};
+}
+
+// neighbour value x^_j (0 when fixed or off the grid; off-grid terms also
+// have zero weight)
+__device__ __forceinline__ df ld_xdf(const DfOp& op, const float2* __restrict__ x, int idx, bool ok) {
+  const int j = (ok && CK(idx, op.n)) ? idx : 0;
+  const float2 v = x[j];
+  return (ok && !op.fixed[j]) ? df{v.x, v.y} : df{0.f, 0.f};
+}
+
+// acc += w * (xi - xj)
+__device__ __forceinline__ void df_term(df& acc, df w, df xi, df xj) {
+  float s, e;
+  two_sum(xi.hi, -xj.hi, s, e);
+  e = __fadd_rn(e, __fsub_rn(xi.lo, xj.lo));
+  acc = df_add(acc, df_mul(w, df_make(s, e)));
+}
+
+__device__ __forceinline__ df df_row2(const DfOp& op, const float2* __restrict__ x, int i, int j) {
+  const int idx = i + op.NX * j;
+  const float2 xv = x[idx];
+  const df xi{xv.x, xv.y};
+  if (op.fixed[idx]) return xi;
+  const bool xm = i > 0, xp = i < op.ex, ym = j > 0, yp = j < op.ey;
+  const int e00 = (i - 1) + op.ex * (j - 1);
+  const df k00 = ld_kdf(op, e00, xm && ym), k01 = ld_kdf(op, e00 + 1, xp && ym);
+  const df k10 = ld_kdf(op, e00 + op.ex, xm && yp), k11 = ld_kdf(op, e00 + op.ex + 1, xp && yp);
+  const int NX = op.NX;
+  df acc{0.f, 0.f};
+  df_term(acc, df_add(k00, k10), xi, ld_xdf(op, x, idx - 1, xm));
+  df_term(acc, df_add(k01, k11), xi, ld_xdf(op, x, idx + 1, xp));
+  df_term(acc, df_add(k00, k01), xi, ld_xdf(op, x, idx - NX, ym));
+  df_term(acc, df_add(k10, k11), xi, ld_xdf(op, x, idx + NX, yp));
+  df_term(acc, df_add(k00, k00), xi, ld_xdf(op, x, idx - NX - 1, xm && ym));
+  df_term(acc, df_add(k01, k01), xi, ld_xdf(op, x, idx - NX + 1, xp && ym));
+  df_term(acc, df_add(k10, k10), xi, ld_xdf(op, x, idx + NX - 1, xm && yp));
+  df_term(acc, df_add(k11, k11), xi, ld_xdf(op, x, idx + NX + 1, xp && yp));
+  return df_mul(acc, op.scale);
+}
+
+__device__ __forceinline__ df df_row3(const DfOp& op, const float2* __restrict__ x, int i, int j, int k) {
+  const int NX = op.NX, NXY = op.NX * op.NY;
+  const int idx = i + NX * j + NXY * k;
+  const float2 xv = x[idx];
+  const df xi{xv.x, xv.y};
+  if (op.fixed[idx]) return xi;
+  const bool xm = i > 0, xp = i < op.ex, ym = j > 0, yp = j < op.ey, zm = k > 0, zp = k < op.ez;
+  const int EX = op.ex, EXY = op.ex * op.ey;
+  const int e000 = (i - 1) + EX * (j - 1) + EXY * (k - 1);
+  const df k000 = ld_kdf(op, e000, xm && ym && zm);
+  const df k001 = ld_kdf(op, e000 + 1, xp && ym && zm);
+  const df k010 = ld_kdf(op, e000 + EX, xm && yp && zm);
+  const df k011 = ld_kdf(op, e000 + EX + 1, xp && yp && zm);
+  const df k100 = ld_kdf(op, e000 + EXY, xm && ym && zp);
+  const df k101 = ld_kdf(op, e000 + EXY + 1, xp && ym && zp);
+  const df k110 = ld_kdf(op, e000 + EXY + EX, xm && yp && zp);
+  const df k111 = ld_kdf(op, e000 + EXY + EX + 1, xp && yp && zp);
+  df acc{0.f, 0.f};
+  // face diagonals in the xy, xz and yz planes (two elements each)
+  df_term(acc, df_add(k000, k100), xi, ld_xdf(op, x, idx - 1 - NX, xm && ym));
+  df_term(acc, df_add(k001, k101), xi, ld_xdf(op, x, idx + 1 - NX, xp && ym));
+  df_term(acc, df_add(k010, k110), xi, ld_xdf(op, x, idx - 1 + NX, xm && yp));
+  df_term(acc, df_add(k011, k111), xi, ld_xdf(op, x, idx + 1 + NX, xp && yp));
+  df_term(acc, df_add(k000, k010), xi, ld_xdf(op, x, idx - 1 - NXY, xm && zm));
+  df_term(acc, df_add(k001, k011), xi, ld_xdf(op, x, idx + 1 - NXY, xp && zm));
+  df_term(acc, df_add(k100, k110), xi, ld_xdf(op, x, idx - 1 + NXY, xm && zp));
+  df_term(acc, df_add(k101, k111), xi, ld_xdf(op, x, idx + 1 + NXY, xp && zp));
+  df_term(acc, df_add(k000, k001), xi, ld_xdf(op, x, idx - NX - NXY, ym && zm));
+  df_term(acc, df_add(k010, k011), xi, ld_xdf(op, x, idx + NX - NXY, yp && zm));
+  df_term(acc, df_add(k100, k101), xi, ld_xdf(op, x, idx - NX + NXY, ym && zp));
+  df_term(acc, df_add(k110, k111), xi, ld_xdf(op, x, idx + NX + NXY, yp && zp));
+  // body diagonals (one element each)
+  df_term(acc, k000, xi, ld_xdf(op, x, idx - 1 - NX - NXY, xm && ym && zm));
+  df_term(acc, k001, xi, ld_xdf(op, x, idx + 1 - NX - NXY, xp && ym && zm));
+  df_term(acc, k010, xi, ld_xdf(op, x, idx - 1 + NX - NXY, xm && yp && zm));
+  df_term(acc, k011, xi, ld_xdf(op, x, idx + 1 + NX - NXY, xp && yp && zm));
+  df_term(acc, k100, xi, ld_xdf(op, x, idx - 1 - NX + NXY, xm && ym && zp));
+  df_term(acc, k101, xi, ld_xdf(op, x, idx + 1 - NX + NXY, xp && ym && zp));
+  df_term(acc, k110, xi, ld_xdf(op, x, idx - 1 + NX + NXY, xm && yp && zp));
+  df_term(acc, k111, xi, ld_xdf(op, x, idx + 1 + NX + NXY, xp && yp && zp));
+  return df_mul(acc, op.scale);
+}
+
+template <int DIM>
+__device__ __forceinline__ df df_row(const DfOp& op, const float2* __restrict__ x, int idx) {
+  int i, j, k;
+  coords(idx, op.fNX, op.fNXY, i, j, k);
+  return DIM == 2 ? df_row2(op, x, i, j) : df_row3(op, x, i, j, k);
+}
+
+__device__ __forceinline__ float2 pack(df a) { return make_float2(a.hi, a.lo); }
+__device__ __forceinline__ df unpack(float2 v) { return df{v.x, v.y}; }
+
+// y = A x; with DOT, x.y into out (per-thread df sums, FP64 across threads)
+template <int DIM, bool DOT>
+__global__ void k_df_apply(DfOp op, const float2* __restrict__ x, float2* __restrict__ y,
+                           double* partials, unsigned int* counter, double* out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  double v[1] = {0.0};
+  if (idx < op.n) {
+    const df yv = df_row<DIM>(op, x, idx);
+    y[idx] = pack(yv);
+    if (DOT) v[0] = df_to_double(df_mul(unpack(x[idx]), yv));
+  }
+  if (DOT) block_sum_finish<1>(v, partials, counter, out);
+}
+
+// r = q - A x and ||r||^2
+template <int DIM>
+__global__ void k_df_residual(DfOp op, const float2* __restrict__ q, const float2* __restrict__ x,
+                              float2* __restrict__ r, double* partials, unsigned int* counter,
+                              double* out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  double v[1] = {0.0};
+  if (idx < op.n) {
+    const df ri = df_sub(unpack(q[idx]), df_row<DIM>(op, x, idx));
+    r[idx] = pack(ri);
+    v[0] = df_to_double(df_mul(ri, ri));
+  }
+  block_sum_finish<1>(v, partials, counter, out);
+}
+
+// alpha = rz / pAp; x += alpha p; r -= alpha Ap; ||r||^2
+__global__ void k_df_cg_xr(float2* __restrict__ x, float2* __restrict__ r, const float2* __restrict__ p,
+                           const float2* __restrict__ Ap, int n, const double* __restrict__ rz,
+                           const double* __restrict__ pap, double* partials, unsigned int* counter,
+                           double* out) {
+  const df alpha = df_from_double(*rz / *pap);
+  df acc{0.f, 0.f};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    x[i] = pack(df_add(unpack(x[i]), df_mul(alpha, unpack(p[i]))));
+    const df ri = df_sub(unpack(r[i]), df_mul(alpha, unpack(Ap[i])));
+    r[i] = pack(ri);
+    acc = df_add(acc, df_mul(ri, ri));
+  }
+  double v[1] = {df_to_double(acc)};
+  block_sum_finish<1>(v, partials, counter, out);
+}
+
+// p = z + (rz_new / rz_old) p, z in FP32
+__global__ void k_df_cg_p(float2* __restrict__ p, const float* __restrict__ z, int n,
+                          const double* __restrict__ rz_new, const double* __restrict__ rz_old) {
+  const df beta = df_from_double(*rz_new / *rz_old);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    p[i] = pack(df_add(df{z[i], 0.f}, df_mul(beta, unpack(p[i]))));
+}
+
+// r . z with z in FP32
+__global__ void k_df_dot_f(const float2* __restrict__ r, const float* __restrict__ z, int n,
+                           double* partials, unsigned int* counter, double* out) {
+  df acc{0.f, 0.f};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    acc = df_add(acc, df_mulf(unpack(r[i]), z[i]));
+  double v[1] = {df_to_double(acc)};
+  block_sum_finish<1>(v, partials, counter, out);
+}
+
+__global__ void k_df_to_f32(const float2* __restrict__ a, float* __restrict__ b, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = __fadd_rn(a[i].x, a[i].y);
+}
+
+__global__ void k_f32_to_df(const float* __restrict__ a, float2* __restrict__ b, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = make_float2(a[i], 0.f);
+}
+
+__global__ void k_d_to_df(const double* __restrict__ a, float2* __restrict__ b, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = pack(df_from_double(a[i]));
+}
+
+__global__ void k_df_to_d(const float2* __restrict__ a, double* __restrict__ b, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = df_to_double(unpack(a[i]));
+}
+
+DfOp make_op(Ctx& c) {
+  const Dims& d = c.L[0];
+  DfOp op;
+  op.ke = c.ke_df;
+  op.fixed = c.fixed;
+  op.ex = d.ex;
+  op.ey = d.ey;
+  op.ez = d.ez;
+  op.NX = d.NX;
+  op.NY = d.NY;
+  op.NZ = d.NZ;
+  op.n = (int)d.n;
+  op.fNX = d.fNX;
+  op.fNXY = d.fNXY;
+  op.scale = df_from_double(c.dim == 2 ? 1.0 / 6.0 : 1.0 / 12.0);
+  return op;
+}
+
+}  // namespace
+
+// y = A x for FP64 vectors through df64 arithmetic (x converted on the way in,
+// y on the way out); the MGAR projection of the mixed path uses it.
+void apply_df64(Ctx& c, const double* x, double* y) {
+  const int n = (int)c.n;
+  ProfScope ps(c, MGAR_KC_APPLY64);
+  k_d_to_df<<<blocks_for(n), kThreads, 0, c.stream>>>(x, c.df_p, n);
+  MGAR_LAUNCH_CHECK();
+  const DfOp op = make_op(c);
+  if (c.dim == 2)
+    k_df_apply<2, false><<<blocks_for(n), kThreads, 0, c.stream>>>(op, c.df_p, c.df_Ap, nullptr,
+                                                                   nullptr, nullptr);
+  else
+    k_df_apply<3, false><<<blocks_for(n), kThreads, 0, c.stream>>>(op, c.df_p, c.df_Ap, nullptr,
+                                                                   nullptr, nullptr);
+  MGAR_LAUNCH_CHECK();
+  k_df_to_d<<<blocks_for(n), kThreads, 0, c.stream>>>(c.df_Ap, y, n);
+  MGAR_LAUNCH_CHECK();
+}
+
+// k_e of the current design in df64 form
+void ke_to_df(Ctx& c) {
+  k_d_to_df<<<blocks_for(c.ne), kThreads, 0, c.stream>>>(c.ke, c.ke_df, (int)c.ne);
+  MGAR_LAUNCH_CHECK();
+}
+
+void q_to_df(Ctx& c) {
+  k_d_to_df<<<blocks_for(c.n), kThreads, 0, c.stream>>>(c.q, c.df_q, (int)c.n);
+  MGAR_LAUNCH_CHECK();
+}
+
+// z32 = M r with r in df64: FP32 copy of r, then the FP32 V-cycle
+static void precondition_df(Ctx& c) {
+  const int n = (int)c.n;
+  const bool prof_inside = c.prof_class == MGAR_KC_SMOOTH0 || c.prof_class == MGAR_KC_RESID0;
+  run_graph(c, 6, c.df_r, c.x32, prof_inside, [&] {
+    k_df_to_f32<<<blocks_for(n), kThreads, 0, c.stream>>>(c.df_r, c.b32, n);
+    MGAR_LAUNCH_CHECK();
+    vcycle<float>(c, c.b32, c.x32, true);
+  });
+}
+
+int solve_mgcg_df(Ctx& c, double* T, int* iters, double* relres) {
+  const int n = (int)c.n;
+  const int rb = c.grid_blocks;
+  const DfOp op = make_op(c);
+  k_d_to_df<<<blocks_for(n), kThreads, 0, c.stream>>>(T, c.df_x, n);
+  MGAR_LAUNCH_CHECK();
+  {
+    ProfScope ps(c, MGAR_KC_APPLY64);
+    if (c.dim == 2)
+      k_df_residual<2><<<blocks_for(n), kThreads, 0, c.stream>>>(op, c.df_q, c.df_x, c.df_r,
+                                                                 c.partials, c.counter, c.dsc + S_RR);
+    else
+      k_df_residual<3><<<blocks_for(n), kThreads, 0, c.stream>>>(op, c.df_q, c.df_x, c.df_r,
+                                                                 c.partials, c.counter, c.dsc + S_RR);
+    MGAR_LAUNCH_CHECK();
+  }
+  fetch_scalars(c, S_RR, 1);
+  double rel = std::sqrt(c.hsc[S_RR]) / c.qnorm;
+  int it = 0;
+  if (!(rel <= c.p.eps2)) {
+    require(std::isfinite(rel), MGAR_ERR_NONFINITE, "non-finite initial residual");
+    precondition_df(c);
+    int a = S_RZ0, b = S_RZ1;
+    k_df_dot_f<<<rb, kThreads, 0, c.stream>>>(c.df_r, c.x32, n, c.partials, c.counter, c.dsc + a);
+    MGAR_LAUNCH_CHECK();
+    k_f32_to_df<<<blocks_for(n), kThreads, 0, c.stream>>>(c.x32, c.df_p, n);
+    MGAR_LAUNCH_CHECK();
+    while (it < c.p.cg_max) {
+      {
+        ProfScope ps(c, MGAR_KC_APPLY64);
+        if (c.dim == 2)
+          k_df_apply<2, true><<<blocks_for(n), kThreads, 0, c.stream>>>(
+              op, c.df_p, c.df_Ap, c.partials, c.counter, c.dsc + S_PAP);
+        else
+          k_df_apply<3, true><<<blocks_for(n), kThreads, 0, c.stream>>>(
+              op, c.df_p, c.df_Ap, c.partials, c.counter, c.dsc + S_PAP);
+        MGAR_LAUNCH_CHECK();
+      }
+      k_df_cg_xr<<<rb, kThreads, 0, c.stream>>>(c.df_x, c.df_r, c.df_p, c.df_Ap, n, c.dsc + a,
+                                                c.dsc + S_PAP, c.partials, c.counter, c.dsc + S_RR);
+      MGAR_LAUNCH_CHECK();
+      ++it;
+      fetch_scalars(c, S_RR, 1);
+      rel = std::sqrt(c.hsc[S_RR]) / c.qnorm;
+      require(std::isfinite(rel), MGAR_ERR_NONFINITE, "CG breakdown (non-finite residual)");
+      if (rel <= c.p.eps2) break;
+      precondition_df(c);
+      k_df_dot_f<<<rb, kThreads, 0, c.stream>>>(c.df_r, c.x32, n, c.partials, c.counter, c.dsc + b);
+      MGAR_LAUNCH_CHECK();
+      k_df_cg_p<<<rb, kThreads, 0, c.stream>>>(c.df_p, c.x32, n, c.dsc + b, c.dsc + a);
+      MGAR_LAUNCH_CHECK();
+      std::swap(a, b);
+    }
+  }
+  k_df_to_d<<<blocks_for(n), kThreads, 0, c.stream>>>(c.df_x, T, n);
+  MGAR_LAUNCH_CHECK();
+  if (iters) *iters = it;
+  if (relres) *relres = rel;
+  return rel <= c.p.eps2 ? MGAR_OK : MGAR_ERR_MAXIT;
+}
+
+}  // namespace mgar

@@ -41,9 +41,9 @@ constexpr int kThreads = 256;
 constexpr int kMaxFilterOffsets = 1024;
 constexpr int kMaxM = 8;
 constexpr int kOcCand = 31;      // multisection candidates per pass (5 bits)
-constexpr int kOcPasses = 5;     // FP32 passes: ln-bracket 92 -> 3e-6
+constexpr int kOcPasses = 6;     // FP32 passes: ln-bracket 92 -> 9e-8
 constexpr int kOcAmbMax = 4096;  // ambiguous elements handled by the FP64 finish
-constexpr double kOcMargin = 1e-3;  // ln-bracket widening that absorbs FP32 volume rounding
+constexpr double kOcMargin = 2e-5;  // ln-bracket widening that absorbs FP32 volume rounding
 constexpr size_t kBandSmemMax = 160 * 1024;  // band factorised in shared memory up to this size
 
 // Slots of the device scalar array.
@@ -116,6 +116,7 @@ struct Ctx {
 
   // fine level, problem data
   uint8_t* fixed = nullptr;
+  uint8_t* efix = nullptr;   // per fine element: 1 if any of its nodes is fixed
   double* q = nullptr;
   double qnorm = 0.0;
   double* rho_phys = nullptr;
@@ -127,6 +128,7 @@ struct Ctx {
   int4* f_offs = nullptr;   // filter offsets (dx, dy, dz)
   double* f_w = nullptr;    // filter weights max(0, r - |d|)
   double* dv = nullptr;     // F^T (1/E)
+  double* rsdv = nullptr;   // 1 / sqrt(dv)
   int n_filter = 0;
 
   // hierarchy
@@ -139,12 +141,16 @@ struct Ctx {
   double* cinv = nullptr;   // [nc][nc] inverse of the coarsest operator
   float* cinv_f = nullptr;
   double* tables = nullptr;  // k0 (nen^2) then Galerkin sub-element tables G
+  float* tables_f = nullptr; // G in FP32
 
   // Krylov / reanalysis vectors
   double *r = nullptr, *z = nullptr, *pv = nullptr, *Ap = nullptr, *tm = nullptr;
   double* tmp_dc = nullptr;
   double *R = nullptr, *W = nullptr;    // [m][n]
   float *b32 = nullptr, *x32 = nullptr; // mixed-mode level-0 buffers
+  // mixed mode: double-float (hi, lo) copies for the outer CG
+  float2 *ke_df = nullptr, *df_q = nullptr, *df_x = nullptr, *df_r = nullptr, *df_p = nullptr,
+         *df_Ap = nullptr;
   double *tmp_e = nullptr, *oc_s = nullptr, *oc_lo = nullptr, *oc_hi = nullptr;
   float *oc_s32 = nullptr, *oc_lo32 = nullptr, *oc_hi32 = nullptr, *dv32 = nullptr;
   int *oc_amb = nullptr, *oc_namb = nullptr;
@@ -179,9 +185,15 @@ struct Ctx {
   int prof_class = 0;
   int prof_used = 0;
   cudaEvent_t* prof_ev = nullptr;  // [2 * kProfMax]
+  // timeline mode (prof_class == MGAR_KC_TIMELINE): an event after every
+  // launch site; device time between consecutive marks goes to the later site
+  const char** prof_sites = nullptr;  // [2 * kProfMax]
+  std::string prof_report;
 };
 
 constexpr int kProfMax = 65536;
+// handle whose API call is running on this host thread (set by the C ABI)
+Ctx*& current_ctx();
 
 // Brackets the launches issued in its scope with two events when the
 // handle is timing kernel class `kc`.
@@ -212,14 +224,19 @@ struct Error {
       throw ::mgar::Error{MGAR_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
   } while (0)
 
-// Every kernel launch is followed by MGAR_LAUNCH_CHECK(), which also counts it.
+// Every kernel launch is followed by MGAR_LAUNCH_CHECK(), which also counts
+// it and, while a handle records a device timeline, marks the launch site.
 void count_launch();
 void count_launches(int64_t delta);
 int64_t launches_so_far();
-#define MGAR_LAUNCH_CHECK()            \
-  do {                                 \
-    ::mgar::count_launch();            \
-    MGAR_CUDA(cudaGetLastError());     \
+void prof_mark(const char* site);
+#define MGAR_STR2(x) #x
+#define MGAR_STR(x) MGAR_STR2(x)
+#define MGAR_LAUNCH_CHECK()                              \
+  do {                                                   \
+    ::mgar::count_launch();                              \
+    ::mgar::prof_mark(__FILE__ ":" MGAR_STR(__LINE__));  \
+    MGAR_CUDA(cudaGetLastError());                       \
   } while (0)
 
 inline void require(bool ok, int code, const std::string& msg) {
@@ -234,9 +251,11 @@ inline int blocks_for(int64_t n, int threads = kThreads) {
 // ------------------------------------------------------------ reductions
 // Deterministic block sum of N values: each block's partial sums go to
 // partials[k*gridDim.x + blockIdx.x]; the last block to arrive (ticket on
-// *counter) adds them up in block order, resets the ticket, and returns true
-// with the totals in every thread.  Other blocks return false.  Every thread
-// of every block must call it.
+// *counter) adds them up, every thread accumulating all N sums over its
+// share of the blocks (independent loads, no barrier per value), resets the
+// ticket, and returns true with the totals in every thread.  Other blocks
+// return false.  Every thread of every block must call it.  The summation
+// order is fixed, so results are reproducible run to run.
 template <int N>
 __device__ __forceinline__ bool block_sum_last(double (&v)[N], double* partials,
                                                unsigned int* counter, double (&total)[N]) {
@@ -252,40 +271,40 @@ __device__ __forceinline__ bool block_sum_last(double (&v)[N], double* partials,
     if (lane == 0) sh[k][warp] = s;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-      double s = 0.0;
-      for (int w = 0; w < nw; ++w) s += sh[k][w];
-      if (CK(k * gridDim.x + blockIdx.x, g_partials_len)) partials[k * gridDim.x + blockIdx.x] = s;
-    }
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += sh[k][w];
+    if (CK(k * gridDim.x + blockIdx.x, g_partials_len)) partials[k * gridDim.x + blockIdx.x] = s;
     __threadfence();
-    unsigned int t = atomicAdd(counter, 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned int t = atomicAdd(counter, 1u);
     last = (t == gridDim.x - 1);
   }
   __syncthreads();
   if (!last) return false;
   __threadfence();
+  double acc[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) acc[k] = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < N; ++k) acc[k] += ((volatile double*)partials)[k * gridDim.x + b];
 #pragma unroll
   for (int k = 0; k < N; ++k) {
-    double s = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-      s += ((volatile double*)partials)[k * gridDim.x + b];
+    double s = acc[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    __syncthreads();
     if (lane == 0) sh[k][warp] = s;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-      double s = 0.0;
-      for (int w = 0; w < nw; ++w) s += sh[k][w];
-      tot[k] = s;
-    }
-    *counter = 0u;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += sh[k][w];
+    tot[k] = s;
   }
+  if (threadIdx.x == 0) *counter = 0u;
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < N; ++k) total[k] = tot[k];
@@ -551,6 +570,11 @@ void apply_dK64(Ctx& c, const double* x, double* y);
 void apply_dK32(Ctx& c, const float* x, float* y);
 void convert_d2f(Ctx& c, const double* a, float* b, int64_t n);
 void convert_f2d(Ctx& c, const float* a, double* b, int64_t n);
+// cg_df.cu (mixed precision: df64 outer CG)
+int solve_mgcg_df(Ctx& c, double* T, int* iters, double* relres);
+void apply_df64(Ctx& c, const double* x, double* y);
+void ke_to_df(Ctx& c);
+void q_to_df(Ctx& c);
 // solvers.cu
 int solve_mgcg(Ctx& c, double* T, int* iters, double* relres);
 void solve_mgar(Ctx& c, const double* T_prev, double* T, double* res, int* accepted);
@@ -622,5 +646,9 @@ void run_graph(Ctx& c, int kind, const void* a, const void* b, bool profiled_ins
   }
   MGAR_CUDA(cudaGraphLaunch(hit->exec, c.stream));
   count_launches(hit->kernels);
+  static const char* kGraphSites[] = {"graph:0", "graph:1 precondition", "graph:2 mgar-vcycle64-zero",
+                                      "graph:3 mgar-vcycle64-guess", "graph:4 mgar-vcycle32-zero",
+                                      "graph:5 mgar-vcycle32-guess", "graph:6", "graph:7"};
+  prof_mark(kGraphSites[kind & 7]);
 }
 }  // namespace mgar

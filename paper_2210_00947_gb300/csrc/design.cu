@@ -103,15 +103,16 @@ __global__ void k_elem_sens(const double* __restrict__ T, const double* __restri
   out[e] = -coef * rp * energy;
 }
 
-// OC preparation: s_e = rho_e sqrt(max(-dc_e, 0) / dv_e) and the move box.
+// OC preparation: s_e = rho_e sqrt(max(-dc_e, 0) / dv_e) and the move box;
+// rsdv = 1 / sqrt(dv) is fixed by the filter and computed once.
 __global__ void k_oc_prep(const double* __restrict__ rho, const double* __restrict__ dc,
-                          const double* __restrict__ dv, double* __restrict__ s,
+                          const double* __restrict__ rsdv, double* __restrict__ s,
                           double* __restrict__ lo, double* __restrict__ hi, int64_t ne,
                           double move) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= ne) return;
   const double r = rho[e];
-  s[e] = r * sqrt(fmax(-dc[e], 0.0) / dv[e]);
+  s[e] = r * sqrt(fmax(-dc[e], 0.0)) * rsdv[e];
   lo[e] = fmax(0.0, r - move);
   hi[e] = fmin(1.0, r + move);
 }
@@ -348,6 +349,11 @@ __global__ void k_oc_apply(double* __restrict__ rho, const double* __restrict__ 
   if (blockIdx.x == 0 && threadIdx.x == 0) dsc[S_OC_LAM] = 1.0 / (mu * mu);
 }
 
+__global__ void k_rsqrt_e(const double* __restrict__ a, double* __restrict__ b, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = 1.0 / sqrt(a[i]);
+}
+
 __global__ void k_d2f_e(const double* __restrict__ a, float* __restrict__ b, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
@@ -397,6 +403,8 @@ void setup_filter(Ctx& c) {
   filter(c, c.tmp_e, c.dv, true);
   k_d2f_e<<<blocks_for(c.ne), kThreads, 0, c.stream>>>(c.dv, c.dv32, (int)c.ne);
   MGAR_LAUNCH_CHECK();
+  k_rsqrt_e<<<blocks_for(c.ne), kThreads, 0, c.stream>>>(c.dv, c.rsdv, (int)c.ne);
+  MGAR_LAUNCH_CHECK();
   MGAR_CUDA(cudaStreamSynchronize(c.stream));
 }
 
@@ -422,6 +430,7 @@ void set_density(Ctx& c, const double* rho, bool physical) {
                                                       c.p.precision == MGAR_FP64 ? nullptr : c.ke_f,
                                                       c.ne, c.p.k0, c.p.kmin, c.p.penal);
   MGAR_LAUNCH_CHECK();
+  if (c.p.precision == MGAR_MIXED) ke_to_df(c);
 }
 
 void sensitivity(Ctx& c, const double* T, double* dc, double* dv, double* compliance) {
@@ -455,8 +464,8 @@ void oc_update(Ctx& c, double* rho, const double* dc, double volfrac, double mov
                double* change) {
   const int ne = (int)c.ne;
   const int rb = c.grid_blocks_e;
-  k_oc_prep<<<blocks_for(ne), kThreads, 0, c.stream>>>(rho, dc, c.dv, c.oc_s, c.oc_lo, c.oc_hi, ne,
-                                                       move);
+  k_oc_prep<<<blocks_for(ne), kThreads, 0, c.stream>>>(rho, dc, c.rsdv, c.oc_s, c.oc_lo, c.oc_hi,
+                                                       ne, move);
   MGAR_LAUNCH_CHECK();
   // lambda in [1e-40, 1e40]  <=>  ln(mu) in [-20 ln 10, 20 ln 10]
   const double Lmax = 20.0 * std::log(10.0), Lmin = -Lmax;
@@ -468,8 +477,9 @@ void oc_update(Ctx& c, double* rho, const double* dc, double volfrac, double mov
     MGAR_LAUNCH_CHECK();
     k_oc_start<<<1, 32, 0, c.stream>>>(c.dsc, Lmin, Lmax);
     MGAR_LAUNCH_CHECK();
+    const int msb = std::min(rb, 152 * 2);  // one wave of blocks: short reduction tail
     for (int pass = 0; pass < kOcPasses; ++pass) {
-      k_oc_multisect<<<rb, kThreads, 0, c.stream>>>(c.oc_s32, c.oc_lo32, c.oc_hi32, c.dv32, ne,
+      k_oc_multisect<<<msb, kThreads, 0, c.stream>>>(c.oc_s32, c.oc_lo32, c.oc_hi32, c.dv32, ne,
                                                     volfrac, c.dsc, c.partials, c.counter);
       MGAR_LAUNCH_CHECK();
     }

@@ -21,16 +21,17 @@ namespace mgar {
 
 // 1D interpolation weight of coarse local node c onto fine local node f of a
 // sub-element of position type t (0: first half, 1: second half, 2: the
-// single fine element of a truncated coarse element).
-__host__ __device__ __forceinline__ double w1(int t, int f, int c) {
-  if (t == 0) return f == 0 ? (c == 0 ? 1.0 : 0.0) : 0.5;
-  if (t == 1) return f == 1 ? (c == 1 ? 1.0 : 0.0) : 0.5;
-  return f == c ? 1.0 : 0.0;
+// single fine element of a truncated coarse element).  Values are exact in
+// any precision.
+__host__ __device__ __forceinline__ float w1(int t, int f, int c) {
+  if (t == 0) return f == 0 ? (c == 0 ? 1.f : 0.f) : 0.5f;
+  if (t == 1) return f == 1 ? (c == 1 ? 1.f : 0.f) : 0.5f;
+  return f == c ? 1.f : 0.f;
 }
 
 template <int DIM>
-__device__ __forceinline__ double pw(const int (&t)[3], int a, int I) {
-  double w = w1(t[0], a & 1, I & 1) * w1(t[1], (a >> 1) & 1, (I >> 1) & 1);
+__device__ __forceinline__ float pw(const int (&t)[3], int a, int I) {
+  float w = w1(t[0], a & 1, I & 1) * w1(t[1], (a >> 1) & 1, (I >> 1) & 1);
   if (DIM == 3) w *= w1(t[2], (a >> 2) & 1, (I >> 2) & 1);
   return w;
 }
@@ -46,117 +47,145 @@ static void unit_element(int dim, double* k) {
     }
 }
 
+// Unique (I <= J) entries of a symmetric 2^d x 2^d element matrix, spread
+// evenly over the 2^d threads that build one coarse element.
+__device__ __forceinline__ void pair_of(int u, int nen, int& I, int& J) {
+  I = 0;
+  int rowlen = nen;
+  while (u >= rowlen) {
+    u -= rowlen;
+    ++I;
+    --rowlen;
+  }
+  J = I + u;
+}
+
+// Sub-element s of coarse element (cx, cy, cz): fine element index, validity
+// and 1D position types.
+template <int DIM>
+__device__ __forceinline__ bool sub_element(const Dims& f, int cx, int cy, int cz, int s, int& e,
+                                            int (&t)[3]) {
+  const int sx = s & 1, sy = (s >> 1) & 1, sz = (s >> 2) & 1;
+  const int fx = 2 * cx + sx, fy = 2 * cy + sy, fz = 2 * cz + sz;
+  const bool ok = !(fx >= f.ex || fy >= f.ey || (DIM == 3 && fz >= f.ez));
+  e = ok ? fx + f.ex * (fy + f.ey * fz) : 0;  // a valid address either way
+  t[0] = (2 * cx + 1 < f.ex) ? sx : 2;
+  t[1] = (2 * cy + 1 < f.ey) ? sy : 2;
+  t[2] = DIM == 3 ? ((2 * cz + 1 < f.ez) ? sz : 2) : 0;
+  return ok;
+}
+
 // ------------------------------------------------------------------ kernels
-// Level 0 -> 1: element matrices of A_1 from k_e, one thread per (coarse
-// element, row I).
+// Level 0 -> 1: element matrices of A_1 from k_e, 2^d threads per coarse
+// element, each computing its share of the unique entries.  Sub-elements
+// without fixed nodes use the tables G_type = P_type^T k0 P_type; a coarse
+// element with any fixed fine node takes (Z P)^T k0 (Z P) entry by entry.
 template <typename Real, int DIM>
 __global__ void k_galerkin_fine(const Real* __restrict__ ke, const uint8_t* __restrict__ fixed,
-                                Dims f, Dims cd, const double* __restrict__ G,
-                                const double* __restrict__ k0, Real* __restrict__ elem) {
+                                const uint8_t* __restrict__ efix, Dims f, Dims cd,
+                                const Real* __restrict__ G, const double* __restrict__ k0,
+                                Real* __restrict__ elem) {
   constexpr int nen = 1 << DIM;
+  constexpr int npairs = nen * (nen + 1) / 2;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= (int)cd.ne * nen) return;
   const int E = tid / nen;
-  const int I = tid - E * nen;
+  const int th = tid - E * nen;
   int cx, cy, cz;
   coords(E, cd.fEX, cd.fEXY, cx, cy, cz);
-  double out[nen];
+  Real kv[nen];
+  int ty[nen], sub_ok = 0, any_fixed = 0;
 #pragma unroll
-  for (int J = 0; J < nen; ++J) out[J] = 0.0;
-  const int nsub = 1 << DIM;
-  for (int s = 0; s < nsub; ++s) {
-    const int sx = s & 1, sy = (s >> 1) & 1, sz = (s >> 2) & 1;
-    const int fx = 2 * cx + sx, fy = 2 * cy + sy, fz = 2 * cz + sz;
-    const bool ok = !(fx >= f.ex || fy >= f.ey || (DIM == 3 && fz >= f.ez));
-    const int e = ok ? fx + f.ex * (fy + f.ey * fz) : 0;  // valid address either way
-    if (!ok || !CK(e, f.ne)) continue;
-    int t[3];
-    t[0] = (2 * cx + 1 < f.ex) ? sx : 2;
-    t[1] = (2 * cy + 1 < f.ey) ? sy : 2;
-    t[2] = DIM == 3 ? ((2 * cz + 1 < f.ez) ? sz : 2) : 0;
-    const double k = (double)ke[e];
-    // fixed nodes of the sub-element
-    unsigned fmask = 0;
-#pragma unroll
-    for (int a = 0; a < nen; ++a) {
-      const int nd = (fx + (a & 1)) + f.NX * ((fy + ((a >> 1) & 1)) + f.NY * (fz + ((a >> 2) & 1)));
-      if (CK(nd, f.n) && fixed[nd]) fmask |= 1u << a;
-    }
-    if (fmask == 0) {
-      const int type = t[0] + 3 * t[1] + 9 * t[2];
-      const double* g = G + (size_t)type * nen * nen + I * nen;
-#pragma unroll
-      for (int J = 0; J < nen; ++J)
-        if (CK((size_t)type * nen * nen + I * nen + J, (DIM == 2 ? 9 : 27) * nen * nen)) out[J] += k * g[J];
-    } else {
-      // (Z P_s)^T (k k0) (Z P_s), row I
-      for (int a = 0; a < nen; ++a) {
-        if (fmask & (1u << a)) continue;
-        const double pa = pw<DIM>(t, a, I);
-        if (pa == 0.0) continue;
-        for (int b = 0; b < nen; ++b) {
-          if (fmask & (1u << b)) continue;
-          const double m = k * k0[a * nen + b] * pa;
-#pragma unroll
-          for (int J = 0; J < nen; ++J) out[J] += m * pw<DIM>(t, b, J);
-        }
-      }
+  for (int s = 0; s < nen; ++s) {
+    int e, t[3];
+    const bool ok = sub_element<DIM>(f, cx, cy, cz, s, e, t) && CK(e, f.ne);
+    kv[s] = ok ? ke[e] : Real(0);
+    ty[s] = t[0] + 3 * t[1] + 9 * t[2];
+    if (ok) {
+      sub_ok |= 1 << s;
+      any_fixed |= efix[e];
     }
   }
-  Real* dst = elem + (size_t)E * nen * nen + I * nen;
+  Real* dst = elem + (size_t)E * nen * nen;
+  for (int u = th; u < npairs; u += nen) {
+    int I, J;
+    pair_of(u, nen, I, J);
+    Real acc = Real(0);
+    if (!any_fixed) {
 #pragma unroll
-  for (int J = 0; J < nen; ++J)
-    if (CK((size_t)E * nen * nen + I * nen + J, cd.ne * nen * nen)) dst[J] = (Real)out[J];
+      for (int s = 0; s < nen; ++s)
+        acc += kv[s] * G[(size_t)ty[s] * nen * nen + I * nen + J];
+    } else {
+      for (int s = 0; s < nen; ++s) {
+        if (!(sub_ok & (1 << s))) continue;
+        int e, t[3];
+        sub_element<DIM>(f, cx, cy, cz, s, e, t);
+        const int fx = 2 * cx + (s & 1), fy = 2 * cy + ((s >> 1) & 1), fz = 2 * cz + ((s >> 2) & 1);
+        unsigned fm = 0;
+        for (int a = 0; a < nen; ++a) {
+          const int nd = (fx + (a & 1)) + f.NX * ((fy + ((a >> 1) & 1)) + f.NY * (fz + ((a >> 2) & 1)));
+          if (CK(nd, f.n) && fixed[nd]) fm |= 1u << a;
+        }
+        Real part = Real(0);
+        for (int a = 0; a < nen; ++a) {
+          const float pa = pw<DIM>(t, a, I);
+          if ((fm & (1u << a)) || pa == 0.f) continue;
+          for (int b = 0; b < nen; ++b) {
+            const float pb = pw<DIM>(t, b, J);
+            if ((fm & (1u << b)) || pb == 0.f) continue;
+            part += (Real)(pa * pb) * (Real)k0[a * nen + b];
+          }
+        }
+        acc += kv[s] * part;
+      }
+    }
+    if (CK((size_t)E * nen * nen + I * nen + J, cd.ne * nen * nen)) {
+      dst[I * nen + J] = acc;
+      dst[J * nen + I] = acc;
+    }
+  }
 }
 
-// Level l -> l+1 (l >= 1) from stored element matrices.
+// Level l -> l+1 (l >= 1) from stored element matrices: entry (I, J) of the
+// coarse element is sum_s sum_a sum_b P_s[a,I] M_s[a,b] P_s[b,J].
 template <typename Real, int DIM>
 __global__ void k_galerkin_coarse(const Real* __restrict__ elem_f, Dims f, Dims cd,
                                   Real* __restrict__ elem_c) {
   constexpr int nen = 1 << DIM;
+  constexpr int npairs = nen * (nen + 1) / 2;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= (int)cd.ne * nen) return;
   const int E = tid / nen;
-  const int I = tid - E * nen;
+  const int th = tid - E * nen;
   int cx, cy, cz;
   coords(E, cd.fEX, cd.fEXY, cx, cy, cz);
-  Real out[nen];
+  Real* dst = elem_c + (size_t)E * nen * nen;
+  for (int u = th; u < npairs; u += nen) {
+    int I, J;
+    pair_of(u, nen, I, J);
+    Real acc = Real(0);
+    for (int s = 0; s < nen; ++s) {
+      int e, t[3];
+      if (!sub_element<DIM>(f, cx, cy, cz, s, e, t) || !CK(e, f.ne)) continue;
+      const Real* M = elem_f + (size_t)e * nen * nen;
 #pragma unroll
-  for (int J = 0; J < nen; ++J) out[J] = Real(0);
-  for (int s = 0; s < nen; ++s) {
-    const int sx = s & 1, sy = (s >> 1) & 1, sz = (s >> 2) & 1;
-    const int fx = 2 * cx + sx, fy = 2 * cy + sy, fz = 2 * cz + sz;
-    const bool ok = !(fx >= f.ex || fy >= f.ey || (DIM == 3 && fz >= f.ez));
-    const int e = ok ? fx + f.ex * (fy + f.ey * fz) : 0;  // valid address either way
-    if (!ok || !CK(e, f.ne)) continue;
-    int t[3];
-    t[0] = (2 * cx + 1 < f.ex) ? sx : 2;
-    t[1] = (2 * cy + 1 < f.ey) ? sy : 2;
-    t[2] = DIM == 3 ? ((2 * cz + 1 < f.ez) ? sz : 2) : 0;
-    const Real* M = elem_f + (size_t)e * nen * nen;
-    Real v[nen];
+      for (int a = 0; a < nen; ++a) {
+        const float pa = pw<DIM>(t, a, I);
+        if (pa == 0.f) continue;
+        Real row = Real(0);
 #pragma unroll
-    for (int b = 0; b < nen; ++b) v[b] = Real(0);
-#pragma unroll
-    for (int a = 0; a < nen; ++a) {
-      const Real pa = (Real)pw<DIM>(t, a, I);
-      if (pa == Real(0)) continue;
-#pragma unroll
-      for (int b = 0; b < nen; ++b) v[b] += pa * M[a * nen + b];
-    }
-#pragma unroll
-    for (int b = 0; b < nen; ++b) {
-#pragma unroll
-      for (int J = 0; J < nen; ++J) {
-        const Real pb = (Real)pw<DIM>(t, b, J);
-        if (pb != Real(0)) out[J] += v[b] * pb;
+        for (int b = 0; b < nen; ++b) {
+          const float pb = pw<DIM>(t, b, J);
+          if (pb != 0.f) row += (Real)pb * M[a * nen + b];
+        }
+        acc += (Real)pa * row;
       }
     }
+    if (CK((size_t)E * nen * nen + I * nen + J, cd.ne * nen * nen)) {
+      dst[I * nen + J] = acc;
+      dst[J * nen + I] = acc;
+    }
   }
-  Real* dst = elem_c + (size_t)E * nen * nen + I * nen;
-#pragma unroll
-  for (int J = 0; J < nen; ++J)
-    if (CK((size_t)E * nen * nen + I * nen + J, cd.ne * nen * nen)) dst[J] = out[J];
 }
 
 // Node stencils and inverse diagonal of a level from its element matrices.
@@ -292,44 +321,53 @@ __global__ void k_band_cholesky(double* __restrict__ gband, double* __restrict__
 
 // Columns of the inverse, one warp per column: forward then backward
 // substitution with the band factor; inv is row-major n x n.  With SMEM the
-// band is staged in shared memory once per block.
+// band is staged in shared memory once per block and each warp keeps its
+// column there too (the substitutions are chains of dependent reads).
 template <bool SMEM>
 __global__ void k_band_inverse(const double* __restrict__ gband, const double* __restrict__ rdiag,
                                int n, int bw, double* inv) {
   extern __shared__ double sband[];
   const int ld = bw + 1;
+  const int warps = blockDim.x >> 5;
+  const int wid = threadIdx.x >> 5;
   const double* band = gband;
+  double* colbuf = nullptr;
   if (SMEM) {
     const int64_t size = (int64_t)n * ld;
     for (int64_t t = threadIdx.x; t < size; t += blockDim.x) sband[t] = gband[t];
     __syncthreads();
     band = sband;
+    colbuf = sband + size + (int64_t)wid * n;
   }
-  const int warps = blockDim.x >> 5;
-  const int col = blockIdx.x * warps + (threadIdx.x >> 5);
+  const int col = blockIdx.x * warps + wid;
   const int lane = threadIdx.x & 31;
   if (col >= n) return;
+  // column values live in colbuf (shared) or in inv itself (global)
+  auto cv = [&](int i) -> double& { return SMEM ? colbuf[i] : inv[(int64_t)i * n + col]; };
+  if (SMEM)
+    for (int i = lane; i < n; i += 32) colbuf[i] = 0.0;
+  __syncwarp();
   for (int i = col; i < n; ++i) {
     double s = 0.0;
     for (int p = max(col, i - bw) + lane; p < i; p += 32)
-      if (CK((int64_t)i * ld + (p - i + bw), (int64_t)n * ld) && CK(p - i + bw, ld) &&
-          CK((int64_t)p * n + col, (int64_t)n * n))
-        s += band[(int64_t)i * ld + (p - i + bw)] * inv[(int64_t)p * n + col];
+      if (CK((int64_t)i * ld + (p - i + bw), (int64_t)n * ld) && CK(p - i + bw, ld))
+        s += band[(int64_t)i * ld + (p - i + bw)] * cv(p);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) inv[(int64_t)i * n + col] = ((i == col ? 1.0 : 0.0) - s) * rdiag[i];
+    if (lane == 0) cv(i) = ((i == col ? 1.0 : 0.0) - s) * rdiag[i];
     __syncwarp();
   }
   for (int i = n - 1; i >= 0; --i) {
     double s = 0.0;
     const int last = min(n - 1, i + bw);
     for (int p = i + 1 + lane; p <= last; p += 32)
-      if (CK((int64_t)p * ld + (i - p + bw), (int64_t)n * ld) && CK(i - p + bw, ld) &&
-          CK((int64_t)p * n + col, (int64_t)n * n))
-        s += band[(int64_t)p * ld + (i - p + bw)] * inv[(int64_t)p * n + col];
+      if (CK((int64_t)p * ld + (i - p + bw), (int64_t)n * ld) && CK(i - p + bw, ld))
+        s += band[(int64_t)p * ld + (i - p + bw)] * cv(p);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) inv[(int64_t)i * n + col] = (inv[(int64_t)i * n + col] - s) * rdiag[i];
+    if (lane == 0) cv(i) = (cv(i) - s) * rdiag[i];
     __syncwarp();
   }
+  if (SMEM)
+    for (int i = lane; i < n; i += 32) inv[(int64_t)i * n + col] = colbuf[i];
 }
 
 __global__ void k_d2f(const double* a, float* b, int64_t n) {
@@ -412,6 +450,9 @@ void alloc_hierarchy(Ctx& c) {
   MGAR_CUDA(cudaMemcpy(c.tables, k0.data(), k0.size() * sizeof(double), cudaMemcpyHostToDevice));
   MGAR_CUDA(cudaMemcpy(c.tables + k0.size(), G.data(), G.size() * sizeof(double),
                        cudaMemcpyHostToDevice));
+  std::vector<float> Gf(G.begin(), G.end());
+  MGAR_CUDA(cudaMalloc(&c.tables_f, Gf.size() * sizeof(float)));
+  MGAR_CUDA(cudaMemcpy(c.tables_f, Gf.data(), Gf.size() * sizeof(float), cudaMemcpyHostToDevice));
 }
 
 void free_hierarchy(Ctx& c) {
@@ -422,6 +463,8 @@ void free_hierarchy(Ctx& c) {
   cudaFree(c.cinv);
   cudaFree(c.cinv_f);
   cudaFree(c.tables);
+  cudaFree(c.tables_f);
+  c.tables_f = nullptr;
   c.band = nullptr;
   c.rdiag = nullptr;
   c.cinv = nullptr;
@@ -429,12 +472,19 @@ void free_hierarchy(Ctx& c) {
   c.tables = nullptr;
 }
 
+template <typename Real>
+static const Real* g_tables(Ctx& c);
+template <>
+const double* g_tables<double>(Ctx& c) { return c.tables + c.nen * c.nen; }
+template <>
+const float* g_tables<float>(Ctx& c) { return c.tables_f; }
+
 template <typename Real, int DIM>
 static void build_levels(Ctx& c, const Real* ke0, LevelBuf<Real>* h) {
   cudaStream_t s = c.stream;
   const int nen = 1 << DIM;
   const double* k0 = c.tables;
-  const double* G = c.tables + nen * nen;
+  const Real* G = g_tables<Real>(c);
   k_fine_dinv<Real, DIM><<<blocks_for(c.L[0].n), kThreads, 0, s>>>(ke0, c.fixed, c.L[0], h[0].dinv);
   MGAR_LAUNCH_CHECK();
   for (int l = 0; l + 1 < c.nl; ++l) {
@@ -443,8 +493,8 @@ static void build_levels(Ctx& c, const Real* ke0, LevelBuf<Real>* h) {
     const int64_t work = cd.ne * nen;
     ProfScope ps(c, l == 0 ? MGAR_KC_GALERKIN0 : -1);
     if (l == 0)
-      k_galerkin_fine<Real, DIM><<<blocks_for(work), kThreads, 0, s>>>(ke0, c.fixed, f, cd, G, k0,
-                                                                         h[1].elem);
+      k_galerkin_fine<Real, DIM><<<blocks_for(work), kThreads, 0, s>>>(ke0, c.fixed, c.efix, f, cd, G,
+                                                                         k0, h[1].elem);
     else
       k_galerkin_coarse<Real, DIM><<<blocks_for(work), kThreads, 0, s>>>(h[l].elem, f, cd,
                                                                            h[l + 1].elem);
@@ -466,8 +516,9 @@ static void build_levels(Ctx& c, const Real* ke0, LevelBuf<Real>* h) {
   }
   MGAR_LAUNCH_CHECK();
   MGAR_CUDA(cudaMemsetAsync(c.cinv, 0, (size_t)c.nc * c.nc * sizeof(double), s));
-  if (smem)
-    k_band_inverse<true><<<(c.nc + 7) / 8, 256, band_bytes, s>>>(c.band, c.rdiag, c.nc, c.bw, c.cinv);
+  const size_t inv_smem = band_bytes + (size_t)8 * c.nc * sizeof(double);
+  if (smem && inv_smem <= kBandSmemMax)
+    k_band_inverse<true><<<(c.nc + 7) / 8, 256, inv_smem, s>>>(c.band, c.rdiag, c.nc, c.bw, c.cinv);
   else
     k_band_inverse<false><<<(c.nc + 7) / 8, 256, 0, s>>>(c.band, c.rdiag, c.nc, c.bw, c.cinv);
   MGAR_LAUNCH_CHECK();

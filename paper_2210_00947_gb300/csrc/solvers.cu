@@ -78,16 +78,17 @@ __global__ void k_axpy_dev(double* __restrict__ v, const double* __restrict__ u,
     v[i] -= a * u[i];
 }
 
+// y = a - y
+__global__ void k_sub_from(double* __restrict__ y, const double* __restrict__ a, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a[i] - y[i];
+}
+
 __global__ void k_scale(double* __restrict__ v, int64_t n, double s) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     v[i] *= s;
-}
-
-__global__ void k_neg_copy(const double* __restrict__ a, double* __restrict__ b, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    b[i] = a[i];
 }
 
 // Reduced m x m solve (Eq. 19-21): K_R y = q_R by Cholesky, one thread.
@@ -199,6 +200,7 @@ static void residual_norm(Ctx& c, const double* x, double* r, double* out) {
 int solve_mgcg(Ctx& c, double* T, int* iters, double* relres) {
   build_hierarchy(c);
   check_device_error(c);
+  if (c.p.precision == MGAR_MIXED) return solve_mgcg_df(c, T, iters, relres);
   const int64_t n = c.n;
   if (c.dim == 2) residual_norm<2>(c, T, c.r, c.dsc + S_RR);
   else residual_norm<3>(c, T, c.r, c.dsc + S_RR);
@@ -251,13 +253,26 @@ void solve_mgar(Ctx& c, const double* T_prev, double* T, double* res, int* accep
         MGAR_CUDA(cudaMemcpyAsync(ri, prev, n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
       run_graph(c, zero ? 2 : 3, c.r, ri, vcycle_profiled(c),
                 [&] { vcycle<double>(c, c.r, ri, zero); });
-    } else {
-      run_graph(c, zero ? 4 : 5, prev, ri, vcycle_profiled(c), [&] {
+    } else if (zero) {
+      run_graph(c, 4, prev, ri, vcycle_profiled(c), [&] {
         convert_d2f(c, prev, c.x32, n);
-        apply_dK32(c, c.x32, c.b32);  // b32 = -dK r_{i-1}; x32 keeps r_{i-1} as the guess
-        vcycle<float>(c, c.b32, c.x32, zero);
+        apply_dK32(c, c.x32, c.b32);  // b32 = -dK r_{i-1}
+        vcycle<float>(c, c.b32, c.x32, true);
         convert_f2d(c, c.x32, ri, n);
       });
+    } else {
+      // One V-cycle from the guess r_{i-1} equals r_{i-1} + MG(-dK r_{i-1} - K0 r_{i-1}, 0)
+      // = r_{i-1} - MG(K r_{i-1}, 0) (the V-cycle is affine in its guess).  In the
+      // mixed path only the correction goes through FP32, so the large r_{i-1}
+      // never cancels in single precision.
+      apply_df64(c, prev, c.r);  // c.r = K r_{i-1}
+      run_graph(c, 5, c.r, ri, vcycle_profiled(c), [&] {
+        convert_d2f(c, c.r, c.b32, n);
+        vcycle<float>(c, c.b32, c.x32, true);
+        convert_f2d(c, c.x32, ri, n);
+      });
+      k_sub_from<<<rb, kThreads, 0, c.stream>>>(ri, prev, n);  // ri = r_{i-1} - ri
+      MGAR_LAUNCH_CHECK();
     }
   }
   // Eq. 18: orthonormal basis (modified Gram-Schmidt, twice)
@@ -290,8 +305,12 @@ void solve_mgar(Ctx& c, const double* T_prev, double* T, double* res, int* accep
   }
   require(kept > 0, MGAR_ERR_NONFINITE, "MGAR basis vanished");
   // Eq. 19-21: reduced system
-  for (int j = 0; j < kept; ++j)
-    apply_fine64(c, c.ke, c.R + (int64_t)j * n, c.W + (int64_t)j * n, nullptr);
+  for (int j = 0; j < kept; ++j) {
+    if (c.p.precision == MGAR_MIXED)
+      apply_df64(c, c.R + (int64_t)j * n, c.W + (int64_t)j * n);
+    else
+      apply_fine64(c, c.ke, c.R + (int64_t)j * n, c.W + (int64_t)j * n, nullptr);
+  }
   for (int i = 0; i < kept; ++i) {
     for (int j = 0; j <= i; ++j) {
       dot(c, c.R + (int64_t)i * n, c.W + (int64_t)j * n, n, c.dsc + S_KR + i * kMaxM + j);

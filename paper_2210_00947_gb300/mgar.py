@@ -38,11 +38,12 @@ EXPORTS = ("mgar_default_params", "mgar_create", "mgar_destroy", "mgar_set_strea
            "mgar_last_error", "mgar_filter", "mgar_set_density", "mgar_apply_K",
            "mgar_build_hierarchy", "mgar_vcycle", "mgar_solve_mgcg", "mgar_solve_mgar",
            "mgar_sensitivity", "mgar_oc_update", "mgar_step", "mgar_sizes", "mgar_run",
-           "mgar_profile_start", "mgar_profile_stop", "mgar_kernel_launches",
-           "mgar_sensitivity_noalloc")
+           "mgar_profile_start", "mgar_profile_stop", "mgar_profile_report",
+           "mgar_kernel_launches", "mgar_sensitivity_noalloc")
 
 # kernel classes of mgar_profile_start
 KC_APPLY64, KC_SMOOTH0, KC_RESID0, KC_OC, KC_GALERKIN0, KC_FILTER, KC_SENS = range(1, 8)
+KC_TIMELINE = 100
 
 
 class Params(ctypes.Structure):
@@ -111,6 +112,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "mgar_run": (i32, [vp, vp, i32, vp, P(StepInfo)]),
         "mgar_profile_start": (i32, [vp, i32]),
         "mgar_profile_stop": (i32, [vp, dp, P(ctypes.c_int64)]),
+        "mgar_profile_report": (i32, [vp, ctypes.c_char_p, ctypes.c_int64]),
         "mgar_kernel_launches": (ctypes.c_int64, []),
         "mgar_sensitivity_noalloc": (i32, [P(Params), vp, vp, vp, vp]),
     }
@@ -266,6 +268,11 @@ class Solver:
         n = ctypes.c_int64()
         self._check(self._lib.mgar_profile_stop(self._h, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
+
+    def profile_report(self) -> str:
+        buf = ctypes.create_string_buffer(1 << 16)
+        self._check(self._lib.mgar_profile_report(self._h, buf, len(buf)))
+        return buf.value.decode()
 
     def step(self, rho, T, cycle):
         info = StepInfo()

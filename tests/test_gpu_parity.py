@@ -252,3 +252,50 @@ def test_oc_large_matches_oracle(dims):
         lam, change = s.oc_update(r, dev(dc), 0.35, 0.2)
         assert abs(lam - lam_ref) / lam_ref < 1e-12
         np.testing.assert_allclose(host(r), ref, rtol=1e-11, atol=1e-12)
+
+
+@pytest.mark.parametrize("dims,nl", [((64, 48, 0), 4), ((100, 100, 0), 4), ((16, 16, 12), 3),
+                                     ((20, 18, 16), 4)])
+def test_mixed_mgcg_matches_exact_solve(dims, nl):
+    """Mixed path: df64 outer CG with the FP32 V-cycle.  The preconditioner
+    only changes the iteration count.  Double-float vectors carry ~48 bits,
+    so the true residual bottoms out near 2^-46 ||A|| ||T|| / ||q|| (a few
+    1e-10 here) even when the recursive one is driven to 1e-11; the bars are
+    set from that floor, two orders below the 1e-8 the workloads use."""
+    g, rho, fixed, q = make_problem(dims, mask="sink")
+    A = fem.system_matrix(g, rho, fixed)
+    t_ex = solvers.exact_solve(A, q)
+    with solver_for(dims, fixed, q, nl=nl, eps2=1e-11, cg_max=500, precision=mgar.MGAR_MIXED) as s:
+        s.set_density(dev(rho), physical=True)
+        T = torch.zeros(g.n_nodes, dtype=torch.float64, device=DEV)
+        it, rr, ok = s.solve_mgcg(T)
+        assert ok and rr <= 1e-11
+        t = host(T)
+        # the true residual, evaluated by the oracle
+        assert np.linalg.norm(q - A @ t) / np.linalg.norm(q) < 2e-9
+        assert relerr(t, t_ex) < 1e-7
+        assert abs(q @ t - q @ t_ex) / abs(q @ t_ex) < 1e-8
+
+
+@pytest.mark.parametrize("dims,nl", [((100, 100, 0), 4), ((13, 11, 9), 3)])
+@pytest.mark.parametrize("guess", ["previous", "zero"])
+def test_mixed_mgar_compliance_matches_oracle(dims, nl, guess):
+    """Mixed MGAR: FP32 basis V-cycles, FP64 Gram-Schmidt and reduced solve;
+    the reduced solution's compliance within 1e-6 of the oracle's."""
+    g, rho, rho0, fixed, q = _mgar_case(dims, nl)
+    dims_e = dims[:2] if dims[2] == 0 else dims
+    A = fem.system_matrix(g, rho, fixed)
+    A0 = fem.system_matrix(g, rho0, fixed)
+    levels0 = mg.build_hierarchy(A0, fixed, dims_e, nl)
+    t0 = solvers.exact_solve(A0, q)
+    t_ref, res_ref = solvers.mgar(A, A0, levels0, q, t0, m=2, basis_guess=guess)
+    bg = mgar.MGAR_GUESS_PREVIOUS if guess == "previous" else mgar.MGAR_GUESS_ZERO
+    with solver_for(dims, fixed, q, nl=nl, m=2, basis_guess=bg, precision=mgar.MGAR_MIXED) as s:
+        s.set_density(dev(rho0), physical=True)
+        s.build_hierarchy()
+        s.set_density(dev(rho), physical=True)
+        T = torch.empty(g.n_nodes, dtype=torch.float64, device=DEV)
+        res, acc = s.solve_mgar(dev(t0), T)
+        t = host(T)
+        assert abs(q @ t - q @ t_ref) / abs(q @ t_ref) < 1e-6
+        assert abs(res - res_ref) < 1e-4 * max(1.0, res_ref)
