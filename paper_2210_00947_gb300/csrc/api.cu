@@ -314,6 +314,7 @@ int mgar_create(mgar_t* out, const mgar_params* p, const uint8_t* fixed_mask, co
     }
     // debugging aid: MGAR_NO_GRAPHS=1 issues every V-cycle launch directly
     if (const char* ng = std::getenv("MGAR_NO_GRAPHS")) c->use_graphs = !(ng[0] == '1');
+    if (const char* ut = std::getenv("MGAR_UNTILED")) c->untiled = (ut[0] == '1');
   } catch (const Error& e) {
     g_create_error = e.msg;
     free_ctx(*c);

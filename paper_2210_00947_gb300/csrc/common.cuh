@@ -179,6 +179,7 @@ struct Ctx {
   static constexpr int kGraphs = 16;
   GraphEntry graphs[kGraphs];
   bool use_graphs = true;
+  bool untiled = false;  // MGAR_UNTILED=1: generic finest-level kernels (debugging aid)
   cudaStream_t cap_stream = nullptr;
 
   // instrumentation: CUDA-event timing of one kernel class
@@ -238,6 +239,16 @@ void prof_mark(const char* site);
     ::mgar::prof_mark(__FILE__ ":" MGAR_STR(__LINE__));  \
     MGAR_CUDA(cudaGetLastError());                       \
   } while (0)
+// as MGAR_LAUNCH_CHECK, with an explicit site name for the timeline
+#define MGAR_LAUNCH_CHECK_AT(site)     \
+  do {                                 \
+    ::mgar::count_launch();            \
+    ::mgar::prof_mark(site);           \
+    MGAR_CUDA(cudaGetLastError());     \
+  } while (0)
+// "<kind> L<level>" site names (kind: 0 jacobi0, 1 sweep, 2 residual, 3 restrict,
+// 4 prolong, 5 coarse, 6 pre3d, 7 post3d, 8 sweep3d, 9 resid3d)
+const char* level_site(int kind, int level);
 
 inline void require(bool ok, int code, const std::string& msg) {
   if (!ok) throw Error{code, msg};
@@ -564,6 +575,10 @@ void build_hierarchy(Ctx& c);      // K0 <- K, all levels, coarsest factor
 // vcycle.cu
 template <typename Real>
 void vcycle(Ctx& c, const Real* b, Real* x, bool zero_guess);
+// fine3d.cu: tiled finest-level 3D passes (mode 0 pre, 1 post, 2 residual, 3 sweep)
+template <typename Real>
+void fine3d(Ctx& c, int mode, const Real* ke, const Real* b, const Real* dinv, const Real* x,
+            const Real* xc, Real* out0, Real* out1);
 void apply_fine64(Ctx& c, const double* ke, const double* x, double* y, double* dot_out);
 void apply_fine32(Ctx& c, const float* ke, const float* x, float* y);
 void apply_dK64(Ctx& c, const double* x, double* y);

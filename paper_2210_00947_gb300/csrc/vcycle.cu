@@ -12,6 +12,19 @@
 
 namespace mgar {
 
+const char* level_site(int kind, int level) {
+  static const char* names[10] = {"jacobi0", "sweep", "residual", "restrict", "prolong",
+                                  "coarse", "pre3d", "post3d", "sweep3d", "resid3d"};
+  static char table[10][kMaxLevels][24];
+  static bool init = false;
+  if (!init) {
+    for (int k = 0; k < 10; ++k)
+      for (int l = 0; l < kMaxLevels; ++l) snprintf(table[k][l], 24, "vc %s L%d", names[k], l);
+    init = true;
+  }
+  return table[kind % 10][level % kMaxLevels];
+}
+
 // ------------------------------------------------------------ row functors
 template <typename Real, int DIM>
 struct FineRow {
@@ -230,7 +243,7 @@ static void sweep(Ctx& c, int l, const Real* b, const Real* xin, Real* xout) {
   else
     k_jacobi<<<blocks_for(d.n), kThreads, 0, c.stream>>>(stencil_row<Real, DIM>(c, l), b, xin, xout,
                                                          h[l].dinv, om);
-  MGAR_LAUNCH_CHECK();
+  MGAR_LAUNCH_CHECK_AT(level_site(1, l));
 }
 
 template <typename Real, int DIM>
@@ -242,7 +255,7 @@ static void residual(Ctx& c, int l, const Real* b, const Real* x, Real* r) {
                                                            b, x, r);
   else
     k_residual<<<blocks_for(d.n), kThreads, 0, c.stream>>>(stencil_row<Real, DIM>(c, l), b, x, r);
-  MGAR_LAUNCH_CHECK();
+  MGAR_LAUNCH_CHECK_AT(level_site(2, l));
 }
 
 template <typename Real, int DIM>
@@ -251,8 +264,29 @@ static void vcycle_dim(Ctx& c, const Real* b0, Real* x0, bool zero_guess) {
   const int nl = c.nl;
   const Real om = (Real)c.p.omega;
   Real* cur[kMaxLevels];
+  // 3D finest level with one pre- and one post-sweep: tiled, fused kernels
+  // (pre-smooth + residual, interpolation + post-smooth)
+  const bool tiled0 = DIM == 3 && c.p.nu_pre == 1 && c.p.nu_post == 1 && !c.untiled;
+  int first = 0;
+  if (tiled0) {
+    const Dims& d = c.L[0];
+    {
+      ProfScope ps(c, MGAR_KC_SMOOTH0);
+      if (zero_guess) {
+        fine3d<Real>(c, 0, ref_ke<Real>(c), b0, h[0].dinv, nullptr, nullptr, h[0].t, h[0].r);
+      } else {
+        fine3d<Real>(c, 3, ref_ke<Real>(c), b0, h[0].dinv, x0, nullptr, h[0].t, nullptr);
+        fine3d<Real>(c, 2, ref_ke<Real>(c), b0, h[0].dinv, h[0].t, nullptr, h[0].r, nullptr);
+      }
+    }
+    k_restrict<Real, DIM><<<blocks_for(c.L[1].n), kThreads, 0, c.stream>>>(h[0].r, h[1].b, d,
+                                                                            c.L[1], c.fixed);
+    MGAR_LAUNCH_CHECK_AT(level_site(3, 0));
+    cur[0] = h[0].t;
+    first = 1;
+  }
   // downward leg
-  for (int l = 0; l + 1 < nl; ++l) {
+  for (int l = first; l + 1 < nl; ++l) {
     const Dims& d = c.L[l];
     const Real* b = l == 0 ? b0 : h[l].b;
     Real* x = l == 0 ? x0 : h[l].x;
@@ -263,7 +297,7 @@ static void vcycle_dim(Ctx& c, const Real* b0, Real* x0, bool zero_guess) {
       if (sweeps > 0) {
         ProfScope ps(c, l == 0 ? MGAR_KC_SMOOTH0 : -1);
         k_jacobi_zero<<<blocks_for(d.n), kThreads, 0, c.stream>>>(b, x, h[l].dinv, om, (int)d.n);
-        MGAR_LAUNCH_CHECK();
+        MGAR_LAUNCH_CHECK_AT(level_site(0, l));
         --sweeps;
       } else {
         MGAR_CUDA(cudaMemsetAsync(x, 0, d.n * sizeof(Real), c.stream));
@@ -278,7 +312,7 @@ static void vcycle_dim(Ctx& c, const Real* b0, Real* x0, bool zero_guess) {
     residual<Real, DIM>(c, l, b, cu, h[l].r);
     k_restrict<Real, DIM><<<blocks_for(c.L[l + 1].n), kThreads, 0, c.stream>>>(
         h[l].r, h[l + 1].b, d, c.L[l + 1], l == 0 ? c.fixed : nullptr);
-    MGAR_LAUNCH_CHECK();
+    MGAR_LAUNCH_CHECK_AT(level_site(3, l));
   }
   // coarsest level
   {
@@ -286,10 +320,10 @@ static void vcycle_dim(Ctx& c, const Real* b0, Real* x0, bool zero_guess) {
     const int rows_per_block = kThreads / 32;
     k_coarse_solve<Real><<<(c.nc + rows_per_block - 1) / rows_per_block, kThreads, 0, c.stream>>>(
         c.cinv, h[l].b, h[l].x, c.nc);
-    MGAR_LAUNCH_CHECK();
+    MGAR_LAUNCH_CHECK_AT(level_site(5, l));
   }
   // upward leg
-  for (int l = nl - 2; l >= 0; --l) {
+  for (int l = nl - 2; l >= first; --l) {
     const Dims& d = c.L[l];
     const Real* b = l == 0 ? b0 : h[l].b;
     Real* x = l == 0 ? x0 : h[l].x;
@@ -299,13 +333,17 @@ static void vcycle_dim(Ctx& c, const Real* b0, Real* x0, bool zero_guess) {
     k_prolong<Real, DIM><<<blocks_for(d.n), kThreads, 0, c.stream>>>(h[l + 1].x, cur[l], dst, d,
                                                                       c.L[l + 1],
                                                                       l == 0 ? c.fixed : nullptr);
-    MGAR_LAUNCH_CHECK();
+    MGAR_LAUNCH_CHECK_AT(level_site(4, l));
     Real* cu = dst;
     for (int s = 0; s < post; ++s) {
       Real* nxt = (cu == x) ? other : x;
       sweep<Real, DIM>(c, l, b, cu, nxt);
       cu = nxt;
     }
+  }
+  if (tiled0) {
+    ProfScope ps(c, MGAR_KC_SMOOTH0);
+    fine3d<Real>(c, 1, ref_ke<Real>(c), b0, h[0].dinv, h[0].t, h[1].x, x0, nullptr);
   }
 }
 
