@@ -96,7 +96,7 @@ void free_ctx(Ctx& c) {
   cudaFree(c.run_rho);
   cudaFree(c.run_T);
   void* ptrs[] = {c.fixed, c.efix, c.q, c.rho_phys, c.ke, c.ke0, c.ke_f, c.ke0_f, c.inv_hs, c.f_offs, c.f_w,
-                  c.dv, c.rsdv, c.r, c.z, c.pv, c.Ap, c.tm, c.tmp_dc, c.R, c.W, c.b32, c.x32, c.ke_df, c.df_q, c.df_x, c.df_r, c.df_p, c.df_Ap, c.tmp_e, c.oc_s, c.oc_lo,
+                  c.dv, c.rsdv, c.r, c.z, c.pv, c.Ap, c.tm, c.tmp_dc, c.R, c.W, c.b32, c.x32, c.ke_df, c.df_q, c.df_x, c.df_r, c.df_p, c.df_Ap, c.df_p2, c.tmp_e, c.oc_s, c.oc_lo,
                   c.oc_hi, c.oc_s32, c.oc_lo32, c.oc_hi32, c.dv32, c.oc_amb, c.oc_namb, c.partials, c.counter, c.dsc, c.derr};
   for (void* p : ptrs) cudaFree(p);
   if (c.hsc) cudaFreeHost(c.hsc);
@@ -220,7 +220,9 @@ int mgar_create(mgar_t* out, const mgar_params* p, const uint8_t* fixed_mask, co
     c->n = c->L[0].n;
     c->ne = c->L[0].ne;
     const int64_t n = c->n, ne = c->ne;
-    const int64_t maxb = blocks_for(n > ne ? n : ne);
+    // reduction partials: one per block of the widest launch (node/element
+    // kernels, or the z-marching tiles, which stay below kMinPartialBlocks)
+    const int64_t maxb = std::max<int64_t>(blocks_for(n > ne ? n : ne), kMinPartialBlocks);
     c->grid_blocks = (int)std::min<int64_t>(blocks_for(n), 152 * 8);
     c->grid_blocks_e = (int)std::min<int64_t>(blocks_for(ne), 152 * 8);
 
@@ -257,7 +259,7 @@ int mgar_create(mgar_t* out, const mgar_params* p, const uint8_t* fixed_mask, co
       MGAR_CUDA(cudaMalloc(&c->b32, n * sizeof(float)));
       MGAR_CUDA(cudaMalloc(&c->x32, n * sizeof(float)));
       MGAR_CUDA(cudaMalloc(&c->ke_df, ne * sizeof(float2)));
-      for (float2** v : {&c->df_q, &c->df_x, &c->df_r, &c->df_p, &c->df_Ap})
+      for (float2** v : {&c->df_q, &c->df_x, &c->df_r, &c->df_p, &c->df_Ap, &c->df_p2})
         MGAR_CUDA(cudaMalloc(v, n * sizeof(float2)));
     }
     MGAR_CUDA(cudaMalloc(&c->partials, (size_t)32 * maxb * sizeof(double)));
@@ -315,6 +317,10 @@ int mgar_create(mgar_t* out, const mgar_params* p, const uint8_t* fixed_mask, co
     // debugging aid: MGAR_NO_GRAPHS=1 issues every V-cycle launch directly
     if (const char* ng = std::getenv("MGAR_NO_GRAPHS")) c->use_graphs = !(ng[0] == '1');
     if (const char* ut = std::getenv("MGAR_UNTILED")) c->untiled = (ut[0] == '1');
+    if (c->dim == 3) {
+      fine3d_prepare(*c);
+      if (P.precision == MGAR_MIXED) df3d_prepare(*c);
+    }
   } catch (const Error& e) {
     g_create_error = e.msg;
     free_ctx(*c);

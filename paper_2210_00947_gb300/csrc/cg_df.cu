@@ -151,17 +151,19 @@ __global__ void k_df_residual(DfOp op, const float2* __restrict__ q, const float
   block_sum_finish<1>(v, partials, counter, out);
 }
 
-// alpha = rz / pAp; x += alpha p; r -= alpha Ap; ||r||^2
+// alpha = rz / pAp; x += alpha p; r -= alpha Ap; ||r||^2; optionally the
+// FP32 copy of r for the preconditioner
 __global__ void k_df_cg_xr(float2* __restrict__ x, float2* __restrict__ r, const float2* __restrict__ p,
                            const float2* __restrict__ Ap, int n, const double* __restrict__ rz,
                            const double* __restrict__ pap, double* partials, unsigned int* counter,
-                           double* out) {
+                           double* out, float* __restrict__ r32) {
   const df alpha = df_from_double(*rz / *pap);
   df acc{0.f, 0.f};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     x[i] = pack(df_add(unpack(x[i]), df_mul(alpha, unpack(p[i]))));
     const df ri = df_sub(unpack(r[i]), df_mul(alpha, unpack(Ap[i])));
     r[i] = pack(ri);
+    if (r32) r32[i] = __fadd_rn(ri.hi, ri.lo);
     acc = df_add(acc, df_mul(ri, ri));
   }
   double v[1] = {df_to_double(acc)};
@@ -234,13 +236,17 @@ void apply_df64(Ctx& c, const double* x, double* y) {
   k_d_to_df<<<blocks_for(n), kThreads, 0, c.stream>>>(x, c.df_p, n);
   MGAR_LAUNCH_CHECK();
   const DfOp op = make_op(c);
-  if (c.dim == 2)
-    k_df_apply<2, false><<<blocks_for(n), kThreads, 0, c.stream>>>(op, c.df_p, c.df_Ap, nullptr,
-                                                                   nullptr, nullptr);
-  else
-    k_df_apply<3, false><<<blocks_for(n), kThreads, 0, c.stream>>>(op, c.df_p, c.df_Ap, nullptr,
-                                                                   nullptr, nullptr);
-  MGAR_LAUNCH_CHECK();
+  if (c.dim == 3 && !c.untiled) {
+    df3d_apply(c, c.df_p, c.df_Ap, nullptr);
+  } else {
+    if (c.dim == 2)
+      k_df_apply<2, false><<<blocks_for(n), kThreads, 0, c.stream>>>(op, c.df_p, c.df_Ap, nullptr,
+                                                                     nullptr, nullptr);
+    else
+      k_df_apply<3, false><<<blocks_for(n), kThreads, 0, c.stream>>>(op, c.df_p, c.df_Ap, nullptr,
+                                                                     nullptr, nullptr);
+    MGAR_LAUNCH_CHECK();
+  }
   k_df_to_d<<<blocks_for(n), kThreads, 0, c.stream>>>(c.df_Ap, y, n);
   MGAR_LAUNCH_CHECK();
 }
@@ -267,7 +273,67 @@ static void precondition_df(Ctx& c) {
   });
 }
 
+// z32 = M r32 (the FP32 copy of r is written by the residual and update kernels)
+static void precondition_f32(Ctx& c) {
+  const bool prof_inside = c.prof_class == MGAR_KC_SMOOTH0 || c.prof_class == MGAR_KC_RESID0;
+  run_graph(c, 7, c.b32, c.x32, prof_inside, [&] { vcycle<float>(c, c.b32, c.x32, true); });
+}
+
+// 3D: the tiled kernels fuse the direction update into the product
+// (p = z + beta p_old, A p, p.Ap in one pass) and write the FP32 copy of r
+// beside r, so an iteration is: product, update of x and r, V-cycle, r.z.
+static int solve_mgcg_df3(Ctx& c, double* T, int* iters, double* relres) {
+  const int n = (int)c.n;
+  const int rb = c.grid_blocks;
+  k_d_to_df<<<blocks_for(n), kThreads, 0, c.stream>>>(T, c.df_x, n);
+  MGAR_LAUNCH_CHECK();
+  {
+    ProfScope ps(c, MGAR_KC_APPLY64);
+    df3d_resid(c, c.df_q, c.df_x, c.df_r, c.b32, c.dsc + S_RR);
+  }
+  fetch_scalars(c, S_RR, 1);
+  double rel = std::sqrt(c.hsc[S_RR]) / c.qnorm;
+  int it = 0;
+  if (!(rel <= c.p.eps2)) {
+    require(std::isfinite(rel), MGAR_ERR_NONFINITE, "non-finite initial residual");
+    precondition_f32(c);
+    int a = S_RZ0, b = S_RZ1;
+    k_df_dot_f<<<rb, kThreads, 0, c.stream>>>(c.df_r, c.x32, n, c.partials, c.counter, c.dsc + a);
+    MGAR_LAUNCH_CHECK();
+    float2* pcur = c.df_p;
+    float2* pnext = c.df_p2;
+    bool first = true;
+    while (it < c.p.cg_max) {
+      {
+        ProfScope ps(c, MGAR_KC_APPLY64);
+        df3d_dir(c, c.x32, pcur, pnext, c.dsc + a, c.dsc + b, first, c.df_Ap, c.dsc + S_PAP);
+      }
+      first = false;
+      std::swap(pcur, pnext);
+      k_df_cg_xr<<<rb, kThreads, 0, c.stream>>>(c.df_x, c.df_r, pcur, c.df_Ap, n, c.dsc + a,
+                                                c.dsc + S_PAP, c.partials, c.counter, c.dsc + S_RR,
+                                                c.b32);
+      MGAR_LAUNCH_CHECK();
+      ++it;
+      fetch_scalars(c, S_RR, 1);
+      rel = std::sqrt(c.hsc[S_RR]) / c.qnorm;
+      require(std::isfinite(rel), MGAR_ERR_NONFINITE, "CG breakdown (non-finite residual)");
+      if (rel <= c.p.eps2) break;
+      precondition_f32(c);
+      std::swap(a, b);
+      k_df_dot_f<<<rb, kThreads, 0, c.stream>>>(c.df_r, c.x32, n, c.partials, c.counter, c.dsc + a);
+      MGAR_LAUNCH_CHECK();
+    }
+  }
+  k_df_to_d<<<blocks_for(n), kThreads, 0, c.stream>>>(c.df_x, T, n);
+  MGAR_LAUNCH_CHECK();
+  if (iters) *iters = it;
+  if (relres) *relres = rel;
+  return rel <= c.p.eps2 ? MGAR_OK : MGAR_ERR_MAXIT;
+}
+
 int solve_mgcg_df(Ctx& c, double* T, int* iters, double* relres) {
+  if (c.dim == 3 && !c.untiled) return solve_mgcg_df3(c, T, iters, relres);
   const int n = (int)c.n;
   const int rb = c.grid_blocks;
   const DfOp op = make_op(c);
@@ -306,7 +372,8 @@ int solve_mgcg_df(Ctx& c, double* T, int* iters, double* relres) {
         MGAR_LAUNCH_CHECK();
       }
       k_df_cg_xr<<<rb, kThreads, 0, c.stream>>>(c.df_x, c.df_r, c.df_p, c.df_Ap, n, c.dsc + a,
-                                                c.dsc + S_PAP, c.partials, c.counter, c.dsc + S_RR);
+                                                c.dsc + S_PAP, c.partials, c.counter, c.dsc + S_RR,
+                                                nullptr);
       MGAR_LAUNCH_CHECK();
       ++it;
       fetch_scalars(c, S_RR, 1);

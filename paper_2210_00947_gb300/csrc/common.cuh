@@ -38,6 +38,7 @@ constexpr long long g_partials_len = 0;
 
 constexpr int kMaxLevels = 14;
 constexpr int kThreads = 256;
+constexpr int kMinPartialBlocks = 8192;
 constexpr int kMaxFilterOffsets = 1024;
 constexpr int kMaxM = 8;
 constexpr int kOcCand = 31;      // multisection candidates per pass (5 bits)
@@ -150,7 +151,7 @@ struct Ctx {
   float *b32 = nullptr, *x32 = nullptr; // mixed-mode level-0 buffers
   // mixed mode: double-float (hi, lo) copies for the outer CG
   float2 *ke_df = nullptr, *df_q = nullptr, *df_x = nullptr, *df_r = nullptr, *df_p = nullptr,
-         *df_Ap = nullptr;
+         *df_Ap = nullptr, *df_p2 = nullptr;
   double *tmp_e = nullptr, *oc_s = nullptr, *oc_lo = nullptr, *oc_hi = nullptr;
   float *oc_s32 = nullptr, *oc_lo32 = nullptr, *oc_hi32 = nullptr, *dv32 = nullptr;
   int *oc_amb = nullptr, *oc_namb = nullptr;
@@ -180,6 +181,8 @@ struct Ctx {
   GraphEntry graphs[kGraphs];
   bool use_graphs = true;
   bool untiled = false;  // MGAR_UNTILED=1: generic finest-level kernels (debugging aid)
+  int f3d_gz[2][4] = {};  // z runs of the tiled finest-level kernels [FP32, FP64][mode]
+  int df3d_gz[3] = {};    // z runs of the tiled df64 operator kernels [mode]
   cudaStream_t cap_stream = nullptr;
 
   // instrumentation: CUDA-event timing of one kernel class
@@ -267,13 +270,16 @@ inline int blocks_for(int64_t n, int threads = kThreads) {
 // ticket, and returns true with the totals in every thread.  Other blocks
 // return false.  Every thread of every block must call it.  The summation
 // order is fixed, so results are reproducible run to run.
+// Block, thread and grid given as linear ids (tid < nthr <= kThreads, a
+// multiple of 32; bid < nblk), so multi-dimensional launches can use it.
 template <int N>
-__device__ __forceinline__ bool block_sum_last(double (&v)[N], double* partials,
-                                               unsigned int* counter, double (&total)[N]) {
+__device__ __forceinline__ bool block_sum_last_ids(double (&v)[N], double* partials,
+                                                   unsigned int* counter, double (&total)[N],
+                                                   int tid, int nthr, int bid, int nblk) {
   __shared__ double sh[N][kThreads / 32];
   __shared__ double tot[N];
   __shared__ bool last;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     double s = v[k];
@@ -282,16 +288,16 @@ __device__ __forceinline__ bool block_sum_last(double (&v)[N], double* partials,
     if (lane == 0) sh[k][warp] = s;
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+  for (int k = tid; k < N; k += nthr) {
     double s = 0.0;
     for (int w = 0; w < nw; ++w) s += sh[k][w];
-    if (CK(k * gridDim.x + blockIdx.x, g_partials_len)) partials[k * gridDim.x + blockIdx.x] = s;
+    if (CK((int64_t)k * nblk + bid, g_partials_len)) partials[k * nblk + bid] = s;
     __threadfence();
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     const unsigned int t = atomicAdd(counter, 1u);
-    last = (t == gridDim.x - 1);
+    last = (t == (unsigned int)nblk - 1);
   }
   __syncthreads();
   if (!last) return false;
@@ -299,9 +305,9 @@ __device__ __forceinline__ bool block_sum_last(double (&v)[N], double* partials,
   double acc[N];
 #pragma unroll
   for (int k = 0; k < N; ++k) acc[k] = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+  for (int b = tid; b < nblk; b += nthr)
 #pragma unroll
-    for (int k = 0; k < N; ++k) acc[k] += ((volatile double*)partials)[k * gridDim.x + b];
+    for (int k = 0; k < N; ++k) acc[k] += ((volatile double*)partials)[k * nblk + b];
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     double s = acc[k];
@@ -310,16 +316,23 @@ __device__ __forceinline__ bool block_sum_last(double (&v)[N], double* partials,
     if (lane == 0) sh[k][warp] = s;
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+  for (int k = tid; k < N; k += nthr) {
     double s = 0.0;
     for (int w = 0; w < nw; ++w) s += sh[k][w];
     tot[k] = s;
   }
-  if (threadIdx.x == 0) *counter = 0u;
+  if (tid == 0) *counter = 0u;
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < N; ++k) total[k] = tot[k];
   return true;
+}
+
+template <int N>
+__device__ __forceinline__ bool block_sum_last(double (&v)[N], double* partials,
+                                               unsigned int* counter, double (&total)[N]) {
+  return block_sum_last_ids<N>(v, partials, counter, total, threadIdx.x, blockDim.x, blockIdx.x,
+                               gridDim.x);
 }
 
 // As block_sum_last, storing the totals to out[0..N) from the last block.
@@ -579,6 +592,14 @@ void vcycle(Ctx& c, const Real* b, Real* x, bool zero_guess);
 template <typename Real>
 void fine3d(Ctx& c, int mode, const Real* ke, const Real* b, const Real* dinv, const Real* x,
             const Real* xc, Real* out0, Real* out1);
+// launch shapes of the tiled kernels (occupancy query; call outside stream capture)
+void fine3d_prepare(Ctx& c);
+// df3d.cu: tiled df64 finest-level operator (3D)
+void df3d_prepare(Ctx& c);
+void df3d_apply(Ctx& c, const float2* x, float2* y, double* dot);
+void df3d_dir(Ctx& c, const float* z, const float2* p_old, float2* p, const double* rz_new,
+              const double* rz_old, bool first, float2* y, double* dot);
+void df3d_resid(Ctx& c, const float2* q, const float2* x, float2* r, float* r32, double* rr);
 void apply_fine64(Ctx& c, const double* ke, const double* x, double* y, double* dot_out);
 void apply_fine32(Ctx& c, const float* ke, const float* x, float* y);
 void apply_dK64(Ctx& c, const double* x, double* y);

@@ -91,18 +91,18 @@ __global__ void k_apply(Row row, const Real* __restrict__ x, Real* __restrict__ 
 }
 
 // 1D interpolation taps.  Coarse node I sits at fine node min(2I, nf).
-// Restriction (P^T) gathers from fine nodes 2I (weight 1), 2I-1 and 2I+1
-// (weight 1/2, or 1 for the injected last node nf of an odd axis).
-// Unused tap slots point at a valid node with weight 0.
-__device__ __forceinline__ int restrict_taps(int I, int nf, int* idx, float* w) {
-  const int home = min(2 * I, nf);
-  idx[0] = idx[1] = idx[2] = home;
-  w[0] = w[1] = w[2] = 0.f;
-  int c = 0;
-  if (2 * I <= nf) { idx[c] = 2 * I; w[c++] = 1.f; }
-  if (2 * I - 1 >= 1 && 2 * I - 1 <= nf) { idx[c] = 2 * I - 1; w[c++] = (2 * I - 1 < nf) ? 0.5f : 1.f; }
-  if (2 * I + 1 < nf) { idx[c] = 2 * I + 1; w[c++] = 0.5f; }
-  return c;
+// Restriction (P^T) gathers from fine nodes 2I - 1, 2I, 2I + 1 (weights 1/2,
+// 1, 1/2); the last fine node nf of an odd axis is injected (weight 1) into
+// the last coarse node.  All three slots are always read: an unused slot
+// points at a valid node with weight 0, so the loads need no branches.
+__device__ __forceinline__ void restrict_taps(int I, int nf, int* idx, float* w) {
+  const int f = 2 * I;
+  idx[0] = min(max(f - 1, 0), nf);
+  w[0] = (f - 1 >= 1 && f - 1 <= nf) ? ((f - 1 < nf) ? 0.5f : 1.f) : 0.f;
+  idx[1] = min(f, nf);
+  w[1] = (f <= nf) ? 1.f : 0.f;
+  idx[2] = min(f + 1, nf);
+  w[2] = (f + 1 < nf) ? 0.5f : 0.f;
 }
 
 // Interpolation (P) onto fine node i from coarse nodes.
@@ -119,25 +119,25 @@ __global__ void k_restrict(const Real* __restrict__ r, Real* __restrict__ bc, Di
   if (idx >= cd.n) return;
   int I, J, K;
   coords(idx, cd.fNX, cd.fNXY, I, J, K);
-  int ix[3], iy[3], iz[3];
-  float wx[3], wy[3], wz[3];
-  const int nx = restrict_taps(I, f.ex, ix, wx);
-  const int ny = restrict_taps(J, f.ey, iy, wy);
-  int nz = 1;
-  iz[0] = iz[1] = iz[2] = 0;
-  wz[0] = 1.f;
-  wz[1] = wz[2] = 0.f;
-  if (DIM == 3) nz = restrict_taps(K, f.ez, iz, wz);
+  int ix[3], iy[3], iz[3] = {0, 0, 0};
+  float wx[3], wy[3], wz[3] = {1.f, 0.f, 0.f};
+  restrict_taps(I, f.ex, ix, wx);
+  restrict_taps(J, f.ey, iy, wy);
+  if (DIM == 3) restrict_taps(K, f.ez, iz, wz);
   Real acc = Real(0);
-  for (int c = 0; c < nz; ++c)
-    for (int b = 0; b < ny; ++b) {
+#pragma unroll
+  for (int c = 0; c < (DIM == 3 ? 3 : 1); ++c)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
       const int base = f.NX * (iy[b] + f.NY * iz[c]);
       const Real wyz = (Real)(wy[b] * wz[c]);
-      for (int a = 0; a < nx; ++a) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
         const int fi = base + ix[a];
         if (!CK(fi, f.n)) continue;
-        if (fixed && fixed[fi]) continue;
-        acc += (wyz * (Real)wx[a]) * r[fi];
+        const Real rv = r[fi];
+        const bool fx = fixed ? fixed[fi] != 0 : false;
+        acc += fx ? Real(0) : (wyz * (Real)wx[a]) * rv;
       }
     }
   bc[idx] = acc;
@@ -155,24 +155,155 @@ __global__ void k_prolong(const Real* __restrict__ xc, const Real* cur, Real* ds
   }
   int i, j, k;
   coords(idx, f.fNX, f.fNXY, i, j, k);
-  int ix[2], iy[2], iz[2];
-  float wx[2], wy[2], wz[2];
-  const int nx = prolong_taps(i, f.ex, ix, wx);
-  const int ny = prolong_taps(j, f.ey, iy, wy);
-  int nz = 1;
-  iz[0] = iz[1] = 0;
-  wz[0] = 1.f;
-  wz[1] = 0.f;
-  if (DIM == 3) nz = prolong_taps(k, f.ez, iz, wz);
+  int ix[2], iy[2], iz[2] = {0, 0};
+  float wx[2], wy[2], wz[2] = {1.f, 0.f};
+  prolong_taps(i, f.ex, ix, wx);
+  prolong_taps(j, f.ey, iy, wy);
+  if (DIM == 3) prolong_taps(k, f.ez, iz, wz);
   Real acc = Real(0);
-  for (int c = 0; c < nz; ++c)
-    for (int b = 0; b < ny; ++b) {
+#pragma unroll
+  for (int c = 0; c < (DIM == 3 ? 2 : 1); ++c)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
       const int base = cd.NX * (iy[b] + cd.NY * iz[c]);
       const Real wyz = (Real)(wy[b] * wz[c]);
-      for (int a = 0; a < nx; ++a)
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
         if (CK(base + ix[a], cd.n)) acc += (wyz * (Real)wx[a]) * xc[base + ix[a]];
     }
   dst[idx] = cur[idx] + acc;
+}
+
+// Fused pre-smooth from a zero guess and residual on an assembled level:
+// x = w D^-1 b, r = b - A x (the neighbours' x recomputed from b and D^-1).
+template <typename Real, int DIM>
+__global__ void k_pre_coarse(StencilOp<Real> op, const Real* __restrict__ b,
+                             const Real* __restrict__ dinv, Real omega, Real* __restrict__ x,
+                             Real* __restrict__ r) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= op.n) return;
+  int i, j, k;
+  coords(idx, op.fNX, op.fNXY, i, j, k);
+  const int NX = op.NX, NXY = op.NX * op.NY;
+  Real acc = Real(0);
+#pragma unroll
+  for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz) {
+    const int kk = min(max(k + dz, 0), op.NZ - 1);
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int jj = min(max(j + dy, 0), op.NY - 1);
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int ii = min(max(i + dx, 0), op.NX - 1);
+        const int s = (dx + 1) + 3 * (dy + 1) + (DIM == 3 ? 9 * (dz + 1) : 0);
+        const int nb = ii + NX * jj + NXY * kk;
+        if (!CK(nb, op.n)) continue;
+        acc += op.st[s * op.n + idx] * (omega * dinv[nb] * b[nb]);
+      }
+    }
+  }
+  const Real bi = b[idx];
+  x[idx] = omega * dinv[idx] * bi;
+  r[idx] = bi - acc;
+}
+
+// Per axis: the coarse nodes c0, c0+1, c0+2 that interpolate onto the fine
+// positions f-1, f, f+1 (clamped to 0..nf), and the 3x3 weights w[t][u] of
+// coarse node c0+u at fine position f-1+t.
+__device__ __forceinline__ void interp_axis(int f, int nf, int& c0, float (&w)[3][3]) {
+  int t0[3];
+  bool hf[3];
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const int p = min(max(f - 1 + t, 0), nf);
+    hf[t] = (p & 1) && p < nf;
+    t0[t] = (p & 1) ? (hf[t] ? (p - 1) >> 1 : (p + 1) >> 1) : p >> 1;
+  }
+  c0 = t0[0];
+#pragma unroll
+  for (int t = 0; t < 3; ++t)
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+      w[t][u] = (t0[t] == c0 + u ? (hf[t] ? 0.5f : 1.f) : 0.f) + (hf[t] && t0[t] + 1 == c0 + u ? 0.5f : 0.f);
+}
+
+// Fused interpolation and post-smooth on an assembled level:
+// v = x + P x_c at the node and its neighbours, x' = v + w D^-1 (b - A v).
+// The 3^d coarse values around the node are read once and interpolated
+// separably onto the 3^d fine positions.
+template <typename Real, int DIM>
+__global__ void k_post_coarse(StencilOp<Real> op, const Real* __restrict__ xc,
+                              const Real* __restrict__ cur, const Real* __restrict__ b,
+                              const Real* __restrict__ dinv, Real omega, Real* __restrict__ dst,
+                              Dims f, Dims cd) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= op.n) return;
+  int i, j, k;
+  coords(idx, op.fNX, op.fNXY, i, j, k);
+  constexpr int NZ3 = DIM == 3 ? 3 : 1;
+  int cx0, cy0, cz0 = 0;
+  float wx[3][3], wy[3][3], wz[3][3] = {{1.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  interp_axis(i, f.ex, cx0, wx);
+  interp_axis(j, f.ey, cy0, wy);
+  if (DIM == 3) interp_axis(k, f.ez, cz0, wz);
+  // coarse values C[u][v][w] (z, y, x), clamped: weights of clamped slots are 0
+  Real C[NZ3][3][3];
+#pragma unroll
+  for (int uz = 0; uz < NZ3; ++uz)
+#pragma unroll
+    for (int uy = 0; uy < 3; ++uy)
+#pragma unroll
+      for (int ux = 0; ux < 3; ++ux) {
+        const int ci = min(cx0 + ux, cd.NX - 1) + cd.NX * (min(cy0 + uy, cd.NY - 1) +
+                                                           cd.NY * min(cz0 + uz, cd.NZ - 1));
+        C[uz][uy][ux] = CK(ci, cd.n) ? xc[ci] : Real(0);
+      }
+  // along x, then y, then z
+  Real T1[NZ3][3][3];
+#pragma unroll
+  for (int uz = 0; uz < NZ3; ++uz)
+#pragma unroll
+    for (int uy = 0; uy < 3; ++uy)
+#pragma unroll
+      for (int tx = 0; tx < 3; ++tx)
+        T1[uz][uy][tx] = (Real)wx[tx][0] * C[uz][uy][0] + (Real)wx[tx][1] * C[uz][uy][1] +
+                         (Real)wx[tx][2] * C[uz][uy][2];
+  Real T2[NZ3][3][3];
+#pragma unroll
+  for (int uz = 0; uz < NZ3; ++uz)
+#pragma unroll
+    for (int ty = 0; ty < 3; ++ty)
+#pragma unroll
+      for (int tx = 0; tx < 3; ++tx)
+        T2[uz][ty][tx] = (Real)wy[ty][0] * T1[uz][0][tx] + (Real)wy[ty][1] * T1[uz][1][tx] +
+                         (Real)wy[ty][2] * T1[uz][2][tx];
+  const int NX = op.NX, NXY = op.NX * op.NY;
+  Real acc = Real(0), vc = Real(0);
+#pragma unroll
+  for (int tz = 0; tz < NZ3; ++tz) {
+    const int kk = DIM == 3 ? min(max(k - 1 + tz, 0), op.NZ - 1) : 0;
+#pragma unroll
+    for (int ty = 0; ty < 3; ++ty) {
+      const int jj = min(max(j - 1 + ty, 0), op.NY - 1);
+#pragma unroll
+      for (int tx = 0; tx < 3; ++tx) {
+        const int ii = min(max(i - 1 + tx, 0), op.NX - 1);
+        Real pv;
+        if (DIM == 3)
+          pv = (Real)wz[tz][0] * T2[0][ty][tx] + (Real)wz[tz][1] * T2[NZ3 > 1 ? 1 : 0][ty][tx] +
+               (Real)wz[tz][2] * T2[NZ3 > 2 ? 2 : 0][ty][tx];
+        else
+          pv = T2[0][ty][tx];
+        const int nb = ii + NX * jj + NXY * kk;
+        if (!CK(nb, op.n)) continue;
+        const Real v = cur[nb] + pv;
+        const int s = tx + 3 * ty + 9 * tz;
+        acc += op.st[s * op.n + idx] * v;
+        if (tx == 1 && ty == 1 && tz == (DIM == 3 ? 1 : 0)) vc = v;
+      }
+    }
+  }
+  dst[idx] = vc + omega * dinv[idx] * (b[idx] - acc);
 }
 
 // x = C b with the explicit inverse of the coarsest operator (FP64 sums).
@@ -258,35 +389,97 @@ static void residual(Ctx& c, int l, const Real* b, const Real* x, Real* r) {
   MGAR_LAUNCH_CHECK_AT(level_site(2, l));
 }
 
+// Table 1 with one pre- and one post-sweep and a zero guess below the finest
+// level: per level one fused pre kernel (smooth from zero + residual), the
+// restriction, and one fused post kernel (interpolation + smooth).
 template <typename Real, int DIM>
-static void vcycle_dim(Ctx& c, const Real* b0, Real* x0, bool zero_guess) {
+static void vcycle_fused(Ctx& c, const Real* b0, Real* x0, bool zero_guess) {
   LevelBuf<Real>* h = levels<Real>(c);
   const int nl = c.nl;
   const Real om = (Real)c.p.omega;
-  Real* cur[kMaxLevels];
-  // 3D finest level with one pre- and one post-sweep: tiled, fused kernels
-  // (pre-smooth + residual, interpolation + post-smooth)
-  const bool tiled0 = DIM == 3 && c.p.nu_pre == 1 && c.p.nu_post == 1 && !c.untiled;
-  int first = 0;
-  if (tiled0) {
-    const Dims& d = c.L[0];
-    {
-      ProfScope ps(c, MGAR_KC_SMOOTH0);
+  const Real* res[kMaxLevels] = {};  // each coarse level's correction
+  const Dims& d0 = c.L[0];
+  // finest level, pre
+  Real* cur0;
+  {
+    ProfScope ps(c, MGAR_KC_SMOOTH0);
+    if (DIM == 3) {
       if (zero_guess) {
         fine3d<Real>(c, 0, ref_ke<Real>(c), b0, h[0].dinv, nullptr, nullptr, h[0].t, h[0].r);
       } else {
         fine3d<Real>(c, 3, ref_ke<Real>(c), b0, h[0].dinv, x0, nullptr, h[0].t, nullptr);
         fine3d<Real>(c, 2, ref_ke<Real>(c), b0, h[0].dinv, h[0].t, nullptr, h[0].r, nullptr);
       }
+      cur0 = h[0].t;
+    } else {
+      if (zero_guess) {
+        k_jacobi_zero<<<blocks_for(d0.n), kThreads, 0, c.stream>>>(b0, h[0].t, h[0].dinv, om,
+                                                                   (int)d0.n);
+        MGAR_LAUNCH_CHECK_AT(level_site(0, 0));
+      } else {
+        sweep<Real, DIM>(c, 0, b0, x0, h[0].t);
+      }
+      cur0 = h[0].t;
+      residual<Real, DIM>(c, 0, b0, cur0, h[0].r);
     }
-    k_restrict<Real, DIM><<<blocks_for(c.L[1].n), kThreads, 0, c.stream>>>(h[0].r, h[1].b, d,
-                                                                            c.L[1], c.fixed);
-    MGAR_LAUNCH_CHECK_AT(level_site(3, 0));
-    cur[0] = h[0].t;
-    first = 1;
   }
+  k_restrict<Real, DIM><<<blocks_for(c.L[1].n), kThreads, 0, c.stream>>>(h[0].r, h[1].b, d0, c.L[1],
+                                                                          c.fixed);
+  MGAR_LAUNCH_CHECK_AT(level_site(3, 0));
+  // coarse levels, down
+  for (int l = 1; l + 1 < nl; ++l) {
+    const Dims& d = c.L[l];
+    k_pre_coarse<Real, DIM><<<blocks_for(d.n), kThreads, 0, c.stream>>>(
+        stencil_row<Real, DIM>(c, l).op, h[l].b, h[l].dinv, om, h[l].x, h[l].r);
+    MGAR_LAUNCH_CHECK_AT(level_site(0, l));
+    k_restrict<Real, DIM><<<blocks_for(c.L[l + 1].n), kThreads, 0, c.stream>>>(h[l].r, h[l + 1].b, d,
+                                                                                c.L[l + 1], nullptr);
+    MGAR_LAUNCH_CHECK_AT(level_site(3, l));
+  }
+  // coarsest level
+  {
+    const int l = nl - 1;
+    const int rows_per_block = kThreads / 32;
+    k_coarse_solve<Real><<<(c.nc + rows_per_block - 1) / rows_per_block, kThreads, 0, c.stream>>>(
+        c.cinv, h[l].b, h[l].x, c.nc);
+    MGAR_LAUNCH_CHECK_AT(level_site(5, l));
+    res[l] = h[l].x;
+  }
+  // coarse levels, up
+  for (int l = nl - 2; l >= 1; --l) {
+    const Dims& d = c.L[l];
+    k_post_coarse<Real, DIM><<<blocks_for(d.n), kThreads, 0, c.stream>>>(
+        stencil_row<Real, DIM>(c, l).op, res[l + 1], h[l].x, h[l].b, h[l].dinv, om, h[l].t, d,
+        c.L[l + 1]);
+    MGAR_LAUNCH_CHECK_AT(level_site(4, l));
+    res[l] = h[l].t;
+  }
+  // finest level, post
+  ProfScope ps(c, MGAR_KC_SMOOTH0);
+  if (DIM == 3) {
+    fine3d<Real>(c, 1, ref_ke<Real>(c), b0, h[0].dinv, cur0, res[1], x0, nullptr);
+  } else {
+    // interpolation in place on the pre-smoothed iterate, then the sweep into x0
+    k_prolong<Real, DIM><<<blocks_for(d0.n), kThreads, 0, c.stream>>>(res[1], cur0, cur0, d0, c.L[1],
+                                                                       c.fixed);
+    MGAR_LAUNCH_CHECK_AT(level_site(4, 0));
+    sweep<Real, DIM>(c, 0, b0, cur0, x0);
+  }
+}
+
+// General Table 1 V-cycle (any numbers of pre- and post-sweeps).
+template <typename Real, int DIM>
+static void vcycle_dim(Ctx& c, const Real* b0, Real* x0, bool zero_guess) {
+  if (c.p.nu_pre == 1 && c.p.nu_post == 1 && c.nl >= 2 && !c.untiled) {
+    vcycle_fused<Real, DIM>(c, b0, x0, zero_guess);
+    return;
+  }
+  LevelBuf<Real>* h = levels<Real>(c);
+  const int nl = c.nl;
+  const Real om = (Real)c.p.omega;
+  Real* cur[kMaxLevels];
   // downward leg
-  for (int l = first; l + 1 < nl; ++l) {
+  for (int l = 0; l + 1 < nl; ++l) {
     const Dims& d = c.L[l];
     const Real* b = l == 0 ? b0 : h[l].b;
     Real* x = l == 0 ? x0 : h[l].x;
@@ -323,7 +516,7 @@ static void vcycle_dim(Ctx& c, const Real* b0, Real* x0, bool zero_guess) {
     MGAR_LAUNCH_CHECK_AT(level_site(5, l));
   }
   // upward leg
-  for (int l = nl - 2; l >= first; --l) {
+  for (int l = nl - 2; l >= 0; --l) {
     const Dims& d = c.L[l];
     const Real* b = l == 0 ? b0 : h[l].b;
     Real* x = l == 0 ? x0 : h[l].x;
@@ -340,10 +533,6 @@ static void vcycle_dim(Ctx& c, const Real* b0, Real* x0, bool zero_guess) {
       sweep<Real, DIM>(c, l, b, cu, nxt);
       cu = nxt;
     }
-  }
-  if (tiled0) {
-    ProfScope ps(c, MGAR_KC_SMOOTH0);
-    fine3d<Real>(c, 1, ref_ke<Real>(c), b0, h[0].dinv, h[0].t, h[1].x, x0, nullptr);
   }
 }
 
