@@ -39,8 +39,8 @@ def parse():
     ap.add_argument("--cycles", type=int, default=0, help="design cycles per step (0 = workload's)")
     ap.add_argument("--guess", default="previous", choices=["previous", "zero"])
     ap.add_argument("--eps1", type=float, default=None)
-    ap.add_argument("--kernel", default="apply64",
-                    choices=["apply64", "smooth0", "resid0", "oc", "galerkin0", "filter", "sens"])
+    ap.add_argument("--kernel", default=None, choices=["df3d", "apply64", "smooth0", "galerkin0"],
+                    help="kernel class of the roofline (default: the dominant one of the path)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 MGCG comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
     ap.add_argument("--no-check", action="store_true", help="skip the equal-compliance check")
@@ -127,6 +127,11 @@ def max_over_ranks(x, world):
 
 
 # ------------------------------------------------------------- roofline
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+# one ncu capture of the kernel as it stands; a kernel changed since its
+# capture has no entry (traffic null).
+TRAFFIC = {}
+
 def load_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -143,35 +148,45 @@ def fp64_peak_tflops(sm_mhz):
     return 152 * 2 * 2 * mhz * 1e6 / 1e12
 
 
+def fp32_peak_tops(sm_mhz):
+    """FP32-pipe peak of GB300 from its unit count and clock: 152 SMs x 128
+    FP32 lanes, one add, multiply or fused multiply-add each per clock
+    (counted as one operation, as the df64 operation counts are)."""
+    mhz = sm_mhz or 2070.0
+    return 152 * 128 * mhz * 1e6 / 1e12
+
+
 def kernel_model(kernel, w):
     """Algorithmic work per launch of a kernel class on workload w:
-    (bytes, fp64 flops, bound).  Per-unit figures are stated in the design doc."""
+    (bytes, operations, bound, pipe).  Per-unit figures are stated in
+    DESIGN.md."""
     n = w.n_nodes
     e = w.n_elems
+    if kernel == "df3d":
+        # mixed path, tiled df64 H8 product with the fused CG direction update
+        # (p = z + beta p_old, y = A p, p.y), per node in FP32-pipe operations:
+        # direction update 18 (df mul 7 + df add 11), 12 face-diagonal weight
+        # sums 132 (df add 11 each), 20 difference terms 400 (exact
+        # difference 8, TwoProd product 4, TwoSum accumulation 8), final
+        # normalisation and 1/12 scale 10, p.y 18: 578.  Bytes: p_old and y
+        # and p (8 B each), z (4 B), one k_e (8 B), mask (1 B): 37.
+        return 37 * n, 578 * n, "alu", "fp32"
     if kernel == "apply64":
         # 3D H8 y = A x in FP64, node-centred: read x (8 B) and one k_e per
         # node (8 B, each element read once) and the fixed-node mask (1 B),
         # write y (8 B); 62 FP64 FLOP per node (7 adds for sum k, 12 pair
         # sums, 20 FMA, 3 multiplies), + 2 for the fused p.Ap dot.
-        return 25 * n, 64 * n, "alu"
+        return 25 * n, 64 * n, "alu", "fp64"
     if kernel == "smooth0":
-        # FP32 level-0 Jacobi: read x, b, dinv (12 B), k_e (4 B), mask (1 B), write x (4 B)
-        return 21 * n, 0, "hbm"
-    if kernel == "resid0":
-        return 21 * n, 0, "hbm"
-    if kernel == "oc":
-        # read s, lo, hi, dv (32 B per element)
-        return 32 * e, 5 * e, "alu"
-    if kernel == "filter":
-        return 24 * e, 40 * e, "alu"
-    if kernel == "sens":
-        return 8 * n + 16 * e, 50 * e, "alu"
+        # FP32 level-0 fused smoothing passes of the V-cycle: read b, dinv
+        # (8 B), k_e (4 B), mask (1 B), x (4 B), write x and r (8 B)
+        return 25 * n, 0, "hbm", None
     if kernel == "galerkin0":
-        return 8 * e + 64 * 4 * e // 8, 0, "hbm"
+        return 8 * e + 64 * 4 * e // 8, 0, "hbm", None
     raise ValueError(kernel)
 
 
-KC = {"apply64": 1, "smooth0": 2, "resid0": 3, "oc": 4, "galerkin0": 5, "filter": 6, "sens": 7}
+KC = {"df3d": 1, "apply64": 1, "smooth0": 2, "galerkin0": 5}
 
 
 # ------------------------------------------------------------- GPU arm
@@ -215,7 +230,8 @@ def run_gpu(args):
 
     # timed region: K whole runs, L2 flushed between them (outside the events)
     sampler = ClockSampler(local)
-    kc = KC[args.kernel]
+    kernel = args.kernel or ("df3d" if prec == mgar.MGAR_MIXED and w.nz else "apply64")
+    kc = KC[kernel]
     times = []
     infos = []
     barrier(world)
@@ -308,22 +324,30 @@ def run_gpu(args):
                  "reference": "FP64 MGCG (eps2 1e-10) on the same design each cycle"}
 
     peaks = load_peaks()
-    bytes_, flops, bound = kernel_model(args.kernel, w)
+    bytes_, flops, bound, pipe = kernel_model(kernel, w)
     avg_ms = kern_ms / max(kern_launches, 1)
-    if bound == "alu":
+    if bound == "alu" and pipe == "fp32":
+        achieved = flops / (avg_ms * 1e-3) / 1e12
+        peak = fp32_peak_tops(clocks.get("sm_mhz"))
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "Top/s (FP32-pipe operations of the df64 arithmetic)",
+                "frac": achieved / peak, "traffic": TRAFFIC.get(kernel),
+                "peak_source": "152 SMs x 128 FP32 lanes x SM clock under load (derived, see DESIGN.md)",
+                "hbm_gbs": bytes_ / (avg_ms * 1e-3) / 1e9}
+    elif bound == "alu":
         achieved = flops / (avg_ms * 1e-3) / 1e12
         peak = fp64_peak_tflops(clocks.get("sm_mhz"))
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s (fp64)",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": TRAFFIC.get(kernel),
                 "peak_source": "FP64 unit count x SM clock under load (derived, see DESIGN.md)",
                 "hbm_gbs": bytes_ / (avg_ms * 1e-3) / 1e9}
     else:
         achieved = bytes_ / (avg_ms * 1e-3) / 1e9
         peak = peaks.get("hbm_gbs", 6800.0)
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": TRAFFIC.get(kernel),
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
-    roof.update({"kernel": args.kernel, "launches": kern_launches, "avg_launch_us": avg_ms * 1e3,
+    roof.update({"kernel": kernel, "launches": kern_launches, "avg_launch_us": avg_ms * 1e3,
                  "share_of_step": kern_ms / sum(times)})
 
     n_mgcg = sum(1 for i in infos if i["used_mgcg"])

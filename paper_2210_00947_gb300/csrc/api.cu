@@ -317,6 +317,8 @@ int mgar_create(mgar_t* out, const mgar_params* p, const uint8_t* fixed_mask, co
     // debugging aid: MGAR_NO_GRAPHS=1 issues every V-cycle launch directly
     if (const char* ng = std::getenv("MGAR_NO_GRAPHS")) c->use_graphs = !(ng[0] == '1');
     if (const char* ut = std::getenv("MGAR_UNTILED")) c->untiled = (ut[0] == '1');
+    bottom_prepare(*c);
+    if (const char* nb = std::getenv("MGAR_NO_CLUSTER")) c->bottom_ok = c->bottom_ok && nb[0] != '1';
     if (c->dim == 3) {
       fine3d_prepare(*c);
       if (P.precision == MGAR_MIXED) df3d_prepare(*c);

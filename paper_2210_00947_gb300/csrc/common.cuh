@@ -183,6 +183,7 @@ struct Ctx {
   bool untiled = false;  // MGAR_UNTILED=1: generic finest-level kernels (debugging aid)
   int f3d_gz[2][4] = {};  // z runs of the tiled finest-level kernels [FP32, FP64][mode]
   int df3d_gz[3] = {};    // z runs of the tiled df64 operator kernels [mode]
+  bool bottom_ok = false; // the V-cycle's bottom levels run as one cluster launch
   cudaStream_t cap_stream = nullptr;
 
   // instrumentation: CUDA-event timing of one kernel class
@@ -594,6 +595,9 @@ void fine3d(Ctx& c, int mode, const Real* ke, const Real* b, const Real* dinv, c
             const Real* xc, Real* out0, Real* out1);
 // launch shapes of the tiled kernels (occupancy query; call outside stream capture)
 void fine3d_prepare(Ctx& c);
+// vcycle.cu: can the bottom levels run as one thread-block cluster launch
+void bottom_prepare(Ctx& c);
+constexpr int64_t kBottomNodes = 8192;  // largest level handled by the cluster launch
 // df3d.cu: tiled df64 finest-level operator (3D)
 void df3d_prepare(Ctx& c);
 void df3d_apply(Ctx& c, const float2* x, float2* y, double* dot);

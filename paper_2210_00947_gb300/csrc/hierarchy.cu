@@ -47,19 +47,6 @@ static void unit_element(int dim, double* k) {
     }
 }
 
-// Unique (I <= J) entries of a symmetric 2^d x 2^d element matrix, spread
-// evenly over the 2^d threads that build one coarse element.
-__device__ __forceinline__ void pair_of(int u, int nen, int& I, int& J) {
-  I = 0;
-  int rowlen = nen;
-  while (u >= rowlen) {
-    u -= rowlen;
-    ++I;
-    --rowlen;
-  }
-  J = I + u;
-}
-
 // Sub-element s of coarse element (cx, cy, cz): fine element index, validity
 // and 1D position types.
 template <int DIM>
@@ -76,116 +63,121 @@ __device__ __forceinline__ bool sub_element(const Dims& f, int cx, int cy, int c
 }
 
 // ------------------------------------------------------------------ kernels
-// Level 0 -> 1: element matrices of A_1 from k_e, 2^d threads per coarse
-// element, each computing its share of the unique entries.  Sub-elements
-// without fixed nodes use the tables G_type = P_type^T k0 P_type; a coarse
-// element with any fixed fine node takes (Z P)^T k0 (Z P) entry by entry.
+// Level 0 -> 1: element matrices of A_1 from k_e, one thread per entry
+// (I, J) of a coarse element matrix.  Sub-elements without fixed nodes use
+// the tables G_type = P_type^T k0 P_type (entry IJ of all types is read by
+// consecutive threads, so the table reads coalesce); a coarse element with
+// any fixed fine node takes (Z P)^T k0 (Z P) entry by entry.
 template <typename Real, int DIM>
 __global__ void k_galerkin_fine(const Real* __restrict__ ke, const uint8_t* __restrict__ fixed,
                                 const uint8_t* __restrict__ efix, Dims f, Dims cd,
                                 const Real* __restrict__ G, const double* __restrict__ k0,
                                 Real* __restrict__ elem) {
   constexpr int nen = 1 << DIM;
-  constexpr int npairs = nen * (nen + 1) / 2;
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= (int)cd.ne * nen) return;
-  const int E = tid / nen;
-  const int th = tid - E * nen;
+  constexpr int NN = nen * nen;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= cd.ne * NN) return;
+  const int E = (int)(tid / NN);
+  const int IJ = (int)(tid - (int64_t)E * NN);
+  const int I = IJ / nen, J = IJ - (IJ / nen) * nen;
   int cx, cy, cz;
   coords(E, cd.fEX, cd.fEXY, cx, cy, cz);
-  Real kv[nen];
-  int ty[nen], sub_ok = 0, any_fixed = 0;
+  Real acc = Real(0);
+  int any_fixed = 0;
 #pragma unroll
   for (int s = 0; s < nen; ++s) {
     int e, t[3];
     const bool ok = sub_element<DIM>(f, cx, cy, cz, s, e, t) && CK(e, f.ne);
-    kv[s] = ok ? ke[e] : Real(0);
-    ty[s] = t[0] + 3 * t[1] + 9 * t[2];
-    if (ok) {
-      sub_ok |= 1 << s;
-      any_fixed |= efix[e];
-    }
+    const Real kv = ok ? ke[e] : Real(0);
+    any_fixed |= ok ? efix[e] : 0;
+    const int ty = t[0] + 3 * t[1] + 9 * t[2];
+    acc += kv * G[ty * NN + IJ];
   }
-  Real* dst = elem + (size_t)E * nen * nen;
-  for (int u = th; u < npairs; u += nen) {
-    int I, J;
-    pair_of(u, nen, I, J);
-    Real acc = Real(0);
-    if (!any_fixed) {
-#pragma unroll
-      for (int s = 0; s < nen; ++s)
-        acc += kv[s] * G[(size_t)ty[s] * nen * nen + I * nen + J];
-    } else {
-      for (int s = 0; s < nen; ++s) {
-        if (!(sub_ok & (1 << s))) continue;
-        int e, t[3];
-        sub_element<DIM>(f, cx, cy, cz, s, e, t);
-        const int fx = 2 * cx + (s & 1), fy = 2 * cy + ((s >> 1) & 1), fz = 2 * cz + ((s >> 2) & 1);
-        unsigned fm = 0;
-        for (int a = 0; a < nen; ++a) {
-          const int nd = (fx + (a & 1)) + f.NX * ((fy + ((a >> 1) & 1)) + f.NY * (fz + ((a >> 2) & 1)));
-          if (CK(nd, f.n) && fixed[nd]) fm |= 1u << a;
-        }
-        Real part = Real(0);
-        for (int a = 0; a < nen; ++a) {
-          const float pa = pw<DIM>(t, a, I);
-          if ((fm & (1u << a)) || pa == 0.f) continue;
-          for (int b = 0; b < nen; ++b) {
-            const float pb = pw<DIM>(t, b, J);
-            if ((fm & (1u << b)) || pb == 0.f) continue;
-            part += (Real)(pa * pb) * (Real)k0[a * nen + b];
-          }
-        }
-        acc += kv[s] * part;
-      }
-    }
-    if (CK((size_t)E * nen * nen + I * nen + J, cd.ne * nen * nen)) {
-      dst[I * nen + J] = acc;
-      dst[J * nen + I] = acc;
-    }
-  }
-}
-
-// Level l -> l+1 (l >= 1) from stored element matrices: entry (I, J) of the
-// coarse element is sum_s sum_a sum_b P_s[a,I] M_s[a,b] P_s[b,J].
-template <typename Real, int DIM>
-__global__ void k_galerkin_coarse(const Real* __restrict__ elem_f, Dims f, Dims cd,
-                                  Real* __restrict__ elem_c) {
-  constexpr int nen = 1 << DIM;
-  constexpr int npairs = nen * (nen + 1) / 2;
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= (int)cd.ne * nen) return;
-  const int E = tid / nen;
-  const int th = tid - E * nen;
-  int cx, cy, cz;
-  coords(E, cd.fEX, cd.fEXY, cx, cy, cz);
-  Real* dst = elem_c + (size_t)E * nen * nen;
-  for (int u = th; u < npairs; u += nen) {
-    int I, J;
-    pair_of(u, nen, I, J);
-    Real acc = Real(0);
+  if (any_fixed) {
+    acc = Real(0);
     for (int s = 0; s < nen; ++s) {
       int e, t[3];
       if (!sub_element<DIM>(f, cx, cy, cz, s, e, t) || !CK(e, f.ne)) continue;
-      const Real* M = elem_f + (size_t)e * nen * nen;
-#pragma unroll
+      const int fx = 2 * cx + (s & 1), fy = 2 * cy + ((s >> 1) & 1), fz = 2 * cz + ((s >> 2) & 1);
+      unsigned fm = 0;
+      for (int a = 0; a < nen; ++a) {
+        const int nd = (fx + (a & 1)) + f.NX * ((fy + ((a >> 1) & 1)) + f.NY * (fz + ((a >> 2) & 1)));
+        if (CK(nd, f.n) && fixed[nd]) fm |= 1u << a;
+      }
+      Real part = Real(0);
       for (int a = 0; a < nen; ++a) {
         const float pa = pw<DIM>(t, a, I);
-        if (pa == 0.f) continue;
-        Real row = Real(0);
-#pragma unroll
+        if ((fm & (1u << a)) || pa == 0.f) continue;
         for (int b = 0; b < nen; ++b) {
           const float pb = pw<DIM>(t, b, J);
-          if (pb != 0.f) row += (Real)pb * M[a * nen + b];
+          if ((fm & (1u << b)) || pb == 0.f) continue;
+          part += (Real)(pa * pb) * (Real)k0[a * nen + b];
         }
-        acc += (Real)pa * row;
       }
-    }
-    if (CK((size_t)E * nen * nen + I * nen + J, cd.ne * nen * nen)) {
-      dst[I * nen + J] = acc;
-      dst[J * nen + I] = acc;
+      acc += ke[e] * part;
     }
   }
+  elem[tid] = acc;
+}
+
+// Level l -> l+1 (l >= 1) from stored element matrices:
+//   A_E = sum_s P_s^T M_s P_s
+// over the sub-elements s of coarse element E.  A block takes 256 / 2^(2d) coarse
+// elements, stages their sub-element matrices in shared memory, forms
+// T_s = M_s P_s (each thread one entry of every T_s) and then
+// A_E[I, J] = sum_s sum_a P_s[a, I] T_s[a, J], with P_s read from the
+// per-type interpolation tables.
+
+template <typename Real, int DIM>
+__global__ void __launch_bounds__(kThreads) k_galerkin_coarse(const Real* __restrict__ elem_f, Dims f,
+                                                               Dims cd, const Real* __restrict__ Ptab,
+                                                               Real* __restrict__ elem_c) {
+  constexpr int nen = 1 << DIM;
+  constexpr int NN = nen * nen;
+  constexpr int EPB = kThreads / NN;
+  constexpr int NT = DIM == 2 ? 9 : 27;
+  __shared__ Real M[EPB][nen][NN];
+  __shared__ Real T[EPB][nen][NN];
+  __shared__ Real Ps[NT * NN];
+  for (int u = threadIdx.x; u < NT * NN; u += blockDim.x) Ps[u] = Ptab[u];
+  const int le = threadIdx.x / NN;
+  const int IJ = threadIdx.x - le * NN;
+  const int I = IJ / nen, J = IJ - (IJ / nen) * nen;
+  const int64_t E = (int64_t)blockIdx.x * EPB + le;
+  const bool valid = E < cd.ne;
+  int cx = 0, cy = 0, cz = 0;
+  if (valid) coords((int)E, cd.fEX, cd.fEXY, cx, cy, cz);
+  int ty[nen];
+#pragma unroll
+  for (int s = 0; s < nen; ++s) {
+    // sub_element sets e and t on every call, also for the padding threads
+    // past the last coarse element (cx = cy = cz = 0 there)
+    int e = 0, t[3] = {0, 0, 0};
+    const bool in = sub_element<DIM>(f, cx, cy, cz, s, e, t);
+    const bool ok = valid && in && CK((int64_t)e * NN + IJ, f.ne * NN);
+    ty[s] = t[0] + 3 * t[1] + 9 * t[2];
+    M[le][s][IJ] = ok ? elem_f[(int64_t)e * NN + IJ] : Real(0);
+  }
+  __syncthreads();
+  // T_s[I][J] = sum_b M_s[I][b] P_s[b][J]
+#pragma unroll
+  for (int s = 0; s < nen; ++s) {
+    const Real* P = Ps + ty[s] * NN;
+    Real acc = Real(0);
+#pragma unroll
+    for (int b = 0; b < nen; ++b) acc += M[le][s][I * nen + b] * P[b * nen + J];
+    T[le][s][IJ] = acc;
+  }
+  __syncthreads();
+  // A[I][J] = sum_s sum_a P_s[a][I] T_s[a][J]
+  Real acc = Real(0);
+#pragma unroll
+  for (int s = 0; s < nen; ++s) {
+    const Real* P = Ps + ty[s] * NN;
+#pragma unroll
+    for (int a = 0; a < nen; ++a) acc += P[a * nen + I] * T[le][s][a * nen + J];
+  }
+  if (valid) elem_c[E * NN + IJ] = acc;
 }
 
 // Node stencils and inverse diagonal of a level from its element matrices.
@@ -427,7 +419,8 @@ void alloc_hierarchy(Ctx& c) {
   if (c.p.precision != MGAR_FP64) MGAR_CUDA(cudaMalloc(&c.cinv_f, (size_t)c.nc * c.nc * sizeof(float)));
   // constant tables: k0 (nen^2) then G (3^dim * nen^2)
   const int nen = c.nen, ntypes = c.dim == 2 ? 9 : 27;
-  std::vector<double> k0(nen * nen), G((size_t)ntypes * nen * nen, 0.0);
+  std::vector<double> k0(nen * nen), G((size_t)ntypes * nen * nen, 0.0),
+      Pt((size_t)ntypes * nen * nen, 0.0);
   unit_element(c.dim, k0.data());
   for (int type = 0; type < ntypes; ++type) {
     const int t[3] = {type % 3, (type / 3) % 3, type / 9};
@@ -437,6 +430,7 @@ void alloc_hierarchy(Ctx& c) {
         double w = w1(t[0], a & 1, I & 1) * w1(t[1], (a >> 1) & 1, (I >> 1) & 1);
         if (c.dim == 3) w *= w1(t[2], (a >> 2) & 1, (I >> 2) & 1);
         P[a * nen + I] = w;
+        Pt[(size_t)type * nen * nen + a * nen + I] = w;
       }
     for (int I = 0; I < nen; ++I)
       for (int J = 0; J < nen; ++J) {
@@ -446,13 +440,15 @@ void alloc_hierarchy(Ctx& c) {
         G[(size_t)type * nen * nen + I * nen + J] = s;
       }
   }
-  MGAR_CUDA(cudaMalloc(&c.tables, (k0.size() + G.size()) * sizeof(double)));
-  MGAR_CUDA(cudaMemcpy(c.tables, k0.data(), k0.size() * sizeof(double), cudaMemcpyHostToDevice));
-  MGAR_CUDA(cudaMemcpy(c.tables + k0.size(), G.data(), G.size() * sizeof(double),
-                       cudaMemcpyHostToDevice));
-  std::vector<float> Gf(G.begin(), G.end());
-  MGAR_CUDA(cudaMalloc(&c.tables_f, Gf.size() * sizeof(float)));
-  MGAR_CUDA(cudaMemcpy(c.tables_f, Gf.data(), Gf.size() * sizeof(float), cudaMemcpyHostToDevice));
+  // device layout: k0 | G | P (FP64), G | P (FP32)
+  std::vector<double> all(k0);
+  all.insert(all.end(), G.begin(), G.end());
+  all.insert(all.end(), Pt.begin(), Pt.end());
+  MGAR_CUDA(cudaMalloc(&c.tables, all.size() * sizeof(double)));
+  MGAR_CUDA(cudaMemcpy(c.tables, all.data(), all.size() * sizeof(double), cudaMemcpyHostToDevice));
+  std::vector<float> allf(all.begin() + k0.size(), all.end());
+  MGAR_CUDA(cudaMalloc(&c.tables_f, allf.size() * sizeof(float)));
+  MGAR_CUDA(cudaMemcpy(c.tables_f, allf.data(), allf.size() * sizeof(float), cudaMemcpyHostToDevice));
 }
 
 void free_hierarchy(Ctx& c) {
@@ -478,6 +474,11 @@ template <>
 const double* g_tables<double>(Ctx& c) { return c.tables + c.nen * c.nen; }
 template <>
 const float* g_tables<float>(Ctx& c) { return c.tables_f; }
+// interpolation tables P_type[a * nen + I], after the G tables
+template <typename Real>
+static const Real* p_tables(Ctx& c) {
+  return g_tables<Real>(c) + (size_t)(c.dim == 2 ? 9 : 27) * c.nen * c.nen;
+}
 
 template <typename Real, int DIM>
 static void build_levels(Ctx& c, const Real* ke0, LevelBuf<Real>* h) {
@@ -490,14 +491,14 @@ static void build_levels(Ctx& c, const Real* ke0, LevelBuf<Real>* h) {
   for (int l = 0; l + 1 < c.nl; ++l) {
     const Dims& f = c.L[l];
     const Dims& cd = c.L[l + 1];
-    const int64_t work = cd.ne * nen;
     ProfScope ps(c, l == 0 ? MGAR_KC_GALERKIN0 : -1);
+    const int64_t entries = cd.ne * nen * nen;  // one thread per element-matrix entry
     if (l == 0)
-      k_galerkin_fine<Real, DIM><<<blocks_for(work), kThreads, 0, s>>>(ke0, c.fixed, c.efix, f, cd, G,
-                                                                         k0, h[1].elem);
+      k_galerkin_fine<Real, DIM><<<blocks_for(entries), kThreads, 0, s>>>(ke0, c.fixed, c.efix, f, cd,
+                                                                            G, k0, h[1].elem);
     else
-      k_galerkin_coarse<Real, DIM><<<blocks_for(work), kThreads, 0, s>>>(h[l].elem, f, cd,
-                                                                           h[l + 1].elem);
+      k_galerkin_coarse<Real, DIM><<<blocks_for(entries), kThreads, 0, s>>>(
+          h[l].elem, f, cd, p_tables<Real>(c), h[l + 1].elem);
     MGAR_LAUNCH_CHECK();
     k_assemble<Real, DIM><<<blocks_for(cd.n), kThreads, 0, s>>>(h[l + 1].elem, cd, h[l + 1].st,
                                                                  h[l + 1].dinv);

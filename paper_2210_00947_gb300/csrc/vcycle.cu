@@ -51,6 +51,14 @@ struct StencilRow {
   __device__ __forceinline__ int size() const { return op.n; }
 };
 
+// Loads of data written earlier in the same launch by other thread blocks
+// of a cluster go through L2 (CG = true); everything else may use L1.
+template <bool CG, typename Real>
+__device__ __forceinline__ Real ldv(const Real* p) {
+  if (CG) return __ldcg(p);
+  return *p;
+}
+
 // ----------------------------------------------------------------- kernels
 template <class Row, typename Real>
 __global__ void k_jacobi(Row row, const Real* __restrict__ b, const Real* __restrict__ xin,
@@ -112,11 +120,10 @@ __device__ __forceinline__ int prolong_taps(int i, int nf, int* idx, float* w) {
   idx[0] = idx[1] = (i + 1) >> 1; w[0] = 1.f; w[1] = 0.f; return 1;
 }
 
-template <typename Real, int DIM>
-__global__ void k_restrict(const Real* __restrict__ r, Real* __restrict__ bc, Dims f, Dims cd,
-                           const uint8_t* __restrict__ fixed) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= cd.n) return;
+template <typename Real, int DIM, bool CG>
+__device__ __forceinline__ void restrict_node(const Real* __restrict__ r, Real* __restrict__ bc,
+                                              const Dims& f, const Dims& cd,
+                                              const uint8_t* __restrict__ fixed, int idx) {
   int I, J, K;
   coords(idx, cd.fNX, cd.fNXY, I, J, K);
   int ix[3], iy[3], iz[3] = {0, 0, 0};
@@ -135,12 +142,19 @@ __global__ void k_restrict(const Real* __restrict__ r, Real* __restrict__ bc, Di
       for (int a = 0; a < 3; ++a) {
         const int fi = base + ix[a];
         if (!CK(fi, f.n)) continue;
-        const Real rv = r[fi];
+        const Real rv = ldv<CG>(r + fi);
         const bool fx = fixed ? fixed[fi] != 0 : false;
         acc += fx ? Real(0) : (wyz * (Real)wx[a]) * rv;
       }
     }
   bc[idx] = acc;
+}
+
+template <typename Real, int DIM>
+__global__ void k_restrict(const Real* __restrict__ r, Real* __restrict__ bc, Dims f, Dims cd,
+                           const uint8_t* __restrict__ fixed) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < cd.n) restrict_node<Real, DIM, false>(r, bc, f, cd, fixed, idx);
 }
 
 // dst = cur + P xc (fixed fine nodes keep cur); dst may equal cur.
@@ -176,12 +190,10 @@ __global__ void k_prolong(const Real* __restrict__ xc, const Real* cur, Real* ds
 
 // Fused pre-smooth from a zero guess and residual on an assembled level:
 // x = w D^-1 b, r = b - A x (the neighbours' x recomputed from b and D^-1).
-template <typename Real, int DIM>
-__global__ void k_pre_coarse(StencilOp<Real> op, const Real* __restrict__ b,
-                             const Real* __restrict__ dinv, Real omega, Real* __restrict__ x,
-                             Real* __restrict__ r) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= op.n) return;
+template <typename Real, int DIM, bool CG>
+__device__ __forceinline__ void pre_node(const StencilOp<Real>& op, const Real* __restrict__ b,
+                                         const Real* __restrict__ dinv, Real omega,
+                                         Real* __restrict__ x, Real* __restrict__ r, int idx) {
   int i, j, k;
   coords(idx, op.fNX, op.fNXY, i, j, k);
   const int NX = op.NX, NXY = op.NX * op.NY;
@@ -198,13 +210,21 @@ __global__ void k_pre_coarse(StencilOp<Real> op, const Real* __restrict__ b,
         const int s = (dx + 1) + 3 * (dy + 1) + (DIM == 3 ? 9 * (dz + 1) : 0);
         const int nb = ii + NX * jj + NXY * kk;
         if (!CK(nb, op.n)) continue;
-        acc += op.st[s * op.n + idx] * (omega * dinv[nb] * b[nb]);
+        acc += op.st[s * op.n + idx] * (omega * dinv[nb] * ldv<CG>(b + nb));
       }
     }
   }
-  const Real bi = b[idx];
+  const Real bi = ldv<CG>(b + idx);
   x[idx] = omega * dinv[idx] * bi;
   r[idx] = bi - acc;
+}
+
+template <typename Real, int DIM>
+__global__ void k_pre_coarse(StencilOp<Real> op, const Real* __restrict__ b,
+                             const Real* __restrict__ dinv, Real omega, Real* __restrict__ x,
+                             Real* __restrict__ r) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < op.n) pre_node<Real, DIM, false>(op, b, dinv, omega, x, r, idx);
 }
 
 // Per axis: the coarse nodes c0, c0+1, c0+2 that interpolate onto the fine
@@ -231,13 +251,12 @@ __device__ __forceinline__ void interp_axis(int f, int nf, int& c0, float (&w)[3
 // v = x + P x_c at the node and its neighbours, x' = v + w D^-1 (b - A v).
 // The 3^d coarse values around the node are read once and interpolated
 // separably onto the 3^d fine positions.
-template <typename Real, int DIM>
-__global__ void k_post_coarse(StencilOp<Real> op, const Real* __restrict__ xc,
-                              const Real* __restrict__ cur, const Real* __restrict__ b,
-                              const Real* __restrict__ dinv, Real omega, Real* __restrict__ dst,
-                              Dims f, Dims cd) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= op.n) return;
+template <typename Real, int DIM, bool CG>
+__device__ __forceinline__ void post_node(const StencilOp<Real>& op, const Real* __restrict__ xc,
+                                          const Real* __restrict__ cur, const Real* __restrict__ b,
+                                          const Real* __restrict__ dinv, Real omega,
+                                          Real* __restrict__ dst, const Dims& f, const Dims& cd,
+                                          int idx) {
   int i, j, k;
   coords(idx, op.fNX, op.fNXY, i, j, k);
   constexpr int NZ3 = DIM == 3 ? 3 : 1;
@@ -256,7 +275,7 @@ __global__ void k_post_coarse(StencilOp<Real> op, const Real* __restrict__ xc,
       for (int ux = 0; ux < 3; ++ux) {
         const int ci = min(cx0 + ux, cd.NX - 1) + cd.NX * (min(cy0 + uy, cd.NY - 1) +
                                                            cd.NY * min(cz0 + uz, cd.NZ - 1));
-        C[uz][uy][ux] = CK(ci, cd.n) ? xc[ci] : Real(0);
+        C[uz][uy][ux] = CK(ci, cd.n) ? ldv<CG>(xc + ci) : Real(0);
       }
   // along x, then y, then z
   Real T1[NZ3][3][3];
@@ -296,28 +315,97 @@ __global__ void k_post_coarse(StencilOp<Real> op, const Real* __restrict__ xc,
           pv = T2[0][ty][tx];
         const int nb = ii + NX * jj + NXY * kk;
         if (!CK(nb, op.n)) continue;
-        const Real v = cur[nb] + pv;
+        const Real v = ldv<CG>(cur + nb) + pv;
         const int s = tx + 3 * ty + 9 * tz;
         acc += op.st[s * op.n + idx] * v;
         if (tx == 1 && ty == 1 && tz == (DIM == 3 ? 1 : 0)) vc = v;
       }
     }
   }
-  dst[idx] = vc + omega * dinv[idx] * (b[idx] - acc);
+  dst[idx] = vc + omega * dinv[idx] * (ldv<CG>(b + idx) - acc);
+}
+
+template <typename Real, int DIM>
+__global__ void k_post_coarse(StencilOp<Real> op, const Real* __restrict__ xc,
+                              const Real* __restrict__ cur, const Real* __restrict__ b,
+                              const Real* __restrict__ dinv, Real omega, Real* __restrict__ dst,
+                              Dims f, Dims cd) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx < op.n) post_node<Real, DIM, false>(op, xc, cur, b, dinv, omega, dst, f, cd, idx);
 }
 
 // x = C b with the explicit inverse of the coarsest operator (FP64 sums).
+template <typename Real, bool CG>
+__device__ __forceinline__ void coarse_row(const double* __restrict__ cinv, const Real* __restrict__ b,
+                                           Real* __restrict__ x, int n, int row, int lane) {
+  double s = 0.0;
+  for (int j = lane; j < n; j += 32)
+    if (CK((int64_t)row * n + j, (int64_t)n * n)) s += cinv[(int64_t)row * n + j] * (double)ldv<CG>(b + j);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) x[row] = (Real)s;
+}
+
 template <typename Real>
 __global__ void k_coarse_solve(const double* __restrict__ cinv, const Real* __restrict__ b,
                                Real* __restrict__ x, int n) {
   const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (row >= n) return;
-  double s = 0.0;
-  for (int j = lane; j < n; j += 32)
-    if (CK((int64_t)row * n + j, (int64_t)n * n)) s += cinv[(int64_t)row * n + j] * (double)b[j];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if (lane == 0) x[row] = (Real)s;
+  if (row < n) coarse_row<Real, false>(cinv, b, x, n, row, threadIdx.x & 31);
+}
+
+// ------------------------------------------- bottom of the V-cycle, one cluster
+// Levels lb .. nl-1 (each at most kBottomNodes nodes) of the zero-guess
+// V-cycle in one launch of a thread-block cluster: the CTAs of the cluster
+// stride over each level's nodes, and the hardware cluster barrier (release
+// on arrive, acquire on wait) separates the phases, so the small levels cost
+// no kernel launches and no waits of this code's own.
+constexpr int kBottomThreads = 512;
+constexpr int kBottomCluster = 8;
+
+template <typename Real>
+struct BottomArgs {
+  StencilOp<Real> op[kMaxLevels];
+  Dims L[kMaxLevels];
+  Real* b[kMaxLevels];
+  Real* x[kMaxLevels];
+  Real* t[kMaxLevels];
+  Real* r[kMaxLevels];
+  const double* cinv;
+  int nc, lb, nl;
+  Real omega;
+};
+
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile(
+      "barrier.cluster.arrive.release.aligned;\n"
+      "barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+template <typename Real, int DIM>
+__global__ void __launch_bounds__(kBottomThreads) k_bottom(BottomArgs<Real> a) {
+  const int nthr = gridDim.x * blockDim.x;
+  const int vt = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int l = a.lb; l + 1 < a.nl; ++l) {
+    for (int idx = vt; idx < a.L[l].n; idx += nthr)
+      pre_node<Real, DIM, true>(a.op[l], a.b[l], a.op[l].dinv, a.omega, a.x[l], a.r[l], idx);
+    cluster_barrier();
+    for (int idx = vt; idx < a.L[l + 1].n; idx += nthr)
+      restrict_node<Real, DIM, true>(a.r[l], a.b[l + 1], a.L[l], a.L[l + 1], nullptr, idx);
+    cluster_barrier();
+  }
+  {
+    const int l = a.nl - 1;
+    const int warp = vt >> 5, nwarps = nthr >> 5, lane = threadIdx.x & 31;
+    for (int row = warp; row < a.nc; row += nwarps)
+      coarse_row<Real, true>(a.cinv, a.b[l], a.x[l], a.nc, row, lane);
+  }
+  const Real* res = a.x[a.nl - 1];
+  for (int l = a.nl - 2; l >= a.lb; --l) {
+    cluster_barrier();
+    for (int idx = vt; idx < a.L[l].n; idx += nthr)
+      post_node<Real, DIM, true>(a.op[l], res, a.x[l], a.b[l], a.op[l].dinv, a.omega, a.t[l], a.L[l],
+                                 a.L[l + 1], idx);
+    res = a.t[l];
+  }
 }
 
 __global__ void k_convert_d2f(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
@@ -389,9 +477,78 @@ static void residual(Ctx& c, int l, const Real* b, const Real* x, Real* r) {
   MGAR_LAUNCH_CHECK_AT(level_site(2, l));
 }
 
+// First level handled by the cluster kernel (nl if none).
+static int bottom_level(const Ctx& c) {
+  if (!c.bottom_ok) return c.nl;
+  int lb = c.nl - 1;
+  while (lb - 1 >= 1 && c.L[lb - 1].n <= kBottomNodes) --lb;
+  return lb;
+}
+
+template <typename Real, int DIM>
+static void launch_bottom(Ctx& c, int lb) {
+  LevelBuf<Real>* h = levels<Real>(c);
+  BottomArgs<Real> a{};
+  for (int l = lb; l < c.nl; ++l) {
+    a.op[l] = stencil_row<Real, DIM>(c, l).op;
+    a.L[l] = c.L[l];
+    a.b[l] = h[l].b;
+    a.x[l] = h[l].x;
+    a.t[l] = h[l].t;
+    a.r[l] = h[l].r;
+  }
+  a.cinv = c.cinv;
+  a.nc = c.nc;
+  a.lb = lb;
+  a.nl = c.nl;
+  a.omega = (Real)c.p.omega;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kBottomCluster);
+  cfg.blockDim = dim3(kBottomThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = c.stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kBottomCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  MGAR_CUDA(cudaLaunchKernelEx(&cfg, k_bottom<Real, DIM>, a));
+  MGAR_LAUNCH_CHECK_AT("vc bottom");
+}
+
+template <typename Real, int DIM>
+static bool bottom_fits() {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kBottomCluster);
+  cfg.blockDim = dim3(kBottomThreads);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = kBottomCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int clusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&clusters, k_bottom<Real, DIM>, &cfg) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return clusters >= 1;
+}
+
+// Whether the cluster kernel can run here (both precisions); call outside
+// stream capture.
+void bottom_prepare(Ctx& c) {
+  c.bottom_ok = c.dim == 2 ? (bottom_fits<float, 2>() && bottom_fits<double, 2>())
+                           : (bottom_fits<float, 3>() && bottom_fits<double, 3>());
+}
+
 // Table 1 with one pre- and one post-sweep and a zero guess below the finest
 // level: per level one fused pre kernel (smooth from zero + residual), the
-// restriction, and one fused post kernel (interpolation + smooth).
+// restriction, and one fused post kernel (interpolation + smooth); the small
+// levels at the bottom run in one cluster launch.
 template <typename Real, int DIM>
 static void vcycle_fused(Ctx& c, const Real* b0, Real* x0, bool zero_guess) {
   LevelBuf<Real>* h = levels<Real>(c);
@@ -426,8 +583,9 @@ static void vcycle_fused(Ctx& c, const Real* b0, Real* x0, bool zero_guess) {
   k_restrict<Real, DIM><<<blocks_for(c.L[1].n), kThreads, 0, c.stream>>>(h[0].r, h[1].b, d0, c.L[1],
                                                                           c.fixed);
   MGAR_LAUNCH_CHECK_AT(level_site(3, 0));
+  const int lb = bottom_level(c);
   // coarse levels, down
-  for (int l = 1; l + 1 < nl; ++l) {
+  for (int l = 1; l + 1 < nl && l < lb; ++l) {
     const Dims& d = c.L[l];
     k_pre_coarse<Real, DIM><<<blocks_for(d.n), kThreads, 0, c.stream>>>(
         stencil_row<Real, DIM>(c, l).op, h[l].b, h[l].dinv, om, h[l].x, h[l].r);
@@ -436,8 +594,13 @@ static void vcycle_fused(Ctx& c, const Real* b0, Real* x0, bool zero_guess) {
                                                                                 c.L[l + 1], nullptr);
     MGAR_LAUNCH_CHECK_AT(level_site(3, l));
   }
-  // coarsest level
-  {
+  if (lb < nl) {
+    // levels lb .. nl-1 in one cluster launch
+    launch_bottom<Real, DIM>(c, lb);
+    res[nl - 1] = h[nl - 1].x;
+    for (int l = lb; l + 1 < nl; ++l) res[l] = h[l].t;
+  } else {
+    // coarsest level
     const int l = nl - 1;
     const int rows_per_block = kThreads / 32;
     k_coarse_solve<Real><<<(c.nc + rows_per_block - 1) / rows_per_block, kThreads, 0, c.stream>>>(
@@ -446,7 +609,7 @@ static void vcycle_fused(Ctx& c, const Real* b0, Real* x0, bool zero_guess) {
     res[l] = h[l].x;
   }
   // coarse levels, up
-  for (int l = nl - 2; l >= 1; --l) {
+  for (int l = std::min(nl - 2, lb - 1); l >= 1; --l) {
     const Dims& d = c.L[l];
     k_post_coarse<Real, DIM><<<blocks_for(d.n), kThreads, 0, c.stream>>>(
         stencil_row<Real, DIM>(c, l).op, res[l + 1], h[l].x, h[l].b, h[l].dinv, om, h[l].t, d,
