@@ -273,10 +273,13 @@ static void precondition_df(Ctx& c) {
   });
 }
 
-// z32 = M r32 (the FP32 copy of r is written by the residual and update kernels)
-static void precondition_f32(Ctx& c) {
+// z32 = M r32 (the FP32 copy of r is written by the residual and update
+// kernels) and r . z into dsc[slot], fused into the V-cycle's last kernel
+static void precondition_f32(Ctx& c, int slot) {
   const bool prof_inside = c.prof_class == MGAR_KC_SMOOTH0 || c.prof_class == MGAR_KC_RESID0;
-  run_graph(c, 7, c.b32, c.x32, prof_inside, [&] { vcycle<float>(c, c.b32, c.x32, true); });
+  double* out = c.dsc + slot;
+  run_graph(c, slot == S_RZ0 ? 8 : 9, c.b32, c.x32, prof_inside,
+            [&] { vcycle_dot(c, c.b32, c.x32, c.df_r, out); });
 }
 
 // 3D: the tiled kernels fuse the direction update into the product
@@ -296,10 +299,8 @@ static int solve_mgcg_df3(Ctx& c, double* T, int* iters, double* relres) {
   int it = 0;
   if (!(rel <= c.p.eps2)) {
     require(std::isfinite(rel), MGAR_ERR_NONFINITE, "non-finite initial residual");
-    precondition_f32(c);
     int a = S_RZ0, b = S_RZ1;
-    k_df_dot_f<<<rb, kThreads, 0, c.stream>>>(c.df_r, c.x32, n, c.partials, c.counter, c.dsc + a);
-    MGAR_LAUNCH_CHECK();
+    precondition_f32(c, a);
     float2* pcur = c.df_p;
     float2* pnext = c.df_p2;
     bool first = true;
@@ -319,10 +320,8 @@ static int solve_mgcg_df3(Ctx& c, double* T, int* iters, double* relres) {
       rel = std::sqrt(c.hsc[S_RR]) / c.qnorm;
       require(std::isfinite(rel), MGAR_ERR_NONFINITE, "CG breakdown (non-finite residual)");
       if (rel <= c.p.eps2) break;
-      precondition_f32(c);
       std::swap(a, b);
-      k_df_dot_f<<<rb, kThreads, 0, c.stream>>>(c.df_r, c.x32, n, c.partials, c.counter, c.dsc + a);
-      MGAR_LAUNCH_CHECK();
+      precondition_f32(c, a);
     }
   }
   k_df_to_d<<<blocks_for(n), kThreads, 0, c.stream>>>(c.df_x, T, n);

@@ -592,7 +592,11 @@ void vcycle(Ctx& c, const Real* b, Real* x, bool zero_guess);
 // fine3d.cu: tiled finest-level 3D passes (mode 0 pre, 1 post, 2 residual, 3 sweep)
 template <typename Real>
 void fine3d(Ctx& c, int mode, const Real* ke, const Real* b, const Real* dinv, const Real* x,
-            const Real* xc, Real* out0, Real* out1);
+            const Real* xc, Real* out0, Real* out1, const float2* rdot = nullptr,
+            double* dout = nullptr);
+// zero-guess FP32 V-cycle x = M b that also leaves r . x in *dout (r in
+// double-float pairs; 3D tiled path)
+void vcycle_dot(Ctx& c, const float* b, float* x, const float2* r, double* dout);
 // launch shapes of the tiled kernels (occupancy query; call outside stream capture)
 void fine3d_prepare(Ctx& c);
 // vcycle.cu: can the bottom levels run as one thread-block cluster launch
@@ -688,7 +692,8 @@ void run_graph(Ctx& c, int kind, const void* a, const void* b, bool profiled_ins
   count_launches(hit->kernels);
   static const char* kGraphSites[] = {"graph:0", "graph:1 precondition", "graph:2 mgar-vcycle64-zero",
                                       "graph:3 mgar-vcycle64-guess", "graph:4 mgar-vcycle32-zero",
-                                      "graph:5 mgar-vcycle32-guess", "graph:6", "graph:7"};
-  prof_mark(kGraphSites[kind & 7]);
+                                      "graph:5 mgar-vcycle32-guess", "graph:6 precondition-df",
+                                      "graph:7", "graph:8 precondition-rz", "graph:9 precondition-rz"};
+  prof_mark(kGraphSites[kind >= 0 && kind < 10 ? kind : 0]);
 }
 }  // namespace mgar

@@ -48,20 +48,16 @@ struct DfArgs {
   double* out;          // dot product (may be null for APPLY)
 };
 
-__device__ __forceinline__ df ld2(const float2* a, int i) {
-  const float2 v = a[i];
-  return df{v.x, v.y};
-}
-
 template <int MODE>
 struct NodeFetch {
   float2 v = make_float2(0.f, 0.f);  // x, or p_old
   float zf = 0.f;                    // DIR: z
   uint8_t f = 1;
   bool on = false;
-  __device__ __forceinline__ void issue(const DfArgs& a, int i, int j, int k) {
-    on = i >= 0 && i < a.NX && j >= 0 && j < a.NY && k >= 0 && k < a.NZ;
-    const int idx = min(max(i, 0), a.NX - 1) + a.NX * (min(max(j, 0), a.NY - 1) + a.NY * min(max(k, 0), a.NZ - 1));
+  // col: clamped i + NX * clamped j; con: (i, j) inside the grid
+  __device__ __forceinline__ void issue(const DfArgs& a, int col, bool con, int k) {
+    on = con && k >= 0 && k < a.NZ;
+    const int idx = col + a.NX * a.NY * min(max(k, 0), a.NZ - 1);
     if (!CK(idx, (int64_t)a.NX * a.NY * a.NZ)) return;
     f = a.fixed[idx];
     if (MODE == DIR) {
@@ -92,12 +88,15 @@ __device__ __forceinline__ void acc_term(float& ah, float& al, df w, float2 xi, 
   al = __fadd_rn(al, __fadd_rn(te, pe));
 }
 
+__device__ __forceinline__ df dfk(float2 v) { return df{v.x, v.y}; }
+
+// Plane p and element layer p live in slot (p - kb + 1) & 3; the z loop is
+// unrolled by four, so every slot index is a compile-time constant and the
+// centre values of the planes in flight stay in registers.
 template <int MODE>
 __global__ void __launch_bounds__(NT, 4) k_df3d(DfArgs a) {
-  __shared__ float2 X[XS][TY + 2][TX + 2];
-  __shared__ float2 K[KS][TY + 1][TX + 1];
-  __shared__ float2 Cx[XS][TY][TX];  // centre operand, unmasked
-  __shared__ uint8_t Cf[XS][TY][TX];
+  __shared__ float2 X[4][TY + 2][TX + 2];
+  __shared__ float2 K[4][TY + 1][TX + 1];
 
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
@@ -111,119 +110,143 @@ __global__ void __launch_bounds__(NT, 4) k_df3d(DfArgs a) {
   if (kr) kring(tid - KRING0, kxh, kyh);
   df beta{0.f, 0.f};
   if (MODE == DIR && !a.first) beta = df_from_double(*a.rz_new / *a.rz_old);
+  const int NXY = a.NX * a.NY;
+
+  // per-thread column offsets (plane-independent)
+  const int ocol = min(i, a.NX - 1) + a.NX * min(j, a.NY - 1);
+  const int ri = i0 - 1 + rxh, rj = j0 - 1 + ryh;
+  const bool ron = ri >= 0 && ri < a.NX && rj >= 0 && rj < a.NY;
+  const int rcol = min(max(ri, 0), a.NX - 1) + a.NX * min(max(rj, 0), a.NY - 1);
+  const bool keon = i < a.ex && j < a.ey;
+  const int kebase = min(i, a.ex - 1) + a.ex * min(j, a.ey - 1);
+  const int ki = i0 - 1 + kxh, kj = j0 - 1 + kyh;
+  const bool kron = ki >= 0 && ki < a.ex && kj >= 0 && kj < a.ey;
+  const int krbase = min(max(ki, 0), a.ex - 1) + a.ex * min(max(kj, 0), a.ey - 1);
+  const int EXY = a.ex * a.ey;
 
   NodeFetch<MODE> own, ring;
   float2 kown = make_float2(0.f, 0.f), kring_v = make_float2(0.f, 0.f);
   bool kown_on = false, kring_on = false;
+  float2 ownq = make_float2(0.f, 0.f);
+  float2 cv[4], cq[4];
+  bool cf[4];
   df dot{0.f, 0.f};
 
   auto issue_plane = [&](int p) {
-    own.issue(a, i, j, p);
-    if (xr) ring.issue(a, i0 - 1 + rxh, j0 - 1 + ryh, p);
-  };
-  auto finish_plane = [&](int p) {
-    const int s = (p + XS) % XS;
-    const df v = own.value(beta);
-    const float2 v2 = make_float2(v.hi, v.lo);
-    X[s][ty + 1][tx + 1] = (own.on && !own.f) ? v2 : make_float2(0.f, 0.f);
-    Cx[s][ty][tx] = v2;
-    Cf[s][ty][tx] = own.f;
-    if (MODE == DIR && mine && p >= kb && p < kend) {
-      const int idx = i + a.NX * (j + a.NY * p);
-      a.p[idx] = v2;
+    own.issue(a, ocol, mine, p);
+    if (MODE == RESID) {
+      const int idx = ocol + NXY * min(max(p, 0), a.NZ - 1);
+      if (CK(idx, (int64_t)NXY * a.NZ)) ownq = a.q[idx];
     }
-    if (xr) {
-      const df w = ring.value(beta);
-      X[s][ryh][rxh] = (ring.on && !ring.f) ? make_float2(w.hi, w.lo) : make_float2(0.f, 0.f);
-    }
-  };
-  auto issue_elem = [&](int e, int f, int l, float2& v, bool& on) {
-    on = e >= 0 && e < a.ex && f >= 0 && f < a.ey && l >= 0 && l < a.ez;
-    const int idx = min(max(e, 0), a.ex - 1) + a.ex * (min(max(f, 0), a.ey - 1) + a.ey * min(max(l, 0), a.ez - 1));
-    if (CK(idx, (int64_t)a.ex * a.ey * a.ez)) v = a.ke[idx];
+    if (xr) ring.issue(a, rcol, ron, p);
   };
   auto issue_layer = [&](int l) {
-    issue_elem(i, j, l, kown, kown_on);
-    if (kr) issue_elem(i0 - 1 + kxh, j0 - 1 + kyh, l, kring_v, kring_on);
-  };
-  auto finish_layer = [&](int l) {
-    const int s = (l + KS) % KS;
-    K[s][ty + 1][tx + 1] = kown_on ? kown : make_float2(0.f, 0.f);
-    if (kr) K[s][kyh][kxh] = kring_on ? kring_v : make_float2(0.f, 0.f);
+    const int lc = EXY * min(max(l, 0), a.ez - 1);
+    const bool lon = l >= 0 && l < a.ez;
+    kown_on = keon && lon;
+    if (CK(kebase + lc, (int64_t)EXY * a.ez)) kown = a.ke[kebase + lc];
+    if (kr) {
+      kring_on = kron && lon;
+      if (CK(krbase + lc, (int64_t)EXY * a.ez)) kring_v = a.ke[krbase + lc];
+    }
   };
 
+#define D3D_FINISH(S, P)                                                                   \
+  {                                                                                        \
+    const df v = own.value(beta);                                                          \
+    const float2 v2 = make_float2(v.hi, v.lo);                                             \
+    X[S][ty + 1][tx + 1] = (own.on && !own.f) ? v2 : make_float2(0.f, 0.f);                \
+    cv[S] = v2;                                                                            \
+    cf[S] = own.f != 0;                                                                    \
+    cq[S] = ownq;                                                                          \
+    if (MODE == DIR && mine && (P) >= kb && (P) < kend) a.p[ocol + NXY * (P)] = v2;        \
+    if (xr) {                                                                              \
+      const df w = ring.value(beta);                                                       \
+      X[S][ryh][rxh] = (ring.on && !ring.f) ? make_float2(w.hi, w.lo) : make_float2(0.f, 0.f); \
+    }                                                                                      \
+  }
+#define D3D_FINISH_LAYER(S)                                                                \
+  {                                                                                        \
+    K[S][ty + 1][tx + 1] = kown_on ? kown : make_float2(0.f, 0.f);                         \
+    if (kr) K[S][kyh][kxh] = kring_on ? kring_v : make_float2(0.f, 0.f);                   \
+  }
+
   issue_plane(kb - 1);
-  finish_plane(kb - 1);
+  D3D_FINISH(0, kb - 1);
   issue_plane(kb);
   issue_layer(kb - 1);
-  finish_plane(kb);
-  finish_layer(kb - 1);
+  D3D_FINISH(1, kb);
+  D3D_FINISH_LAYER(0);
   issue_plane(kb + 1);
   issue_layer(kb);
 
   const df scale = df_from_double(1.0 / 12.0);
-  for (int k = kb; k < kend; ++k) {
-    finish_plane(k + 1);
-    finish_layer(k);
-    issue_plane(k + 2);
-    issue_layer(k + 1);
-    __syncthreads();
-    if (mine) {
-      const int idx = i + a.NX * (j + a.NY * k);
-      const auto& Xm = X[(k + XS - 1) % XS];
-      const auto& X0 = X[k % XS];
-      const auto& Xp = X[(k + 1) % XS];
-      const auto& Km = K[(k + KS - 1) % KS];
-      const auto& Kp = K[k % KS];
-      const int s = k % XS;
-      const float2 xi = Cx[s][ty][tx];
-      df yv;
-      if (Cf[s][ty][tx]) {
-        yv = df{xi.x, xi.y};
-      } else {
-        const int cx = tx + 1, cy = ty + 1;
-        const df k000 = df{Km[ty][tx].x, Km[ty][tx].y}, k001 = df{Km[ty][tx + 1].x, Km[ty][tx + 1].y},
-                 k010 = df{Km[ty + 1][tx].x, Km[ty + 1][tx].y},
-                 k011 = df{Km[ty + 1][tx + 1].x, Km[ty + 1][tx + 1].y};
-        const df k100 = df{Kp[ty][tx].x, Kp[ty][tx].y}, k101 = df{Kp[ty][tx + 1].x, Kp[ty][tx + 1].y},
-                 k110 = df{Kp[ty + 1][tx].x, Kp[ty + 1][tx].y},
-                 k111 = df{Kp[ty + 1][tx + 1].x, Kp[ty + 1][tx + 1].y};
-        float ah = 0.f, al = 0.f;
-        // face diagonals (two elements each)
-        acc_term(ah, al, df_add(k000, k100), xi, X0[cy - 1][cx - 1]);
-        acc_term(ah, al, df_add(k001, k101), xi, X0[cy - 1][cx + 1]);
-        acc_term(ah, al, df_add(k010, k110), xi, X0[cy + 1][cx - 1]);
-        acc_term(ah, al, df_add(k011, k111), xi, X0[cy + 1][cx + 1]);
-        acc_term(ah, al, df_add(k000, k010), xi, Xm[cy][cx - 1]);
-        acc_term(ah, al, df_add(k001, k011), xi, Xm[cy][cx + 1]);
-        acc_term(ah, al, df_add(k100, k110), xi, Xp[cy][cx - 1]);
-        acc_term(ah, al, df_add(k101, k111), xi, Xp[cy][cx + 1]);
-        acc_term(ah, al, df_add(k000, k001), xi, Xm[cy - 1][cx]);
-        acc_term(ah, al, df_add(k010, k011), xi, Xm[cy + 1][cx]);
-        acc_term(ah, al, df_add(k100, k101), xi, Xp[cy - 1][cx]);
-        acc_term(ah, al, df_add(k110, k111), xi, Xp[cy + 1][cx]);
-        // body diagonals
-        acc_term(ah, al, k000, xi, Xm[cy - 1][cx - 1]);
-        acc_term(ah, al, k001, xi, Xm[cy - 1][cx + 1]);
-        acc_term(ah, al, k010, xi, Xm[cy + 1][cx - 1]);
-        acc_term(ah, al, k011, xi, Xm[cy + 1][cx + 1]);
-        acc_term(ah, al, k100, xi, Xp[cy - 1][cx - 1]);
-        acc_term(ah, al, k101, xi, Xp[cy - 1][cx + 1]);
-        acc_term(ah, al, k110, xi, Xp[cy + 1][cx - 1]);
-        acc_term(ah, al, k111, xi, Xp[cy + 1][cx + 1]);
-        yv = df_mul(df_make(ah, al), scale);
-      }
-      if (MODE == RESID) {
-        const df ri = df_sub(ld2(a.q, idx), yv);
-        a.y[idx] = make_float2(ri.hi, ri.lo);
-        a.r32[idx] = __fadd_rn(ri.hi, ri.lo);
-        dot = df_add(dot, df_mul(ri, ri));
-      } else {
-        a.y[idx] = make_float2(yv.hi, yv.lo);
-        dot = df_add(dot, df_mul(df{xi.x, xi.y}, yv));
-      }
-    }
+#define D3D_STEP(S)                                                                        \
+  {                                                                                        \
+    constexpr int S0 = (S) & 3, S1 = ((S) + 1) & 3, S2 = ((S) + 2) & 3;                    \
+    const int k = kk + (S);                                                                \
+    if (k >= kend) break;                                                                  \
+    D3D_FINISH(S2, k + 1);                                                                 \
+    D3D_FINISH_LAYER(S1);                                                                  \
+    issue_plane(k + 2);                                                                    \
+    issue_layer(k + 1);                                                                    \
+    __syncthreads();                                                                       \
+    if (mine) {                                                                            \
+      const int idx = ocol + NXY * k;                                                      \
+      const float2 xi = cv[S1];                                                            \
+      df yv;                                                                               \
+      if (cf[S1]) {                                                                        \
+        yv = dfk(xi);                                                                      \
+      } else {                                                                             \
+        const int cx = tx + 1, cy = ty + 1;                                                \
+        const df k000 = dfk(K[S0][ty][tx]), k001 = dfk(K[S0][ty][tx + 1]),                 \
+                 k010 = dfk(K[S0][ty + 1][tx]), k011 = dfk(K[S0][ty + 1][tx + 1]);         \
+        const df k100 = dfk(K[S1][ty][tx]), k101 = dfk(K[S1][ty][tx + 1]),                 \
+                 k110 = dfk(K[S1][ty + 1][tx]), k111 = dfk(K[S1][ty + 1][tx + 1]);         \
+        float ah = 0.f, al = 0.f;                                                          \
+        acc_term(ah, al, df_add(k000, k100), xi, X[S1][cy - 1][cx - 1]);                   \
+        acc_term(ah, al, df_add(k001, k101), xi, X[S1][cy - 1][cx + 1]);                   \
+        acc_term(ah, al, df_add(k010, k110), xi, X[S1][cy + 1][cx - 1]);                   \
+        acc_term(ah, al, df_add(k011, k111), xi, X[S1][cy + 1][cx + 1]);                   \
+        acc_term(ah, al, df_add(k000, k010), xi, X[S0][cy][cx - 1]);                       \
+        acc_term(ah, al, df_add(k001, k011), xi, X[S0][cy][cx + 1]);                       \
+        acc_term(ah, al, df_add(k100, k110), xi, X[S2][cy][cx - 1]);                       \
+        acc_term(ah, al, df_add(k101, k111), xi, X[S2][cy][cx + 1]);                       \
+        acc_term(ah, al, df_add(k000, k001), xi, X[S0][cy - 1][cx]);                       \
+        acc_term(ah, al, df_add(k010, k011), xi, X[S0][cy + 1][cx]);                       \
+        acc_term(ah, al, df_add(k100, k101), xi, X[S2][cy - 1][cx]);                       \
+        acc_term(ah, al, df_add(k110, k111), xi, X[S2][cy + 1][cx]);                       \
+        acc_term(ah, al, k000, xi, X[S0][cy - 1][cx - 1]);                                 \
+        acc_term(ah, al, k001, xi, X[S0][cy - 1][cx + 1]);                                 \
+        acc_term(ah, al, k010, xi, X[S0][cy + 1][cx - 1]);                                 \
+        acc_term(ah, al, k011, xi, X[S0][cy + 1][cx + 1]);                                 \
+        acc_term(ah, al, k100, xi, X[S2][cy - 1][cx - 1]);                                 \
+        acc_term(ah, al, k101, xi, X[S2][cy - 1][cx + 1]);                                 \
+        acc_term(ah, al, k110, xi, X[S2][cy + 1][cx - 1]);                                 \
+        acc_term(ah, al, k111, xi, X[S2][cy + 1][cx + 1]);                                 \
+        yv = df_mul(df_make(ah, al), scale);                                               \
+      }                                                                                    \
+      if (MODE == RESID) {                                                                 \
+        const df ri = df_sub(dfk(cq[S1]), yv);                                             \
+        a.y[idx] = make_float2(ri.hi, ri.lo);                                              \
+        a.r32[idx] = __fadd_rn(ri.hi, ri.lo);                                              \
+        dot = df_add(dot, df_mul(ri, ri));                                                 \
+      } else {                                                                             \
+        a.y[idx] = make_float2(yv.hi, yv.lo);                                              \
+        dot = df_add(dot, df_mul(dfk(xi), yv));                                            \
+      }                                                                                    \
+    }                                                                                      \
   }
+
+  for (int kk = kb; kk < kend; kk += 4) {
+    D3D_STEP(0)
+    D3D_STEP(1)
+    D3D_STEP(2)
+    D3D_STEP(3)
+  }
+#undef D3D_STEP
+#undef D3D_FINISH
+#undef D3D_FINISH_LAYER
   if (a.out) {
     double v[1] = {df_to_double(dot)};
     double t[1];

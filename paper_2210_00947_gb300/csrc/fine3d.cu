@@ -23,6 +23,7 @@
 // evenly into as many runs as fill the GPU once.
 #include "common.cuh"
 #include "tile3d.cuh"
+#include "df64.cuh"
 
 namespace mgar {
 namespace f3d {
@@ -43,6 +44,11 @@ struct FineArgs {
   void* out0;       // PRE: x, RESID: r, SWEEP/POST: x'
   void* out1;       // PRE: r
   double omega;
+  // POST, optional: r . x' with r in double-float pairs (the CG's r . z)
+  const float2* rdot;
+  double* partials;
+  unsigned int* counter;
+  double* dout;
 };
 
 // 1D interpolation taps onto fine node i (nf fine elements): coarse index of
@@ -52,20 +58,47 @@ __device__ __forceinline__ int ptap0(int i, int nf, bool& half) {
   return (i & 1) ? (half ? (i - 1) >> 1 : (i + 1) >> 1) : i >> 1;
 }
 
+// A node column (i, j): everything about its loads that does not depend on
+// the plane, computed once per thread.
+struct Column {
+  int base;      // clamped i + NX * clamped j
+  bool on;       // (i, j) inside the grid
+  int cxy[4];    // POST: coarse offsets of (x0|x1) + cNX * (y0|y1)
+  uint8_t hxy;   // POST: half flags of x (bit 0) and y (bit 1)
+};
+
+__device__ __forceinline__ Column make_column(const FineArgs& a, int i, int j, bool post) {
+  Column c;
+  c.on = i >= 0 && i < a.NX && j >= 0 && j < a.NY;
+  const int ic = min(max(i, 0), a.NX - 1), jc = min(max(j, 0), a.NY - 1);
+  c.base = ic + a.NX * jc;
+  c.hxy = 0;
+  c.cxy[0] = c.cxy[1] = c.cxy[2] = c.cxy[3] = 0;
+  if (post) {
+    bool hx, hy;
+    const int x0 = ptap0(ic, a.ex, hx), y0 = ptap0(jc, a.ey, hy);
+    c.hxy = (uint8_t)(hx | (hy << 1));
+    c.cxy[0] = x0 + a.cNX * y0;
+    c.cxy[1] = x0 + hx + a.cNX * y0;
+    c.cxy[2] = x0 + a.cNX * (y0 + hy);
+    c.cxy[3] = x0 + hx + a.cNX * (y0 + hy);
+  }
+  return c;
+}
+
 // Raw loads of one node of a plane, issued one step before use.
 template <typename Real, int MODE>
 struct NodeFetch {
   Real v0 = Real(0), v1 = Real(0);  // PRE: b, dinv; else x (v1 unused)
   Real c[8];                        // POST: coarse values
   uint8_t f = 1;                    // fixed (or off the grid: treated as zero)
-  uint8_t hm = 0;                   // POST: half flags (x, y, z)
+  uint8_t hz = 0;                   // POST: half flag of z
   bool on = false;
 
-  __device__ __forceinline__ void issue(const FineArgs& a, int i, int j, int k) {
-    on = i >= 0 && i < a.NX && j >= 0 && j < a.NY && k >= 0 && k < a.NZ;
-    const int ic = min(max(i, 0), a.NX - 1), jc = min(max(j, 0), a.NY - 1),
-              kc = min(max(k, 0), a.NZ - 1);
-    const int idx = ic + a.NX * (jc + a.NY * kc);
+  __device__ __forceinline__ void issue(const FineArgs& a, const Column& col, int k) {
+    on = col.on && k >= 0 && k < a.NZ;
+    const int kc = min(max(k, 0), a.NZ - 1);
+    const int idx = col.base + a.NX * a.NY * kc;
     if (!CK(idx, (int64_t)a.NX * a.NY * a.NZ)) return;
     f = a.fixed[idx];
     if (MODE == PRE) {
@@ -75,36 +108,32 @@ struct NodeFetch {
       v0 = ((const Real*)a.x)[idx];
     }
     if (MODE == POST) {
-      bool hx, hy, hz;
-      const int x0 = ptap0(ic, a.ex, hx), y0 = ptap0(jc, a.ey, hy), z0 = ptap0(kc, a.ez, hz);
-      hm = (uint8_t)(hx | (hy << 1) | (hz << 2));
-      const int x1 = x0 + hx, y1 = y0 + hy, z1 = z0 + hz;
+      bool h;
+      const int z0 = ptap0(kc, a.ez, h);
+      hz = h;
       const int P = a.cNX * a.cNY;
       const Real* xc = (const Real*)a.xc;
-      const int zz[2] = {z0 * P, z1 * P}, yy[2] = {y0 * a.cNX, y1 * a.cNX};
+      const int z0o = z0 * P, z1o = (z0 + h) * P;
 #pragma unroll
-      for (int cz = 0; cz < 2; ++cz)
-#pragma unroll
-        for (int cy = 0; cy < 2; ++cy) {
-          const int base = zz[cz] + yy[cy];
-          if (CK(base + x1, (int64_t)P * a.cNZ)) {
-            c[4 * cz + 2 * cy] = xc[base + x0];
-            c[4 * cz + 2 * cy + 1] = xc[base + x1];
-          }
+      for (int q = 0; q < 4; ++q) {
+        if (CK(col.cxy[q] + z1o, (int64_t)P * a.cNZ)) {
+          c[q] = xc[col.cxy[q] + z0o];
+          c[4 + q] = xc[col.cxy[q] + z1o];
         }
+      }
     }
   }
 
   // operand value before masking (PRE: w D^-1 b; POST: x + P x_c, fixed
   // nodes keep x; else x)
-  __device__ __forceinline__ Real value(Real omega) const {
+  __device__ __forceinline__ Real value(Real omega, uint8_t hxy) const {
     if (MODE == PRE) return omega * v1 * v0;
     if (MODE == POST) {
       if (f) return v0;
-      const Real wx = (hm & 1) ? Real(0.5) : Real(1), wy = (hm & 2) ? Real(0.5) : Real(1),
-                 wz = (hm & 4) ? Real(0.5) : Real(1);
-      const Real ux = (hm & 1) ? Real(0.5) : Real(0), uy = (hm & 2) ? Real(0.5) : Real(0),
-                 uz = (hm & 4) ? Real(0.5) : Real(0);
+      const Real wx = (hxy & 1) ? Real(0.5) : Real(1), ux = (hxy & 1) ? Real(0.5) : Real(0);
+      const Real wy = (hxy & 2) ? Real(0.5) : Real(1), uy = (hxy & 2) ? Real(0.5) : Real(0);
+      const Real wz = hz ? Real(0.5) : Real(1), uz = hz ? Real(0.5) : Real(0);
+      // c[q + 4 cz] with q = x-tap + 2 y-tap
       const Real r00 = wx * c[0] + ux * c[1], r01 = wx * c[2] + ux * c[3];
       const Real r10 = wx * c[4] + ux * c[5], r11 = wx * c[6] + ux * c[7];
       const Real s0 = wy * r00 + uy * r01, s1 = wy * r10 + uy * r11;
@@ -112,8 +141,8 @@ struct NodeFetch {
     }
     return v0;
   }
-  __device__ __forceinline__ Real masked(Real omega) const {
-    return (on && !f) ? value(omega) : Real(0);
+  __device__ __forceinline__ Real masked(Real omega, uint8_t hxy) const {
+    return (on && !f) ? value(omega, hxy) : Real(0);
   }
 };
 
@@ -121,22 +150,21 @@ template <typename Real>
 struct ElemFetch {
   Real v = Real(0);
   bool on = false;
-  __device__ __forceinline__ void issue(const FineArgs& a, int e, int f, int l) {
-    on = e >= 0 && e < a.ex && f >= 0 && f < a.ey && l >= 0 && l < a.ez;
-    const int idx = min(max(e, 0), a.ex - 1) + a.ex * (min(max(f, 0), a.ey - 1) + a.ey * min(max(l, 0), a.ez - 1));
+  __device__ __forceinline__ void issue(const FineArgs& a, int ebase, bool eon, int l) {
+    on = eon && l >= 0 && l < a.ez;
+    const int idx = ebase + a.ex * a.ey * min(max(l, 0), a.ez - 1);
     if (CK(idx, (int64_t)a.ex * a.ey * a.ez)) v = ((const Real*)a.ke)[idx];
   }
   __device__ __forceinline__ Real get() const { return on ? v : Real(0); }
 };
 
+// Plane slots are relative to the block's first plane: plane p lives in slot
+// (p - kb + 1) & 3, and so does element layer p.  The z loop is unrolled by
+// four, so every slot index is a compile-time constant.
 template <typename Real, int MODE>
-__global__ void __launch_bounds__(NT, sizeof(Real) == 4 ? 4 : 2) k_fine3d(FineArgs a) {
+__global__ void __launch_bounds__(NT, sizeof(Real) == 4 ? (MODE == POST ? 3 : 4) : 2) k_fine3d(FineArgs a) {
   __shared__ Real X[XS][TY + 2][TX + 2];
-  __shared__ Real K[KS][TY + 1][TX + 1];
-  __shared__ Real Cx[XS][TY][TX];  // centre operand value, unmasked
-  __shared__ Real Cb[XS][TY][TX];  // centre right-hand side
-  __shared__ Real Cd[(MODE == POST || MODE == SWEEP) ? XS : 1][TY][TX];  // centre D^-1
-  __shared__ uint8_t Cf[XS][TY][TX];                                       // centre fixed flag
+  __shared__ Real K[4][TY + 1][TX + 1];
 
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
@@ -148,110 +176,143 @@ __global__ void __launch_bounds__(NT, sizeof(Real) == 4 ? 4 : 2) k_fine3d(FineAr
   int rxh = 0, ryh = 0, kxh = 0, kyh = 0;
   if (xr) xring(tid, rxh, ryh);
   if (kr) kring(tid - KRING0, kxh, kyh);
+  const bool mine = i < a.NX && j < a.NY;
+  const int NXY = a.NX * a.NY;
+
+  const Column ocol = make_column(a, i, j, MODE == POST);
+  const Column rcol = make_column(a, i0 - 1 + rxh, j0 - 1 + ryh, MODE == POST);
+  const int ke_i = i, ke_j = j, kr_i = i0 - 1 + kxh, kr_j = j0 - 1 + kyh;
+  const bool keon = ke_i < a.ex && ke_j < a.ey;
+  const bool kron = kr_i >= 0 && kr_i < a.ex && kr_j >= 0 && kr_j < a.ey;
+  const int kebase = min(ke_i, a.ex - 1) + a.ex * min(ke_j, a.ey - 1);
+  const int krbase = min(max(kr_i, 0), a.ex - 1) + a.ex * min(max(kr_j, 0), a.ey - 1);
 
   NodeFetch<Real, MODE> own, ring;
   ElemFetch<Real> kown, kring_;
   Real ownb = Real(0), ownd = Real(0);
+  // centre values per slot: unmasked operand, b, D^-1, fixed flag (and r
+  // for the fused r . x')
+  Real cv[4], cb[4], cd[4];
+  bool cf[4];
+  const bool rdot = MODE == POST && a.dout != nullptr;
+  df dacc{0.f, 0.f};
 
   auto issue_plane = [&](int p) {
-    own.issue(a, i, j, p);
+    own.issue(a, ocol, p);
     if (MODE != PRE) {
-      // centre data beyond the operand
-      const int idx = min(i, a.NX - 1) + a.NX * (min(j, a.NY - 1) + a.NY * min(max(p, 0), a.NZ - 1));
-      if (CK(idx, (int64_t)a.NX * a.NY * a.NZ)) {
+      const int idx = ocol.base + NXY * min(max(p, 0), a.NZ - 1);
+      if (CK(idx, (int64_t)NXY * a.NZ)) {
         ownb = ((const Real*)a.b)[idx];
         if (MODE == POST || MODE == SWEEP) ownd = ((const Real*)a.dinv)[idx];
       }
     }
-    if (xr) ring.issue(a, i0 - 1 + rxh, j0 - 1 + ryh, p);
-  };
-  auto finish_plane = [&](int p) {
-    const int s = (p + XS) % XS;
-    X[s][ty + 1][tx + 1] = own.masked(om);
-    const Real v = own.value(om);
-    Cx[s][ty][tx] = v;
-    Cb[s][ty][tx] = MODE == PRE ? own.v0 : ownb;
-    if (MODE == POST || MODE == SWEEP) Cd[s][ty][tx] = ownd;
-    Cf[s][ty][tx] = own.f;
-    if (xr) X[s][ryh][rxh] = ring.masked(om);
+    if (xr) ring.issue(a, rcol, p);
   };
   auto issue_layer = [&](int l) {
-    kown.issue(a, i, j, l);
-    if (kr) kring_.issue(a, i0 - 1 + kxh, j0 - 1 + kyh, l);
-  };
-  auto finish_layer = [&](int l) {
-    const int s = (l + KS) % KS;
-    K[s][ty + 1][tx + 1] = kown.get();
-    if (kr) K[s][kyh][kxh] = kring_.get();
+    kown.issue(a, kebase, keon, l);
+    if (kr) kring_.issue(a, krbase, kron, l);
   };
 
-  // prologue: planes kb-1, kb and layer kb-1 in place; plane kb+1 and layer
-  // kb in flight
+#define F3D_FINISH(S)                                                  \
+  {                                                                    \
+    X[S][ty + 1][tx + 1] = own.masked(om, ocol.hxy);                   \
+    cv[S] = own.value(om, ocol.hxy);                                   \
+    cb[S] = MODE == PRE ? own.v0 : ownb;                               \
+    cd[S] = ownd;                                                      \
+    cf[S] = own.f != 0;                                                \
+    if (xr) X[S][ryh][rxh] = ring.masked(om, rcol.hxy);                \
+  }
+#define F3D_FINISH_LAYER(S)                                            \
+  {                                                                    \
+    K[S][ty + 1][tx + 1] = kown.get();                                 \
+    if (kr) K[S][kyh][kxh] = kring_.get();                             \
+  }
+
+  // prologue: planes kb-1 (slot 0), kb (slot 1) and layer kb-1 (slot 0) in
+  // place; plane kb+1 and layer kb in flight
   issue_plane(kb - 1);
-  finish_plane(kb - 1);
+  F3D_FINISH(0);
   issue_plane(kb);
   issue_layer(kb - 1);
-  finish_plane(kb);
-  finish_layer(kb - 1);
+  F3D_FINISH(1);
+  F3D_FINISH_LAYER(0);
   issue_plane(kb + 1);
   issue_layer(kb);
 
-  const bool mine = i < a.NX && j < a.NY;
-  for (int k = kb; k < kend; ++k) {
-    finish_plane(k + 1);
-    finish_layer(k);
-    issue_plane(k + 2);
-    issue_layer(k + 1);
-    __syncthreads();
-    if (mine) {
-      const int idx = i + a.NX * (j + a.NY * k);
-      const auto& Xm = X[(k + XS - 1) % XS];
-      const auto& X0 = X[k % XS];
-      const auto& Xp = X[(k + 1) % XS];
-      const auto& Km = K[(k + KS - 1) % KS];
-      const auto& Kp = K[k % KS];
-      const Real k000 = Km[ty][tx], k001 = Km[ty][tx + 1], k010 = Km[ty + 1][tx],
-                 k011 = Km[ty + 1][tx + 1];
-      const Real k100 = Kp[ty][tx], k101 = Kp[ty][tx + 1], k110 = Kp[ty + 1][tx],
-                 k111 = Kp[ty + 1][tx + 1];
-      const int cx = tx + 1, cy = ty + 1;
-      const Real ksum = ((k000 + k001) + (k010 + k011)) + ((k100 + k101) + (k110 + k111));
-      const Real xc = X0[cy][cx];
-      Real acc = Real(4) * ksum * xc;
-      acc -= (k000 + k100) * X0[cy - 1][cx - 1];
-      acc -= (k001 + k101) * X0[cy - 1][cx + 1];
-      acc -= (k010 + k110) * X0[cy + 1][cx - 1];
-      acc -= (k011 + k111) * X0[cy + 1][cx + 1];
-      acc -= (k000 + k010) * Xm[cy][cx - 1];
-      acc -= (k001 + k011) * Xm[cy][cx + 1];
-      acc -= (k100 + k110) * Xp[cy][cx - 1];
-      acc -= (k101 + k111) * Xp[cy][cx + 1];
-      acc -= (k000 + k001) * Xm[cy - 1][cx];
-      acc -= (k010 + k011) * Xm[cy + 1][cx];
-      acc -= (k100 + k101) * Xp[cy - 1][cx];
-      acc -= (k110 + k111) * Xp[cy + 1][cx];
-      acc -= k000 * Xm[cy - 1][cx - 1];
-      acc -= k001 * Xm[cy - 1][cx + 1];
-      acc -= k010 * Xm[cy + 1][cx - 1];
-      acc -= k011 * Xm[cy + 1][cx + 1];
-      acc -= k100 * Xp[cy - 1][cx - 1];
-      acc -= k101 * Xp[cy - 1][cx + 1];
-      acc -= k110 * Xp[cy + 1][cx - 1];
-      acc -= k111 * Xp[cy + 1][cx + 1];
-      const int s = k % XS;
-      const bool fx = Cf[s][ty][tx];
-      const Real xi = Cx[s][ty][tx];  // a fixed row is the identity
-      const Real ax = fx ? xi : acc * Real(1.0 / 12.0);
-      const Real bi = Cb[s][ty][tx];
-      if (MODE == PRE) {
-        ((Real*)a.out0)[idx] = xi;
-        ((Real*)a.out1)[idx] = bi - ax;
-      } else if (MODE == RESID) {
-        ((Real*)a.out0)[idx] = bi - ax;
-      } else {  // POST, SWEEP
-        ((Real*)a.out0)[idx] = xi + om * Cd[s][ty][tx] * (bi - ax);
-      }
-    }
+  // one step for plane k in slot S1 = (S + 1) & 3 (planes k-1, k, k+1 in
+  // slots S, S1, S2; layers k-1, k in slots S, S1)
+#define F3D_STEP(S)                                                                        \
+  {                                                                                        \
+    constexpr int S0 = (S) & 3, S1 = ((S) + 1) & 3, S2 = ((S) + 2) & 3;                    \
+    const int k = kk + (S);                                                                \
+    if (k >= kend) break;                                                                  \
+    F3D_FINISH(S2);                                                                        \
+    F3D_FINISH_LAYER(S1);                                                                  \
+    issue_plane(k + 2);                                                                    \
+    issue_layer(k + 1);                                                                    \
+    __syncthreads();                                                                       \
+    if (mine) {                                                                            \
+      const int idx = i + a.NX * (j + a.NY * k);                                           \
+      /* r for the fused r . x' (its load overlaps the stencil) */                         \
+      const float2 rv = rdot ? a.rdot[idx] : make_float2(0.f, 0.f);                       \
+      const Real k000 = K[S0][ty][tx], k001 = K[S0][ty][tx + 1], k010 = K[S0][ty + 1][tx], \
+                 k011 = K[S0][ty + 1][tx + 1];                                             \
+      const Real k100 = K[S1][ty][tx], k101 = K[S1][ty][tx + 1], k110 = K[S1][ty + 1][tx], \
+                 k111 = K[S1][ty + 1][tx + 1];                                             \
+      const int cx = tx + 1, cy = ty + 1;                                                  \
+      const Real ksum = ((k000 + k001) + (k010 + k011)) + ((k100 + k101) + (k110 + k111)); \
+      Real acc = Real(4) * ksum * X[S1][cy][cx];                                           \
+      acc -= (k000 + k100) * X[S1][cy - 1][cx - 1];                                        \
+      acc -= (k001 + k101) * X[S1][cy - 1][cx + 1];                                        \
+      acc -= (k010 + k110) * X[S1][cy + 1][cx - 1];                                        \
+      acc -= (k011 + k111) * X[S1][cy + 1][cx + 1];                                        \
+      acc -= (k000 + k010) * X[S0][cy][cx - 1];                                            \
+      acc -= (k001 + k011) * X[S0][cy][cx + 1];                                            \
+      acc -= (k100 + k110) * X[S2][cy][cx - 1];                                            \
+      acc -= (k101 + k111) * X[S2][cy][cx + 1];                                            \
+      acc -= (k000 + k001) * X[S0][cy - 1][cx];                                            \
+      acc -= (k010 + k011) * X[S0][cy + 1][cx];                                            \
+      acc -= (k100 + k101) * X[S2][cy - 1][cx];                                            \
+      acc -= (k110 + k111) * X[S2][cy + 1][cx];                                            \
+      acc -= k000 * X[S0][cy - 1][cx - 1];                                                 \
+      acc -= k001 * X[S0][cy - 1][cx + 1];                                                 \
+      acc -= k010 * X[S0][cy + 1][cx - 1];                                                 \
+      acc -= k011 * X[S0][cy + 1][cx + 1];                                                 \
+      acc -= k100 * X[S2][cy - 1][cx - 1];                                                 \
+      acc -= k101 * X[S2][cy - 1][cx + 1];                                                 \
+      acc -= k110 * X[S2][cy + 1][cx - 1];                                                 \
+      acc -= k111 * X[S2][cy + 1][cx + 1];                                                 \
+      const Real xi = cv[S1]; /* a fixed row is the identity */                            \
+      const Real ax = cf[S1] ? xi : acc * Real(1.0 / 12.0);                                \
+      const Real bi = cb[S1];                                                              \
+      if (MODE == PRE) {                                                                   \
+        ((Real*)a.out0)[idx] = xi;                                                         \
+        ((Real*)a.out1)[idx] = bi - ax;                                                    \
+      } else if (MODE == RESID) {                                                          \
+        ((Real*)a.out0)[idx] = bi - ax;                                                    \
+      } else {                                                                             \
+        const Real xo = xi + om * cd[S1] * (bi - ax);                                      \
+        ((Real*)a.out0)[idx] = xo;                                                         \
+        if (rdot) dacc = df_add(dacc, df_mulf(df{rv.x, rv.y}, (float)xo));                 \
+      }                                                                                    \
+    }                                                                                      \
+  }
+
+  for (int kk = kb; kk < kend; kk += 4) {
+    F3D_STEP(0)
+    F3D_STEP(1)
+    F3D_STEP(2)
+    F3D_STEP(3)
+  }
+#undef F3D_STEP
+#undef F3D_FINISH
+#undef F3D_FINISH_LAYER
+  if (rdot) {
+    double v[1] = {df_to_double(dacc)};
+    double t[1];
+    const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    const int nb = gridDim.x * gridDim.y * gridDim.z;
+    if (block_sum_last_ids<1>(v, a.partials, a.counter, t, tid, NT, bid, nb) && tid == 0) a.dout[0] = t[0];
   }
 }
 
@@ -290,7 +351,7 @@ void fine3d_prepare(Ctx& c) {
 // 2 residual, 3 sweep.
 template <typename Real>
 void fine3d(Ctx& c, int mode, const Real* ke, const Real* b, const Real* dinv, const Real* x,
-            const Real* xc, Real* out0, Real* out1) {
+            const Real* xc, Real* out0, Real* out1, const float2* rdot, double* dout) {
   using namespace f3d;
   const Dims& d = c.L[0];
   FineArgs a;
@@ -312,6 +373,10 @@ void fine3d(Ctx& c, int mode, const Real* ke, const Real* b, const Real* dinv, c
   a.out0 = out0;
   a.out1 = out1;
   a.omega = c.p.omega;
+  a.rdot = rdot;
+  a.dout = dout;
+  a.partials = c.partials;
+  a.counter = c.counter;
   const dim3 block(TX, TY);
   const int gx = (d.NX + TX - 1) / TX, gy = (d.NY + TY - 1) / TY;
   a.gz = std::max(1, std::min(c.f3d_gz[sizeof(Real) == 8][mode & 3], d.NZ));
@@ -325,8 +390,8 @@ void fine3d(Ctx& c, int mode, const Real* ke, const Real* b, const Real* dinv, c
   MGAR_LAUNCH_CHECK_AT(level_site(6 + (mode == PRE ? 0 : mode == POST ? 1 : mode == SWEEP ? 2 : 3), 0));
 }
 template void fine3d<float>(Ctx&, int, const float*, const float*, const float*, const float*,
-                            const float*, float*, float*);
+                            const float*, float*, float*, const float2*, double*);
 template void fine3d<double>(Ctx&, int, const double*, const double*, const double*, const double*,
-                             const double*, double*, double*);
+                             const double*, double*, double*, const float2*, double*);
 
 }  // namespace mgar

@@ -550,7 +550,8 @@ void bottom_prepare(Ctx& c) {
 // restriction, and one fused post kernel (interpolation + smooth); the small
 // levels at the bottom run in one cluster launch.
 template <typename Real, int DIM>
-static void vcycle_fused(Ctx& c, const Real* b0, Real* x0, bool zero_guess) {
+static void vcycle_fused(Ctx& c, const Real* b0, Real* x0, bool zero_guess,
+                         const float2* rdot = nullptr, double* dout = nullptr) {
   LevelBuf<Real>* h = levels<Real>(c);
   const int nl = c.nl;
   const Real om = (Real)c.p.omega;
@@ -620,7 +621,7 @@ static void vcycle_fused(Ctx& c, const Real* b0, Real* x0, bool zero_guess) {
   // finest level, post
   ProfScope ps(c, MGAR_KC_SMOOTH0);
   if (DIM == 3) {
-    fine3d<Real>(c, 1, ref_ke<Real>(c), b0, h[0].dinv, cur0, res[1], x0, nullptr);
+    fine3d<Real>(c, 1, ref_ke<Real>(c), b0, h[0].dinv, cur0, res[1], x0, nullptr, rdot, dout);
   } else {
     // interpolation in place on the pre-smoothed iterate, then the sweep into x0
     k_prolong<Real, DIM><<<blocks_for(d0.n), kThreads, 0, c.stream>>>(res[1], cur0, cur0, d0, c.L[1],
@@ -706,6 +707,12 @@ void vcycle(Ctx& c, const Real* b, Real* x, bool zero_guess) {
 }
 template void vcycle<double>(Ctx&, const double*, double*, bool);
 template void vcycle<float>(Ctx&, const float*, float*, bool);
+
+void vcycle_dot(Ctx& c, const float* b, float* x, const float2* r, double* dout) {
+  require(c.dim == 3 && c.p.nu_pre == 1 && c.p.nu_post == 1 && c.nl >= 2 && !c.untiled, MGAR_ERR_ARG,
+          "fused r.z V-cycle needs the tiled 3D path");
+  vcycle_fused<float, 3>(c, b, x, true, r, dout);
+}
 
 template <typename Real, int DIM>
 static void apply_dim(Ctx& c, const Real* ke, const Real* ksub, const Real* x, Real* y, Real scale,
