@@ -157,6 +157,7 @@ __global__ void k_df_cg_xr(float2* __restrict__ x, float2* __restrict__ r, const
                            const float2* __restrict__ Ap, int n, const double* __restrict__ rz,
                            const double* __restrict__ pap, double* partials, unsigned int* counter,
                            double* out, float* __restrict__ r32) {
+  pdl_wait();
   const df alpha = df_from_double(*rz / *pap);
   df acc{0.f, 0.f};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -311,9 +312,9 @@ static int solve_mgcg_df3(Ctx& c, double* T, int* iters, double* relres) {
       }
       first = false;
       std::swap(pcur, pnext);
-      k_df_cg_xr<<<rb, kThreads, 0, c.stream>>>(c.df_x, c.df_r, pcur, c.df_Ap, n, c.dsc + a,
-                                                c.dsc + S_PAP, c.partials, c.counter, c.dsc + S_RR,
-                                                c.b32);
+      launch_pdl(c.stream, c.use_pdl, k_df_cg_xr, dim3(rb), dim3(kThreads), c.df_x, c.df_r,
+                 (const float2*)pcur, (const float2*)c.df_Ap, n, (const double*)(c.dsc + a),
+                 (const double*)(c.dsc + S_PAP), c.partials, c.counter, c.dsc + S_RR, c.b32);
       MGAR_LAUNCH_CHECK();
       ++it;
       fetch_scalars(c, S_RR, 1);

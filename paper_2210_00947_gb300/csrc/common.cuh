@@ -184,6 +184,7 @@ struct Ctx {
   int f3d_gz[2][4] = {};  // z runs of the tiled finest-level kernels [FP32, FP64][mode]
   int df3d_gz[3] = {};    // z runs of the tiled df64 operator kernels [mode]
   bool bottom_ok = false; // the V-cycle's bottom levels run as one cluster launch
+  bool use_pdl = true;    // programmatic dependent launch of the V-cycle and CG kernels
   cudaStream_t cap_stream = nullptr;
 
   // instrumentation: CUDA-event timing of one kernel class
@@ -197,6 +198,15 @@ struct Ctx {
 };
 
 constexpr int kProfMax = 65536;
+
+// Programmatic dependent launch.  A kernel started by launch_pdl may begin
+// while its predecessor on the stream is still running: it calls pdl_wait()
+// first thing, a hardware wait until the predecessor has completed and its
+// memory is visible, so only launch latency and block dispatch overlap.
+// pdl_trigger() lets the successor be dispatched before this grid ends.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // handle whose API call is running on this host thread (set by the C ABI)
 Ctx*& current_ctx();
 
@@ -637,6 +647,23 @@ void oc_update(Ctx& c, double* rho, const double* dc, double volfrac, double mov
 }  // namespace mgar
 
 namespace mgar {
+// Launch with the programmatic-dependent-launch attribute (see pdl_wait).
+template <typename... KArgs, typename... Args>
+inline void launch_pdl(cudaStream_t s, bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  MGAR_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
+}
+
 // Run `issue` (a fixed sequence of launches on c.stream) through a cached
 // CUDA graph keyed by (kind, a, b); falls back to direct launches while a
 // kernel class inside it is being timed.

@@ -97,6 +97,8 @@ template <int MODE>
 __global__ void __launch_bounds__(NT, 4) k_df3d(DfArgs a) {
   __shared__ float2 X[4][TY + 2][TX + 2];
   __shared__ float2 K[4][TY + 1][TX + 1];
+  pdl_wait();  // one wave: the successor may be dispatched right away
+  pdl_trigger();
 
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
@@ -291,7 +293,7 @@ void launch(Ctx& c, DfArgs& a) {
   const Dims& d = c.L[0];
   a.gz = std::max(1, std::min(c.df3d_gz[MODE], d.NZ));
   const dim3 grid((d.NX + TX - 1) / TX, (d.NY + TY - 1) / TY, a.gz);
-  k_df3d<MODE><<<grid, dim3(TX, TY), 0, c.stream>>>(a);
+  launch_pdl(c.stream, c.use_pdl, k_df3d<MODE>, grid, dim3(TX, TY), a);
   MGAR_LAUNCH_CHECK();
 }
 

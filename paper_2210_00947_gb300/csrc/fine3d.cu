@@ -165,6 +165,8 @@ template <typename Real, int MODE>
 __global__ void __launch_bounds__(NT, sizeof(Real) == 4 ? (MODE == POST ? 3 : 4) : 2) k_fine3d(FineArgs a) {
   __shared__ Real X[XS][TY + 2][TX + 2];
   __shared__ Real K[4][TY + 1][TX + 1];
+  pdl_wait();  // one wave: the successor may be dispatched right away
+  pdl_trigger();
 
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
@@ -285,11 +287,12 @@ __global__ void __launch_bounds__(NT, sizeof(Real) == 4 ? (MODE == POST ? 3 : 4)
       const Real xi = cv[S1]; /* a fixed row is the identity */                            \
       const Real ax = cf[S1] ? xi : acc * Real(1.0 / 12.0);                                \
       const Real bi = cb[S1];                                                              \
+      /* r = 0 on fixed nodes: the restriction P^T = (Z P)^T does not read them */       \
       if (MODE == PRE) {                                                                   \
         ((Real*)a.out0)[idx] = xi;                                                         \
-        ((Real*)a.out1)[idx] = bi - ax;                                                    \
+        ((Real*)a.out1)[idx] = cf[S1] ? Real(0) : bi - ax;                                 \
       } else if (MODE == RESID) {                                                          \
-        ((Real*)a.out0)[idx] = bi - ax;                                                    \
+        ((Real*)a.out0)[idx] = cf[S1] ? Real(0) : bi - ax;                                 \
       } else {                                                                             \
         const Real xo = xi + om * cd[S1] * (bi - ax);                                      \
         ((Real*)a.out0)[idx] = xo;                                                         \
@@ -382,10 +385,10 @@ void fine3d(Ctx& c, int mode, const Real* ke, const Real* b, const Real* dinv, c
   a.gz = std::max(1, std::min(c.f3d_gz[sizeof(Real) == 8][mode & 3], d.NZ));
   const dim3 grid(gx, gy, a.gz);
   switch (mode) {
-    case PRE: k_fine3d<Real, PRE><<<grid, block, 0, c.stream>>>(a); break;
-    case POST: k_fine3d<Real, POST><<<grid, block, 0, c.stream>>>(a); break;
-    case RESID: k_fine3d<Real, RESID><<<grid, block, 0, c.stream>>>(a); break;
-    default: k_fine3d<Real, SWEEP><<<grid, block, 0, c.stream>>>(a); break;
+    case PRE: launch_pdl(c.stream, c.use_pdl, k_fine3d<Real, PRE>, grid, block, a); break;
+    case POST: launch_pdl(c.stream, c.use_pdl, k_fine3d<Real, POST>, grid, block, a); break;
+    case RESID: launch_pdl(c.stream, c.use_pdl, k_fine3d<Real, RESID>, grid, block, a); break;
+    default: launch_pdl(c.stream, c.use_pdl, k_fine3d<Real, SWEEP>, grid, block, a); break;
   }
   MGAR_LAUNCH_CHECK_AT(level_site(6 + (mode == PRE ? 0 : mode == POST ? 1 : mode == SWEEP ? 2 : 3), 0));
 }

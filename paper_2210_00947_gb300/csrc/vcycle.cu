@@ -153,8 +153,10 @@ __device__ __forceinline__ void restrict_node(const Real* __restrict__ r, Real* 
 template <typename Real, int DIM>
 __global__ void k_restrict(const Real* __restrict__ r, Real* __restrict__ bc, Dims f, Dims cd,
                            const uint8_t* __restrict__ fixed) {
+  pdl_wait();
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx < cd.n) restrict_node<Real, DIM, false>(r, bc, f, cd, fixed, idx);
+  pdl_trigger();
 }
 
 // dst = cur + P xc (fixed fine nodes keep cur); dst may equal cur.
@@ -223,8 +225,10 @@ template <typename Real, int DIM>
 __global__ void k_pre_coarse(StencilOp<Real> op, const Real* __restrict__ b,
                              const Real* __restrict__ dinv, Real omega, Real* __restrict__ x,
                              Real* __restrict__ r) {
+  pdl_wait();
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx < op.n) pre_node<Real, DIM, false>(op, b, dinv, omega, x, r, idx);
+  pdl_trigger();
 }
 
 // Per axis: the coarse nodes c0, c0+1, c0+2 that interpolate onto the fine
@@ -330,8 +334,10 @@ __global__ void k_post_coarse(StencilOp<Real> op, const Real* __restrict__ xc,
                               const Real* __restrict__ cur, const Real* __restrict__ b,
                               const Real* __restrict__ dinv, Real omega, Real* __restrict__ dst,
                               Dims f, Dims cd) {
+  pdl_wait();
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx < op.n) post_node<Real, DIM, false>(op, xc, cur, b, dinv, omega, dst, f, cd, idx);
+  pdl_trigger();
 }
 
 // x = C b with the explicit inverse of the coarsest operator (FP64 sums).
@@ -348,6 +354,8 @@ __device__ __forceinline__ void coarse_row(const double* __restrict__ cinv, cons
 template <typename Real>
 __global__ void k_coarse_solve(const double* __restrict__ cinv, const Real* __restrict__ b,
                                Real* __restrict__ x, int n) {
+  pdl_wait();
+  pdl_trigger();
   const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (row < n) coarse_row<Real, false>(cinv, b, x, n, row, threadIdx.x & 31);
 }
@@ -382,6 +390,8 @@ __device__ __forceinline__ void cluster_barrier() {
 
 template <typename Real, int DIM>
 __global__ void __launch_bounds__(kBottomThreads) k_bottom(BottomArgs<Real> a) {
+  pdl_wait();
+  pdl_trigger();
   const int nthr = gridDim.x * blockDim.x;
   const int vt = blockIdx.x * blockDim.x + threadIdx.x;
   for (int l = a.lb; l + 1 < a.nl; ++l) {
@@ -507,13 +517,15 @@ static void launch_bottom(Ctx& c, int lb) {
   cfg.blockDim = dim3(kBottomThreads);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = c.stream;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = kBottomCluster;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = c.use_pdl ? 1 : 0;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   MGAR_CUDA(cudaLaunchKernelEx(&cfg, k_bottom<Real, DIM>, a));
   MGAR_LAUNCH_CHECK_AT("vc bottom");
 }
@@ -581,18 +593,21 @@ static void vcycle_fused(Ctx& c, const Real* b0, Real* x0, bool zero_guess,
       residual<Real, DIM>(c, 0, b0, cur0, h[0].r);
     }
   }
-  k_restrict<Real, DIM><<<blocks_for(c.L[1].n), kThreads, 0, c.stream>>>(h[0].r, h[1].b, d0, c.L[1],
-                                                                          c.fixed);
+  // the tiled 3D kernels leave r = 0 on fixed nodes, which P^T = (Z P)^T ignores
+  launch_pdl(c.stream, c.use_pdl, k_restrict<Real, DIM>, dim3(blocks_for(c.L[1].n)), dim3(kThreads),
+             (const Real*)h[0].r, h[1].b, d0, c.L[1], DIM == 3 ? (const uint8_t*)nullptr : c.fixed);
   MGAR_LAUNCH_CHECK_AT(level_site(3, 0));
   const int lb = bottom_level(c);
   // coarse levels, down
   for (int l = 1; l + 1 < nl && l < lb; ++l) {
     const Dims& d = c.L[l];
-    k_pre_coarse<Real, DIM><<<blocks_for(d.n), kThreads, 0, c.stream>>>(
-        stencil_row<Real, DIM>(c, l).op, h[l].b, h[l].dinv, om, h[l].x, h[l].r);
+    launch_pdl(c.stream, c.use_pdl, k_pre_coarse<Real, DIM>, dim3(blocks_for(d.n)), dim3(kThreads),
+               stencil_row<Real, DIM>(c, l).op, (const Real*)h[l].b, (const Real*)h[l].dinv, om,
+               h[l].x, h[l].r);
     MGAR_LAUNCH_CHECK_AT(level_site(0, l));
-    k_restrict<Real, DIM><<<blocks_for(c.L[l + 1].n), kThreads, 0, c.stream>>>(h[l].r, h[l + 1].b, d,
-                                                                                c.L[l + 1], nullptr);
+    launch_pdl(c.stream, c.use_pdl, k_restrict<Real, DIM>, dim3(blocks_for(c.L[l + 1].n)),
+               dim3(kThreads), (const Real*)h[l].r, h[l + 1].b, d, c.L[l + 1],
+               (const uint8_t*)nullptr);
     MGAR_LAUNCH_CHECK_AT(level_site(3, l));
   }
   if (lb < nl) {
@@ -612,9 +627,9 @@ static void vcycle_fused(Ctx& c, const Real* b0, Real* x0, bool zero_guess,
   // coarse levels, up
   for (int l = std::min(nl - 2, lb - 1); l >= 1; --l) {
     const Dims& d = c.L[l];
-    k_post_coarse<Real, DIM><<<blocks_for(d.n), kThreads, 0, c.stream>>>(
-        stencil_row<Real, DIM>(c, l).op, res[l + 1], h[l].x, h[l].b, h[l].dinv, om, h[l].t, d,
-        c.L[l + 1]);
+    launch_pdl(c.stream, c.use_pdl, k_post_coarse<Real, DIM>, dim3(blocks_for(d.n)), dim3(kThreads),
+               stencil_row<Real, DIM>(c, l).op, res[l + 1], (const Real*)h[l].x,
+               (const Real*)h[l].b, (const Real*)h[l].dinv, om, h[l].t, d, c.L[l + 1]);
     MGAR_LAUNCH_CHECK_AT(level_site(4, l));
     res[l] = h[l].t;
   }
