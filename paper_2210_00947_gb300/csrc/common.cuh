@@ -42,7 +42,8 @@ constexpr int kMinPartialBlocks = 8192;
 constexpr int kMaxFilterOffsets = 1024;
 constexpr int kMaxM = 8;
 constexpr int kOcCand = 31;      // multisection candidates per pass (5 bits)
-constexpr int kOcPasses = 6;     // FP32 passes: ln-bracket 92 -> 9e-8
+constexpr int kOcPasses = 6;     // FP32 passes at most: ln-bracket 92 -> 9e-8
+constexpr double kOcTarget = 1e-6;  // passes stop once the ln-bracket is this narrow
 constexpr int kOcAmbMax = 4096;  // ambiguous elements handled by the FP64 finish
 constexpr double kOcMargin = 2e-5;  // ln-bracket widening that absorbs FP32 volume rounding
 constexpr size_t kBandSmemMax = 160 * 1024;  // band factorised in shared memory up to this size
@@ -59,8 +60,10 @@ enum Slot : int {
   S_RES2 = 112, S_FLAG = 113, S_QQ = 114,
   S_OC_LA = 116, S_OC_LB = 117, S_OC_MUA = 118, S_OC_MUB = 119, S_OC_C = 120, S_OC_B = 121,
   S_OC_MU = 122, S_OC_FAIL = 123,
-  S_OC_CAND = 128,  // 128..158 multisection candidates
-  S_COUNT = 160
+  S_OC_LPREV = 124, S_OC_HAVEPREV = 125,  // ln mu of the previous update (warm start)
+  S_OC_CAND = 128,  // 128..158 multisection candidates mu
+  S_OC_CANDL = 160, // 160..190 their ln mu
+  S_COUNT = 192
 };
 
 // Unsigned division by an invariant divisor d >= 1 for numerators below
@@ -112,6 +115,7 @@ struct Ctx {
   int nl = 0;
   Dims L[kMaxLevels]{};
   int64_t n = 0, ne = 0;
+  int sms = 152;          // multiprocessors of the device
   int grid_blocks = 0;    // blocks of grid-stride reduction kernels over nodes
   int grid_blocks_e = 0;  // ... over elements
 
@@ -140,7 +144,6 @@ struct Ctx {
   double* band = nullptr;   // [nc][bw+1] Cholesky factor (lower band)
   double* rdiag = nullptr;  // [nc] reciprocals of the factor's diagonal
   double* cinv = nullptr;   // [nc][nc] inverse of the coarsest operator
-  float* cinv_f = nullptr;
   double* tables = nullptr;  // k0 (nen^2) then Galerkin sub-element tables G
   float* tables_f = nullptr; // G in FP32
 
@@ -152,6 +155,7 @@ struct Ctx {
   // mixed mode: double-float (hi, lo) copies for the outer CG
   float2 *ke_df = nullptr, *df_q = nullptr, *df_x = nullptr, *df_r = nullptr, *df_p = nullptr,
          *df_Ap = nullptr, *df_p2 = nullptr;
+  float2* df_e = nullptr;  // mixed mode: df64 scratch over elements (filter input)
   double *tmp_e = nullptr, *oc_s = nullptr, *oc_lo = nullptr, *oc_hi = nullptr;
   float *oc_s32 = nullptr, *oc_lo32 = nullptr, *oc_hi32 = nullptr, *dv32 = nullptr;
   int *oc_amb = nullptr, *oc_namb = nullptr;
@@ -198,6 +202,19 @@ struct Ctx {
 };
 
 constexpr int kProfMax = 65536;
+
+// Coarsest-level factor and inverse.  Both V-cycle precisions factorise
+// and invert in FP64 and sum the coarse solve in FP64: an FP32 factor of the
+// coarsest operator (condition number up to ~1e5 with the SIMP contrast)
+// moves the V-cycle far enough to change the reanalysis basis of Eq. 17
+// measurably.
+template <typename Real>
+struct CoarseT {
+  using T = double;
+  static double* band(Ctx& c) { return c.band; }
+  static double* rdiag(Ctx& c) { return c.rdiag; }
+  static double* inv(Ctx& c) { return c.cinv; }
+};
 
 // Programmatic dependent launch.  A kernel started by launch_pdl may begin
 // while its predecessor on the stream is still running: it calls pdl_wait()
@@ -344,6 +361,57 @@ __device__ __forceinline__ bool block_sum_last(double (&v)[N], double* partials,
                                                unsigned int* counter, double (&total)[N]) {
   return block_sum_last_ids<N>(v, partials, counter, total, threadIdx.x, blockDim.x, blockIdx.x,
                                gridDim.x);
+}
+
+// Many sums of FP32 per-thread values (N of them, e.g. candidate volumes):
+// warp sums in FP32 (shuffles), then FP64 for the few cross-warp and
+// cross-block additions.  FP64 runs at 1/58 of the FP32 rate here, so
+// reducing N doubles through shuffles costs more than the data pass.  The
+// last block sums each value's per-block partials with one warp, lanes
+// striding over the blocks.  Same ticket protocol and fixed order as
+// block_sum_last.
+template <int N>
+__device__ __forceinline__ bool block_sum_last_f32(float (&v)[N], double* partials,
+                                                   unsigned int* counter, double (&total)[N]) {
+  __shared__ float sh[N][kThreads / 32];
+  __shared__ double tot[N];
+  __shared__ bool last;
+  const int tid = threadIdx.x, nthr = blockDim.x, bid = blockIdx.x, nblk = gridDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    float s = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) sh[k][warp] = s;
+  }
+  __syncthreads();
+  for (int k = tid; k < N; k += nthr) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += (double)sh[k][w];
+    if (CK((int64_t)k * nblk + bid, g_partials_len)) partials[k * nblk + bid] = s;
+    __threadfence();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const unsigned int t = atomicAdd(counter, 1u);
+    last = (t == (unsigned int)nblk - 1);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  for (int k = warp; k < N; k += nw) {
+    double s = 0.0;
+    for (int b = lane; b < nblk; b += 32) s += ((volatile double*)partials)[k * nblk + b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) tot[k] = s;
+  }
+  if (tid == 0) *counter = 0u;
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < N; ++k) total[k] = tot[k];
+  return true;
 }
 
 // As block_sum_last, storing the totals to out[0..N) from the last block.

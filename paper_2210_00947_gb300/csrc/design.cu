@@ -1,6 +1,7 @@
 // Density filter (Eq. 6-8), SIMP conductivities (Eq. 4), compliance and
 // sensitivities (Eq. 5, 9-11), and the optimality-criteria update.
 #include "common.cuh"
+#include "df64.cuh"
 
 #include <vector>
 
@@ -31,6 +32,147 @@ __global__ void k_filter(const double* __restrict__ in, double* __restrict__ out
     else acc += wo * in[nb];
   }
   out[e] = TRANSPOSE ? acc : acc * inv_hs[e];
+}
+
+// ---- mixed path: filter and sensitivities in double-float on the FP32 pipe
+// (FP64 runs at 1/58 of the FP32 rate here).  Weights and inputs are
+// non-negative (densities) or non-positive (sensitivities), so the sums have
+// no cancellation and the pairs' 2^-46 relative precision carries through.
+
+__device__ __forceinline__ df dfk2(float2 v) { return df{v.x, v.y}; }
+
+// (ah, al) += w * x, unnormalised
+__device__ __forceinline__ void acc_prod(float& ah, float& al, df w, df x) {
+  float p, pe;
+  two_prod(w.hi, x.hi, p, pe);
+  pe = __fmaf_rn(w.hi, x.lo, pe);
+  pe = __fmaf_rn(w.lo, x.hi, pe);
+  float t, te;
+  two_sum(ah, p, t, te);
+  ah = t;
+  al = __fadd_rn(al, __fadd_rn(te, pe));
+}
+
+// sum over in-domain offsets o of w_o in_{e+o}
+__device__ __forceinline__ df filter_sum_df(const float2* __restrict__ in, const df* w, const int4* offs,
+                                            int noff, int e, int i, int j, int k, const Dims& d) {
+  float ah = 0.f, al = 0.f;
+  for (int o = 0; o < noff; ++o) {
+    const int4 dd = offs[o];
+    const int ii = i + dd.x, jj = j + dd.y, kk = k + dd.z;
+    const bool ok = !(ii < 0 || ii >= d.ex || jj < 0 || jj >= d.ey || kk < 0 || kk >= d.ez);
+    const int nb = ok ? ii + d.ex * (jj + d.ey * kk) : e;  // valid address either way
+    if (!CK(nb, d.ne)) continue;
+    const df x = dfk2(in[nb]);
+    if (ok) acc_prod(ah, al, w[o], x);
+  }
+  return df_make(ah, al);
+}
+
+// Forward filter (Eq. 6) fused with the SIMP conductivities (Eq. 4):
+// rho~_e = inv_hs_e sum_o w_o rho_{e+o}, k_e = kmin + (k0 - kmin) rho~^3,
+// written as FP64 (rho~, k_e), FP32 and df64 copies of k_e.
+__global__ void k_filter_simp_df(const float2* __restrict__ rho, const double* __restrict__ inv_hs,
+                                 const int4* __restrict__ offs, const double* __restrict__ w, int noff,
+                                 Dims d, double k0, double kmin, double penal,
+                                 double* __restrict__ rho_phys, double* __restrict__ ke,
+                                 float* __restrict__ kf, float2* __restrict__ kdf) {
+  __shared__ df ws[kMaxFilterOffsets];
+  __shared__ int4 os[kMaxFilterOffsets];
+  for (int o = threadIdx.x; o < noff; o += blockDim.x) {
+    ws[o] = df_from_double(w[o]);
+    os[o] = offs[o];
+  }
+  __syncthreads();
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int)d.ne) return;
+  int i, j, k;
+  coords(e, d.fEX, d.fEXY, i, j, k);
+  const df r = df_mul(filter_sum_df(rho, ws, os, noff, e, i, j, k, d), df_from_double(inv_hs[e]));
+  rho_phys[e] = df_to_double(r);
+  df kv;
+  if (penal == 3.0) {
+    kv = df_add(df_from_double(kmin), df_mul(df_from_double(k0 - kmin), df_mul(df_mul(r, r), r)));
+  } else {
+    kv = df_from_double(kmin + (k0 - kmin) * pow(df_to_double(r), penal));
+  }
+  ke[e] = df_to_double(kv);
+  kf[e] = __fadd_rn(kv.hi, kv.lo);
+  kdf[e] = make_float2(kv.hi, kv.lo);
+}
+
+// Element sensitivity (Eq. 10) times inv_hs, as the transpose filter's input:
+// out_e = -p (k0 - kmin) rho~_e^(p-1) t_e^T k0 t_e / sum_e', with the energy
+// from exact pair differences (k0 has zero row sums).
+template <int DIM>
+__global__ void k_sens_df(const float2* __restrict__ T, const double* __restrict__ rho,
+                          const double* __restrict__ inv_hs, float2* __restrict__ out, Dims d,
+                          double coef, double penal) {
+  constexpr int nen = 1 << DIM;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int)d.ne) return;
+  int i, j, k;
+  coords(e, d.fEX, d.fEXY, i, j, k);
+  float2 t[nen];
+#pragma unroll
+  for (int a = 0; a < nen; ++a) {
+    const int nd = (i + (a & 1)) + d.NX * ((j + ((a >> 1) & 1)) + d.NY * (k + ((a >> 2) & 1)));
+    t[a] = CK(nd, d.n) ? T[nd] : make_float2(0.f, 0.f);
+  }
+  // sum over pairs of c_ab (t_a - t_b)^2 with c = 1 (Q4 edges), 2 (Q4
+  // diagonals), 1 (H8 face and body diagonals); scale 1/6 (Q4) or 1/12 (H8)
+  float ah = 0.f, al = 0.f;
+#pragma unroll
+  for (int a = 0; a < nen; ++a)
+#pragma unroll
+    for (int b = a + 1; b < nen; ++b) {
+      const int pc = __popc(a ^ b);
+      const float cab = DIM == 2 ? (pc == 1 ? 1.f : 2.f) : (pc >= 2 ? 1.f : 0.f);
+      if (cab == 0.f) continue;
+      float s, er;
+      two_sum(t[a].x, -t[b].x, s, er);
+      er = __fadd_rn(er, __fsub_rn(t[a].y, t[b].y));
+      // (s + er)^2 ~ s^2 + 2 s er
+      float p, pe;
+      two_prod(s, s, p, pe);
+      pe = __fmaf_rn(2.f * s, er, pe);
+      p *= cab;
+      pe *= cab;
+      float u, ue;
+      two_sum(ah, p, u, ue);
+      ah = u;
+      al = __fadd_rn(al, __fadd_rn(ue, pe));
+    }
+  const df energy = df_mul(df_make(ah, al), df_from_double(DIM == 2 ? 1.0 / 6.0 : 1.0 / 12.0));
+  const df r = df_from_double(rho[e]);
+  const df rp = penal == 3.0 ? df_mul(r, r) : df_from_double(pow(rho[e], penal - 1.0));
+  const df v = df_mul(df_mul(df_from_double(-coef), rp), df_mul(energy, df_from_double(inv_hs[e])));
+  out[e] = make_float2(v.hi, v.lo);
+}
+
+// Transpose filter (Eq. 9/11) of a df64 input already scaled by inv_hs.
+__global__ void k_filter_t_df(const float2* __restrict__ in, const int4* __restrict__ offs,
+                              const double* __restrict__ w, int noff, Dims d, double* __restrict__ out) {
+  __shared__ df ws[kMaxFilterOffsets];
+  __shared__ int4 os[kMaxFilterOffsets];
+  for (int o = threadIdx.x; o < noff; o += blockDim.x) {
+    ws[o] = df_from_double(w[o]);
+    os[o] = offs[o];
+  }
+  __syncthreads();
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int)d.ne) return;
+  int i, j, k;
+  coords(e, d.fEX, d.fEXY, i, j, k);
+  out[e] = df_to_double(filter_sum_df(in, ws, os, noff, e, i, j, k, d));
+}
+
+__global__ void k_to_df(const double* __restrict__ a, float2* __restrict__ b, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const df v = df_from_double(a[i]);
+    b[i] = make_float2(v.hi, v.lo);
+  }
 }
 
 __global__ void k_filter_norm(double* __restrict__ inv_hs, const int4* __restrict__ offs,
@@ -185,41 +327,82 @@ __global__ void k_oc_init(double* dsc, double lo, double hi) {
 // bisection of k_oc_pass.
 
 // candidates mu_k, k = 0..kOcCand-1, at fractions (k+1)/(kOcCand+1) of [La, Lb]
+// evenly spaced candidates strictly inside the ln-bracket [La, Lb]
 __device__ __forceinline__ void oc_candidates(double* dsc) {
   const double La = dsc[S_OC_LA], Lb = dsc[S_OC_LB];
-  for (int k = threadIdx.x; k < kOcCand; k += blockDim.x)
-    dsc[S_OC_CAND + k] = exp(La + (Lb - La) * (double)(k + 1) / (double)(kOcCand + 1));
+  for (int k = threadIdx.x; k < kOcCand; k += blockDim.x) {
+    const double L = La + (Lb - La) * (double)(k + 1) / (double)(kOcCand + 1);
+    dsc[S_OC_CANDL + k] = L;
+    dsc[S_OC_CAND + k] = exp(L);
+  }
 }
 
-__global__ void k_oc_start(double* dsc, double La, double Lb) {
+// First pass.  Cold: evenly spaced over [La, Lb].  Warm (ln mu of the
+// previous update known): a two-sided geometric ladder L0 +- 1e-3 * 2^(j-1),
+// j = 1..14, around it, with the range ends as outermost candidates, so the
+// first pass brackets the root anywhere in the range and finely near L0.
+__global__ void k_oc_start(double* dsc, double La, double Lb, int warm) {
+  const bool w = warm && dsc[S_OC_HAVEPREV] != 0.0;
+  const double L0 = fmin(fmax(dsc[S_OC_LPREV], La), Lb);
   if (threadIdx.x == 0) {
     dsc[S_OC_LA] = La;
     dsc[S_OC_LB] = Lb;
     dsc[S_OC_FAIL] = 0.0;
   }
-  __syncthreads();
-  oc_candidates(dsc);
+  if (!w) {
+    __syncthreads();
+    oc_candidates(dsc);
+    return;
+  }
+  for (int k = threadIdx.x; k < kOcCand; k += blockDim.x) {
+    const int j = k - kOcCand / 2;
+    double L;
+    if (k == 0) L = La;
+    else if (k == kOcCand - 1) L = Lb;
+    else if (j == 0) L = L0;
+    else L = L0 + (j > 0 ? 1.0 : -1.0) * 1e-3 * exp2((double)(abs(j) - 1));
+    L = fmin(fmax(L, La), Lb);
+    dsc[S_OC_CANDL + k] = L;
+    dsc[S_OC_CAND + k] = exp(L);
+  }
 }
 
 __global__ void k_oc_multisect(const float* __restrict__ s, const float* __restrict__ lo,
                                const float* __restrict__ hi, const float* __restrict__ dv, int ne,
                                double volfrac, double* dsc, double* partials,
                                unsigned int* counter) {
+  // the bracket is read by every block before the last one moves it
+  if (dsc[S_OC_LB] - dsc[S_OC_LA] <= kOcTarget) return;  // narrow enough: pass skipped
   __shared__ float mu[kOcCand];
   if (threadIdx.x < kOcCand) mu[threadIdx.x] = (float)dsc[S_OC_CAND + threadIdx.x];
   __syncthreads();
   float acc[kOcCand];
 #pragma unroll
   for (int k = 0; k < kOcCand; ++k) acc[k] = 0.f;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
+  const int stride = gridDim.x * blockDim.x;
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  // four elements per iteration: their loads are in flight together
+  for (; e + 3 * stride < ne; e += 4 * stride) {
+    float sv[4], lv[4], hv[4], dd[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      sv[u] = s[e + u * stride];
+      lv[u] = lo[e + u * stride];
+      hv[u] = hi[e + u * stride];
+      dd[u] = dv[e + u * stride];
+    }
+#pragma unroll
+    for (int k = 0; k < kOcCand; ++k)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[k] += dd[u] * fminf(fmaxf(sv[u] * mu[k], lv[u]), hv[u]);
+  }
+  for (; e < ne; e += stride) {
     const float se = s[e], l = lo[e], h = hi[e], d = dv[e];
 #pragma unroll
     for (int k = 0; k < kOcCand; ++k) acc[k] += d * fminf(fmaxf(se * mu[k], l), h);
   }
-  double v[kOcCand], tot[kOcCand];
-#pragma unroll
-  for (int k = 0; k < kOcCand; ++k) v[k] = (double)acc[k];
-  const bool last = block_sum_last<kOcCand>(v, partials, counter, tot);
+  double tot[kOcCand];
+  const bool last = block_sum_last_f32<kOcCand>(acc, partials, counter, tot);
   if (!last) return;
   if (threadIdx.x == 0) {
     int ks = kOcCand;
@@ -229,8 +412,8 @@ __global__ void k_oc_multisect(const float* __restrict__ s, const float* __restr
         break;
       }
     const double La = dsc[S_OC_LA], Lb = dsc[S_OC_LB];
-    dsc[S_OC_LA] = La + (Lb - La) * (double)ks / (double)(kOcCand + 1);
-    dsc[S_OC_LB] = La + (Lb - La) * (double)(ks + 1) / (double)(kOcCand + 1);
+    dsc[S_OC_LA] = ks == 0 ? La : dsc[S_OC_CANDL + ks - 1];
+    dsc[S_OC_LB] = ks == kOcCand ? Lb : dsc[S_OC_CANDL + ks];
   }
   __syncthreads();
   oc_candidates(dsc);
@@ -346,7 +529,14 @@ __global__ void k_oc_apply(double* __restrict__ rho, const double* __restrict__ 
     rho[e] = rn;
   }
   block_max_finish(ch, partials, counter, dsc + S_OC_CHANGE);
-  if (blockIdx.x == 0 && threadIdx.x == 0) dsc[S_OC_LAM] = 1.0 / (mu * mu);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    dsc[S_OC_LAM] = 1.0 / (mu * mu);
+    // ln mu for the next update's warm start
+    const double L = log(mu);
+    const bool ok = isfinite(L) && fabs(L) < 20.0 * 2.302585092994046;
+    dsc[S_OC_LPREV] = ok ? L : 0.0;
+    dsc[S_OC_HAVEPREV] = ok ? 1.0 : 0.0;
+  }
 }
 
 __global__ void k_rsqrt_e(const double* __restrict__ a, double* __restrict__ b, int n) {
@@ -421,6 +611,17 @@ void filter(Ctx& c, const double* in, double* out, bool transpose) {
 }
 
 void set_density(Ctx& c, const double* rho, bool physical) {
+  if (c.p.precision == MGAR_MIXED && !physical) {
+    // filter + SIMP in one df64 pass
+    ProfScope ps(c, MGAR_KC_FILTER);
+    k_to_df<<<blocks_for(c.ne), kThreads, 0, c.stream>>>(rho, c.df_e, (int)c.ne);
+    MGAR_LAUNCH_CHECK();
+    k_filter_simp_df<<<blocks_for(c.ne), kThreads, 0, c.stream>>>(
+        c.df_e, c.inv_hs, c.f_offs, c.f_w, c.n_filter, c.L[0], c.p.k0, c.p.kmin, c.p.penal,
+        c.rho_phys, c.ke, c.ke_f, c.ke_df);
+    MGAR_LAUNCH_CHECK();
+    return;
+  }
   if (physical)
     MGAR_CUDA(cudaMemcpyAsync(c.rho_phys, rho, c.ne * sizeof(double), cudaMemcpyDeviceToDevice,
                               c.stream));
@@ -436,7 +637,21 @@ void set_density(Ctx& c, const double* rho, bool physical) {
 void sensitivity(Ctx& c, const double* T, double* dc, double* dv, double* compliance) {
   const Dims& d = c.L[0];
   const double coef = c.p.penal * (c.p.k0 - c.p.kmin);
-  if (dc) {
+  if (dc && c.p.precision == MGAR_MIXED) {
+    ProfScope ps(c, MGAR_KC_SENS);
+    k_to_df<<<blocks_for(c.n), kThreads, 0, c.stream>>>(T, c.df_p2, (int)c.n);
+    MGAR_LAUNCH_CHECK();
+    if (c.dim == 2)
+      k_sens_df<2><<<blocks_for(c.ne), kThreads, 0, c.stream>>>(c.df_p2, c.rho_phys, c.inv_hs, c.df_e,
+                                                                d, coef, c.p.penal);
+    else
+      k_sens_df<3><<<blocks_for(c.ne), kThreads, 0, c.stream>>>(c.df_p2, c.rho_phys, c.inv_hs, c.df_e,
+                                                                d, coef, c.p.penal);
+    MGAR_LAUNCH_CHECK();
+    k_filter_t_df<<<blocks_for(c.ne), kThreads, 0, c.stream>>>(c.df_e, c.f_offs, c.f_w, c.n_filter, d,
+                                                               dc);
+    MGAR_LAUNCH_CHECK();
+  } else if (dc) {
     ProfScope ps(c, MGAR_KC_SENS);
     if (c.dim == 2)
       k_elem_sens<2><<<blocks_for(c.ne), kThreads, 0, c.stream>>>(T, c.rho_phys, c.tmp_e, d, coef,
@@ -475,9 +690,10 @@ void oc_update(Ctx& c, double* rho, const double* dc, double volfrac, double mov
     k_oc_prep32<<<blocks_for(ne), kThreads, 0, c.stream>>>(c.oc_s, c.oc_lo, c.oc_hi, c.oc_s32,
                                                            c.oc_lo32, c.oc_hi32, ne);
     MGAR_LAUNCH_CHECK();
-    k_oc_start<<<1, 32, 0, c.stream>>>(c.dsc, Lmin, Lmax);
+    k_oc_start<<<1, 32, 0, c.stream>>>(c.dsc, Lmin, Lmax, 1);
     MGAR_LAUNCH_CHECK();
-    const int msb = std::min(rb, 152 * 2);  // one wave of blocks: short reduction tail
+    // two blocks per SM: the last block's FP64 sum over the partials stays short
+    const int msb = std::min(blocks_for(ne), c.sms * 2);
     for (int pass = 0; pass < kOcPasses; ++pass) {
       k_oc_multisect<<<msb, kThreads, 0, c.stream>>>(c.oc_s32, c.oc_lo32, c.oc_hi32, c.dv32, ne,
                                                     volfrac, c.dsc, c.partials, c.counter);

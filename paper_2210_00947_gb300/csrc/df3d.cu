@@ -90,6 +90,15 @@ __device__ __forceinline__ void acc_term(float& ah, float& al, df w, float2 xi, 
 
 __device__ __forceinline__ df dfk(float2 v) { return df{v.x, v.y}; }
 
+// k_a + k_b as an unnormalised pair (TwoSum of the high parts, low parts
+// added): exact to the pair's precision; acc_term multiplies both halves,
+// so the pair needs no renormalisation.
+__device__ __forceinline__ df wsum(df a, df b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  return df{s, __fadd_rn(e, __fadd_rn(a.lo, b.lo))};
+}
+
 // Plane p and element layer p live in slot (p - kb + 1) & 3; the z loop is
 // unrolled by four, so every slot index is a compile-time constant and the
 // centre values of the planes in flight stay in registers.
@@ -206,18 +215,18 @@ __global__ void __launch_bounds__(NT, 4) k_df3d(DfArgs a) {
         const df k100 = dfk(K[S1][ty][tx]), k101 = dfk(K[S1][ty][tx + 1]),                 \
                  k110 = dfk(K[S1][ty + 1][tx]), k111 = dfk(K[S1][ty + 1][tx + 1]);         \
         float ah = 0.f, al = 0.f;                                                          \
-        acc_term(ah, al, df_add(k000, k100), xi, X[S1][cy - 1][cx - 1]);                   \
-        acc_term(ah, al, df_add(k001, k101), xi, X[S1][cy - 1][cx + 1]);                   \
-        acc_term(ah, al, df_add(k010, k110), xi, X[S1][cy + 1][cx - 1]);                   \
-        acc_term(ah, al, df_add(k011, k111), xi, X[S1][cy + 1][cx + 1]);                   \
-        acc_term(ah, al, df_add(k000, k010), xi, X[S0][cy][cx - 1]);                       \
-        acc_term(ah, al, df_add(k001, k011), xi, X[S0][cy][cx + 1]);                       \
-        acc_term(ah, al, df_add(k100, k110), xi, X[S2][cy][cx - 1]);                       \
-        acc_term(ah, al, df_add(k101, k111), xi, X[S2][cy][cx + 1]);                       \
-        acc_term(ah, al, df_add(k000, k001), xi, X[S0][cy - 1][cx]);                       \
-        acc_term(ah, al, df_add(k010, k011), xi, X[S0][cy + 1][cx]);                       \
-        acc_term(ah, al, df_add(k100, k101), xi, X[S2][cy - 1][cx]);                       \
-        acc_term(ah, al, df_add(k110, k111), xi, X[S2][cy + 1][cx]);                       \
+        acc_term(ah, al, wsum(k000, k100), xi, X[S1][cy - 1][cx - 1]);                   \
+        acc_term(ah, al, wsum(k001, k101), xi, X[S1][cy - 1][cx + 1]);                   \
+        acc_term(ah, al, wsum(k010, k110), xi, X[S1][cy + 1][cx - 1]);                   \
+        acc_term(ah, al, wsum(k011, k111), xi, X[S1][cy + 1][cx + 1]);                   \
+        acc_term(ah, al, wsum(k000, k010), xi, X[S0][cy][cx - 1]);                       \
+        acc_term(ah, al, wsum(k001, k011), xi, X[S0][cy][cx + 1]);                       \
+        acc_term(ah, al, wsum(k100, k110), xi, X[S2][cy][cx - 1]);                       \
+        acc_term(ah, al, wsum(k101, k111), xi, X[S2][cy][cx + 1]);                       \
+        acc_term(ah, al, wsum(k000, k001), xi, X[S0][cy - 1][cx]);                       \
+        acc_term(ah, al, wsum(k010, k011), xi, X[S0][cy + 1][cx]);                       \
+        acc_term(ah, al, wsum(k100, k101), xi, X[S2][cy - 1][cx]);                       \
+        acc_term(ah, al, wsum(k110, k111), xi, X[S2][cy + 1][cx]);                       \
         acc_term(ah, al, k000, xi, X[S0][cy - 1][cx - 1]);                                 \
         acc_term(ah, al, k001, xi, X[S0][cy - 1][cx + 1]);                                 \
         acc_term(ah, al, k010, xi, X[S0][cy + 1][cx - 1]);                                 \

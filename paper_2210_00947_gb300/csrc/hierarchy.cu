@@ -243,8 +243,8 @@ __global__ void k_fine_dinv(const Real* __restrict__ ke, const uint8_t* __restri
 }
 
 // Lower band of the coarsest operator: band[i*(bw+1) + (j - i + bw)].
-template <typename Real, int DIM>
-__global__ void k_band_fill(const Real* __restrict__ st, Dims d, int bw, double* __restrict__ band) {
+template <typename Real, int DIM, typename B>
+__global__ void k_band_fill(const Real* __restrict__ st, Dims d, int bw, B* __restrict__ band) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int)d.n) return;
   int i, j, k;
@@ -257,32 +257,33 @@ __global__ void k_band_fill(const Real* __restrict__ st, Dims d, int bw, double*
     const int col = ii + d.NX * (jj + d.NY * kk);  // no load depends on it before the check
     if (col > idx) continue;
     if (CK((int64_t)idx * (bw + 1) + (col - idx + bw), d.n * (bw + 1)) && CK(col - idx + bw, bw + 1))
-      band[(int64_t)idx * (bw + 1) + (col - idx + bw)] = (double)st[s * (int)d.n + idx];
+      band[(int64_t)idx * (bw + 1) + (col - idx + bw)] = (B)st[s * (int)d.n + idx];
   }
 }
 
 // Right-looking banded Cholesky in one block, on a shared-memory copy of
 // the band when it fits (SMEM) or in place in global memory.  Stores the
 // factor and the reciprocals of its diagonal (rdiag).
-template <bool SMEM>
-__global__ void k_band_cholesky(double* __restrict__ gband, double* __restrict__ rdiag, int n,
-                                int bw, int* __restrict__ err) {
-  extern __shared__ double sband[];
-  __shared__ double piv, rpiv;
+template <typename B, bool SMEM>
+__global__ void k_band_cholesky(B* __restrict__ gband, B* __restrict__ rdiag, int n, int bw,
+                                int* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  B* sband = reinterpret_cast<B*>(smraw);
+  __shared__ B piv, rpiv;
   __shared__ int bad;
   const int ld = bw + 1;
   const int64_t size = (int64_t)n * ld;
-  double* band = SMEM ? sband : gband;
+  B* band = SMEM ? sband : gband;
   if (SMEM)
     for (int64_t t = threadIdx.x; t < size; t += blockDim.x) band[t] = gband[t];
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
   for (int k = 0; k < n; ++k) {
     if (threadIdx.x == 0) {
-      const double a = band[(int64_t)k * ld + bw];
-      if (!(a > 0.0) || !isfinite(a)) bad = 1;
+      const B a = band[(int64_t)k * ld + bw];
+      if (!(a > B(0)) || !isfinite(a)) bad = 1;
       piv = sqrt(a);
-      rpiv = 1.0 / piv;
+      rpiv = B(1) / piv;
       band[(int64_t)k * ld + bw] = piv;
       rdiag[k] = rpiv;
     }
@@ -315,15 +316,16 @@ __global__ void k_band_cholesky(double* __restrict__ gband, double* __restrict__
 // substitution with the band factor; inv is row-major n x n.  With SMEM the
 // band is staged in shared memory once per block and each warp keeps its
 // column there too (the substitutions are chains of dependent reads).
-template <bool SMEM>
-__global__ void k_band_inverse(const double* __restrict__ gband, const double* __restrict__ rdiag,
-                               int n, int bw, double* inv) {
-  extern __shared__ double sband[];
+template <typename B, bool SMEM>
+__global__ void k_band_inverse(const B* __restrict__ gband, const B* __restrict__ rdiag, int n, int bw,
+                               B* inv) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  B* sband = reinterpret_cast<B*>(smraw);
   const int ld = bw + 1;
   const int warps = blockDim.x >> 5;
   const int wid = threadIdx.x >> 5;
-  const double* band = gband;
-  double* colbuf = nullptr;
+  const B* band = gband;
+  B* colbuf = nullptr;
   if (SMEM) {
     const int64_t size = (int64_t)n * ld;
     for (int64_t t = threadIdx.x; t < size; t += blockDim.x) sband[t] = gband[t];
@@ -335,21 +337,21 @@ __global__ void k_band_inverse(const double* __restrict__ gband, const double* _
   const int lane = threadIdx.x & 31;
   if (col >= n) return;
   // column values live in colbuf (shared) or in inv itself (global)
-  auto cv = [&](int i) -> double& { return SMEM ? colbuf[i] : inv[(int64_t)i * n + col]; };
+  auto cv = [&](int i) -> B& { return SMEM ? colbuf[i] : inv[(int64_t)i * n + col]; };
   if (SMEM)
-    for (int i = lane; i < n; i += 32) colbuf[i] = 0.0;
+    for (int i = lane; i < n; i += 32) colbuf[i] = B(0);
   __syncwarp();
   for (int i = col; i < n; ++i) {
-    double s = 0.0;
+    B s = B(0);
     for (int p = max(col, i - bw) + lane; p < i; p += 32)
       if (CK((int64_t)i * ld + (p - i + bw), (int64_t)n * ld) && CK(p - i + bw, ld))
         s += band[(int64_t)i * ld + (p - i + bw)] * cv(p);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) cv(i) = ((i == col ? 1.0 : 0.0) - s) * rdiag[i];
+    if (lane == 0) cv(i) = ((i == col ? B(1) : B(0)) - s) * rdiag[i];
     __syncwarp();
   }
   for (int i = n - 1; i >= 0; --i) {
-    double s = 0.0;
+    B s = B(0);
     const int last = min(n - 1, i + bw);
     for (int p = i + 1 + lane; p <= last; p += 32)
       if (CK((int64_t)p * ld + (i - p + bw), (int64_t)n * ld) && CK(i - p + bw, ld))
@@ -408,15 +410,15 @@ void alloc_hierarchy(Ctx& c) {
   if (c.bw > c.nc - 1) c.bw = c.nc - 1 > 0 ? c.nc - 1 : 0;
   MGAR_CUDA(cudaMalloc(&c.band, (size_t)c.nc * (c.bw + 1) * sizeof(double)));
   MGAR_CUDA(cudaMalloc(&c.rdiag, (size_t)c.nc * sizeof(double)));
-  const size_t band_bytes = (size_t)c.nc * (c.bw + 1) * sizeof(double);
-  if (band_bytes <= kBandSmemMax) {
-    MGAR_CUDA(cudaFuncSetAttribute(k_band_cholesky<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)kBandSmemMax));
-    MGAR_CUDA(cudaFuncSetAttribute(k_band_inverse<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)kBandSmemMax));
-  }
   MGAR_CUDA(cudaMalloc(&c.cinv, (size_t)c.nc * c.nc * sizeof(double)));
-  if (c.p.precision != MGAR_FP64) MGAR_CUDA(cudaMalloc(&c.cinv_f, (size_t)c.nc * c.nc * sizeof(float)));
+  MGAR_CUDA(cudaFuncSetAttribute(k_band_cholesky<double, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandSmemMax));
+  MGAR_CUDA(cudaFuncSetAttribute(k_band_inverse<double, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandSmemMax));
+  MGAR_CUDA(cudaFuncSetAttribute(k_band_cholesky<float, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandSmemMax));
+  MGAR_CUDA(cudaFuncSetAttribute(k_band_inverse<float, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandSmemMax));
   // constant tables: k0 (nen^2) then G (3^dim * nen^2)
   const int nen = c.nen, ntypes = c.dim == 2 ? 9 : 27;
   std::vector<double> k0(nen * nen), G((size_t)ntypes * nen * nen, 0.0),
@@ -457,14 +459,12 @@ void free_hierarchy(Ctx& c) {
   cudaFree(c.band);
   cudaFree(c.rdiag);
   cudaFree(c.cinv);
-  cudaFree(c.cinv_f);
   cudaFree(c.tables);
   cudaFree(c.tables_f);
   c.tables_f = nullptr;
   c.band = nullptr;
   c.rdiag = nullptr;
   c.cinv = nullptr;
-  c.cinv_f = nullptr;
   c.tables = nullptr;
 }
 
@@ -478,6 +478,34 @@ const float* g_tables<float>(Ctx& c) { return c.tables_f; }
 template <typename Real>
 static const Real* p_tables(Ctx& c) {
   return g_tables<Real>(c) + (size_t)(c.dim == 2 ? 9 : 27) * c.nen * c.nen;
+}
+
+// Band Cholesky of the coarsest operator and its explicit inverse, in B
+// (the V-cycle's working precision).
+template <typename Real, int DIM, typename B>
+static void coarse_factor(Ctx& c, const Real* st, const Dims& dcst) {
+  cudaStream_t s = c.stream;
+  B* band = CoarseT<Real>::band(c);
+  B* rdiag = CoarseT<Real>::rdiag(c);
+  B* inv = CoarseT<Real>::inv(c);
+  MGAR_CUDA(cudaMemsetAsync(band, 0, (size_t)c.nc * (c.bw + 1) * sizeof(B), s));
+  k_band_fill<Real, DIM, B><<<blocks_for(dcst.n), kThreads, 0, s>>>(st, dcst, c.bw, band);
+  MGAR_LAUNCH_CHECK();
+  const size_t band_bytes = (size_t)c.nc * (c.bw + 1) * sizeof(B);
+  const bool smem = band_bytes <= kBandSmemMax;
+  if (smem) {
+    k_band_cholesky<B, true><<<1, 1024, band_bytes, s>>>(band, rdiag, c.nc, c.bw, c.derr);
+  } else {
+    k_band_cholesky<B, false><<<1, 1024, 0, s>>>(band, rdiag, c.nc, c.bw, c.derr);
+  }
+  MGAR_LAUNCH_CHECK();
+  MGAR_CUDA(cudaMemsetAsync(inv, 0, (size_t)c.nc * c.nc * sizeof(B), s));
+  const size_t inv_smem = band_bytes + (size_t)8 * c.nc * sizeof(B);
+  if (smem && inv_smem <= kBandSmemMax)
+    k_band_inverse<B, true><<<(c.nc + 7) / 8, 256, inv_smem, s>>>(band, rdiag, c.nc, c.bw, inv);
+  else
+    k_band_inverse<B, false><<<(c.nc + 7) / 8, 256, 0, s>>>(band, rdiag, c.nc, c.bw, inv);
+  MGAR_LAUNCH_CHECK();
 }
 
 template <typename Real, int DIM>
@@ -505,28 +533,7 @@ static void build_levels(Ctx& c, const Real* ke0, LevelBuf<Real>* h) {
     MGAR_LAUNCH_CHECK();
   }
   const Dims& dcst = c.L[c.nl - 1];
-  MGAR_CUDA(cudaMemsetAsync(c.band, 0, (size_t)c.nc * (c.bw + 1) * sizeof(double), s));
-  k_band_fill<Real, DIM><<<blocks_for(dcst.n), kThreads, 0, s>>>(h[c.nl - 1].st, dcst, c.bw, c.band);
-  MGAR_LAUNCH_CHECK();
-  const size_t band_bytes = (size_t)c.nc * (c.bw + 1) * sizeof(double);
-  const bool smem = band_bytes <= kBandSmemMax;
-  if (smem) {
-    k_band_cholesky<true><<<1, 1024, band_bytes, s>>>(c.band, c.rdiag, c.nc, c.bw, c.derr);
-  } else {
-    k_band_cholesky<false><<<1, 1024, 0, s>>>(c.band, c.rdiag, c.nc, c.bw, c.derr);
-  }
-  MGAR_LAUNCH_CHECK();
-  MGAR_CUDA(cudaMemsetAsync(c.cinv, 0, (size_t)c.nc * c.nc * sizeof(double), s));
-  const size_t inv_smem = band_bytes + (size_t)8 * c.nc * sizeof(double);
-  if (smem && inv_smem <= kBandSmemMax)
-    k_band_inverse<true><<<(c.nc + 7) / 8, 256, inv_smem, s>>>(c.band, c.rdiag, c.nc, c.bw, c.cinv);
-  else
-    k_band_inverse<false><<<(c.nc + 7) / 8, 256, 0, s>>>(c.band, c.rdiag, c.nc, c.bw, c.cinv);
-  MGAR_LAUNCH_CHECK();
-  if (c.cinv_f) {
-    k_d2f<<<blocks_for((int64_t)c.nc * c.nc), kThreads, 0, s>>>(c.cinv, c.cinv_f, (int64_t)c.nc * c.nc);
-    MGAR_LAUNCH_CHECK();
-  }
+  coarse_factor<Real, DIM, typename CoarseT<Real>::T>(c, h[c.nl - 1].st, dcst);
 }
 
 void build_hierarchy(Ctx& c) {

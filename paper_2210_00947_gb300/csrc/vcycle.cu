@@ -341,23 +341,23 @@ __global__ void k_post_coarse(StencilOp<Real> op, const Real* __restrict__ xc,
 }
 
 // x = C b with the explicit inverse of the coarsest operator (FP64 sums).
-template <typename Real, bool CG>
-__device__ __forceinline__ void coarse_row(const double* __restrict__ cinv, const Real* __restrict__ b,
+template <typename Real, bool CG, typename M>
+__device__ __forceinline__ void coarse_row(const M* __restrict__ cinv, const Real* __restrict__ b,
                                            Real* __restrict__ x, int n, int row, int lane) {
-  double s = 0.0;
+  M s = M(0);
   for (int j = lane; j < n; j += 32)
-    if (CK((int64_t)row * n + j, (int64_t)n * n)) s += cinv[(int64_t)row * n + j] * (double)ldv<CG>(b + j);
+    if (CK((int64_t)row * n + j, (int64_t)n * n)) s += cinv[(int64_t)row * n + j] * (M)ldv<CG>(b + j);
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   if (lane == 0) x[row] = (Real)s;
 }
 
-template <typename Real>
-__global__ void k_coarse_solve(const double* __restrict__ cinv, const Real* __restrict__ b,
+template <typename Real, typename M>
+__global__ void k_coarse_solve(const M* __restrict__ cinv, const Real* __restrict__ b,
                                Real* __restrict__ x, int n) {
   pdl_wait();
   pdl_trigger();
   const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (row < n) coarse_row<Real, false>(cinv, b, x, n, row, threadIdx.x & 31);
+  if (row < n) coarse_row<Real, false, M>(cinv, b, x, n, row, threadIdx.x & 31);
 }
 
 // ------------------------------------------- bottom of the V-cycle, one cluster
@@ -377,7 +377,7 @@ struct BottomArgs {
   Real* x[kMaxLevels];
   Real* t[kMaxLevels];
   Real* r[kMaxLevels];
-  const double* cinv;
+  const typename CoarseT<Real>::T* cinv;
   int nc, lb, nl;
   Real omega;
 };
@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom(BottomArgs<Real> a) {
     const int l = a.nl - 1;
     const int warp = vt >> 5, nwarps = nthr >> 5, lane = threadIdx.x & 31;
     for (int row = warp; row < a.nc; row += nwarps)
-      coarse_row<Real, true>(a.cinv, a.b[l], a.x[l], a.nc, row, lane);
+      coarse_row<Real, true, typename CoarseT<Real>::T>(a.cinv, a.b[l], a.x[l], a.nc, row, lane);
   }
   const Real* res = a.x[a.nl - 1];
   for (int l = a.nl - 2; l >= a.lb; --l) {
@@ -507,7 +507,7 @@ static void launch_bottom(Ctx& c, int lb) {
     a.t[l] = h[l].t;
     a.r[l] = h[l].r;
   }
-  a.cinv = c.cinv;
+  a.cinv = CoarseT<Real>::inv(c);
   a.nc = c.nc;
   a.lb = lb;
   a.nl = c.nl;
@@ -619,8 +619,9 @@ static void vcycle_fused(Ctx& c, const Real* b0, Real* x0, bool zero_guess,
     // coarsest level
     const int l = nl - 1;
     const int rows_per_block = kThreads / 32;
-    k_coarse_solve<Real><<<(c.nc + rows_per_block - 1) / rows_per_block, kThreads, 0, c.stream>>>(
-        c.cinv, h[l].b, h[l].x, c.nc);
+    k_coarse_solve<Real, typename CoarseT<Real>::T>
+        <<<(c.nc + rows_per_block - 1) / rows_per_block, kThreads, 0, c.stream>>>(
+            CoarseT<Real>::inv(c), h[l].b, h[l].x, c.nc);
     MGAR_LAUNCH_CHECK_AT(level_site(5, l));
     res[l] = h[l].x;
   }
@@ -690,8 +691,9 @@ static void vcycle_dim(Ctx& c, const Real* b0, Real* x0, bool zero_guess) {
   {
     const int l = nl - 1;
     const int rows_per_block = kThreads / 32;
-    k_coarse_solve<Real><<<(c.nc + rows_per_block - 1) / rows_per_block, kThreads, 0, c.stream>>>(
-        c.cinv, h[l].b, h[l].x, c.nc);
+    k_coarse_solve<Real, typename CoarseT<Real>::T>
+        <<<(c.nc + rows_per_block - 1) / rows_per_block, kThreads, 0, c.stream>>>(
+            CoarseT<Real>::inv(c), h[l].b, h[l].x, c.nc);
     MGAR_LAUNCH_CHECK_AT(level_site(5, l));
   }
   // upward leg

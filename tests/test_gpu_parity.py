@@ -203,6 +203,31 @@ def test_sensitivity_matches_oracle(dims):
         np.testing.assert_allclose(host(dv), dv_ref, rtol=1e-13, atol=0)
 
 
+@pytest.mark.parametrize("dims,r", [((37, 23, 0), 1.5), ((13, 11, 9), 1.5), ((12, 10, 8), 2.2)])
+def test_mixed_filter_and_sensitivity_match_oracle(dims, r):
+    """Mixed path: filter + SIMP (Eq. 4, 6) and the sensitivities (Eq. 9-11)
+    run in double-float pairs (2^-46 relative per operation).  The filter
+    sums have terms of one sign; the element energy is a sum of squared
+    pair differences.  Rounding t to a pair moves a difference by up to
+    2^-47 |t|, which bounds the energy error as eps |t_e|^2 does in FP64."""
+    g, rho, fixed, q = make_problem(dims, mask="sink")
+    H, Hs = design.filter_matrix(g, r)
+    rho_phys = design.filter_forward(H, Hs, rho)
+    t = solvers.exact_solve(fem.system_matrix(g, rho_phys, fixed), q)
+    dc_ref, _ = design.sensitivities(g, H, Hs, rho_phys, t)
+    with solver_for(dims, fixed, q, rmin=r, nl=2, precision=mgar.MGAR_MIXED) as s:
+        s.set_density(dev(rho), physical=False)
+        dc = torch.empty(g.n_elems, dtype=torch.float64, device=DEV)
+        s.sensitivity(dev(t), dc, None)
+        te = t[g.element_nodes()]
+        eps_df = 2.0 ** -46
+        bound = 16 * eps_df * (3.0 * (1 - 1e-3)) * rho_phys ** 2 * (te * te).sum(axis=1)
+        atol = 10 * design.filter_transpose(H, Hs, bound)
+        got = host(dc)
+        assert np.all(np.abs(got - dc_ref) <= atol + 1e-12 * np.abs(dc_ref))
+        assert relerr(got, dc_ref) < 1e-9
+
+
 @pytest.mark.parametrize("dims", [(37, 23, 0), (13, 11, 9), (100, 100, 0)])
 def test_oc_matches_oracle(dims):
     g, rho, fixed, q = make_problem(dims, mask="sink")
