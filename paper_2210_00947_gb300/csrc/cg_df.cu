@@ -160,7 +160,27 @@ __global__ void k_df_cg_xr(float2* __restrict__ x, float2* __restrict__ r, const
   pdl_wait();
   const df alpha = df_from_double(*rz / *pap);
   df acc{0.f, 0.f};
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  const int stride = gridDim.x * blockDim.x;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  // two nodes per iteration: their eight loads are in flight together
+  for (; i + stride < n; i += 2 * stride) {
+    const int j = i + stride;
+    const float2 xa = x[i], xb = x[j], pa = p[i], pb = p[j];
+    const float2 ra = r[i], rb = r[j], qa = Ap[i], qb = Ap[j];
+    x[i] = pack(df_add(unpack(xa), df_mul(alpha, unpack(pa))));
+    x[j] = pack(df_add(unpack(xb), df_mul(alpha, unpack(pb))));
+    const df ria = df_sub(unpack(ra), df_mul(alpha, unpack(qa)));
+    const df rib = df_sub(unpack(rb), df_mul(alpha, unpack(qb)));
+    r[i] = pack(ria);
+    r[j] = pack(rib);
+    if (r32) {
+      r32[i] = __fadd_rn(ria.hi, ria.lo);
+      r32[j] = __fadd_rn(rib.hi, rib.lo);
+    }
+    acc = df_add(acc, df_mul(ria, ria));
+    acc = df_add(acc, df_mul(rib, rib));
+  }
+  for (; i < n; i += stride) {
     x[i] = pack(df_add(unpack(x[i]), df_mul(alpha, unpack(p[i]))));
     const df ri = df_sub(unpack(r[i]), df_mul(alpha, unpack(Ap[i])));
     r[i] = pack(ri);

@@ -17,10 +17,19 @@ namespace mgar {
 // ----------------------------------------------------------------- kernels
 __global__ void k_dot(const double* __restrict__ a, const double* __restrict__ b, int64_t n,
                       double* partials, unsigned int* counter, double* out) {
-  double v[1] = {0.0};
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    v[0] += a[i] * b[i];
+  // four independent partial sums per thread: four loads in flight, and no
+  // chain of dependent FP64 additions (fixed order, so still reproducible)
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  for (; i + 3 * stride < n; i += 4 * stride) {
+    s0 += a[i] * b[i];
+    s1 += a[i + stride] * b[i + stride];
+    s2 += a[i + 2 * stride] * b[i + 2 * stride];
+    s3 += a[i + 3 * stride] * b[i + 3 * stride];
+  }
+  for (; i < n; i += stride) s0 += a[i] * b[i];
+  double v[1] = {(s0 + s1) + (s2 + s3)};
   block_sum_finish<1>(v, partials, counter, out);
 }
 
