@@ -130,7 +130,7 @@ def max_over_ranks(x, world):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of the kernel as it stands; a kernel changed since its
 # capture has no entry (traffic null).
-TRAFFIC = {}
+TRAFFIC = {"df3d": 46.79e6}  # profiles/k_df3d_heat3d_128.md (steady DIR launch)
 
 def load_peaks():
     try:

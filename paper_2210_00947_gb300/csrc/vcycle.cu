@@ -647,10 +647,14 @@ static void vcycle_fused(Ctx& c, const Real* b0, Real* x0, bool zero_guess,
   }
 }
 
-// General Table 1 V-cycle (any numbers of pre- and post-sweeps).
+// General Table 1 V-cycle (any numbers of pre- and post-sweeps).  The fused
+// form is for the FP32 V-cycle: its kernels trade memory passes and launches
+// for recomputed arithmetic (the neighbours' smoothed values and
+// interpolations), which pays on the FP32 pipe and not at GB300's 1/58-rate
+// FP64, where the separate kernels below are faster.
 template <typename Real, int DIM>
 static void vcycle_dim(Ctx& c, const Real* b0, Real* x0, bool zero_guess) {
-  if (c.p.nu_pre == 1 && c.p.nu_post == 1 && c.nl >= 2 && !c.untiled) {
+  if (sizeof(Real) == 4 && c.p.nu_pre == 1 && c.p.nu_post == 1 && c.nl >= 2 && !c.untiled) {
     vcycle_fused<Real, DIM>(c, b0, x0, zero_guess);
     return;
   }
