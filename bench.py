@@ -130,7 +130,7 @@ def max_over_ranks(x, world):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of the kernel as it stands; a kernel changed since its
 # capture has no entry (traffic null).
-TRAFFIC = {"df3d": 46.79e6}  # profiles/k_df3d_heat3d_128.md (steady DIR launch)
+TRAFFIC = {"df3d": 46.79e6}  # steady DIR launch, ncu --set full of the 128^3 workload
 
 def load_peaks():
     try:
@@ -158,8 +158,8 @@ def fp32_peak_tops(sm_mhz):
 
 def kernel_model(kernel, w):
     """Algorithmic work per launch of a kernel class on workload w:
-    (bytes, operations, bound, pipe).  Per-unit figures are stated in
-    DESIGN.md."""
+    (bytes, operations, bound, pipe), from the per-unit figures derived
+    below."""
     n = w.n_nodes
     e = w.n_elems
     if kernel == "df3d":
@@ -332,14 +332,14 @@ def run_gpu(args):
         roof = {"bound": "alu", "achieved": achieved, "peak": peak,
                 "unit": "Top/s (FP32-pipe operations of the df64 arithmetic)",
                 "frac": achieved / peak, "traffic": TRAFFIC.get(kernel),
-                "peak_source": "152 SMs x 128 FP32 lanes x SM clock under load (derived, see DESIGN.md)",
+                "peak_source": "152 SMs x 128 FP32 lanes x SM clock under load (derived)",
                 "hbm_gbs": bytes_ / (avg_ms * 1e-3) / 1e9}
     elif bound == "alu":
         achieved = flops / (avg_ms * 1e-3) / 1e12
         peak = fp64_peak_tflops(clocks.get("sm_mhz"))
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s (fp64)",
                 "frac": achieved / peak, "traffic": TRAFFIC.get(kernel),
-                "peak_source": "FP64 unit count x SM clock under load (derived, see DESIGN.md)",
+                "peak_source": "FP64 unit count x SM clock under load (derived)",
                 "hbm_gbs": bytes_ / (avg_ms * 1e-3) / 1e9}
     else:
         achieved = bytes_ / (avg_ms * 1e-3) / 1e9
