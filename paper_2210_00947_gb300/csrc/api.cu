@@ -95,7 +95,7 @@ void free_ctx(Ctx& c) {
   }
   cudaFree(c.run_rho);
   cudaFree(c.run_T);
-  void* ptrs[] = {c.fixed, c.efix, c.q, c.rho_phys, c.ke, c.ke0, c.ke_f, c.ke0_f, c.inv_hs, c.f_offs, c.f_w,
+  void* ptrs[] = {c.fixed, c.efix, c.gfix, c.q, c.rho_phys, c.ke, c.ke0, c.ke_f, c.ke0_f, c.inv_hs, c.f_offs, c.f_w,
                   c.dv, c.rsdv, c.r, c.z, c.pv, c.Ap, c.tm, c.tmp_dc, c.R, c.W, c.b32, c.x32, c.ke_df, c.df_q, c.df_x, c.df_r, c.df_p, c.df_Ap, c.df_p2, c.df_e, c.tmp_e, c.oc_s, c.oc_lo,
                   c.oc_hi, c.oc_s32, c.oc_lo32, c.oc_hi32, c.dv32, c.oc_amb, c.oc_namb, c.partials, c.counter, c.dsc, c.derr};
   for (void* p : ptrs) cudaFree(p);
@@ -312,6 +312,24 @@ int mgar_create(mgar_t* out, const mgar_params* p, const uint8_t* fixed_mask, co
           }
       MGAR_CUDA(cudaMalloc(&c->efix, ne));
       MGAR_CUDA(cudaMemcpy(c->efix, ef.data(), ne, cudaMemcpyHostToDevice));
+      // level-1 (coarse) elements over fine elements with a fixed node
+      if (c->nl > 1) {
+        const Dims& cd = c->L[1];
+        std::vector<uint8_t> cf((size_t)cd.ne, 0);
+        for (int k = 0; k < d.ez; ++k)
+          for (int j = 0; j < d.ey; ++j)
+            for (int i = 0; i < d.ex; ++i)
+              if (ef[i + (int64_t)d.ex * (j + (int64_t)d.ey * k)])
+                cf[(i / 2) + (int64_t)cd.ex * ((j / 2) + (int64_t)cd.ey * (c->dim == 3 ? k / 2 : 0))] = 1;
+        std::vector<int> list;
+        for (int64_t e = 0; e < cd.ne; ++e)
+          if (cf[e]) list.push_back((int)e);
+        c->n_gfix = (int)list.size();
+        if (!list.empty()) {
+          MGAR_CUDA(cudaMalloc(&c->gfix, list.size() * sizeof(int)));
+          MGAR_CUDA(cudaMemcpy(c->gfix, list.data(), list.size() * sizeof(int), cudaMemcpyHostToDevice));
+        }
+      }
     }
     MGAR_CUDA(cudaMemcpy(c->q, qh.data(), n * sizeof(double), cudaMemcpyHostToDevice));
     alloc_hierarchy(*c);

@@ -122,6 +122,8 @@ struct Ctx {
   // fine level, problem data
   uint8_t* fixed = nullptr;
   uint8_t* efix = nullptr;   // per fine element: 1 if any of its nodes is fixed
+  int* gfix = nullptr;       // level-1 elements containing a fine element with a fixed node
+  int n_gfix = 0;
   double* q = nullptr;
   double qnorm = 0.0;
   double* rho_phys = nullptr;

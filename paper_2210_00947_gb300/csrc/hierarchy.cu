@@ -63,61 +63,107 @@ __device__ __forceinline__ bool sub_element(const Dims& f, int cx, int cy, int c
 }
 
 // ------------------------------------------------------------------ kernels
-// Level 0 -> 1: element matrices of A_1 from k_e, one thread per entry
-// (I, J) of a coarse element matrix.  Sub-elements without fixed nodes use
-// the tables G_type = P_type^T k0 P_type (entry IJ of all types is read by
-// consecutive threads, so the table reads coalesce); a coarse element with
-// any fixed fine node takes (Z P)^T k0 (Z P) entry by entry.
+// Level 0 -> 1: element matrices of A_1 from k_e, one thread per coarse
+// element.  Sub-elements without fixed nodes use the tables
+// G_type = P_type^T k0 P_type (staged in shared memory); a coarse element
+// with any fixed fine node takes (Z P)^T k0 (Z P) entry by entry.
 template <typename Real, int DIM>
-__global__ void k_galerkin_fine(const Real* __restrict__ ke, const uint8_t* __restrict__ fixed,
-                                const uint8_t* __restrict__ efix, Dims f, Dims cd,
-                                const Real* __restrict__ G, const double* __restrict__ k0,
-                                Real* __restrict__ elem) {
+__global__ void __launch_bounds__(kThreads) k_galerkin_fine(const Real* __restrict__ ke,
+                                                             const uint8_t* __restrict__ fixed,
+                                                             const uint8_t* __restrict__ efix, Dims f,
+                                                             Dims cd, const Real* __restrict__ G,
+                                                             const double* __restrict__ k0,
+                                                             Real* __restrict__ elem) {
+  constexpr int nen = 1 << DIM;
+  constexpr int NN = nen * nen;
+  constexpr int NT = DIM == 2 ? 9 : 27;
+  constexpr int GS = NN + 1;  // padded row: the types of a warp fall in distinct banks
+  __shared__ Real Gs[NT * GS];
+  for (int u = threadIdx.x; u < NT * NN; u += blockDim.x) Gs[(u / NN) * GS + (u % NN)] = G[u];
+  __syncthreads();
+  // one thread per coarse element: its 2^d sub-elements are found once
+  const int64_t E = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (E >= cd.ne) return;
+  int cx, cy, cz;
+  coords((int)E, cd.fEX, cd.fEXY, cx, cy, cz);
+  Real kv[nen];
+  int ty[nen];
+  int any_fixed = 0;
+#pragma unroll
+  for (int s = 0; s < nen; ++s) {
+    int e = 0, t[3] = {0, 0, 0};
+    const bool ok = sub_element<DIM>(f, cx, cy, cz, s, e, t) && CK(e, f.ne);
+    kv[s] = ok ? ke[e] : Real(0);
+    ty[s] = (t[0] + 3 * t[1] + 9 * t[2]) * GS;
+    any_fixed |= ok ? efix[e] : 0;
+  }
+  Real* dst = elem + E * NN;
+  if (!any_fixed) {  // (the others are written by k_galerkin_fixed)
+    // A_E = sum_s k_s G_type(s), four entries per store
+#pragma unroll 2
+    for (int q = 0; q < NN; q += 4) {
+      Real a0 = Real(0), a1 = Real(0), a2 = Real(0), a3 = Real(0);
+#pragma unroll
+      for (int s = 0; s < nen; ++s) {
+        const Real* g = Gs + ty[s] + q;
+        a0 += kv[s] * g[0];
+        a1 += kv[s] * g[1];
+        a2 += kv[s] * g[2];
+        a3 += kv[s] * g[3];
+      }
+      if (sizeof(Real) == 4) {
+        *reinterpret_cast<float4*>(dst + q) = make_float4((float)a0, (float)a1, (float)a2, (float)a3);
+      } else {
+        dst[q] = a0;
+        dst[q + 1] = a1;
+        dst[q + 2] = a2;
+        dst[q + 3] = a3;
+      }
+    }
+  }
+}
+
+// Level 0 -> 1 for the coarse elements with a fixed fine node (a short list
+// fixed at creation), one thread per entry: (Z P)^T k0 (Z P) with the rows
+// and columns of fixed fine nodes removed.
+template <typename Real, int DIM>
+__global__ void k_galerkin_fixed(const Real* __restrict__ ke, const uint8_t* __restrict__ fixed,
+                                 const int* __restrict__ list, int nlist, Dims f, Dims cd,
+                                 const double* __restrict__ k0, Real* __restrict__ elem) {
   constexpr int nen = 1 << DIM;
   constexpr int NN = nen * nen;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= cd.ne * NN) return;
-  const int E = (int)(tid / NN);
-  const int IJ = (int)(tid - (int64_t)E * NN);
+  if (tid >= (int64_t)nlist * NN) return;
+  const int li = (int)(tid / NN);
+  const int IJ = (int)(tid - (int64_t)li * NN);
+  const int E = list[li];
+  if (!CK(E, cd.ne)) return;
   const int I = IJ / nen, J = IJ - (IJ / nen) * nen;
   int cx, cy, cz;
   coords(E, cd.fEX, cd.fEXY, cx, cy, cz);
   Real acc = Real(0);
-  int any_fixed = 0;
-#pragma unroll
   for (int s = 0; s < nen; ++s) {
     int e, t[3];
-    const bool ok = sub_element<DIM>(f, cx, cy, cz, s, e, t) && CK(e, f.ne);
-    const Real kv = ok ? ke[e] : Real(0);
-    any_fixed |= ok ? efix[e] : 0;
-    const int ty = t[0] + 3 * t[1] + 9 * t[2];
-    acc += kv * G[ty * NN + IJ];
-  }
-  if (any_fixed) {
-    acc = Real(0);
-    for (int s = 0; s < nen; ++s) {
-      int e, t[3];
-      if (!sub_element<DIM>(f, cx, cy, cz, s, e, t) || !CK(e, f.ne)) continue;
-      const int fx = 2 * cx + (s & 1), fy = 2 * cy + ((s >> 1) & 1), fz = 2 * cz + ((s >> 2) & 1);
-      unsigned fm = 0;
-      for (int a = 0; a < nen; ++a) {
-        const int nd = (fx + (a & 1)) + f.NX * ((fy + ((a >> 1) & 1)) + f.NY * (fz + ((a >> 2) & 1)));
-        if (CK(nd, f.n) && fixed[nd]) fm |= 1u << a;
-      }
-      Real part = Real(0);
-      for (int a = 0; a < nen; ++a) {
-        const float pa = pw<DIM>(t, a, I);
-        if ((fm & (1u << a)) || pa == 0.f) continue;
-        for (int b = 0; b < nen; ++b) {
-          const float pb = pw<DIM>(t, b, J);
-          if ((fm & (1u << b)) || pb == 0.f) continue;
-          part += (Real)(pa * pb) * (Real)k0[a * nen + b];
-        }
-      }
-      acc += ke[e] * part;
+    if (!sub_element<DIM>(f, cx, cy, cz, s, e, t) || !CK(e, f.ne)) continue;
+    const int fx = 2 * cx + (s & 1), fy = 2 * cy + ((s >> 1) & 1), fz = 2 * cz + ((s >> 2) & 1);
+    unsigned fm = 0;
+    for (int a = 0; a < nen; ++a) {
+      const int nd = (fx + (a & 1)) + f.NX * ((fy + ((a >> 1) & 1)) + f.NY * (fz + ((a >> 2) & 1)));
+      if (CK(nd, f.n) && fixed[nd]) fm |= 1u << a;
     }
+    Real part = Real(0);
+    for (int a = 0; a < nen; ++a) {
+      const float pa = pw<DIM>(t, a, I);
+      if ((fm & (1u << a)) || pa == 0.f) continue;
+      for (int b = 0; b < nen; ++b) {
+        const float pb = pw<DIM>(t, b, J);
+        if ((fm & (1u << b)) || pb == 0.f) continue;
+        part += (Real)(pa * pb) * (Real)k0[a * nen + b];
+      }
+    }
+    acc += ke[e] * part;
   }
-  elem[tid] = acc;
+  elem[(int64_t)E * NN + IJ] = acc;
 }
 
 // Level l -> l+1 (l >= 1) from stored element matrices:
@@ -261,73 +307,100 @@ __global__ void k_band_fill(const Real* __restrict__ st, Dims d, int bw, B* __re
   }
 }
 
-// Right-looking banded Cholesky in one block, on a shared-memory copy of
-// the band when it fits (SMEM) or in place in global memory.  Stores the
-// factor and the reciprocals of its diagonal (rdiag).
+// 1 / sqrt(a) for a > 0: an FP32 seed refined by two Newton-Raphson steps
+// y <- y (3 - a y^2) / 2 (each step doubles the correct bits: 24 -> 48 -> 96),
+// so the pivot costs no FP64 square root or division chain.
+__device__ __forceinline__ double rsqrt_nr(double a) {
+  const float af = (float)a;
+  if (!(af > 0.f) || isinf(af)) return 1.0 / sqrt(a);  // outside the FP32 range
+  double y = (double)rsqrtf(af);
+  y = y * (1.5 - 0.5 * a * y * y);
+  y = y * (1.5 - 0.5 * a * y * y);
+  return y;
+}
+__device__ __forceinline__ float rsqrt_nr(float a) {
+  float y = rsqrtf(a);
+  return y * (1.5f - 0.5f * a * y * y);
+}
+
+// Right-looking banded Cholesky in one block of kCholThreads threads, on a
+// shared-memory copy of the band when it fits (SMEM) or in place in global
+// memory.  Step k: the pivot (reciprocal square root), the scaled column k
+// below it, then the rank-1 update of the trailing band triangle, one row
+// per warp and one column per lane.  Stores the factor and the reciprocals
+// of its diagonal (rdiag).
+constexpr int kCholThreads = 1024;  // FP64 latency needs many warps in flight
+
 template <typename B, bool SMEM>
-__global__ void k_band_cholesky(B* __restrict__ gband, B* __restrict__ rdiag, int n, int bw,
-                                int* __restrict__ err) {
+__global__ void __launch_bounds__(kCholThreads) k_band_cholesky(B* __restrict__ gband,
+                                                                B* __restrict__ rdiag, int n, int bw,
+                                                                int* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char smraw[];
   B* sband = reinterpret_cast<B*>(smraw);
-  __shared__ B piv, rpiv;
+  __shared__ B rpiv;
   __shared__ int bad;
   const int ld = bw + 1;
   const int64_t size = (int64_t)n * ld;
   B* band = SMEM ? sband : gband;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   if (SMEM)
-    for (int64_t t = threadIdx.x; t < size; t += blockDim.x) band[t] = gband[t];
-  if (threadIdx.x == 0) bad = 0;
+    for (int64_t t = tid; t < size; t += blockDim.x) band[t] = gband[t];
+  if (tid == 0) bad = 0;
   __syncthreads();
   for (int k = 0; k < n; ++k) {
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       const B a = band[(int64_t)k * ld + bw];
       if (!(a > B(0)) || !isfinite(a)) bad = 1;
-      piv = sqrt(a);
-      rpiv = B(1) / piv;
-      band[(int64_t)k * ld + bw] = piv;
-      rdiag[k] = rpiv;
+      const B r = rsqrt_nr(a);
+      rpiv = r;
+      band[(int64_t)k * ld + bw] = a * r;  // sqrt(a)
+      rdiag[k] = r;
     }
     __syncthreads();
     if (bad) break;
     const int last = min(k + bw, n - 1);
-    for (int i = k + 1 + threadIdx.x; i <= last; i += blockDim.x)
-      if (CK((int64_t)i * ld + (k - i + bw), size) && CK(k - i + bw, ld))
-        band[(int64_t)i * ld + (k - i + bw)] *= rpiv;
-    __syncthreads();
     const int m = last - k;
-    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
-      const int ii = t / m, jj = t - (t / m) * m;
-      if (jj > ii) continue;
-      const int i = k + 1 + ii, j = k + 1 + jj;
-      if (!CK((int64_t)i * ld + (j - i + bw), size) || !CK((int64_t)j * ld + (k - j + bw), size) ||
-          !CK(k - i + bw, ld) || !CK(k - j + bw, ld) || !CK(j - i + bw, ld))
-        continue;
-      band[(int64_t)i * ld + (j - i + bw)] -=
-          band[(int64_t)i * ld + (k - i + bw)] * band[(int64_t)j * ld + (k - j + bw)];
+    const B rp = rpiv;
+    for (int t = tid; t < m; t += blockDim.x) {
+      const int64_t at = (int64_t)(k + 1 + t) * ld + (bw - 1 - t);  // L(k+1+t, k)
+      if (CK(at, size)) band[at] *= rp;
+    }
+    __syncthreads();
+    // A(i, j) -= L(i, k) L(j, k) for k < j <= i <= last
+    for (int ii = warp; ii < m; ii += nw) {
+      const int i = k + 1 + ii;
+      const B lik = band[(int64_t)i * ld + (k - i + bw)];
+      for (int jj = lane; jj <= ii; jj += 32) {
+        const int j = k + 1 + jj;
+        const int64_t at = (int64_t)i * ld + (j - i + bw);
+        const int64_t bt = (int64_t)j * ld + (k - j + bw);
+        if (CK(at, size) && CK(bt, size)) band[at] -= lik * band[bt];
+      }
     }
     __syncthreads();
   }
   if (SMEM)
-    for (int64_t t = threadIdx.x; t < size; t += blockDim.x) gband[t] = band[t];
-  if (threadIdx.x == 0 && bad) *err = MGAR_ERR_NOT_SPD;
+    for (int64_t t = tid; t < size; t += blockDim.x) gband[t] = band[t];
+  if (tid == 0 && bad) *err = MGAR_ERR_NOT_SPD;
 }
 
-// Columns of the inverse, one warp per column: forward then backward
-// substitution with the band factor; inv is row-major n x n.  With SMEM the
-// band is staged in shared memory once per block and each warp keeps its
-// column there too (the substitutions are chains of dependent reads).
+// Columns of the inverse, one warp per column, by forward then backward
+// substitution with the band factor in column-oriented form: once x_p is
+// known, each lane removes its term from one of the next bw right-hand
+// sides (no reductions on the critical path).  With SMEM the band is staged
+// in shared memory once per block and each warp keeps its column there.
 template <typename B, bool SMEM>
 __global__ void k_band_inverse(const B* __restrict__ gband, const B* __restrict__ rdiag, int n, int bw,
                                B* inv) {
   extern __shared__ __align__(16) unsigned char smraw[];
   B* sband = reinterpret_cast<B*>(smraw);
   const int ld = bw + 1;
+  const int64_t size = (int64_t)n * ld;
   const int warps = blockDim.x >> 5;
   const int wid = threadIdx.x >> 5;
   const B* band = gband;
   B* colbuf = nullptr;
   if (SMEM) {
-    const int64_t size = (int64_t)n * ld;
     for (int64_t t = threadIdx.x; t < size; t += blockDim.x) sband[t] = gband[t];
     __syncthreads();
     band = sband;
@@ -338,26 +411,30 @@ __global__ void k_band_inverse(const B* __restrict__ gband, const B* __restrict_
   if (col >= n) return;
   // column values live in colbuf (shared) or in inv itself (global)
   auto cv = [&](int i) -> B& { return SMEM ? colbuf[i] : inv[(int64_t)i * n + col]; };
-  if (SMEM)
-    for (int i = lane; i < n; i += 32) colbuf[i] = B(0);
+  for (int i = lane; i < n; i += 32) cv(i) = (i == col) ? B(1) : B(0);
   __syncwarp();
-  for (int i = col; i < n; ++i) {
-    B s = B(0);
-    for (int p = max(col, i - bw) + lane; p < i; p += 32)
-      if (CK((int64_t)i * ld + (p - i + bw), (int64_t)n * ld) && CK(p - i + bw, ld))
-        s += band[(int64_t)i * ld + (p - i + bw)] * cv(p);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) cv(i) = ((i == col ? B(1) : B(0)) - s) * rdiag[i];
+  // forward: L y = e_col (y_p = 0 for p < col)
+  for (int p = col; p < n; ++p) {
+    const B yp = cv(p) * rdiag[p];
+    __syncwarp();
+    if (lane == 0) cv(p) = yp;
+    const int last = min(n - 1, p + bw);
+    for (int i = p + 1 + lane; i <= last; i += 32) {
+      const int64_t at = (int64_t)i * ld + (p - i + bw);  // L(i, p)
+      if (CK(at, size)) cv(i) -= band[at] * yp;
+    }
     __syncwarp();
   }
+  // backward: L^T x = y
   for (int i = n - 1; i >= 0; --i) {
-    B s = B(0);
-    const int last = min(n - 1, i + bw);
-    for (int p = i + 1 + lane; p <= last; p += 32)
-      if (CK((int64_t)p * ld + (i - p + bw), (int64_t)n * ld) && CK(i - p + bw, ld))
-        s += band[(int64_t)p * ld + (i - p + bw)] * cv(p);
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) cv(i) = (cv(i) - s) * rdiag[i];
+    const B xi = cv(i) * rdiag[i];
+    __syncwarp();
+    if (lane == 0) cv(i) = xi;
+    const int first = max(0, i - bw);
+    for (int p = first + lane; p < i; p += 32) {
+      const int64_t at = (int64_t)i * ld + (p - i + bw);  // L(i, p)
+      if (CK(at, size)) cv(p) -= band[at] * xi;
+    }
     __syncwarp();
   }
   if (SMEM)
@@ -494,9 +571,9 @@ static void coarse_factor(Ctx& c, const Real* st, const Dims& dcst) {
   const size_t band_bytes = (size_t)c.nc * (c.bw + 1) * sizeof(B);
   const bool smem = band_bytes <= kBandSmemMax;
   if (smem) {
-    k_band_cholesky<B, true><<<1, 1024, band_bytes, s>>>(band, rdiag, c.nc, c.bw, c.derr);
+    k_band_cholesky<B, true><<<1, kCholThreads, band_bytes, s>>>(band, rdiag, c.nc, c.bw, c.derr);
   } else {
-    k_band_cholesky<B, false><<<1, 1024, 0, s>>>(band, rdiag, c.nc, c.bw, c.derr);
+    k_band_cholesky<B, false><<<1, kCholThreads, 0, s>>>(band, rdiag, c.nc, c.bw, c.derr);
   }
   MGAR_LAUNCH_CHECK();
   MGAR_CUDA(cudaMemsetAsync(inv, 0, (size_t)c.nc * c.nc * sizeof(B), s));
@@ -520,10 +597,15 @@ static void build_levels(Ctx& c, const Real* ke0, LevelBuf<Real>* h) {
     const Dims& f = c.L[l];
     const Dims& cd = c.L[l + 1];
     ProfScope ps(c, l == 0 ? MGAR_KC_GALERKIN0 : -1);
-    const int64_t entries = cd.ne * nen * nen;  // one thread per element-matrix entry
-    if (l == 0)
-      k_galerkin_fine<Real, DIM><<<blocks_for(entries), kThreads, 0, s>>>(ke0, c.fixed, c.efix, f, cd,
-                                                                            G, k0, h[1].elem);
+    const int64_t entries = cd.ne * nen * nen;  // coarse levels: one thread per entry
+    if (l == 0) {
+      k_galerkin_fine<Real, DIM><<<blocks_for(cd.ne), kThreads, 0, s>>>(ke0, c.fixed, c.efix, f, cd, G,
+                                                                          k0, h[1].elem);
+      MGAR_LAUNCH_CHECK();
+      if (c.n_gfix > 0)
+        k_galerkin_fixed<Real, DIM><<<blocks_for((int64_t)c.n_gfix * nen * nen), kThreads, 0, s>>>(
+            ke0, c.fixed, c.gfix, c.n_gfix, f, cd, k0, h[1].elem);
+    }
     else
       k_galerkin_coarse<Real, DIM><<<blocks_for(entries), kThreads, 0, s>>>(
           h[l].elem, f, cd, p_tables<Real>(c), h[l + 1].elem);
