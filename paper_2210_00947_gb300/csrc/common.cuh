@@ -190,6 +190,7 @@ struct Ctx {
   int f3d_gz[2][4] = {};  // z runs of the tiled finest-level kernels [FP32, FP64][mode]
   int df3d_gz[3] = {};    // z runs of the tiled df64 operator kernels [mode]
   bool bottom_ok = false; // the V-cycle's bottom levels run as one cluster launch
+  int bottom_cluster = 8; // CTAs in that cluster
   bool use_pdl = true;    // programmatic dependent launch of the V-cycle and CG kernels
   cudaStream_t cap_stream = nullptr;
 

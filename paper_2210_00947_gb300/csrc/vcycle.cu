@@ -367,7 +367,7 @@ __global__ void k_coarse_solve(const M* __restrict__ cinv, const Real* __restric
 // on arrive, acquire on wait) separates the phases, so the small levels cost
 // no kernel launches and no waits of this code's own.
 constexpr int kBottomThreads = 512;
-constexpr int kBottomCluster = 8;
+constexpr int kBottomClusterMax = 16;  // non-portable cluster size, used when it fits
 
 template <typename Real>
 struct BottomArgs {
@@ -513,13 +513,13 @@ static void launch_bottom(Ctx& c, int lb) {
   a.nl = c.nl;
   a.omega = (Real)c.p.omega;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(kBottomCluster);
+  cfg.gridDim = dim3(c.bottom_cluster);
   cfg.blockDim = dim3(kBottomThreads);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = c.stream;
   cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = kBottomCluster;
+  attr[0].val.clusterDim.x = c.bottom_cluster;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -531,13 +531,19 @@ static void launch_bottom(Ctx& c, int lb) {
 }
 
 template <typename Real, int DIM>
-static bool bottom_fits() {
+static bool bottom_fits(int csize) {
+  if (csize > 8 &&
+      cudaFuncSetAttribute(k_bottom<Real, DIM>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+          cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(kBottomCluster);
+  cfg.gridDim = dim3(csize);
   cfg.blockDim = dim3(kBottomThreads);
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = kBottomCluster;
+  attr[0].val.clusterDim.x = csize;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
@@ -550,11 +556,15 @@ static bool bottom_fits() {
   return clusters >= 1;
 }
 
-// Whether the cluster kernel can run here (both precisions); call outside
+// Whether the cluster kernel can run here (FP32 V-cycle), and with how many
+// CTAs (16 if the device allows the non-portable size, else 8); call outside
 // stream capture.
 void bottom_prepare(Ctx& c) {
-  c.bottom_ok = c.dim == 2 ? (bottom_fits<float, 2>() && bottom_fits<double, 2>())
-                           : (bottom_fits<float, 3>() && bottom_fits<double, 3>());
+  c.bottom_ok = false;
+  for (int csize = kBottomClusterMax; csize >= 8 && !c.bottom_ok; csize /= 2) {
+    c.bottom_ok = c.dim == 2 ? bottom_fits<float, 2>(csize) : bottom_fits<float, 3>(csize);
+    if (c.bottom_ok) c.bottom_cluster = csize;
+  }
 }
 
 // Table 1 with one pre- and one post-sweep and a zero guess below the finest
