@@ -187,8 +187,10 @@ struct Ctx {
   GraphEntry graphs[kGraphs];
   bool use_graphs = true;
   bool untiled = false;  // MGAR_UNTILED=1: generic finest-level kernels (debugging aid)
-  int f3d_gz[2][4] = {};  // z runs of the tiled finest-level kernels [FP32, FP64][mode]
+  int f3d_gz[4] = {};     // z runs of the tiled finest-level kernels [mode]
+  int f3d_tile[4] = {};   // their tile shape [mode]: 0 = 32 x 8, 1 = 43 x 11 (POST 43 x 7)
   int df3d_gz[3] = {};    // z runs of the tiled df64 operator kernels [mode]
+  bool df3d_tile = false; // their tile: 32 x 8, or 43 x 11 when that leaves fewer lanes idle
   bool bottom_ok = false; // the V-cycle's bottom levels run as one cluster launch
   int bottom_cluster = 8; // CTAs in that cluster
   bool use_pdl = true;    // programmatic dependent launch of the V-cycle and CG kernels
@@ -301,13 +303,13 @@ inline int blocks_for(int64_t n, int threads = kThreads) {
 // ticket, and returns true with the totals in every thread.  Other blocks
 // return false.  Every thread of every block must call it.  The summation
 // order is fixed, so results are reproducible run to run.
-// Block, thread and grid given as linear ids (tid < nthr <= kThreads, a
-// multiple of 32; bid < nblk), so multi-dimensional launches can use it.
+// Block, thread and grid given as linear ids (tid < nthr <= 1024; a last
+// partial warp is fine; bid < nblk), so multi-dimensional launches can use it.
 template <int N>
 __device__ __forceinline__ bool block_sum_last_ids(double (&v)[N], double* partials,
                                                    unsigned int* counter, double (&total)[N],
                                                    int tid, int nthr, int bid, int nblk) {
-  __shared__ double sh[N][kThreads / 32];
+  __shared__ double sh[N][32];  // up to 1024 threads
   __shared__ double tot[N];
   __shared__ bool last;
   const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
@@ -671,9 +673,8 @@ void build_hierarchy(Ctx& c);      // K0 <- K, all levels, coarsest factor
 template <typename Real>
 void vcycle(Ctx& c, const Real* b, Real* x, bool zero_guess);
 // fine3d.cu: tiled finest-level 3D passes (mode 0 pre, 1 post, 2 residual, 3 sweep)
-template <typename Real>
-void fine3d(Ctx& c, int mode, const Real* ke, const Real* b, const Real* dinv, const Real* x,
-            const Real* xc, Real* out0, Real* out1, const float2* rdot = nullptr,
+void fine3d(Ctx& c, int mode, const float* ke, const float* b, const float* dinv, const float* x,
+            const float* xc, float* out0, float* out1, const float2* rdot = nullptr,
             double* dout = nullptr);
 // zero-guess FP32 V-cycle x = M b that also leaves r . x in *dout (r in
 // double-float pairs; 3D tiled path)

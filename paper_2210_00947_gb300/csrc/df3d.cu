@@ -102,23 +102,28 @@ __device__ __forceinline__ df wsum(df a, df b) {
 // Plane p and element layer p live in slot (p - kb + 1) & 3; the z loop is
 // unrolled by four, so every slot index is a compile-time constant and the
 // centre values of the planes in flight stay in registers.
-template <int MODE>
-__global__ void __launch_bounds__(NT, 4) k_df3d(DfArgs a) {
+template <int MODE, class T>
+__global__ void __launch_bounds__(T::NTB, T::NT <= 256 ? 4 : 2) k_df3d(DfArgs a) {
+  constexpr int TX = T::TX, TY = T::TY, NT = T::NT;
+  constexpr int XRING = T::XRING, KRING = T::KRING, KRING0 = T::KRING0;
   __shared__ float2 X[4][TY + 2][TX + 2];
   __shared__ float2 K[4][TY + 1][TX + 1];
   pdl_wait();  // one wave: the successor may be dispatched right away
   pdl_trigger();
 
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+  // 1D block of whole warps; threads past TX * TY only help with the ring
+  // loads and the reduction
+  const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+  const bool real = tid < NT;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const int kb = (int)(((int64_t)blockIdx.z * a.NZ) / a.gz);
   const int kend = (int)(((int64_t)(blockIdx.z + 1) * a.NZ) / a.gz);
   const int i = i0 + tx, j = j0 + ty;
-  const bool mine = i < a.NX && j < a.NY;
+  const bool mine = real && i < a.NX && j < a.NY;
   const bool xr = tid < XRING, kr = tid >= KRING0 && tid < KRING0 + KRING;
   int rxh = 0, ryh = 0, kxh = 0, kyh = 0;
-  if (xr) xring(tid, rxh, ryh);
-  if (kr) kring(tid - KRING0, kxh, kyh);
+  if (xr) T::xring(tid, rxh, ryh);
+  if (kr) T::kring(tid - KRING0, kxh, kyh);
   df beta{0.f, 0.f};
   if (MODE == DIR && !a.first) beta = df_from_double(*a.rz_new / *a.rz_old);
   const int NXY = a.NX * a.NY;
@@ -166,7 +171,7 @@ __global__ void __launch_bounds__(NT, 4) k_df3d(DfArgs a) {
   {                                                                                        \
     const df v = own.value(beta);                                                          \
     const float2 v2 = make_float2(v.hi, v.lo);                                             \
-    X[S][ty + 1][tx + 1] = (own.on && !own.f) ? v2 : make_float2(0.f, 0.f);                \
+    if (real) X[S][ty + 1][tx + 1] = (own.on && !own.f) ? v2 : make_float2(0.f, 0.f);      \
     cv[S] = v2;                                                                            \
     cf[S] = own.f != 0;                                                                    \
     cq[S] = ownq;                                                                          \
@@ -178,7 +183,7 @@ __global__ void __launch_bounds__(NT, 4) k_df3d(DfArgs a) {
   }
 #define D3D_FINISH_LAYER(S)                                                                \
   {                                                                                        \
-    K[S][ty + 1][tx + 1] = kown_on ? kown : make_float2(0.f, 0.f);                         \
+    if (real) K[S][ty + 1][tx + 1] = kown_on ? kown : make_float2(0.f, 0.f);               \
     if (kr) K[S][kyh][kxh] = kring_on ? kring_v : make_float2(0.f, 0.f);                   \
   }
 
@@ -263,16 +268,17 @@ __global__ void __launch_bounds__(NT, 4) k_df3d(DfArgs a) {
     double t[1];
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     const int nb = gridDim.x * gridDim.y * gridDim.z;
-    if (block_sum_last_ids<1>(v, a.partials, a.counter, t, tid, NT, bid, nb) && tid == 0) a.out[0] = t[0];
+    if (block_sum_last_ids<1>(v, a.partials, a.counter, t, tid, T::NTB, bid, nb) && tid == 0)
+      a.out[0] = t[0];
   }
 }
 
-template <int MODE>
+template <int MODE, class T>
 int runs_for(const Dims& d, int sms) {
   int per_sm = 0;
-  MGAR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_df3d<MODE>, NT, 0));
+  MGAR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_df3d<MODE, T>, T::NTB, 0));
   per_sm = std::max(per_sm, 1);
-  const int64_t cols = (int64_t)((d.NX + TX - 1) / TX) * ((d.NY + TY - 1) / TY);
+  const int64_t cols = (int64_t)((d.NX + T::TX - 1) / T::TX) * ((d.NY + T::TY - 1) / T::TY);
   const int64_t want = (int64_t)per_sm * sms;
   int64_t gz = std::max<int64_t>(1, (want + cols / 2) / cols);
   gz = std::min<int64_t>(gz, d.NZ);
@@ -297,13 +303,24 @@ DfArgs base_args(Ctx& c) {
   return a;
 }
 
-template <int MODE>
-void launch(Ctx& c, DfArgs& a) {
+template <int MODE, class T>
+void launch_t(Ctx& c, DfArgs& a) {
   const Dims& d = c.L[0];
   a.gz = std::max(1, std::min(c.df3d_gz[MODE], d.NZ));
-  const dim3 grid((d.NX + TX - 1) / TX, (d.NY + TY - 1) / TY, a.gz);
-  launch_pdl(c.stream, c.use_pdl, k_df3d<MODE>, grid, dim3(TX, TY), a);
+  const dim3 grid((d.NX + T::TX - 1) / T::TX, (d.NY + T::TY - 1) / T::TY, a.gz);
+  launch_pdl(c.stream, c.use_pdl, k_df3d<MODE, T>, grid, dim3(T::NTB), a);
   MGAR_LAUNCH_CHECK();
+}
+
+template <int MODE>
+void launch(Ctx& c, DfArgs& a) {
+  if (c.df3d_tile) launch_t<MODE, T43x11>(c, a);
+  else launch_t<MODE, T32x8>(c, a);
+}
+
+template <int MODE>
+int runs(const Ctx& c, int sms) {
+  return c.df3d_tile ? runs_for<MODE, T43x11>(c.L[0], sms) : runs_for<MODE, T32x8>(c.L[0], sms);
 }
 
 }  // namespace d3d
@@ -313,9 +330,11 @@ void df3d_prepare(Ctx& c) {
   int dev = 0, sms = 0;
   MGAR_CUDA(cudaGetDevice(&dev));
   MGAR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  c.df3d_gz[APPLY] = runs_for<APPLY>(c.L[0], sms);
-  c.df3d_gz[DIR] = runs_for<DIR>(c.L[0], sms);
-  c.df3d_gz[RESID] = runs_for<RESID>(c.L[0], sms);
+  const Dims& d = c.L[0];
+  c.df3d_tile = tile_use(d.NX, d.NY, T43x11::TX, T43x11::TY) > tile_use(d.NX, d.NY, T32x8::TX, T32x8::TY);
+  c.df3d_gz[APPLY] = runs<APPLY>(c, sms);
+  c.df3d_gz[DIR] = runs<DIR>(c, sms);
+  c.df3d_gz[RESID] = runs<RESID>(c, sms);
 }
 
 // y = A x; x . y into *dot when given

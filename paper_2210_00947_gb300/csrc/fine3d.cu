@@ -161,14 +161,25 @@ struct ElemFetch {
 // Plane slots are relative to the block's first plane: plane p lives in slot
 // (p - kb + 1) & 3, and so does element layer p.  The z loop is unrolled by
 // four, so every slot index is a compile-time constant.
-template <typename Real, int MODE>
-__global__ void __launch_bounds__(NT, sizeof(Real) == 4 ? (MODE == POST ? 3 : 4) : 2) k_fine3d(FineArgs a) {
-  __shared__ Real X[XS][TY + 2][TX + 2];
+// resident blocks per SM the registers are budgeted for (POST holds the
+// interpolation's coarse values and needs more)
+constexpr int f3d_minb(int mode, int nt) {
+  return mode == POST ? (nt <= 256 ? 3 : (nt <= 400 ? 2 : 1)) : (nt <= 256 ? 4 : 2);
+}
+
+template <typename Real, int MODE, class T>
+__global__ void __launch_bounds__(T::NTB, f3d_minb(MODE, T::NT)) k_fine3d(FineArgs a) {
+  constexpr int TX = T::TX, TY = T::TY, NT = T::NT;
+  constexpr int XRING = T::XRING, KRING = T::KRING, KRING0 = T::KRING0;
+  __shared__ Real X[4][TY + 2][TX + 2];
   __shared__ Real K[4][TY + 1][TX + 1];
   pdl_wait();  // one wave: the successor may be dispatched right away
   pdl_trigger();
 
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+  // 1D block of whole warps; threads past TX * TY only help with the ring
+  // loads and the reduction
+  const int tid = threadIdx.x, tx = tid % TX, ty = tid / TX;
+  const bool real = tid < NT;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const int kb = (int)(((int64_t)blockIdx.z * a.NZ) / a.gz);
   const int kend = (int)(((int64_t)(blockIdx.z + 1) * a.NZ) / a.gz);
@@ -176,9 +187,9 @@ __global__ void __launch_bounds__(NT, sizeof(Real) == 4 ? (MODE == POST ? 3 : 4)
   const Real om = (Real)a.omega;
   const bool xr = tid < XRING, kr = tid >= KRING0 && tid < KRING0 + KRING;
   int rxh = 0, ryh = 0, kxh = 0, kyh = 0;
-  if (xr) xring(tid, rxh, ryh);
-  if (kr) kring(tid - KRING0, kxh, kyh);
-  const bool mine = i < a.NX && j < a.NY;
+  if (xr) T::xring(tid, rxh, ryh);
+  if (kr) T::kring(tid - KRING0, kxh, kyh);
+  const bool mine = real && i < a.NX && j < a.NY;
   const int NXY = a.NX * a.NY;
 
   const Column ocol = make_column(a, i, j, MODE == POST);
@@ -217,7 +228,7 @@ __global__ void __launch_bounds__(NT, sizeof(Real) == 4 ? (MODE == POST ? 3 : 4)
 
 #define F3D_FINISH(S)                                                  \
   {                                                                    \
-    X[S][ty + 1][tx + 1] = own.masked(om, ocol.hxy);                   \
+    if (real) X[S][ty + 1][tx + 1] = own.masked(om, ocol.hxy);         \
     cv[S] = own.value(om, ocol.hxy);                                   \
     cb[S] = MODE == PRE ? own.v0 : ownb;                               \
     cd[S] = ownd;                                                      \
@@ -226,7 +237,7 @@ __global__ void __launch_bounds__(NT, sizeof(Real) == 4 ? (MODE == POST ? 3 : 4)
   }
 #define F3D_FINISH_LAYER(S)                                            \
   {                                                                    \
-    K[S][ty + 1][tx + 1] = kown.get();                                 \
+    if (real) K[S][ty + 1][tx + 1] = kown.get();                       \
     if (kr) K[S][kyh][kxh] = kring_.get();                             \
   }
 
@@ -315,18 +326,19 @@ __global__ void __launch_bounds__(NT, sizeof(Real) == 4 ? (MODE == POST ? 3 : 4)
     double t[1];
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     const int nb = gridDim.x * gridDim.y * gridDim.z;
-    if (block_sum_last_ids<1>(v, a.partials, a.counter, t, tid, NT, bid, nb) && tid == 0) a.dout[0] = t[0];
+    if (block_sum_last_ids<1>(v, a.partials, a.counter, t, tid, T::NTB, bid, nb) && tid == 0)
+      a.dout[0] = t[0];
   }
 }
 
 // z runs so that the grid fills the GPU once: resident blocks per SM x SMs,
 // split over the column tiles
-template <typename Real, int MODE>
+template <typename Real, int MODE, class T>
 int runs_for(const Dims& d, int sms) {
   int per_sm = 0;
-  MGAR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fine3d<Real, MODE>, NT, 0));
+  MGAR_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fine3d<Real, MODE, T>, T::NTB, 0));
   per_sm = std::max(per_sm, 1);
-  const int64_t cols = (int64_t)((d.NX + TX - 1) / TX) * ((d.NY + TY - 1) / TY);
+  const int64_t cols = (int64_t)((d.NX + T::TX - 1) / T::TX) * ((d.NY + T::TY - 1) / T::TY);
   const int64_t want = (int64_t)per_sm * sms;
   const int64_t gz = std::max<int64_t>(1, (want + cols / 2) / cols);
   return (int)std::min<int64_t>(gz, d.NZ);
@@ -334,27 +346,41 @@ int runs_for(const Dims& d, int sms) {
 
 }  // namespace f3d
 
+// Tile per mode: the shape with the most busy lanes on this grid (POST, which
+// holds more registers, takes the 43 x 7 tile instead of 43 x 11).
 void fine3d_prepare(Ctx& c) {
   using namespace f3d;
   int dev = 0, sms = 0;
   MGAR_CUDA(cudaGetDevice(&dev));
   MGAR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const Dims& d = c.L[0];
-  c.f3d_gz[0][PRE] = runs_for<float, PRE>(d, sms);
-  c.f3d_gz[0][POST] = runs_for<float, POST>(d, sms);
-  c.f3d_gz[0][RESID] = runs_for<float, RESID>(d, sms);
-  c.f3d_gz[0][SWEEP] = runs_for<float, SWEEP>(d, sms);
-  c.f3d_gz[1][PRE] = runs_for<double, PRE>(d, sms);
-  c.f3d_gz[1][POST] = runs_for<double, POST>(d, sms);
-  c.f3d_gz[1][RESID] = runs_for<double, RESID>(d, sms);
-  c.f3d_gz[1][SWEEP] = runs_for<double, SWEEP>(d, sms);
+  for (int mode = 0; mode < 4; ++mode) {
+    const bool post = mode == POST;
+    const double u0 = tile_use(d.NX, d.NY, T32x8::TX, T32x8::TY);
+    const double u1 = post ? tile_use(d.NX, d.NY, T43x7::TX, T43x7::TY)
+                           : tile_use(d.NX, d.NY, T43x11::TX, T43x11::TY);
+    c.f3d_tile[mode] = u1 > u0 ? 1 : 0;
+  }
+  c.f3d_gz[PRE] = c.f3d_tile[PRE] ? runs_for<float, PRE, T43x11>(d, sms) : runs_for<float, PRE, T32x8>(d, sms);
+  c.f3d_gz[POST] = c.f3d_tile[POST] ? runs_for<float, POST, T43x7>(d, sms) : runs_for<float, POST, T32x8>(d, sms);
+  c.f3d_gz[RESID] = c.f3d_tile[RESID] ? runs_for<float, RESID, T43x11>(d, sms) : runs_for<float, RESID, T32x8>(d, sms);
+  c.f3d_gz[SWEEP] = c.f3d_tile[SWEEP] ? runs_for<float, SWEEP, T43x11>(d, sms) : runs_for<float, SWEEP, T32x8>(d, sms);
 }
 
-// Launch one tiled finest-level pass (3D only).  mode: 0 pre, 1 post,
-// 2 residual, 3 sweep.
-template <typename Real>
-void fine3d(Ctx& c, int mode, const Real* ke, const Real* b, const Real* dinv, const Real* x,
-            const Real* xc, Real* out0, Real* out1, const float2* rdot, double* dout) {
+namespace f3d {
+template <int MODE, class T>
+void launch(Ctx& c, FineArgs& a) {
+  const Dims& d = c.L[0];
+  a.gz = std::max(1, std::min(c.f3d_gz[MODE], d.NZ));
+  const dim3 grid((d.NX + T::TX - 1) / T::TX, (d.NY + T::TY - 1) / T::TY, a.gz);
+  launch_pdl(c.stream, c.use_pdl, k_fine3d<float, MODE, T>, grid, dim3(T::NTB), a);
+}
+}  // namespace f3d
+
+// Launch one tiled finest-level pass of the FP32 V-cycle (3D only).
+// mode: 0 pre, 1 post, 2 residual, 3 sweep.
+void fine3d(Ctx& c, int mode, const float* ke, const float* b, const float* dinv, const float* x,
+            const float* xc, float* out0, float* out1, const float2* rdot, double* dout) {
   using namespace f3d;
   const Dims& d = c.L[0];
   FineArgs a;
@@ -380,21 +406,14 @@ void fine3d(Ctx& c, int mode, const Real* ke, const Real* b, const Real* dinv, c
   a.dout = dout;
   a.partials = c.partials;
   a.counter = c.counter;
-  const dim3 block(TX, TY);
-  const int gx = (d.NX + TX - 1) / TX, gy = (d.NY + TY - 1) / TY;
-  a.gz = std::max(1, std::min(c.f3d_gz[sizeof(Real) == 8][mode & 3], d.NZ));
-  const dim3 grid(gx, gy, a.gz);
+  const bool big = c.f3d_tile[mode & 3] != 0;
   switch (mode) {
-    case PRE: launch_pdl(c.stream, c.use_pdl, k_fine3d<Real, PRE>, grid, block, a); break;
-    case POST: launch_pdl(c.stream, c.use_pdl, k_fine3d<Real, POST>, grid, block, a); break;
-    case RESID: launch_pdl(c.stream, c.use_pdl, k_fine3d<Real, RESID>, grid, block, a); break;
-    default: launch_pdl(c.stream, c.use_pdl, k_fine3d<Real, SWEEP>, grid, block, a); break;
+    case PRE: big ? launch<PRE, T43x11>(c, a) : launch<PRE, T32x8>(c, a); break;
+    case POST: big ? launch<POST, T43x7>(c, a) : launch<POST, T32x8>(c, a); break;
+    case RESID: big ? launch<RESID, T43x11>(c, a) : launch<RESID, T32x8>(c, a); break;
+    default: big ? launch<SWEEP, T43x11>(c, a) : launch<SWEEP, T32x8>(c, a); break;
   }
   MGAR_LAUNCH_CHECK_AT(level_site(6 + (mode == PRE ? 0 : mode == POST ? 1 : mode == SWEEP ? 2 : 3), 0));
 }
-template void fine3d<float>(Ctx&, int, const float*, const float*, const float*, const float*,
-                            const float*, float*, float*, const float2*, double*);
-template void fine3d<double>(Ctx&, int, const double*, const double*, const double*, const double*,
-                             const double*, double*, double*, const float2*, double*);
 
 }  // namespace mgar

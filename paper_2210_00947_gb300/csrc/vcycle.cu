@@ -571,9 +571,10 @@ void bottom_prepare(Ctx& c) {
 // level: per level one fused pre kernel (smooth from zero + residual), the
 // restriction, and one fused post kernel (interpolation + smooth); the small
 // levels at the bottom run in one cluster launch.
-template <typename Real, int DIM>
-static void vcycle_fused(Ctx& c, const Real* b0, Real* x0, bool zero_guess,
+template <int DIM>
+static void vcycle_fused(Ctx& c, const float* b0, float* x0, bool zero_guess,
                          const float2* rdot = nullptr, double* dout = nullptr) {
+  using Real = float;
   LevelBuf<Real>* h = levels<Real>(c);
   const int nl = c.nl;
   const Real om = (Real)c.p.omega;
@@ -585,10 +586,10 @@ static void vcycle_fused(Ctx& c, const Real* b0, Real* x0, bool zero_guess,
     ProfScope ps(c, MGAR_KC_SMOOTH0);
     if (DIM == 3) {
       if (zero_guess) {
-        fine3d<Real>(c, 0, ref_ke<Real>(c), b0, h[0].dinv, nullptr, nullptr, h[0].t, h[0].r);
+        fine3d(c, 0, ref_ke<Real>(c), b0, h[0].dinv, nullptr, nullptr, h[0].t, h[0].r);
       } else {
-        fine3d<Real>(c, 3, ref_ke<Real>(c), b0, h[0].dinv, x0, nullptr, h[0].t, nullptr);
-        fine3d<Real>(c, 2, ref_ke<Real>(c), b0, h[0].dinv, h[0].t, nullptr, h[0].r, nullptr);
+        fine3d(c, 3, ref_ke<Real>(c), b0, h[0].dinv, x0, nullptr, h[0].t, nullptr);
+        fine3d(c, 2, ref_ke<Real>(c), b0, h[0].dinv, h[0].t, nullptr, h[0].r, nullptr);
       }
       cur0 = h[0].t;
     } else {
@@ -647,7 +648,7 @@ static void vcycle_fused(Ctx& c, const Real* b0, Real* x0, bool zero_guess,
   // finest level, post
   ProfScope ps(c, MGAR_KC_SMOOTH0);
   if (DIM == 3) {
-    fine3d<Real>(c, 1, ref_ke<Real>(c), b0, h[0].dinv, cur0, res[1], x0, nullptr, rdot, dout);
+    fine3d(c, 1, ref_ke<Real>(c), b0, h[0].dinv, cur0, res[1], x0, nullptr, rdot, dout);
   } else {
     // interpolation in place on the pre-smoothed iterate, then the sweep into x0
     k_prolong<Real, DIM><<<blocks_for(d0.n), kThreads, 0, c.stream>>>(res[1], cur0, cur0, d0, c.L[1],
@@ -664,9 +665,11 @@ static void vcycle_fused(Ctx& c, const Real* b0, Real* x0, bool zero_guess,
 // FP64, where the separate kernels below are faster.
 template <typename Real, int DIM>
 static void vcycle_dim(Ctx& c, const Real* b0, Real* x0, bool zero_guess) {
-  if (sizeof(Real) == 4 && c.p.nu_pre == 1 && c.p.nu_post == 1 && c.nl >= 2 && !c.untiled) {
-    vcycle_fused<Real, DIM>(c, b0, x0, zero_guess);
-    return;
+  if constexpr (sizeof(Real) == 4) {
+    if (c.p.nu_pre == 1 && c.p.nu_post == 1 && c.nl >= 2 && !c.untiled) {
+      vcycle_fused<DIM>(c, b0, x0, zero_guess);
+      return;
+    }
   }
   LevelBuf<Real>* h = levels<Real>(c);
   const int nl = c.nl;
@@ -742,7 +745,7 @@ template void vcycle<float>(Ctx&, const float*, float*, bool);
 void vcycle_dot(Ctx& c, const float* b, float* x, const float2* r, double* dout) {
   require(c.dim == 3 && c.p.nu_pre == 1 && c.p.nu_post == 1 && c.nl >= 2 && !c.untiled, MGAR_ERR_ARG,
           "fused r.z V-cycle needs the tiled 3D path");
-  vcycle_fused<float, 3>(c, b, x, true, r, dout);
+  vcycle_fused<3>(c, b, x, true, r, dout);
 }
 
 template <typename Real, int DIM>
