@@ -188,12 +188,15 @@ struct Ctx {
   bool use_graphs = true;
   bool untiled = false;  // MGAR_UNTILED=1: generic finest-level kernels (debugging aid)
   int f3d_gz[4] = {};     // z runs of the tiled finest-level kernels [mode]
-  int f3d_tile[4] = {};   // their tile shape [mode]: 0 = 32 x 8, 1 = 43 x 11 (POST 43 x 7)
   int df3d_gz[3] = {};    // z runs of the tiled df64 operator kernels [mode]
   bool df3d_tile = false; // their tile: 32 x 8, or 43 x 11 when that leaves fewer lanes idle
   bool bottom_ok = false; // the V-cycle's bottom levels run as one cluster launch
   int bottom_cluster = 8; // CTAs in that cluster
   bool use_pdl = true;    // programmatic dependent launch of the V-cycle and CG kernels
+  // finest post-smoothing as a thin interpolation pass + the tiled sweep
+  // (faster than interpolating inside the tiled pass: 6.67 vs 6.83 ms per
+  // design cycle at 128^3); MGAR_FUSED_POST=1 selects the fused pass
+  bool split_post = true;
   cudaStream_t cap_stream = nullptr;
 
   // instrumentation: CUDA-event timing of one kernel class

@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(T::NTB, f3d_minb(MODE, T::NT)) k_fine3d(FineAr
   // for the fused r . x')
   Real cv[4], cb[4], cd[4];
   bool cf[4];
-  const bool rdot = MODE == POST && a.dout != nullptr;
+  const bool rdot = (MODE == POST || MODE == SWEEP) && a.dout != nullptr;
   df dacc{0.f, 0.f};
 
   auto issue_plane = [&](int p) {
@@ -346,25 +346,20 @@ int runs_for(const Dims& d, int sms) {
 
 }  // namespace f3d
 
-// Tile per mode: the shape with the most busy lanes on this grid (POST, which
-// holds more registers, takes the 43 x 7 tile instead of 43 x 11).
+// The finest-level V-cycle kernels keep the 32 x 8 tile: a wider tile has
+// fewer idle lanes on 129-node planes but, at one wave, a longer chain of
+// plane steps per block, which costs more in these latency-bound passes
+// (measured: pre 23.6 vs 25.5 us, post 37 vs 47 us on 129^3).
 void fine3d_prepare(Ctx& c) {
   using namespace f3d;
   int dev = 0, sms = 0;
   MGAR_CUDA(cudaGetDevice(&dev));
   MGAR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const Dims& d = c.L[0];
-  for (int mode = 0; mode < 4; ++mode) {
-    const bool post = mode == POST;
-    const double u0 = tile_use(d.NX, d.NY, T32x8::TX, T32x8::TY);
-    const double u1 = post ? tile_use(d.NX, d.NY, T43x7::TX, T43x7::TY)
-                           : tile_use(d.NX, d.NY, T43x11::TX, T43x11::TY);
-    c.f3d_tile[mode] = u1 > u0 ? 1 : 0;
-  }
-  c.f3d_gz[PRE] = c.f3d_tile[PRE] ? runs_for<float, PRE, T43x11>(d, sms) : runs_for<float, PRE, T32x8>(d, sms);
-  c.f3d_gz[POST] = c.f3d_tile[POST] ? runs_for<float, POST, T43x7>(d, sms) : runs_for<float, POST, T32x8>(d, sms);
-  c.f3d_gz[RESID] = c.f3d_tile[RESID] ? runs_for<float, RESID, T43x11>(d, sms) : runs_for<float, RESID, T32x8>(d, sms);
-  c.f3d_gz[SWEEP] = c.f3d_tile[SWEEP] ? runs_for<float, SWEEP, T43x11>(d, sms) : runs_for<float, SWEEP, T32x8>(d, sms);
+  c.f3d_gz[PRE] = runs_for<float, PRE, T32x8>(d, sms);
+  c.f3d_gz[POST] = runs_for<float, POST, T32x8>(d, sms);
+  c.f3d_gz[RESID] = runs_for<float, RESID, T32x8>(d, sms);
+  c.f3d_gz[SWEEP] = runs_for<float, SWEEP, T32x8>(d, sms);
 }
 
 namespace f3d {
@@ -406,12 +401,11 @@ void fine3d(Ctx& c, int mode, const float* ke, const float* b, const float* dinv
   a.dout = dout;
   a.partials = c.partials;
   a.counter = c.counter;
-  const bool big = c.f3d_tile[mode & 3] != 0;
   switch (mode) {
-    case PRE: big ? launch<PRE, T43x11>(c, a) : launch<PRE, T32x8>(c, a); break;
-    case POST: big ? launch<POST, T43x7>(c, a) : launch<POST, T32x8>(c, a); break;
-    case RESID: big ? launch<RESID, T43x11>(c, a) : launch<RESID, T32x8>(c, a); break;
-    default: big ? launch<SWEEP, T43x11>(c, a) : launch<SWEEP, T32x8>(c, a); break;
+    case PRE: launch<PRE, T32x8>(c, a); break;
+    case POST: launch<POST, T32x8>(c, a); break;
+    case RESID: launch<RESID, T32x8>(c, a); break;
+    default: launch<SWEEP, T32x8>(c, a); break;
   }
   MGAR_LAUNCH_CHECK_AT(level_site(6 + (mode == PRE ? 0 : mode == POST ? 1 : mode == SWEEP ? 2 : 3), 0));
 }

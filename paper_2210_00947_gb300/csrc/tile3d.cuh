@@ -6,9 +6,9 @@
 // threads) and by the next warps (layers, KRING threads from KRING0).
 //
 // The tile width need not be a multiple of 32 (warps then span two rows):
-// the host picks, per grid, the instantiated shape with the fewest idle
-// lanes, e.g. 43 x 11 for 129 x 129 node planes (3 x 12 tiles, 96 % of the
-// lanes busy) instead of 32 x 8 (5 x 17 tiles, 77 %).
+// the df64 operator picks, per grid, the shape with the fewest idle lanes,
+// e.g. 43 x 11 for 129 x 129 node planes (3 x 12 tiles, 96 % of the lanes
+// busy) instead of 32 x 8 (5 x 17 tiles, 77 %).
 #pragma once
 
 namespace mgar {
@@ -39,7 +39,6 @@ struct Tile {
 
 using T32x8 = Tile<32, 8>;
 using T43x11 = Tile<43, 11>;
-using T43x7 = Tile<43, 7>;
 
 // Fraction of busy lanes of a TX x TY tiling of an NX x NY node plane.
 inline double tile_use(int NX, int NY, int TX, int TY) {

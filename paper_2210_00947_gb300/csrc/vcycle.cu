@@ -163,6 +163,8 @@ __global__ void k_restrict(const Real* __restrict__ r, Real* __restrict__ bc, Di
 template <typename Real, int DIM>
 __global__ void k_prolong(const Real* __restrict__ xc, const Real* cur, Real* dst, Dims f, Dims cd,
                           const uint8_t* __restrict__ fixed) {
+  pdl_wait();
+  pdl_trigger();
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= f.n) return;
   if (fixed && fixed[idx]) {
@@ -647,8 +649,14 @@ static void vcycle_fused(Ctx& c, const float* b0, float* x0, bool zero_guess,
   }
   // finest level, post
   ProfScope ps(c, MGAR_KC_SMOOTH0);
-  if (DIM == 3) {
+  if (DIM == 3 && !c.split_post) {
     fine3d(c, 1, ref_ke<Real>(c), b0, h[0].dinv, cur0, res[1], x0, nullptr, rdot, dout);
+  } else if (DIM == 3) {
+    // interpolation in place on the pre-smoothed iterate, then the tiled sweep
+    launch_pdl(c.stream, c.use_pdl, k_prolong<Real, DIM>, dim3(blocks_for(d0.n)), dim3(kThreads),
+               (const Real*)res[1], (const Real*)cur0, cur0, d0, c.L[1], (const uint8_t*)c.fixed);
+    MGAR_LAUNCH_CHECK_AT(level_site(4, 0));
+    fine3d(c, 3, ref_ke<Real>(c), b0, h[0].dinv, cur0, nullptr, x0, nullptr, rdot, dout);
   } else {
     // interpolation in place on the pre-smoothed iterate, then the sweep into x0
     k_prolong<Real, DIM><<<blocks_for(d0.n), kThreads, 0, c.stream>>>(res[1], cur0, cur0, d0, c.L[1],
