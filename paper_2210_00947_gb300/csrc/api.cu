@@ -344,6 +344,7 @@ int mgar_create(mgar_t* out, const mgar_params* p, const uint8_t* fixed_mask, co
     bottom_prepare(*c);
     if (const char* np = std::getenv("MGAR_NO_PDL")) c->use_pdl = np[0] != '1';
     if (const char* fp = std::getenv("MGAR_FUSED_POST")) c->split_post = fp[0] != '1';
+    if (const char* sc = std::getenv("MGAR_SPLIT_COARSE")) c->split_coarse_nodes = std::atoll(sc);
     if (const char* nb = std::getenv("MGAR_NO_CLUSTER")) c->bottom_ok = c->bottom_ok && nb[0] != '1';
     if (c->dim == 3) {
       fine3d_prepare(*c);

@@ -197,6 +197,9 @@ struct Ctx {
   // (faster than interpolating inside the tiled pass: 6.67 vs 6.83 ms per
   // design cycle at 128^3); MGAR_FUSED_POST=1 selects the fused pass
   bool split_post = true;
+  // coarse levels above this many nodes post-smooth as interpolation + sweep
+  // (the 65^3 level of a 128^3 grid: 6.60 vs 6.66 ms per design cycle)
+  int64_t split_coarse_nodes = 100000;
   cudaStream_t cap_stream = nullptr;
 
   // instrumentation: CUDA-event timing of one kernel class

@@ -641,10 +641,18 @@ static void vcycle_fused(Ctx& c, const float* b0, float* x0, bool zero_guess,
   // coarse levels, up
   for (int l = std::min(nl - 2, lb - 1); l >= 1; --l) {
     const Dims& d = c.L[l];
-    launch_pdl(c.stream, c.use_pdl, k_post_coarse<Real, DIM>, dim3(blocks_for(d.n)), dim3(kThreads),
-               stencil_row<Real, DIM>(c, l).op, res[l + 1], (const Real*)h[l].x,
-               (const Real*)h[l].b, (const Real*)h[l].dinv, om, h[l].t, d, c.L[l + 1]);
-    MGAR_LAUNCH_CHECK_AT(level_site(4, l));
+    if (d.n > c.split_coarse_nodes) {
+      // large level: thin interpolation in place on x_l, then the sweep into t_l
+      launch_pdl(c.stream, c.use_pdl, k_prolong<Real, DIM>, dim3(blocks_for(d.n)), dim3(kThreads),
+                 res[l + 1], (const Real*)h[l].x, h[l].x, d, c.L[l + 1], (const uint8_t*)nullptr);
+      MGAR_LAUNCH_CHECK_AT(level_site(4, l));
+      sweep<Real, DIM>(c, l, h[l].b, h[l].x, h[l].t);
+    } else {
+      launch_pdl(c.stream, c.use_pdl, k_post_coarse<Real, DIM>, dim3(blocks_for(d.n)),
+                 dim3(kThreads), stencil_row<Real, DIM>(c, l).op, res[l + 1], (const Real*)h[l].x,
+                 (const Real*)h[l].b, (const Real*)h[l].dinv, om, h[l].t, d, c.L[l + 1]);
+      MGAR_LAUNCH_CHECK_AT(level_site(4, l));
+    }
     res[l] = h[l].t;
   }
   // finest level, post
