@@ -198,8 +198,9 @@ int mgar_run(mgar_t h, const double* rho_host, int cycles, double* rho_out_host,
 
 /* Instrumentation (no counterpart in the paper).  Kernel classes whose
  * launches can be timed with CUDA events on the handle's stream: */
-#define MGAR_KC_APPLY64 1 /* FP64 finest-level K x (CG matvec, MGAR projection) */
-#define MGAR_KC_SMOOTH0 2 /* finest-level damped-Jacobi sweep (any precision) */
+#define MGAR_KC_APPLY64 1 /* finest-level K x of the outer CG and the MGAR projection:
+                             FP64, or double-float (df64) in the mixed path */
+#define MGAR_KC_SMOOTH0 2 /* finest-level smoothing passes of the V-cycle (any precision) */
 #define MGAR_KC_RESID0 3  /* finest-level residual inside the V-cycle */
 #define MGAR_KC_OC 4      /* OC bisection pass */
 #define MGAR_KC_GALERKIN0 5 /* Galerkin element matrices of level 1 */
