@@ -254,12 +254,14 @@ DfOp make_op(Ctx& c) {
 void apply_df64(Ctx& c, const double* x, double* y) {
   const int n = (int)c.n;
   ProfScope ps(c, MGAR_KC_APPLY64);
+  if (c.dim == 3 && !c.untiled) {
+    df3d_apply(c, x, y, nullptr);  // FP64 in and out, converted in the kernel
+    return;
+  }
   k_d_to_df<<<blocks_for(n), kThreads, 0, c.stream>>>(x, c.df_p, n);
   MGAR_LAUNCH_CHECK();
   const DfOp op = make_op(c);
-  if (c.dim == 3 && !c.untiled) {
-    df3d_apply(c, c.df_p, c.df_Ap, nullptr);
-  } else {
+  {
     if (c.dim == 2)
       k_df_apply<2, false><<<blocks_for(n), kThreads, 0, c.stream>>>(op, c.df_p, c.df_Ap, nullptr,
                                                                      nullptr, nullptr);

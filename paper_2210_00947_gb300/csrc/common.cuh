@@ -692,7 +692,7 @@ void bottom_prepare(Ctx& c);
 constexpr int64_t kBottomNodes = 8192;  // largest level handled by the cluster launch
 // df3d.cu: tiled df64 finest-level operator (3D)
 void df3d_prepare(Ctx& c);
-void df3d_apply(Ctx& c, const float2* x, float2* y, double* dot);
+void df3d_apply(Ctx& c, const double* x, double* y, double* dot);
 void df3d_dir(Ctx& c, const float* z, const float2* p_old, float2* p, const double* rz_new,
               const double* rz_old, bool first, float2* y, double* dot);
 void df3d_resid(Ctx& c, const float2* q, const float2* x, float2* r, float* r32, double* rr);

@@ -15,7 +15,8 @@
 // term is rounded relative to its own size.
 //
 // Three fused forms:
-//   APPLY : y = A x                              [x . y]
+//   APPLY : y = A x with FP64 x and y (the MGAR projection; converted on
+//           load and store)                       [x . y]
 //   DIR   : p = z + beta p_old, y = A p           [p . y]   (CG direction update + product)
 //   RESID : r = q - A x, r32 = fl32(r)            [r . r]
 // p is written to a buffer other than p_old, because neighbouring blocks
@@ -34,7 +35,9 @@ struct DfArgs {
   int ex, ey, ez, NX, NY, NZ, gz;
   const uint8_t* fixed;
   const float2* ke;
-  const float2* x;      // APPLY/RESID: operand; DIR: p_old (unused when first)
+  const float2* x;      // RESID: operand; DIR: p_old (unused when first)
+  const double* x64;    // APPLY: operand
+  double* y64;          // APPLY: A x
   const float* z;       // DIR
   const float2* q;      // RESID
   const double* rz_new; // DIR: beta = rz_new / rz_old
@@ -52,6 +55,7 @@ template <int MODE>
 struct NodeFetch {
   float2 v = make_float2(0.f, 0.f);  // x, or p_old
   float zf = 0.f;                    // DIR: z
+  double xd = 0.0;                   // APPLY: x
   uint8_t f = 1;
   bool on = false;
   // col: clamped i + NX * clamped j; con: (i, j) inside the grid
@@ -63,12 +67,15 @@ struct NodeFetch {
     if (MODE == DIR) {
       zf = a.z[idx];
       if (!a.first) v = a.x[idx];
+    } else if (MODE == APPLY) {
+      xd = a.x64[idx];
     } else {
       v = a.x[idx];
     }
   }
   __device__ __forceinline__ df value(df beta) const {
     if (MODE == DIR) return df_add(df{zf, 0.f}, df_mul(beta, df{v.x, v.y}));
+    if (MODE == APPLY) return df_from_double(xd);
     return df{v.x, v.y};
   }
 };
@@ -247,6 +254,9 @@ __global__ void __launch_bounds__(T::NTB, T::NT <= 256 ? 4 : 2) k_df3d(DfArgs a)
         a.y[idx] = make_float2(ri.hi, ri.lo);                                              \
         a.r32[idx] = __fadd_rn(ri.hi, ri.lo);                                              \
         dot = df_add(dot, df_mul(ri, ri));                                                 \
+      } else if (MODE == APPLY) {                                                          \
+        a.y64[idx] = df_to_double(yv);                                                     \
+        if (a.out) dot = df_add(dot, df_mul(dfk(xi), yv));                                 \
       } else {                                                                             \
         a.y[idx] = make_float2(yv.hi, yv.lo);                                              \
         dot = df_add(dot, df_mul(dfk(xi), yv));                                            \
@@ -337,12 +347,12 @@ void df3d_prepare(Ctx& c) {
   c.df3d_gz[RESID] = runs<RESID>(c, sms);
 }
 
-// y = A x; x . y into *dot when given
-void df3d_apply(Ctx& c, const float2* x, float2* y, double* dot) {
+// y = A x for FP64 x, y; x . y into *dot when given
+void df3d_apply(Ctx& c, const double* x, double* y, double* dot) {
   using namespace d3d;
   DfArgs a = base_args(c);
-  a.x = x;
-  a.y = y;
+  a.x64 = x;
+  a.y64 = y;
   a.out = dot;
   launch<APPLY>(c, a);
 }

@@ -33,6 +33,42 @@ __global__ void k_dot(const double* __restrict__ a, const double* __restrict__ b
   block_sum_finish<1>(v, partials, counter, out);
 }
 
+// The reduced system's products in one pass over R, W and q (Eq. 19-20):
+// K_R[i][j] = R_i . W_j (j <= i) and q_R[i] = R_i . q, i < KEPT.
+template <int KEPT>
+__global__ void k_reduced_dots(const double* __restrict__ R, const double* __restrict__ W,
+                               const double* __restrict__ q, int64_t n, double* partials,
+                               unsigned int* counter, double* dsc) {
+  constexpr int NP = KEPT * (KEPT + 1) / 2 + KEPT;
+  double v[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) v[k] = 0.0;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    double r[KEPT], w[KEPT];
+#pragma unroll
+    for (int i = 0; i < KEPT; ++i) {
+      r[i] = R[(int64_t)i * n + e];
+      w[i] = W[(int64_t)i * n + e];
+    }
+    const double qe = q[e];
+    int k = 0;
+#pragma unroll
+    for (int i = 0; i < KEPT; ++i)
+#pragma unroll
+      for (int j = 0; j <= i; ++j) v[k++] += r[i] * w[j];
+#pragma unroll
+    for (int i = 0; i < KEPT; ++i) v[k++] += r[i] * qe;
+  }
+  double t[NP];
+  if (block_sum_last<NP>(v, partials, counter, t) && threadIdx.x == 0) {
+    int k = 0;
+    for (int i = 0; i < KEPT; ++i)
+      for (int j = 0; j <= i; ++j) dsc[S_KR + i * kMaxM + j] = t[k++];
+    for (int i = 0; i < KEPT; ++i) dsc[S_QR + i] = t[k++];
+  }
+}
+
 // r = q - A x with ||r||^2 (A from the current conductivities).
 template <int DIM>
 __global__ void k_residual_norm(FineOp<double> op, const double* __restrict__ q,
@@ -320,11 +356,20 @@ void solve_mgar(Ctx& c, const double* T_prev, double* T, double* res, int* accep
     else
       apply_fine64(c, c.ke, c.R + (int64_t)j * n, c.W + (int64_t)j * n, nullptr);
   }
-  for (int i = 0; i < kept; ++i) {
-    for (int j = 0; j <= i; ++j) {
-      dot(c, c.R + (int64_t)i * n, c.W + (int64_t)j * n, n, c.dsc + S_KR + i * kMaxM + j);
+  if (kept <= 3) {
+    switch (kept) {
+      case 1: k_reduced_dots<1><<<rb, kThreads, 0, c.stream>>>(c.R, c.W, c.q, n, c.partials, c.counter, c.dsc); break;
+      case 2: k_reduced_dots<2><<<rb, kThreads, 0, c.stream>>>(c.R, c.W, c.q, n, c.partials, c.counter, c.dsc); break;
+      default: k_reduced_dots<3><<<rb, kThreads, 0, c.stream>>>(c.R, c.W, c.q, n, c.partials, c.counter, c.dsc); break;
     }
-    dot(c, c.R + (int64_t)i * n, c.q, n, c.dsc + S_QR + i);
+    MGAR_LAUNCH_CHECK();
+  } else {
+    for (int i = 0; i < kept; ++i) {
+      for (int j = 0; j <= i; ++j) {
+        dot(c, c.R + (int64_t)i * n, c.W + (int64_t)j * n, n, c.dsc + S_KR + i * kMaxM + j);
+      }
+      dot(c, c.R + (int64_t)i * n, c.q, n, c.dsc + S_QR + i);
+    }
   }
   k_reduced_solve<<<1, 1, 0, c.stream>>>(c.dsc, kept, c.derr);
   MGAR_LAUNCH_CHECK();
