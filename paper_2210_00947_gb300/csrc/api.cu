@@ -130,7 +130,9 @@ mgar_step_info design_cycle(Ctx& c, double* rho, double* T, int cycle) {
     inf.relres = rr;
   }
   double comp = 0.0;
-  sensitivity(c, T, c.tmp_dc, nullptr, &comp);
+  // after a mixed 3D MGCG solve the double-float pairs of T are still in df_x
+  const bool t_df = need_mgcg && c.p.precision == MGAR_MIXED && c.dim == 3 && !c.untiled;
+  sensitivity(c, T, c.tmp_dc, nullptr, &comp, t_df ? c.df_x : nullptr);
   inf.compliance = comp;
   double lam = 0.0, change = 0.0;
   oc_update(c, rho, c.tmp_dc, c.p.volfrac, c.p.move, &lam, &change);
@@ -345,6 +347,7 @@ int mgar_create(mgar_t* out, const mgar_params* p, const uint8_t* fixed_mask, co
     if (const char* np = std::getenv("MGAR_NO_PDL")) c->use_pdl = np[0] != '1';
     if (const char* fp = std::getenv("MGAR_FUSED_POST")) c->split_post = fp[0] != '1';
     if (const char* sc = std::getenv("MGAR_SPLIT_COARSE")) c->split_coarse_nodes = std::atoll(sc);
+    if (const char* bn = std::getenv("MGAR_BOTTOM_NODES")) c->bottom_nodes = std::atoll(bn);
     if (const char* nb = std::getenv("MGAR_NO_CLUSTER")) c->bottom_ok = c->bottom_ok && nb[0] != '1';
     if (c->dim == 3) {
       fine3d_prepare(*c);

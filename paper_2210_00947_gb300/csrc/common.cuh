@@ -39,6 +39,7 @@ constexpr long long g_partials_len = 0;
 constexpr int kMaxLevels = 14;
 constexpr int kThreads = 256;
 constexpr int kMinPartialBlocks = 8192;
+constexpr int64_t kBottomNodes = 8192;  // largest level handled by the V-cycle's cluster launch
 constexpr int kMaxFilterOffsets = 1024;
 constexpr int kMaxM = 8;
 constexpr int kOcCand = 31;      // multisection candidates per pass (5 bits)
@@ -65,6 +66,22 @@ enum Slot : int {
   S_OC_CANDL = 160, // 160..190 their ln mu
   S_COUNT = 192
 };
+
+// 1 / sqrt(a) for a > 0: an FP32 seed refined by two Newton-Raphson steps
+// y <- y (3 - a y^2) / 2 (each step doubles the correct bits: 24 -> 48 -> 96),
+// so the pivot costs no FP64 square root or division chain.
+__device__ __forceinline__ double rsqrt_nr(double a) {
+  const float af = (float)a;
+  if (!(af > 0.f) || isinf(af)) return 1.0 / sqrt(a);  // outside the FP32 range
+  double y = (double)rsqrtf(af);
+  y = y * (1.5 - 0.5 * a * y * y);
+  y = y * (1.5 - 0.5 * a * y * y);
+  return y;
+}
+__device__ __forceinline__ float rsqrt_nr(float a) {
+  float y = rsqrtf(a);
+  return y * (1.5f - 0.5f * a * y * y);
+}
 
 // Unsigned division by an invariant divisor d >= 1 for numerators below
 // 2^31, by multiply-high and shift (Granlund and Montgomery, "Division by
@@ -192,6 +209,7 @@ struct Ctx {
   bool df3d_tile = false; // their tile: 32 x 8, or 43 x 11 when that leaves fewer lanes idle
   bool bottom_ok = false; // the V-cycle's bottom levels run as one cluster launch
   int bottom_cluster = 8; // CTAs in that cluster
+  int64_t bottom_nodes = kBottomNodes;  // largest level it takes
   bool use_pdl = true;    // programmatic dependent launch of the V-cycle and CG kernels
   // finest post-smoothing as a thin interpolation pass + the tiled sweep
   // (faster than interpolating inside the tiled pass: 6.67 vs 6.83 ms per
@@ -689,7 +707,6 @@ void vcycle_dot(Ctx& c, const float* b, float* x, const float2* r, double* dout)
 void fine3d_prepare(Ctx& c);
 // vcycle.cu: can the bottom levels run as one thread-block cluster launch
 void bottom_prepare(Ctx& c);
-constexpr int64_t kBottomNodes = 8192;  // largest level handled by the cluster launch
 // df3d.cu: tiled df64 finest-level operator (3D)
 void df3d_prepare(Ctx& c);
 void df3d_apply(Ctx& c, const double* x, double* y, double* dot);
@@ -718,7 +735,10 @@ void fetch_scalars(Ctx& c, int first, int count);
 void setup_filter(Ctx& c);
 void filter(Ctx& c, const double* in, double* out, bool transpose);
 void set_density(Ctx& c, const double* rho, bool physical);
-void sensitivity(Ctx& c, const double* T, double* dc, double* dv, double* compliance);
+// T_df: the same temperatures as double-float pairs when the caller has them
+// (mixed path), else null
+void sensitivity(Ctx& c, const double* T, double* dc, double* dv, double* compliance,
+                 const float2* T_df = nullptr);
 void oc_update(Ctx& c, double* rho, const double* dc, double volfrac, double move, double* lambda,
                double* change);
 

@@ -254,7 +254,11 @@ __global__ void k_oc_prep(const double* __restrict__ rho, const double* __restri
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= ne) return;
   const double r = rho[e];
-  s[e] = r * sqrt(fmax(-dc[e], 0.0)) * rsdv[e];
+  // sqrt(x) = x / sqrt(x) with the Newton-refined reciprocal square root:
+  // a few FP64 multiplies instead of GB300's long FP64 square-root sequence
+  const double x = fmax(-dc[e], 0.0);
+  const double sq = x > 0.0 ? x * rsqrt_nr(x) : 0.0;
+  s[e] = r * sq * rsdv[e];
   lo[e] = fmax(0.0, r - move);
   hi[e] = fmin(1.0, r + move);
 }
@@ -634,19 +638,23 @@ void set_density(Ctx& c, const double* rho, bool physical) {
   if (c.p.precision == MGAR_MIXED) ke_to_df(c);
 }
 
-void sensitivity(Ctx& c, const double* T, double* dc, double* dv, double* compliance) {
+void sensitivity(Ctx& c, const double* T, double* dc, double* dv, double* compliance,
+                 const float2* T_df) {
   const Dims& d = c.L[0];
   const double coef = c.p.penal * (c.p.k0 - c.p.kmin);
   if (dc && c.p.precision == MGAR_MIXED) {
     ProfScope ps(c, MGAR_KC_SENS);
-    k_to_df<<<blocks_for(c.n), kThreads, 0, c.stream>>>(T, c.df_p2, (int)c.n);
-    MGAR_LAUNCH_CHECK();
+    if (!T_df) {
+      k_to_df<<<blocks_for(c.n), kThreads, 0, c.stream>>>(T, c.df_p2, (int)c.n);
+      MGAR_LAUNCH_CHECK();
+      T_df = c.df_p2;
+    }
     if (c.dim == 2)
-      k_sens_df<2><<<blocks_for(c.ne), kThreads, 0, c.stream>>>(c.df_p2, c.rho_phys, c.inv_hs, c.df_e,
-                                                                d, coef, c.p.penal);
+      k_sens_df<2><<<blocks_for(c.ne), kThreads, 0, c.stream>>>(T_df, c.rho_phys, c.inv_hs, c.df_e, d,
+                                                                coef, c.p.penal);
     else
-      k_sens_df<3><<<blocks_for(c.ne), kThreads, 0, c.stream>>>(c.df_p2, c.rho_phys, c.inv_hs, c.df_e,
-                                                                d, coef, c.p.penal);
+      k_sens_df<3><<<blocks_for(c.ne), kThreads, 0, c.stream>>>(T_df, c.rho_phys, c.inv_hs, c.df_e, d,
+                                                                coef, c.p.penal);
     MGAR_LAUNCH_CHECK();
     k_filter_t_df<<<blocks_for(c.ne), kThreads, 0, c.stream>>>(c.df_e, c.f_offs, c.f_w, c.n_filter, d,
                                                                dc);

@@ -307,22 +307,6 @@ __global__ void k_band_fill(const Real* __restrict__ st, Dims d, int bw, B* __re
   }
 }
 
-// 1 / sqrt(a) for a > 0: an FP32 seed refined by two Newton-Raphson steps
-// y <- y (3 - a y^2) / 2 (each step doubles the correct bits: 24 -> 48 -> 96),
-// so the pivot costs no FP64 square root or division chain.
-__device__ __forceinline__ double rsqrt_nr(double a) {
-  const float af = (float)a;
-  if (!(af > 0.f) || isinf(af)) return 1.0 / sqrt(a);  // outside the FP32 range
-  double y = (double)rsqrtf(af);
-  y = y * (1.5 - 0.5 * a * y * y);
-  y = y * (1.5 - 0.5 * a * y * y);
-  return y;
-}
-__device__ __forceinline__ float rsqrt_nr(float a) {
-  float y = rsqrtf(a);
-  return y * (1.5f - 0.5f * a * y * y);
-}
-
 // Right-looking banded Cholesky in one block of kCholThreads threads, on a
 // shared-memory copy of the band when it fits (SMEM) or in place in global
 // memory.  Step k: the pivot (reciprocal square root), the scaled column k

@@ -493,7 +493,7 @@ static void residual(Ctx& c, int l, const Real* b, const Real* x, Real* r) {
 static int bottom_level(const Ctx& c) {
   if (!c.bottom_ok) return c.nl;
   int lb = c.nl - 1;
-  while (lb - 1 >= 1 && c.L[lb - 1].n <= kBottomNodes) --lb;
+  while (lb - 1 >= 1 && c.L[lb - 1].n <= c.bottom_nodes) --lb;
   return lb;
 }
 
