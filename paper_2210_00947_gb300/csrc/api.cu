@@ -100,6 +100,7 @@ void free_ctx(Ctx& c) {
                   c.oc_hi, c.oc_s32, c.oc_lo32, c.oc_hi32, c.dv32, c.oc_amb, c.oc_namb, c.partials, c.counter, c.dsc, c.derr};
   for (void* p : ptrs) cudaFree(p);
   if (c.hsc) cudaFreeHost(c.hsc);
+  if (c.hseq) cudaFreeHost(c.hseq);
 }
 
 // One design cycle of Figure 5 on device arrays rho (design) and T.
@@ -281,7 +282,17 @@ int mgar_create(mgar_t* out, const mgar_params* p, const uint8_t* fixed_mask, co
     MGAR_CUDA(cudaMemset(c->counter, 0, 8 * sizeof(unsigned int)));
     MGAR_CUDA(cudaMalloc(&c->dsc, S_COUNT * sizeof(double)));
     MGAR_CUDA(cudaMemset(c->dsc, 0, S_COUNT * sizeof(double)));
-    MGAR_CUDA(cudaMallocHost(&c->hsc, S_COUNT * sizeof(double)));
+    MGAR_CUDA(cudaHostAlloc(&c->hsc, S_COUNT * sizeof(double), cudaHostAllocMapped));
+    // mapped sequence number for fetch_scalars (blocking copies if unavailable)
+    if (cudaHostAlloc(&c->hseq, sizeof(unsigned long long), cudaHostAllocMapped) == cudaSuccess &&
+        cudaHostGetDevicePointer(&c->hsc_dev, c->hsc, 0) == cudaSuccess &&
+        cudaHostGetDevicePointer(&c->hseq_dev, c->hseq, 0) == cudaSuccess) {
+      *c->hseq = 0;
+    } else {
+      (void)cudaGetLastError();
+      if (c->hseq) cudaFreeHost(c->hseq);
+      c->hseq = nullptr;
+    }
     MGAR_CUDA(cudaMalloc(&c->derr, sizeof(int)));
     MGAR_CUDA(cudaMemset(c->derr, 0, sizeof(int)));
 

@@ -185,6 +185,10 @@ struct Ctx {
   unsigned int* counter = nullptr;   // ticket counters [8]
   double* dsc = nullptr;             // device scalars [S_COUNT]
   double* hsc = nullptr;             // pinned host mirror [S_COUNT]
+  double* hsc_dev = nullptr;         // its device-side address (mapped)
+  unsigned long long* hseq = nullptr;      // mapped pinned sequence number
+  unsigned long long* hseq_dev = nullptr;
+  unsigned long long seq_sent = 0;
   int* derr = nullptr;               // device error flag
 
   // whole-run buffers (mgar_run)

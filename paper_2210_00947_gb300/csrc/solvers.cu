@@ -12,6 +12,9 @@
 // device; t~ = R~ y; Res = ||W y - q|| / ||q||.
 #include "common.cuh"
 
+#include <atomic>
+#include <chrono>
+
 namespace mgar {
 
 // ----------------------------------------------------------------- kernels
@@ -198,10 +201,48 @@ void dot(Ctx& c, const double* a, const double* b, int64_t n, double* out_dev) {
   MGAR_LAUNCH_CHECK();
 }
 
+// Copies device scalars into the mapped pinned mirror, then bumps a
+// sequence number there (after a system-scope fence).
+__global__ void k_publish(const double* __restrict__ dsc, double* hmir, int first, int count,
+                          volatile unsigned long long* seq, unsigned long long value) {
+  for (int k = threadIdx.x; k < count; k += blockDim.x) hmir[first + k] = dsc[first + k];
+  __threadfence_system();
+  __syncwarp();
+  if (threadIdx.x == 0) *seq = value;
+}
+
+// Device scalars to the host.  A one-warp kernel writes them straight into
+// mapped pinned memory and the host spins on a sequence number: no copy
+// engine round trip and no blocking stream synchronisation on the critical
+// path between CG iterations.  The spin is bounded; after it (or if mapped
+// memory is unavailable) the stream is synchronised, which also surfaces
+// any device error.
 void fetch_scalars(Ctx& c, int first, int count) {
-  MGAR_CUDA(cudaMemcpyAsync(c.hsc + first, c.dsc + first, count * sizeof(double),
-                            cudaMemcpyDeviceToHost, c.stream));
-  MGAR_CUDA(cudaStreamSynchronize(c.stream));
+  if (!c.hseq) {
+    MGAR_CUDA(cudaMemcpyAsync(c.hsc + first, c.dsc + first, count * sizeof(double),
+                              cudaMemcpyDeviceToHost, c.stream));
+    MGAR_CUDA(cudaStreamSynchronize(c.stream));
+    return;
+  }
+  const unsigned long long want = ++c.seq_sent;
+  k_publish<<<1, 32, 0, c.stream>>>(c.dsc, c.hsc_dev, first, count, c.hseq_dev, want);
+  MGAR_LAUNCH_CHECK();
+  const auto t0 = std::chrono::steady_clock::now();
+  for (uint64_t spins = 0;; ++spins) {
+    if (*(volatile unsigned long long*)c.hseq >= want) {
+      std::atomic_thread_fence(std::memory_order_acquire);
+      return;
+    }
+    if ((spins & 1023) == 1023 &&
+        std::chrono::steady_clock::now() - t0 > std::chrono::seconds(2)) {
+      // slow or failed work: a blocking wait, which also reports a device error
+      MGAR_CUDA(cudaStreamSynchronize(c.stream));
+      require(*(volatile unsigned long long*)c.hseq >= want, MGAR_ERR_CUDA,
+              "device scalars were not published");
+      std::atomic_thread_fence(std::memory_order_acquire);
+      return;
+    }
+  }
 }
 
 static void check_device_error(Ctx& c) {
