@@ -130,7 +130,7 @@ def max_over_ranks(x, world):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of the kernel as it stands; a kernel changed since its
 # capture has no entry (traffic null).
-TRAFFIC = {}
+TRAFFIC = {"df3d": 46.46e6}  # steady DIR launch, ncu --set full of the 128^3 workload
 
 def load_peaks():
     try:
