@@ -238,7 +238,6 @@ def run_gpu(args):
     torch.cuda.synchronize()
     sampler.start()
     launches0 = mgar.kernel_launches()
-    solver.profile_start(kc)
     for _ in range(args.steps):
         flush.zero_()
         start = torch.cuda.Event(enable_timing=True)
@@ -248,10 +247,26 @@ def run_gpu(args):
         end.record(stream)
         end.synchronize()
         times.append(start.elapsed_time(end))
-    kern_ms, kern_launches = solver.profile_stop()
     launches = mgar.kernel_launches() - launches0
     torch.cuda.synchronize()
     barrier(world)
+    # The dominant kernel's launches are timed with CUDA events on the
+    # handle's stream over a second timed region of the same K runs: events
+    # between launches keep the CG on its host-driven loop, so they stay out
+    # of the region that gives `value`.
+    solver.profile_start(kc)
+    prof_times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        one_run(solver, rho, T)
+        end.record(stream)
+        end.synchronize()
+        prof_times.append(start.elapsed_time(end))
+    kern_ms, kern_launches = solver.profile_stop()
+    torch.cuda.synchronize()
     clocks = sampler.stop()
     step_ms = max_over_ranks(statistics.mean(times), world)
     value = step_ms / (cycles * world)
@@ -348,7 +363,8 @@ def run_gpu(args):
                 "frac": achieved / peak, "traffic": TRAFFIC.get(kernel),
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
     roof.update({"kernel": kernel, "launches": kern_launches, "avg_launch_us": avg_ms * 1e3,
-                 "share_of_step": kern_ms / sum(times)})
+                 "share_of_step": kern_ms / sum(prof_times),
+                 "timed_region": "a second timed region of the same runs, events around each launch"})
 
     n_mgcg = sum(1 for i in infos if i["used_mgcg"])
     n_acc = sum(1 for i in infos if i["accepted"])

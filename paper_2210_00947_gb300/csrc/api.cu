@@ -83,6 +83,7 @@ int guarded(mgar_t h, F&& f) {
 void free_ctx(Ctx& c) {
   for (auto& g : c.graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (c.cg_exec) cudaGraphExecDestroy(c.cg_exec);
   if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
   free_hierarchy(c);
   if (c.prof_ev) {
@@ -356,6 +357,7 @@ int mgar_create(mgar_t* out, const mgar_params* p, const uint8_t* fixed_mask, co
     if (const char* ut = std::getenv("MGAR_UNTILED")) c->untiled = (ut[0] == '1');
     bottom_prepare(*c);
     if (const char* np = std::getenv("MGAR_NO_PDL")) c->use_pdl = np[0] != '1';
+    if (const char* ng = std::getenv("MGAR_NO_CG_GRAPH")) c->cg_graph = ng[0] != '1';
     if (const char* fp = std::getenv("MGAR_FUSED_POST")) c->split_post = fp[0] != '1';
     if (const char* sc = std::getenv("MGAR_SPLIT_COARSE")) c->split_coarse_nodes = std::atoll(sc);
     if (const char* bn = std::getenv("MGAR_BOTTOM_NODES")) c->bottom_nodes = std::atoll(bn);

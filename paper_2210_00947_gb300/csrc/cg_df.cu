@@ -156,8 +156,12 @@ __global__ void k_df_residual(DfOp op, const float2* __restrict__ q, const float
 __global__ void k_df_cg_xr(float2* __restrict__ x, float2* __restrict__ r, const float2* __restrict__ p,
                            const float2* __restrict__ Ap, int n, const double* __restrict__ rz,
                            const double* __restrict__ pap, double* partials, unsigned int* counter,
-                           double* out, float* __restrict__ r32) {
+                           double* out, float* __restrict__ r32,
+                           const float2* __restrict__ p_alt = nullptr,
+                           const double* parity = nullptr) {
   pdl_wait();
+  // device-side CG loop: the two direction buffers swap with the parity
+  if (parity && (((int)*parity) & 1)) p = p_alt;
   const df alpha = df_from_double(*rz / *pap);
   df acc{0.f, 0.f};
   const int stride = gridDim.x * blockDim.x;
@@ -296,6 +300,27 @@ static void precondition_df(Ctx& c) {
   });
 }
 
+// Device-side CG loop (one graph per handle): iteration count and buffer
+// parity start at zero ...
+__global__ void k_cg_reset(double* dsc) {
+  dsc[S_CGIT] = 0.0;
+  dsc[S_CGPAR] = 0.0;
+}
+
+// ... and after each update of x and r: count the iteration, flip the
+// parity, and continue while ||r|| / ||q|| > eps2 (the host loop's test,
+// same arithmetic) and fewer than cg_max iterations ran; a non-finite
+// residual stops the loop and the host reports it.
+__global__ void k_cg_check(double* dsc, double qnorm, double eps2, int cg_max,
+                           cudaGraphConditionalHandle loop) {
+  const double rel = sqrt(dsc[S_RR]) / qnorm;
+  const int it = (int)dsc[S_CGIT] + 1;
+  dsc[S_CGIT] = (double)it;
+  dsc[S_CGPAR] = (double)(((int)dsc[S_CGPAR]) ^ 1);
+  const bool go = isfinite(rel) && rel > eps2 && it < cg_max;
+  cudaGraphSetConditional(loop, go ? 1u : 0u);
+}
+
 // z32 = M r32 (the FP32 copy of r is written by the residual and update
 // kernels) and r . z into dsc[slot], fused into the V-cycle's last kernel
 static void precondition_f32(Ctx& c, int slot) {
@@ -308,6 +333,107 @@ static void precondition_f32(Ctx& c, int slot) {
 // 3D: the tiled kernels fuse the direction update into the product
 // (p = z + beta p_old, A p, p.Ap in one pass) and write the FP32 copy of r
 // beside r, so an iteration is: product, update of x and r, V-cycle, r.z.
+// One CG iteration of the device-side loop: V-cycle (r . z into RZ1), the
+// direction update and product (beta = RZ1 / RZ0, then RZ0 <- RZ1), the
+// update of x and r, the convergence check.
+static void cg_iteration(Ctx& c, bool first, cudaGraphConditionalHandle loop) {
+  const int n = (int)c.n;
+  vcycle_dot(c, c.b32, c.x32, c.df_r, c.dsc + S_RZ1);
+  df3d_dir(c, c.x32, c.df_p, c.df_p2, c.dsc + S_RZ1, c.dsc + S_RZ0, first, c.df_Ap, c.dsc + S_PAP,
+           c.dsc + S_CGPAR, c.dsc + S_RZ0);
+  // parity 0: the new p is in df_p2
+  launch_pdl(c.stream, c.use_pdl, k_df_cg_xr, dim3(c.grid_blocks), dim3(kThreads), c.df_x, c.df_r,
+             (const float2*)c.df_p2, (const float2*)c.df_Ap, n, (const double*)(c.dsc + S_RZ0),
+             (const double*)(c.dsc + S_PAP), c.partials, c.counter, c.dsc + S_RR, c.b32,
+             (const float2*)c.df_p, (const double*)(c.dsc + S_CGPAR));
+  MGAR_LAUNCH_CHECK();
+  k_cg_check<<<1, 1, 0, c.stream>>>(c.dsc, c.qnorm, c.p.eps2, c.p.cg_max, loop);
+  MGAR_LAUNCH_CHECK();
+}
+
+// Builds the graph of the whole preconditioned CG after the initial
+// residual: reset, one peeled iteration, then a WHILE node whose body is one
+// iteration and whose condition the check kernel sets.  The host waits once
+// per solve instead of once per iteration.  False if the device or driver
+// refuses any part (the host loop is used then).
+static bool build_cg_graph(Ctx& c) {
+  cudaGraph_t g = nullptr;
+  cudaGraphConditionalHandle loop = 0;
+  cudaStream_t saved = c.stream;
+  bool ok = false;
+  const int64_t before = launches_so_far();
+  auto fail = [&](cudaError_t e) {
+    (void)e;
+    (void)cudaGetLastError();
+    return false;
+  };
+  do {
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) { fail(e); break; }
+    e = cudaGraphConditionalHandleCreate(&loop, g, 0, 0);
+    if (e != cudaSuccess) { fail(e); break; }
+    e = cudaStreamBeginCaptureToGraph(c.cap_stream, g, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { fail(e); break; }
+    c.stream = c.cap_stream;
+    bool issued = true;
+    cudaGraph_t body = nullptr;
+    try {
+      k_cg_reset<<<1, 1, 0, c.stream>>>(c.dsc);
+      MGAR_LAUNCH_CHECK();
+      cg_iteration(c, true, loop);
+      // the WHILE node after everything captured so far
+      cudaStreamCaptureStatus st;
+      cudaGraph_t cg = nullptr;
+      const cudaGraphNode_t* deps = nullptr;
+      const cudaGraphEdgeData* edges = nullptr;
+      size_t ndeps = 0;
+      MGAR_CUDA(cudaStreamGetCaptureInfo(c.stream, &st, nullptr, &cg, &deps, &edges, &ndeps));
+      cudaGraphNodeParams cp = {};
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = loop;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      cudaGraphNode_t wnode = nullptr;
+      MGAR_CUDA(cudaGraphAddNode(&wnode, cg, deps, nullptr, ndeps, &cp));
+      body = cp.conditional.phGraph_out[0];
+      MGAR_CUDA(cudaStreamUpdateCaptureDependencies(c.stream, &wnode, nullptr, 1,
+                                                    cudaStreamSetCaptureDependencies));
+    } catch (...) {
+      issued = false;
+    }
+    cudaGraph_t gout = nullptr;
+    e = cudaStreamEndCapture(c.cap_stream, &gout);
+    c.stream = saved;
+    if (!issued || e != cudaSuccess || !body) { fail(e); break; }
+    // the body: one more iteration per pass
+    e = cudaStreamBeginCaptureToGraph(c.cap_stream, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { fail(e); break; }
+    c.stream = c.cap_stream;
+    const int64_t body_before = launches_so_far();
+    try {
+      cg_iteration(c, false, loop);
+    } catch (...) {
+      issued = false;
+    }
+    c.body_kernels = launches_so_far() - body_before;
+    cudaGraph_t bout = nullptr;
+    e = cudaStreamEndCapture(c.cap_stream, &bout);
+    c.stream = saved;
+    if (!issued || e != cudaSuccess) { fail(e); break; }
+    e = cudaGraphInstantiate(&c.cg_exec, g, 0);
+    if (e != cudaSuccess) { c.cg_exec = nullptr; fail(e); break; }
+    ok = true;
+  } while (false);
+  c.stream = saved;
+  const int64_t captured = launches_so_far() - before;
+  count_launches(-captured);  // captured, not executed
+  c.prologue_kernels = captured - c.body_kernels;
+  if (g) cudaGraphDestroy(g);
+  return ok;
+}
+
 static int solve_mgcg_df3(Ctx& c, double* T, int* iters, double* relres) {
   const int n = (int)c.n;
   const int rb = c.grid_blocks;
@@ -320,7 +446,20 @@ static int solve_mgcg_df3(Ctx& c, double* T, int* iters, double* relres) {
   fetch_scalars(c, S_RR, 1);
   double rel = std::sqrt(c.hsc[S_RR]) / c.qnorm;
   int it = 0;
-  if (!(rel <= c.p.eps2)) {
+  // the device-side loop while no kernel class is being timed with events
+  // (event records cannot sit inside a conditional body)
+  if (!(rel <= c.p.eps2) && c.cg_graph && c.prof_class == 0 && c.use_graphs) {
+    require(std::isfinite(rel), MGAR_ERR_NONFINITE, "non-finite initial residual");
+    if (!c.cg_exec && !build_cg_graph(c)) c.cg_graph = false;
+  }
+  if (!(rel <= c.p.eps2) && c.cg_exec && c.prof_class == 0 && c.use_graphs) {
+    MGAR_CUDA(cudaGraphLaunch(c.cg_exec, c.stream));
+    fetch_scalars(c, S_RR, S_CGIT - S_RR + 1);
+    it = (int)c.hsc[S_CGIT];
+    count_launches(c.prologue_kernels + (int64_t)std::max(it - 1, 0) * c.body_kernels);
+    rel = std::sqrt(c.hsc[S_RR]) / c.qnorm;
+    require(std::isfinite(rel), MGAR_ERR_NONFINITE, "CG breakdown (non-finite residual)");
+  } else if (!(rel <= c.p.eps2)) {
     require(std::isfinite(rel), MGAR_ERR_NONFINITE, "non-finite initial residual");
     int a = S_RZ0, b = S_RZ1;
     precondition_f32(c, a);
@@ -336,7 +475,8 @@ static int solve_mgcg_df3(Ctx& c, double* T, int* iters, double* relres) {
       std::swap(pcur, pnext);
       launch_pdl(c.stream, c.use_pdl, k_df_cg_xr, dim3(rb), dim3(kThreads), c.df_x, c.df_r,
                  (const float2*)pcur, (const float2*)c.df_Ap, n, (const double*)(c.dsc + a),
-                 (const double*)(c.dsc + S_PAP), c.partials, c.counter, c.dsc + S_RR, c.b32);
+                 (const double*)(c.dsc + S_PAP), c.partials, c.counter, c.dsc + S_RR, c.b32,
+                 (const float2*)nullptr, (const double*)nullptr);
       MGAR_LAUNCH_CHECK();
       ++it;
       fetch_scalars(c, S_RR, 1);

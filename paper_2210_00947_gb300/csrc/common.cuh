@@ -52,6 +52,7 @@ constexpr size_t kBandSmemMax = 160 * 1024;  // band factorised in shared memory
 // Slots of the device scalar array.
 enum Slot : int {
   S_RZ0 = 0, S_RZ1 = 1, S_PAP = 2, S_RR = 3, S_TMP = 4, S_NORM = 5,
+  S_CGIT = 6, S_CGPAR = 7,  // device-side CG loop: iteration count, buffer parity
   S_OC_LO = 8, S_OC_HI = 9, S_OC_DONE = 10, S_OC_LAM = 11, S_OC_VOL = 12, S_OC_CHANGE = 13,
   S_OC_STEPS = 14, S_COMPL = 15,
   S_GS = 16,      // 16..31 Gram-Schmidt coefficients
@@ -215,6 +216,10 @@ struct Ctx {
   int bottom_cluster = 8; // CTAs in that cluster
   int64_t bottom_nodes = kBottomNodes;  // largest level it takes
   bool use_pdl = true;    // programmatic dependent launch of the V-cycle and CG kernels
+  // device-side CG loop (3D mixed path): one graph with a conditional WHILE node
+  bool cg_graph = true;
+  cudaGraphExec_t cg_exec = nullptr;
+  int64_t prologue_kernels = 0, body_kernels = 0;
   // finest post-smoothing as a thin interpolation pass + the tiled sweep
   // (faster than interpolating inside the tiled pass: 6.67 vs 6.83 ms per
   // design cycle at 128^3); MGAR_FUSED_POST=1 selects the fused pass
@@ -714,8 +719,11 @@ void bottom_prepare(Ctx& c);
 // df3d.cu: tiled df64 finest-level operator (3D)
 void df3d_prepare(Ctx& c);
 void df3d_apply(Ctx& c, const double* x, double* y, double* dot);
+// parity (device scalar, may be null): odd swaps the roles of p_old and p;
+// rz_set (may be null) receives *rz_new after the launch has used it
 void df3d_dir(Ctx& c, const float* z, const float2* p_old, float2* p, const double* rz_new,
-              const double* rz_old, bool first, float2* y, double* dot);
+              const double* rz_old, bool first, float2* y, double* dot,
+              const double* parity = nullptr, double* rz_set = nullptr);
 void df3d_resid(Ctx& c, const float2* q, const float2* x, float2* r, float* r32, double* rr);
 void apply_fine64(Ctx& c, const double* ke, const double* x, double* y, double* dot_out);
 void apply_fine32(Ctx& c, const float* ke, const float* x, float* y);

@@ -49,6 +49,13 @@ struct DfArgs {
   double* partials;
   unsigned int* counter;
   double* out;          // dot product (may be null for APPLY)
+  // DIR inside the device-side CG loop: with parity odd, p_old is x_alt and
+  // the new p goes to p_alt (the two direction buffers swap each iteration);
+  // rz_set, when given, receives rz_new once every block has read it
+  const float2* x_alt;
+  float2* p_alt;
+  const double* parity;
+  double* rz_set;
 };
 
 template <int MODE>
@@ -59,18 +66,19 @@ struct NodeFetch {
   uint8_t f = 1;
   bool on = false;
   // col: clamped i + NX * clamped j; con: (i, j) inside the grid
-  __device__ __forceinline__ void issue(const DfArgs& a, int col, bool con, int k) {
+  // xsrc: the operand (RESID) or p_old (DIR)
+  __device__ __forceinline__ void issue(const DfArgs& a, const float2* xsrc, int col, bool con, int k) {
     on = con && k >= 0 && k < a.NZ;
     const int idx = col + a.NX * a.NY * min(max(k, 0), a.NZ - 1);
     if (!CK(idx, (int64_t)a.NX * a.NY * a.NZ)) return;
     f = a.fixed[idx];
     if (MODE == DIR) {
       zf = a.z[idx];
-      if (!a.first) v = a.x[idx];
+      if (!a.first) v = xsrc[idx];
     } else if (MODE == APPLY) {
       xd = a.x64[idx];
     } else {
-      v = a.x[idx];
+      v = xsrc[idx];
     }
   }
   __device__ __forceinline__ df value(df beta) const {
@@ -133,6 +141,9 @@ __global__ void __launch_bounds__(T::NTB, T::NT <= 256 ? 4 : 2) k_df3d(DfArgs a)
   if (kr) T::kring(tid - KRING0, kxh, kyh);
   df beta{0.f, 0.f};
   if (MODE == DIR && !a.first) beta = df_from_double(*a.rz_new / *a.rz_old);
+  const bool odd = MODE == DIR && a.parity && (((int)*a.parity) & 1);
+  const float2* const xsrc = odd ? a.x_alt : a.x;
+  float2* const pdst = odd ? a.p_alt : a.p;
   const int NXY = a.NX * a.NY;
 
   // per-thread column offsets (plane-independent)
@@ -156,12 +167,12 @@ __global__ void __launch_bounds__(T::NTB, T::NT <= 256 ? 4 : 2) k_df3d(DfArgs a)
   df dot{0.f, 0.f};
 
   auto issue_plane = [&](int p) {
-    own.issue(a, ocol, mine, p);
+    own.issue(a, xsrc, ocol, mine, p);
     if (MODE == RESID) {
       const int idx = ocol + NXY * min(max(p, 0), a.NZ - 1);
       if (CK(idx, (int64_t)NXY * a.NZ)) ownq = a.q[idx];
     }
-    if (xr) ring.issue(a, rcol, ron, p);
+    if (xr) ring.issue(a, xsrc, rcol, ron, p);
   };
   auto issue_layer = [&](int l) {
     const int lc = EXY * min(max(l, 0), a.ez - 1);
@@ -182,7 +193,7 @@ __global__ void __launch_bounds__(T::NTB, T::NT <= 256 ? 4 : 2) k_df3d(DfArgs a)
     cv[S] = v2;                                                                            \
     cf[S] = own.f != 0;                                                                    \
     cq[S] = ownq;                                                                          \
-    if (MODE == DIR && mine && (P) >= kb && (P) < kend) a.p[ocol + NXY * (P)] = v2;        \
+    if (MODE == DIR && mine && (P) >= kb && (P) < kend) pdst[ocol + NXY * (P)] = v2;       \
     if (xr) {                                                                              \
       const df w = ring.value(beta);                                                       \
       X[S][ryh][rxh] = (ring.on && !ring.f) ? make_float2(w.hi, w.lo) : make_float2(0.f, 0.f); \
@@ -278,8 +289,10 @@ __global__ void __launch_bounds__(T::NTB, T::NT <= 256 ? 4 : 2) k_df3d(DfArgs a)
     double t[1];
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     const int nb = gridDim.x * gridDim.y * gridDim.z;
-    if (block_sum_last_ids<1>(v, a.partials, a.counter, t, tid, T::NTB, bid, nb) && tid == 0)
+    if (block_sum_last_ids<1>(v, a.partials, a.counter, t, tid, T::NTB, bid, nb) && tid == 0) {
       a.out[0] = t[0];
+      if (MODE == DIR && a.rz_set) *a.rz_set = *a.rz_new;  // every block has read rz_new
+    }
   }
 }
 
@@ -359,12 +372,17 @@ void df3d_apply(Ctx& c, const double* x, double* y, double* dot) {
 
 // p = z + (rz_new / rz_old) p_old (p = z when first), y = A p, p . y into *dot
 void df3d_dir(Ctx& c, const float* z, const float2* p_old, float2* p, const double* rz_new,
-              const double* rz_old, bool first, float2* y, double* dot) {
+              const double* rz_old, bool first, float2* y, double* dot, const double* parity,
+              double* rz_set) {
   using namespace d3d;
   DfArgs a = base_args(c);
   a.z = z;
   a.x = p_old;
   a.p = p;
+  a.x_alt = p;        // odd parity: the buffers swap roles
+  a.p_alt = const_cast<float2*>(p_old);
+  a.parity = parity;
+  a.rz_set = rz_set;
   a.rz_new = rz_new;
   a.rz_old = rz_old;
   a.first = first ? 1 : 0;
