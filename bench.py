@@ -130,7 +130,7 @@ def max_over_ranks(x, world):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
 # one ncu capture of the kernel as it stands; a kernel changed since its
 # capture has no entry (traffic null).
-TRAFFIC = {"df3d": 46.46e6}  # steady DIR launch, ncu --set full of the 128^3 workload
+TRAFFIC = {}
 
 def load_peaks():
     try:
@@ -164,13 +164,14 @@ def kernel_model(kernel, w):
     e = w.n_elems
     if kernel == "df3d":
         # mixed path, tiled df64 H8 product with the fused CG direction update
-        # (p = z + beta p_old, y = A p, p.y), per node in FP32-pipe operations:
-        # direction update 18 (df mul 7 + df add 11), 12 face-diagonal weight
-        # sums 132 (df add 11 each), 20 difference terms 400 (exact
-        # difference 8, TwoProd product 4, TwoSum accumulation 8), final
-        # normalisation and 1/12 scale 10, p.y 18: 578.  Bytes: p_old and y
-        # and p (8 B each), z (4 B), one k_e (8 B), mask (1 B): 37.
-        return 37 * n, 578 * n, "alu", "fp32"
+        # (p = z + beta p_old, y = A p, p.y), element form, per node in
+        # FP32-pipe operations: direction update 18 (df mul 7 + df add 11),
+        # 8 element sums f_e 192 (TwoSum chain of four pairs, 24 each), 8
+        # products k_e f_e accumulated 96 (TwoProd with cross terms 4, TwoSum
+        # accumulation 8), sum of the 8 k_e 58, diagonal product 7,
+        # subtraction 14, 1/12 scale 7, p.y 18: 410.  Bytes: p_old and y and
+        # p (8 B each), z (4 B), one k_e (8 B), mask (1 B): 37.
+        return 37 * n, 410 * n, "alu", "fp32"
     if kernel == "apply64":
         # 3D H8 y = A x in FP64, node-centred: read x (8 B) and one k_e per
         # node (8 B, each element read once) and the fixed-node mask (1 B),

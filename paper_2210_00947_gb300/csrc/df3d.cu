@@ -1,18 +1,21 @@
 // Tiled double-float (df64) finest-level operator for 3D (H8) grids, used
 // by the outer CG of the mixed path (Sections 1 and 3.2).
 //
-// Same z-marching tile as the V-cycle's finest-level kernels: a 32 x 8 block
-// walks a run of node planes, the operand planes (float2 hi/lo pairs, zero on
-// fixed nodes and off the grid) and element-conductivity layers rotate in
-// shared memory, and the loads of plane k+2 are in flight while plane k is
-// computed.  The product uses the difference form of the conductivity
-// stencil (K has zero row sums):
-//   (A x)_i = (1/12) sum_j w_ij (x_i - x^_j),
-// w_ij = k_a + k_b over the 12 face diagonals and k_e over the 8 body
-// diagonals; a fixed row is the identity.  Each difference x_i - x^_j is
-// formed exactly (TwoSum of the high parts), multiplied by w_ij with TwoProd
-// and summed with TwoSum into an unnormalised (hi, lo) accumulator, so every
-// term is rounded relative to its own size.
+// Same z-marching tile as the V-cycle's finest-level kernels: a TX x TY
+// block (43 x 11 on 129-node planes, else 32 x 8) walks a run of node
+// planes, the operand planes (float2 hi/lo pairs, zero on fixed nodes and off
+// the grid) and element-conductivity layers rotate in shared memory, and the loads of plane k+2 are in flight while plane k is
+// computed.  The product uses the element form of the conductivity stencil:
+//   (A x)_i = (1/12) (4 x_i sum_e k_e - sum_e k_e f_e),
+// summed over the 8 elements e around node i, where f_e is the sum of the
+// operand x^ over the four nodes of e that are not edge neighbours of i
+// (three face diagonals and the body diagonal); a fixed row is the
+// identity.  Each f_e is a TwoSum chain of the (hi, lo) pairs, each k_e f_e
+// is a TwoProd with its cross terms, and the products are summed with TwoSum
+// into an unnormalised (hi, lo) accumulator.  Rounding errors are of order
+// 2^-47 |x| sum_e k_e (those of the FP64 operator, which sums the same
+// terms, are of order 2^-53 |x| sum_e k_e); the form needs about a third
+// fewer FP32 operations than the difference form sum_j w_ij (x_i - x_j).
 //
 // Three fused forms:
 //   APPLY : y = A x with FP64 x and y (the MGAR projection; converted on
@@ -88,30 +91,43 @@ struct NodeFetch {
   }
 };
 
-// acc (unnormalised hi, lo) += w * (xi - xj)
-__device__ __forceinline__ void acc_term(float& ah, float& al, df w, float2 xi, float2 xj) {
-  float s, e;
-  two_sum(xi.x, -xj.x, s, e);
-  e = __fadd_rn(e, __fsub_rn(xi.y, xj.y));
+__device__ __forceinline__ df dfk(float2 v) { return df{v.x, v.y}; }
+
+// a + b + c + d as an unnormalised (hi, lo) pair: TwoSum chain of the high
+// words, low words and rounding errors added in FP32
+__device__ __forceinline__ df far4(float2 a, float2 b, float2 c, float2 d) {
+  float s, e, t;
+  two_sum(a.x, b.x, s, e);
+  t = __fadd_rn(e, __fadd_rn(a.y, b.y));
+  two_sum(s, c.x, s, e);
+  t = __fadd_rn(t, __fadd_rn(e, c.y));
+  two_sum(s, d.x, s, e);
+  t = __fadd_rn(t, __fadd_rn(e, d.y));
+  return df{s, t};
+}
+
+// acc (unnormalised hi, lo) += k * f
+__device__ __forceinline__ void acc_prod(float& ah, float& al, df k, df f) {
   float p, pe;
-  two_prod(w.hi, s, p, pe);
-  pe = __fmaf_rn(w.hi, e, pe);
-  pe = __fmaf_rn(w.lo, s, pe);
+  two_prod(k.hi, f.hi, p, pe);
+  pe = __fmaf_rn(k.hi, f.lo, pe);
+  pe = __fmaf_rn(k.lo, f.hi, pe);
   float t, te;
   two_sum(ah, p, t, te);
   ah = t;
   al = __fadd_rn(al, __fadd_rn(te, pe));
 }
 
-__device__ __forceinline__ df dfk(float2 v) { return df{v.x, v.y}; }
-
-// k_a + k_b as an unnormalised pair (TwoSum of the high parts, low parts
-// added): exact to the pair's precision; acc_term multiplies both halves,
-// so the pair needs no renormalisation.
-__device__ __forceinline__ df wsum(df a, df b) {
-  float s, e;
-  two_sum(a.hi, b.hi, s, e);
-  return df{s, __fadd_rn(e, __fadd_rn(a.lo, b.lo))};
+// sum of the eight element conductivities around a node, unnormalised
+__device__ __forceinline__ df ksum8(df a, df b, df c, df d, df e, df f, df g, df h) {
+  float s = a.hi, t = a.lo, r;
+  const df v[7] = {b, c, d, e, f, g, h};
+#pragma unroll
+  for (int q = 0; q < 7; ++q) {
+    two_sum(s, v[q].hi, s, r);
+    t = __fadd_rn(t, __fadd_rn(r, v[q].lo));
+  }
+  return df{s, t};
 }
 
 // Plane p and element layer p live in slot (p - kb + 1) & 3; the z loop is
@@ -237,28 +253,35 @@ __global__ void __launch_bounds__(T::NTB, T::NT <= 256 ? 4 : 2) k_df3d(DfArgs a)
                  k010 = dfk(K[S0][ty + 1][tx]), k011 = dfk(K[S0][ty + 1][tx + 1]);         \
         const df k100 = dfk(K[S1][ty][tx]), k101 = dfk(K[S1][ty][tx + 1]),                 \
                  k110 = dfk(K[S1][ty + 1][tx]), k111 = dfk(K[S1][ty + 1][tx + 1]);         \
+        /* f_e: in-plane face diagonal, two out-of-plane face diagonals, body diagonal */ \
+        const df f000 = far4(X[S1][cy - 1][cx - 1], X[S0][cy][cx - 1], X[S0][cy - 1][cx],     \
+                             X[S0][cy - 1][cx - 1]);                                           \
+        const df f001 = far4(X[S1][cy - 1][cx + 1], X[S0][cy][cx + 1], X[S0][cy - 1][cx],     \
+                             X[S0][cy - 1][cx + 1]);                                           \
+        const df f010 = far4(X[S1][cy + 1][cx - 1], X[S0][cy][cx - 1], X[S0][cy + 1][cx],     \
+                             X[S0][cy + 1][cx - 1]);                                           \
+        const df f011 = far4(X[S1][cy + 1][cx + 1], X[S0][cy][cx + 1], X[S0][cy + 1][cx],     \
+                             X[S0][cy + 1][cx + 1]);                                           \
+        const df f100 = far4(X[S1][cy - 1][cx - 1], X[S2][cy][cx - 1], X[S2][cy - 1][cx],     \
+                             X[S2][cy - 1][cx - 1]);                                           \
+        const df f101 = far4(X[S1][cy - 1][cx + 1], X[S2][cy][cx + 1], X[S2][cy - 1][cx],     \
+                             X[S2][cy - 1][cx + 1]);                                           \
+        const df f110 = far4(X[S1][cy + 1][cx - 1], X[S2][cy][cx - 1], X[S2][cy + 1][cx],     \
+                             X[S2][cy + 1][cx - 1]);                                           \
+        const df f111 = far4(X[S1][cy + 1][cx + 1], X[S2][cy][cx + 1], X[S2][cy + 1][cx],     \
+                             X[S2][cy + 1][cx + 1]);                                           \
         float ah = 0.f, al = 0.f;                                                          \
-        acc_term(ah, al, wsum(k000, k100), xi, X[S1][cy - 1][cx - 1]);                   \
-        acc_term(ah, al, wsum(k001, k101), xi, X[S1][cy - 1][cx + 1]);                   \
-        acc_term(ah, al, wsum(k010, k110), xi, X[S1][cy + 1][cx - 1]);                   \
-        acc_term(ah, al, wsum(k011, k111), xi, X[S1][cy + 1][cx + 1]);                   \
-        acc_term(ah, al, wsum(k000, k010), xi, X[S0][cy][cx - 1]);                       \
-        acc_term(ah, al, wsum(k001, k011), xi, X[S0][cy][cx + 1]);                       \
-        acc_term(ah, al, wsum(k100, k110), xi, X[S2][cy][cx - 1]);                       \
-        acc_term(ah, al, wsum(k101, k111), xi, X[S2][cy][cx + 1]);                       \
-        acc_term(ah, al, wsum(k000, k001), xi, X[S0][cy - 1][cx]);                       \
-        acc_term(ah, al, wsum(k010, k011), xi, X[S0][cy + 1][cx]);                       \
-        acc_term(ah, al, wsum(k100, k101), xi, X[S2][cy - 1][cx]);                       \
-        acc_term(ah, al, wsum(k110, k111), xi, X[S2][cy + 1][cx]);                       \
-        acc_term(ah, al, k000, xi, X[S0][cy - 1][cx - 1]);                                 \
-        acc_term(ah, al, k001, xi, X[S0][cy - 1][cx + 1]);                                 \
-        acc_term(ah, al, k010, xi, X[S0][cy + 1][cx - 1]);                                 \
-        acc_term(ah, al, k011, xi, X[S0][cy + 1][cx + 1]);                                 \
-        acc_term(ah, al, k100, xi, X[S2][cy - 1][cx - 1]);                                 \
-        acc_term(ah, al, k101, xi, X[S2][cy - 1][cx + 1]);                                 \
-        acc_term(ah, al, k110, xi, X[S2][cy + 1][cx - 1]);                                 \
-        acc_term(ah, al, k111, xi, X[S2][cy + 1][cx + 1]);                                 \
-        yv = df_mul(df_make(ah, al), scale);                                               \
+        acc_prod(ah, al, k000, f000);                                                      \
+        acc_prod(ah, al, k001, f001);                                                      \
+        acc_prod(ah, al, k010, f010);                                                      \
+        acc_prod(ah, al, k011, f011);                                                      \
+        acc_prod(ah, al, k100, f100);                                                      \
+        acc_prod(ah, al, k101, f101);                                                      \
+        acc_prod(ah, al, k110, f110);                                                      \
+        acc_prod(ah, al, k111, f111);                                                      \
+        const df ks = ksum8(k000, k001, k010, k011, k100, k101, k110, k111);               \
+        const df diag = df_mul(df{4.f * ks.hi, 4.f * ks.lo}, dfk(xi));                     \
+        yv = df_mul(df_sub(diag, df_make(ah, al)), scale);                                 \
       }                                                                                    \
       if (MODE == RESID) {                                                                 \
         const df ri = df_sub(dfk(cq[S1]), yv);                                             \
