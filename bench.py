@@ -167,11 +167,13 @@ def kernel_model(kernel, w):
         # (p = z + beta p_old, y = A p, p.y), element form, per node in
         # FP32-pipe operations: direction update 18 (df mul 7 + df add 11),
         # 8 element sums f_e 192 (TwoSum chain of four pairs, 24 each), 8
-        # products k_e f_e accumulated 96 (TwoProd with cross terms 4, TwoSum
-        # accumulation 8), sum of the 8 k_e 58, diagonal product 7,
-        # subtraction 14, 1/12 scale 7, p.y 18: 410.  Bytes: p_old and y and
-        # p (8 B each), z (4 B), one k_e (8 B), mask (1 B): 37.
-        return 37 * n, 410 * n, "alu", "fp32"
+        # products k_e f_e in two accumulators 80 (first term TwoProd with
+        # cross terms 4, the others 4 + TwoSum accumulation 8), joining the
+        # accumulators 11, diagonal product with the per-node 4 sum k_e 7,
+        # subtraction 11, 1/12 scale 7, p.y 18: 344.  Bytes: p_old and y and
+        # p (8 B each), z (4 B), one k_e (8 B), 4 sum k_e (8 B), mask (1 B):
+        # 45.
+        return 45 * n, 344 * n, "alu", "fp32"
     if kernel == "apply64":
         # 3D H8 y = A x in FP64, node-centred: read x (8 B) and one k_e per
         # node (8 B, each element read once) and the fixed-node mask (1 B),

@@ -97,7 +97,7 @@ void free_ctx(Ctx& c) {
   cudaFree(c.run_rho);
   cudaFree(c.run_T);
   void* ptrs[] = {c.fixed, c.efix, c.gfix, c.q, c.rho_phys, c.ke, c.ke0, c.ke_f, c.ke0_f, c.inv_hs, c.f_offs, c.f_w,
-                  c.dv, c.rsdv, c.r, c.z, c.pv, c.Ap, c.tm, c.tmp_dc, c.R, c.W, c.b32, c.x32, c.ke_df, c.df_q, c.df_x, c.df_r, c.df_p, c.df_Ap, c.df_p2, c.df_e, c.tmp_e, c.oc_s, c.oc_lo,
+                  c.dv, c.rsdv, c.r, c.z, c.pv, c.Ap, c.tm, c.tmp_dc, c.R, c.W, c.b32, c.x32, c.ke_df, c.df_q, c.df_x, c.df_r, c.df_p, c.df_Ap, c.df_p2, c.df_e, c.kd_df, c.tmp_e, c.oc_s, c.oc_lo,
                   c.oc_hi, c.oc_s32, c.oc_lo32, c.oc_hi32, c.dv32, c.oc_amb, c.oc_namb, c.partials, c.counter, c.dsc, c.derr};
   for (void* p : ptrs) cudaFree(p);
   if (c.hsc) cudaFreeHost(c.hsc);
@@ -269,7 +269,7 @@ int mgar_create(mgar_t* out, const mgar_params* p, const uint8_t* fixed_mask, co
       MGAR_CUDA(cudaMalloc(&c->x32, n * sizeof(float)));
       MGAR_CUDA(cudaMalloc(&c->ke_df, ne * sizeof(float2)));
       MGAR_CUDA(cudaMalloc(&c->df_e, ne * sizeof(float2)));
-      for (float2** v : {&c->df_q, &c->df_x, &c->df_r, &c->df_p, &c->df_Ap, &c->df_p2})
+      for (float2** v : {&c->df_q, &c->df_x, &c->df_r, &c->df_p, &c->df_Ap, &c->df_p2, &c->kd_df})
         MGAR_CUDA(cudaMalloc(v, n * sizeof(float2)));
     }
     MGAR_CUDA(cudaMalloc(&c->partials, (size_t)32 * maxb * sizeof(double)));

@@ -176,6 +176,7 @@ struct Ctx {
   float2 *ke_df = nullptr, *df_q = nullptr, *df_x = nullptr, *df_r = nullptr, *df_p = nullptr,
          *df_Ap = nullptr, *df_p2 = nullptr;
   float2* df_e = nullptr;  // mixed mode: df64 scratch over elements (filter input)
+  float2* kd_df = nullptr; // mixed mode: 4 sum_e k_e per node (df64), the 3D operator's diagonal x 12
   double *tmp_e = nullptr, *oc_s = nullptr, *oc_lo = nullptr, *oc_hi = nullptr;
   float *oc_s32 = nullptr, *oc_lo32 = nullptr, *oc_hi32 = nullptr, *dv32 = nullptr;
   int *oc_amb = nullptr, *oc_namb = nullptr;
@@ -718,6 +719,8 @@ void fine3d_prepare(Ctx& c);
 void bottom_prepare(Ctx& c);
 // df3d.cu: tiled df64 finest-level operator (3D)
 void df3d_prepare(Ctx& c);
+// kd_df from ke_df (after every change of the design)
+void df3d_node_diag(Ctx& c);
 void df3d_apply(Ctx& c, const double* x, double* y, double* dot);
 // parity (device scalar, may be null): odd swaps the roles of p_old and p;
 // rz_set (may be null) receives *rz_new after the launch has used it

@@ -624,6 +624,7 @@ void set_density(Ctx& c, const double* rho, bool physical) {
         c.df_e, c.inv_hs, c.f_offs, c.f_w, c.n_filter, c.L[0], c.p.k0, c.p.kmin, c.p.penal,
         c.rho_phys, c.ke, c.ke_f, c.ke_df);
     MGAR_LAUNCH_CHECK();
+    if (c.dim == 3) df3d_node_diag(c);
     return;
   }
   if (physical)
@@ -635,7 +636,10 @@ void set_density(Ctx& c, const double* rho, bool physical) {
                                                       c.p.precision == MGAR_FP64 ? nullptr : c.ke_f,
                                                       c.ne, c.p.k0, c.p.kmin, c.p.penal);
   MGAR_LAUNCH_CHECK();
-  if (c.p.precision == MGAR_MIXED) ke_to_df(c);
+  if (c.p.precision == MGAR_MIXED) {
+    ke_to_df(c);
+    if (c.dim == 3) df3d_node_diag(c);
+  }
 }
 
 void sensitivity(Ctx& c, const double* T, double* dc, double* dv, double* compliance,

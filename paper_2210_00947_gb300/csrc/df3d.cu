@@ -10,9 +10,11 @@
 // summed over the 8 elements e around node i, where f_e is the sum of the
 // operand x^ over the four nodes of e that are not edge neighbours of i
 // (three face diagonals and the body diagonal); a fixed row is the
-// identity.  Each f_e is a TwoSum chain of the (hi, lo) pairs, each k_e f_e
+// identity.  4 sum_e k_e is a per-node input computed once per design
+// (k_node_kdiag).  Each f_e is a TwoSum chain of the (hi, lo) pairs, each k_e f_e
 // is a TwoProd with its cross terms, and the products are summed with TwoSum
-// into an unnormalised (hi, lo) accumulator.  Rounding errors are of order
+// into two unnormalised (hi, lo) accumulators (elements below and above the
+// node's plane, for instruction-level parallelism).  Rounding errors are of order
 // 2^-47 |x| sum_e k_e (those of the FP64 operator, which sums the same
 // terms, are of order 2^-53 |x| sum_e k_e); the form needs about a third
 // fewer FP32 operations than the difference form sum_j w_ij (x_i - x_j).
@@ -38,6 +40,7 @@ struct DfArgs {
   int ex, ey, ez, NX, NY, NZ, gz;
   const uint8_t* fixed;
   const float2* ke;
+  const float2* kd;     // per node: 4 sum_e k_e (df64)
   const float2* x;      // RESID: operand; DIR: p_old (unused when first)
   const double* x64;    // APPLY: operand
   double* y64;          // APPLY: A x
@@ -106,6 +109,13 @@ __device__ __forceinline__ df far4(float2 a, float2 b, float2 c, float2 d) {
   return df{s, t};
 }
 
+// acc (unnormalised hi, lo) = k * f
+__device__ __forceinline__ void acc_first(float& ah, float& al, df k, df f) {
+  two_prod(k.hi, f.hi, ah, al);
+  al = __fmaf_rn(k.hi, f.lo, al);
+  al = __fmaf_rn(k.lo, f.hi, al);
+}
+
 // acc (unnormalised hi, lo) += k * f
 __device__ __forceinline__ void acc_prod(float& ah, float& al, df k, df f) {
   float p, pe;
@@ -116,18 +126,6 @@ __device__ __forceinline__ void acc_prod(float& ah, float& al, df k, df f) {
   two_sum(ah, p, t, te);
   ah = t;
   al = __fadd_rn(al, __fadd_rn(te, pe));
-}
-
-// sum of the eight element conductivities around a node, unnormalised
-__device__ __forceinline__ df ksum8(df a, df b, df c, df d, df e, df f, df g, df h) {
-  float s = a.hi, t = a.lo, r;
-  const df v[7] = {b, c, d, e, f, g, h};
-#pragma unroll
-  for (int q = 0; q < 7; ++q) {
-    two_sum(s, v[q].hi, s, r);
-    t = __fadd_rn(t, __fadd_rn(r, v[q].lo));
-  }
-  return df{s, t};
 }
 
 // Plane p and element layer p live in slot (p - kb + 1) & 3; the z loop is
@@ -177,16 +175,19 @@ __global__ void __launch_bounds__(T::NTB, T::NT <= 256 ? 4 : 2) k_df3d(DfArgs a)
   NodeFetch<MODE> own, ring;
   float2 kown = make_float2(0.f, 0.f), kring_v = make_float2(0.f, 0.f);
   bool kown_on = false, kring_on = false;
-  float2 ownq = make_float2(0.f, 0.f);
-  float2 cv[4], cq[4];
+  float2 ownq = make_float2(0.f, 0.f), ownkd = make_float2(0.f, 0.f);
+  float2 cv[4], cq[4], ckd[4];
   bool cf[4];
   df dot{0.f, 0.f};
 
   auto issue_plane = [&](int p) {
     own.issue(a, xsrc, ocol, mine, p);
-    if (MODE == RESID) {
+    {
       const int idx = ocol + NXY * min(max(p, 0), a.NZ - 1);
-      if (CK(idx, (int64_t)NXY * a.NZ)) ownq = a.q[idx];
+      if (CK(idx, (int64_t)NXY * a.NZ)) {
+        ownkd = a.kd[idx];
+        if (MODE == RESID) ownq = a.q[idx];
+      }
     }
     if (xr) ring.issue(a, xsrc, rcol, ron, p);
   };
@@ -209,6 +210,7 @@ __global__ void __launch_bounds__(T::NTB, T::NT <= 256 ? 4 : 2) k_df3d(DfArgs a)
     cv[S] = v2;                                                                            \
     cf[S] = own.f != 0;                                                                    \
     cq[S] = ownq;                                                                          \
+    ckd[S] = ownkd;                                                                        \
     if (MODE == DIR && mine && (P) >= kb && (P) < kend) pdst[ocol + NXY * (P)] = v2;       \
     if (xr) {                                                                              \
       const df w = ring.value(beta);                                                       \
@@ -270,18 +272,21 @@ __global__ void __launch_bounds__(T::NTB, T::NT <= 256 ? 4 : 2) k_df3d(DfArgs a)
                              X[S2][cy + 1][cx - 1]);                                           \
         const df f111 = far4(X[S1][cy + 1][cx + 1], X[S2][cy][cx + 1], X[S2][cy + 1][cx],     \
                              X[S2][cy + 1][cx + 1]);                                           \
-        float ah = 0.f, al = 0.f;                                                          \
-        acc_prod(ah, al, k000, f000);                                                      \
+        /* two independent accumulators (elements below and above the plane) */         \
+        float ah, al, bh, bl;                                                              \
+        acc_first(ah, al, k000, f000);                                                     \
+        acc_first(bh, bl, k100, f100);                                                     \
         acc_prod(ah, al, k001, f001);                                                      \
+        acc_prod(bh, bl, k101, f101);                                                      \
         acc_prod(ah, al, k010, f010);                                                      \
+        acc_prod(bh, bl, k110, f110);                                                      \
         acc_prod(ah, al, k011, f011);                                                      \
-        acc_prod(ah, al, k100, f100);                                                      \
-        acc_prod(ah, al, k101, f101);                                                      \
-        acc_prod(ah, al, k110, f110);                                                      \
-        acc_prod(ah, al, k111, f111);                                                      \
-        const df ks = ksum8(k000, k001, k010, k011, k100, k101, k110, k111);               \
-        const df diag = df_mul(df{4.f * ks.hi, 4.f * ks.lo}, dfk(xi));                     \
-        yv = df_mul(df_sub(diag, df_make(ah, al)), scale);                                 \
+        acc_prod(bh, bl, k111, f111);                                                      \
+        float sh, se;                                                                      \
+        two_sum(ah, bh, sh, se);                                                           \
+        const df acc = df_make(sh, __fadd_rn(se, __fadd_rn(al, bl)));                      \
+        const df diag = df_mul(dfk(ckd[S1]), dfk(xi));                                     \
+        yv = df_mul(df_sub(diag, acc), scale);                                 \
       }                                                                                    \
       if (MODE == RESID) {                                                                 \
         const df ri = df_sub(dfk(cq[S1]), yv);                                             \
@@ -344,6 +349,7 @@ DfArgs base_args(Ctx& c) {
   a.NZ = d.NZ;
   a.fixed = c.fixed;
   a.ke = c.ke_df;
+  a.kd = c.kd_df;
   a.partials = c.partials;
   a.counter = c.counter;
   return a;
@@ -369,7 +375,39 @@ int runs(const Ctx& c, int sms) {
   return c.df3d_tile ? runs_for<MODE, T43x11>(c.L[0], sms) : runs_for<MODE, T32x8>(c.L[0], sms);
 }
 
+// kd_i = 4 sum_e k_e over the (up to 8) elements around node i, df64: a
+// TwoSum chain of the high words, low words and errors added, then
+// normalised; the factor 4 is exact
+__global__ void k_node_kdiag(const float2* __restrict__ ke, float2* __restrict__ kd, int ex, int ey,
+                             int ez) {
+  const int NX = ex + 1, NY = ey + 1, NZ = ez + 1;
+  const int64_t n = (int64_t)NX * NY * NZ;
+  const int64_t id = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= n) return;
+  const int i = (int)(id % NX), j = (int)((id / NX) % NY), k = (int)(id / ((int64_t)NX * NY));
+  float s = 0.f, t = 0.f;
+  for (int dz = -1; dz <= 0; ++dz)
+    for (int dy = -1; dy <= 0; ++dy)
+      for (int dx = -1; dx <= 0; ++dx) {
+        const int e0 = i + dx, e1 = j + dy, e2 = k + dz;
+        if (e0 < 0 || e0 >= ex || e1 < 0 || e1 >= ey || e2 < 0 || e2 >= ez) continue;
+        const float2 v = ke[e0 + (int64_t)ex * (e1 + (int64_t)ey * e2)];
+        float r;
+        two_sum(s, v.x, s, r);
+        t = __fadd_rn(t, __fadd_rn(r, v.y));
+      }
+  const df d = df_make(s, t);
+  kd[id] = make_float2(4.f * d.hi, 4.f * d.lo);
+}
+
 }  // namespace d3d
+
+// per-node diagonal factor of the df64 operator for the current k_e
+void df3d_node_diag(Ctx& c) {
+  const Dims& d = c.L[0];
+  d3d::k_node_kdiag<<<blocks_for(d.n), kThreads, 0, c.stream>>>(c.ke_df, c.kd_df, d.ex, d.ey, d.ez);
+  MGAR_LAUNCH_CHECK();
+}
 
 void df3d_prepare(Ctx& c) {
   using namespace d3d;
