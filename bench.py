@@ -39,7 +39,8 @@ def parse():
     ap.add_argument("--cycles", type=int, default=0, help="design cycles per step (0 = workload's)")
     ap.add_argument("--guess", default="previous", choices=["previous", "zero"])
     ap.add_argument("--eps1", type=float, default=None)
-    ap.add_argument("--kernel", default=None, choices=["df3d", "apply64", "smooth0", "galerkin0"],
+    ap.add_argument("--kernel", default=None,
+                    choices=["df3d", "apply64", "apply32", "resid64", "smooth0", "galerkin0"],
                     help="kernel class of the roofline (default: the dominant one of the path)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 MGCG comparison run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
@@ -174,6 +175,20 @@ def kernel_model(kernel, w):
         # p (8 B each), z (4 B), one k_e (8 B), 4 sum k_e (8 B), mask (1 B):
         # 45.
         return 45 * n, 344 * n, "alu", "fp32"
+    if kernel == "apply32":
+        # mixed path, 3D: FP32 product of a CG iteration with the fused
+        # direction update and p.Ap (tiled, 21-point H8 stencil): read z,
+        # p_old, k_e (4 B each) and the mask (1 B), write p and A p (4 B
+        # each): 21 B per node
+        return 21 * n, 0, "hbm", None
+    if kernel == "resid64":
+        # mixed path, 3D: df64 residual r = q - A x in the difference form,
+        # per node in FP32-pipe operations: 12 face-diagonal weight sums 96
+        # (TwoSum pair 8), 20 terms 380 (exact difference 8, TwoProd with
+        # cross terms 4, TwoSum accumulation 8 minus the shared 1), 1/12
+        # scale 7, q - A x 11, r.r 18, FP32 copy 1: 513.  Bytes: x, q, one
+        # k_e (8 B each), mask (1 B), FP32 r (4 B): 29.
+        return 29 * n, 513 * n, "alu", "fp32"
     if kernel == "apply64":
         # 3D H8 y = A x in FP64, node-centred: read x (8 B) and one k_e per
         # node (8 B, each element read once) and the fixed-node mask (1 B),
@@ -181,15 +196,17 @@ def kernel_model(kernel, w):
         # sums, 20 FMA, 3 multiplies), + 2 for the fused p.Ap dot.
         return 25 * n, 64 * n, "alu", "fp64"
     if kernel == "smooth0":
-        # FP32 level-0 fused smoothing passes of the V-cycle: read b, dinv
-        # (8 B), k_e (4 B), mask (1 B), x (4 B), write x and r (8 B)
-        return 25 * n, 0, "hbm", None
+        # FP32 level-0 passes of the V-cycle, per node 21 B for either: the
+        # pre-smoothing pass reads b, D^-1, one k_e (4 B each) and the mask
+        # (1 B) and writes x and r (4 B each); the post-smoothing sweep reads
+        # x, b, D^-1, one k_e and the mask and writes x'
+        return 21 * n, 0, "hbm", None
     if kernel == "galerkin0":
         return 8 * e + 64 * 4 * e // 8, 0, "hbm", None
     raise ValueError(kernel)
 
 
-KC = {"df3d": 1, "apply64": 1, "smooth0": 2, "galerkin0": 5}
+KC = {"df3d": 1, "apply64": 1, "smooth0": 2, "galerkin0": 5, "apply32": 8, "resid64": 9}
 
 
 # ------------------------------------------------------------- GPU arm
@@ -233,8 +250,12 @@ def run_gpu(args):
 
     # timed region: K whole runs, L2 flushed between them (outside the events)
     sampler = ClockSampler(local)
-    kernel = args.kernel or ("df3d" if prec == mgar.MGAR_MIXED and w.nz else "apply64")
-    kc = KC[kernel]
+    if args.kernel:
+        kernels = [args.kernel]
+    elif prec == mgar.MGAR_MIXED and w.nz:
+        kernels = ["apply32", "smooth0", "resid64"]
+    else:
+        kernels = ["apply64"]
     times = []
     infos = []
     barrier(world)
@@ -253,23 +274,29 @@ def run_gpu(args):
     launches = mgar.kernel_launches() - launches0
     torch.cuda.synchronize()
     barrier(world)
-    # The dominant kernel's launches are timed with CUDA events on the
-    # handle's stream over a second timed region of the same K runs: events
-    # between launches keep the CG on its host-driven loop, so they stay out
-    # of the region that gives `value`.
-    solver.profile_start(kc)
-    prof_times = []
-    for _ in range(args.steps):
-        flush.zero_()
-        start = torch.cuda.Event(enable_timing=True)
-        end = torch.cuda.Event(enable_timing=True)
-        start.record(stream)
-        one_run(solver, rho, T)
-        end.record(stream)
-        end.synchronize()
-        prof_times.append(start.elapsed_time(end))
-    kern_ms, kern_launches = solver.profile_stop()
+    # The launches of each candidate kernel class are timed with CUDA events
+    # on the handle's stream, each class over one more timed region of the
+    # same K runs: events between launches keep the CG on its host-driven
+    # loop, so they stay out of the region that gives `value`.  The class
+    # with the largest share of its region is the dominant kernel.
+    prof = {}
+    for kname in kernels:
+        solver.profile_start(KC[kname])
+        prof_times = []
+        for _ in range(args.steps):
+            flush.zero_()
+            start = torch.cuda.Event(enable_timing=True)
+            end = torch.cuda.Event(enable_timing=True)
+            start.record(stream)
+            one_run(solver, rho, T)
+            end.record(stream)
+            end.synchronize()
+            prof_times.append(start.elapsed_time(end))
+        k_ms, k_n = solver.profile_stop()
+        prof[kname] = (k_ms, k_n, sum(prof_times))
     torch.cuda.synchronize()
+    kernel = max(prof, key=lambda k: prof[k][0] / prof[k][2])
+    kern_ms, kern_launches, prof_total = prof[kernel]
     clocks = sampler.stop()
     step_ms = max_over_ranks(statistics.mean(times), world)
     value = step_ms / (cycles * world)
@@ -366,8 +393,12 @@ def run_gpu(args):
                 "frac": achieved / peak, "traffic": TRAFFIC.get(kernel),
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs" if "hbm_gbs" in peaks else "fallback"}
     roof.update({"kernel": kernel, "launches": kern_launches, "avg_launch_us": avg_ms * 1e3,
-                 "share_of_step": kern_ms / sum(prof_times),
-                 "timed_region": "a second timed region of the same runs, events around each launch"})
+                 "share_of_step": kern_ms / prof_total,
+                 "timed_region": "one more timed region of the same runs per kernel class, "
+                                 "events around each launch",
+                 "classes": [{"kernel": k, "launches": v[1],
+                              "avg_launch_us": v[0] / max(v[1], 1) * 1e3,
+                              "share_of_step": v[0] / v[2]} for k, v in prof.items()]})
 
     n_mgcg = sum(1 for i in infos if i["used_mgcg"])
     n_acc = sum(1 for i in infos if i["accepted"])
@@ -378,7 +409,8 @@ def run_gpu(args):
         "config": {"workload": args.workload, "grid": f"{w.nx}x{w.ny}x{w.nz} H8" if w.nz else
                    f"{w.nx}x{w.ny} Q4", "dofs": w.n_nodes, "cycles_per_step": cycles,
                    "nl": w.nl, "m": w.m, "eps1": p_mix.eps1, "eps2": w.eps2,
-                   "basis_guess": args.guess, "precision": "mixed (FP32 V-cycle, FP64 CG/GS/reduced)" if prec == mgar.MGAR_MIXED
+                   "basis_guess": args.guess, "precision": "mixed (FP32 V-cycle and CG with df64 reliable updates; FP64 scalars, "
+                                "Gram-Schmidt and reduced system)" if prec == mgar.MGAR_MIXED
                    else "fp64",
                    "parallelism": f"replicas x{world}", "l2": "flushed (256 MB write) between steps"},
         "cycles": {"mgcg": n_mgcg, "mgar_accepted": n_acc,

@@ -199,13 +199,18 @@ int mgar_run(mgar_t h, const double* rho_host, int cycles, double* rho_out_host,
 /* Instrumentation (no counterpart in the paper).  Kernel classes whose
  * launches can be timed with CUDA events on the handle's stream: */
 #define MGAR_KC_APPLY64 1 /* finest-level K x of the outer CG and the MGAR projection:
-                             FP64, or double-float (df64) in the mixed path */
+                             FP64, or double-float (df64) in the mixed path (on 3D
+                             grids the mixed path's CG iterations use MGAR_KC_APPLY32
+                             and its residuals MGAR_KC_RESID64) */
 #define MGAR_KC_SMOOTH0 2 /* finest-level smoothing passes of the V-cycle (any precision) */
 #define MGAR_KC_RESID0 3  /* finest-level residual inside the V-cycle */
 #define MGAR_KC_OC 4      /* OC bisection pass */
 #define MGAR_KC_GALERKIN0 5 /* Galerkin element matrices of level 1 */
 #define MGAR_KC_FILTER 6  /* density filter / its transpose */
 #define MGAR_KC_SENS 7    /* element sensitivities (Eq. 10) */
+#define MGAR_KC_APPLY32 8 /* mixed path, 3D: FP32 direction update + K p + p.Kp of a CG iteration */
+#define MGAR_KC_RESID64 9 /* mixed path, 3D: df64 residual q - K x of the CG (its start and
+                             every reliable update) */
 #define MGAR_KC_TIMELINE 100 /* every launch site: device time between consecutive launches */
 
 /* Start timing every launch of one kernel class (0 stops).  Each launch

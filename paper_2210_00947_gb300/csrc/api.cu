@@ -21,7 +21,9 @@ Ctx*& current_ctx() {
 }
 void prof_mark(const char* site) {
   Ctx* c = current_ctx();
-  if (!c || c->prof_class != MGAR_KC_TIMELINE || c->stream == c->cap_stream) return;
+  if (!c || c->prof_class != MGAR_KC_TIMELINE || c->stream == c->cap_stream ||
+      c->stream == c->cap_stream2)
+    return;
   if (c->prof_used >= 2 * kProfMax) return;
   cudaEventRecord(c->prof_ev[c->prof_used], c->stream);
   c->prof_sites[c->prof_used] = site;
@@ -84,7 +86,9 @@ void free_ctx(Ctx& c) {
   for (auto& g : c.graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   if (c.cg_exec) cudaGraphExecDestroy(c.cg_exec);
+  if (c.ru_exec) cudaGraphExecDestroy(c.ru_exec);
   if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
+  if (c.cap_stream2) cudaStreamDestroy(c.cap_stream2);
   free_hierarchy(c);
   if (c.prof_ev) {
     for (int i = 0; i < 2 * kProfMax; ++i)
@@ -97,7 +101,7 @@ void free_ctx(Ctx& c) {
   cudaFree(c.run_rho);
   cudaFree(c.run_T);
   void* ptrs[] = {c.fixed, c.efix, c.gfix, c.q, c.rho_phys, c.ke, c.ke0, c.ke_f, c.ke0_f, c.inv_hs, c.f_offs, c.f_w,
-                  c.dv, c.rsdv, c.r, c.z, c.pv, c.Ap, c.tm, c.tmp_dc, c.R, c.W, c.b32, c.x32, c.ke_df, c.df_q, c.df_x, c.df_r, c.df_p, c.df_Ap, c.df_p2, c.df_e, c.kd_df, c.tmp_e, c.oc_s, c.oc_lo,
+                  c.dv, c.rsdv, c.r, c.z, c.pv, c.Ap, c.tm, c.tmp_dc, c.R, c.W, c.b32, c.x32, c.ke_df, c.df_q, c.df_x, c.df_r, c.df_p, c.df_Ap, c.df_p2, c.df_e, c.kd_df, c.xc32, c.p32, c.p32b, c.y32, c.tmp_e, c.oc_s, c.oc_lo,
                   c.oc_hi, c.oc_s32, c.oc_lo32, c.oc_hi32, c.dv32, c.oc_amb, c.oc_namb, c.partials, c.counter, c.dsc, c.derr};
   for (void* p : ptrs) cudaFree(p);
   if (c.hsc) cudaFreeHost(c.hsc);
@@ -236,6 +240,7 @@ int mgar_create(mgar_t* out, const mgar_params* p, const uint8_t* fixed_mask, co
     c->grid_blocks_e = (int)std::min<int64_t>(blocks_for(ne), (int64_t)c->sms * 8);
 
     MGAR_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    MGAR_CUDA(cudaStreamCreateWithFlags(&c->cap_stream2, cudaStreamNonBlocking));
     MGAR_CUDA(cudaMalloc(&c->fixed, n));
     MGAR_CUDA(cudaMalloc(&c->q, n * sizeof(double)));
     MGAR_CUDA(cudaMalloc(&c->rho_phys, ne * sizeof(double)));
@@ -271,6 +276,8 @@ int mgar_create(mgar_t* out, const mgar_params* p, const uint8_t* fixed_mask, co
       MGAR_CUDA(cudaMalloc(&c->df_e, ne * sizeof(float2)));
       for (float2** v : {&c->df_q, &c->df_x, &c->df_r, &c->df_p, &c->df_Ap, &c->df_p2, &c->kd_df})
         MGAR_CUDA(cudaMalloc(v, n * sizeof(float2)));
+      for (float** v : {&c->xc32, &c->p32, &c->p32b, &c->y32})
+        MGAR_CUDA(cudaMalloc(v, n * sizeof(float)));
     }
     MGAR_CUDA(cudaMalloc(&c->partials, (size_t)32 * maxb * sizeof(double)));
 #ifdef MGAR_CHECKED
@@ -358,6 +365,8 @@ int mgar_create(mgar_t* out, const mgar_params* p, const uint8_t* fixed_mask, co
     bottom_prepare(*c);
     if (const char* np = std::getenv("MGAR_NO_PDL")) c->use_pdl = np[0] != '1';
     if (const char* ng = std::getenv("MGAR_NO_CG_GRAPH")) c->cg_graph = ng[0] != '1';
+    if (const char* dc = std::getenv("MGAR_DF64_CG")) c->ru_cg = dc[0] != '1';
+    if (const char* rd = std::getenv("MGAR_RU_DELTA")) c->ru_delta = std::atof(rd);
     if (const char* fp = std::getenv("MGAR_FUSED_POST")) c->split_post = fp[0] != '1';
     if (const char* sc = std::getenv("MGAR_SPLIT_COARSE")) c->split_coarse_nodes = std::atoll(sc);
     if (const char* bn = std::getenv("MGAR_BOTTOM_NODES")) c->bottom_nodes = std::atoll(bn);

@@ -1,4 +1,7 @@
-// MGCG of the mixed-precision path in double-float arithmetic.
+// MGCG of the mixed-precision path.  3D grids by default run FP32 CG
+// iterations with reliable df64 updates (solve_mgcg_ru3, below); the rest of
+// this file is the CG in double-float arithmetic (2D grids, and 3D on
+// request).
 //
 // The outer conjugate-gradient iteration (Sections 1 and 3.2) keeps its
 // vectors as df64 pairs (about 48 bits) and runs every operation on the FP32
@@ -162,7 +165,7 @@ __global__ void k_df_cg_xr(float2* __restrict__ x, float2* __restrict__ r, const
   pdl_wait();
   // device-side CG loop: the two direction buffers swap with the parity
   if (parity && (((int)*parity) & 1)) p = p_alt;
-  const df alpha = df_from_double(*rz / *pap);
+  const df alpha = block_div_df(rz, pap);
   df acc{0.f, 0.f};
   const int stride = gridDim.x * blockDim.x;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -191,14 +194,13 @@ __global__ void k_df_cg_xr(float2* __restrict__ x, float2* __restrict__ r, const
     if (r32) r32[i] = __fadd_rn(ri.hi, ri.lo);
     acc = df_add(acc, df_mul(ri, ri));
   }
-  double v[1] = {df_to_double(acc)};
-  block_sum_finish<1>(v, partials, counter, out);
+  block_sum_finish_df(acc, partials, counter, out);
 }
 
 // p = z + (rz_new / rz_old) p, z in FP32
 __global__ void k_df_cg_p(float2* __restrict__ p, const float* __restrict__ z, int n,
                           const double* __restrict__ rz_new, const double* __restrict__ rz_old) {
-  const df beta = df_from_double(*rz_new / *rz_old);
+  const df beta = block_div_df(rz_new, rz_old);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     p[i] = pack(df_add(df{z[i], 0.f}, df_mul(beta, unpack(p[i]))));
 }
@@ -209,8 +211,7 @@ __global__ void k_df_dot_f(const float2* __restrict__ r, const float* __restrict
   df acc{0.f, 0.f};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
     acc = df_add(acc, df_mulf(unpack(r[i]), z[i]));
-  double v[1] = {df_to_double(acc)};
-  block_sum_finish<1>(v, partials, counter, out);
+  block_sum_finish_df(acc, partials, counter, out);
 }
 
 __global__ void k_df_to_f32(const float2* __restrict__ a, float* __restrict__ b, int n) {
@@ -494,8 +495,295 @@ static int solve_mgcg_df3(Ctx& c, double* T, int* iters, double* relres) {
   return rel <= c.p.eps2 ? MGAR_OK : MGAR_ERR_MAXIT;
 }
 
+// ---------------------------------------------------------------------------
+// 3D: FP32 conjugate-gradient iterations with reliable updates.
+//
+// The Krylov vectors (the correction xc accumulated since the last update,
+// r, p, A p) are FP32, so an iteration costs an FP32 product instead of the
+// df64 one.  Whenever the recursively updated ||r|| has fallen below
+// ru_delta times its value at the last update, or below eps2 ||q||, or the
+// iteration limit is reached, the correction is added to the df64 solution
+// (x += xc, xc = 0) and r is recomputed from it in df64 (r = q - A x): the
+// reliable updates of Sleijpen and van der Vorst ("Reliable updated
+// residuals in hybrid Bi-CG methods", Computing 56, 1996), as mixed-precision
+// lattice solvers use them.  The search direction is kept across an update.
+// Convergence is decided on the recomputed residual, so the reported
+// ||r|| / ||q|| is a df64 residual of the returned x.
+
+// alpha = rz / pAp; xc += alpha p; r -= alpha A p; ||r||^2
+__global__ void k_cg_xr32(float* __restrict__ xc, float* __restrict__ r, const float* __restrict__ p,
+                          const float* __restrict__ p_alt, const double* parity,
+                          const float* __restrict__ Ap, int n, const double* __restrict__ rz,
+                          const double* __restrict__ pap, double* partials, unsigned int* counter,
+                          double* out) {
+  pdl_wait();
+  if (parity && (((int)*parity) & 1)) p = p_alt;
+  const float alpha = block_div_f(rz, pap);
+  float acc = 0.f;
+  const int stride = gridDim.x * blockDim.x;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + stride < n; i += 2 * stride) {
+    const int j = i + stride;
+    const float xa = xc[i], xb = xc[j], pa = p[i], pb = p[j];
+    const float ra = r[i], rb = r[j], qa = Ap[i], qb = Ap[j];
+    xc[i] = fmaf(alpha, pa, xa);
+    xc[j] = fmaf(alpha, pb, xb);
+    const float ria = fmaf(-alpha, qa, ra), rib = fmaf(-alpha, qb, rb);
+    r[i] = ria;
+    r[j] = rib;
+    acc = fmaf(ria, ria, acc);
+    acc = fmaf(rib, rib, acc);
+  }
+  for (; i < n; i += stride) {
+    xc[i] = fmaf(alpha, p[i], xc[i]);
+    const float ri = fmaf(-alpha, Ap[i], r[i]);
+    r[i] = ri;
+    acc = fmaf(ri, ri, acc);
+  }
+  block_sum_finish_df(df{acc, 0.f}, partials, counter, out);
+}
+
+// iteration count, buffer parity, first-direction flag and the reference
+// ||r|| after the initial residual
+__global__ void k_ru_start(double* dsc) {
+  dsc[S_CGIT] = 0.0;
+  dsc[S_CGPAR] = 0.0;
+  dsc[S_CGFIRST] = 1.0;
+  dsc[S_RMAX] = sqrt(dsc[S_RR]);
+  dsc[S_RUCOUNT] = 0.0;
+}
+
+// after an iteration: count it, flip the parity, and decide whether a
+// reliable update is due: ||r|| <= eps2 ||q||, ||r|| <= delta ||r||_last
+// update, cg_max iterations, or a non-finite ||r||.  Inside the graph the
+// decision sets the IF node of the update (ru) and, when no update follows,
+// the WHILE loop goes on; the flag is also left in S_FLAG.
+__global__ void k_ru_check(double* dsc, double qnorm, double eps2, double delta, int cg_max,
+                           cudaGraphConditionalHandle ru, int set) {
+  const double rn = sqrt(dsc[S_RR]);
+  const int it = (int)dsc[S_CGIT] + 1;
+  dsc[S_CGIT] = (double)it;
+  dsc[S_CGPAR] = (double)(((int)dsc[S_CGPAR]) ^ 1);
+  dsc[S_CGFIRST] = 0.0;
+  const bool upd = !(isfinite(rn) && rn > eps2 * qnorm && rn > delta * dsc[S_RMAX] && it < cg_max);
+  dsc[S_FLAG] = upd ? 1.0 : 0.0;
+  if (set) cudaGraphSetConditional(ru, upd ? 1u : 0u);
+}
+
+// x += xc in df64, xc = 0
+__global__ void k_ru_update(float2* __restrict__ x, float* __restrict__ xc, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    x[i] = pack(df_add(unpack(x[i]), df{xc[i], 0.f}));
+    xc[i] = 0.f;
+  }
+}
+
+__global__ void k_ru_mark(double* dsc) {
+  dsc[S_RMAX] = sqrt(dsc[S_RR]);
+  dsc[S_RUCOUNT] += 1.0;
+}
+
+// end of a pass of the graph's WHILE body: stop once an update has shown
+// ||r|| <= eps2 ||q||, at cg_max iterations, or on a non-finite ||r||
+__global__ void k_ru_loop(double* dsc, double qnorm, double eps2, int cg_max,
+                          cudaGraphConditionalHandle loop) {
+  const double rn = sqrt(dsc[S_RR]);
+  const int it = (int)dsc[S_CGIT];
+  const bool conv = dsc[S_FLAG] != 0.0 && rn <= eps2 * qnorm;
+  const bool go = !conv && isfinite(rn) && it < cg_max;
+  cudaGraphSetConditional(loop, go ? 1u : 0u);
+}
+
+// One FP32 iteration: V-cycle z = M r with r . z into RZ1, direction update
+// and product (beta = RZ1 / RZ0, then RZ0 <- RZ1), update of xc and r, and
+// the update decision.  set: inside the graph (the decision sets the IF
+// handle ru); otherwise the V-cycle is replayed from its own graph and the
+// host reads the decision.
+static void ru_iteration(Ctx& c, cudaGraphConditionalHandle ru, bool set) {
+  const int n = (int)c.n;
+  if (set) {
+    vcycle_dot(c, c.b32, c.x32, nullptr, c.dsc + S_RZ1);
+  } else {
+    const bool prof_inside = c.prof_class == MGAR_KC_SMOOTH0 || c.prof_class == MGAR_KC_RESID0;
+    run_graph(c, 10, c.b32, c.x32, prof_inside,
+              [&] { vcycle_dot(c, c.b32, c.x32, nullptr, c.dsc + S_RZ1); });
+  }
+  {
+    ProfScope ps(c, MGAR_KC_APPLY32);
+    fine3d_dir(c, c.x32, c.p32, c.p32b, c.dsc + S_RZ1, c.dsc + S_RZ0, c.dsc + S_CGFIRST,
+               c.dsc + S_CGPAR, c.y32, c.dsc + S_PAP, c.dsc + S_RZ0);
+  }
+  // parity 0: the new p is in p32b
+  launch_pdl(c.stream, c.use_pdl, k_cg_xr32, dim3(c.grid_blocks), dim3(kThreads), c.xc32, c.b32,
+             (const float*)c.p32b, (const float*)c.p32, (const double*)(c.dsc + S_CGPAR),
+             (const float*)c.y32, n, (const double*)(c.dsc + S_RZ0),
+             (const double*)(c.dsc + S_PAP), c.partials, c.counter, c.dsc + S_RR);
+  MGAR_LAUNCH_CHECK();
+  k_ru_check<<<1, 1, 0, c.stream>>>(c.dsc, c.qnorm, c.p.eps2, c.ru_delta, c.p.cg_max, ru,
+                                    set ? 1 : 0);
+  MGAR_LAUNCH_CHECK();
+}
+
+// Reliable update: x += xc, r = q - A x in df64 (only its FP32 copy and
+// ||r||^2 are kept), reference ||r|| for the next decision.
+static void ru_update(Ctx& c) {
+  k_ru_update<<<c.grid_blocks, kThreads, 0, c.stream>>>(c.df_x, c.xc32, (int)c.n);
+  MGAR_LAUNCH_CHECK();
+  {
+    ProfScope ps(c, MGAR_KC_RESID64);
+    df3d_resid(c, c.df_q, c.df_x, nullptr, c.b32, c.dsc + S_RR);
+  }
+  k_ru_mark<<<1, 1, 0, c.stream>>>(c.dsc);
+  MGAR_LAUNCH_CHECK();
+}
+
+// The graph of the whole FP32 iteration with its reliable updates: one
+// WHILE node (condition 1 at every launch) whose body is an iteration, an
+// IF node holding the update (condition set by the iteration's decision),
+// and the loop test.  The host waits once per solve.  False if the device or
+// driver refuses any part (the host loop is used then).
+static bool build_ru_graph(Ctx& c) {
+  cudaGraph_t g = nullptr;
+  cudaGraphConditionalHandle loop = 0, ru = 0;
+  cudaStream_t saved = c.stream;
+  bool ok = false;
+  const int64_t before = launches_so_far();
+  int64_t upd_kernels = 0;
+  do {
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) break;
+    if (cudaGraphConditionalHandleCreate(&loop, g, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+      break;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = loop;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wnode = nullptr;
+    if (cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &cp) != cudaSuccess) break;
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    if (cudaGraphConditionalHandleCreate(&ru, body, 0, cudaGraphCondAssignDefault) != cudaSuccess)
+      break;
+    if (cudaStreamBeginCaptureToGraph(c.cap_stream, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      break;
+    c.stream = c.cap_stream;
+    bool issued = true;
+    try {
+      ru_iteration(c, ru, true);
+      // the IF node after the decision, its body captured on a second stream
+      cudaStreamCaptureStatus st;
+      cudaGraph_t bg = nullptr;
+      const cudaGraphNode_t* deps = nullptr;
+      const cudaGraphEdgeData* edges = nullptr;
+      size_t ndeps = 0;
+      MGAR_CUDA(cudaStreamGetCaptureInfo(c.stream, &st, nullptr, &bg, &deps, &edges, &ndeps));
+      cudaGraphNodeParams ip = {};
+      ip.type = cudaGraphNodeTypeConditional;
+      ip.conditional.handle = ru;
+      ip.conditional.type = cudaGraphCondTypeIf;
+      ip.conditional.size = 1;
+      cudaGraphNode_t inode = nullptr;
+      MGAR_CUDA(cudaGraphAddNode(&inode, bg, deps, nullptr, ndeps, &ip));
+      cudaGraph_t ibody = ip.conditional.phGraph_out[0];
+      MGAR_CUDA(cudaStreamBeginCaptureToGraph(c.cap_stream2, ibody, nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal));
+      c.stream = c.cap_stream2;
+      const int64_t u0 = launches_so_far();
+      bool upd_ok = true;
+      try {
+        ru_update(c);
+      } catch (...) {
+        upd_ok = false;
+      }
+      upd_kernels = launches_so_far() - u0;
+      cudaGraph_t iout = nullptr;
+      const cudaError_t ie = cudaStreamEndCapture(c.cap_stream2, &iout);
+      c.stream = c.cap_stream;
+      if (!upd_ok || ie != cudaSuccess) throw Error{MGAR_ERR_CUDA, "update capture failed"};
+      MGAR_CUDA(cudaStreamUpdateCaptureDependencies(c.stream, &inode, nullptr, 1,
+                                                    cudaStreamSetCaptureDependencies));
+      k_ru_loop<<<1, 1, 0, c.stream>>>(c.dsc, c.qnorm, c.p.eps2, c.p.cg_max, loop);
+      MGAR_LAUNCH_CHECK();
+    } catch (...) {
+      issued = false;
+    }
+    cudaGraph_t bout = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c.cap_stream, &bout);
+    c.stream = saved;
+    if (!issued || e != cudaSuccess) break;
+    if (cudaGraphInstantiate(&c.ru_exec, g, 0) != cudaSuccess) {
+      c.ru_exec = nullptr;
+      break;
+    }
+    ok = true;
+  } while (false);
+  if (!ok) (void)cudaGetLastError();
+  c.stream = saved;
+  const int64_t captured = launches_so_far() - before;
+  count_launches(-captured);  // captured, not executed
+  c.ru_body_kernels = captured - upd_kernels;
+  c.ru_update_kernels = upd_kernels;
+  if (g) cudaGraphDestroy(g);
+  return ok;
+}
+
+static int solve_mgcg_ru3(Ctx& c, double* T, int* iters, double* relres) {
+  const int n = (int)c.n;
+  k_d_to_df<<<blocks_for(n), kThreads, 0, c.stream>>>(T, c.df_x, n);
+  MGAR_LAUNCH_CHECK();
+  {
+    ProfScope ps(c, MGAR_KC_RESID64);
+    df3d_resid(c, c.df_q, c.df_x, nullptr, c.b32, c.dsc + S_RR);
+  }
+  fetch_scalars(c, S_RR, 1);
+  double rel = std::sqrt(c.hsc[S_RR]) / c.qnorm;
+  int it = 0;
+  if (!(rel <= c.p.eps2)) {
+    require(std::isfinite(rel), MGAR_ERR_NONFINITE, "non-finite initial residual");
+    MGAR_CUDA(cudaMemsetAsync(c.xc32, 0, (size_t)n * sizeof(float), c.stream));
+    k_ru_start<<<1, 1, 0, c.stream>>>(c.dsc);
+    MGAR_LAUNCH_CHECK();
+    // the graph while no kernel class is being timed with events
+    const bool use_graph = c.cg_graph && c.prof_class == 0 && c.use_graphs &&
+                           (c.ru_exec || build_ru_graph(c));
+    if (use_graph) {
+      MGAR_CUDA(cudaGraphLaunch(c.ru_exec, c.stream));
+      fetch_scalars(c, S_RR, S_CGIT - S_RR + 1);
+      it = (int)c.hsc[S_CGIT];
+      fetch_scalars(c, S_RUCOUNT, 1);
+      count_launches((int64_t)it * c.ru_body_kernels +
+                     (int64_t)c.hsc[S_RUCOUNT] * c.ru_update_kernels);
+      rel = std::sqrt(c.hsc[S_RR]) / c.qnorm;
+    } else {
+      double rmax = std::sqrt(c.hsc[S_RR]);  // ||r|| at the last reliable update
+      while (true) {
+        ru_iteration(c, 0, false);
+        fetch_scalars(c, S_RR, S_CGIT - S_RR + 1);
+        const double rn = std::sqrt(c.hsc[S_RR]);
+        it = (int)c.hsc[S_CGIT];
+        if (std::isfinite(rn) && rn > c.p.eps2 * c.qnorm && rn > c.ru_delta * rmax &&
+            it < c.p.cg_max)
+          continue;
+        ru_update(c);
+        fetch_scalars(c, S_RR, 1);
+        rmax = std::sqrt(c.hsc[S_RR]);
+        rel = rmax / c.qnorm;
+        require(std::isfinite(rel), MGAR_ERR_NONFINITE, "CG breakdown (non-finite residual)");
+        if (rel <= c.p.eps2 || it >= c.p.cg_max) break;
+      }
+    }
+    require(std::isfinite(rel), MGAR_ERR_NONFINITE, "CG breakdown (non-finite residual)");
+  }
+  k_df_to_d<<<blocks_for(n), kThreads, 0, c.stream>>>(c.df_x, T, n);
+  MGAR_LAUNCH_CHECK();
+  if (iters) *iters = it;
+  if (relres) *relres = rel;
+  return rel <= c.p.eps2 ? MGAR_OK : MGAR_ERR_MAXIT;
+}
+
 int solve_mgcg_df(Ctx& c, double* T, int* iters, double* relres) {
-  if (c.dim == 3 && !c.untiled) return solve_mgcg_df3(c, T, iters, relres);
+  if (c.dim == 3 && !c.untiled)
+    return c.ru_cg ? solve_mgcg_ru3(c, T, iters, relres) : solve_mgcg_df3(c, T, iters, relres);
   const int n = (int)c.n;
   const int rb = c.grid_blocks;
   const DfOp op = make_op(c);

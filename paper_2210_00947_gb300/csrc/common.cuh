@@ -9,6 +9,7 @@
 #include <string>
 
 #include "../../include/mgar.h"
+#include "df64.cuh"
 
 namespace mgar {
 
@@ -60,9 +61,12 @@ enum Slot : int {
   S_QR = 96,      // 96..103 reduced right-hand side
   S_Y = 104,      // 104..111 reduced solution
   S_RES2 = 112, S_FLAG = 113, S_QQ = 114,
+  S_RUCOUNT = 115,  // FP32 CG: reliable updates so far
   S_OC_LA = 116, S_OC_LB = 117, S_OC_MUA = 118, S_OC_MUB = 119, S_OC_C = 120, S_OC_B = 121,
   S_OC_MU = 122, S_OC_FAIL = 123,
   S_OC_LPREV = 124, S_OC_HAVEPREV = 125,  // ln mu of the previous update (warm start)
+  S_CGFIRST = 126,  // FP32 CG: nonzero until the first direction is formed
+  S_RMAX = 127,     // FP32 CG: ||r|| at the last reliable update
   S_OC_CAND = 128,  // 128..158 multisection candidates mu
   S_OC_CANDL = 160, // 160..190 their ln mu
   S_COUNT = 192
@@ -172,6 +176,9 @@ struct Ctx {
   double* tmp_dc = nullptr;
   double *R = nullptr, *W = nullptr;    // [m][n]
   float *b32 = nullptr, *x32 = nullptr; // mixed-mode level-0 buffers
+  // mixed 3D CG with reliable updates: FP32 correction since the last update,
+  // the two direction buffers and A p
+  float *xc32 = nullptr, *p32 = nullptr, *p32b = nullptr, *y32 = nullptr;
   // mixed mode: double-float (hi, lo) copies for the outer CG
   float2 *ke_df = nullptr, *df_q = nullptr, *df_x = nullptr, *df_r = nullptr, *df_p = nullptr,
          *df_Ap = nullptr, *df_p2 = nullptr;
@@ -210,7 +217,7 @@ struct Ctx {
   GraphEntry graphs[kGraphs];
   bool use_graphs = true;
   bool untiled = false;  // MGAR_UNTILED=1: generic finest-level kernels (debugging aid)
-  int f3d_gz[4] = {};     // z runs of the tiled finest-level kernels [mode]
+  int f3d_gz[5] = {};     // z runs of the tiled finest-level kernels [mode]
   int df3d_gz[3] = {};    // z runs of the tiled df64 operator kernels [mode]
   bool df3d_tile = false; // their tile: 32 x 8, or 43 x 11 when that leaves fewer lanes idle
   bool bottom_ok = false; // the V-cycle's bottom levels run as one cluster launch
@@ -221,6 +228,13 @@ struct Ctx {
   bool cg_graph = true;
   cudaGraphExec_t cg_exec = nullptr;
   int64_t prologue_kernels = 0, body_kernels = 0;
+  // 3D mixed path: FP32 CG iterations with reliable updates of x and r in
+  // df64 (MGAR_DF64_CG=1 selects the df64 CG); an update whenever ||r||
+  // falls below ru_delta times its value at the previous update
+  bool ru_cg = true;
+  double ru_delta = 1e-2;
+  cudaGraphExec_t ru_exec = nullptr;
+  int64_t ru_body_kernels = 0, ru_update_kernels = 0;
   // finest post-smoothing as a thin interpolation pass + the tiled sweep
   // (faster than interpolating inside the tiled pass: 6.67 vs 6.83 ms per
   // design cycle at 128^3); MGAR_FUSED_POST=1 selects the fused pass
@@ -229,6 +243,7 @@ struct Ctx {
   // (the 65^3 level of a 128^3 grid: 6.60 vs 6.66 ms per design cycle)
   int64_t split_coarse_nodes = 100000;
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t cap_stream2 = nullptr;  // captures the body of a graph's IF node
 
   // instrumentation: CUDA-event timing of one kernel class
   int prof_class = 0;
@@ -339,25 +354,23 @@ inline int blocks_for(int64_t n, int threads = kThreads) {
 // order is fixed, so results are reproducible run to run.
 // Block, thread and grid given as linear ids (tid < nthr <= 1024; a last
 // partial warp is fine; bid < nblk), so multi-dimensional launches can use it.
+// The ticket and cross-block stage, given each warp's sums in its lane 0
+// (w; other lanes ignored).
 template <int N>
-__device__ __forceinline__ bool block_sum_last_ids(double (&v)[N], double* partials,
-                                                   unsigned int* counter, double (&total)[N],
-                                                   int tid, int nthr, int bid, int nblk) {
+__device__ __forceinline__ bool block_sum_last_core(const double (&w)[N], double* partials,
+                                                    unsigned int* counter, double (&total)[N],
+                                                    int tid, int nthr, int bid, int nblk) {
   __shared__ double sh[N][32];  // up to 1024 threads
   __shared__ double tot[N];
   __shared__ bool last;
   const int lane = tid & 31, warp = tid >> 5, nw = nthr >> 5;
 #pragma unroll
-  for (int k = 0; k < N; ++k) {
-    double s = v[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) sh[k][warp] = s;
-  }
+  for (int k = 0; k < N; ++k)
+    if (lane == 0) sh[k][warp] = w[k];
   __syncthreads();
   for (int k = tid; k < N; k += nthr) {
     double s = 0.0;
-    for (int w = 0; w < nw; ++w) s += sh[k][w];
+    for (int q = 0; q < nw; ++q) s += sh[k][q];
     if (CK((int64_t)k * nblk + bid, g_partials_len)) partials[k * nblk + bid] = s;
     __threadfence();
   }
@@ -393,6 +406,41 @@ __device__ __forceinline__ bool block_sum_last_ids(double (&v)[N], double* parti
 #pragma unroll
   for (int k = 0; k < N; ++k) total[k] = tot[k];
   return true;
+}
+
+template <int N>
+__device__ __forceinline__ bool block_sum_last_ids(double (&v)[N], double* partials,
+                                                   unsigned int* counter, double (&total)[N],
+                                                   int tid, int nthr, int bid, int nblk) {
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    double s = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    v[k] = s;
+  }
+  return block_sum_last_core<N>(v, partials, counter, total, tid, nthr, bid, nblk);
+}
+
+// One double-float value per thread: the warp sums are formed in df64 on
+// the FP32 pipe (GB300 runs FP64 at 1/58 of the FP32 rate, and an FP64
+// shuffle tree over every warp of a wide grid costs microseconds), then
+// FP64 across warps and blocks as in block_sum_last_ids.
+__device__ __forceinline__ bool block_sum_last_df(df v, double* partials, unsigned int* counter,
+                                                  double& total, int tid, int nthr, int bid,
+                                                  int nblk) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h = __shfl_down_sync(0xffffffffu, v.hi, o);
+    const float l = __shfl_down_sync(0xffffffffu, v.lo, o);
+    v = df_add(v, df{h, l});
+  }
+  double w[1] = {0.0};
+  if ((tid & 31) == 0) w[0] = df_to_double(v);
+  double t[1];
+  const bool last = block_sum_last_core<1>(w, partials, counter, t, tid, nthr, bid, nblk);
+  total = t[0];
+  return last;
 }
 
 template <int N>
@@ -462,6 +510,41 @@ __device__ __forceinline__ void block_sum_finish(double (&v)[N], double* partial
 #pragma unroll
     for (int k = 0; k < N; ++k) out[k] = t[k];
   }
+}
+
+// As block_sum_last_df over a 1D grid, storing the total to *out.
+__device__ __forceinline__ void block_sum_finish_df(df v, double* partials, unsigned int* counter,
+                                                    double* out) {
+  double t;
+  if (block_sum_last_df(v, partials, counter, t, threadIdx.x, blockDim.x, blockIdx.x, gridDim.x) &&
+      threadIdx.x == 0)
+    *out = t;
+}
+
+// *a / *b for the whole block, computed once by thread 0: GB300's FP64
+// division costs tens of FP64 operations at 1/58 of the FP32 rate, so one
+// per thread of a wide grid costs microseconds.  Every thread of the block
+// must call these, once per kernel.
+__device__ __forceinline__ double block_div(const double* a, const double* b) {
+  __shared__ double s;
+  if (threadIdx.x == 0) s = *a / *b;
+  __syncthreads();
+  return s;
+}
+__device__ __forceinline__ float block_div_f(const double* a, const double* b) {
+  __shared__ float s;
+  if (threadIdx.x == 0) s = (float)(*a / *b);
+  __syncthreads();
+  return s;
+}
+__device__ __forceinline__ df block_div_df(const double* a, const double* b) {
+  __shared__ float2 s;
+  if (threadIdx.x == 0) {
+    const df d = df_from_double(*a / *b);
+    s = make_float2(d.hi, d.lo);
+  }
+  __syncthreads();
+  return df{s.x, s.y};
 }
 
 // Deterministic block max (values >= 0) with the same last-block scheme.
@@ -710,8 +793,14 @@ void vcycle(Ctx& c, const Real* b, Real* x, bool zero_guess);
 void fine3d(Ctx& c, int mode, const float* ke, const float* b, const float* dinv, const float* x,
             const float* xc, float* out0, float* out1, const float2* rdot = nullptr,
             double* dout = nullptr);
+// FP32 CG direction update and product: p = z + beta p_old (beta = *rz_new /
+// *rz_old, 0 while *first is nonzero), y = A p with the current k_e, p . y
+// into *dot; odd *parity swaps p_old and p; rz_set receives *rz_new
+void fine3d_dir(Ctx& c, const float* z, const float* p_old, float* p, const double* rz_new,
+                const double* rz_old, const double* first, const double* parity, float* y,
+                double* dot, double* rz_set);
 // zero-guess FP32 V-cycle x = M b that also leaves r . x in *dout (r in
-// double-float pairs; 3D tiled path)
+// double-float pairs, or r = b when r is null; 3D tiled path)
 void vcycle_dot(Ctx& c, const float* b, float* x, const float2* r, double* dout);
 // launch shapes of the tiled kernels (occupancy query; call outside stream capture)
 void fine3d_prepare(Ctx& c);
@@ -833,7 +922,8 @@ void run_graph(Ctx& c, int kind, const void* a, const void* b, bool profiled_ins
   static const char* kGraphSites[] = {"graph:0", "graph:1 precondition", "graph:2 mgar-vcycle64-zero",
                                       "graph:3 mgar-vcycle64-guess", "graph:4 mgar-vcycle32-zero",
                                       "graph:5 mgar-vcycle32-guess", "graph:6 precondition-df",
-                                      "graph:7", "graph:8 precondition-rz", "graph:9 precondition-rz"};
-  prof_mark(kGraphSites[kind >= 0 && kind < 10 ? kind : 0]);
+                                      "graph:7", "graph:8 precondition-rz", "graph:9 precondition-rz",
+                                      "graph:10 precondition-rz32"};
+  prof_mark(kGraphSites[kind >= 0 && kind < 11 ? kind : 0]);
 }
 }  // namespace mgar

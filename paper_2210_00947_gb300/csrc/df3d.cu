@@ -3,27 +3,37 @@
 //
 // Same z-marching tile as the V-cycle's finest-level kernels: a TX x TY
 // block (43 x 11 on 129-node planes, else 32 x 8) walks a run of node
-// planes, the operand planes (float2 hi/lo pairs, zero on fixed nodes and off
-// the grid) and element-conductivity layers rotate in shared memory, and the loads of plane k+2 are in flight while plane k is
-// computed.  The product uses the element form of the conductivity stencil:
+// planes, the operand planes (float2 hi/lo pairs, zero on fixed nodes and
+// off the grid) and element-conductivity layers rotate in shared memory,
+// and the loads of plane k+2 are in flight while plane k is computed.  The
+// product and direction forms use the element form of the conductivity
+// stencil:
 //   (A x)_i = (1/12) (4 x_i sum_e k_e - sum_e k_e f_e),
 // summed over the 8 elements e around node i, where f_e is the sum of the
 // operand x^ over the four nodes of e that are not edge neighbours of i
 // (three face diagonals and the body diagonal); a fixed row is the
 // identity.  4 sum_e k_e is a per-node input computed once per design
-// (k_node_kdiag).  Each f_e is a TwoSum chain of the (hi, lo) pairs, each k_e f_e
-// is a TwoProd with its cross terms, and the products are summed with TwoSum
-// into two unnormalised (hi, lo) accumulators (elements below and above the
-// node's plane, for instruction-level parallelism).  Rounding errors are of order
-// 2^-47 |x| sum_e k_e (those of the FP64 operator, which sums the same
-// terms, are of order 2^-53 |x| sum_e k_e); the form needs about a third
-// fewer FP32 operations than the difference form sum_j w_ij (x_i - x_j).
+// (k_node_kdiag).  Each f_e is a TwoSum chain of the (hi, lo) pairs, each
+// k_e f_e is a TwoProd with its cross terms, and the products are summed
+// with TwoSum into two unnormalised (hi, lo) accumulators (elements below
+// and above the node's plane, for instruction-level parallelism).  Rounding
+// errors are of order 2^-47 |x| sum_e k_e (those of the FP64 operator, which
+// sums the same terms, are of order 2^-53 |x| sum_e k_e); the form needs
+// about a third fewer FP32 operations than the difference form below.
+//
+// The residual form keeps the difference form of the stencil,
+//   (A x)_i = (1/12) sum_j w_ij (x_i - x^_j)
+// (w_ij = k_a + k_b over the 12 face diagonals, k_e over the 8 body
+// diagonals), each difference formed exactly, so its rounding is relative to
+// the differences and not to |x|: a residual recomputed from x keeps its
+// accuracy far below 2^-47 ||A|| ||x||, which the reliable updates of the CG
+// need when they drive ||r|| / ||q|| to 1e-11.
 //
 // Three fused forms:
 //   APPLY : y = A x with FP64 x and y (the MGAR projection; converted on
 //           load and store)                       [x . y]
 //   DIR   : p = z + beta p_old, y = A p           [p . y]   (CG direction update + product)
-//   RESID : r = q - A x, r32 = fl32(r)            [r . r]
+//   RESID : r = q - A x, r32 = fl32(r)            [r . r]   (r optional)
 // p is written to a buffer other than p_old, because neighbouring blocks
 // still read p_old.
 #include "common.cuh"
@@ -96,6 +106,28 @@ struct NodeFetch {
 
 __device__ __forceinline__ df dfk(float2 v) { return df{v.x, v.y}; }
 
+// acc (unnormalised hi, lo) += w * (xi - xj), the difference formed exactly
+__device__ __forceinline__ void acc_term(float& ah, float& al, df w, float2 xi, float2 xj) {
+  float s, e;
+  two_sum(xi.x, -xj.x, s, e);
+  e = __fadd_rn(e, __fsub_rn(xi.y, xj.y));
+  float p, pe;
+  two_prod(w.hi, s, p, pe);
+  pe = __fmaf_rn(w.hi, e, pe);
+  pe = __fmaf_rn(w.lo, s, pe);
+  float t, te;
+  two_sum(ah, p, t, te);
+  ah = t;
+  al = __fadd_rn(al, __fadd_rn(te, pe));
+}
+
+// k_a + k_b as an unnormalised pair (acc_term multiplies both halves)
+__device__ __forceinline__ df wsum(df a, df b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  return df{s, __fadd_rn(e, __fadd_rn(a.lo, b.lo))};
+}
+
 // a + b + c + d as an unnormalised (hi, lo) pair: TwoSum chain of the high
 // words, low words and rounding errors added in FP32
 __device__ __forceinline__ df far4(float2 a, float2 b, float2 c, float2 d) {
@@ -110,14 +142,14 @@ __device__ __forceinline__ df far4(float2 a, float2 b, float2 c, float2 d) {
 }
 
 // acc (unnormalised hi, lo) = k * f
-__device__ __forceinline__ void acc_first(float& ah, float& al, df k, df f) {
+__device__ __forceinline__ void acc_kf_first(float& ah, float& al, df k, df f) {
   two_prod(k.hi, f.hi, ah, al);
   al = __fmaf_rn(k.hi, f.lo, al);
   al = __fmaf_rn(k.lo, f.hi, al);
 }
 
 // acc (unnormalised hi, lo) += k * f
-__device__ __forceinline__ void acc_prod(float& ah, float& al, df k, df f) {
+__device__ __forceinline__ void acc_kf(float& ah, float& al, df k, df f) {
   float p, pe;
   two_prod(k.hi, f.hi, p, pe);
   pe = __fmaf_rn(k.hi, f.lo, pe);
@@ -154,7 +186,10 @@ __global__ void __launch_bounds__(T::NTB, T::NT <= 256 ? 4 : 2) k_df3d(DfArgs a)
   if (xr) T::xring(tid, rxh, ryh);
   if (kr) T::kring(tid - KRING0, kxh, kyh);
   df beta{0.f, 0.f};
-  if (MODE == DIR && !a.first) beta = df_from_double(*a.rz_new / *a.rz_old);
+  if (MODE == DIR) {
+    const df q = block_div_df(a.rz_new, a.rz_old);  // once per block
+    if (!a.first) beta = q;
+  }
   const bool odd = MODE == DIR && a.parity && (((int)*a.parity) & 1);
   const float2* const xsrc = odd ? a.x_alt : a.x;
   float2* const pdst = odd ? a.p_alt : a.p;
@@ -185,7 +220,7 @@ __global__ void __launch_bounds__(T::NTB, T::NT <= 256 ? 4 : 2) k_df3d(DfArgs a)
     {
       const int idx = ocol + NXY * min(max(p, 0), a.NZ - 1);
       if (CK(idx, (int64_t)NXY * a.NZ)) {
-        ownkd = a.kd[idx];
+        if (MODE != RESID) ownkd = a.kd[idx];
         if (MODE == RESID) ownq = a.q[idx];
       }
     }
@@ -255,42 +290,68 @@ __global__ void __launch_bounds__(T::NTB, T::NT <= 256 ? 4 : 2) k_df3d(DfArgs a)
                  k010 = dfk(K[S0][ty + 1][tx]), k011 = dfk(K[S0][ty + 1][tx + 1]);         \
         const df k100 = dfk(K[S1][ty][tx]), k101 = dfk(K[S1][ty][tx + 1]),                 \
                  k110 = dfk(K[S1][ty + 1][tx]), k111 = dfk(K[S1][ty + 1][tx + 1]);         \
-        /* f_e: in-plane face diagonal, two out-of-plane face diagonals, body diagonal */ \
-        const df f000 = far4(X[S1][cy - 1][cx - 1], X[S0][cy][cx - 1], X[S0][cy - 1][cx],     \
-                             X[S0][cy - 1][cx - 1]);                                           \
-        const df f001 = far4(X[S1][cy - 1][cx + 1], X[S0][cy][cx + 1], X[S0][cy - 1][cx],     \
-                             X[S0][cy - 1][cx + 1]);                                           \
-        const df f010 = far4(X[S1][cy + 1][cx - 1], X[S0][cy][cx - 1], X[S0][cy + 1][cx],     \
-                             X[S0][cy + 1][cx - 1]);                                           \
-        const df f011 = far4(X[S1][cy + 1][cx + 1], X[S0][cy][cx + 1], X[S0][cy + 1][cx],     \
-                             X[S0][cy + 1][cx + 1]);                                           \
-        const df f100 = far4(X[S1][cy - 1][cx - 1], X[S2][cy][cx - 1], X[S2][cy - 1][cx],     \
-                             X[S2][cy - 1][cx - 1]);                                           \
-        const df f101 = far4(X[S1][cy - 1][cx + 1], X[S2][cy][cx + 1], X[S2][cy - 1][cx],     \
-                             X[S2][cy - 1][cx + 1]);                                           \
-        const df f110 = far4(X[S1][cy + 1][cx - 1], X[S2][cy][cx - 1], X[S2][cy + 1][cx],     \
-                             X[S2][cy + 1][cx - 1]);                                           \
-        const df f111 = far4(X[S1][cy + 1][cx + 1], X[S2][cy][cx + 1], X[S2][cy + 1][cx],     \
-                             X[S2][cy + 1][cx + 1]);                                           \
-        /* two independent accumulators (elements below and above the plane) */         \
-        float ah, al, bh, bl;                                                              \
-        acc_first(ah, al, k000, f000);                                                     \
-        acc_first(bh, bl, k100, f100);                                                     \
-        acc_prod(ah, al, k001, f001);                                                      \
-        acc_prod(bh, bl, k101, f101);                                                      \
-        acc_prod(ah, al, k010, f010);                                                      \
-        acc_prod(bh, bl, k110, f110);                                                      \
-        acc_prod(ah, al, k011, f011);                                                      \
-        acc_prod(bh, bl, k111, f111);                                                      \
-        float sh, se;                                                                      \
-        two_sum(ah, bh, sh, se);                                                           \
-        const df acc = df_make(sh, __fadd_rn(se, __fadd_rn(al, bl)));                      \
-        const df diag = df_mul(dfk(ckd[S1]), dfk(xi));                                     \
-        yv = df_mul(df_sub(diag, acc), scale);                                 \
+        if (MODE == RESID) {                                                               \
+          /* difference form: each term rounded relative to its own size */               \
+          float ah = 0.f, al = 0.f;                                                        \
+          acc_term(ah, al, wsum(k000, k100), xi, X[S1][cy - 1][cx - 1]);                 \
+          acc_term(ah, al, wsum(k001, k101), xi, X[S1][cy - 1][cx + 1]);                 \
+          acc_term(ah, al, wsum(k010, k110), xi, X[S1][cy + 1][cx - 1]);                 \
+          acc_term(ah, al, wsum(k011, k111), xi, X[S1][cy + 1][cx + 1]);                 \
+          acc_term(ah, al, wsum(k000, k010), xi, X[S0][cy][cx - 1]);                     \
+          acc_term(ah, al, wsum(k001, k011), xi, X[S0][cy][cx + 1]);                     \
+          acc_term(ah, al, wsum(k100, k110), xi, X[S2][cy][cx - 1]);                     \
+          acc_term(ah, al, wsum(k101, k111), xi, X[S2][cy][cx + 1]);                     \
+          acc_term(ah, al, wsum(k000, k001), xi, X[S0][cy - 1][cx]);                     \
+          acc_term(ah, al, wsum(k010, k011), xi, X[S0][cy + 1][cx]);                     \
+          acc_term(ah, al, wsum(k100, k101), xi, X[S2][cy - 1][cx]);                     \
+          acc_term(ah, al, wsum(k110, k111), xi, X[S2][cy + 1][cx]);                     \
+          acc_term(ah, al, k000, xi, X[S0][cy - 1][cx - 1]);                               \
+          acc_term(ah, al, k001, xi, X[S0][cy - 1][cx + 1]);                               \
+          acc_term(ah, al, k010, xi, X[S0][cy + 1][cx - 1]);                               \
+          acc_term(ah, al, k011, xi, X[S0][cy + 1][cx + 1]);                               \
+          acc_term(ah, al, k100, xi, X[S2][cy - 1][cx - 1]);                               \
+          acc_term(ah, al, k101, xi, X[S2][cy - 1][cx + 1]);                               \
+          acc_term(ah, al, k110, xi, X[S2][cy + 1][cx - 1]);                               \
+          acc_term(ah, al, k111, xi, X[S2][cy + 1][cx + 1]);                               \
+          yv = df_mul(df_make(ah, al), scale);                                             \
+        } else {                                                                           \
+          /* f_e: in-plane face diagonal, two out-of-plane face diagonals, body diagonal */\
+          const df f000 = far4(X[S1][cy - 1][cx - 1], X[S0][cy][cx - 1], X[S0][cy - 1][cx],\
+                               X[S0][cy - 1][cx - 1]);                                     \
+          const df f001 = far4(X[S1][cy - 1][cx + 1], X[S0][cy][cx + 1], X[S0][cy - 1][cx],\
+                               X[S0][cy - 1][cx + 1]);                                     \
+          const df f010 = far4(X[S1][cy + 1][cx - 1], X[S0][cy][cx - 1], X[S0][cy + 1][cx],\
+                               X[S0][cy + 1][cx - 1]);                                     \
+          const df f011 = far4(X[S1][cy + 1][cx + 1], X[S0][cy][cx + 1], X[S0][cy + 1][cx],\
+                               X[S0][cy + 1][cx + 1]);                                     \
+          const df f100 = far4(X[S1][cy - 1][cx - 1], X[S2][cy][cx - 1], X[S2][cy - 1][cx],\
+                               X[S2][cy - 1][cx - 1]);                                     \
+          const df f101 = far4(X[S1][cy - 1][cx + 1], X[S2][cy][cx + 1], X[S2][cy - 1][cx],\
+                               X[S2][cy - 1][cx + 1]);                                     \
+          const df f110 = far4(X[S1][cy + 1][cx - 1], X[S2][cy][cx - 1], X[S2][cy + 1][cx],\
+                               X[S2][cy + 1][cx - 1]);                                     \
+          const df f111 = far4(X[S1][cy + 1][cx + 1], X[S2][cy][cx + 1], X[S2][cy + 1][cx],\
+                               X[S2][cy + 1][cx + 1]);                                     \
+          /* two independent accumulators (elements below and above the plane) */          \
+          float ah, al, bh, bl;                                                            \
+          acc_kf_first(ah, al, k000, f000);                                                \
+          acc_kf_first(bh, bl, k100, f100);                                                \
+          acc_kf(ah, al, k001, f001);                                                      \
+          acc_kf(bh, bl, k101, f101);                                                      \
+          acc_kf(ah, al, k010, f010);                                                      \
+          acc_kf(bh, bl, k110, f110);                                                      \
+          acc_kf(ah, al, k011, f011);                                                      \
+          acc_kf(bh, bl, k111, f111);                                                      \
+          float sh, se;                                                                    \
+          two_sum(ah, bh, sh, se);                                                         \
+          const df acc = df_make(sh, __fadd_rn(se, __fadd_rn(al, bl)));                    \
+          const df diag = df_mul(dfk(ckd[S1]), dfk(xi));                                   \
+          yv = df_mul(df_sub(diag, acc), scale);                                           \
+        }                                                                                  \
       }                                                                                    \
       if (MODE == RESID) {                                                                 \
         const df ri = df_sub(dfk(cq[S1]), yv);                                             \
-        a.y[idx] = make_float2(ri.hi, ri.lo);                                              \
+        if (a.y) a.y[idx] = make_float2(ri.hi, ri.lo);                                     \
         a.r32[idx] = __fadd_rn(ri.hi, ri.lo);                                              \
         dot = df_add(dot, df_mul(ri, ri));                                                 \
       } else if (MODE == APPLY) {                                                          \
@@ -313,12 +374,11 @@ __global__ void __launch_bounds__(T::NTB, T::NT <= 256 ? 4 : 2) k_df3d(DfArgs a)
 #undef D3D_FINISH
 #undef D3D_FINISH_LAYER
   if (a.out) {
-    double v[1] = {df_to_double(dot)};
-    double t[1];
+    double t;
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     const int nb = gridDim.x * gridDim.y * gridDim.z;
-    if (block_sum_last_ids<1>(v, a.partials, a.counter, t, tid, T::NTB, bid, nb) && tid == 0) {
-      a.out[0] = t[0];
+    if (block_sum_last_df(dot, a.partials, a.counter, t, tid, T::NTB, bid, nb) && tid == 0) {
+      a.out[0] = t;
       if (MODE == DIR && a.rz_set) *a.rz_set = *a.rz_new;  // every block has read rz_new
     }
   }

@@ -11,7 +11,9 @@
 // one post-sweep):
 //   pre:  x = w D^-1 b  and  r = b - A x             (jacobi from zero + residual)
 //   post: x' = v + w D^-1 (b - A v),  v = x + P x_c   (interpolation + post-smooth)
-// and a generic form computes r = b - A x or one damped-Jacobi sweep.
+// and a generic form computes r = b - A x or one damped-Jacobi sweep.  A
+// fifth form serves the FP32 conjugate-gradient iteration of the mixed path:
+//   dir:  p = z + beta p_old,  y = A p,  p . y       (direction update + product)
 //
 // Latency: the global loads of plane k+2 (and element layer k+1) are issued
 // into registers before the block computes plane k, and are turned into the
@@ -29,26 +31,38 @@ namespace mgar {
 namespace f3d {
 using namespace tile;
 
-enum Mode { PRE = 0, POST = 1, RESID = 2, SWEEP = 3 };
+enum Mode { PRE = 0, POST = 1, RESID = 2, SWEEP = 3, DIR = 4 };
 
 struct FineArgs {
   int ex, ey, ez, NX, NY, NZ;
   int gz;  // z runs
   const uint8_t* fixed;
   const void* ke;
-  const void* b;
+  const void* b;    // DIR: z
   const void* dinv;
-  const void* x;    // RESID / SWEEP: iterate; POST: x before interpolation
+  const void* x;    // RESID / SWEEP: iterate; POST: x before interpolation; DIR: p_old
   const void* xc;   // POST: coarse correction
   int cNX, cNY, cNZ;  // POST: coarse node dims
-  void* out0;       // PRE: x, RESID: r, SWEEP/POST: x'
-  void* out1;       // PRE: r
+  void* out0;       // PRE: x, RESID: r, SWEEP/POST: x', DIR: p
+  void* out1;       // PRE: r, DIR: A p
   double omega;
-  // POST, optional: r . x' with r in double-float pairs (the CG's r . z)
+  // POST / SWEEP, optional (dout given): r . x' with r in double-float
+  // pairs (the CG's r . z), or with r = b when rdot is null
   const float2* rdot;
   double* partials;
   unsigned int* counter;
-  double* dout;
+  double* dout;     // POST / SWEEP: r . x'; DIR: p . A p
+  // DIR: beta = rz_new / rz_old, or 0 while *first is nonzero; with *parity
+  // odd, p_old is x_alt and p goes to out_alt (the two direction buffers swap
+  // each iteration); rz_set, when given, receives *rz_new once every block
+  // has read it
+  const double* rz_new;
+  const double* rz_old;
+  const double* first;
+  const double* parity;
+  const void* x_alt;
+  void* out_alt;
+  double* rz_set;
 };
 
 // 1D interpolation taps onto fine node i (nf fine elements): coarse index of
@@ -89,13 +103,15 @@ __device__ __forceinline__ Column make_column(const FineArgs& a, int i, int j, b
 // Raw loads of one node of a plane, issued one step before use.
 template <typename Real, int MODE>
 struct NodeFetch {
-  Real v0 = Real(0), v1 = Real(0);  // PRE: b, dinv; else x (v1 unused)
+  Real v0 = Real(0), v1 = Real(0);  // PRE: b, dinv; DIR: z, p_old; else x (v1 unused)
   Real c[8];                        // POST: coarse values
   uint8_t f = 1;                    // fixed (or off the grid: treated as zero)
   uint8_t hz = 0;                   // POST: half flag of z
   bool on = false;
 
-  __device__ __forceinline__ void issue(const FineArgs& a, const Column& col, int k) {
+  // xsrc: DIR's p_old (null on the first iteration)
+  __device__ __forceinline__ void issue(const FineArgs& a, const Column& col, int k,
+                                        const Real* xsrc = nullptr) {
     on = col.on && k >= 0 && k < a.NZ;
     const int kc = min(max(k, 0), a.NZ - 1);
     const int idx = col.base + a.NX * a.NY * kc;
@@ -104,6 +120,9 @@ struct NodeFetch {
     if (MODE == PRE) {
       v0 = ((const Real*)a.b)[idx];
       v1 = ((const Real*)a.dinv)[idx];
+    } else if (MODE == DIR) {
+      v0 = ((const Real*)a.b)[idx];
+      if (xsrc) v1 = xsrc[idx];
     } else {
       v0 = ((const Real*)a.x)[idx];
     }
@@ -125,9 +144,10 @@ struct NodeFetch {
   }
 
   // operand value before masking (PRE: w D^-1 b; POST: x + P x_c, fixed
-  // nodes keep x; else x)
+  // nodes keep x; DIR: z + beta p_old, beta passed as omega; else x)
   __device__ __forceinline__ Real value(Real omega, uint8_t hxy) const {
     if (MODE == PRE) return omega * v1 * v0;
+    if (MODE == DIR) return v0 + omega * v1;
     if (MODE == POST) {
       if (f) return v0;
       const Real wx = (hxy & 1) ? Real(0.5) : Real(1), ux = (hxy & 1) ? Real(0.5) : Real(0);
@@ -184,7 +204,18 @@ __global__ void __launch_bounds__(T::NTB, f3d_minb(MODE, T::NT)) k_fine3d(FineAr
   const int kb = (int)(((int64_t)blockIdx.z * a.NZ) / a.gz);
   const int kend = (int)(((int64_t)(blockIdx.z + 1) * a.NZ) / a.gz);
   const int i = i0 + tx, j = j0 + ty;
-  const Real om = (Real)a.omega;
+  // DIR: beta takes omega's place, and the direction buffers follow the parity
+  Real om = (Real)a.omega;
+  const Real* dsrc = nullptr;
+  Real* pdst = nullptr;
+  if (MODE == DIR) {
+    const bool first = *a.first != 0.0;
+    const bool odd = a.parity && (((int)*a.parity) & 1);
+    const float q = block_div_f(a.rz_new, a.rz_old);  // once per block
+    om = first ? Real(0) : (Real)q;
+    dsrc = first ? nullptr : (const Real*)(odd ? a.x_alt : a.x);
+    pdst = (Real*)(odd ? a.out_alt : a.out0);
+  }
   const bool xr = tid < XRING, kr = tid >= KRING0 && tid < KRING0 + KRING;
   int rxh = 0, ryh = 0, kxh = 0, kyh = 0;
   if (xr) T::xring(tid, rxh, ryh);
@@ -207,19 +238,19 @@ __global__ void __launch_bounds__(T::NTB, f3d_minb(MODE, T::NT)) k_fine3d(FineAr
   // for the fused r . x')
   Real cv[4], cb[4], cd[4];
   bool cf[4];
-  const bool rdot = (MODE == POST || MODE == SWEEP) && a.dout != nullptr;
+  const bool rdot = (MODE == POST || MODE == SWEEP || MODE == DIR) && a.dout != nullptr;
   df dacc{0.f, 0.f};
 
   auto issue_plane = [&](int p) {
-    own.issue(a, ocol, p);
-    if (MODE != PRE) {
+    own.issue(a, ocol, p, dsrc);
+    if (MODE != PRE && MODE != DIR) {
       const int idx = ocol.base + NXY * min(max(p, 0), a.NZ - 1);
       if (CK(idx, (int64_t)NXY * a.NZ)) {
         ownb = ((const Real*)a.b)[idx];
         if (MODE == POST || MODE == SWEEP) ownd = ((const Real*)a.dinv)[idx];
       }
     }
-    if (xr) ring.issue(a, rcol, p);
+    if (xr) ring.issue(a, rcol, p, dsrc);
   };
   auto issue_layer = [&](int l) {
     kown.issue(a, kebase, keon, l);
@@ -267,7 +298,7 @@ __global__ void __launch_bounds__(T::NTB, f3d_minb(MODE, T::NT)) k_fine3d(FineAr
     if (mine) {                                                                            \
       const int idx = i + a.NX * (j + a.NY * k);                                           \
       /* r for the fused r . x' (its load overlaps the stencil) */                         \
-      const float2 rv = rdot ? a.rdot[idx] : make_float2(0.f, 0.f);                       \
+      const float2 rv = (rdot && a.rdot) ? a.rdot[idx] : make_float2(0.f, 0.f);           \
       const Real k000 = K[S0][ty][tx], k001 = K[S0][ty][tx + 1], k010 = K[S0][ty + 1][tx], \
                  k011 = K[S0][ty + 1][tx + 1];                                             \
       const Real k100 = K[S1][ty][tx], k101 = K[S1][ty][tx + 1], k110 = K[S1][ty + 1][tx], \
@@ -304,10 +335,17 @@ __global__ void __launch_bounds__(T::NTB, f3d_minb(MODE, T::NT)) k_fine3d(FineAr
         ((Real*)a.out1)[idx] = cf[S1] ? Real(0) : bi - ax;                                 \
       } else if (MODE == RESID) {                                                          \
         ((Real*)a.out0)[idx] = cf[S1] ? Real(0) : bi - ax;                                 \
+      } else if (MODE == DIR) {                                                            \
+        pdst[idx] = xi;                                                                    \
+        ((Real*)a.out1)[idx] = ax;                                                         \
+        if (rdot) dacc = df_add(dacc, df_mulf(df{(float)xi, 0.f}, (float)ax));             \
       } else {                                                                             \
         const Real xo = xi + om * cd[S1] * (bi - ax);                                      \
         ((Real*)a.out0)[idx] = xo;                                                         \
-        if (rdot) dacc = df_add(dacc, df_mulf(df{rv.x, rv.y}, (float)xo));                 \
+        if (rdot) {                                                                        \
+          const df rr = a.rdot ? df{rv.x, rv.y} : df{(float)bi, 0.f};                      \
+          dacc = df_add(dacc, df_mulf(rr, (float)xo));                                     \
+        }                                                                                  \
       }                                                                                    \
     }                                                                                      \
   }
@@ -322,12 +360,13 @@ __global__ void __launch_bounds__(T::NTB, f3d_minb(MODE, T::NT)) k_fine3d(FineAr
 #undef F3D_FINISH
 #undef F3D_FINISH_LAYER
   if (rdot) {
-    double v[1] = {df_to_double(dacc)};
-    double t[1];
+    double t;
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     const int nb = gridDim.x * gridDim.y * gridDim.z;
-    if (block_sum_last_ids<1>(v, a.partials, a.counter, t, tid, T::NTB, bid, nb) && tid == 0)
-      a.dout[0] = t[0];
+    if (block_sum_last_df(dacc, a.partials, a.counter, t, tid, T::NTB, bid, nb) && tid == 0) {
+      a.dout[0] = t;
+      if (MODE == DIR && a.rz_set) *a.rz_set = *a.rz_new;  // every block has read rz_new
+    }
   }
 }
 
@@ -360,6 +399,7 @@ void fine3d_prepare(Ctx& c) {
   c.f3d_gz[POST] = runs_for<float, POST, T32x8>(d, sms);
   c.f3d_gz[RESID] = runs_for<float, RESID, T32x8>(d, sms);
   c.f3d_gz[SWEEP] = runs_for<float, SWEEP, T32x8>(d, sms);
+  c.f3d_gz[DIR] = runs_for<float, DIR, T32x8>(d, sms);
 }
 
 namespace f3d {
@@ -378,7 +418,7 @@ void fine3d(Ctx& c, int mode, const float* ke, const float* b, const float* dinv
             const float* xc, float* out0, float* out1, const float2* rdot, double* dout) {
   using namespace f3d;
   const Dims& d = c.L[0];
-  FineArgs a;
+  FineArgs a{};
   a.ex = d.ex;
   a.ey = d.ey;
   a.ez = d.ez;
@@ -408,6 +448,40 @@ void fine3d(Ctx& c, int mode, const float* ke, const float* b, const float* dinv
     default: launch<SWEEP, T32x8>(c, a); break;
   }
   MGAR_LAUNCH_CHECK_AT(level_site(6 + (mode == PRE ? 0 : mode == POST ? 1 : mode == SWEEP ? 2 : 3), 0));
+}
+
+// p = z + (rz_new / rz_old) p_old (p = z while *first is nonzero), y = A p,
+// p . y into *dot; FP32 vectors
+void fine3d_dir(Ctx& c, const float* z, const float* p_old, float* p, const double* rz_new,
+                const double* rz_old, const double* first, const double* parity, float* y,
+                double* dot, double* rz_set) {
+  using namespace f3d;
+  const Dims& d = c.L[0];
+  FineArgs a{};
+  a.ex = d.ex;
+  a.ey = d.ey;
+  a.ez = d.ez;
+  a.NX = d.NX;
+  a.NY = d.NY;
+  a.NZ = d.NZ;
+  a.fixed = c.fixed;
+  a.ke = c.ke_f;
+  a.b = z;
+  a.x = p_old;
+  a.out0 = p;
+  a.x_alt = p;  // odd parity: the buffers swap roles
+  a.out_alt = const_cast<float*>(p_old);
+  a.out1 = y;
+  a.rz_new = rz_new;
+  a.rz_old = rz_old;
+  a.first = first;
+  a.parity = parity;
+  a.rz_set = rz_set;
+  a.dout = dot;
+  a.partials = c.partials;
+  a.counter = c.counter;
+  launch<DIR, T32x8>(c, a);
+  MGAR_LAUNCH_CHECK();
 }
 
 }  // namespace mgar

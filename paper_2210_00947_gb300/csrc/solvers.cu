@@ -96,7 +96,7 @@ __global__ void k_cg_xr(double* __restrict__ x, double* __restrict__ r, const do
                         const double* __restrict__ Ap, int64_t n, const double* __restrict__ rz,
                         const double* __restrict__ pap, double* partials, unsigned int* counter,
                         double* out) {
-  const double alpha = *rz / *pap;
+  const double alpha = block_div(rz, pap);
   double v[1] = {0.0};
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -111,7 +111,7 @@ __global__ void k_cg_xr(double* __restrict__ x, double* __restrict__ r, const do
 // p = z + (rz_new / rz_old) p
 __global__ void k_cg_p(double* __restrict__ p, const double* __restrict__ z, int64_t n,
                        const double* __restrict__ rz_new, const double* __restrict__ rz_old) {
-  const double beta = *rz_new / *rz_old;
+  const double beta = block_div(rz_new, rz_old);
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
     p[i] = z[i] + beta * p[i];

@@ -43,6 +43,7 @@ EXPORTS = ("mgar_default_params", "mgar_create", "mgar_destroy", "mgar_set_strea
 
 # kernel classes of mgar_profile_start
 KC_APPLY64, KC_SMOOTH0, KC_RESID0, KC_OC, KC_GALERKIN0, KC_FILTER, KC_SENS = range(1, 8)
+KC_APPLY32, KC_RESID64 = 8, 9
 KC_TIMELINE = 100
 
 

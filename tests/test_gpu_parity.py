@@ -279,14 +279,19 @@ def test_oc_large_matches_oracle(dims):
         np.testing.assert_allclose(host(r), ref, rtol=1e-11, atol=1e-12)
 
 
-@pytest.mark.parametrize("dims,nl", [((64, 48, 0), 4), ((100, 100, 0), 4), ((16, 16, 12), 3),
-                                     ((20, 18, 16), 4)])
-def test_mixed_mgcg_matches_exact_solve(dims, nl):
-    """Mixed path: df64 outer CG with the FP32 V-cycle.  The preconditioner
-    only changes the iteration count.  Double-float vectors carry ~48 bits,
-    so the true residual bottoms out near 2^-46 ||A|| ||T|| / ||q|| (a few
-    1e-10 here) even when the recursive one is driven to 1e-11; the bars are
-    set from that floor, two orders below the 1e-8 the workloads use."""
+@pytest.mark.parametrize("dims,nl,cg", [((64, 48, 0), 4, "df64"), ((100, 100, 0), 4, "df64"),
+                                        ((16, 16, 12), 3, "ru"), ((20, 18, 16), 4, "ru"),
+                                        ((16, 16, 12), 3, "df64"), ((20, 18, 16), 4, "df64")])
+def test_mixed_mgcg_matches_exact_solve(dims, nl, cg, monkeypatch):
+    """Mixed path with the FP32 V-cycle as preconditioner: on 2D grids (and
+    on 3D grids with MGAR_DF64_CG=1) a df64 CG, on 3D grids by default FP32
+    CG iterations with reliable df64 updates.  The preconditioner and the
+    precision of the Krylov vectors only change the iteration count.
+    Double-float vectors carry ~48 bits, so the true residual bottoms out
+    near 2^-46 ||A|| ||T|| / ||q|| (a few 1e-10 here); the bars are set from
+    that floor, two orders below the 1e-8 the workloads use."""
+    if cg == "df64":
+        monkeypatch.setenv("MGAR_DF64_CG", "1")
     g, rho, fixed, q = make_problem(dims, mask="sink")
     A = fem.system_matrix(g, rho, fixed)
     t_ex = solvers.exact_solve(A, q)
