@@ -56,6 +56,14 @@ int ck_report(Ctx& c) {
 }
 #endif
 
+// after a failed call: order the stream after a pending factorisation
+// anyway (best effort; errors here are not reported)
+static void release_side(Ctx& c) {
+  if (c.coarse_pending && c.ev_join && c.stream != c.cap_stream && c.stream != c.cap_stream2 &&
+      cudaStreamWaitEvent(c.stream, c.ev_join, 0) == cudaSuccess)
+    c.coarse_pending = false;
+}
+
 template <class F>
 int guarded(mgar_t h, F&& f) {
   Ctx* c = reinterpret_cast<Ctx*>(h);
@@ -66,18 +74,24 @@ int guarded(mgar_t h, F&& f) {
     ~CurGuard() { current_ctx() = prev; }
   } cur_guard(c);
   try {
+    // every call returns with the handle's stream ordered after its work
 #ifdef MGAR_CHECKED
     const int rc = f(*c);
+    join_coarse(*c);
     const int ck = ck_report(*c);
     return ck != MGAR_OK ? ck : rc;
 #else
-    return f(*c);
+    const int rc = f(*c);
+    join_coarse(*c);
+    return rc;
 #endif
   } catch (const Error& e) {
     c->err = e.msg;
+    release_side(*c);
     return e.code;
   } catch (const std::exception& e) {
     c->err = e.what();
+    release_side(*c);
     return MGAR_ERR_CUDA;
   }
 }
@@ -89,6 +103,9 @@ void free_ctx(Ctx& c) {
   if (c.ru_exec) cudaGraphExecDestroy(c.ru_exec);
   if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
   if (c.cap_stream2) cudaStreamDestroy(c.cap_stream2);
+  if (c.side_stream) cudaStreamDestroy(c.side_stream);
+  if (c.ev_fork) cudaEventDestroy(c.ev_fork);
+  if (c.ev_join) cudaEventDestroy(c.ev_join);
   free_hierarchy(c);
   if (c.prof_ev) {
     for (int i = 0; i < 2 * kProfMax; ++i)
@@ -241,6 +258,9 @@ int mgar_create(mgar_t* out, const mgar_params* p, const uint8_t* fixed_mask, co
 
     MGAR_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
     MGAR_CUDA(cudaStreamCreateWithFlags(&c->cap_stream2, cudaStreamNonBlocking));
+    MGAR_CUDA(cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking));
+    MGAR_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    MGAR_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
     MGAR_CUDA(cudaMalloc(&c->fixed, n));
     MGAR_CUDA(cudaMalloc(&c->q, n * sizeof(double)));
     MGAR_CUDA(cudaMalloc(&c->rho_phys, ne * sizeof(double)));
@@ -435,6 +455,7 @@ int mgar_apply_K(mgar_t h, const double* x, double* y) {
 int mgar_build_hierarchy(mgar_t h) {
   return guarded(h, [&](Ctx& c) {
     build_hierarchy(c);
+    join_coarse(c);
     MGAR_CUDA(cudaStreamSynchronize(c.stream));
     int e = 0;
     MGAR_CUDA(cudaMemcpy(&e, c.derr, sizeof(int), cudaMemcpyDeviceToHost));

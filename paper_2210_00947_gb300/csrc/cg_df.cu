@@ -454,6 +454,7 @@ static int solve_mgcg_df3(Ctx& c, double* T, int* iters, double* relres) {
     if (!c.cg_exec && !build_cg_graph(c)) c.cg_graph = false;
   }
   if (!(rel <= c.p.eps2) && c.cg_exec && c.prof_class == 0 && c.use_graphs) {
+    join_coarse(c);
     MGAR_CUDA(cudaGraphLaunch(c.cg_exec, c.stream));
     fetch_scalars(c, S_RR, S_CGIT - S_RR + 1);
     it = (int)c.hsc[S_CGIT];
@@ -521,20 +522,32 @@ __global__ void k_cg_xr32(float* __restrict__ xc, float* __restrict__ r, const f
   const float alpha = block_div_f(rz, pap);
   float acc = 0.f;
   const int stride = gridDim.x * blockDim.x;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  for (; i + stride < n; i += 2 * stride) {
-    const int j = i + stride;
-    const float xa = xc[i], xb = xc[j], pa = p[i], pb = p[j];
-    const float ra = r[i], rb = r[j], qa = Ap[i], qb = Ap[j];
-    xc[i] = fmaf(alpha, pa, xa);
-    xc[j] = fmaf(alpha, pb, xb);
-    const float ria = fmaf(-alpha, qa, ra), rib = fmaf(-alpha, qb, rb);
-    r[i] = ria;
-    r[j] = rib;
-    acc = fmaf(ria, ria, acc);
-    acc = fmaf(rib, rib, acc);
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+  // four nodes per access (the vectors are 256-byte aligned allocations)
+  const int n4 = n >> 2;
+  float4* __restrict__ xc4 = reinterpret_cast<float4*>(xc);
+  float4* __restrict__ r4 = reinterpret_cast<float4*>(r);
+  const float4* __restrict__ p4 = reinterpret_cast<const float4*>(p);
+  const float4* __restrict__ a4 = reinterpret_cast<const float4*>(Ap);
+  for (int q = t0; q < n4; q += stride) {
+    float4 xv = xc4[q], rv = r4[q];
+    const float4 pv = p4[q], av = a4[q];
+    xv.x = fmaf(alpha, pv.x, xv.x);
+    xv.y = fmaf(alpha, pv.y, xv.y);
+    xv.z = fmaf(alpha, pv.z, xv.z);
+    xv.w = fmaf(alpha, pv.w, xv.w);
+    rv.x = fmaf(-alpha, av.x, rv.x);
+    rv.y = fmaf(-alpha, av.y, rv.y);
+    rv.z = fmaf(-alpha, av.z, rv.z);
+    rv.w = fmaf(-alpha, av.w, rv.w);
+    xc4[q] = xv;
+    r4[q] = rv;
+    acc = fmaf(rv.x, rv.x, acc);
+    acc = fmaf(rv.y, rv.y, acc);
+    acc = fmaf(rv.z, rv.z, acc);
+    acc = fmaf(rv.w, rv.w, acc);
   }
-  for (; i < n; i += stride) {
+  for (int i = 4 * n4 + t0; i < n; i += stride) {
     xc[i] = fmaf(alpha, p[i], xc[i]);
     const float ri = fmaf(-alpha, Ap[i], r[i]);
     r[i] = ri;
@@ -747,6 +760,7 @@ static int solve_mgcg_ru3(Ctx& c, double* T, int* iters, double* relres) {
     const bool use_graph = c.cg_graph && c.prof_class == 0 && c.use_graphs &&
                            (c.ru_exec || build_ru_graph(c));
     if (use_graph) {
+      join_coarse(c);
       MGAR_CUDA(cudaGraphLaunch(c.ru_exec, c.stream));
       fetch_scalars(c, S_RR, S_CGIT - S_RR + 1);
       it = (int)c.hsc[S_CGIT];

@@ -69,6 +69,7 @@ enum Slot : int {
   S_RMAX = 127,     // FP32 CG: ||r|| at the last reliable update
   S_OC_CAND = 128,  // 128..158 multisection candidates mu
   S_OC_CANDL = 160, // 160..190 their ln mu
+  S_DERR = 191,     // host mirror only: the device error flag, published with every fetch
   S_COUNT = 192
 };
 
@@ -243,6 +244,13 @@ struct Ctx {
   // (the 65^3 level of a 128^3 grid: 6.60 vs 6.66 ms per design cycle)
   int64_t split_coarse_nodes = 100000;
   cudaStream_t cap_stream = nullptr;
+  // the coarsest factorisation runs on a side stream while the solve starts
+  // (it needs one SM for ~200 us); join_coarse orders the main stream after
+  // it before the first V-cycle
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool coarse_pending = false;
+  bool derr_fresh = true;  // the last published device error flag follows every factorisation
   cudaStream_t cap_stream2 = nullptr;  // captures the body of a graph's IF node
 
   // instrumentation: CUDA-event timing of one kernel class
@@ -869,8 +877,17 @@ inline void launch_pdl(cudaStream_t s, bool pdl, void (*kernel)(KArgs...), dim3 
 // Run `issue` (a fixed sequence of launches on c.stream) through a cached
 // CUDA graph keyed by (kind, a, b); falls back to direct launches while a
 // kernel class inside it is being timed.
+// Orders the handle's stream after a pending coarsest factorisation (no-op
+// otherwise, and never inside a stream capture).
+inline void join_coarse(Ctx& c) {
+  if (!c.coarse_pending || c.stream == c.cap_stream || c.stream == c.cap_stream2) return;
+  MGAR_CUDA(cudaStreamWaitEvent(c.stream, c.ev_join, 0));
+  c.coarse_pending = false;
+}
+
 template <class F>
 void run_graph(Ctx& c, int kind, const void* a, const void* b, bool profiled_inside, F&& issue) {
+  join_coarse(c);
   if (!c.use_graphs || profiled_inside) {
     issue();
     return;

@@ -542,10 +542,18 @@ static const Real* p_tables(Ctx& c) {
 }
 
 // Band Cholesky of the coarsest operator and its explicit inverse, in B
-// (the V-cycle's working precision).
+// (the V-cycle's working precision).  On the side stream when there is one:
+// the factorisation is a chain of 125 dependent pivots on one SM, and the
+// solve's first kernels (the df64 residual) do not need it; join_coarse
+// orders the main stream after it.
 template <typename Real, int DIM, typename B>
 static void coarse_factor(Ctx& c, const Real* st, const Dims& dcst) {
   cudaStream_t s = c.stream;
+  if (c.side_stream) {
+    MGAR_CUDA(cudaEventRecord(c.ev_fork, c.stream));
+    MGAR_CUDA(cudaStreamWaitEvent(c.side_stream, c.ev_fork, 0));
+    s = c.side_stream;
+  }
   B* band = CoarseT<Real>::band(c);
   B* rdiag = CoarseT<Real>::rdiag(c);
   B* inv = CoarseT<Real>::inv(c);
@@ -567,6 +575,11 @@ static void coarse_factor(Ctx& c, const Real* st, const Dims& dcst) {
   else
     k_band_inverse<B, false><<<(c.nc + 7) / 8, 256, 0, s>>>(band, rdiag, c.nc, c.bw, inv);
   MGAR_LAUNCH_CHECK();
+  if (c.side_stream) {
+    MGAR_CUDA(cudaEventRecord(c.ev_join, s));
+    c.coarse_pending = true;
+    c.derr_fresh = false;
+  }
 }
 
 template <typename Real, int DIM>

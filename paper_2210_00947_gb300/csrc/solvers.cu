@@ -204,8 +204,10 @@ void dot(Ctx& c, const double* a, const double* b, int64_t n, double* out_dev) {
 // Copies device scalars into the mapped pinned mirror, then bumps a
 // sequence number there (after a system-scope fence).
 __global__ void k_publish(const double* __restrict__ dsc, double* hmir, int first, int count,
-                          volatile unsigned long long* seq, unsigned long long value) {
+                          volatile unsigned long long* seq, unsigned long long value,
+                          const int* __restrict__ derr) {
   for (int k = threadIdx.x; k < count; k += blockDim.x) hmir[first + k] = dsc[first + k];
+  if (threadIdx.x == 0) hmir[S_DERR] = (double)*derr;
   __threadfence_system();
   __syncwarp();
   if (threadIdx.x == 0) *seq = value;
@@ -216,16 +218,21 @@ __global__ void k_publish(const double* __restrict__ dsc, double* hmir, int firs
 // engine round trip and no blocking stream synchronisation on the critical
 // path between CG iterations.  The spin is bounded; after it (or if mapped
 // memory is unavailable) the stream is synchronised, which also surfaces
-// any device error.
+// any device error.  The device error flag is published with the scalars
+// (slot S_DERR of the mirror).
 void fetch_scalars(Ctx& c, int first, int count) {
+  if (!c.coarse_pending) c.derr_fresh = true;  // ordered after every factorisation
   if (!c.hseq) {
+    int e = 0;
     MGAR_CUDA(cudaMemcpyAsync(c.hsc + first, c.dsc + first, count * sizeof(double),
                               cudaMemcpyDeviceToHost, c.stream));
+    MGAR_CUDA(cudaMemcpyAsync(&e, c.derr, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
     MGAR_CUDA(cudaStreamSynchronize(c.stream));
+    c.hsc[S_DERR] = (double)e;
     return;
   }
   const unsigned long long want = ++c.seq_sent;
-  k_publish<<<1, 32, 0, c.stream>>>(c.dsc, c.hsc_dev, first, count, c.hseq_dev, want);
+  k_publish<<<1, 32, 0, c.stream>>>(c.dsc, c.hsc_dev, first, count, c.hseq_dev, want, c.derr);
   MGAR_LAUNCH_CHECK();
   const auto t0 = std::chrono::steady_clock::now();
   for (uint64_t spins = 0;; ++spins) {
@@ -245,10 +252,9 @@ void fetch_scalars(Ctx& c, int first, int count) {
   }
 }
 
-static void check_device_error(Ctx& c) {
-  int e = 0;
-  MGAR_CUDA(cudaMemcpyAsync(&e, c.derr, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
-  MGAR_CUDA(cudaStreamSynchronize(c.stream));
+// The device error flag as published by the last fetch_scalars.
+static void check_published_error(Ctx& c) {
+  const int e = (int)c.hsc[S_DERR];
   if (e != 0) {
     MGAR_CUDA(cudaMemsetAsync(c.derr, 0, sizeof(int), c.stream));
     throw Error{e, e == MGAR_ERR_NOT_SPD ? "factorisation met a non-positive pivot"
@@ -283,9 +289,29 @@ static void residual_norm(Ctx& c, const double* x, double* r, double* out) {
   MGAR_LAUNCH_CHECK();
 }
 
+static int solve_mgcg_fp(Ctx& c, double* T, int* iters, double* relres);
+
+// The factorisation's error flag is read with the solve's last scalar fetch
+// (one more fetch only when none followed the factorisation); a failed
+// factorisation is reported in place of any error it caused in the solve.
 int solve_mgcg(Ctx& c, double* T, int* iters, double* relres) {
   build_hierarchy(c);
-  check_device_error(c);
+  int rc = MGAR_OK;
+  try {
+    rc = solve_mgcg_fp(c, T, iters, relres);
+  } catch (const Error&) {
+    join_coarse(c);
+    fetch_scalars(c, S_RR, 1);
+    check_published_error(c);
+    throw;
+  }
+  join_coarse(c);
+  if (!c.derr_fresh) fetch_scalars(c, S_RR, 1);
+  check_published_error(c);
+  return rc;
+}
+
+static int solve_mgcg_fp(Ctx& c, double* T, int* iters, double* relres) {
   if (c.p.precision == MGAR_MIXED) return solve_mgcg_df(c, T, iters, relres);
   const int64_t n = c.n;
   if (c.dim == 2) residual_norm<2>(c, T, c.r, c.dsc + S_RR);
@@ -417,8 +443,8 @@ void solve_mgar(Ctx& c, const double* T_prev, double* T, double* res, int* accep
   k_reduced_combine<<<rb, kThreads, 0, c.stream>>>(c.R, c.W, c.q, n, kept, c.dsc, T, c.partials,
                                                    c.counter, c.dsc + S_RES2);
   MGAR_LAUNCH_CHECK();
-  check_device_error(c);
   fetch_scalars(c, S_RES2, 1);
+  check_published_error(c);
   const double r = std::sqrt(c.hsc[S_RES2]) / c.qnorm;
   require(std::isfinite(r), MGAR_ERR_NONFINITE, "non-finite MGAR residual");
   if (res) *res = r;
