@@ -155,10 +155,13 @@ mgar_step_info design_cycle(Ctx& c, double* rho, double* T, int cycle) {
   double comp = 0.0;
   // after a mixed 3D MGCG solve the double-float pairs of T are still in df_x
   const bool t_df = need_mgcg && c.p.precision == MGAR_MIXED && c.dim == 3 && !c.untiled;
-  sensitivity(c, T, c.tmp_dc, nullptr, &comp, t_df ? c.df_x : nullptr);
-  inf.compliance = comp;
+  sensitivity(c, T, c.tmp_dc, nullptr, nullptr, t_df ? c.df_x : nullptr);
+  // f = q^T T (Eq. 5), read with the OC update's first scalar fetch
+  dot(c, c.q, T, c.n, c.dsc + S_COMPL);
   double lam = 0.0, change = 0.0;
   oc_update(c, rho, c.tmp_dc, c.p.volfrac, c.p.move, &lam, &change);
+  comp = c.hsc[S_COMPL];
+  inf.compliance = comp;
   inf.lambda = lam;
   inf.status = status;
   return inf;
@@ -386,6 +389,7 @@ int mgar_create(mgar_t* out, const mgar_params* p, const uint8_t* fixed_mask, co
     if (const char* np = std::getenv("MGAR_NO_PDL")) c->use_pdl = np[0] != '1';
     if (const char* ng = std::getenv("MGAR_NO_CG_GRAPH")) c->cg_graph = ng[0] != '1';
     if (const char* dc = std::getenv("MGAR_DF64_CG")) c->ru_cg = dc[0] != '1';
+    if (const char* pp = std::getenv("MGAR_PROLONG_POINT")) c->prolong_col = pp[0] != '1';
     if (const char* rd = std::getenv("MGAR_RU_DELTA")) c->ru_delta = std::atof(rd);
     if (const char* fp = std::getenv("MGAR_FUSED_POST")) c->split_post = fp[0] != '1';
     if (const char* sc = std::getenv("MGAR_SPLIT_COARSE")) c->split_coarse_nodes = std::atoll(sc);

@@ -762,9 +762,8 @@ static int solve_mgcg_ru3(Ctx& c, double* T, int* iters, double* relres) {
     if (use_graph) {
       join_coarse(c);
       MGAR_CUDA(cudaGraphLaunch(c.ru_exec, c.stream));
-      fetch_scalars(c, S_RR, S_CGIT - S_RR + 1);
+      fetch_scalars(c, S_RR, S_RUCOUNT - S_RR + 1);  // one fetch: RR..CGIT and RUCOUNT
       it = (int)c.hsc[S_CGIT];
-      fetch_scalars(c, S_RUCOUNT, 1);
       count_launches((int64_t)it * c.ru_body_kernels +
                      (int64_t)c.hsc[S_RUCOUNT] * c.ru_update_kernels);
       rel = std::sqrt(c.hsc[S_RR]) / c.qnorm;

@@ -225,6 +225,7 @@ struct Ctx {
   int bottom_cluster = 8; // CTAs in that cluster
   int64_t bottom_nodes = kBottomNodes;  // largest level it takes
   bool use_pdl = true;    // programmatic dependent launch of the V-cycle and CG kernels
+  bool prolong_col = true;  // 3D interpolation by z-columns (MGAR_PROLONG_POINT=1: one node per thread)
   // device-side CG loop (3D mixed path): one graph with a conditional WHILE node
   bool cg_graph = true;
   cudaGraphExec_t cg_exec = nullptr;

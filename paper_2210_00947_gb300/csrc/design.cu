@@ -719,7 +719,9 @@ void oc_update(Ctx& c, double* rho, const double* dc, double volfrac, double mov
     k_oc_finish<<<1, 1024, 0, c.stream>>>(c.oc_s, c.oc_lo, c.oc_hi, c.dv, ne, volfrac, c.dsc,
                                           c.oc_amb, c.oc_namb);
     MGAR_LAUNCH_CHECK();
-    fetch_scalars(c, S_OC_FAIL, 1);
+    // one fetch from S_COMPL on: a compliance dot launched before the
+    // update arrives with the check
+    fetch_scalars(c, S_COMPL, S_OC_FAIL - S_COMPL + 1);
     fast_ok = c.hsc[S_OC_FAIL] == 0.0;
   }
   if (!fast_ok) {

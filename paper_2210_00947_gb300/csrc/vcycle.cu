@@ -192,6 +192,65 @@ __global__ void k_prolong(const Real* __restrict__ xc, const Real* cur, Real* ds
   dst[idx] = cur[idx] + acc;
 }
 
+// 3D interpolation by z-columns: a thread owns fine nodes (i, j, k0..k1)
+// and interpolates each coarse plane in x and y once (4 loads), so a fine
+// node costs one or two cached plane values instead of 8 coarse loads, and
+// the taps in x and y are formed once per column.
+template <typename Real>
+__global__ void k_prolong3(const Real* __restrict__ xc, const Real* cur, Real* dst, Dims f, Dims cd,
+                           const uint8_t* __restrict__ fixed, int kchunk) {
+  pdl_wait();
+  pdl_trigger();
+  const int NXY = f.NX * f.NY;
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= NXY) return;
+  const int i = col % f.NX, j = col / f.NX;
+  int ix[2], iy[2];
+  float wx[2], wy[2];
+  prolong_taps(i, f.ex, ix, wx);
+  prolong_taps(j, f.ey, iy, wy);
+  int o[4];
+  Real w[4];
+#pragma unroll
+  for (int b = 0; b < 2; ++b)
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+      o[2 * b + a] = ix[a] + cd.NX * iy[b];
+      w[2 * b + a] = (Real)(wx[a] * wy[b]);
+    }
+  const int cNXY = cd.NX * cd.NY;
+  // the two most recent coarse planes, interpolated in x and y
+  int pk0 = -1, pk1 = -1;
+  Real pv0 = Real(0), pv1 = Real(0);
+  auto plane = [&](int K) -> Real {
+    if (K == pk1) return pv1;
+    if (K == pk0) return pv0;
+    Real v = Real(0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (CK(o[q] + cNXY * K, cd.n)) v += w[q] * xc[o[q] + cNXY * K];
+    pk0 = pk1;
+    pv0 = pv1;
+    pk1 = K;
+    pv1 = v;
+    return v;
+  };
+  const int k0 = blockIdx.y * kchunk, k1 = min(k0 + kchunk, f.NZ);
+  for (int k = k0; k < k1; ++k) {
+    const int idx = col + NXY * k;
+    if (fixed && fixed[idx]) {
+      dst[idx] = cur[idx];
+      continue;
+    }
+    int iz[2];
+    float wz[2];
+    const int taps = prolong_taps(k, f.ez, iz, wz);
+    Real acc = (Real)wz[0] * plane(iz[0]);
+    if (taps == 2) acc += (Real)wz[1] * plane(iz[1]);
+    dst[idx] = cur[idx] + acc;
+  }
+}
+
 // Fused pre-smooth from a zero guess and residual on an assembled level:
 // x = w D^-1 b, r = b - A x (the neighbours' x recomputed from b and D^-1).
 template <typename Real, int DIM, bool CG>
@@ -569,6 +628,26 @@ void bottom_prepare(Ctx& c) {
   }
 }
 
+// dst = cur + P xc on level f (P from level cd; fixed nodes of f keep cur).
+template <typename Real, int DIM>
+static void launch_prolong(Ctx& c, bool pdl, const Real* xc, const Real* cur, Real* dst,
+                           const Dims& f, const Dims& cd, const uint8_t* fixed) {
+  if (DIM == 3 && c.prolong_col) {
+    const int64_t cols = (int64_t)f.NX * f.NY;
+    const int bx = blocks_for(cols);
+    // z chunks so that the grid holds about eight blocks per SM
+    int gz = (int)std::max<int64_t>(
+        1, std::min<int64_t>(f.NZ, ((int64_t)c.sms * 8 + bx - 1) / bx));
+    const int kchunk = (f.NZ + gz - 1) / gz;
+    gz = (f.NZ + kchunk - 1) / kchunk;
+    launch_pdl(c.stream, pdl && c.use_pdl, k_prolong3<Real>, dim3(bx, gz), dim3(kThreads), xc, cur,
+               dst, f, cd, fixed, kchunk);
+  } else {
+    launch_pdl(c.stream, pdl && c.use_pdl, k_prolong<Real, DIM>, dim3(blocks_for(f.n)),
+               dim3(kThreads), xc, cur, dst, f, cd, fixed);
+  }
+}
+
 // Table 1 with one pre- and one post-sweep and a zero guess below the finest
 // level: per level one fused pre kernel (smooth from zero + residual), the
 // restriction, and one fused post kernel (interpolation + smooth); the small
@@ -643,8 +722,8 @@ static void vcycle_fused(Ctx& c, const float* b0, float* x0, bool zero_guess,
     const Dims& d = c.L[l];
     if (d.n > c.split_coarse_nodes) {
       // large level: thin interpolation in place on x_l, then the sweep into t_l
-      launch_pdl(c.stream, c.use_pdl, k_prolong<Real, DIM>, dim3(blocks_for(d.n)), dim3(kThreads),
-                 res[l + 1], (const Real*)h[l].x, h[l].x, d, c.L[l + 1], (const uint8_t*)nullptr);
+      launch_prolong<Real, DIM>(c, true, res[l + 1], (const Real*)h[l].x, h[l].x, d, c.L[l + 1],
+                                (const uint8_t*)nullptr);
       MGAR_LAUNCH_CHECK_AT(level_site(4, l));
       sweep<Real, DIM>(c, l, h[l].b, h[l].x, h[l].t);
     } else {
@@ -661,8 +740,8 @@ static void vcycle_fused(Ctx& c, const float* b0, float* x0, bool zero_guess,
     fine3d(c, 1, ref_ke<Real>(c), b0, h[0].dinv, cur0, res[1], x0, nullptr, rdot, dout);
   } else if (DIM == 3) {
     // interpolation in place on the pre-smoothed iterate, then the tiled sweep
-    launch_pdl(c.stream, c.use_pdl, k_prolong<Real, DIM>, dim3(blocks_for(d0.n)), dim3(kThreads),
-               (const Real*)res[1], (const Real*)cur0, cur0, d0, c.L[1], (const uint8_t*)c.fixed);
+    launch_prolong<Real, DIM>(c, true, (const Real*)res[1], (const Real*)cur0, cur0, d0, c.L[1],
+                              (const uint8_t*)c.fixed);
     MGAR_LAUNCH_CHECK_AT(level_site(4, 0));
     fine3d(c, 3, ref_ke<Real>(c), b0, h[0].dinv, cur0, nullptr, x0, nullptr, rdot, dout);
   } else {
@@ -737,9 +816,8 @@ static void vcycle_dim(Ctx& c, const Real* b0, Real* x0, bool zero_guess) {
     Real* other = h[l].t;
     const int post = c.p.nu_post;
     Real* dst = (post % 2 == 0) ? x : other;
-    k_prolong<Real, DIM><<<blocks_for(d.n), kThreads, 0, c.stream>>>(h[l + 1].x, cur[l], dst, d,
-                                                                      c.L[l + 1],
-                                                                      l == 0 ? c.fixed : nullptr);
+    launch_prolong<Real, DIM>(c, false, (const Real*)h[l + 1].x, (const Real*)cur[l], dst, d,
+                              c.L[l + 1], l == 0 ? (const uint8_t*)c.fixed : nullptr);
     MGAR_LAUNCH_CHECK_AT(level_site(4, l));
     Real* cu = dst;
     for (int s = 0; s < post; ++s) {
