@@ -49,6 +49,12 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--timeline", action="store_true",
                     help="after timing, print a per-launch-site device-time table to stderr")
+    ap.add_argument("--replay", default=None,
+                    help="comma-separated paper-setting workloads (e.g. paper2d_m1,paper2d_m2): "
+                         "MGAR against pure MGCG as in Table 2, one JSON line each")
+    ap.add_argument("--nl", type=int, default=0, help="replay: number of levels (0 = workload's)")
+    ap.add_argument("--replay-precisions", default="mixed,fp64")
+    ap.add_argument("--replay-guesses", default="previous,zero")
     return ap.parse_args()
 
 
@@ -502,9 +508,96 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------ paper-setting replay
+# Table 2 of the paper (2D heat sink, nl 3, eps1 0.5, eps2 1e-6, 300 cycles):
+# costs normalised to Model 1's MGAR run, MGCG evaluations inside MGAR,
+# efficiency improvement and relative objective difference of MGAR against
+# pure MGCG.  Context only: another machine, FP64 Matlab.
+PAPER_TABLE2 = {
+    "paper2d_m1": dict(cost_mgar=1.0, cost_mgcg=1.71, mgcg_evaluations=107,
+                       efficiency_improvement=0.4165, relative_difference=0.0015),
+    "paper2d_m2": dict(cost_mgar=5.58, cost_mgcg=9.16, mgcg_evaluations=115,
+                       efficiency_improvement=0.3911, relative_difference=0.00037),
+    "paper2d_m3": dict(cost_mgar=42.25, cost_mgcg=65.17, mgcg_evaluations=125,
+                       efficiency_improvement=0.3518, relative_difference=0.000040),
+    "paper2d_m4": dict(cost_mgar=102.81, cost_mgcg=156.01, mgcg_evaluations=127,
+                       efficiency_improvement=0.3410, relative_difference=0.000033),
+}
+
+
+def run_replay(args):
+    """MGAR against pure MGCG on the paper's 2D models: one whole run of
+    each (after a short warm-up run), device time with CUDA events, for both
+    precisions and both readings of Eq. 17's initial guess."""
+    import torch
+
+    from paper_2210_00947_gb300 import mgar, workloads
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    base_ms = {}
+    for name in args.replay.split(","):
+        w = workloads.WORKLOADS[name]
+        cycles = args.cycles or w.iters
+        fixed, q, rho0 = w.fixed(), w.q(), w.density()
+        rho0_d = torch.tensor(rho0, device=dev)
+        nl = args.nl or w.nl
+        for prec_name in args.replay_precisions.split(","):
+            prec = mgar.MGAR_MIXED if prec_name == "mixed" else mgar.MGAR_FP64
+            for guess_name in args.replay_guesses.split(","):
+                guess = (mgar.MGAR_GUESS_PREVIOUS if guess_name == "previous"
+                         else mgar.MGAR_GUESS_ZERO)
+                runs = {}
+                for mode, n_on in (("mgar", w.n_on), ("mgcg", cycles + 1)):
+                    p = mgar.params_for(w, precision=prec, basis_guess=guess, n_on=n_on, nl=nl)
+                    solver = mgar.Solver(p, fixed, q, stream=stream)
+                    rho = torch.empty_like(rho0_d)
+                    T = torch.zeros(solver.n_nodes, dtype=torch.float64, device=dev)
+
+                    def one_run(nc):
+                        rho.copy_(rho0_d)
+                        T.zero_()
+                        return [solver.step(rho, T, k) for k in range(1, nc + 1)]
+
+                    one_run(min(cycles, 3))  # graphs and buffers
+                    torch.cuda.synchronize()
+                    start = torch.cuda.Event(enable_timing=True)
+                    end = torch.cuda.Event(enable_timing=True)
+                    start.record(stream)
+                    infos = one_run(cycles)
+                    end.record(stream)
+                    end.synchronize()
+                    runs[mode] = (start.elapsed_time(end), infos)
+                    solver.close()
+                t_mgar, inf_a = runs["mgar"]
+                t_mgcg, inf_c = runs["mgcg"]
+                key = (prec_name, guess_name)
+                base_ms.setdefault(key, t_mgar)
+                fa, fc = inf_a[-1]["compliance"], inf_c[-1]["compliance"]
+                line = {
+                    "replay": name, "dofs": w.n_nodes, "cycles": cycles, "nl": nl,
+                    "precision": prec_name,
+                    "basis_guess": guess_name, "mgar_ms": t_mgar, "mgcg_ms": t_mgcg,
+                    "savings_ms": t_mgcg - t_mgar,
+                    "cost_mgar": t_mgar / base_ms[key], "cost_mgcg": t_mgcg / base_ms[key],
+                    "mgcg_evaluations": sum(1 for i in inf_a if i["used_mgcg"]),
+                    "mgar_accepted": sum(1 for i in inf_a if i["accepted"]),
+                    "efficiency_improvement": 1.0 - t_mgar / t_mgcg,
+                    "relative_difference": abs(fa - fc) / abs(fc),
+                    "objective_mgar": fa, "objective_mgcg": fc,
+                    "cg_iters_mean_mgcg": statistics.mean(i["cg_iters"] for i in inf_c),
+                    "paper": PAPER_TABLE2.get(name),
+                    "data": "synthetic (the paper's geometry, source and settings)",
+                }
+                print(json.dumps(line), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.replay:
+        run_replay(a)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_gpu(a)

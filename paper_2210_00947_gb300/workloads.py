@@ -207,6 +207,8 @@ class Workload:
     m: int = 2
     eps1: float = 0.5
     load: float = 0.01
+    # heat source per unit volume (Section 3.2); None: the uniform nodal load
+    source: float | None = None
 
     @property
     def dim(self) -> int:
@@ -230,13 +232,56 @@ class Workload:
         return heat_sink_mask(self.nx, self.ny, self.nz)
 
     def q(self) -> np.ndarray:
+        if self.source is not None:
+            return volumetric_load(self.nx, self.ny, self.nz, self.source, self.fixed())
         return nodal_load(self.fixed(), self.load)
 
     def density(self) -> np.ndarray:
         return uniform_density(self.n_elems, self.rho0)
 
 
+# largest coarsest grid (nodes) the explicit coarse inverse is built for
+COARSEST_MAX_NODES = 8192
+
+
+# coarsest grid size (nodes) the paper-setting workloads aim for
+COARSEST_TARGET_NODES = 300
+
+
+def levels_for_direct_coarsest(nx: int, ny: int, nz: int = 0, nl_min: int = 3,
+                               max_nodes: int = COARSEST_MAX_NODES) -> int:
+    """Fewest levels >= nl_min whose coarsest grid (ceil coarsening) has at
+    most max_nodes nodes."""
+    nl = nl_min
+    while True:
+        ex, ey, ez = nx, ny, nz
+        for _ in range(nl - 1):
+            ex, ey, ez = (ex + 1) // 2, (ey + 1) // 2, (ez + 1) // 2 if nz else 0
+        if num_nodes(ex, ey, ez) <= max_nodes:
+            return nl
+        nl += 1
+
+
+def _paper2d(name: str, n: int) -> Workload:
+    # The 2D heat-sink models of Table 2 (Sections 3.2 and 4.1): n x n
+    # elements, volume fraction 0.5, r_min 3, two basis vectors, eps1 0.5,
+    # eps2 1e-6, cg_max 200, source 1e-4 per unit volume, 300 design cycles
+    # (the figures' run length), N_on = 2/15 of them.  The paper uses nl = 3
+    # (coarsest 91^2 .. 511^2 nodes, a sparse direct solve).  Here the
+    # coarsest level is factorised (a chain of sequential pivots on one SM)
+    # at every MGCG call, so nl is the fewest levels >= 3 whose coarsest grid
+    # holds at most 300 nodes (on Model 1, nl 4 with a 2116-node coarsest
+    # grid costs 14.5 ms per MGCG design cycle, nl 6 with 169 nodes 1.8 ms).
+    return Workload(name, n, n, 0, volfrac=0.5, rho0=0.5,
+                    nl=levels_for_direct_coarsest(n, n, max_nodes=COARSEST_TARGET_NODES),
+                    iters=300, eps2=1e-6, cg_max=200, rmin=3.0, source=1e-4)
+
+
 WORKLOADS = {
+    "paper2d_m1": _paper2d("paper2d_m1", 360),
+    "paper2d_m2": _paper2d("paper2d_m2", 720),
+    "paper2d_m3": _paper2d("paper2d_m3", 1560),
+    "paper2d_m4": _paper2d("paper2d_m4", 2040),
     "heat2d_100": Workload("heat2d_100", 100, 100, 0, volfrac=0.4, rho0=0.4, nl=4, iters=100),
     "heat2d_1024": Workload("heat2d_1024", 1024, 1024, 0, volfrac=0.4, rho0=0.4, nl=7, iters=50),
     "heat3d_128": Workload("heat3d_128", 128, 128, 128, volfrac=0.3, rho0=0.3, nl=6, iters=50),

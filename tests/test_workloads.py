@@ -1,0 +1,53 @@
+"""The paper-setting workloads against the figures the paper prints for
+them (Table 2: DOF counts of Models 1-4; Section 3.2: source, sink patch,
+N_on)."""
+import numpy as np
+import pytest
+
+from paper_2210_00947_gb300 import workloads
+
+
+@pytest.mark.parametrize("name,dofs", [("paper2d_m1", 130321), ("paper2d_m2", 519841),
+                                       ("paper2d_m3", 2436721), ("paper2d_m4", 4165681)])
+def test_paper_models_match_table2_dofs(name, dofs):
+    w = workloads.WORKLOADS[name]
+    assert w.n_nodes == dofs
+    # the axial element count is a multiple of 2^(3-1) for the paper's nl = 3
+    # (Section 3.2); the level count used here keeps the coarsest grid small
+    # enough for the explicit coarse inverse
+    assert w.nx % 4 == 0 and w.ny % 4 == 0
+    assert w.nl >= 3
+    ex = w.nx
+    for _ in range(w.nl - 1):
+        ex = (ex + 1) // 2
+    assert (ex + 1) ** 2 <= workloads.COARSEST_TARGET_NODES
+    # and one level fewer would not be
+    ex2 = w.nx
+    for _ in range(w.nl - 2):
+        ex2 = (ex2 + 1) // 2
+    assert w.nl == 3 or (ex2 + 1) ** 2 > workloads.COARSEST_TARGET_NODES
+    # N_on is 2/15 of the 300 design cycles
+    assert w.iters == 300 and w.n_on == 40
+
+
+def test_paper_model_load_and_sink():
+    w = workloads.WORKLOADS["paper2d_m1"]
+    fixed = w.fixed()
+    q = w.q()
+    # sink: the middle tenth of the left edge (j in [162, 198] of 0..360)
+    sink = np.flatnonzero(fixed)
+    NX = w.nx + 1
+    assert np.all(sink % NX == 0)
+    rows = sink // NX
+    assert rows.min() == 162 and rows.max() == 198 and len(rows) == 37
+    # 1e-4 per unit volume over 360^2 unit elements, each node receiving a
+    # quarter of each adjacent element's share; sink nodes receive nothing
+    # the 37 sink nodes lie on the left edge, each touching two elements (the
+    # end nodes of the edge would touch one; the patch is in the middle)
+    assert abs(q.sum() - (1e-4 * 360 * 360 - 37 * 2 * 1e-4 / 4)) < 1e-12
+    full = workloads.volumetric_load(w.nx, w.ny, 0, 1e-4, np.zeros_like(fixed))
+    assert abs(full.sum() - 1e-4 * 360 * 360) < 1e-12
+    assert np.all(q[fixed != 0] == 0.0)
+    np.testing.assert_allclose(q[fixed == 0], full[fixed == 0])
+    # interior node: four elements x 1e-4 / 4
+    assert abs(full[NX * 100 + 100] - 1e-4) < 1e-18
