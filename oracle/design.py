@@ -20,6 +20,7 @@ with geometric midpoints until (hi - lo) / (hi + lo) <= 1e-13 or 200 steps.
 from __future__ import annotations
 
 import itertools
+import math
 
 import numpy as np
 import scipy.sparse as sp
@@ -51,6 +52,22 @@ def filter_matrix(grid: Grid, r: float) -> tuple[sp.csr_matrix, np.ndarray]:
                       shape=(grid.n_elems, grid.n_elems))
     Hs = np.asarray(H.sum(axis=1)).reshape(-1)
     return H, Hs
+
+
+def filter_radius(k: int, rmin: float, alpha: float, L: float, lp: int) -> float:
+    """Filter radius of design cycle k (1-based) under the continuous
+    schedule, Eq. 22-23: r^(k) = max(r_min, eta r^(k-1)) from r^(0) = alpha L,
+    eta = exp((ln r_min - ln(alpha L)) / lp), so that r reaches r_min after lp
+    cycles.  Reading: the recursion is applied from the first cycle on; when
+    alpha L <= r_min there is nothing to shrink and r = r_min throughout."""
+    r0 = alpha * L
+    if not (r0 > rmin) or lp <= 0:
+        return rmin
+    eta = math.exp((math.log(rmin) - math.log(r0)) / lp)
+    r = r0
+    for _ in range(k):
+        r = max(rmin, eta * r)
+    return r
 
 
 def filter_forward(H, Hs, x):

@@ -10,7 +10,8 @@ Per design cycle k = 1..iters:
       else: t = MGCG(K(rho~), q, t_prev); K0 <- K(rho~)
   f = q^T t; (dc, dv) = sensitivities                 (Eq. 5, 9-11)
   rho = OC(rho, dc, dv)                               (not in the paper)
-Reading: t_prev starts at zero; MGCG always starts from t_prev.
+Reading: t_prev starts at zero; MGCG always starts from t_prev.  With the
+continuous filter (Eq. 22-23) the filter of cycle k has radius r^(k).
 """
 from __future__ import annotations
 
@@ -45,6 +46,11 @@ class LoopSettings:
     nu_post: int = 1
     basis_guess: str = "previous"
     use_mgar: bool = True
+    # continuous filter radius (Eq. 22-23): off when filter_alpha is 0;
+    # L defaults to the longest side in elements
+    filter_alpha: float = 0.0
+    filter_lp: int = 0
+    filter_L: float = 0.0
 
 
 class Analysis:
@@ -56,7 +62,8 @@ class Analysis:
         self.grid = fem.Grid(s.nx, s.ny, s.nz)
         self.fixed = np.asarray(fixed)
         self.q = np.asarray(q, dtype=np.float64)
-        self.H, self.Hs = design.filter_matrix(self.grid, s.rmin)
+        self.r = s.rmin
+        self.H, self.Hs = design.filter_matrix(self.grid, self.r)
         self.A0 = None
         self.levels0 = None
         self.dims = (s.nx, s.ny) if s.nz == 0 else (s.nx, s.ny, s.nz)
@@ -76,6 +83,12 @@ class Analysis:
     def cycle(self, k, rho, t_prev):
         """One design cycle; returns (rho_new, t, info)."""
         s = self.s
+        if s.filter_alpha > 0.0:
+            L = s.filter_L or float(max(s.nx, s.ny, s.nz))
+            r = design.filter_radius(k, s.rmin, s.filter_alpha, L, s.filter_lp)
+            if r != self.r:
+                self.r = r
+                self.H, self.Hs = design.filter_matrix(self.grid, r)
         rho_phys = design.filter_forward(self.H, self.Hs, rho)
         A = self.system(rho_phys)
         info = dict(cycle=k, mgcg=False, accepted=False, res=float("nan"), cg_iters=0)

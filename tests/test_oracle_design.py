@@ -93,3 +93,25 @@ def test_oc_keeps_volume_and_limits(dims):
     raw = rho * np.sqrt(-dc / (lam * dv))
     inside = (raw > rho - 0.2 + 1e-9) & (raw < rho + 0.2 - 1e-9) & (raw < 1 - 1e-9) & (raw > 1e-9)
     np.testing.assert_allclose(rn[inside], raw[inside], rtol=1e-14)
+
+
+def test_filter_radius_schedule_eq22_23():
+    """Eq. 22-23: r starts at alpha L, shrinks geometrically by eta per cycle
+    and reaches r_min after lp cycles; the recursion with max() equals the
+    closed form max(r_min, (alpha L) eta^k)."""
+    import math
+    rmin, alpha, L, lp = 3.0, 1.4 / 50, 480.0, 250
+    r0 = alpha * L
+    eta = math.exp((math.log(rmin) - math.log(r0)) / lp)
+    assert abs(eta ** lp * r0 - rmin) < 1e-12
+    prev = r0
+    for k in range(1, 301):
+        r = design.filter_radius(k, rmin, alpha, L, lp)
+        assert r <= prev + 1e-15 and r >= rmin
+        assert abs(r - max(rmin, r0 * eta ** k)) < 1e-11 * r0
+        prev = r
+    assert abs(design.filter_radius(lp, rmin, alpha, L, lp) - rmin) < 1e-11
+    assert design.filter_radius(lp + 1, rmin, alpha, L, lp) == rmin
+    assert design.filter_radius(300, rmin, alpha, L, lp) == rmin
+    # nothing to shrink: alpha L below r_min
+    assert design.filter_radius(5, 3.0, 0.01, 100.0, 10) == 3.0

@@ -42,3 +42,29 @@ def test_accepted_reanalysis_is_close():
     acc = [h for h in hist if h["accepted"]]
     assert len(acc) > 0
     assert all(h["res"] <= 0.5 for h in acc)
+
+
+def test_continuous_filter_schedule_in_the_loop():
+    """With the continuous filter (Eq. 22-23) cycle k filters with radius
+    r^(k): the filter the loop holds after cycle k is the filter of that
+    radius, and once the radius has reached r_min the loop equals the plain
+    filter's loop started from the same design."""
+    s = _settings(nx=20, ny=20, iters=5, n_on=6, filter_alpha=0.2, filter_lp=3)
+    fixed = workloads.heat_sink_mask(s.nx, s.ny)
+    q = workloads.nodal_load(fixed)
+    an = loop.Analysis(s, fixed, q)
+    rho = np.full(s.nx * s.ny, 0.4)
+    t = np.zeros(an.grid.n_nodes)
+    radii = []
+    for k in range(1, s.iters + 1):
+        rho, t, _ = an.cycle(k, rho, t)
+        radii.append(an.r)
+        H, Hs = design.filter_matrix(an.grid, an.r)
+        assert abs(H - an.H).max() == 0.0
+    assert radii[0] < 4.0 and radii[0] > radii[1] > 1.5
+    assert radii[2] == radii[3] == radii[4] == 1.5 or abs(radii[2] - 1.5) < 1e-12
+    # from the cycle after r reached r_min on, the plain loop continues identically
+    plain = loop.Analysis(_settings(nx=20, ny=20, iters=5, n_on=6), fixed, q)
+    r_a, t_a, _ = an.cycle(6, rho, t)
+    r_b, t_b, _ = plain.cycle(6, rho, t)
+    np.testing.assert_array_equal(r_a, r_b)
