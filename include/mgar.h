@@ -72,6 +72,16 @@ typedef struct mgar_params {
   int32_t n_on;         /* MGAR activation cycle N_on (Section 3.1) */
   double volfrac;       /* volume fraction of the OC update */
   double move;          /* OC move limit */
+  /* Continuous filter radius (Section 2.3, Eq. 22-23): design cycle k of
+   * mgar_step / mgar_run filters with r^(k) = max(rmin, eta r^(k-1)),
+   * r^(0) = filter_alpha * filter_L, eta = exp((ln rmin - ln r^(0)) /
+   * filter_lp).  Off when filter_alpha <= 0 (the filter keeps rmin); with
+   * filter_L <= 0 the longest side in elements is used.  The largest radius
+   * must leave at most 2048 filter offsets (about r <= 25 in 2D, 7.8 in 3D),
+   * else mgar_create fails with MGAR_ERR_ARG. */
+  double filter_alpha;
+  int32_t filter_lp;
+  double filter_L;
 } mgar_params;
 
 /* Per-cycle report of mgar_step. */

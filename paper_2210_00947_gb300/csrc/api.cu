@@ -122,6 +122,8 @@ void free_ctx(Ctx& c) {
                   c.oc_hi, c.oc_s32, c.oc_lo32, c.oc_hi32, c.dv32, c.oc_amb, c.oc_namb, c.partials, c.counter, c.dsc, c.derr};
   for (void* p : ptrs) cudaFree(p);
   if (c.hsc) cudaFreeHost(c.hsc);
+  if (c.f_offs_h) cudaFreeHost(c.f_offs_h);
+  if (c.f_w_h) cudaFreeHost(c.f_w_h);
   if (c.hseq) cudaFreeHost(c.hseq);
 }
 
@@ -131,6 +133,10 @@ mgar_step_info design_cycle(Ctx& c, double* rho, double* T, int cycle) {
   inf.res = NAN;
   inf.relres = NAN;
   int status = MGAR_OK;
+  if (c.p.filter_alpha > 0.0) {
+    const double r = filter_radius(c, cycle);
+    if (r != c.filter_r) set_filter_radius(c, r);
+  }
   set_density(c, rho, false);
   bool need_mgcg = cycle < c.p.n_on || !c.have_ref;
   if (!need_mgcg) {
@@ -191,6 +197,9 @@ void mgar_default_params(mgar_params* p) {
   p->n_on = 0;
   p->volfrac = 0.4;
   p->move = 0.2;
+  p->filter_alpha = 0.0;
+  p->filter_lp = 0;
+  p->filter_L = 0.0;
 }
 
 const char* mgar_last_error(mgar_t h) {

@@ -41,7 +41,7 @@ constexpr int kMaxLevels = 14;
 constexpr int kThreads = 256;
 constexpr int kMinPartialBlocks = 8192;
 constexpr int64_t kBottomNodes = 8192;  // largest level handled by the V-cycle's cluster launch
-constexpr int kMaxFilterOffsets = 1024;
+constexpr int kMaxFilterOffsets = 2048;
 constexpr int kMaxM = 8;
 constexpr int kOcCand = 31;      // multisection candidates per pass (5 bits)
 constexpr int kOcPasses = 6;     // FP32 passes at most: ln-bracket 92 -> 9e-8
@@ -160,6 +160,10 @@ struct Ctx {
   double* dv = nullptr;     // F^T (1/E)
   double* rsdv = nullptr;   // 1 / sqrt(dv)
   int n_filter = 0;
+  double filter_r = 0.0;    // radius of the current tables
+  int filter_cap = 0;       // offsets the tables have room for
+  int4* f_offs_h = nullptr; // pinned staging of the tables (continuous filter)
+  double* f_w_h = nullptr;
 
   // hierarchy
   LevelBuf<double> h64[kMaxLevels];
@@ -846,6 +850,10 @@ void dot(Ctx& c, const double* a, const double* b, int64_t n, double* out_dev);
 void fetch_scalars(Ctx& c, int first, int count);
 // design.cu
 void setup_filter(Ctx& c);
+// continuous filter (Eq. 22-23): radius of design cycle k, and new tables
+// (offsets, weights, 1/Hs, dv and its copies) for radius r, stream-ordered
+double filter_radius(const Ctx& c, int k);
+void set_filter_radius(Ctx& c, double r);
 void filter(Ctx& c, const double* in, double* out, bool transpose);
 void set_density(Ctx& c, const double* rho, bool physical);
 // T_df: the same temperatures as double-float pairs when the caller has them

@@ -1,5 +1,8 @@
 // Density filter (Eq. 6-8), SIMP conductivities (Eq. 4), compliance and
 // sensitivities (Eq. 5, 9-11), and the optimality-criteria update.
+#include <algorithm>
+#include <vector>
+
 #include "common.cuh"
 #include "df64.cuh"
 
@@ -54,11 +57,11 @@ __device__ __forceinline__ void acc_prod(float& ah, float& al, df w, df x) {
 }
 
 // sum over in-domain offsets o of w_o in_{e+o}
-__device__ __forceinline__ df filter_sum_df(const float2* __restrict__ in, const df* w, const int4* offs,
+__device__ __forceinline__ df filter_sum_df(const float2* __restrict__ in, const df* w, const char4* offs,
                                             int noff, int e, int i, int j, int k, const Dims& d) {
   float ah = 0.f, al = 0.f;
   for (int o = 0; o < noff; ++o) {
-    const int4 dd = offs[o];
+    const char4 dd = offs[o];
     const int ii = i + dd.x, jj = j + dd.y, kk = k + dd.z;
     const bool ok = !(ii < 0 || ii >= d.ex || jj < 0 || jj >= d.ey || kk < 0 || kk >= d.ez);
     const int nb = ok ? ii + d.ex * (jj + d.ey * kk) : e;  // valid address either way
@@ -77,11 +80,13 @@ __global__ void k_filter_simp_df(const float2* __restrict__ rho, const double* _
                                  Dims d, double k0, double kmin, double penal,
                                  double* __restrict__ rho_phys, double* __restrict__ ke,
                                  float* __restrict__ kf, float2* __restrict__ kdf) {
+  // offsets staged as bytes: |d| <= 127 for any radius the tables allow
   __shared__ df ws[kMaxFilterOffsets];
-  __shared__ int4 os[kMaxFilterOffsets];
+  __shared__ char4 os[kMaxFilterOffsets];
   for (int o = threadIdx.x; o < noff; o += blockDim.x) {
     ws[o] = df_from_double(w[o]);
-    os[o] = offs[o];
+    const int4 v = offs[o];
+    os[o] = make_char4((signed char)v.x, (signed char)v.y, (signed char)v.z, 0);
   }
   __syncthreads();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -153,11 +158,13 @@ __global__ void k_sens_df(const float2* __restrict__ T, const double* __restrict
 // Transpose filter (Eq. 9/11) of a df64 input already scaled by inv_hs.
 __global__ void k_filter_t_df(const float2* __restrict__ in, const int4* __restrict__ offs,
                               const double* __restrict__ w, int noff, Dims d, double* __restrict__ out) {
+  // offsets staged as bytes: |d| <= 127 for any radius the tables allow
   __shared__ df ws[kMaxFilterOffsets];
-  __shared__ int4 os[kMaxFilterOffsets];
+  __shared__ char4 os[kMaxFilterOffsets];
   for (int o = threadIdx.x; o < noff; o += blockDim.x) {
     ws[o] = df_from_double(w[o]);
-    os[o] = offs[o];
+    const int4 v = offs[o];
+    os[o] = make_char4((signed char)v.x, (signed char)v.y, (signed char)v.z, 0);
   }
   __syncthreads();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -565,12 +572,13 @@ __global__ void k_oc_prep32(const double* __restrict__ s, const double* __restri
 }
 
 // ------------------------------------------------------------------- host
-void setup_filter(Ctx& c) {
-  const double r = c.p.rmin;
+// Offsets and weights max(0, r - |d|) of a radius-r filter (Eq. 7), in the
+// order dz, dy, dx.
+static void filter_tables(double r, int dim, std::vector<int4>& offs, std::vector<double>& w) {
   const int reach = (int)std::ceil(r);
-  std::vector<int4> offs;
-  std::vector<double> w;
-  const int zr = c.dim == 3 ? reach : 0;
+  offs.clear();
+  w.clear();
+  const int zr = dim == 3 ? reach : 0;
   for (int dz = -zr; dz <= zr; ++dz)
     for (int dy = -reach; dy <= reach; ++dy)
       for (int dx = -reach; dx <= reach; ++dx) {
@@ -580,26 +588,83 @@ void setup_filter(Ctx& c) {
           w.push_back(wt);
         }
       }
-  require((int)offs.size() <= kMaxFilterOffsets, MGAR_ERR_ARG, "filter radius too large");
-  c.n_filter = (int)offs.size();
-  MGAR_CUDA(cudaMalloc(&c.f_offs, offs.size() * sizeof(int4)));
-  MGAR_CUDA(cudaMalloc(&c.f_w, w.size() * sizeof(double)));
-  MGAR_CUDA(cudaMemcpy(c.f_offs, offs.data(), offs.size() * sizeof(int4), cudaMemcpyHostToDevice));
-  MGAR_CUDA(cudaMemcpy(c.f_w, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice));
+}
+
+// Eq. 22-23, applied as a recursion from r^(0) = alpha L exactly as written
+// (the same sequence of multiplications as the oracle); r_min throughout
+// when alpha L <= r_min.
+double filter_radius(const Ctx& c, int k) {
+  const double L = c.p.filter_L > 0.0 ? c.p.filter_L : (double)std::max(std::max(c.p.nx, c.p.ny), c.p.nz);
+  const double r0 = c.p.filter_alpha * L, rmin = c.p.rmin;
+  if (!(r0 > rmin) || c.p.filter_lp <= 0) return rmin;
+  const double eta = std::exp((std::log(rmin) - std::log(r0)) / c.p.filter_lp);
+  double r = r0;
+  for (int i = 0; i < k; ++i) r = std::max(rmin, eta * r);
+  return r;
+}
+
+__global__ void k_fill(double* __restrict__ a, double v, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = v;
+}
+
+// 1/Hs and dv = F^T (1/E) (with its FP32 copy and 1/sqrt) for the current tables
+static void filter_derived(Ctx& c) {
   const Dims& d = c.L[0];
   k_filter_norm<<<blocks_for(c.ne), kThreads, 0, c.stream>>>(c.inv_hs, c.f_offs, c.f_w, c.n_filter,
                                                              d);
   MGAR_LAUNCH_CHECK();
-  // dv = F^T (1/E)
-  std::vector<double> ones(c.ne, 1.0 / (double)c.ne);
-  MGAR_CUDA(cudaMemcpyAsync(c.tmp_e, ones.data(), c.ne * sizeof(double), cudaMemcpyHostToDevice,
-                            c.stream));
+  k_fill<<<blocks_for(c.ne), kThreads, 0, c.stream>>>(c.tmp_e, 1.0 / (double)c.ne, (int)c.ne);
+  MGAR_LAUNCH_CHECK();
   filter(c, c.tmp_e, c.dv, true);
   k_d2f_e<<<blocks_for(c.ne), kThreads, 0, c.stream>>>(c.dv, c.dv32, (int)c.ne);
   MGAR_LAUNCH_CHECK();
   k_rsqrt_e<<<blocks_for(c.ne), kThreads, 0, c.stream>>>(c.dv, c.rsdv, (int)c.ne);
   MGAR_LAUNCH_CHECK();
+}
+
+void setup_filter(Ctx& c) {
+  // room for the largest radius the run will use
+  double rcap = c.p.rmin;
+  if (c.p.filter_alpha > 0.0) rcap = std::max(rcap, filter_radius(c, 0));
+  std::vector<int4> offs;
+  std::vector<double> w;
+  filter_tables(rcap, c.dim, offs, w);
+  require((int)offs.size() <= kMaxFilterOffsets, MGAR_ERR_ARG, "filter radius too large");
+  c.filter_cap = (int)offs.size();
+  MGAR_CUDA(cudaMalloc(&c.f_offs, offs.size() * sizeof(int4)));
+  MGAR_CUDA(cudaMalloc(&c.f_w, w.size() * sizeof(double)));
+  if (c.p.filter_alpha > 0.0) {
+    MGAR_CUDA(cudaHostAlloc(&c.f_offs_h, offs.size() * sizeof(int4), cudaHostAllocDefault));
+    MGAR_CUDA(cudaHostAlloc(&c.f_w_h, w.size() * sizeof(double), cudaHostAllocDefault));
+  }
+  filter_tables(c.p.rmin, c.dim, offs, w);
+  c.n_filter = (int)offs.size();
+  c.filter_r = c.p.rmin;
+  MGAR_CUDA(cudaMemcpy(c.f_offs, offs.data(), offs.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  MGAR_CUDA(cudaMemcpy(c.f_w, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice));
+  filter_derived(c);
   MGAR_CUDA(cudaStreamSynchronize(c.stream));
+}
+
+// New tables through the pinned staging buffers.  The previous copy out of
+// them has completed: every design cycle waits on the stream (scalar
+// fetches) after its filter work.
+void set_filter_radius(Ctx& c, double r) {
+  std::vector<int4> offs;
+  std::vector<double> w;
+  filter_tables(r, c.dim, offs, w);
+  require((int)offs.size() <= c.filter_cap && c.f_offs_h, MGAR_ERR_ARG,
+          "filter radius beyond the tables' capacity");
+  std::copy(offs.begin(), offs.end(), c.f_offs_h);
+  std::copy(w.begin(), w.end(), c.f_w_h);
+  MGAR_CUDA(cudaMemcpyAsync(c.f_offs, c.f_offs_h, offs.size() * sizeof(int4),
+                            cudaMemcpyHostToDevice, c.stream));
+  MGAR_CUDA(cudaMemcpyAsync(c.f_w, c.f_w_h, w.size() * sizeof(double), cudaMemcpyHostToDevice,
+                            c.stream));
+  c.n_filter = (int)offs.size();
+  c.filter_r = r;
+  filter_derived(c);
 }
 
 void filter(Ctx& c, const double* in, double* out, bool transpose) {

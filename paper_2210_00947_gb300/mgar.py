@@ -54,7 +54,9 @@ class Params(ctypes.Structure):
                 ("eps1", ctypes.c_double), ("eps2", ctypes.c_double), ("cg_max", ctypes.c_int32),
                 ("omega", ctypes.c_double), ("nu_pre", ctypes.c_int32), ("nu_post", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("basis_guess", ctypes.c_int32),
-                ("n_on", ctypes.c_int32), ("volfrac", ctypes.c_double), ("move", ctypes.c_double)]
+                ("n_on", ctypes.c_int32), ("volfrac", ctypes.c_double), ("move", ctypes.c_double),
+                ("filter_alpha", ctypes.c_double), ("filter_lp", ctypes.c_int32),
+                ("filter_L", ctypes.c_double)]
 
 
 class StepInfo(ctypes.Structure):

@@ -31,7 +31,7 @@ def test_library_builds_and_exports_header():
 
 def test_params_layout_and_defaults():
     p = mgar.default_params()
-    assert ctypes.sizeof(mgar.Params) == 128
+    assert ctypes.sizeof(mgar.Params) == 152
     assert (p.k0, p.kmin, p.penal, p.rmin, p.nl, p.m) == (1.0, 1e-3, 3.0, 1.5, 4, 2)
     assert (p.eps1, p.eps2, p.cg_max, p.omega) == (0.5, 1e-8, 200, 0.6)
 

@@ -13,16 +13,18 @@ DEV = "cuda:0"
 
 
 def run_stepwise(nx, ny, nz, nl, iters, n_on, precision, eps1=0.5, eps2=1e-12, guess="previous",
-                 volfrac=0.4):
+                 volfrac=0.4, filter_alpha=0.0, filter_lp=0):
     fixed = workloads.heat_sink_mask(nx, ny, nz)
     q = workloads.nodal_load(fixed)
     nel = workloads.num_elements(nx, ny, nz)
     s = loop.LoopSettings(nx=nx, ny=ny, nz=nz, volfrac=volfrac, iters=iters, n_on=n_on, nl=nl,
-                          eps1=eps1, eps2=eps2, basis_guess=guess)
+                          eps1=eps1, eps2=eps2, basis_guess=guess, filter_alpha=filter_alpha,
+                          filter_lp=filter_lp)
     an = loop.Analysis(s, fixed, q)
     bg = mgar.MGAR_GUESS_PREVIOUS if guess == "previous" else mgar.MGAR_GUESS_ZERO
     p = mgar.default_params(nx=nx, ny=ny, nz=nz, nl=nl, eps1=eps1, eps2=eps2, n_on=n_on,
-                            volfrac=volfrac, move=0.2, precision=precision, basis_guess=bg)
+                            volfrac=volfrac, move=0.2, precision=precision, basis_guess=bg,
+                            filter_alpha=filter_alpha, filter_lp=filter_lp)
     out = []
     with mgar.Solver(p, fixed, q) as solver:
         rho = np.full(nel, volfrac)
@@ -82,3 +84,25 @@ def test_mixed_loop_compliance_within_1e6(guess):
             assert abs(o["res"] - 0.5) < 1e-3, k
             continue
         assert abs(g["compliance"] - o["compliance"]) / o["compliance"] < 1e-6, k
+
+
+@pytest.mark.parametrize("dims,nl,precision,tol", [
+    ((48, 40, 0), 3, "fp64", 1e-9), ((48, 40, 0), 3, "mixed", 1e-6),
+    ((16, 16, 12), 3, "mixed", 1e-6)])
+def test_loop_continuous_filter(dims, nl, precision, tol):
+    """Continuous filter radius (Eq. 22-23): r^(0) = 0.2 L shrinking to
+    r_min = 1.5 over 5 cycles; the GPU rebuilds its filter tables each cycle
+    and follows the oracle's loop (MGAR from cycle 4 on)."""
+    prec = mgar.MGAR_FP64 if precision == "fp64" else mgar.MGAR_MIXED
+    nx, ny, nz = dims
+    out = run_stepwise(nx, ny, nz, nl=nl, iters=8, n_on=4, precision=prec, guess="zero",
+                       eps2=1e-12 if precision == "fp64" else 1e-10, volfrac=0.4,
+                       filter_alpha=0.2, filter_lp=5)
+    assert len(out) >= 4
+    for k, g, o, rg, ro, tg, to in out:
+        if g["used_mgcg"] != o["mgcg"]:
+            assert abs(o["res"] - 0.5) < 1e-3, k
+            continue
+        assert abs(g["compliance"] - o["compliance"]) / o["compliance"] < tol, k
+        if precision == "fp64":
+            assert np.max(np.abs(rg - ro)) < 1e-8, k
