@@ -77,7 +77,7 @@ typedef struct mgar_params {
    * r^(0) = filter_alpha * filter_L, eta = exp((ln rmin - ln r^(0)) /
    * filter_lp).  Off when filter_alpha <= 0 (the filter keeps rmin); with
    * filter_L <= 0 the longest side in elements is used.  The largest radius
-   * must leave at most 2048 filter offsets (about r <= 25 in 2D, 7.8 in 3D),
+   * must leave at most 3072 filter offsets (about r <= 31 in 2D, 9 in 3D),
    * else mgar_create fails with MGAR_ERR_ARG. */
   double filter_alpha;
   int32_t filter_lp;

@@ -41,7 +41,7 @@ constexpr int kMaxLevels = 14;
 constexpr int kThreads = 256;
 constexpr int kMinPartialBlocks = 8192;
 constexpr int64_t kBottomNodes = 8192;  // largest level handled by the V-cycle's cluster launch
-constexpr int kMaxFilterOffsets = 2048;
+constexpr int kMaxFilterOffsets = 3072;
 constexpr int kMaxM = 8;
 constexpr int kOcCand = 31;      // multisection candidates per pass (5 bits)
 constexpr int kOcPasses = 6;     // FP32 passes at most: ln-bracket 92 -> 9e-8

@@ -295,7 +295,9 @@ def params_for(workload, precision=MGAR_FP64, basis_guess=MGAR_GUESS_PREVIOUS, *
     p = default_params(nx=w.nx, ny=w.ny, nz=w.nz, k0=w.k0, kmin=w.kmin, penal=w.penal,
                        rmin=w.rmin, nl=w.nl, m=w.m, eps1=w.eps1, eps2=w.eps2, cg_max=w.cg_max,
                        precision=precision, basis_guess=basis_guess, n_on=w.n_on,
-                       volfrac=w.volfrac, move=w.move)
+                       volfrac=w.volfrac, move=w.move,
+                       filter_alpha=getattr(w, "filter_alpha", 0.0),
+                       filter_lp=getattr(w, "filter_lp", 0))
     for k, v in overrides.items():
         setattr(p, k, v)
     return p

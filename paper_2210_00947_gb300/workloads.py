@@ -207,8 +207,12 @@ class Workload:
     m: int = 2
     eps1: float = 0.5
     load: float = 0.01
-    # heat source per unit volume (Section 3.2); None: the uniform nodal load
-    source: float | None = None
+    # heat source per unit volume (Section 3.2), or "quadrants" for the four
+    # sub-domain sources of Section 4.2; None: the uniform nodal load
+    source: float | str | None = None
+    # continuous filter radius (Eq. 22-23): alpha (0 = off) and lp cycles
+    filter_alpha: float = 0.0
+    filter_lp: int = 0
 
     @property
     def dim(self) -> int:
@@ -232,6 +236,9 @@ class Workload:
         return heat_sink_mask(self.nx, self.ny, self.nz)
 
     def q(self) -> np.ndarray:
+        if isinstance(self.source, str):
+            return volumetric_load(self.nx, self.ny, self.nz, quadrant_source(self.nx, self.ny),
+                                   self.fixed())
         if self.source is not None:
             return volumetric_load(self.nx, self.ny, self.nz, self.source, self.fixed())
         return nodal_load(self.fixed(), self.load)
@@ -262,7 +269,8 @@ def levels_for_direct_coarsest(nx: int, ny: int, nz: int = 0, nl_min: int = 3,
         nl += 1
 
 
-def _paper2d(name: str, n: int) -> Workload:
+def _paper2d(name: str, n: int, volfrac: float = 0.5, source=1e-4,
+             continuous: bool = False) -> Workload:
     # The 2D heat-sink models of Table 2 (Sections 3.2 and 4.1): n x n
     # elements, volume fraction 0.5, r_min 3, two basis vectors, eps1 0.5,
     # eps2 1e-6, cg_max 200, source 1e-4 per unit volume, 300 design cycles
@@ -272,9 +280,12 @@ def _paper2d(name: str, n: int) -> Workload:
     # at every MGCG call, so nl is the fewest levels >= 3 whose coarsest grid
     # holds at most 300 nodes (on Model 1, nl 4 with a 2116-node coarsest
     # grid costs 14.5 ms per MGCG design cycle, nl 6 with 169 nodes 1.8 ms).
-    return Workload(name, n, n, 0, volfrac=0.5, rho0=0.5,
+    # With continuous=True the filter radius follows Eq. 22-23 with the
+    # paper's defaults alpha = 1.4/50 and lp = 5/6 of the cycles.
+    return Workload(name, n, n, 0, volfrac=volfrac, rho0=volfrac,
                     nl=levels_for_direct_coarsest(n, n, max_nodes=COARSEST_TARGET_NODES),
-                    iters=300, eps2=1e-6, cg_max=200, rmin=3.0, source=1e-4)
+                    iters=300, eps2=1e-6, cg_max=200, rmin=3.0, source=source,
+                    filter_alpha=1.4 / 50 if continuous else 0.0, filter_lp=250 if continuous else 0)
 
 
 WORKLOADS = {
@@ -282,6 +293,14 @@ WORKLOADS = {
     "paper2d_m2": _paper2d("paper2d_m2", 720),
     "paper2d_m3": _paper2d("paper2d_m3", 1560),
     "paper2d_m4": _paper2d("paper2d_m4", 2040),
+    # the same with the continuous filter (Section 2.3 defaults)
+    "paper2d_m1c": _paper2d("paper2d_m1c", 360, continuous=True),
+    "paper2d_m2c": _paper2d("paper2d_m2c", 720, continuous=True),
+    # Section 4.2: four sub-domain sources, 480^2 and 960^2, volume 0.4 / 0.6
+    "paper2d_q480_v04": _paper2d("paper2d_q480_v04", 480, 0.4, "quadrants", True),
+    "paper2d_q480_v06": _paper2d("paper2d_q480_v06", 480, 0.6, "quadrants", True),
+    "paper2d_q960_v04": _paper2d("paper2d_q960_v04", 960, 0.4, "quadrants", True),
+    "paper2d_q960_v06": _paper2d("paper2d_q960_v06", 960, 0.6, "quadrants", True),
     "heat2d_100": Workload("heat2d_100", 100, 100, 0, volfrac=0.4, rho0=0.4, nl=4, iters=100),
     "heat2d_1024": Workload("heat2d_1024", 1024, 1024, 0, volfrac=0.4, rho0=0.4, nl=7, iters=50),
     "heat3d_128": Workload("heat3d_128", 128, 128, 128, volfrac=0.3, rho0=0.3, nl=6, iters=50),
