@@ -22,6 +22,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -53,6 +55,10 @@ def parse():
                     help="comma-separated paper-setting workloads (e.g. paper2d_m1,paper2d_m2): "
                          "MGAR against pure MGCG as in Table 2, one JSON line each")
     ap.add_argument("--nl", type=int, default=0, help="replay: number of levels (0 = workload's)")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="run this many seeded independent 2D designs concurrently and one after "
+                         "another (--cycles each, default 30); one JSON line")
+    ap.add_argument("--batch-workers", type=int, default=16)
     ap.add_argument("--replay-precisions", default="mixed,fp64")
     ap.add_argument("--replay-guesses", default="previous,zero")
     return ap.parse_args()
@@ -608,9 +614,36 @@ def run_replay(args):
                 print(json.dumps(line), flush=True)
 
 
+def run_batch(args):
+    """Independent designs (the workload module's seeded uneven 2D set): the
+    same designs once one after another and once `--batch-workers` at a
+    time, each with its own handle, stream and host thread."""
+    from paper_2210_00947_gb300 import batch, mgar
+
+    designs = batch.designs_from_workload(args.batch)
+    cycles = args.cycles or 30
+    prec = mgar.MGAR_MIXED if args.precision == "mixed" else mgar.MGAR_FP64
+    batch.run_designs(designs[:2], cycles=2, workers=2, precision=prec)  # warm-up
+    seq, t_seq = batch.run_designs(designs, cycles=cycles, workers=1, precision=prec)
+    par, t_par = batch.run_designs(designs, cycles=cycles, workers=args.batch_workers,
+                                   precision=prec)
+    same = all(np.array_equal(a[0], b[0]) for a, b in zip(seq, par))
+    total = len(designs) * cycles
+    line = {"batch": len(designs), "cycles": cycles, "precision": args.precision,
+            "dofs_total": sum((d.nx + 1) * (d.ny + 1) for d in designs),
+            "sequential_s": t_seq, "concurrent_s": t_par, "workers": args.batch_workers,
+            "design_cycles_per_s": total / t_par, "speedup": t_seq / t_par,
+            "identical_results": same,
+            "timing": "host wall clock from the start of the first run to the end of the last",
+            "data": "synthetic (seeded uneven 2D designs)"}
+    print(json.dumps(line), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.replay:
+    if a.batch:
+        run_batch(a)
+    elif a.replay:
         run_replay(a)
     elif a.impl == "reference":
         run_reference(a)

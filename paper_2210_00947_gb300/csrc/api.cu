@@ -29,9 +29,18 @@ void prof_mark(const char* site) {
   c->prof_sites[c->prof_used] = site;
   ++c->prof_used;
 }
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
-void count_launches(int64_t delta) { g_launches.fetch_add(delta, std::memory_order_relaxed); }
-int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+// The process-wide count (mgar_kernel_launches) and this thread's own, which
+// the graph captures difference: handles may run in several host threads.
+thread_local int64_t t_launches = 0;
+void count_launch() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  ++t_launches;
+}
+void count_launches(int64_t delta) {
+  g_launches.fetch_add(delta, std::memory_order_relaxed);
+  t_launches += delta;
+}
+int64_t launches_so_far() { return t_launches; }
 }  // namespace mgar
 
 namespace {
