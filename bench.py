@@ -59,6 +59,9 @@ def parse():
                     help="run this many seeded independent 2D designs concurrently and one after "
                          "another (--cycles each, default 30); one JSON line")
     ap.add_argument("--batch-workers", type=int, default=16)
+    ap.add_argument("--autograd", default=None,
+                    help="time the differentiable compliance (forward solve + adjoint gradient) "
+                         "on this workload; one JSON line")
     ap.add_argument("--replay-precisions", default="mixed,fp64")
     ap.add_argument("--replay-guesses", default="previous,zero")
     return ap.parse_args()
@@ -639,9 +642,47 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_autograd(args):
+    """Forward (filter, SIMP, MGCG from the previous temperatures) and backward
+    (adjoint sensitivity) of the compliance of a design, as a PyTorch user
+    calls it; device time with CUDA events."""
+    import torch
+
+    from paper_2210_00947_gb300 import autograd, mgar, workloads
+
+    w = workloads.WORKLOADS[args.autograd]
+    dev = torch.device("cuda", 0)
+    prec = mgar.MGAR_MIXED if args.precision == "mixed" else mgar.MGAR_FP64
+    comp = autograd.Compliance(mgar.params_for(w, precision=prec), w.fixed(), w.q())
+    rho = torch.tensor(w.density(), device=dev, requires_grad=True)
+    stream = torch.cuda.current_stream(dev)
+    times = []
+    for step in range(args.warmup + args.steps):
+        rho.grad = None
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        c = comp(rho)
+        c.backward()
+        end.record(stream)
+        end.synchronize()
+        if step >= args.warmup:
+            times.append(start.elapsed_time(end))
+        with torch.no_grad():  # a small descent step, so each solve starts warm but not converged
+            rho -= 1e-3 * rho.grad / rho.grad.abs().max()
+            rho.clamp_(1e-3, 1.0)
+    line = {"autograd": args.autograd, "dofs": w.n_nodes, "precision": args.precision,
+            "ms_forward_backward": statistics.mean(times), "steps": args.steps,
+            "compliance": c.item(), "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    comp.close()
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.batch:
+    if a.autograd:
+        run_autograd(a)
+    elif a.batch:
         run_batch(a)
     elif a.replay:
         run_replay(a)
