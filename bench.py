@@ -59,6 +59,9 @@ def parse():
                     help="run this many seeded independent 2D designs concurrently and one after "
                          "another (--cycles each, default 30); one JSON line")
     ap.add_argument("--batch-workers", type=int, default=16)
+    ap.add_argument("--postprocess", default=None,
+                    help="time the boundary post-processing (Eq. 24-27) after --cycles design "
+                         "cycles of this workload; one JSON line")
     ap.add_argument("--autograd", default=None,
                     help="time the differentiable compliance (forward solve + adjoint gradient) "
                          "on this workload; one JSON line")
@@ -678,9 +681,48 @@ def run_autograd(args):
     comp.close()
 
 
+def run_postprocess(args):
+    """A short optimisation (--cycles, default 10), then the post-processing
+    of its design, timed with CUDA events (it runs once per optimisation)."""
+    import torch
+
+    from paper_2210_00947_gb300 import mgar, workloads
+
+    w = workloads.WORKLOADS[args.postprocess]
+    dev = torch.device("cuda", 0)
+    prec = mgar.MGAR_MIXED if args.precision == "mixed" else mgar.MGAR_FP64
+    cycles = args.cycles or 10
+    solver = mgar.Solver(mgar.params_for(w, precision=prec), w.fixed(), w.q())
+    rho = torch.tensor(w.density(), device=dev)
+    T = torch.zeros(solver.n_nodes, dtype=torch.float64, device=dev)
+    for k in range(1, cycles + 1):
+        solver.step(rho, T, k)
+    solver.set_density(rho)
+    solver.solve_mgcg(T)
+    out = torch.empty_like(rho)
+    stream = torch.cuda.current_stream(dev)
+    times = []
+    for _ in range(max(args.steps, 1) + 1):
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        start.record(stream)
+        level, vol = solver.postprocess(rho, T, w.volfrac, out)
+        end.record(stream)
+        end.synchronize()
+        times.append(start.elapsed_time(end))
+    crisp = float(((out == 0) | (out == 1)).double().mean().item())
+    line = {"postprocess": args.postprocess, "elements": w.n_elems, "cycles_before": cycles,
+            "ms": statistics.mean(times[1:]), "level": level, "volume": vol,
+            "volfrac": w.volfrac, "crisp_share": crisp, "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    solver.close()
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.autograd:
+    if a.postprocess:
+        run_postprocess(a)
+    elif a.autograd:
         run_autograd(a)
     elif a.batch:
         run_batch(a)

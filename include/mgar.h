@@ -182,6 +182,22 @@ int mgar_sensitivity(mgar_t h, const double* T, double* dc, double* dv, double* 
  * rho+move, [0,1]) with lambda by bisection so that mean(F rho) = volfrac.
  *   rho: device E doubles, updated in place; dc: device E doubles.
  *   lambda, change: host (may be NULL); change = max |rho_new - rho|. */
+/* Projection-based boundary post-processing (Section 2.3, Eq. 24-27), run
+ * once after the optimisation: the element sensitivities of the design
+ * (Eq. 10, magnitude) are projected onto the nodes with the filter's weights
+ * (radius rmin); an element is solid when all its nodes exceed the level,
+ * void when all are below it, and otherwise gets the share of a 5 x 5
+ * (x 5) lattice of points over the element at which the bilinear /
+ * trilinear interpolation of the nodal values exceeds the level (Eq. 25-27);
+ * the level is bisected so that the mean density is the largest attainable
+ * at or below volfrac.
+ *   rho: device E doubles, the design (filtered inside); T: device N
+ *   doubles, its temperatures; rho_out: device E doubles (densities in
+ *   [0, 1], multiples of 1/25 or 1/125).  level, volume: host (may be NULL).
+ *   Errors: MGAR_ERR_ARG on null pointers or volfrac outside (0, 1). */
+int mgar_postprocess(mgar_t h, const double* rho, const double* T, double volfrac, double* rho_out,
+                     double* level, double* volume);
+
 int mgar_oc_update(mgar_t h, double* rho, const double* dc, double volfrac, double move,
                    double* lambda, double* change);
 

@@ -535,6 +535,16 @@ int mgar_sensitivity(mgar_t h, const double* T, double* dc, double* dv, double* 
   });
 }
 
+int mgar_postprocess(mgar_t h, const double* rho, const double* T, double volfrac, double* rho_out,
+                     double* level, double* volume) {
+  return guarded(h, [&](Ctx& c) {
+    require(rho && T && rho_out, MGAR_ERR_ARG, "postprocess: null pointer");
+    require(volfrac > 0.0 && volfrac < 1.0, MGAR_ERR_ARG, "postprocess: volfrac outside (0, 1)");
+    postprocess(c, rho, T, volfrac, rho_out, level, volume);
+    return MGAR_OK;
+  });
+}
+
 int mgar_oc_update(mgar_t h, double* rho, const double* dc, double volfrac, double move,
                    double* lambda, double* change) {
   return guarded(h, [&](Ctx& c) {

@@ -860,6 +860,8 @@ void set_density(Ctx& c, const double* rho, bool physical);
 // (mixed path), else null
 void sensitivity(Ctx& c, const double* T, double* dc, double* dv, double* compliance,
                  const float2* T_df = nullptr);
+void postprocess(Ctx& c, const double* rho, const double* T, double volfrac, double* rho_out,
+                 double* level_out, double* volume_out);
 void oc_update(Ctx& c, double* rho, const double* dc, double volfrac, double move, double* lambda,
                double* change);
 

@@ -817,4 +817,155 @@ void oc_update(Ctx& c, double* rho, const double* dc, double volfrac, double mov
   c.oc_fallbacks += fast_ok ? 0 : 1;
 }
 
+
+// ---------------------------------------------------------------------------
+// Projection-based boundary post-processing, Section 2.3, Eq. 24-27 (run once
+// after the loop).  s_e = -df/drho~_e of the final design (Eq. 10) is
+// projected onto the nodes with the filter's weights, ns_i = sum_e w_ie s_e /
+// sum_e w_ie, w_ie = max(0, r - |x_i - c_e|); an element is solid when all
+// its nodes have ns > level, void when all have ns < level, and otherwise
+// gets the share of the (S+1)^d points of a lattice over the element (the
+// original nodes included) at which the bilinear / trilinear interpolation
+// of ns exceeds the level (Eq. 25-27); the level is bisected so that the
+// mean density stays at or below the volume fraction.
+
+constexpr int kPpLattice = 4;  // S: lattice intervals per axis
+
+template <int DIM>
+__global__ void k_pp_nodal(const double* __restrict__ dcp, double* __restrict__ ns, Dims d,
+                           double r, int reach) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int)d.n) return;
+  int i, j, k;
+  coords(idx, d.fNX, d.fNXY, i, j, k);
+  double num = 0.0, den = 0.0;
+  // element (i + ox, j + oy, k + oz) has its centroid at offset o + 1/2
+  for (int ox = -reach; ox < reach; ++ox)
+    for (int oy = -reach; oy < reach; ++oy)
+      for (int oz = (DIM == 3 ? -reach : 0); oz < (DIM == 3 ? reach : 1); ++oz) {
+        const double dz = DIM == 3 ? oz + 0.5 : 0.0;
+        const double w = r - sqrt((ox + 0.5) * (ox + 0.5) + (oy + 0.5) * (oy + 0.5) + dz * dz);
+        const int ei = i + ox, ej = j + oy, ek = k + oz;
+        if (w <= 0.0 || ei < 0 || ei >= d.ex || ej < 0 || ej >= d.ey || ek < 0 || ek >= d.ez)
+          continue;
+        const int e = ei + d.ex * (ej + d.ey * ek);
+        if (!CK(e, d.ne)) continue;
+        num += w * -dcp[e];
+        den += w;
+      }
+  ns[idx] = num / den;
+}
+
+// Eq. 24 with ev of Eq. 25-27; the densities into rho (may be null) and their
+// sum into *sum
+template <int DIM>
+__global__ void k_pp_density(const double* __restrict__ ns, Dims d, double level,
+                             double* __restrict__ rho, double* partials, unsigned int* counter,
+                             double* sum) {
+  constexpr int nen = 1 << DIM, P = kPpLattice + 1;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  double v[1] = {0.0};
+  if (e < (int)d.ne) {
+    int i, j, k;
+    coords(e, d.fEX, d.fEXY, i, j, k);
+    double t[nen];
+    bool all_above = true, all_below = true;
+#pragma unroll
+    for (int a = 0; a < nen; ++a) {
+      const int nd = (i + (a & 1)) + d.NX * ((j + ((a >> 1) & 1)) + d.NY * (k + ((a >> 2) & 1)));
+      t[a] = CK(nd, d.n) ? ns[nd] : 0.0;
+      all_above = all_above && t[a] > level;
+      all_below = all_below && t[a] < level;
+    }
+    double val;
+    if (all_above) {
+      val = 1.0;
+    } else if (all_below) {
+      val = 0.0;
+    } else {
+      int count = 0, total = 0;
+      for (int pz = 0; pz < (DIM == 3 ? P : 1); ++pz)
+        for (int px = 0; px < P; ++px)
+          for (int py = 0; py < P; ++py) {
+            // local coordinates of the lattice point
+            const double xi = -1.0 + 2.0 * px / kPpLattice;
+            const double eta = -1.0 + 2.0 * py / kPpLattice;
+            const double zeta = DIM == 3 ? -1.0 + 2.0 * pz / kPpLattice : 0.0;
+            double s = 0.0;
+#pragma unroll
+            for (int a = 0; a < nen; ++a) {
+              const double lx = 2 * (a & 1) - 1, ly = 2 * ((a >> 1) & 1) - 1,
+                           lz = 2 * ((a >> 2) & 1) - 1;
+              double nval = (1.0 + xi * lx) * (1.0 + eta * ly);
+              if (DIM == 3) nval *= (1.0 + zeta * lz);
+              s += nval / nen * t[a];
+            }
+            count += s > level ? 1 : 0;
+            ++total;
+          }
+      val = (double)count / (double)total;
+    }
+    if (rho) rho[e] = val;
+    v[0] = val;
+  }
+  block_sum_finish<1>(v, partials, counter, sum);
+}
+
+__global__ void k_pp_max(const double* __restrict__ ns, int n, double* partials,
+                         unsigned int* counter, double* out) {
+  double m = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    m = fmax(m, ns[i]);
+  block_max_finish(m, partials, counter, out);
+}
+
+void postprocess(Ctx& c, const double* rho, const double* T, double volfrac, double* rho_out,
+                 double* level_out, double* volume_out) {
+  const Dims& d = c.L[0];
+  const int ne = (int)c.ne;
+  set_density(c, rho, false);
+  const double coef = c.p.penal * (c.p.k0 - c.p.kmin);
+  if (c.dim == 2)
+    k_elem_sens<2><<<blocks_for(ne), kThreads, 0, c.stream>>>(T, c.rho_phys, c.tmp_e, d, coef,
+                                                              c.p.penal);
+  else
+    k_elem_sens<3><<<blocks_for(ne), kThreads, 0, c.stream>>>(T, c.rho_phys, c.tmp_e, d, coef,
+                                                              c.p.penal);
+  MGAR_LAUNCH_CHECK();
+  const double r = c.p.rmin;
+  const int reach = (int)std::ceil(r + 0.5);
+  double* ns = c.tm;
+  if (c.dim == 2)
+    k_pp_nodal<2><<<blocks_for(c.n), kThreads, 0, c.stream>>>(c.tmp_e, ns, d, r, reach);
+  else
+    k_pp_nodal<3><<<blocks_for(c.n), kThreads, 0, c.stream>>>(c.tmp_e, ns, d, r, reach);
+  MGAR_LAUNCH_CHECK();
+  k_pp_max<<<c.grid_blocks, kThreads, 0, c.stream>>>(ns, (int)c.n, c.partials, c.counter,
+                                                      c.dsc + S_TMP);
+  MGAR_LAUNCH_CHECK();
+  fetch_scalars(c, S_TMP, 1);
+  auto volume = [&](double level, double* out) {
+    if (c.dim == 2)
+      k_pp_density<2><<<blocks_for(ne), kThreads, 0, c.stream>>>(ns, d, level, out, c.partials,
+                                                                 c.counter, c.dsc + S_TMP);
+    else
+      k_pp_density<3><<<blocks_for(ne), kThreads, 0, c.stream>>>(ns, d, level, out, c.partials,
+                                                                 c.counter, c.dsc + S_TMP);
+    MGAR_LAUNCH_CHECK();
+    fetch_scalars(c, S_TMP, 1);
+    return c.hsc[S_TMP] / (double)ne;
+  };
+  // ns >= 0: below -1 every node is above the level (volume 1), at max(ns)
+  // none is (volume 0)
+  double lo = -1.0, hi = c.hsc[S_TMP];
+  for (int step = 0; step < 200; ++step) {
+    const double mid = 0.5 * (lo + hi);
+    if (!(lo < mid && mid < hi)) break;
+    if (volume(mid, nullptr) > volfrac) lo = mid;
+    else hi = mid;
+  }
+  const double v = volume(hi, rho_out);
+  if (level_out) *level_out = hi;
+  if (volume_out) *volume_out = v;
+}
 }  // namespace mgar

@@ -37,7 +37,7 @@ ERROR_NAMES = {MGAR_ERR_ARG: "MGAR_ERR_ARG", MGAR_ERR_CUDA: "MGAR_ERR_CUDA",
 EXPORTS = ("mgar_default_params", "mgar_create", "mgar_destroy", "mgar_set_stream",
            "mgar_last_error", "mgar_filter", "mgar_set_density", "mgar_apply_K",
            "mgar_build_hierarchy", "mgar_vcycle", "mgar_solve_mgcg", "mgar_solve_mgar",
-           "mgar_sensitivity", "mgar_oc_update", "mgar_step", "mgar_sizes", "mgar_run",
+           "mgar_sensitivity", "mgar_postprocess", "mgar_oc_update", "mgar_step", "mgar_sizes", "mgar_run",
            "mgar_profile_start", "mgar_profile_stop", "mgar_profile_report",
            "mgar_kernel_launches", "mgar_sensitivity_noalloc")
 
@@ -110,6 +110,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "mgar_solve_mgar": (i32, [vp, vp, vp, dp, P(i32)]),
         "mgar_sensitivity": (i32, [vp, vp, vp, vp, dp]),
         "mgar_oc_update": (i32, [vp, vp, vp, ctypes.c_double, ctypes.c_double, dp, dp]),
+        "mgar_postprocess": (i32, [vp, vp, vp, ctypes.c_double, vp, dp, dp]),
         "mgar_step": (i32, [vp, vp, vp, i32, P(StepInfo)]),
         "mgar_sizes": (i32, [vp, P(ctypes.c_int64), P(ctypes.c_int64)]),
         "mgar_run": (i32, [vp, vp, i32, vp, P(StepInfo)]),
@@ -254,6 +255,15 @@ class Solver:
         self._check(self._lib.mgar_oc_update(self._h, _ptr(rho), _ptr(dc), float(volfrac),
                                              float(move), ctypes.byref(lam), ctypes.byref(ch)))
         return lam.value, ch.value
+
+    def postprocess(self, rho, T, volfrac, rho_out):
+        """mgar_postprocess (Eq. 24-27); returns (level, volume)."""
+        lev = ctypes.c_double()
+        vol = ctypes.c_double()
+        self._check(self._lib.mgar_postprocess(self._h, _ptr(rho), _ptr(T), float(volfrac),
+                                               _ptr(rho_out), ctypes.byref(lev),
+                                               ctypes.byref(vol)))
+        return lev.value, vol.value
 
     def run(self, rho_host, cycles, rho_out_host):
         """mgar_run: host arrays in and out (numpy arrays or pinned CPU
