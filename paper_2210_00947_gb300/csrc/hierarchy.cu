@@ -622,8 +622,8 @@ void build_hierarchy(Ctx& c) {
     if (c.dim == 2) build_levels<double, 2>(c, c.ke0, c.h64);
     else build_levels<double, 3>(c, c.ke0, c.h64);
   } else {
-    k_d2f<<<blocks_for(c.ne), kThreads, 0, s>>>(c.ke0, c.ke0_f, c.ne);
-    MGAR_LAUNCH_CHECK();
+    // the FP32 copy of k_e is already fl32(k_e) (set_density writes both)
+    MGAR_CUDA(cudaMemcpyAsync(c.ke0_f, c.ke_f, c.ne * sizeof(float), cudaMemcpyDeviceToDevice, s));
     if (c.dim == 2) build_levels<float, 2>(c, c.ke0_f, c.h32);
     else build_levels<float, 3>(c, c.ke0_f, c.h32);
   }

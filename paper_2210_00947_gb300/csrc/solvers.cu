@@ -402,9 +402,12 @@ void solve_mgar(Ctx& c, const double* T_prev, double* T, double* res, int* accep
         k_axpy_dev<<<rb, kThreads, 0, c.stream>>>(v, qj, n, c.dsc + S_GS);
         MGAR_LAUNCH_CHECK();
       }
-    dot(c, v, v, n, c.dsc + S_NORM);
-    fetch_scalars(c, S_NORM, 1);
-    const double nv = std::sqrt(c.hsc[S_NORM]);
+    // the first vector's norm is the reference just fetched
+    if (i > 0 || kept > 0) {
+      dot(c, v, v, n, c.dsc + S_NORM);
+      fetch_scalars(c, S_NORM, 1);
+    }
+    const double nv = (i > 0 || kept > 0) ? std::sqrt(c.hsc[S_NORM]) : ref;
     require(std::isfinite(nv), MGAR_ERR_NONFINITE, "non-finite MGAR basis");
     if (nv > 1e-12 * ref && nv > 0.0) {
       double* dst = c.R + (int64_t)kept * n;
