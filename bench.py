@@ -544,6 +544,8 @@ PAPER_TABLE2 = {
     "paper2d_q960_v06": dict(mgcg_evaluations=109, efficiency_improvement=0.4368,
                              relative_difference=0.000015, cg_iters=7.47, cg_iters_mgcg=7.24),
 }
+# Section 4.3 (3D quarter model): efficiency improvement and MGAR objective
+PAPER_TABLE2["paper3d_quarter"] = dict(efficiency_improvement=0.5125, objective_mgar=5792.03)
 PAPER_TABLE2["paper2d_m1c"] = PAPER_TABLE2["paper2d_m1"]
 PAPER_TABLE2["paper2d_m2c"] = PAPER_TABLE2["paper2d_m2"]
 

@@ -116,6 +116,17 @@ def edge_patch_mask(nx: int, ny: int, edge: int, offset: float, frac: float = 0.
     return mask.reshape(-1)
 
 
+def quarter_sink_mask(nx: int, ny: int, nz: int, half_side: int) -> np.ndarray:
+    """3D quarter model of a cube with a centred square sink on its x = 0
+    face (Section 4.3): the quarter keeps y, z in [0, L/2] with the symmetry
+    planes y = ny, z = nz (adiabatic), so the sink is the corner square
+    ny - half_side <= j <= ny, nz - half_side <= k <= nz of the x = 0 face."""
+    NX, NY, NZ = node_dims(nx, ny, nz)
+    mask = np.zeros((NZ, NY, NX), dtype=np.uint8)
+    mask[nz - half_side:, ny - half_side:, 0] = 1
+    return mask.reshape(-1)
+
+
 def nodal_load(fixed: np.ndarray, value: float = 0.01) -> np.ndarray:
     """Uniform nodal heat load `value` on every free node, 0 on sink nodes."""
     q = np.full(fixed.shape[0], value, dtype=np.float64)
@@ -213,6 +224,10 @@ class Workload:
     # continuous filter radius (Eq. 22-23): alpha (0 = off) and lp cycles
     filter_alpha: float = 0.0
     filter_lp: int = 0
+    # sink: "centre" (heat_sink_mask) or "quarter" (quarter_sink_mask with
+    # half side sink_half)
+    sink: str = "centre"
+    sink_half: int = 0
 
     @property
     def dim(self) -> int:
@@ -233,6 +248,8 @@ class Workload:
         return int(math.floor(2.0 * self.iters / 15.0 + 0.5))
 
     def fixed(self) -> np.ndarray:
+        if self.sink == "quarter":
+            return quarter_sink_mask(self.nx, self.ny, self.nz, self.sink_half)
         return heat_sink_mask(self.nx, self.ny, self.nz)
 
     def q(self) -> np.ndarray:
@@ -301,6 +318,14 @@ WORKLOADS = {
     "paper2d_q480_v06": _paper2d("paper2d_q480_v06", 480, 0.6, "quadrants", True),
     "paper2d_q960_v04": _paper2d("paper2d_q960_v04", 960, 0.4, "quadrants", True),
     "paper2d_q960_v06": _paper2d("paper2d_q960_v06", 960, 0.6, "quadrants", True),
+    # Section 4.3: the 224^3 cube as its quarter 224 x 112 x 112 (2,873,025
+    # nodes), sink of side L/8 centred on the x = 0 face, volume 0.3, r_min 3
+    # with the continuous filter (L = 224), cg_max 50, source 1e-4
+    "paper3d_quarter": Workload("paper3d_quarter", 224, 112, 112, volfrac=0.3, rho0=0.3,
+                                nl=levels_for_direct_coarsest(224, 112, 112, max_nodes=300),
+                                iters=300, eps2=1e-6, cg_max=50, rmin=3.0, source=1e-4,
+                                filter_alpha=1.4 / 50, filter_lp=250, sink="quarter",
+                                sink_half=14),
     "heat2d_100": Workload("heat2d_100", 100, 100, 0, volfrac=0.4, rho0=0.4, nl=4, iters=100),
     "heat2d_1024": Workload("heat2d_1024", 1024, 1024, 0, volfrac=0.4, rho0=0.4, nl=7, iters=50),
     "heat3d_128": Workload("heat3d_128", 128, 128, 128, volfrac=0.3, rho0=0.3, nl=6, iters=50),

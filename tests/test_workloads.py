@@ -51,3 +51,20 @@ def test_paper_model_load_and_sink():
     np.testing.assert_allclose(q[fixed == 0], full[fixed == 0])
     # interior node: four elements x 1e-4 / 4
     assert abs(full[NX * 100 + 100] - 1e-4) < 1e-18
+
+
+def test_quarter_model_matches_section_4_3():
+    w = workloads.WORKLOADS["paper3d_quarter"]
+    assert w.n_nodes == 2873025  # the DOF count the paper prints
+    fixed = w.fixed()
+    NX, NY, NZ = w.nx + 1, w.ny + 1, w.nz + 1
+    f = fixed.reshape(NZ, NY, NX)
+    # a 14 x 14-element square (15 x 15 nodes) in the corner of the x = 0 face
+    # at the symmetry planes: a quarter of the L/8 = 28-element sink
+    assert f[:, :, 1:].sum() == 0
+    assert f[98:, 98:, 0].all() and f[:, :, 0].sum() == 15 * 15
+    # source 1e-4 per unit volume: the whole load less the sink nodes' shares
+    q = w.q()
+    full = workloads.volumetric_load(w.nx, w.ny, w.nz, 1e-4, np.zeros_like(fixed))
+    assert abs(full.sum() - 1e-4 * 224 * 112 * 112) < 1e-9
+    assert abs(q.sum() - (full.sum() - full[fixed != 0].sum())) < 1e-9
