@@ -511,13 +511,33 @@ static int solve_mgcg_df3(Ctx& c, double* T, int* iters, double* relres) {
 // Convergence is decided on the recomputed residual, so the reported
 // ||r|| / ||q|| is a df64 residual of the returned x.
 
-// alpha = rz / pAp; xc += alpha p; r -= alpha A p; ||r||^2
+// After an iteration: count it, flip the parity, and decide whether a
+// reliable update is due: ||r|| <= eps2 ||q||, ||r|| <= delta ||r||_last
+// update, cg_max iterations, or a non-finite ||r||.  Inside the graph the
+// decision sets the IF node of the update (ru); the flag is also left in
+// S_FLAG.  Run by one thread after ||r||^2 is in S_RR.
+__device__ void ru_decide(double* dsc, double qnorm, double eps2, double delta, int cg_max,
+                          cudaGraphConditionalHandle ru, int set) {
+  const double rn = sqrt(dsc[S_RR]);
+  const int it = (int)dsc[S_CGIT] + 1;
+  dsc[S_CGIT] = (double)it;
+  dsc[S_CGPAR] = (double)(((int)dsc[S_CGPAR]) ^ 1);
+  dsc[S_CGFIRST] = 0.0;
+  const bool upd = !(isfinite(rn) && rn > eps2 * qnorm && rn > delta * dsc[S_RMAX] && it < cg_max);
+  dsc[S_FLAG] = upd ? 1.0 : 0.0;
+  if (set) cudaGraphSetConditional(ru, upd ? 1u : 0u);
+}
+
+// alpha = rz / pAp; xc += alpha p; r -= alpha A p; ||r||^2 into dsc[S_RR],
+// then the update decision (ru_decide) in the last block
 __global__ void k_cg_xr32(float* __restrict__ xc, float* __restrict__ r, const float* __restrict__ p,
                           const float* __restrict__ p_alt, const double* parity,
                           const float* __restrict__ Ap, int n, const double* __restrict__ rz,
                           const double* __restrict__ pap, double* partials, unsigned int* counter,
-                          double* out) {
+                          double* dsc, double qnorm, double eps2, double delta, int cg_max,
+                          cudaGraphConditionalHandle ru, int set) {
   pdl_wait();
+  // every block reads the parity before the last one flips it
   if (parity && (((int)*parity) & 1)) p = p_alt;
   const float alpha = block_div_f(rz, pap);
   float acc = 0.f;
@@ -553,7 +573,13 @@ __global__ void k_cg_xr32(float* __restrict__ xc, float* __restrict__ r, const f
     r[i] = ri;
     acc = fmaf(ri, ri, acc);
   }
-  block_sum_finish_df(df{acc, 0.f}, partials, counter, out);
+  double t;
+  if (block_sum_last_df(df{acc, 0.f}, partials, counter, t, threadIdx.x, blockDim.x, blockIdx.x,
+                        gridDim.x) &&
+      threadIdx.x == 0) {
+    dsc[S_RR] = t;
+    ru_decide(dsc, qnorm, eps2, delta, cg_max, ru, set);
+  }
 }
 
 // iteration count, buffer parity, first-direction flag and the reference
@@ -564,23 +590,6 @@ __global__ void k_ru_start(double* dsc) {
   dsc[S_CGFIRST] = 1.0;
   dsc[S_RMAX] = sqrt(dsc[S_RR]);
   dsc[S_RUCOUNT] = 0.0;
-}
-
-// after an iteration: count it, flip the parity, and decide whether a
-// reliable update is due: ||r|| <= eps2 ||q||, ||r|| <= delta ||r||_last
-// update, cg_max iterations, or a non-finite ||r||.  Inside the graph the
-// decision sets the IF node of the update (ru) and, when no update follows,
-// the WHILE loop goes on; the flag is also left in S_FLAG.
-__global__ void k_ru_check(double* dsc, double qnorm, double eps2, double delta, int cg_max,
-                           cudaGraphConditionalHandle ru, int set) {
-  const double rn = sqrt(dsc[S_RR]);
-  const int it = (int)dsc[S_CGIT] + 1;
-  dsc[S_CGIT] = (double)it;
-  dsc[S_CGPAR] = (double)(((int)dsc[S_CGPAR]) ^ 1);
-  dsc[S_CGFIRST] = 0.0;
-  const bool upd = !(isfinite(rn) && rn > eps2 * qnorm && rn > delta * dsc[S_RMAX] && it < cg_max);
-  dsc[S_FLAG] = upd ? 1.0 : 0.0;
-  if (set) cudaGraphSetConditional(ru, upd ? 1u : 0u);
 }
 
 // x += xc in df64, xc = 0
@@ -630,10 +639,8 @@ static void ru_iteration(Ctx& c, cudaGraphConditionalHandle ru, bool set) {
   launch_pdl(c.stream, c.use_pdl, k_cg_xr32, dim3(c.grid_blocks), dim3(kThreads), c.xc32, c.b32,
              (const float*)c.p32b, (const float*)c.p32, (const double*)(c.dsc + S_CGPAR),
              (const float*)c.y32, n, (const double*)(c.dsc + S_RZ0),
-             (const double*)(c.dsc + S_PAP), c.partials, c.counter, c.dsc + S_RR);
-  MGAR_LAUNCH_CHECK();
-  k_ru_check<<<1, 1, 0, c.stream>>>(c.dsc, c.qnorm, c.p.eps2, c.ru_delta, c.p.cg_max, ru,
-                                    set ? 1 : 0);
+             (const double*)(c.dsc + S_PAP), c.partials, c.counter, c.dsc, c.qnorm, c.p.eps2,
+             c.ru_delta, c.p.cg_max, ru, set ? 1 : 0);
   MGAR_LAUNCH_CHECK();
 }
 
