@@ -1,0 +1,115 @@
+"""The benchmark's workload at full size (128^3 H8, 2,146,689 nodes, mixed
+path, the parameters the benchmark runs with): one MGCG design cycle from the
+uniform start, checked against the oracle on the whole grid where the
+oracle's vectorised operator reaches it, and on sampled elements elsewhere.
+
+Uniform densities filter to themselves (the filter preserves constants), so
+the oracle's operator at the start needs no filter matrix of the full grid.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import design, fem  # noqa: E402
+from paper_2210_00947_gb300 import mgar, workloads  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def cycle1():
+    w = workloads.WORKLOADS["heat3d_128"]
+    fixed, q = w.fixed(), w.q()
+    p = mgar.params_for(w, precision=mgar.MGAR_MIXED)
+    s = mgar.Solver(p, fixed, q)
+    rho0 = w.density()
+    rho = torch.tensor(rho0, device=DEV)
+    T = torch.zeros(s.n_nodes, dtype=torch.float64, device=DEV)
+    info = s.step(rho, T, 1)
+    dc = torch.empty_like(rho)
+    s.set_density(torch.tensor(rho0, device=DEV))
+    comp = s.sensitivity(T, dc)
+    dv = torch.empty_like(rho)
+    s.filter(torch.full_like(rho, 1.0 / w.n_elems), dv, transpose=True)
+    frho = torch.empty_like(rho)
+    s.filter(rho, frho)
+    out = dict(w=w, fixed=fixed, q=q, p=p, rho0=rho0, info=info, comp=comp,
+               T=T.cpu().numpy(), rho=rho.cpu().numpy(), dc=dc.cpu().numpy(),
+               dv=dv.cpu().numpy(), frho=frho.cpu().numpy())
+    s.close()
+    return out
+
+
+def test_fullsize_true_residual_and_compliance(cycle1):
+    c = cycle1
+    w = c["w"]
+    g = fem.Grid(w.nx, w.ny, w.nz)
+    kval = fem.simp(np.full(g.n_elems, 0.3), w.k0, w.kmin, w.penal)
+    r = c["q"] - fem.apply_structured(g, kval, c["fixed"], c["T"])
+    assert c["info"]["used_mgcg"]
+    assert np.linalg.norm(r) / np.linalg.norm(c["q"]) < 10 * w.eps2
+    f = design.compliance(c["q"], c["T"])
+    assert abs(c["info"]["compliance"] - f) / f < 1e-12
+    assert abs(c["comp"] - f) / f < 1e-12
+
+
+def test_fullsize_sensitivities_on_sampled_elements(cycle1):
+    """dc_e = sum over the filter neighbourhood of e of w_ej / Hs_j times
+    -p (k0 - kmin) rho~_j^(p-1) t_j^T k0 t_j (Eq. 9-11), element by element
+    with the oracle's element matrix."""
+    c = cycle1
+    w = c["w"]
+    g = fem.Grid(w.nx, w.ny, w.nz)
+    ke = fem.element_conductivity(3)
+    nodes = g.element_nodes()
+    rmin = c["p"].rmin
+    reach = int(np.ceil(rmin))
+    rng = np.random.default_rng(7)
+    ex, ey, ez = w.nx, w.ny, w.nz
+    sample = np.concatenate([rng.integers(0, g.n_elems, 300),
+                             [0, ex - 1, ex * ey - 1, g.n_elems - 1]])
+
+    def coords(e):
+        return e % ex, (e // ex) % ey, e // (ex * ey)
+
+    def neighbours(e):
+        i, j, k = coords(e)
+        for dz in range(-reach, reach + 1):
+            for dy in range(-reach, reach + 1):
+                for dx in range(-reach, reach + 1):
+                    wt = rmin - np.sqrt(dx * dx + dy * dy + dz * dz)
+                    ii, jj, kk = i + dx, j + dy, k + dz
+                    if wt > 0 and 0 <= ii < ex and 0 <= jj < ey and 0 <= kk < ez:
+                        yield ii + ex * (jj + ey * kk), wt
+
+    # the mixed path works in double-float pairs (2^-46 relative per
+    # operation): rounding t to a pair moves each difference of the element
+    # energy by up to 2^-47 |t|, the bound of the mixed parity test
+    eps_df = 2.0 ** -46
+    rho_phys = 0.3
+    coef = w.penal * (w.k0 - w.kmin) * rho_phys ** (w.penal - 1)
+    for e in sample:
+        acc, bound = 0.0, 0.0
+        for jdx, wt in neighbours(int(e)):
+            hs = sum(v for _, v in neighbours(jdx))
+            te = c["T"][nodes[jdx]]
+            acc += wt / hs * (-coef * te @ ke @ te)
+            bound += wt / hs * 16 * eps_df * coef * (te @ te)
+        assert abs(c["dc"][e] - acc) <= 10 * bound + 1e-12 * abs(acc), e
+
+
+def test_fullsize_oc_keeps_the_volume_and_the_update_rule(cycle1):
+    """After the OC update: the filtered design has the volume fraction, and
+    each sampled element follows the update rule with the returned lambda."""
+    c = cycle1
+    w = c["w"]
+    assert abs(c["frho"].mean() - w.volfrac) < 1e-10
+    lam = c["info"]["lam"]
+    rng = np.random.default_rng(8)
+    for e in rng.integers(0, w.n_elems, 500):
+        r0 = c["rho0"][e]
+        cand = r0 * np.sqrt(max(-c["dc"][e], 0.0) / (lam * c["dv"][e]))
+        expect = min(max(cand, max(0.0, r0 - w.move)), min(1.0, r0 + w.move))
+        assert abs(c["rho"][e] - expect) <= 1e-9, e
