@@ -119,13 +119,19 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ distributed
-def dist_setup(args):
+def dist_setup(args=None, backend=None):
+    """Ranks of a torchrun launch (one process per GPU; replicas, no
+    collective on the data path): NCCL between GPUs, gloo without CUDA."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
+        import torch
         import torch.distributed as dist
-        dist.init_process_group("nccl")
+        if backend is None:
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if not dist.is_initialized():
+            dist.init_process_group(backend)
     return world, rank, local
 
 
@@ -140,9 +146,15 @@ def max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def shard(items, rank, world):
+    """Independent problems over ranks: item i goes to rank i mod world."""
+    return list(items)[rank::world]
 
 
 # ------------------------------------------------------------- roofline
@@ -628,17 +640,24 @@ def run_batch(args):
     time, each with its own handle, stream and host thread."""
     from paper_2210_00947_gb300 import batch, mgar
 
-    designs = batch.designs_from_workload(args.batch)
+    world, rank, local = dist_setup(args)
+    designs = shard(batch.designs_from_workload(args.batch), rank, world)
     cycles = args.cycles or 30
     prec = mgar.MGAR_MIXED if args.precision == "mixed" else mgar.MGAR_FP64
-    batch.run_designs(designs[:2], cycles=2, workers=2, precision=prec)  # warm-up
-    seq, t_seq = batch.run_designs(designs, cycles=cycles, workers=1, precision=prec)
+    batch.run_designs(designs[:2], cycles=2, workers=2, precision=prec, device=local)  # warm-up
+    seq, t_seq = batch.run_designs(designs, cycles=cycles, workers=1, precision=prec,
+                                   device=local)
     par, t_par = batch.run_designs(designs, cycles=cycles, workers=args.batch_workers,
-                                   precision=prec)
+                                   precision=prec, device=local)
     same = all(np.array_equal(a[0], b[0]) for a, b in zip(seq, par))
-    total = len(designs) * cycles
-    line = {"batch": len(designs), "cycles": cycles, "precision": args.precision,
-            "dofs_total": sum((d.nx + 1) * (d.ny + 1) for d in designs),
+    t_seq = max_over_ranks(t_seq, world)
+    t_par = max_over_ranks(t_par, world)
+    total = args.batch * cycles
+    if rank != 0:
+        return
+    line = {"batch": args.batch, "n_gpus": world, "cycles": cycles, "precision": args.precision,
+            "dofs_total": sum((d.nx + 1) * (d.ny + 1)
+                              for d in batch.designs_from_workload(args.batch)),
             "sequential_s": t_seq, "concurrent_s": t_par, "workers": args.batch_workers,
             "design_cycles_per_s": total / t_par, "speedup": t_seq / t_par,
             "identical_results": same,

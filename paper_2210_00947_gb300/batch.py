@@ -57,11 +57,12 @@ def designs_from_workload(count: int = 64, seed: int = 2210) -> list[Design]:
 
 
 def run_designs(designs: list[Design], cycles: int, workers: int = 16,
-                precision: int = mgar.MGAR_MIXED, **overrides):
+                precision: int = mgar.MGAR_MIXED, device: int = 0, **overrides):
     """Optimise every design for `cycles` design cycles, `workers` at a time
-    (workers = 1: one after another).  Returns, per design, the final
-    densities and the per-cycle reports, and the seconds the runs took
-    (after every handle has been created, before any is destroyed)."""
+    (workers = 1: one after another) on CUDA device `device`.  Returns, per
+    design, the final densities and the per-cycle reports, and the seconds
+    the runs took (after every handle has been created, before any is
+    destroyed)."""
     import time
 
     import torch
@@ -80,7 +81,7 @@ def run_designs(designs: list[Design], cycles: int, workers: int = 16,
     def worker(jobs):
         built = []
         try:
-            torch.cuda.set_device(0)
+            torch.cuda.set_device(device)
             stream = torch.cuda.Stream()
             for i in jobs:
                 d = designs[i]
