@@ -18,11 +18,13 @@
 // Latency: the global loads of plane k+2 (and element layer k+1) are issued
 // into registers before the block computes plane k, and are turned into the
 // operand and stored to shared memory one step later, so each step overlaps
-// its memory round trip with the previous step's arithmetic.  Four plane
-// slots and three layer slots let one barrier per step suffice.  Each thread
-// loads its own node; the one-node ring around the tile is loaded by a few
-// warps, so no thread divides to find its halo cell.  The z extent is split
-// evenly into as many runs as fill the GPU once.
+// its memory round trip with the previous step's arithmetic.  A step reads
+// one plane and one layer of the tile (the rows are split by element layer
+// and the lower layer's share, with plane k's in-plane neighbours, is carried
+// in registers), and four slots of each let one barrier per step suffice.
+// Each thread loads its own node; the one-node ring around the tile is
+// loaded by a few warps, so no thread divides to find its halo cell.  The z
+// extent is split evenly into as many runs as fill the GPU once.
 #include "common.cuh"
 #include "tile3d.cuh"
 #include "df64.cuh"
@@ -178,6 +180,51 @@ struct ElemFetch {
   __device__ __forceinline__ Real get() const { return on ? v : Real(0); }
 };
 
+// The eight in-plane neighbours of node (tx, ty) of a plane tile: the four
+// diagonal ones (-x-y, +x-y, -x+y, +x+y), then -x, +x, -y, +y.
+template <typename Real, int TX, int TY>
+__device__ __forceinline__ void plane_ring8(const Real (&Xp)[TY + 2][TX + 2], int tx, int ty,
+                                            Real (&h)[8]) {
+  const int cx = tx + 1, cy = ty + 1;
+  h[0] = Xp[cy - 1][cx - 1];
+  h[1] = Xp[cy - 1][cx + 1];
+  h[2] = Xp[cy + 1][cx - 1];
+  h[3] = Xp[cy + 1][cx + 1];
+  h[4] = Xp[cy][cx - 1];
+  h[5] = Xp[cy][cx + 1];
+  h[6] = Xp[cy - 1][cx];
+  h[7] = Xp[cy + 1][cx];
+}
+
+// The four elements e_q of one layer around a node column, q = (qy, qx) for
+// the element at (i - 1 + qx, j - 1 + qy), give the H8 rows (times 12) of the
+// column's nodes below (plane lo) and above (plane hi) the layer:
+//   up   = 4 S x_lo - C - E(hi),   down = 4 S x_hi - C - E(lo),
+// with S = sum_q e_q, C = sum_q e_q (x_lo + x_hi at the in-plane diagonal
+// neighbour q) and E(p) = sum over the four in-plane edge neighbours of plane
+// p of the two elements sharing that edge times its value.  Row (i,j,k) is
+// up(layer k) + down(layer k-1).  nb holds plane lo's neighbours on entry
+// and plane hi's on return.
+template <typename Real, int TX, int TY>
+__device__ __forceinline__ void layer_rows(const Real (&Kl)[TY + 1][TX + 1],
+                                           const Real (&Xhi)[TY + 2][TX + 2], int tx, int ty,
+                                           Real (&nb)[8], Real x_lo, Real x_hi, Real& up,
+                                           Real& down) {
+  const Real e00 = Kl[ty][tx], e01 = Kl[ty][tx + 1], e10 = Kl[ty + 1][tx], e11 = Kl[ty + 1][tx + 1];
+  Real h[8];
+  plane_ring8<Real, TX, TY>(Xhi, tx, ty, h);
+  const Real ew = e00 + e10, ee = e01 + e11, es = e00 + e01, en = e10 + e11;
+  const Real s4 = Real(4) * (es + en);
+  const Real cc = e00 * (nb[0] + h[0]) + e01 * (nb[1] + h[1]) + e10 * (nb[2] + h[2]) +
+                  e11 * (nb[3] + h[3]);
+  const Real elo = ew * nb[4] + ee * nb[5] + es * nb[6] + en * nb[7];
+  const Real ehi = ew * h[4] + ee * h[5] + es * h[6] + en * h[7];
+  up = s4 * x_lo - cc - ehi;
+  down = s4 * x_hi - cc - elo;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) nb[q] = h[q];
+}
+
 // Plane slots are relative to the block's first plane: plane p lives in slot
 // (p - kb + 1) & 3, and so does element layer p.  The z loop is unrolled by
 // four, so every slot index is a compile-time constant.
@@ -236,7 +283,7 @@ __global__ void __launch_bounds__(T::NTB, f3d_minb(MODE, T::NT)) k_fine3d(FineAr
   Real ownb = Real(0), ownd = Real(0);
   // centre values per slot: unmasked operand, b, D^-1, fixed flag (and r
   // for the fused r . x')
-  Real cv[4], cb[4], cd[4];
+  Real cv[4], cb[4], cd[4], mv[4];
   bool cf[4];
   const bool rdot = (MODE == POST || MODE == SWEEP || MODE == DIR) && a.dout != nullptr;
   df dacc{0.f, 0.f};
@@ -259,7 +306,8 @@ __global__ void __launch_bounds__(T::NTB, f3d_minb(MODE, T::NT)) k_fine3d(FineAr
 
 #define F3D_FINISH(S)                                                  \
   {                                                                    \
-    if (real) X[S][ty + 1][tx + 1] = own.masked(om, ocol.hxy);         \
+    mv[S] = own.masked(om, ocol.hxy);                                  \
+    if (real) X[S][ty + 1][tx + 1] = mv[S];                            \
     cv[S] = own.value(om, ocol.hxy);                                   \
     cb[S] = MODE == PRE ? own.v0 : ownb;                               \
     cd[S] = ownd;                                                      \
@@ -283,11 +331,24 @@ __global__ void __launch_bounds__(T::NTB, f3d_minb(MODE, T::NT)) k_fine3d(FineAr
   issue_plane(kb + 1);
   issue_layer(kb);
 
-  // one step for plane k in slot S1 = (S + 1) & 3 (planes k-1, k, k+1 in
-  // slots S, S1, S2; layers k-1, k in slots S, S1)
+  // Row (i,j,k) of the operator is split by element layer: the layer between
+  // planes k and k+1 gives its "up" part and the next row's "down" part
+  // (layer_rows).  The down part and plane k's in-plane neighbours come from
+  // the step before, so a step reads one layer and one plane of the tile.
+  // Prologue: planes kb-1 and kb and layer kb-1 are in place.
+  __syncthreads();
+  Real nb[8], dk = Real(0);
+  if (mine) {
+    Real up;
+    plane_ring8<Real, TX, TY>(X[0], tx, ty, nb);
+    layer_rows<Real, TX, TY>(K[0], X[1], tx, ty, nb, mv[0], mv[1], up, dk);
+  }
+
+  // one step for plane k in slot S1 = (S + 1) & 3 (plane k+1 in slot S2,
+  // layer k in slot S1)
 #define F3D_STEP(S)                                                                        \
   {                                                                                        \
-    constexpr int S0 = (S) & 3, S1 = ((S) + 1) & 3, S2 = ((S) + 2) & 3;                    \
+    constexpr int S1 = ((S) + 1) & 3, S2 = ((S) + 2) & 3;                                  \
     const int k = kk + (S);                                                                \
     if (k >= kend) break;                                                                  \
     F3D_FINISH(S2);                                                                        \
@@ -299,33 +360,10 @@ __global__ void __launch_bounds__(T::NTB, f3d_minb(MODE, T::NT)) k_fine3d(FineAr
       const int idx = i + a.NX * (j + a.NY * k);                                           \
       /* r for the fused r . x' (its load overlaps the stencil) */                         \
       const float2 rv = (rdot && a.rdot) ? a.rdot[idx] : make_float2(0.f, 0.f);           \
-      const Real k000 = K[S0][ty][tx], k001 = K[S0][ty][tx + 1], k010 = K[S0][ty + 1][tx], \
-                 k011 = K[S0][ty + 1][tx + 1];                                             \
-      const Real k100 = K[S1][ty][tx], k101 = K[S1][ty][tx + 1], k110 = K[S1][ty + 1][tx], \
-                 k111 = K[S1][ty + 1][tx + 1];                                             \
-      const int cx = tx + 1, cy = ty + 1;                                                  \
-      const Real ksum = ((k000 + k001) + (k010 + k011)) + ((k100 + k101) + (k110 + k111)); \
-      Real acc = Real(4) * ksum * X[S1][cy][cx];                                           \
-      acc -= (k000 + k100) * X[S1][cy - 1][cx - 1];                                        \
-      acc -= (k001 + k101) * X[S1][cy - 1][cx + 1];                                        \
-      acc -= (k010 + k110) * X[S1][cy + 1][cx - 1];                                        \
-      acc -= (k011 + k111) * X[S1][cy + 1][cx + 1];                                        \
-      acc -= (k000 + k010) * X[S0][cy][cx - 1];                                            \
-      acc -= (k001 + k011) * X[S0][cy][cx + 1];                                            \
-      acc -= (k100 + k110) * X[S2][cy][cx - 1];                                            \
-      acc -= (k101 + k111) * X[S2][cy][cx + 1];                                            \
-      acc -= (k000 + k001) * X[S0][cy - 1][cx];                                            \
-      acc -= (k010 + k011) * X[S0][cy + 1][cx];                                            \
-      acc -= (k100 + k101) * X[S2][cy - 1][cx];                                            \
-      acc -= (k110 + k111) * X[S2][cy + 1][cx];                                            \
-      acc -= k000 * X[S0][cy - 1][cx - 1];                                                 \
-      acc -= k001 * X[S0][cy - 1][cx + 1];                                                 \
-      acc -= k010 * X[S0][cy + 1][cx - 1];                                                 \
-      acc -= k011 * X[S0][cy + 1][cx + 1];                                                 \
-      acc -= k100 * X[S2][cy - 1][cx - 1];                                                 \
-      acc -= k101 * X[S2][cy - 1][cx + 1];                                                 \
-      acc -= k110 * X[S2][cy + 1][cx - 1];                                                 \
-      acc -= k111 * X[S2][cy + 1][cx + 1];                                                 \
+      Real up, down;                                                                       \
+      layer_rows<Real, TX, TY>(K[S1], X[S2], tx, ty, nb, mv[S1], mv[S2], up, down);        \
+      const Real acc = up + dk;                                                            \
+      dk = down;                                                                           \
       const Real xi = cv[S1]; /* a fixed row is the identity */                            \
       const Real ax = cf[S1] ? xi : acc * Real(1.0 / 12.0);                                \
       const Real bi = cb[S1];                                                              \
