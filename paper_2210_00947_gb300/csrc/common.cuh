@@ -225,6 +225,7 @@ struct Ctx {
   int f3d_gz[5] = {};     // z runs of the tiled finest-level kernels [mode]
   int df3d_gz[3] = {};    // z runs of the tiled df64 operator kernels [mode]
   bool df3d_tile = false; // their tile: 32 x 8, or 43 x 11 when that leaves fewer lanes idle
+  bool f3d_tile = false;  // FP32 finest-level tile: 32 x 8, or 43 x 5 when that leaves fewer lanes idle
   bool bottom_ok = false; // the V-cycle's bottom levels run as one cluster launch
   int bottom_cluster = 8; // CTAs in that cluster
   int64_t bottom_nodes = kBottomNodes;  // largest level it takes

@@ -417,36 +417,49 @@ int runs_for(const Dims& d, int sms) {
   per_sm = std::max(per_sm, 1);
   const int64_t cols = (int64_t)((d.NX + T::TX - 1) / T::TX) * ((d.NY + T::TY - 1) / T::TY);
   const int64_t want = (int64_t)per_sm * sms;
-  const int64_t gz = std::max<int64_t>(1, (want + cols / 2) / cols);
+  // at most one wave: a few blocks past it would run as a second wave
+  const int64_t gz = std::max<int64_t>(1, want / cols);
   return (int)std::min<int64_t>(gz, d.NZ);
 }
 
 }  // namespace f3d
 
-// The finest-level V-cycle kernels keep the 32 x 8 tile: a wider tile has
-// fewer idle lanes on 129-node planes but, at one wave, a longer chain of
-// plane steps per block, which costs more in these latency-bound passes
-// (measured: pre 23.6 vs 25.5 us, post 37 vs 47 us on 129^3).
+// The tile: 32 x 8, or 43 x 5 where that leaves fewer lanes idle (129-node
+// planes: 95 % of the lanes busy instead of 76 %).
 void fine3d_prepare(Ctx& c) {
   using namespace f3d;
   int dev = 0, sms = 0;
   MGAR_CUDA(cudaGetDevice(&dev));
   MGAR_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const Dims& d = c.L[0];
-  c.f3d_gz[PRE] = runs_for<float, PRE, T32x8>(d, sms);
-  c.f3d_gz[POST] = runs_for<float, POST, T32x8>(d, sms);
-  c.f3d_gz[RESID] = runs_for<float, RESID, T32x8>(d, sms);
-  c.f3d_gz[SWEEP] = runs_for<float, SWEEP, T32x8>(d, sms);
-  c.f3d_gz[DIR] = runs_for<float, DIR, T32x8>(d, sms);
+  c.f3d_tile = tile_use(d.NX, d.NY, T43x5::TX, T43x5::TY) > tile_use(d.NX, d.NY, T32x8::TX, T32x8::TY);
+  if (c.f3d_tile) {
+    c.f3d_gz[PRE] = runs_for<float, PRE, T43x5>(d, sms);
+    c.f3d_gz[POST] = runs_for<float, POST, T43x5>(d, sms);
+    c.f3d_gz[RESID] = runs_for<float, RESID, T43x5>(d, sms);
+    c.f3d_gz[SWEEP] = runs_for<float, SWEEP, T43x5>(d, sms);
+    c.f3d_gz[DIR] = runs_for<float, DIR, T43x5>(d, sms);
+  } else {
+    c.f3d_gz[PRE] = runs_for<float, PRE, T32x8>(d, sms);
+    c.f3d_gz[POST] = runs_for<float, POST, T32x8>(d, sms);
+    c.f3d_gz[RESID] = runs_for<float, RESID, T32x8>(d, sms);
+    c.f3d_gz[SWEEP] = runs_for<float, SWEEP, T32x8>(d, sms);
+    c.f3d_gz[DIR] = runs_for<float, DIR, T32x8>(d, sms);
+  }
 }
 
 namespace f3d {
 template <int MODE, class T>
-void launch(Ctx& c, FineArgs& a) {
+void launch_t(Ctx& c, FineArgs& a) {
   const Dims& d = c.L[0];
   a.gz = std::max(1, std::min(c.f3d_gz[MODE], d.NZ));
   const dim3 grid((d.NX + T::TX - 1) / T::TX, (d.NY + T::TY - 1) / T::TY, a.gz);
   launch_pdl(c.stream, c.use_pdl, k_fine3d<float, MODE, T>, grid, dim3(T::NTB), a);
+}
+template <int MODE>
+void launch(Ctx& c, FineArgs& a) {
+  if (c.f3d_tile) launch_t<MODE, T43x5>(c, a);
+  else launch_t<MODE, T32x8>(c, a);
 }
 }  // namespace f3d
 
@@ -480,10 +493,10 @@ void fine3d(Ctx& c, int mode, const float* ke, const float* b, const float* dinv
   a.partials = c.partials;
   a.counter = c.counter;
   switch (mode) {
-    case PRE: launch<PRE, T32x8>(c, a); break;
-    case POST: launch<POST, T32x8>(c, a); break;
-    case RESID: launch<RESID, T32x8>(c, a); break;
-    default: launch<SWEEP, T32x8>(c, a); break;
+    case PRE: launch<PRE>(c, a); break;
+    case POST: launch<POST>(c, a); break;
+    case RESID: launch<RESID>(c, a); break;
+    default: launch<SWEEP>(c, a); break;
   }
   MGAR_LAUNCH_CHECK_AT(level_site(6 + (mode == PRE ? 0 : mode == POST ? 1 : mode == SWEEP ? 2 : 3), 0));
 }
@@ -518,7 +531,7 @@ void fine3d_dir(Ctx& c, const float* z, const float* p_old, float* p, const doub
   a.dout = dot;
   a.partials = c.partials;
   a.counter = c.counter;
-  launch<DIR, T32x8>(c, a);
+  launch<DIR>(c, a);
   MGAR_LAUNCH_CHECK();
 }
 

@@ -8,7 +8,8 @@
 // The tile width need not be a multiple of 32 (warps then span two rows):
 // the df64 operator picks, per grid, the shape with the fewest idle lanes,
 // e.g. 43 x 11 for 129 x 129 node planes (3 x 12 tiles, 96 % of the lanes
-// busy) instead of 32 x 8 (5 x 17 tiles, 77 %).
+// busy) instead of 32 x 8 (5 x 17 tiles, 77 %); the FP32 kernels, which
+// keep four blocks per SM, take 43 x 5 (3 x 26 tiles of 7 warps, 95 %).
 #pragma once
 
 namespace mgar {
@@ -39,6 +40,7 @@ struct Tile {
 
 using T32x8 = Tile<32, 8>;
 using T43x11 = Tile<43, 11>;
+using T43x5 = Tile<43, 5>;
 
 // Fraction of busy lanes of a TX x TY tiling of an NX x NY node plane.
 inline double tile_use(int NX, int NY, int TX, int TY) {
