@@ -192,13 +192,18 @@ __global__ void k_prolong(const Real* __restrict__ xc, const Real* cur, Real* ds
   dst[idx] = cur[idx] + acc;
 }
 
-// 3D interpolation by z-columns: a thread owns fine nodes (i, j, k0..k1)
-// and interpolates each coarse plane in x and y once (4 loads), so a fine
-// node costs one or two cached plane values instead of 8 coarse loads, and
-// the taps in x and y are formed once per column.
+// 3D interpolation by z-columns: a thread owns the fine nodes (i, j, k0 ..
+// k0 + kProlongChunk - 1), k0 even, and interpolates each of the coarse
+// planes k0/2 .. k0/2 + kProlongChunk/2 in x and y once (4 loads), so a
+// fine node costs one or two plane values instead of 8 coarse loads.  Every
+// load of the chunk is issued before the first use (compile-time slots), so
+// the column costs one memory round trip.
+constexpr int kProlongChunk = 8;
+
 template <typename Real>
 __global__ void k_prolong3(const Real* __restrict__ xc, const Real* cur, Real* dst, Dims f, Dims cd,
-                           const uint8_t* __restrict__ fixed, int kchunk) {
+                           const uint8_t* __restrict__ fixed) {
+  constexpr int KC = kProlongChunk, NP = KC / 2 + 1;
   pdl_wait();
   pdl_trigger();
   const int NXY = f.NX * f.NY;
@@ -209,45 +214,48 @@ __global__ void k_prolong3(const Real* __restrict__ xc, const Real* cur, Real* d
   float wx[2], wy[2];
   prolong_taps(i, f.ex, ix, wx);
   prolong_taps(j, f.ey, iy, wy);
-  int o[4];
-  Real w[4];
-#pragma unroll
-  for (int b = 0; b < 2; ++b)
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
-      o[2 * b + a] = ix[a] + cd.NX * iy[b];
-      w[2 * b + a] = (Real)(wx[a] * wy[b]);
-    }
   const int cNXY = cd.NX * cd.NY;
-  // the two most recent coarse planes, interpolated in x and y
-  int pk0 = -1, pk1 = -1;
-  Real pv0 = Real(0), pv1 = Real(0);
-  auto plane = [&](int K) -> Real {
-    if (K == pk1) return pv1;
-    if (K == pk0) return pv0;
-    Real v = Real(0);
+  const int k0 = blockIdx.y * KC, Kb = k0 >> 1;
+  // coarse planes Kb .. Kb + NP - 1, interpolated in x and y
+  Real P[NP];
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      if (CK(o[q] + cNXY * K, cd.n)) v += w[q] * xc[o[q] + cNXY * K];
-    pk0 = pk1;
-    pv0 = pv1;
-    pk1 = K;
-    pv1 = v;
-    return v;
-  };
-  const int k0 = blockIdx.y * kchunk, k1 = min(k0 + kchunk, f.NZ);
-  for (int k = k0; k < k1; ++k) {
-    const int idx = col + NXY * k;
-    if (fixed && fixed[idx]) {
-      dst[idx] = cur[idx];
-      continue;
+  for (int t = 0; t < NP; ++t) {
+    P[t] = Real(0);
+    const int K = Kb + t;
+    if (K < cd.NZ) {
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+          const int o = ix[a] + cd.NX * iy[b] + cNXY * K;
+          if (CK(o, cd.n)) P[t] += (Real)(wx[a] * wy[b]) * xc[o];
+        }
     }
-    int iz[2];
-    float wz[2];
-    const int taps = prolong_taps(k, f.ez, iz, wz);
-    Real acc = (Real)wz[0] * plane(iz[0]);
-    if (taps == 2) acc += (Real)wz[1] * plane(iz[1]);
-    dst[idx] = cur[idx] + acc;
+  }
+  Real cv[KC];
+  uint8_t fx[KC];
+#pragma unroll
+  for (int u = 0; u < KC; ++u) {
+    const int k = k0 + u;
+    cv[u] = Real(0);
+    fx[u] = 0;
+    if (k < f.NZ) {
+      const int idx = col + NXY * k;
+      cv[u] = cur[idx];
+      if (fixed) fx[u] = fixed[idx];
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < KC; ++u) {
+    const int k = k0 + u;
+    if (k >= f.NZ) break;
+    // taps along z: even k -> plane k/2; odd k -> halfway, or the top node
+    // of an odd element count -> plane (k+1)/2
+    Real pz;
+    if ((u & 1) == 0) pz = P[u >> 1];
+    else if (k < f.ez) pz = Real(0.5) * (P[u >> 1] + P[(u >> 1) + 1]);
+    else pz = P[(u >> 1) + 1];
+    dst[col + NXY * k] = fx[u] ? cv[u] : cv[u] + pz;
   }
 }
 
@@ -634,14 +642,9 @@ static void launch_prolong(Ctx& c, bool pdl, const Real* xc, const Real* cur, Re
                            const Dims& f, const Dims& cd, const uint8_t* fixed) {
   if (DIM == 3 && c.prolong_col) {
     const int64_t cols = (int64_t)f.NX * f.NY;
-    const int bx = blocks_for(cols);
-    // z chunks so that the grid holds about eight blocks per SM
-    int gz = (int)std::max<int64_t>(
-        1, std::min<int64_t>(f.NZ, ((int64_t)c.sms * 8 + bx - 1) / bx));
-    const int kchunk = (f.NZ + gz - 1) / gz;
-    gz = (f.NZ + kchunk - 1) / kchunk;
-    launch_pdl(c.stream, pdl && c.use_pdl, k_prolong3<Real>, dim3(bx, gz), dim3(kThreads), xc, cur,
-               dst, f, cd, fixed, kchunk);
+    const int gz = (f.NZ + kProlongChunk - 1) / kProlongChunk;
+    launch_pdl(c.stream, pdl && c.use_pdl, k_prolong3<Real>, dim3(blocks_for(cols), gz),
+               dim3(kThreads), xc, cur, dst, f, cd, fixed);
   } else {
     launch_pdl(c.stream, pdl && c.use_pdl, k_prolong<Real, DIM>, dim3(blocks_for(f.n)),
                dim3(kThreads), xc, cur, dst, f, cd, fixed);
