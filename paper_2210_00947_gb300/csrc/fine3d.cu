@@ -288,32 +288,35 @@ __global__ void __launch_bounds__(T::NTB, f3d_minb(MODE, T::NT)) k_fine3d(FineAr
   const bool rdot = (MODE == POST || MODE == SWEEP || MODE == DIR) && a.dout != nullptr;
   df dacc{0.f, 0.f};
 
-  auto issue_plane = [&](int p) {
-    own.issue(a, ocol, p, dsrc);
+  auto issue_plane_to = [&](int p, NodeFetch<Real, MODE>& o, NodeFetch<Real, MODE>& rg, Real& ob,
+                            Real& od) {
+    o.issue(a, ocol, p, dsrc);
     if (MODE != PRE && MODE != DIR) {
       const int idx = ocol.base + NXY * min(max(p, 0), a.NZ - 1);
       if (CK(idx, (int64_t)NXY * a.NZ)) {
-        ownb = ((const Real*)a.b)[idx];
-        if (MODE == POST || MODE == SWEEP) ownd = ((const Real*)a.dinv)[idx];
+        ob = ((const Real*)a.b)[idx];
+        if (MODE == POST || MODE == SWEEP) od = ((const Real*)a.dinv)[idx];
       }
     }
-    if (xr) ring.issue(a, rcol, p, dsrc);
+    if (xr) rg.issue(a, rcol, p, dsrc);
   };
+  auto issue_plane = [&](int p) { issue_plane_to(p, own, ring, ownb, ownd); };
   auto issue_layer = [&](int l) {
     kown.issue(a, kebase, keon, l);
     if (kr) kring_.issue(a, krbase, kron, l);
   };
 
-#define F3D_FINISH(S)                                                  \
+#define F3D_FINISH_FROM(S, O, RG, OB, OD)                              \
   {                                                                    \
-    mv[S] = own.masked(om, ocol.hxy);                                  \
+    mv[S] = O.masked(om, ocol.hxy);                                    \
     if (real) X[S][ty + 1][tx + 1] = mv[S];                            \
-    cv[S] = own.value(om, ocol.hxy);                                   \
-    cb[S] = MODE == PRE ? own.v0 : ownb;                               \
-    cd[S] = ownd;                                                      \
-    cf[S] = own.f != 0;                                                \
-    if (xr) X[S][ryh][rxh] = ring.masked(om, rcol.hxy);                \
+    cv[S] = O.value(om, ocol.hxy);                                     \
+    cb[S] = MODE == PRE ? O.v0 : OB;                                   \
+    cd[S] = OD;                                                        \
+    cf[S] = O.f != 0;                                                  \
+    if (xr) X[S][ryh][rxh] = RG.masked(om, rcol.hxy);                  \
   }
+#define F3D_FINISH(S) F3D_FINISH_FROM(S, own, ring, ownb, ownd)
 #define F3D_FINISH_LAYER(S)                                            \
   {                                                                    \
     if (real) K[S][ty + 1][tx + 1] = kown.get();                       \
@@ -321,13 +324,18 @@ __global__ void __launch_bounds__(T::NTB, f3d_minb(MODE, T::NT)) k_fine3d(FineAr
   }
 
   // prologue: planes kb-1 (slot 0), kb (slot 1) and layer kb-1 (slot 0) in
-  // place; plane kb+1 and layer kb in flight
-  issue_plane(kb - 1);
-  F3D_FINISH(0);
-  issue_plane(kb);
-  issue_layer(kb - 1);
-  F3D_FINISH(1);
-  F3D_FINISH_LAYER(0);
+  // place, their loads in flight together; then plane kb+1 and layer kb in
+  // flight
+  {
+    NodeFetch<Real, MODE> own2, ring2;
+    Real ownb2 = Real(0), ownd2 = Real(0);
+    issue_plane(kb - 1);
+    issue_plane_to(kb, own2, ring2, ownb2, ownd2);
+    issue_layer(kb - 1);
+    F3D_FINISH(0);
+    F3D_FINISH_FROM(1, own2, ring2, ownb2, ownd2);
+    F3D_FINISH_LAYER(0);
+  }
   issue_plane(kb + 1);
   issue_layer(kb);
 
@@ -396,6 +404,7 @@ __global__ void __launch_bounds__(T::NTB, f3d_minb(MODE, T::NT)) k_fine3d(FineAr
   }
 #undef F3D_STEP
 #undef F3D_FINISH
+#undef F3D_FINISH_FROM
 #undef F3D_FINISH_LAYER
   if (rdot) {
     double t;
