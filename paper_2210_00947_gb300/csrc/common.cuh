@@ -396,12 +396,25 @@ __device__ __forceinline__ bool block_sum_last_core(const double (&w)[N], double
   __syncthreads();
   if (!last) return false;
   __threadfence();
+  // L2-coherent loads (ld.global.cg: the partials of other blocks, ordered
+  // by their fences and the counter), U rows of blocks in flight together;
+  // the adds keep the order b = tid, tid + nthr, ...
+  constexpr int U = N <= 2 ? 4 : 1;
   double acc[N];
 #pragma unroll
   for (int k = 0; k < N; ++k) acc[k] = 0.0;
-  for (int b = tid; b < nblk; b += nthr)
+  for (int b = tid; b < nblk; b += U * nthr) {
+    double v[U][N];
 #pragma unroll
-    for (int k = 0; k < N; ++k) acc[k] += ((volatile double*)partials)[k * nblk + b];
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int k = 0; k < N; ++k)
+        v[u][k] = b + u * nthr < nblk ? __ldcg(partials + k * nblk + b + u * nthr) : 0.0;
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int k = 0; k < N; ++k) acc[k] += v[u][k];
+  }
 #pragma unroll
   for (int k = 0; k < N; ++k) {
     double s = acc[k];
@@ -503,7 +516,18 @@ __device__ __forceinline__ bool block_sum_last_f32(float (&v)[N], double* partia
   __threadfence();
   for (int k = warp; k < N; k += nw) {
     double s = 0.0;
-    for (int b = lane; b < nblk; b += 32) s += ((volatile double*)partials)[k * nblk + b];
+    // four loads in flight per lane (L2-coherent), added in block order
+    const double* pk = partials + (size_t)k * nblk;
+    int b = lane;
+    for (; b + 96 < nblk; b += 128) {
+      const double v0 = __ldcg(pk + b), v1 = __ldcg(pk + b + 32), v2 = __ldcg(pk + b + 64),
+                   v3 = __ldcg(pk + b + 96);
+      s += v0;
+      s += v1;
+      s += v2;
+      s += v3;
+    }
+    for (; b < nblk; b += 32) s += __ldcg(pk + b);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if (lane == 0) tot[k] = s;
@@ -582,8 +606,8 @@ __device__ __forceinline__ void block_max_finish(double v, double* partials, uns
   if (!last) return;
   __threadfence();
   double s = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
-    s = fmax(s, ((volatile double*)partials)[b]);
+#pragma unroll 4
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s = fmax(s, __ldcg(partials + b));
   for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_down_sync(0xffffffffu, s, o));
   if (lane == 0) sh[warp] = s;
   __syncthreads();
