@@ -762,7 +762,7 @@ struct StencilOp {
   FastDiv fNX, fNXY;
 };
 
-template <typename Real>
+template <typename Real, bool CG = false>
 __device__ __forceinline__ Real stencil_row2(const StencilOp<Real>& op, const Real* __restrict__ x,
                                              int i, int j) {
   const int idx = i + op.NX * j;
@@ -778,18 +778,21 @@ __device__ __forceinline__ Real stencil_row2(const StencilOp<Real>& op, const Re
       const int s = (dx + 1) + 3 * (dy + 1);
       const int nb = ii + op.NX * jj;
       if (!CK(nb, op.n) || !CK(idx, op.n)) continue;
-      acc += op.st[s * op.n + idx] * x[nb];
+      acc += op.st[s * op.n + idx] * (CG ? __ldcg(x + nb) : x[nb]);
     }
   }
   return acc;
 }
 
-template <typename Real>
+// The 27 coefficients and operand values are loaded before the first
+// product (compile-time slots), so a row costs one memory round trip; the
+// products are summed in the slot order s = (dx+1) + 3 (dy+1) + 9 (dz+1).
+template <typename Real, bool CG = false>
 __device__ __forceinline__ Real stencil_row3(const StencilOp<Real>& op, const Real* __restrict__ x,
                                              int i, int j, int k) {
   const int NX = op.NX, NXY = op.NX * op.NY;
   const int idx = i + NX * j + NXY * k;
-  Real acc = Real(0);
+  Real sv[27], xv[27];
 #pragma unroll
   for (int dz = -1; dz <= 1; ++dz) {
     const int kk = min(max(k + dz, 0), op.NZ - 1);
@@ -801,11 +804,15 @@ __device__ __forceinline__ Real stencil_row3(const StencilOp<Real>& op, const Re
         const int ii = min(max(i + dx, 0), op.NX - 1);
         const int s = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
         const int nb = ii + NX * jj + NXY * kk;
-        if (!CK(nb, op.n) || !CK(idx, op.n)) continue;
-        acc += op.st[s * op.n + idx] * x[nb];
+        const bool ok = CK(nb, op.n) && CK(idx, op.n);
+        sv[s] = ok ? op.st[s * op.n + idx] : Real(0);
+        xv[s] = ok ? (CG ? __ldcg(x + nb) : x[nb]) : Real(0);
       }
     }
   }
+  Real acc = Real(0);
+#pragma unroll
+  for (int s = 0; s < 27; ++s) acc += sv[s] * xv[s];
   return acc;
 }
 

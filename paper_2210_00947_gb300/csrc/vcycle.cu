@@ -120,10 +120,17 @@ __device__ __forceinline__ int prolong_taps(int i, int nf, int* idx, float* w) {
   idx[0] = idx[1] = (i + 1) >> 1; w[0] = 1.f; w[1] = 0.f; return 1;
 }
 
+// b_c = P^T r at coarse node idx (fixed fine nodes excluded when given);
+// with xc, also the zero-guess smoothing x_c = w D_c^-1 b_c of the coarse
+// level, so its first sweep reduces to a residual.  The 3^d fine values are
+// loaded before the first product.
 template <typename Real, int DIM, bool CG>
 __device__ __forceinline__ void restrict_node(const Real* __restrict__ r, Real* __restrict__ bc,
                                               const Dims& f, const Dims& cd,
-                                              const uint8_t* __restrict__ fixed, int idx) {
+                                              const uint8_t* __restrict__ fixed, int idx,
+                                              const Real* __restrict__ dinvc = nullptr,
+                                              Real omega = Real(0), Real* __restrict__ xc = nullptr) {
+  constexpr int NZ3 = DIM == 3 ? 3 : 1, NV = 9 * NZ3;
   int I, J, K;
   coords(idx, cd.fNX, cd.fNXY, I, J, K);
   int ix[3], iy[3], iz[3] = {0, 0, 0};
@@ -131,31 +138,44 @@ __device__ __forceinline__ void restrict_node(const Real* __restrict__ r, Real* 
   restrict_taps(I, f.ex, ix, wx);
   restrict_taps(J, f.ey, iy, wy);
   if (DIM == 3) restrict_taps(K, f.ez, iz, wz);
-  Real acc = Real(0);
+  Real rv[NV];
+  bool fx[NV];
 #pragma unroll
-  for (int c = 0; c < (DIM == 3 ? 3 : 1); ++c)
+  for (int c = 0; c < NZ3; ++c)
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
       const int base = f.NX * (iy[b] + f.NY * iz[c]);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int q = a + 3 * b + 9 * c, fi = base + ix[a];
+        const bool ok = CK(fi, f.n);
+        rv[q] = ok ? ldv<CG>(r + fi) : Real(0);
+        fx[q] = ok && fixed ? fixed[fi] != 0 : false;
+      }
+    }
+  Real acc = Real(0);
+#pragma unroll
+  for (int c = 0; c < NZ3; ++c)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
       const Real wyz = (Real)(wy[b] * wz[c]);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        const int fi = base + ix[a];
-        if (!CK(fi, f.n)) continue;
-        const Real rv = ldv<CG>(r + fi);
-        const bool fx = fixed ? fixed[fi] != 0 : false;
-        acc += fx ? Real(0) : (wyz * (Real)wx[a]) * rv;
+        const int q = a + 3 * b + 9 * c;
+        acc += fx[q] ? Real(0) : (wyz * (Real)wx[a]) * rv[q];
       }
     }
   bc[idx] = acc;
+  if (xc) xc[idx] = omega * dinvc[idx] * acc;
 }
 
 template <typename Real, int DIM>
 __global__ void k_restrict(const Real* __restrict__ r, Real* __restrict__ bc, Dims f, Dims cd,
-                           const uint8_t* __restrict__ fixed) {
+                           const uint8_t* __restrict__ fixed, const Real* __restrict__ dinvc = nullptr,
+                           Real omega = Real(0), Real* __restrict__ xc = nullptr) {
   pdl_wait();
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx < cd.n) restrict_node<Real, DIM, false>(r, bc, f, cd, fixed, idx);
+  if (idx < cd.n) restrict_node<Real, DIM, false>(r, bc, f, cd, fixed, idx, dinvc, omega, xc);
   pdl_trigger();
 }
 
@@ -259,44 +279,25 @@ __global__ void k_prolong3(const Real* __restrict__ xc, const Real* cur, Real* d
   }
 }
 
-// Fused pre-smooth from a zero guess and residual on an assembled level:
-// x = w D^-1 b, r = b - A x (the neighbours' x recomputed from b and D^-1).
+// Residual r = b - A x on an assembled level.  Below the finest level the
+// V-cycle's first sweep starts from zero, x = w D^-1 b, and the restriction
+// that made b has already written that x, so the sweep and its residual
+// reduce to this.
 template <typename Real, int DIM, bool CG>
-__device__ __forceinline__ void pre_node(const StencilOp<Real>& op, const Real* __restrict__ b,
-                                         const Real* __restrict__ dinv, Real omega,
-                                         Real* __restrict__ x, Real* __restrict__ r, int idx) {
+__device__ __forceinline__ void resid_node(const StencilOp<Real>& op, const Real* __restrict__ b,
+                                           const Real* __restrict__ x, Real* __restrict__ r, int idx) {
   int i, j, k;
   coords(idx, op.fNX, op.fNXY, i, j, k);
-  const int NX = op.NX, NXY = op.NX * op.NY;
-  Real acc = Real(0);
-#pragma unroll
-  for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz) {
-    const int kk = min(max(k + dz, 0), op.NZ - 1);
-#pragma unroll
-    for (int dy = -1; dy <= 1; ++dy) {
-      const int jj = min(max(j + dy, 0), op.NY - 1);
-#pragma unroll
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int ii = min(max(i + dx, 0), op.NX - 1);
-        const int s = (dx + 1) + 3 * (dy + 1) + (DIM == 3 ? 9 * (dz + 1) : 0);
-        const int nb = ii + NX * jj + NXY * kk;
-        if (!CK(nb, op.n)) continue;
-        acc += op.st[s * op.n + idx] * (omega * dinv[nb] * ldv<CG>(b + nb));
-      }
-    }
-  }
-  const Real bi = ldv<CG>(b + idx);
-  x[idx] = omega * dinv[idx] * bi;
-  r[idx] = bi - acc;
+  const Real ax = DIM == 3 ? stencil_row3<Real, CG>(op, x, i, j, k) : stencil_row2<Real, CG>(op, x, i, j);
+  r[idx] = ldv<CG>(b + idx) - ax;
 }
 
 template <typename Real, int DIM>
-__global__ void k_pre_coarse(StencilOp<Real> op, const Real* __restrict__ b,
-                             const Real* __restrict__ dinv, Real omega, Real* __restrict__ x,
-                             Real* __restrict__ r) {
+__global__ void k_resid_coarse(StencilOp<Real> op, const Real* __restrict__ b,
+                               const Real* __restrict__ x, Real* __restrict__ r) {
   pdl_wait();
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx < op.n) pre_node<Real, DIM, false>(op, b, dinv, omega, x, r, idx);
+  if (idx < op.n) resid_node<Real, DIM, false>(op, b, x, r, idx);
   pdl_trigger();
 }
 
@@ -463,12 +464,15 @@ __global__ void __launch_bounds__(kBottomThreads) k_bottom(BottomArgs<Real> a) {
   pdl_trigger();
   const int nthr = gridDim.x * blockDim.x;
   const int vt = blockIdx.x * blockDim.x + threadIdx.x;
+  // x_l = w D^-1 b_l is already in place (left by the restriction)
   for (int l = a.lb; l + 1 < a.nl; ++l) {
     for (int idx = vt; idx < a.L[l].n; idx += nthr)
-      pre_node<Real, DIM, true>(a.op[l], a.b[l], a.op[l].dinv, a.omega, a.x[l], a.r[l], idx);
+      resid_node<Real, DIM, true>(a.op[l], a.b[l], a.x[l], a.r[l], idx);
     cluster_barrier();
+    Real* xn = l + 2 < a.nl ? a.x[l + 1] : nullptr;  // the coarsest level is solved
     for (int idx = vt; idx < a.L[l + 1].n; idx += nthr)
-      restrict_node<Real, DIM, true>(a.r[l], a.b[l + 1], a.L[l], a.L[l + 1], nullptr, idx);
+      restrict_node<Real, DIM, true>(a.r[l], a.b[l + 1], a.L[l], a.L[l + 1], nullptr, idx,
+                                     a.op[l + 1].dinv, a.omega, xn);
     cluster_barrier();
   }
   {
@@ -689,20 +693,23 @@ static void vcycle_fused(Ctx& c, const float* b0, float* x0, bool zero_guess,
     }
   }
   // the tiled 3D kernels leave r = 0 on fixed nodes, which P^T = (Z P)^T ignores
+  // each restriction into a level above the coarsest also leaves that
+  // level's zero-guess sweep x = w D^-1 b
   launch_pdl(c.stream, c.use_pdl, k_restrict<Real, DIM>, dim3(blocks_for(c.L[1].n)), dim3(kThreads),
-             (const Real*)h[0].r, h[1].b, d0, c.L[1], DIM == 3 ? (const uint8_t*)nullptr : c.fixed);
+             (const Real*)h[0].r, h[1].b, d0, c.L[1], DIM == 3 ? (const uint8_t*)nullptr : c.fixed,
+             (const Real*)h[1].dinv, om, nl > 2 ? h[1].x : (Real*)nullptr);
   MGAR_LAUNCH_CHECK_AT(level_site(3, 0));
   const int lb = bottom_level(c);
   // coarse levels, down
   for (int l = 1; l + 1 < nl && l < lb; ++l) {
     const Dims& d = c.L[l];
-    launch_pdl(c.stream, c.use_pdl, k_pre_coarse<Real, DIM>, dim3(blocks_for(d.n)), dim3(kThreads),
-               stencil_row<Real, DIM>(c, l).op, (const Real*)h[l].b, (const Real*)h[l].dinv, om,
-               h[l].x, h[l].r);
+    launch_pdl(c.stream, c.use_pdl, k_resid_coarse<Real, DIM>, dim3(blocks_for(d.n)), dim3(kThreads),
+               stencil_row<Real, DIM>(c, l).op, (const Real*)h[l].b, (const Real*)h[l].x, h[l].r);
     MGAR_LAUNCH_CHECK_AT(level_site(0, l));
     launch_pdl(c.stream, c.use_pdl, k_restrict<Real, DIM>, dim3(blocks_for(c.L[l + 1].n)),
                dim3(kThreads), (const Real*)h[l].r, h[l + 1].b, d, c.L[l + 1],
-               (const uint8_t*)nullptr);
+               (const uint8_t*)nullptr, (const Real*)h[l + 1].dinv, om,
+               l + 2 < nl ? h[l + 1].x : (Real*)nullptr);
     MGAR_LAUNCH_CHECK_AT(level_site(3, l));
   }
   if (lb < nl) {
