@@ -215,17 +215,18 @@ __global__ void __launch_bounds__(T::NTB, T::NT <= 256 ? 4 : 2) k_df3d(DfArgs a)
   bool cf[4];
   df dot{0.f, 0.f};
 
-  auto issue_plane = [&](int p) {
-    own.issue(a, xsrc, ocol, mine, p);
+  auto issue_plane_to = [&](int p, NodeFetch<MODE>& o, NodeFetch<MODE>& rg, float2& oq, float2& okd) {
+    o.issue(a, xsrc, ocol, mine, p);
     {
       const int idx = ocol + NXY * min(max(p, 0), a.NZ - 1);
       if (CK(idx, (int64_t)NXY * a.NZ)) {
-        if (MODE != RESID) ownkd = a.kd[idx];
-        if (MODE == RESID) ownq = a.q[idx];
+        if (MODE != RESID) okd = a.kd[idx];
+        if (MODE == RESID) oq = a.q[idx];
       }
     }
-    if (xr) ring.issue(a, xsrc, rcol, ron, p);
+    if (xr) rg.issue(a, xsrc, rcol, ron, p);
   };
+  auto issue_plane = [&](int p) { issue_plane_to(p, own, ring, ownq, ownkd); };
   auto issue_layer = [&](int l) {
     const int lc = EXY * min(max(l, 0), a.ez - 1);
     const bool lon = l >= 0 && l < a.ez;
@@ -237,33 +238,39 @@ __global__ void __launch_bounds__(T::NTB, T::NT <= 256 ? 4 : 2) k_df3d(DfArgs a)
     }
   };
 
-#define D3D_FINISH(S, P)                                                                   \
+#define D3D_FINISH_FROM(S, P, O, RG, OQ, OKD)                                              \
   {                                                                                        \
-    const df v = own.value(beta);                                                          \
+    const df v = O.value(beta);                                                            \
     const float2 v2 = make_float2(v.hi, v.lo);                                             \
-    if (real) X[S][ty + 1][tx + 1] = (own.on && !own.f) ? v2 : make_float2(0.f, 0.f);      \
+    if (real) X[S][ty + 1][tx + 1] = (O.on && !O.f) ? v2 : make_float2(0.f, 0.f);          \
     cv[S] = v2;                                                                            \
-    cf[S] = own.f != 0;                                                                    \
-    cq[S] = ownq;                                                                          \
-    ckd[S] = ownkd;                                                                        \
+    cf[S] = O.f != 0;                                                                      \
+    cq[S] = OQ;                                                                            \
+    ckd[S] = OKD;                                                                          \
     if (MODE == DIR && mine && (P) >= kb && (P) < kend) pdst[ocol + NXY * (P)] = v2;       \
     if (xr) {                                                                              \
-      const df w = ring.value(beta);                                                       \
-      X[S][ryh][rxh] = (ring.on && !ring.f) ? make_float2(w.hi, w.lo) : make_float2(0.f, 0.f); \
+      const df w = RG.value(beta);                                                         \
+      X[S][ryh][rxh] = (RG.on && !RG.f) ? make_float2(w.hi, w.lo) : make_float2(0.f, 0.f); \
     }                                                                                      \
   }
+#define D3D_FINISH(S, P) D3D_FINISH_FROM(S, P, own, ring, ownq, ownkd)
 #define D3D_FINISH_LAYER(S)                                                                \
   {                                                                                        \
     if (real) K[S][ty + 1][tx + 1] = kown_on ? kown : make_float2(0.f, 0.f);               \
     if (kr) K[S][kyh][kxh] = kring_on ? kring_v : make_float2(0.f, 0.f);                   \
   }
 
-  issue_plane(kb - 1);
-  D3D_FINISH(0, kb - 1);
-  issue_plane(kb);
-  issue_layer(kb - 1);
-  D3D_FINISH(1, kb);
-  D3D_FINISH_LAYER(0);
+  // prologue: planes kb-1 and kb and layer kb-1, their loads in flight together
+  {
+    NodeFetch<MODE> own2, ring2;
+    float2 ownq2 = make_float2(0.f, 0.f), ownkd2 = make_float2(0.f, 0.f);
+    issue_plane(kb - 1);
+    issue_plane_to(kb, own2, ring2, ownq2, ownkd2);
+    issue_layer(kb - 1);
+    D3D_FINISH(0, kb - 1);
+    D3D_FINISH_FROM(1, kb, own2, ring2, ownq2, ownkd2);
+    D3D_FINISH_LAYER(0);
+  }
   issue_plane(kb + 1);
   issue_layer(kb);
 
@@ -372,6 +379,7 @@ __global__ void __launch_bounds__(T::NTB, T::NT <= 256 ? 4 : 2) k_df3d(DfArgs a)
   }
 #undef D3D_STEP
 #undef D3D_FINISH
+#undef D3D_FINISH_FROM
 #undef D3D_FINISH_LAYER
   if (a.out) {
     double t;
