@@ -162,8 +162,9 @@ def shard(items, rank, world):
 # one ncu capture of the kernel as it stands; a kernel changed since its
 # capture has no entry (traffic null).
 TRAFFIC = {
-    # cold-cache ncu capture of one pre-smoothing (27.73 MB) and one
-    # post-smoothing pass (36.33 MB) of the 128^3 workload: their mean
+    # cold-cache ncu capture (43 x 5 tiles, layer-split stencil) of one
+    # pre-smoothing (27.73 MB) and one post-smoothing pass (36.34 MB) of the
+    # 128^3 workload: their mean
     "smooth0": 32.03e6,
     # the same capture, FP32 CG product
     "apply32": 27.74e6,

@@ -744,17 +744,19 @@ static void vcycle_fused(Ctx& c, const float* b0, float* x0, bool zero_guess,
     }
     res[l] = h[l].t;
   }
-  // finest level, post
-  ProfScope ps(c, MGAR_KC_SMOOTH0);
+  // finest level, post (the timed class is the tiled pass alone)
   if (DIM == 3 && !c.split_post) {
+    ProfScope ps(c, MGAR_KC_SMOOTH0);
     fine3d(c, 1, ref_ke<Real>(c), b0, h[0].dinv, cur0, res[1], x0, nullptr, rdot, dout);
   } else if (DIM == 3) {
     // interpolation in place on the pre-smoothed iterate, then the tiled sweep
     launch_prolong<Real, DIM>(c, true, (const Real*)res[1], (const Real*)cur0, cur0, d0, c.L[1],
                               (const uint8_t*)c.fixed);
     MGAR_LAUNCH_CHECK_AT(level_site(4, 0));
+    ProfScope ps(c, MGAR_KC_SMOOTH0);
     fine3d(c, 3, ref_ke<Real>(c), b0, h[0].dinv, cur0, nullptr, x0, nullptr, rdot, dout);
   } else {
+    ProfScope ps(c, MGAR_KC_SMOOTH0);
     // interpolation in place on the pre-smoothed iterate, then the sweep into x0
     k_prolong<Real, DIM><<<blocks_for(d0.n), kThreads, 0, c.stream>>>(res[1], cur0, cur0, d0, c.L[1],
                                                                        c.fixed);
