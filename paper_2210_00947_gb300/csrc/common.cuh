@@ -155,6 +155,8 @@ struct Ctx {
   float* ke_f = nullptr;    // FP32 copies (mixed mode)
   float* ke0_f = nullptr;
   double* inv_hs = nullptr; // 1 / sum of filter weights
+  float2* inv_hs_df = nullptr;  // the same as double-float pairs (mixed path)
+  float2* rho_phys_df = nullptr; // rho~ as double-float pairs (mixed path)
   int4* f_offs = nullptr;   // filter offsets (dx, dy, dz)
   double* f_w = nullptr;    // filter weights max(0, r - |d|)
   double* dv = nullptr;     // F^T (1/E)

@@ -60,6 +60,8 @@ __device__ __forceinline__ void acc_prod(float& ah, float& al, df w, df x) {
 __device__ __forceinline__ df filter_sum_df(const float2* __restrict__ in, const df* w, const char4* offs,
                                             int noff, int e, int i, int j, int k, const Dims& d) {
   float ah = 0.f, al = 0.f;
+  // unrolled: the neighbours' loads of several offsets in flight together
+#pragma unroll 4
   for (int o = 0; o < noff; ++o) {
     const char4 dd = offs[o];
     const int ii = i + dd.x, jj = j + dd.y, kk = k + dd.z;
@@ -75,10 +77,13 @@ __device__ __forceinline__ df filter_sum_df(const float2* __restrict__ in, const
 // Forward filter (Eq. 6) fused with the SIMP conductivities (Eq. 4):
 // rho~_e = inv_hs_e sum_o w_o rho_{e+o}, k_e = kmin + (k0 - kmin) rho~^3,
 // written as FP64 (rho~, k_e), FP32 and df64 copies of k_e.
-__global__ void k_filter_simp_df(const float2* __restrict__ rho, const double* __restrict__ inv_hs,
+// The constants come as double-float pairs (kmin_df, dk_df = k0 - kmin) and
+// 1/Hs as pairs, so no thread converts from FP64 (1/58 of the FP32 rate).
+__global__ void k_filter_simp_df(const float2* __restrict__ rho, const float2* __restrict__ inv_hs,
                                  const int4* __restrict__ offs, const double* __restrict__ w, int noff,
-                                 Dims d, double k0, double kmin, double penal,
-                                 double* __restrict__ rho_phys, double* __restrict__ ke,
+                                 Dims d, double k0, double kmin, double penal, float2 kmin_df,
+                                 float2 dk_df, double* __restrict__ rho_phys,
+                                 float2* __restrict__ rho_df, double* __restrict__ ke,
                                  float* __restrict__ kf, float2* __restrict__ kdf) {
   // offsets staged as bytes: |d| <= 127 for any radius the tables allow
   __shared__ df ws[kMaxFilterOffsets];
@@ -93,11 +98,12 @@ __global__ void k_filter_simp_df(const float2* __restrict__ rho, const double* _
   if (e >= (int)d.ne) return;
   int i, j, k;
   coords(e, d.fEX, d.fEXY, i, j, k);
-  const df r = df_mul(filter_sum_df(rho, ws, os, noff, e, i, j, k, d), df_from_double(inv_hs[e]));
+  const df r = df_mul(filter_sum_df(rho, ws, os, noff, e, i, j, k, d), dfk2(inv_hs[e]));
   rho_phys[e] = df_to_double(r);
+  rho_df[e] = make_float2(r.hi, r.lo);  // the pair k_e comes from (rho_phys: its FP64 rounding)
   df kv;
   if (penal == 3.0) {
-    kv = df_add(df_from_double(kmin), df_mul(df_from_double(k0 - kmin), df_mul(df_mul(r, r), r)));
+    kv = df_add(dfk2(kmin_df), df_mul(dfk2(dk_df), df_mul(df_mul(r, r), r)));
   } else {
     kv = df_from_double(kmin + (k0 - kmin) * pow(df_to_double(r), penal));
   }
@@ -111,8 +117,8 @@ __global__ void k_filter_simp_df(const float2* __restrict__ rho, const double* _
 // from exact pair differences (k0 has zero row sums).
 template <int DIM>
 __global__ void k_sens_df(const float2* __restrict__ T, const double* __restrict__ rho,
-                          const double* __restrict__ inv_hs, float2* __restrict__ out, Dims d,
-                          double coef, double penal) {
+                          const float2* __restrict__ rho_df, const float2* __restrict__ inv_hs,
+                          float2* __restrict__ out, Dims d, float2 mcoef_df, double penal) {
   constexpr int nen = 1 << DIM;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int)d.ne) return;
@@ -149,9 +155,9 @@ __global__ void k_sens_df(const float2* __restrict__ T, const double* __restrict
       al = __fadd_rn(al, __fadd_rn(ue, pe));
     }
   const df energy = df_mul(df_make(ah, al), df_from_double(DIM == 2 ? 1.0 / 6.0 : 1.0 / 12.0));
-  const df r = df_from_double(rho[e]);
+  const df r = dfk2(rho_df[e]);
   const df rp = penal == 3.0 ? df_mul(r, r) : df_from_double(pow(rho[e], penal - 1.0));
-  const df v = df_mul(df_mul(df_from_double(-coef), rp), df_mul(energy, df_from_double(inv_hs[e])));
+  const df v = df_mul(df_mul(dfk2(mcoef_df), rp), df_mul(energy, dfk2(inv_hs[e])));
   out[e] = make_float2(v.hi, v.lo);
 }
 
@@ -614,6 +620,8 @@ static void filter_derived(Ctx& c) {
   k_filter_norm<<<blocks_for(c.ne), kThreads, 0, c.stream>>>(c.inv_hs, c.f_offs, c.f_w, c.n_filter,
                                                              d);
   MGAR_LAUNCH_CHECK();
+  k_to_df<<<blocks_for(c.ne), kThreads, 0, c.stream>>>(c.inv_hs, c.inv_hs_df, (int)c.ne);
+  MGAR_LAUNCH_CHECK();
   k_fill<<<blocks_for(c.ne), kThreads, 0, c.stream>>>(c.tmp_e, 1.0 / (double)c.ne, (int)c.ne);
   MGAR_LAUNCH_CHECK();
   filter(c, c.tmp_e, c.dv, true);
@@ -685,9 +693,11 @@ void set_density(Ctx& c, const double* rho, bool physical) {
     ProfScope ps(c, MGAR_KC_FILTER);
     k_to_df<<<blocks_for(c.ne), kThreads, 0, c.stream>>>(rho, c.df_e, (int)c.ne);
     MGAR_LAUNCH_CHECK();
+    const df kmin_df = df_from_double(c.p.kmin), dk_df = df_from_double(c.p.k0 - c.p.kmin);
     k_filter_simp_df<<<blocks_for(c.ne), kThreads, 0, c.stream>>>(
-        c.df_e, c.inv_hs, c.f_offs, c.f_w, c.n_filter, c.L[0], c.p.k0, c.p.kmin, c.p.penal,
-        c.rho_phys, c.ke, c.ke_f, c.ke_df);
+        c.df_e, c.inv_hs_df, c.f_offs, c.f_w, c.n_filter, c.L[0], c.p.k0, c.p.kmin, c.p.penal,
+        make_float2(kmin_df.hi, kmin_df.lo), make_float2(dk_df.hi, dk_df.lo), c.rho_phys,
+        c.rho_phys_df, c.ke, c.ke_f, c.ke_df);
     MGAR_LAUNCH_CHECK();
     if (c.dim == 3) df3d_node_diag(c);
     return;
@@ -703,6 +713,8 @@ void set_density(Ctx& c, const double* rho, bool physical) {
   MGAR_LAUNCH_CHECK();
   if (c.p.precision == MGAR_MIXED) {
     ke_to_df(c);
+    k_to_df<<<blocks_for(c.ne), kThreads, 0, c.stream>>>(c.rho_phys, c.rho_phys_df, (int)c.ne);
+    MGAR_LAUNCH_CHECK();
     if (c.dim == 3) df3d_node_diag(c);
   }
 }
@@ -718,12 +730,16 @@ void sensitivity(Ctx& c, const double* T, double* dc, double* dv, double* compli
       MGAR_LAUNCH_CHECK();
       T_df = c.df_p2;
     }
+    const df mc = df_from_double(-coef);
+    const float2 mcoef_df = make_float2(mc.hi, mc.lo);
     if (c.dim == 2)
-      k_sens_df<2><<<blocks_for(c.ne), kThreads, 0, c.stream>>>(T_df, c.rho_phys, c.inv_hs, c.df_e, d,
-                                                                coef, c.p.penal);
+      k_sens_df<2><<<blocks_for(c.ne), kThreads, 0, c.stream>>>(T_df, c.rho_phys, c.rho_phys_df,
+                                                                c.inv_hs_df, c.df_e, d, mcoef_df,
+                                                                c.p.penal);
     else
-      k_sens_df<3><<<blocks_for(c.ne), kThreads, 0, c.stream>>>(T_df, c.rho_phys, c.inv_hs, c.df_e, d,
-                                                                coef, c.p.penal);
+      k_sens_df<3><<<blocks_for(c.ne), kThreads, 0, c.stream>>>(T_df, c.rho_phys, c.rho_phys_df,
+                                                                c.inv_hs_df, c.df_e, d, mcoef_df,
+                                                                c.p.penal);
     MGAR_LAUNCH_CHECK();
     k_filter_t_df<<<blocks_for(c.ne), kThreads, 0, c.stream>>>(c.df_e, c.f_offs, c.f_w, c.n_filter, d,
                                                                dc);
