@@ -525,6 +525,7 @@ __device__ void ru_decide(double* dsc, double qnorm, double eps2, double delta, 
   dsc[S_CGFIRST] = 0.0;
   const bool upd = !(isfinite(rn) && rn > eps2 * qnorm && rn > delta * dsc[S_RMAX] && it < cg_max);
   dsc[S_FLAG] = upd ? 1.0 : 0.0;
+  dsc[S_RREC] = rn;
   if (set) cudaGraphSetConditional(ru, upd ? 1u : 0u);
 }
 
@@ -590,6 +591,7 @@ __global__ void k_ru_start(double* dsc) {
   dsc[S_CGFIRST] = 1.0;
   dsc[S_RMAX] = sqrt(dsc[S_RR]);
   dsc[S_RUCOUNT] = 0.0;
+  dsc[S_RUSTALL] = 0.0;
 }
 
 // x += xc in df64, xc = 0
@@ -600,19 +602,29 @@ __global__ void k_ru_update(float2* __restrict__ x, float* __restrict__ xc, int 
   }
 }
 
+// After an update: the new reference ||r||.  Near the accuracy floor of the
+// FP32 iterations the recursive residual drifts from the true one; an update
+// that finds the true ||r|| above twice the recursive one restarts the
+// direction (beta = 0), since beta's old r . z belongs to the drifted
+// recursion, and updates that no longer halve the true ||r|| are counted so
+// the loop can stop and leave the rest to the df64 CG.
 __global__ void k_ru_mark(double* dsc) {
-  dsc[S_RMAX] = sqrt(dsc[S_RR]);
+  const double rt = sqrt(dsc[S_RR]);
+  if (rt > 2.0 * dsc[S_RREC]) dsc[S_CGFIRST] = 1.0;
+  dsc[S_RUSTALL] = rt > 0.5 * dsc[S_RMAX] ? dsc[S_RUSTALL] + 1.0 : 0.0;
+  dsc[S_RMAX] = rt;
   dsc[S_RUCOUNT] += 1.0;
 }
 
 // end of a pass of the graph's WHILE body: stop once an update has shown
-// ||r|| <= eps2 ||q||, at cg_max iterations, or on a non-finite ||r||
+// ||r|| <= eps2 ||q||, at cg_max iterations, on a non-finite ||r||, or after
+// two updates in a row that did not halve the true ||r||
 __global__ void k_ru_loop(double* dsc, double qnorm, double eps2, int cg_max,
                           cudaGraphConditionalHandle loop) {
   const double rn = sqrt(dsc[S_RR]);
   const int it = (int)dsc[S_CGIT];
   const bool conv = dsc[S_FLAG] != 0.0 && rn <= eps2 * qnorm;
-  const bool go = !conv && isfinite(rn) && it < cg_max;
+  const bool go = !conv && isfinite(rn) && it < cg_max && dsc[S_RUSTALL] < 2.0;
   cudaGraphSetConditional(loop, go ? 1u : 0u);
 }
 
@@ -790,12 +802,33 @@ static int solve_mgcg_ru3(Ctx& c, double* T, int* iters, double* relres) {
         rel = rmax / c.qnorm;
         require(std::isfinite(rel), MGAR_ERR_NONFINITE, "CG breakdown (non-finite residual)");
         if (rel <= c.p.eps2 || it >= c.p.cg_max) break;
+        fetch_scalars(c, S_RUSTALL, 1);
+        if (c.hsc[S_RUSTALL] >= 2.0) break;
       }
     }
     require(std::isfinite(rel), MGAR_ERR_NONFINITE, "CG breakdown (non-finite residual)");
   }
   k_df_to_d<<<blocks_for(n), kThreads, 0, c.stream>>>(c.df_x, T, n);
   MGAR_LAUNCH_CHECK();
+  if (!(rel <= c.p.eps2) && it < c.p.cg_max) {
+    // the FP32 iterations stalled above eps2 (their accuracy floor): the
+    // df64 CG continues from x with the iterations left
+    const int cg_max = c.p.cg_max;
+    int it2 = 0;
+    c.p.cg_max = cg_max - it;
+    int rc = MGAR_OK;
+    try {
+      rc = solve_mgcg_df3(c, T, &it2, &rel);
+    } catch (...) {
+      c.p.cg_max = cg_max;
+      throw;
+    }
+    c.p.cg_max = cg_max;
+    it += it2;
+    if (iters) *iters = it;
+    if (relres) *relres = rel;
+    return rc;
+  }
   if (iters) *iters = it;
   if (relres) *relres = rel;
   return rel <= c.p.eps2 ? MGAR_OK : MGAR_ERR_MAXIT;

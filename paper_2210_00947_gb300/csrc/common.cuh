@@ -70,7 +70,9 @@ enum Slot : int {
   S_OC_CAND = 128,  // 128..158 multisection candidates mu
   S_OC_CANDL = 160, // 160..190 their ln mu
   S_DERR = 191,     // host mirror only: the device error flag, published with every fetch
-  S_COUNT = 192
+  S_RREC = 192,     // FP32 CG: recursive ||r|| at the last update decision
+  S_RUSTALL = 193,  // FP32 CG: successive updates that did not halve the true ||r||
+  S_COUNT = 194
 };
 
 // 1 / sqrt(a) for a > 0: an FP32 seed refined by two Newton-Raphson steps

@@ -279,9 +279,17 @@ def test_oc_large_matches_oracle(dims):
         np.testing.assert_allclose(host(r), ref, rtol=1e-11, atol=1e-12)
 
 
+# (42, 42, 21): 43-node planes select the 43 x 5 FP32 tile and the 43 x 11
+# df64 tile (one tile column, ragged rows), and 22 planes leave a ragged run
+# of the four-plane unrolled z march.  (42, 42, 21) and (32, 32, 20) at
+# eps2 = 1e-11 lie below the accuracy floor of the FP32 iterations: without
+# the restart on drift and the hand-over to the df64 CG the first stalled
+# near 5e-10 and the second diverged.
 @pytest.mark.parametrize("dims,nl,cg", [((64, 48, 0), 4, "df64"), ((100, 100, 0), 4, "df64"),
                                         ((16, 16, 12), 3, "ru"), ((20, 18, 16), 4, "ru"),
-                                        ((16, 16, 12), 3, "df64"), ((20, 18, 16), 4, "df64")])
+                                        ((16, 16, 12), 3, "df64"), ((20, 18, 16), 4, "df64"),
+                                        ((42, 42, 21), 3, "ru"), ((42, 42, 21), 3, "df64"),
+                                        ((32, 32, 20), 3, "ru")])
 def test_mixed_mgcg_matches_exact_solve(dims, nl, cg, monkeypatch):
     """Mixed path with the FP32 V-cycle as preconditioner: on 2D grids (and
     on 3D grids with MGAR_DF64_CG=1) a df64 CG, on 3D grids by default FP32
