@@ -377,9 +377,12 @@ void solve_mgar(Ctx& c, const double* T_prev, double* T, double* res, int* accep
       // = r_{i-1} - MG(K r_{i-1}, 0) (the V-cycle is affine in its guess).  In the
       // mixed path only the correction goes through FP32, so the large r_{i-1}
       // never cancels in single precision.
-      apply_df64(c, prev, c.r);  // c.r = K r_{i-1}
-      run_graph(c, 5, c.r, ri, vcycle_profiled(c), [&] {
-        convert_d2f(c, c.r, c.b32, n);
+      // K r_0 goes straight to W_0: the first basis vector is r_0 / ||r_0||, so
+      // the reduced system's W_0 = K R_0 is it scaled (Eq. 19)
+      double* kprev = i == 1 ? c.W : c.r;
+      apply_df64(c, prev, kprev);  // K r_{i-1}
+      run_graph(c, 5, kprev, ri, vcycle_profiled(c), [&] {
+        convert_d2f(c, kprev, c.b32, n);
         vcycle<float>(c, c.b32, c.x32, true);
         convert_f2d(c, c.x32, ri, n);
       });
@@ -420,11 +423,16 @@ void solve_mgar(Ctx& c, const double* T_prev, double* T, double* res, int* accep
   }
   require(kept > 0, MGAR_ERR_NONFINITE, "MGAR basis vanished");
   // Eq. 19-21: reduced system
+  const bool w0_held = c.p.precision == MGAR_MIXED && !zero && m > 1;  // W_0 = K r_0 from Eq. 17
   for (int j = 0; j < kept; ++j) {
-    if (c.p.precision == MGAR_MIXED)
+    if (j == 0 && w0_held) {
+      k_scale<<<rb, kThreads, 0, c.stream>>>(c.W, n, 1.0 / ref);
+      MGAR_LAUNCH_CHECK();
+    } else if (c.p.precision == MGAR_MIXED) {
       apply_df64(c, c.R + (int64_t)j * n, c.W + (int64_t)j * n);
-    else
+    } else {
       apply_fine64(c, c.ke, c.R + (int64_t)j * n, c.W + (int64_t)j * n, nullptr);
+    }
   }
   if (kept <= 3) {
     switch (kept) {
