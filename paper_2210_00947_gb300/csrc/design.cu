@@ -785,8 +785,10 @@ void oc_update(Ctx& c, double* rho, const double* dc, double volfrac, double mov
     MGAR_LAUNCH_CHECK();
     k_oc_start<<<1, 32, 0, c.stream>>>(c.dsc, Lmin, Lmax, 1);
     MGAR_LAUNCH_CHECK();
-    // two blocks per SM: the last block's FP64 sum over the partials stays short
-    const int msb = std::min(blocks_for(ne), c.sms * 2);
+    // three blocks per SM (the 80 registers of the 31 accumulators allow
+    // three): more loads in flight; the last block's sum over the partials
+    // stays short
+    const int msb = std::min(blocks_for(ne), c.sms * 3);
     for (int pass = 0; pass < kOcPasses; ++pass) {
       k_oc_multisect<<<msb, kThreads, 0, c.stream>>>(c.oc_s32, c.oc_lo32, c.oc_hi32, c.dv32, ne,
                                                     volfrac, c.dsc, c.partials, c.counter);
