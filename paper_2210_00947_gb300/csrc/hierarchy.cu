@@ -125,13 +125,18 @@ __global__ void __launch_bounds__(kThreads) k_galerkin_fine(const Real* __restri
 
 // Level 0 -> 1 for the coarse elements with a fixed fine node (a short list
 // fixed at creation), one thread per entry: (Z P)^T k0 (Z P) with the rows
-// and columns of fixed fine nodes removed.
+// and columns of fixed fine nodes removed.  k0 sits in shared memory in the
+// working precision, and each sub-element's double sum is factored as
+// sum_b P_bJ (sum_a P_aI k0_ab) over the free fine nodes a, b.
 template <typename Real, int DIM>
 __global__ void k_galerkin_fixed(const Real* __restrict__ ke, const uint8_t* __restrict__ fixed,
                                  const int* __restrict__ list, int nlist, Dims f, Dims cd,
                                  const double* __restrict__ k0, Real* __restrict__ elem) {
   constexpr int nen = 1 << DIM;
   constexpr int NN = nen * nen;
+  __shared__ Real k0s[NN];
+  for (int u = threadIdx.x; u < NN; u += blockDim.x) k0s[u] = (Real)k0[u];
+  __syncthreads();
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= (int64_t)nlist * NN) return;
   const int li = (int)(tid / NN);
@@ -147,20 +152,24 @@ __global__ void k_galerkin_fixed(const Real* __restrict__ ke, const uint8_t* __r
     if (!sub_element<DIM>(f, cx, cy, cz, s, e, t) || !CK(e, f.ne)) continue;
     const int fx = 2 * cx + (s & 1), fy = 2 * cy + ((s >> 1) & 1), fz = 2 * cz + ((s >> 2) & 1);
     unsigned fm = 0;
+#pragma unroll
     for (int a = 0; a < nen; ++a) {
       const int nd = (fx + (a & 1)) + f.NX * ((fy + ((a >> 1) & 1)) + f.NY * (fz + ((a >> 2) & 1)));
       if (CK(nd, f.n) && fixed[nd]) fm |= 1u << a;
     }
-    Real part = Real(0);
+    Real u[nen];
+#pragma unroll
+    for (int b = 0; b < nen; ++b) u[b] = Real(0);
+#pragma unroll
     for (int a = 0; a < nen; ++a) {
-      const float pa = pw<DIM>(t, a, I);
-      if ((fm & (1u << a)) || pa == 0.f) continue;
-      for (int b = 0; b < nen; ++b) {
-        const float pb = pw<DIM>(t, b, J);
-        if ((fm & (1u << b)) || pb == 0.f) continue;
-        part += (Real)(pa * pb) * (Real)k0[a * nen + b];
-      }
+      const Real pa = (fm & (1u << a)) ? Real(0) : (Real)pw<DIM>(t, a, I);
+#pragma unroll
+      for (int b = 0; b < nen; ++b) u[b] += pa * k0s[a * nen + b];
     }
+    Real part = Real(0);
+#pragma unroll
+    for (int b = 0; b < nen; ++b)
+      if (!(fm & (1u << b))) part += (Real)pw<DIM>(t, b, J) * u[b];
     acc += ke[e] * part;
   }
   elem[(int64_t)E * NN + IJ] = acc;
