@@ -110,6 +110,36 @@ def test_vcycle_matches_oracle(dims, nl, zero_guess):
         assert relerr(host(x), ref) < 1e-10
 
 
+# The mixed path's FP32 V-cycle (tiled finest-level passes, the restriction
+# that leaves each coarse level's zero-guess sweep, the coarse residual, the
+# cluster kernel for the small levels, the column interpolation) against the
+# oracle's FP64 V-cycle on the same hierarchy.  FP32 storage and arithmetic
+# bound the agreement (the operands carry 2^-24 and each stencil row cancels
+# its 21-27 terms down to the residual); the bar is 1e-4.  (42, 42, 21)
+# selects the 43 x 5 tiles and coarsens z oddly.
+@pytest.mark.parametrize("dims,nl", [((37, 23, 0), 3), ((100, 100, 0), 4), ((13, 11, 9), 3),
+                                     ((20, 18, 16), 4), ((42, 42, 21), 3)])
+@pytest.mark.parametrize("zero_guess", [True, False])
+def test_mixed_vcycle_matches_oracle(dims, nl, zero_guess):
+    g, rho, fixed, q = make_problem(dims, mask="sink")
+    A = fem.system_matrix(g, rho, fixed)
+    dims_e = dims[:2] if dims[2] == 0 else dims
+    levels = mg.build_hierarchy(A, fixed, dims_e, nl)
+    rng = np.random.default_rng(5)
+    b = rng.standard_normal(g.n_nodes)
+    b[fixed != 0] = 0.0
+    x0 = np.zeros(g.n_nodes) if zero_guess else rng.standard_normal(g.n_nodes)
+    if not zero_guess:
+        x0[fixed != 0] = 0.0
+    ref = mg.vcycle(levels, b, x0.copy())
+    with solver_for(dims, fixed, q, nl=nl, precision=mgar.MGAR_MIXED) as s:
+        s.set_density(dev(rho), physical=True)
+        s.build_hierarchy()
+        x = dev(x0)
+        s.vcycle(dev(b), x)
+        assert relerr(host(x), ref) < 1e-4
+
+
 @pytest.mark.parametrize("dims,nl", [((37, 23, 0), 3), ((100, 100, 0), 4), ((13, 11, 9), 3),
                                      ((16, 16, 12), 3)])
 def test_mgcg_matches_oracle(dims, nl):
