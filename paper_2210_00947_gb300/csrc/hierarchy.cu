@@ -63,10 +63,14 @@ __device__ __forceinline__ bool sub_element(const Dims& f, int cx, int cy, int c
 }
 
 // ------------------------------------------------------------------ kernels
-// Level 0 -> 1: element matrices of A_1 from k_e, one thread per coarse
-// element.  Sub-elements without fixed nodes use the tables
-// G_type = P_type^T k0 P_type (staged in shared memory); a coarse element
-// with any fixed fine node takes (Z P)^T k0 (Z P) entry by entry.
+// Level 0 -> 1: element matrices of A_1 from k_e, kGalerkinTPE threads per
+// coarse element, each forming every kGalerkinTPE-th group of four entries,
+// so the threads of an element store 64 contiguous bytes at a time.
+// Sub-elements without fixed nodes use the tables G_type = P_type^T k0 P_type
+// (staged in shared memory); a coarse element with any fixed fine node takes
+// (Z P)^T k0 (Z P) entry by entry.
+constexpr int kGalerkinTPE = 4;
+
 template <typename Real, int DIM>
 __global__ void __launch_bounds__(kThreads) k_galerkin_fine(const Real* __restrict__ ke,
                                                              const uint8_t* __restrict__ fixed,
@@ -81,8 +85,9 @@ __global__ void __launch_bounds__(kThreads) k_galerkin_fine(const Real* __restri
   __shared__ Real Gs[NT * GS];
   for (int u = threadIdx.x; u < NT * NN; u += blockDim.x) Gs[(u / NN) * GS + (u % NN)] = G[u];
   __syncthreads();
-  // one thread per coarse element: its 2^d sub-elements are found once
-  const int64_t E = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t E = gt / kGalerkinTPE;
+  const int part = (int)(gt - E * kGalerkinTPE);
   if (E >= cd.ne) return;
   int cx, cy, cz;
   coords((int)E, cd.fEX, cd.fEXY, cx, cy, cz);
@@ -100,8 +105,8 @@ __global__ void __launch_bounds__(kThreads) k_galerkin_fine(const Real* __restri
   Real* dst = elem + E * NN;
   if (!any_fixed) {  // (the others are written by k_galerkin_fixed)
     // A_E = sum_s k_s G_type(s), four entries per store
-#pragma unroll 2
-    for (int q = 0; q < NN; q += 4) {
+#pragma unroll
+    for (int q = 4 * part; q < NN; q += 4 * kGalerkinTPE) {
       Real a0 = Real(0), a1 = Real(0), a2 = Real(0), a3 = Real(0);
 #pragma unroll
       for (int s = 0; s < nen; ++s) {
@@ -257,7 +262,23 @@ __global__ void k_assemble(const Real* __restrict__ elem, Dims d, Real* __restri
     const int e = ok ? exi + d.ex * (eyi + d.ey * ezi) : 0;  // valid address either way
     if (!ok || !CK(e, d.ne)) continue;
     const int Iloc = o;  // node position inside the element equals -offset
-    const Real* row = elem + (size_t)e * nen * nen + Iloc * nen;
+    // the row: nen consecutive entries at a multiple of nen (16-byte loads
+    // for FP32; the element matrices are 256-byte aligned allocations)
+    Real row[nen];
+    const Real* src = elem + (size_t)e * nen * nen + Iloc * nen;
+    if (sizeof(Real) == 4) {
+#pragma unroll
+      for (int J = 0; J < nen; J += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(src + J);
+        row[J] = (Real)v.x;
+        row[J + 1] = (Real)v.y;
+        row[J + 2] = (Real)v.z;
+        row[J + 3] = (Real)v.w;
+      }
+    } else {
+#pragma unroll
+      for (int J = 0; J < nen; ++J) row[J] = src[J];
+    }
 #pragma unroll
     for (int J = 0; J < nen; ++J) {
       const int dx = (J & 1) + ox, dy = ((J >> 1) & 1) + oy;
@@ -605,8 +626,8 @@ static void build_levels(Ctx& c, const Real* ke0, LevelBuf<Real>* h) {
     ProfScope ps(c, l == 0 ? MGAR_KC_GALERKIN0 : -1);
     const int64_t entries = cd.ne * nen * nen;  // coarse levels: one thread per entry
     if (l == 0) {
-      k_galerkin_fine<Real, DIM><<<blocks_for(cd.ne), kThreads, 0, s>>>(ke0, c.fixed, c.efix, f, cd, G,
-                                                                          k0, h[1].elem);
+      k_galerkin_fine<Real, DIM><<<blocks_for(cd.ne * kGalerkinTPE), kThreads, 0, s>>>(
+          ke0, c.fixed, c.efix, f, cd, G, k0, h[1].elem);
       MGAR_LAUNCH_CHECK();
       if (c.n_gfix > 0)
         k_galerkin_fixed<Real, DIM><<<blocks_for((int64_t)c.n_gfix * nen * nen), kThreads, 0, s>>>(
