@@ -56,10 +56,26 @@ __device__ __forceinline__ void acc_prod(float& ah, float& al, df w, df x) {
   al = __fadd_rn(al, __fadd_rn(te, pe));
 }
 
-// sum over in-domain offsets o of w_o in_{e+o}
+// sum over in-domain offsets o of w_o in_{e+o}.  Every lane of the warp
+// must call it (a warp vote): a warp whose elements all lie at least reach
+// (reach_z along z) from the boundary takes every offset without bounds
+// tests; the sum is taken in the same order either way.
 __device__ __forceinline__ df filter_sum_df(const float2* __restrict__ in, const df* w, const char4* offs,
-                                            int noff, int e, int i, int j, int k, const Dims& d) {
+                                            int noff, int e, int i, int j, int k, const Dims& d,
+                                            int reach, int reach_z) {
   float ah = 0.f, al = 0.f;
+  const bool inner = i >= reach && i < d.ex - reach && j >= reach && j < d.ey - reach &&
+                     k >= reach_z && k < d.ez - reach_z;
+  if (__all_sync(0xffffffffu, inner)) {
+#pragma unroll 4
+    for (int o = 0; o < noff; ++o) {
+      const char4 dd = offs[o];
+      const int nb = e + dd.x + d.ex * (dd.y + d.ey * dd.z);
+      if (!CK(nb, d.ne)) continue;
+      acc_prod(ah, al, w[o], dfk2(in[nb]));
+    }
+    return df_make(ah, al);
+  }
   // unrolled: the neighbours' loads of several offsets in flight together
 #pragma unroll 4
   for (int o = 0; o < noff; ++o) {
@@ -81,8 +97,8 @@ __device__ __forceinline__ df filter_sum_df(const float2* __restrict__ in, const
 // 1/Hs as pairs, so no thread converts from FP64 (1/58 of the FP32 rate).
 __global__ void k_filter_simp_df(const float2* __restrict__ rho, const float2* __restrict__ inv_hs,
                                  const int4* __restrict__ offs, const double* __restrict__ w, int noff,
-                                 Dims d, double k0, double kmin, double penal, float2 kmin_df,
-                                 float2 dk_df, double* __restrict__ rho_phys,
+                                 Dims d, int reach, int reach_z, double k0, double kmin, double penal,
+                                 float2 kmin_df, float2 dk_df, double* __restrict__ rho_phys,
                                  float2* __restrict__ rho_df, double* __restrict__ ke,
                                  float* __restrict__ kf, float2* __restrict__ kdf) {
   // offsets staged as bytes: |d| <= 127 for any radius the tables allow
@@ -94,11 +110,16 @@ __global__ void k_filter_simp_df(const float2* __restrict__ rho, const float2* _
     os[o] = make_char4((signed char)v.x, (signed char)v.y, (signed char)v.z, 0);
   }
   __syncthreads();
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (int)d.ne) return;
+  // lanes past the last element work on the last one (the warp vote in
+  // filter_sum_df needs every lane) and store nothing
+  const int e0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = e0 < (int)d.ne;
+  const int e = valid ? e0 : (int)d.ne - 1;
   int i, j, k;
   coords(e, d.fEX, d.fEXY, i, j, k);
-  const df r = df_mul(filter_sum_df(rho, ws, os, noff, e, i, j, k, d), dfk2(inv_hs[e]));
+  const df r = df_mul(filter_sum_df(rho, ws, os, noff, e, i, j, k, d, reach, reach_z),
+                      dfk2(inv_hs[e]));
+  if (!valid) return;
   rho_phys[e] = df_to_double(r);
   rho_df[e] = make_float2(r.hi, r.lo);  // the pair k_e comes from (rho_phys: its FP64 rounding)
   df kv;
@@ -163,7 +184,8 @@ __global__ void k_sens_df(const float2* __restrict__ T, const double* __restrict
 
 // Transpose filter (Eq. 9/11) of a df64 input already scaled by inv_hs.
 __global__ void k_filter_t_df(const float2* __restrict__ in, const int4* __restrict__ offs,
-                              const double* __restrict__ w, int noff, Dims d, double* __restrict__ out) {
+                              const double* __restrict__ w, int noff, Dims d, int reach, int reach_z,
+                              double* __restrict__ out) {
   // offsets staged as bytes: |d| <= 127 for any radius the tables allow
   __shared__ df ws[kMaxFilterOffsets];
   __shared__ char4 os[kMaxFilterOffsets];
@@ -173,11 +195,14 @@ __global__ void k_filter_t_df(const float2* __restrict__ in, const int4* __restr
     os[o] = make_char4((signed char)v.x, (signed char)v.y, (signed char)v.z, 0);
   }
   __syncthreads();
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (int)d.ne) return;
+  // lanes past the last element work on the last one (warp vote) and store nothing
+  const int e0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = e0 < (int)d.ne;
+  const int e = valid ? e0 : (int)d.ne - 1;
   int i, j, k;
   coords(e, d.fEX, d.fEXY, i, j, k);
-  out[e] = df_to_double(filter_sum_df(in, ws, os, noff, e, i, j, k, d));
+  const df v = filter_sum_df(in, ws, os, noff, e, i, j, k, d, reach, reach_z);
+  if (valid) out[e] = df_to_double(v);
 }
 
 __global__ void k_to_df(const double* __restrict__ a, float2* __restrict__ b, int n) {
@@ -580,6 +605,10 @@ __global__ void k_oc_prep32(const double* __restrict__ s, const double* __restri
 // ------------------------------------------------------------------- host
 // Offsets and weights max(0, r - |d|) of a radius-r filter (Eq. 7), in the
 // order dz, dy, dx.
+// The largest |offset| component of the current tables (filter_tables
+// reaches ceil(r) along each axis).
+static int filter_reach(const Ctx& c) { return (int)std::ceil(c.filter_r); }
+
 static void filter_tables(double r, int dim, std::vector<int4>& offs, std::vector<double>& w) {
   const int reach = (int)std::ceil(r);
   offs.clear();
@@ -695,7 +724,8 @@ void set_density(Ctx& c, const double* rho, bool physical) {
     MGAR_LAUNCH_CHECK();
     const df kmin_df = df_from_double(c.p.kmin), dk_df = df_from_double(c.p.k0 - c.p.kmin);
     k_filter_simp_df<<<blocks_for(c.ne), kThreads, 0, c.stream>>>(
-        c.df_e, c.inv_hs_df, c.f_offs, c.f_w, c.n_filter, c.L[0], c.p.k0, c.p.kmin, c.p.penal,
+        c.df_e, c.inv_hs_df, c.f_offs, c.f_w, c.n_filter, c.L[0], filter_reach(c),
+        c.dim == 3 ? filter_reach(c) : 0, c.p.k0, c.p.kmin, c.p.penal,
         make_float2(kmin_df.hi, kmin_df.lo), make_float2(dk_df.hi, dk_df.lo), c.rho_phys,
         c.rho_phys_df, c.ke, c.ke_f, c.ke_df);
     MGAR_LAUNCH_CHECK();
@@ -741,8 +771,8 @@ void sensitivity(Ctx& c, const double* T, double* dc, double* dv, double* compli
                                                                 c.inv_hs_df, c.df_e, d, mcoef_df,
                                                                 c.p.penal);
     MGAR_LAUNCH_CHECK();
-    k_filter_t_df<<<blocks_for(c.ne), kThreads, 0, c.stream>>>(c.df_e, c.f_offs, c.f_w, c.n_filter, d,
-                                                               dc);
+    k_filter_t_df<<<blocks_for(c.ne), kThreads, 0, c.stream>>>(
+        c.df_e, c.f_offs, c.f_w, c.n_filter, d, filter_reach(c), c.dim == 3 ? filter_reach(c) : 0, dc);
     MGAR_LAUNCH_CHECK();
   } else if (dc) {
     ProfScope ps(c, MGAR_KC_SENS);
