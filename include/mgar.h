@@ -94,11 +94,13 @@ typedef struct mgar_step_info {
   int32_t accepted;   /* 1 when the MGAR solution was accepted */
   int32_t cg_iters;   /* MGCG iterations of this cycle */
   int32_t status;     /* MGAR_OK, or MGAR_ERR_MAXIT when MGCG hit cg_max */
+  double compliance_mgar; /* q^T t~ of the MGAR reduced solution (Eq. 5, 21) whether
+                             Eq. 28 accepted it or not; NaN when MGAR did not run */
 } mgar_step_info;
 
 /* Fill *p with the defaults of the paper's experiments (Section 3.2): k0 1,
  * kmin 1e-3, p 3, rmin 1.5, nl 4, m 2, eps1 0.5, eps2 1e-8, cg_max 200,
- * omega 0.6, one pre- and post-sweep, FP64, Eq. 17 as printed, n_on 0,
+ * omega 0.9, one pre- and post-sweep, FP64, Eq. 17 as printed, n_on 0,
  * volfrac 0.4, move 0.2.  The grid size is left zero. */
 void mgar_default_params(mgar_params* p);
 
@@ -177,11 +179,6 @@ int mgar_solve_mgar(mgar_t h, const double* T_prev, double* T, double* res, int*
  *   compliance: host (may be NULL), q^T T. */
 int mgar_sensitivity(mgar_t h, const double* T, double* dc, double* dv, double* compliance);
 
-/* Optimality-criteria update (not in the paper; the classical SIMP
- * framework it names): rho <- clamp(rho sqrt(-dc/(lambda dv)), rho-move,
- * rho+move, [0,1]) with lambda by bisection so that mean(F rho) = volfrac.
- *   rho: device E doubles, updated in place; dc: device E doubles.
- *   lambda, change: host (may be NULL); change = max |rho_new - rho|. */
 /* Projection-based boundary post-processing (Section 2.3, Eq. 24-27), run
  * once after the optimisation: the element sensitivities of the design
  * (Eq. 10, magnitude) are projected onto the nodes with the filter's weights
@@ -198,6 +195,11 @@ int mgar_sensitivity(mgar_t h, const double* T, double* dc, double* dv, double* 
 int mgar_postprocess(mgar_t h, const double* rho, const double* T, double volfrac, double* rho_out,
                      double* level, double* volume);
 
+/* Optimality-criteria update (not in the paper; the classical SIMP
+ * framework it names): rho <- clamp(rho sqrt(-dc/(lambda dv)), rho-move,
+ * rho+move, [0,1]) with lambda by bisection so that mean(F rho) = volfrac.
+ *   rho: device E doubles, updated in place; dc: device E doubles.
+ *   lambda, change: host (may be NULL); change = max |rho_new - rho|. */
 int mgar_oc_update(mgar_t h, double* rho, const double* dc, double volfrac, double move,
                    double* lambda, double* change);
 
@@ -264,16 +266,20 @@ int64_t mgar_kernel_launches(void);
  * allocation: the per-element intermediate lives in a static device array
  * of 2^20 doubles (8 MiB) that every GPU loading the library keeps until
  * the process exits.
- *   p:        host; nx, ny, nz, k0, kmin, penal and rmin are read.
+ *   p:        host; nx, ny, nz, k0, kmin, penal, rmin and filter_alpha are
+ *             read.  The filter is the fixed-radius one of radius rmin; a
+ *             continuation schedule (filter_alpha > 0, Eq. 22-23) is refused
+ *             with MGAR_ERR_ARG: pass the radius wanted as rmin instead.
  *   rho_phys: device, E doubles, the physical (filtered) density.
  *   T:        device, n doubles; dc: device, E doubles (output).
  *   stream:   cudaStream_t the two kernels are queued on.
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call outside any
- * stream capture.  All calls share the array, so calls whose work overlaps
+ * stream capture.  The address is kept for the life of the process, so a
+ * device reset (cudaDeviceReset) after the first call is not supported.  All calls share the array, so calls whose work overlaps
  * on the GPU (other streams or host threads) race; each call writes every
  * entry it reads, so nothing needs clearing between calls.
- * Errors: MGAR_ERR_ARG (null pointer, bad grid or rmin > 8),
+ * Errors: MGAR_ERR_ARG (null pointer, bad grid, rmin > 8 or filter_alpha > 0),
  * MGAR_ERR_TOO_LARGE (more than 2^20 elements), MGAR_ERR_CUDA (symbol lookup
  * or launch failed).  Returns without synchronising the stream. */
 int mgar_sensitivity_noalloc(const mgar_params* p, const double* rho_phys, const double* T,

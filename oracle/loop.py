@@ -41,7 +41,7 @@ class LoopSettings:
     eps2: float = 1e-8
     cg_max: int = 200
     m: int = 2
-    omega: float = 0.6
+    omega: float = 0.9
     nu_pre: int = 1
     nu_post: int = 1
     basis_guess: str = "previous"
@@ -91,7 +91,8 @@ class Analysis:
                 self.H, self.Hs = design.filter_matrix(self.grid, r)
         rho_phys = design.filter_forward(self.H, self.Hs, rho)
         A = self.system(rho_phys)
-        info = dict(cycle=k, mgcg=False, accepted=False, res=float("nan"), cg_iters=0)
+        info = dict(cycle=k, mgcg=False, accepted=False, res=float("nan"), cg_iters=0,
+                    compliance_mgar=float("nan"))
         if (not s.use_mgar) or k < s.n_on or self.levels0 is None:
             t, it, relres = self.run_mgcg(A, t_prev)
             info.update(mgcg=True, cg_iters=it, relres=relres)
@@ -99,6 +100,7 @@ class Analysis:
             t, res = solvers.mgar(A, self.A0, self.levels0, self.q, t_prev, s.m, s.omega,
                                   s.nu_pre, s.nu_post, s.basis_guess)
             info["res"] = res
+            info["compliance_mgar"] = design.compliance(self.q, t)
             if res <= s.eps1:
                 info["accepted"] = True
             else:

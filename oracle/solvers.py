@@ -31,7 +31,7 @@ def exact_solve(A, b) -> np.ndarray:
     return spla.spsolve(A.tocsc(), b)
 
 
-def mgcg(A, b, x0, levels, eps2=1e-8, cg_max=200, omega=0.6, nu_pre=1, nu_post=1):
+def mgcg(A, b, x0, levels, eps2=1e-8, cg_max=200, omega=0.9, nu_pre=1, nu_post=1):
     """Preconditioned CG with z = V-cycle(r) (zero initial guess).
     Returns (x, iterations, relres)."""
     x = np.array(x0, dtype=np.float64, copy=True)
@@ -86,7 +86,7 @@ def orthonormal_basis_svd(R: np.ndarray, drop_tol=1e-12) -> np.ndarray:
     return U[:, s > drop_tol * s[0]]
 
 
-def mgar_basis(A, A0, levels0, t0, m, omega=0.6, nu_pre=1, nu_post=1, basis_guess="previous"):
+def mgar_basis(A, A0, levels0, t0, m, omega=0.9, nu_pre=1, nu_post=1, basis_guess="previous"):
     """Eq. 17: r_1 = t_0; r_i = one V-cycle on K0 with right-hand side
     -dK r_{i-1} and initial guess r_{i-1} (or zero)."""
     R = [np.array(t0, dtype=np.float64, copy=True)]
@@ -110,7 +110,7 @@ def reduced_solve(A, q, Rt):
     return t, res, y
 
 
-def mgar(A, A0, levels0, q, t0, m=2, omega=0.6, nu_pre=1, nu_post=1, basis_guess="previous",
+def mgar(A, A0, levels0, q, t0, m=2, omega=0.9, nu_pre=1, nu_post=1, basis_guess="previous",
          orthonormalise="gs"):
     """One MGAR reanalysis.  Returns (t~, Res)."""
     R = mgar_basis(A, A0, levels0, t0, m, omega, nu_pre, nu_post, basis_guess)

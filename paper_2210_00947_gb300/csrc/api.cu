@@ -141,6 +141,7 @@ mgar_step_info design_cycle(Ctx& c, double* rho, double* T, int cycle) {
   mgar_step_info inf{};
   inf.res = NAN;
   inf.relres = NAN;
+  inf.compliance_mgar = NAN;
   int status = MGAR_OK;
   if (c.p.filter_alpha > 0.0) {
     const double r = filter_radius(c, cycle);
@@ -154,6 +155,7 @@ mgar_step_info design_cycle(Ctx& c, double* rho, double* T, int cycle) {
     solve_mgar(c, T, c.tm, &res, &acc);  // t_prev in T, t~ in tm
     inf.res = res;
     inf.accepted = acc;
+    inf.compliance_mgar = c.mgar_cred;
     if (acc)
       MGAR_CUDA(cudaMemcpyAsync(T, c.tm, c.n * sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
     else
@@ -198,7 +200,7 @@ void mgar_default_params(mgar_params* p) {
   p->eps1 = 0.5;
   p->eps2 = 1e-8;
   p->cg_max = 200;
-  p->omega = 0.6;
+  p->omega = 0.9;
   p->nu_pre = 1;
   p->nu_post = 1;
   p->precision = MGAR_FP64;

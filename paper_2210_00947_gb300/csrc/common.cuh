@@ -60,7 +60,8 @@ enum Slot : int {
   S_KR = 32,      // 32..95 reduced matrix (8x8)
   S_QR = 96,      // 96..103 reduced right-hand side
   S_Y = 104,      // 104..111 reduced solution
-  S_RES2 = 112, S_FLAG = 113, S_QQ = 114,
+  S_RES2 = 112, S_FLAG = 113,
+  S_CRED = 114,     // MGAR: compliance of the reduced solution, q_R . y = q . t~
   S_RUCOUNT = 115,  // FP32 CG: reliable updates so far
   S_OC_LA = 116, S_OC_LB = 117, S_OC_MUA = 118, S_OC_MUB = 119, S_OC_C = 120, S_OC_B = 121,
   S_OC_MU = 122, S_OC_FAIL = 123,
@@ -151,6 +152,7 @@ struct Ctx {
   int n_gfix = 0;
   double* q = nullptr;
   double qnorm = 0.0;
+  double mgar_cred = 0.0;  // q . t~ of the last MGAR solve (Eq. 19-21)
   double* rho_phys = nullptr;
   double* ke = nullptr;     // current conductivities k_e(rho~)
   double* ke0 = nullptr;    // reference conductivities (K0)

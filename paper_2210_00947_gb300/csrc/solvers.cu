@@ -168,7 +168,13 @@ __global__ void k_reduced_solve(double* dsc, int m, int* err) {
     for (int k = i + 1; k < m; ++k) s -= L[k * kMaxM + i] * y[k];
     y[i] = s / L[i * kMaxM + i];
   }
-  for (int i = 0; i < m; ++i) dsc[S_Y + i] = y[i];
+  // the reduced solution's compliance q . t~ = q . R~ y = q_R . y (Eq. 5, 21)
+  double cred = 0.0;
+  for (int i = 0; i < m; ++i) {
+    dsc[S_Y + i] = y[i];
+    cred += dsc[S_QR + i] * y[i];
+  }
+  dsc[S_CRED] = cred;
 }
 
 // t = sum_j y_j Q_j ; ||sum_j y_j W_j - q||^2
@@ -454,8 +460,9 @@ void solve_mgar(Ctx& c, const double* T_prev, double* T, double* res, int* accep
   k_reduced_combine<<<rb, kThreads, 0, c.stream>>>(c.R, c.W, c.q, n, kept, c.dsc, T, c.partials,
                                                    c.counter, c.dsc + S_RES2);
   MGAR_LAUNCH_CHECK();
-  fetch_scalars(c, S_RES2, 1);
+  fetch_scalars(c, S_RES2, S_CRED - S_RES2 + 1);
   check_published_error(c);
+  c.mgar_cred = c.hsc[S_CRED];
   const double r = std::sqrt(c.hsc[S_RES2]) / c.qnorm;
   require(std::isfinite(r), MGAR_ERR_NONFINITE, "non-finite MGAR residual");
   if (res) *res = r;

@@ -63,12 +63,14 @@ class StepInfo(ctypes.Structure):
     _fields_ = [("compliance", ctypes.c_double), ("res", ctypes.c_double),
                 ("relres", ctypes.c_double), ("lambda_", ctypes.c_double),
                 ("used_mgcg", ctypes.c_int32), ("accepted", ctypes.c_int32),
-                ("cg_iters", ctypes.c_int32), ("status", ctypes.c_int32)]
+                ("cg_iters", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("compliance_mgar", ctypes.c_double)]
 
     def as_dict(self):
         return dict(compliance=self.compliance, res=self.res, relres=self.relres,
                     lam=self.lambda_, used_mgcg=bool(self.used_mgcg),
-                    accepted=bool(self.accepted), cg_iters=self.cg_iters, status=self.status)
+                    accepted=bool(self.accepted), cg_iters=self.cg_iters, status=self.status,
+                    compliance_mgar=self.compliance_mgar)
 
 
 _LIB = None

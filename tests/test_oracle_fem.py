@@ -107,3 +107,61 @@ def test_node_by_node_matches_assembly(dims):
     x = rng.standard_normal(g.n_nodes)
     nodes = np.arange(g.n_nodes)
     np.testing.assert_allclose(fem.apply_node(g, kv, fixed, x, nodes), A @ x, atol=1e-13)
+
+
+# ------------------------------------------------- the vectorised operator
+# apply_structured is the checker of the full-size residual test; it is pinned
+# here to the assembled matrix, to a brute-force element loop over the
+# Kronecker-built element matrix, and to the textbook solution it must map to
+# the load.
+@pytest.mark.parametrize("dims", [(7, 5, 0), (13, 1, 0), (4, 3, 5), (5, 2, 3), (1, 1, 1)])
+def test_structured_matches_assembly(dims):
+    g = fem.Grid(*dims)
+    rng = np.random.default_rng(3)
+    kv = fem.simp(rng.uniform(0.0, 1.0, g.n_elems), 1.0, 1e-3, 3.0)
+    fixed = (rng.uniform(size=g.n_nodes) < 0.15).astype(np.uint8)
+    A = fem.apply_dirichlet(fem.assemble(g, kv), fixed)
+    x = rng.standard_normal(g.n_nodes)
+    np.testing.assert_allclose(fem.apply_structured(g, kv, fixed, x), A @ x, atol=1e-13)
+
+
+@pytest.mark.parametrize("dims", [(4, 3, 0), (3, 2, 2)])
+def test_structured_matches_element_loop(dims):
+    """y_i = x_i on fixed nodes, else sum over elements e and local pairs (a, b)
+    with node_a(e) = i and node_b(e) free of k_e k0_ab x_b."""
+    g = fem.Grid(*dims)
+    dim = 2 if dims[2] == 0 else 3
+    k0 = kron_sum(dim)
+    rng = np.random.default_rng(4)
+    kv = rng.uniform(0.01, 2.0, g.n_elems)
+    fixed = (rng.uniform(size=g.n_nodes) < 0.2).astype(np.uint8)
+    x = rng.standard_normal(g.n_nodes)
+    y = np.zeros(g.n_nodes)
+    nz = max(dims[2], 1)
+    for ek in range(nz):
+        for ej in range(dims[1]):
+            for ei in range(dims[0]):
+                e = ei + dims[0] * (ej + dims[1] * ek)
+                nodes = [(ei + (a & 1)) + g.NX * ((ej + ((a >> 1) & 1)) + g.NY * (ek + ((a >> 2) & 1)))
+                         for a in range(2 ** dim)]
+                for a, na in enumerate(nodes):
+                    for b, nb in enumerate(nodes):
+                        if not fixed[na] and not fixed[nb]:
+                            y[na] += kv[e] * k0[a, b] * x[nb]
+    y[fixed == 1] = x[fixed == 1]
+    np.testing.assert_allclose(fem.apply_structured(g, kv, fixed, x), y, atol=1e-13)
+
+
+@pytest.mark.parametrize("dims", [(12, 3, 0), (8, 2, 2)])
+def test_structured_maps_exact_solution_to_load(dims):
+    """With rho = 1 and T = 0 on the x = 0 face, A applied to the nodally exact
+    T = Q (L x - x^2/2) returns the consistent load (zero on fixed nodes)."""
+    nx, ny, nz = dims
+    g = fem.Grid(nx, ny, nz)
+    x = np.arange(g.n_nodes) % g.NX
+    fixed = (x == 0).astype(np.uint8)
+    Q = 0.37
+    q = workloads.volumetric_load(nx, ny, nz, Q, fixed)
+    t = Q * (nx * x - 0.5 * x * x)
+    np.testing.assert_allclose(fem.apply_structured(g, np.ones(g.n_elems), fixed, t), q,
+                               rtol=1e-12, atol=1e-12)

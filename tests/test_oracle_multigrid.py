@@ -138,3 +138,35 @@ def test_coarse_operators_spd_with_dirichlet():
     # fixed fine nodes receive no coarse correction
     P0 = levels[0].P.toarray()
     assert np.all(P0[fixed != 0] == 0.0)
+
+
+@pytest.mark.parametrize("dim,lo,hi,at_lo", [(2, 0.75, 1.5, (0.5, 0.0)),
+                                              (3, 0.5, 1.5, (1.0, 1.0, 1.0))])
+def test_default_smoother_weight_damps_oscillatory_modes(dim, lo, hi, at_lo):
+    """The reading omega = 0.9: on a periodic unit-conductivity grid the
+    Fourier modes with some |theta_d| >= pi/2 are eigenvectors of D^-1 A with
+    eigenvalues in [lo, hi] (checked here by applying the assembled interior
+    stencil of the oracle's element matrix to sampled modes), so one damped
+    Jacobi sweep with the default weight multiplies each by at most
+    max(|1 - omega lo|, |1 - omega hi|) < 0.6."""
+    import inspect
+    omega = inspect.signature(mg.vcycle).parameters["omega"].default
+    assert omega == 0.9
+    k0 = kron_sum(dim)  # element matrix built from 1D matrices, not the oracle's
+    stencil = {}
+    for a in range(2 ** dim):
+        for b in range(2 ** dim):
+            off = tuple(((b >> d) & 1) - ((a >> d) & 1) for d in range(dim))
+            stencil[off] = stencil.get(off, 0.0) + k0[a, b]
+    diag = stencil[(0,) * dim]
+    rng = np.random.default_rng(0)
+    thetas = rng.uniform(-np.pi, np.pi, (4000, dim))
+    thetas[:, 0] = np.where(np.abs(thetas[:, 0]) < np.pi / 2, np.pi, thetas[:, 0])
+    lam = np.array([sum(v * np.cos(np.dot(o, t)) for o, v in stencil.items()) / diag
+                    for t in thetas])
+    assert lam.min() >= lo - 1e-12 and lam.max() <= hi + 1e-12
+    # the extremes are reached: hi at theta = (pi, 0, ...), lo at at_lo * pi
+    for t, want in ((np.pi * np.eye(dim)[0], hi), (np.pi * np.array(at_lo), lo)):
+        v = sum(c * np.cos(np.dot(o, t)) for o, c in stencil.items()) / diag
+        assert abs(v - want) < 1e-12
+    assert max(abs(1 - omega * lo), abs(1 - omega * hi)) < 0.6
