@@ -26,7 +26,10 @@ std::mutex g_noalloc_mutex;
 double* g_noalloc_ptr[kMaxDevices] = {};
 
 // Device address of the scratch array on the current device, looked up once
-// per device (the host-side symbol is only a stand-in, not an address).
+// per device (the host-side symbol is only a stand-in, not an address).  The
+// cached address belongs to the device's primary context as it was at the
+// lookup: after cudaDeviceReset it is stale, so this entry point does not
+// support a device reset during the life of the process.
 int scratch_address(double** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MGAR_ERR_CUDA;
@@ -112,6 +115,9 @@ extern "C" int mgar_sensitivity_noalloc(const mgar_params* p, const double* rho_
   const int dim = p->nz == 0 ? 2 : 3;
   const int64_t ex = p->nx, ey = p->ny, ez = dim == 3 ? p->nz : 1;
   if (ex < 1 || ey < 1 || ez < 1 || !(p->rmin > 0.0) || p->rmin > 8.0) return MGAR_ERR_ARG;
+  // the filter is the fixed-radius one of radius rmin: a continuation
+  // schedule (filter_alpha > 0) belongs to a handle's loop and is refused
+  if (p->filter_alpha > 0.0) return MGAR_ERR_ARG;
   const int64_t ne = ex * ey * ez;
   if (ne > kNoAllocMaxElems) return MGAR_ERR_TOO_LARGE;  // beyond the static scratch array
   double* scratch = nullptr;
