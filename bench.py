@@ -54,6 +54,8 @@ def parse():
                     help="skip the paper-setting MGAR legs (eps1 = 0.5, both readings)")
     ap.add_argument("--cpu-all-cores", action="store_true",
                     help="also time the oracle with BLAS/OpenMP on every host core")
+    ap.add_argument("--cpu-cycles", type=int, default=1,
+                    help="design cycles of the oracle's loop in the CPU baseline")
     ap.add_argument("--kernel", default=None,
                     choices=["df3d", "apply64", "apply32", "resid64", "smooth0", "galerkin0"],
                     help="kernel class of the roofline (default: the dominant one of the path)")
@@ -523,10 +525,21 @@ def run_gpu(args):
         "gpu_launches": launches, "roofline": roof, "clocks": clocks,
     }
     if rank == 0 and not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(args.workload, cycles=1)
+        cb = cpu_baseline(args.workload, cycles=args.cpu_cycles)
+        # the oracle's own loop from the same rho0: its compliances beside the
+        # timed path's for the cycles it ran (free-running, each side its own
+        # trajectory)
+        oc = cb.pop("compliance", None)
+        line["cpu_baseline"] = cb
+        if oc:
+            errs = [abs(i["compliance"] - c) / abs(c) for i, c in zip(infos, oc)]
+            line["oracle_compliance"] = {"cycles": len(errs), "max_rel_err": max(errs),
+                                         "rel_err": errs,
+                                         "note": "oracle loop and timed path, each from rho0"}
         if args.cpu_all_cores:
-            line["cpu_baseline_all_cores"] = cpu_baseline(args.workload, cycles=1,
-                                                          threads=os.cpu_count() or 1)
+            cba = cpu_baseline(args.workload, cycles=args.cpu_cycles, threads=os.cpu_count() or 1)
+            cba.pop("compliance", None)
+            line["cpu_baseline_all_cores"] = cba
     if rank == 0:
         print(json.dumps(line), flush=True)
     solver.close()
@@ -571,6 +584,7 @@ def cpu_baseline(name, cycles=1, threads=1):
     cyc = json.loads(res.stdout.strip().splitlines()[-1])
     ms = 1e3 * statistics.mean(c["seconds"] for c in cyc)
     return {"value": ms, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "compliance": [c["compliance"] for c in cyc],
             "sample": f"design cycles 1..{cycles} of {name} (MGCG cycles incl. assembly and "
                       f"hierarchy), mean per cycle, numpy/scipy FP64, BLAS/OpenMP threads "
                       f"{threads} (scipy.sparse kernels run on one thread regardless)"}
@@ -584,6 +598,7 @@ def run_reference(args):
     times = []
     for i in range(args.warmup + args.steps):
         b = cpu_baseline(args.workload, cycles=1)
+        b.pop("compliance", None)
         if b["value"] is None:
             print(json.dumps({"impl": "reference", "unavailable": b["sample"]}))
             return

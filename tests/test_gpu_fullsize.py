@@ -113,3 +113,17 @@ def test_fullsize_oc_keeps_the_volume_and_the_update_rule(cycle1):
         cand = r0 * np.sqrt(max(-c["dc"][e], 0.0) / (lam * c["dv"][e]))
         expect = min(max(cand, max(0.0, r0 - w.move)), min(1.0, r0 + w.move))
         assert abs(c["rho"][e] - expect) <= 1e-9, e
+
+
+def test_heat2d_1024_stepwise_against_the_oracle():
+    """The 1024^2 Q4 workload (1,050,625 nodes, nl 7), mixed path, stepwise
+    against the oracle's loop for 10 design cycles: MGCG in cycles 1-6, then
+    MGAR attempts with the zero-guess basis of Eq. 17 (rejected at the
+    paper's eps1 = 0.5, Res 2.4-2.9 here) and the MGCG fallback.  Every
+    cycle's compliance and every attempt's reduced compliance within 1e-6
+    of the oracle's."""
+    from test_gpu_loop import check_mixed, run_stepwise
+    out = run_stepwise(1024, 1024, 0, nl=7, iters=10, n_on=7, precision=mgar.MGAR_MIXED,
+                       eps1=0.5, eps2=1e-10, guess="zero")
+    check_mixed(out, 10, 0.5, 1e-6, 0)
+    assert sum(1 for e in out if e[2]["res"] == e[2]["res"]) == 4  # four attempts compared
