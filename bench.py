@@ -80,6 +80,9 @@ def parse():
     ap.add_argument("--autograd", default=None,
                     help="time the differentiable compliance (forward solve + adjoint gradient) "
                          "on this workload; one JSON line")
+    ap.add_argument("--random-density", action="store_true",
+                    help="autograd: start from i.i.d. U[0.05, 1] densities (the differentiation "
+                         "workload) instead of the workload's uniform field")
     ap.add_argument("--replay-precisions", default="mixed,fp64")
     ap.add_argument("--replay-guesses", default="previous,zero")
     return ap.parse_args()
@@ -721,20 +724,30 @@ def run_replay(args):
 
 def run_batch(args):
     """Independent designs (the workload module's seeded uneven 2D set): the
-    same designs once one after another and once `--batch-workers` at a
-    time, each with its own handle, stream and host thread."""
+    batched solve (one launch per V-cycle level and operation over all
+    designs, one CUDA graph per solve, autotuned V-cycle block sizes), against
+    the same designs run concurrently with one handle, stream and host thread
+    each, and one after another."""
     from paper_2210_00947_gb300 import batch, mgar
 
     world, rank, local = dist_setup(args)
     designs = shard(batch.designs_from_workload(args.batch), rank, world)
     cycles = args.cycles or 30
     prec = mgar.MGAR_MIXED if args.precision == "mixed" else mgar.MGAR_FP64
-    batch.run_designs(designs[:2], cycles=2, workers=2, precision=prec, device=local)  # warm-up
-    seq, t_seq = batch.run_designs(designs, cycles=cycles, workers=1, precision=prec,
-                                   device=local)
+    # warm-up: library load, graphs of a small set
+    batch.run_designs_batched(designs[:2], cycles=2, workers=2, device=local)
+    batch.run_designs(designs[:2], cycles=2, workers=2, precision=prec, device=local)
+    bat, t_bat, report = batch.run_designs_batched(designs, cycles=cycles,
+                                                   workers=args.batch_workers, device=local)
+    n_on = {"n_on": cycles + 1}  # MGCG in every cycle, as the batched run
     par, t_par = batch.run_designs(designs, cycles=cycles, workers=args.batch_workers,
-                                   precision=prec, device=local)
+                                   precision=prec, device=local, **n_on)
+    seq, t_seq = batch.run_designs(designs, cycles=cycles, workers=1, precision=prec,
+                                   device=local, **n_on)
     same = all(np.array_equal(a[0], b[0]) for a, b in zip(seq, par))
+    diff = max(abs(hb["compliance"] - hp["compliance"]) / abs(hp["compliance"])
+               for (_, hsb), (_, hsp) in zip(bat, par) for hb, hp in zip(hsb, hsp))
+    t_bat = max_over_ranks(t_bat, world)
     t_seq = max_over_ranks(t_seq, world)
     t_par = max_over_ranks(t_par, world)
     total = args.batch * cycles
@@ -743,11 +756,20 @@ def run_batch(args):
     line = {"batch": args.batch, "n_gpus": world, "cycles": cycles, "precision": args.precision,
             "dofs_total": sum((d.nx + 1) * (d.ny + 1)
                               for d in batch.designs_from_workload(args.batch)),
-            "sequential_s": t_seq, "concurrent_s": t_par, "workers": args.batch_workers,
-            "design_cycles_per_s": total / t_par, "speedup": t_seq / t_par,
-            "identical_results": same,
-            "timing": "host wall clock from the start of the first run to the end of the last",
-            "data": "synthetic (seeded uneven 2D designs)"}
+            "batched": {"seconds": t_bat, "design_cycles_per_s": total / t_bat,
+                        "nl": 5, "solve": "one launch per V-cycle level and operation over all "
+                                          "designs, FP32 V-cycle and FP64 CG in one CUDA graph",
+                        "cg_iters_mean": statistics.mean(h["cg_iters"] for _, hs in bat
+                                                         for h in hs),
+                        "autotuner": [l for l in report.splitlines() if not l.startswith("  ")]},
+            "per_handle_concurrent": {"seconds": t_par, "design_cycles_per_s": total / t_par,
+                                      "workers": args.batch_workers},
+            "one_after_another": {"seconds": t_seq, "design_cycles_per_s": total / t_seq},
+            "speedup_batched_vs_one_after_another": t_seq / t_bat,
+            "identical_results_concurrent_vs_sequential": same,
+            "max_rel_compliance_diff_batched_vs_per_handle": diff,
+            "timing": "host wall clock from the start of the first cycle to the end of the last",
+            "data": "synthetic (seeded uneven 2D designs, sides 64-512)"}
     print(json.dumps(line), flush=True)
 
 
@@ -763,7 +785,10 @@ def run_autograd(args):
     dev = torch.device("cuda", 0)
     prec = mgar.MGAR_MIXED if args.precision == "mixed" else mgar.MGAR_FP64
     comp = autograd.Compliance(mgar.params_for(w, precision=prec), w.fixed(), w.q())
-    rho = torch.tensor(w.density(), device=dev, requires_grad=True)
+    # the differentiation workload starts from i.i.d. U[0.05, 1] densities
+    rho0 = (workloads.random_density(w.n_elems, 0.05, 1.0, seed=2210) if args.random_density
+            else w.density())
+    rho = torch.tensor(rho0, device=dev, requires_grad=True)
     stream = torch.cuda.current_stream(dev)
     times = []
     for step in range(args.warmup + args.steps):
@@ -780,11 +805,36 @@ def run_autograd(args):
         with torch.no_grad():  # a small descent step, so each solve starts warm but not converged
             rho -= 1e-3 * rho.grad / rho.grad.abs().max()
             rho.clamp_(1e-3, 1.0)
-    line = {"autograd": args.autograd, "dofs": w.n_nodes, "precision": args.precision,
-            "ms_forward_backward": statistics.mean(times), "steps": args.steps,
-            "compliance": c.item(), "data": "synthetic"}
-    print(json.dumps(line), flush=True)
     comp.close()
+    # then the workload's design cycles of the MGAR loop (Figure 5) from the same
+    # starting field, mixed precision, zero-guess basis of Eq. 17, eps1 0.5
+    cycles = args.cycles or w.iters
+    sp = mgar.Solver(mgar.params_for(w, precision=prec, basis_guess=mgar.MGAR_GUESS_ZERO),
+                     w.fixed(), w.q(), stream=stream)
+    r = torch.tensor(rho0, device=dev)
+    T = torch.zeros(sp.n_nodes, dtype=torch.float64, device=dev)
+    sp.step(r, T, 1)  # graphs and buffers
+    r.copy_(torch.tensor(rho0, device=dev))
+    T.zero_()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    infos = [sp.step(r, T, k) for k in range(1, cycles + 1)]
+    b.record(stream)
+    b.synchronize()
+    sp.close()
+    line = {"autograd": args.autograd, "dofs": w.n_nodes, "precision": args.precision,
+            "density": "iid U[0.05, 1], SplitMix64(2210)" if args.random_density else "uniform",
+            "ms_forward_backward": statistics.mean(times), "steps": args.steps,
+            "compliance": c.item(),
+            "mgar_loop": {"cycles": cycles, "ms_per_iteration": a.elapsed_time(b) / cycles,
+                          "n_on": w.n_on, "basis_guess": "zero", "eps1": w.eps1,
+                          "mgar_accepted": sum(1 for i in infos if i["accepted"]),
+                          "cg_iters_mean": statistics.mean(
+                              [i["cg_iters"] for i in infos if i["used_mgcg"]] or [0]),
+                          "final_compliance": infos[-1]["compliance"]},
+            "data": "synthetic"}
+    print(json.dumps(line), flush=True)
 
 
 def run_postprocess(args):

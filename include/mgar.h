@@ -137,6 +137,15 @@ int mgar_filter(mgar_t h, const double* in, double* out, int transpose);
  * derived here; the multigrid hierarchy is not touched. */
 int mgar_set_density(mgar_t h, const double* rho, int is_physical);
 
+/* Replace the nodal heat load q of Eq. 3 (the right-hand side of every
+ * later MGCG / MGAR solve, the compliance of Eq. 5 and the Res of Eq. 28).
+ *   q: device, n doubles, copied; entries on fixed nodes are treated as zero.
+ * A solve for another right-hand side, such as the difference solve
+ * (K + dK) dt = -dK t of a finite-difference check, sets its load here and
+ * the original one back afterwards.  Errors: MGAR_ERR_ARG when q is NULL or
+ * zero on every free node. */
+int mgar_set_load(mgar_t h, const double* q);
+
 /* y = A(rho~) x for the current design (Eq. 3, fixed nodes eliminated).
  *   x, y: device, n doubles, must not overlap. */
 int mgar_apply_K(mgar_t h, const double* x, double* y);
@@ -258,6 +267,51 @@ int mgar_profile_report(mgar_t h, char* buf, int64_t len);
 /* Number of kernels this library has launched in this process (all
  * handles), for accounting in benchmarks. */
 int64_t mgar_kernel_launches(void);
+
+/* Batched MGCG over many independent 2D designs (Section 3.2's solve with
+ * the Table 1 V-cycle as preconditioner), each design a handle of its own
+ * (its grid, sink, load, density and parameters).  A batch holds no copy of
+ * the designs' data, only device tables of their sizes and buffers: every
+ * step of the solve is one launch over all designs (one per V-cycle level
+ * and operation), the outer CG runs in FP64 around the FP32 V-cycle, and
+ * the solve after the hierarchy builds is one CUDA graph that iterates while
+ * any design is unconverged.  The V-cycle kernels' block sizes come from an
+ * autotuner at the first solve (mgar_batch_report lists its timings and
+ * choices); no choice changes a result, and each design's result does not
+ * depend on the other designs in the batch. */
+typedef struct mgar_batch_ctx* mgar_batch_t;
+
+/* Create a batch over `count` handles (host array), all 2D and created with
+ * MGAR_MIXED; a handle may appear once.  The handles must outlive the batch
+ * and must not be used by other calls while a batch call runs.  Work is
+ * ordered on `stream` (cudaStream_t, NULL = legacy default).
+ * Errors: MGAR_ERR_ARG (bad arguments, 3D or FP64 handles), MGAR_ERR_CUDA. */
+int mgar_batch_create(mgar_batch_t* out, const mgar_t* handles, int count, void* stream);
+
+/* Release the batch (not its handles).  b may be NULL. */
+int mgar_batch_destroy(mgar_batch_t b);
+
+/* Text of the batch's last error (b = NULL: of the last failed create). */
+const char* mgar_batch_last_error(mgar_batch_t b);
+
+/* Solve A(rho~_d) T_d = q_d for every design d of the batch at its current
+ * density (mgar_set_density), as mgar_solve_mgcg does for one handle: each
+ * handle's hierarchy is rebuilt from its design (K0 <- K), then the
+ * preconditioned CG runs until the design's ||r|| / ||q|| <= eps2 or its
+ * cg_max, designs finishing independently.
+ *   T: host array of `count` device pointers, each n_d doubles: warm start
+ *      in, solution out.
+ *   iters, relres, status: host arrays of `count` entries, each may be NULL;
+ *      status[d] is MGAR_OK, MGAR_ERR_MAXIT or MGAR_ERR_NONFINITE.
+ * Returns MGAR_OK, or the worst per-design status (solutions still written),
+ * or MGAR_ERR_NOT_SPD when a coarsest factorisation failed.  Synchronises
+ * the stream. */
+int mgar_batch_solve_mgcg(mgar_batch_t b, double* const* T, int* iters, double* relres,
+                          int* status);
+
+/* The autotuner's timings and choices as text (empty before the first
+ * solve), written to buf (host, len bytes, NUL-terminated). */
+int mgar_batch_report(mgar_batch_t b, char* buf, int64_t len);
 
 /* Design sensitivities dc, as mgar_sensitivity computes them, for callers
  * that cannot allocate device memory (no counterpart in the paper): code

@@ -1,0 +1,852 @@
+// Batched MGCG over many independent 2D designs (Section 3.2's solve with
+// Table 1's V-cycle as preconditioner), for the uneven designs of a batch.
+//
+// Every handle keeps its own data (conductivities, hierarchy, vectors); the
+// batch only holds device tables of their pointers and sizes.  Each step of
+// the solve is one launch over all designs: block b of a launch belongs to
+// design bdes[b], and its nodes are (b - b0[design]) * blockDim + thread of
+// that design's level.  So one launch per V-cycle level and operation serves
+// every design, and the designs' different depths only decide which of them
+// take part in a level (a design's coarsest level is solved by one launch
+// over all designs' coarsest levels).  The outer CG runs in FP64 around the
+// FP32 V-cycle (FP32 preconditioner, FP64 refinement); its per-design scalars
+// stay on the device, a design stops when its own ||r|| / ||q|| <= eps2 or
+// at cg_max (its blocks then leave at once), and the whole solve after the
+// hierarchy builds is one CUDA graph: a WHILE node repeats the iteration
+// while any design is still active.
+//
+// Reductions are per design in a fixed order (each design's blocks write
+// partials, the design's last block adds them in block order), and the
+// reduction kernels use a fixed block size, so a design's result does not
+// depend on the other designs in the batch.  The node kernels of the
+// V-cycle (no reductions) take their block size per level from an
+// autotuner run at the first solve, which times the candidates on the
+// batch's own levels and keeps the fastest.
+#include "common.cuh"
+#include "levelops.cuh"
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+namespace mgar {
+namespace bat {
+
+constexpr int kRedThreads = 256;  // block size of every reducing kernel
+constexpr int kBS = 16;           // device scalars per design
+enum : int { BS_RZ = 0, BS_PAP = 2, BS_RR = 3, BS_IT = 4, BS_ACT = 5, BS_QN = 6, BS_EPS = 7,
+             BS_CGMAX = 8, BS_BAD = 9 };
+
+// One design at one level of the V-cycle.
+struct Lev {
+  FineOp<float> f0;      // level 0: FP32 reference conductivities (matrix-free)
+  StencilOp<float> op;   // levels >= 1: assembled stencil and 1/diag
+  Dims d, dn;            // this level and the next coarser one
+  const float* dinv;     // this level's 1/diag
+  const float* dinv_n;   // the next level's 1/diag
+  float *x, *b, *t, *r;  // level 0: x = V-cycle result, b = its input
+  float *bn, *xn;        // the next level's b, and its x (null when it is the coarsest)
+  const float* resn;     // the next level's result (x at the coarsest, t above)
+  const uint8_t* fixed;  // level 0: Dirichlet mask
+  float omega;
+};
+
+struct Coarse {
+  const double* cinv;  // explicit inverse of the design's coarsest operator (FP64)
+  const float* b;
+  float* x;
+  int nc;
+};
+
+struct Des {
+  FineOp<double> f;    // current conductivities (FP64, matrix-free)
+  const double* q;
+  double *x, *r, *z, *p, *Ap;
+  float *b32, *x32;    // FP32 input and output of the V-cycle at level 0
+};
+
+// Launch shape: which design each block serves.
+struct Shape {
+  int threads = kRedThreads;
+  int nblocks = 0;
+  int* bdes = nullptr;  // [nblocks]
+  int* b0 = nullptr;    // [designs]: first block of the design, -1 if absent
+};
+
+__device__ __forceinline__ bool active(const double* bsc, int d) { return bsc[d * kBS + BS_ACT] != 0.0; }
+
+// Deterministic per-design sum: the design's blocks write partials, its last
+// block adds them in block order into *out.
+template <int N>
+__device__ __forceinline__ void seg_finish(double (&v)[N], double* partials, unsigned int* counters,
+                                           int d, int b0, int nb, double* out) {
+  double t[N];
+  if (block_sum_last_ids<N>(v, partials + (size_t)N * b0, counters + d, t, threadIdx.x, blockDim.x,
+                            blockIdx.x - b0, nb) &&
+      threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) out[k] = t[k];
+  }
+}
+
+// ------------------------------------------------------------ FP64 CG kernels
+// Per design: scalars of this solve, iteration 0, active.
+__global__ void kb_init(double* bsc, const double* consts, int nd) {
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= nd) return;
+  double* s = bsc + d * kBS;
+  s[BS_IT] = 0.0;
+  s[BS_ACT] = 1.0;
+  s[BS_BAD] = 0.0;
+  s[BS_QN] = consts[3 * d];
+  s[BS_EPS] = consts[3 * d + 1];
+  s[BS_CGMAX] = consts[3 * d + 2];
+}
+
+// r = q - A x, its FP32 copy, ||r||^2 (the start of each design's CG).
+__global__ void kb_resid64(const Des* D, const int* bdes, const int* b0, double* bsc,
+                           double* partials, unsigned int* counters) {
+  const int d = bdes[blockIdx.x];
+  const Des& g = D[d];
+  const int nb = (g.f.n + blockDim.x - 1) / blockDim.x;
+  const int idx = (blockIdx.x - b0[d]) * blockDim.x + threadIdx.x;
+  double v[1] = {0.0};
+  if (idx < g.f.n) {
+    int i, j, k;
+    coords(idx, g.f.fNX, g.f.fNXY, i, j, k);
+    double diag;
+    const double ri = g.q[idx] - fine_row2(g.f, g.x, i, j, diag);
+    g.r[idx] = ri;
+    g.b32[idx] = (float)ri;
+    v[0] = ri * ri;
+  }
+  seg_finish<1>(v, partials, counters, d, b0[d], nb, bsc + d * kBS + BS_RR);
+}
+
+// After the initial residual: a design whose start already meets eps2 (or
+// whose cg_max is 0) is done; a non-finite residual stops it and is flagged.
+__global__ void kb_start(double* bsc, int nd) {
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= nd) return;
+  double* s = bsc + d * kBS;
+  const double rel = sqrt(s[BS_RR]) / s[BS_QN];
+  if (!isfinite(rel)) s[BS_BAD] = 1.0;
+  s[BS_ACT] = (isfinite(rel) && rel > s[BS_EPS] && s[BS_CGMAX] > 0.0) ? 1.0 : 0.0;
+}
+
+// Ap = A p and p . Ap.
+__global__ void kb_apply_dot(const Des* D, const int* bdes, const int* b0, double* bsc,
+                             double* partials, unsigned int* counters) {
+  const int d = bdes[blockIdx.x];
+  if (!active(bsc, d)) return;
+  const Des& g = D[d];
+  const int nb = (g.f.n + blockDim.x - 1) / blockDim.x;
+  const int idx = (blockIdx.x - b0[d]) * blockDim.x + threadIdx.x;
+  double v[1] = {0.0};
+  if (idx < g.f.n) {
+    int i, j, k;
+    coords(idx, g.f.fNX, g.f.fNXY, i, j, k);
+    double diag;
+    const double ap = fine_row2(g.f, g.p, i, j, diag);
+    g.Ap[idx] = ap;
+    v[0] = g.p[idx] * ap;
+  }
+  seg_finish<1>(v, partials, counters, d, b0[d], nb, bsc + d * kBS + BS_PAP);
+}
+
+// alpha = r.z / p.Ap; x += alpha p; r -= alpha Ap; ||r||^2; FP32 copy of r.
+__global__ void kb_cg_xr(const Des* D, const int* bdes, const int* b0, double* bsc,
+                         double* partials, unsigned int* counters) {
+  const int d = bdes[blockIdx.x];
+  if (!active(bsc, d)) return;
+  const Des& g = D[d];
+  const double* s = bsc + d * kBS;
+  const int par = ((int)s[BS_IT]) & 1;
+  const double alpha = block_div(s + BS_RZ + par, s + BS_PAP);
+  const int nb = (g.f.n + blockDim.x - 1) / blockDim.x;
+  const int idx = (blockIdx.x - b0[d]) * blockDim.x + threadIdx.x;
+  double v[1] = {0.0};
+  if (idx < g.f.n) {
+    g.x[idx] += alpha * g.p[idx];
+    const double ri = g.r[idx] - alpha * g.Ap[idx];
+    g.r[idx] = ri;
+    g.b32[idx] = (float)ri;
+    v[0] = ri * ri;
+  }
+  seg_finish<1>(v, partials, counters, d, b0[d], nb, bsc + d * kBS + BS_RR);
+}
+
+// One iteration done: count it and decide, per design, whether to go on;
+// the WHILE node repeats while any design is active.
+__global__ void kb_check(double* bsc, int nd, cudaGraphConditionalHandle loop) {
+  __shared__ int any;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  for (int d = threadIdx.x; d < nd; d += blockDim.x) {
+    double* s = bsc + d * kBS;
+    if (s[BS_ACT] == 0.0) continue;
+    const double it = s[BS_IT] + 1.0;
+    s[BS_IT] = it;
+    const double rel = sqrt(s[BS_RR]) / s[BS_QN];
+    if (!isfinite(rel)) s[BS_BAD] = 1.0;
+    const bool go = isfinite(rel) && rel > s[BS_EPS] && it < s[BS_CGMAX];
+    s[BS_ACT] = go ? 1.0 : 0.0;
+    if (go) atomicOr(&any, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) cudaGraphSetConditional(loop, any ? 1u : 0u);
+}
+
+// p = z + (r.z_new / r.z_old) p (p = z in the first iteration).
+__global__ void kb_cg_p(const Des* D, const int* bdes, const int* b0, const double* bsc) {
+  const int d = bdes[blockIdx.x];
+  if (!active(bsc, d)) return;
+  const Des& g = D[d];
+  const double* s = bsc + d * kBS;
+  const int it = (int)s[BS_IT];
+  const double beta = it == 0 ? 0.0 : block_div(s + BS_RZ + (it & 1), s + BS_RZ + ((it - 1) & 1));
+  const int idx = (blockIdx.x - b0[d]) * blockDim.x + threadIdx.x;
+  if (idx < g.f.n) g.p[idx] = it == 0 ? g.z[idx] : g.z[idx] + beta * g.p[idx];
+}
+
+// --------------------------------------------------------- V-cycle kernels
+// The design and node of a thread of a level launch (false: nothing to do).
+__device__ __forceinline__ bool lev_node(const int* bdes, const int* b0, const double* bsc, int& d,
+                                         int& idx) {
+  d = bdes[blockIdx.x];
+  if (!active(bsc, d)) return false;
+  idx = (blockIdx.x - b0[d]) * blockDim.x + threadIdx.x;
+  return true;
+}
+
+// level 0, zero initial guess: t = w D^-1 b
+__global__ void kb_jz0(const Lev* L, const int* bdes, const int* b0, const double* bsc) {
+  int d, idx;
+  if (!lev_node(bdes, b0, bsc, d, idx)) return;
+  const Lev& v = L[d];
+  if (idx < v.d.n) v.t[idx] = v.omega * v.dinv[idx] * v.b[idx];
+}
+
+// level 0: r = b - A t (matrix-free FP32 operator)
+__global__ void kb_resid0(const Lev* L, const int* bdes, const int* b0, const double* bsc) {
+  int d, idx;
+  if (!lev_node(bdes, b0, bsc, d, idx)) return;
+  const Lev& v = L[d];
+  if (idx >= v.d.n) return;
+  int i, j, k;
+  coords(idx, v.f0.fNX, v.f0.fNXY, i, j, k);
+  float diag;
+  v.r[idx] = v.b[idx] - fine_row2(v.f0, v.t, i, j, diag);
+}
+
+// b_next = P^T r (fixed fine nodes excluded at level 0), and the next level's
+// zero-guess sweep x_next = w D^-1 b_next unless it is the coarsest
+__global__ void kb_restrict(const Lev* L, const int* bdes, const int* b0, const double* bsc) {
+  int d, idx;
+  if (!lev_node(bdes, b0, bsc, d, idx)) return;
+  const Lev& v = L[d];
+  if (idx < v.dn.n)
+    restrict_node<float, 2, false>(v.r, v.bn, v.d, v.dn, v.fixed, idx, v.dinv_n, v.omega, v.xn);
+}
+
+// levels >= 1 above the coarsest: r = b - A x (x left by the restriction)
+__global__ void kb_resid(const Lev* L, const int* bdes, const int* b0, const double* bsc) {
+  int d, idx;
+  if (!lev_node(bdes, b0, bsc, d, idx)) return;
+  const Lev& v = L[d];
+  if (idx < v.d.n) resid_node<float, 2, false>(v.op, v.b, v.x, v.r, idx);
+}
+
+// each design's coarsest level: x = C b, one warp per row
+__global__ void kb_coarse(const Coarse* C, const int* bdes, const int* b0, const double* bsc) {
+  const int d = bdes[blockIdx.x];
+  if (!active(bsc, d)) return;
+  const Coarse& c = C[d];
+  const int wpb = blockDim.x >> 5;
+  const int row = (blockIdx.x - b0[d]) * wpb + (threadIdx.x >> 5);
+  if (row < c.nc) coarse_row<float, false, double>(c.cinv, c.b, c.x, c.nc, row, threadIdx.x & 31);
+}
+
+// levels >= 1 above the coarsest: t = post-smoothing of x + P res_next
+__global__ void kb_post(const Lev* L, const int* bdes, const int* b0, const double* bsc) {
+  int d, idx;
+  if (!lev_node(bdes, b0, bsc, d, idx)) return;
+  const Lev& v = L[d];
+  if (idx < v.d.n)
+    post_node<float, 2, false>(v.op, v.resn, v.x, v.b, v.dinv, v.omega, v.t, v.d, v.dn, idx);
+}
+
+// level 0: t += P res_1 (fixed nodes keep t)
+__global__ void kb_prolong0(const Lev* L, const int* bdes, const int* b0, const double* bsc) {
+  int d, idx;
+  if (!lev_node(bdes, b0, bsc, d, idx)) return;
+  const Lev& v = L[d];
+  if (idx < v.d.n) prolong_node<float, 2>(v.resn, v.t, v.t, v.d, v.dn, v.fixed, idx);
+}
+
+// level 0: x = t + w D^-1 (b - A t), z = x in FP64 and r . z (the CG's new
+// r.z, slot by iteration parity)
+__global__ void kb_sweep0(const Lev* L, const Des* D, const int* bdes, const int* b0,
+                          double* bsc, double* partials, unsigned int* counters) {
+  const int d = bdes[blockIdx.x];
+  if (!active(bsc, d)) return;
+  const Lev& v = L[d];
+  const Des& g = D[d];
+  const int nb = (v.d.n + blockDim.x - 1) / blockDim.x;
+  const int idx = (blockIdx.x - b0[d]) * blockDim.x + threadIdx.x;
+  double s[1] = {0.0};
+  if (idx < v.d.n) {
+    int i, j, k;
+    coords(idx, v.f0.fNX, v.f0.fNXY, i, j, k);
+    float diag;
+    const float ti = v.t[idx];
+    const float xo = ti + v.omega * v.dinv[idx] * (v.b[idx] - fine_row2(v.f0, v.t, i, j, diag));
+    v.x[idx] = xo;
+    const double zi = (double)xo;
+    g.z[idx] = zi;
+    s[0] = g.r[idx] * zi;
+  }
+  const int par = ((int)bsc[d * kBS + BS_IT]) & 1;
+  seg_finish<1>(s, partials, counters, d, b0[d], nb, bsc + d * kBS + BS_RZ + par);
+}
+
+// ------------------------------------------------------------------- host
+struct Batch {
+  std::vector<Ctx*> h;
+  int nd = 0, lmax = 0;
+  cudaStream_t stream = nullptr, cap = nullptr;
+  std::string err;
+  Lev* dlev = nullptr;  // [lmax][nd]
+  Coarse* dco = nullptr;
+  Des* ddes = nullptr;
+  std::vector<Des> hdes;       // host copy of the design table
+  double* bsc = nullptr;       // [nd][kBS]
+  double* consts = nullptr;    // [nd][3] qnorm, eps2, cg_max (device)
+  double* hconsts = nullptr;   // pinned
+  double* hbsc = nullptr;      // pinned
+  double* partials = nullptr;
+  unsigned int* counters = nullptr;
+  Shape s_red;                 // level 0, reducing kernels
+  std::vector<int> tuned;      // threads per level (node kernels); [lmax] + coarse warps last
+  std::vector<Shape> shapes;   // all shapes made (freed at destroy)
+  // per level l: nodes of l (designs with a level below l), nodes of l + 1
+  std::vector<Shape> s_node, s_next;
+  Shape s_coarse;
+  cudaGraphExec_t exec = nullptr;
+  int64_t prologue = 0, body = 0;
+  std::string report;
+};
+
+static void free_shape(Shape& s) {
+  cudaFree(s.bdes);
+  cudaFree(s.b0);
+  s.bdes = s.b0 = nullptr;
+}
+
+// A shape over per-design unit counts (0: the design takes no part).
+static Shape make_shape(const std::vector<int64_t>& units, int per_block, int threads) {
+  Shape s;
+  s.threads = threads;
+  std::vector<int> bdes, b0(units.size(), -1);
+  for (size_t d = 0; d < units.size(); ++d) {
+    if (units[d] <= 0) continue;
+    b0[d] = (int)bdes.size();
+    const int64_t nb = (units[d] + per_block - 1) / per_block;
+    for (int64_t k = 0; k < nb; ++k) bdes.push_back((int)d);
+  }
+  s.nblocks = (int)bdes.size();
+  MGAR_CUDA(cudaMalloc(&s.b0, b0.size() * sizeof(int)));
+  MGAR_CUDA(cudaMemcpy(s.b0, b0.data(), b0.size() * sizeof(int), cudaMemcpyHostToDevice));
+  if (s.nblocks > 0) {
+    MGAR_CUDA(cudaMalloc(&s.bdes, bdes.size() * sizeof(int)));
+    MGAR_CUDA(cudaMemcpy(s.bdes, bdes.data(), bdes.size() * sizeof(int), cudaMemcpyHostToDevice));
+  }
+  return s;
+}
+
+// Nodes of level l per design for the level's own kernels (designs for
+// which l is above the coarsest), or of level l + 1 (its restriction).
+static std::vector<int64_t> level_units(const Batch& b, int l, bool next) {
+  std::vector<int64_t> u(b.nd, 0);
+  for (int d = 0; d < b.nd; ++d) {
+    const Ctx& c = *b.h[d];
+    if (l + 1 < c.nl) u[d] = next ? c.L[l + 1].n : c.L[l].n;
+  }
+  return u;
+}
+
+static void make_level_shapes(Batch& b, int l, int threads) {
+  free_shape(b.s_node[l]);
+  free_shape(b.s_next[l]);
+  b.s_node[l] = make_shape(level_units(b, l, false), threads, threads);
+  b.s_next[l] = make_shape(level_units(b, l, true), threads, threads);
+}
+
+static void make_coarse_shape(Batch& b, int warps) {
+  free_shape(b.s_coarse);
+  std::vector<int64_t> rows(b.nd);
+  for (int d = 0; d < b.nd; ++d) rows[d] = b.h[d]->nc;
+  b.s_coarse = make_shape(rows, warps, warps * 32);
+}
+
+template <typename K, typename... Args>
+static void launch_shape(Batch& b, const Shape& s, K kernel, Args... args) {
+  if (s.nblocks == 0) return;
+  kernel<<<s.nblocks, s.threads, 0, b.stream>>>(args..., s.bdes, s.b0, b.bsc);
+  MGAR_LAUNCH_CHECK();
+}
+
+// The FP32 V-cycle z = M r of every active design (Table 1, zero guess).
+static void vcycle(Batch& b) {
+  Lev* L0 = b.dlev;
+  // down
+  for (int l = 0; l + 1 < b.lmax; ++l) {
+    Lev* L = b.dlev + (size_t)l * b.nd;
+    if (l == 0) {
+      launch_shape(b, b.s_node[0], kb_jz0, (const Lev*)L);
+      launch_shape(b, b.s_node[0], kb_resid0, (const Lev*)L);
+    } else {
+      launch_shape(b, b.s_node[l], kb_resid, (const Lev*)L);
+    }
+    launch_shape(b, b.s_next[l], kb_restrict, (const Lev*)L);
+  }
+  launch_shape(b, b.s_coarse, kb_coarse, (const Coarse*)b.dco);
+  // up
+  for (int l = b.lmax - 2; l >= 1; --l)
+    launch_shape(b, b.s_node[l], kb_post, (const Lev*)(b.dlev + (size_t)l * b.nd));
+  launch_shape(b, b.s_node[0], kb_prolong0, (const Lev*)L0);
+  kb_sweep0<<<b.s_red.nblocks, kRedThreads, 0, b.stream>>>(L0, b.ddes, b.s_red.bdes, b.s_red.b0,
+                                                           b.bsc, b.partials, b.counters);
+  MGAR_LAUNCH_CHECK();
+}
+
+static void red_launch_resid(Batch& b) {
+  kb_resid64<<<b.s_red.nblocks, kRedThreads, 0, b.stream>>>(b.ddes, b.s_red.bdes, b.s_red.b0, b.bsc,
+                                                            b.partials, b.counters);
+  MGAR_LAUNCH_CHECK();
+}
+
+static void iteration(Batch& b, cudaGraphConditionalHandle loop) {
+  kb_apply_dot<<<b.s_red.nblocks, kRedThreads, 0, b.stream>>>(b.ddes, b.s_red.bdes, b.s_red.b0,
+                                                              b.bsc, b.partials, b.counters);
+  MGAR_LAUNCH_CHECK();
+  kb_cg_xr<<<b.s_red.nblocks, kRedThreads, 0, b.stream>>>(b.ddes, b.s_red.bdes, b.s_red.b0, b.bsc,
+                                                          b.partials, b.counters);
+  MGAR_LAUNCH_CHECK();
+  kb_check<<<1, 256, 0, b.stream>>>(b.bsc, b.nd, loop);
+  MGAR_LAUNCH_CHECK();
+  vcycle(b);
+  kb_cg_p<<<b.s_red.nblocks, kRedThreads, 0, b.stream>>>(b.ddes, b.s_red.bdes, b.s_red.b0, b.bsc);
+  MGAR_LAUNCH_CHECK();
+}
+
+// The solve after the hierarchy builds as one graph: scalars, initial
+// residuals, first V-cycle and direction, then WHILE(any active) iteration.
+static void build_graph(Batch& b) {
+  cudaGraph_t g = nullptr;
+  cudaGraphConditionalHandle loop = 0;
+  MGAR_CUDA(cudaGraphCreate(&g, 0));
+  cudaStream_t saved = b.stream;
+  const int64_t before = launches_so_far();
+  bool ok = false;
+  try {
+    MGAR_CUDA(cudaGraphConditionalHandleCreate(&loop, g, 1, cudaGraphCondAssignDefault));
+    MGAR_CUDA(cudaStreamBeginCaptureToGraph(b.cap, g, nullptr, nullptr, 0,
+                                            cudaStreamCaptureModeThreadLocal));
+    b.stream = b.cap;
+    const int th = 128;
+    kb_init<<<(b.nd + th - 1) / th, th, 0, b.stream>>>(b.bsc, b.consts, b.nd);
+    MGAR_LAUNCH_CHECK();
+    red_launch_resid(b);
+    kb_start<<<(b.nd + th - 1) / th, th, 0, b.stream>>>(b.bsc, b.nd);
+    MGAR_LAUNCH_CHECK();
+    vcycle(b);
+    kb_cg_p<<<b.s_red.nblocks, kRedThreads, 0, b.stream>>>(b.ddes, b.s_red.bdes, b.s_red.b0, b.bsc);
+    MGAR_LAUNCH_CHECK();
+    cudaStreamCaptureStatus st;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edges = nullptr;
+    size_t ndeps = 0;
+    MGAR_CUDA(cudaStreamGetCaptureInfo(b.stream, &st, nullptr, &cg, &deps, &edges, &ndeps));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = loop;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t wnode = nullptr;
+    MGAR_CUDA(cudaGraphAddNode(&wnode, cg, deps, nullptr, ndeps, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    MGAR_CUDA(cudaStreamUpdateCaptureDependencies(b.stream, &wnode, nullptr, 1,
+                                                  cudaStreamSetCaptureDependencies));
+    cudaGraph_t out = nullptr;
+    MGAR_CUDA(cudaStreamEndCapture(b.cap, &out));
+    b.stream = saved;
+    b.prologue = launches_so_far() - before;
+    MGAR_CUDA(cudaStreamBeginCaptureToGraph(b.cap, body, nullptr, nullptr, 0,
+                                            cudaStreamCaptureModeThreadLocal));
+    b.stream = b.cap;
+    const int64_t b0 = launches_so_far();
+    iteration(b, loop);
+    b.body = launches_so_far() - b0;
+    MGAR_CUDA(cudaStreamEndCapture(b.cap, &out));
+    b.stream = saved;
+    MGAR_CUDA(cudaGraphInstantiate(&b.exec, g, 0));
+    ok = true;
+  } catch (...) {
+    b.stream = saved;
+    cudaStreamCaptureStatus st;
+    if (cudaStreamIsCapturing(b.cap, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+      cudaGraph_t junk = nullptr;
+      cudaStreamEndCapture(b.cap, &junk);
+      if (junk) cudaGraphDestroy(junk);
+    }
+    (void)cudaGetLastError();
+    count_launches(-(launches_so_far() - before));
+    cudaGraphDestroy(g);
+    throw;
+  }
+  count_launches(-(launches_so_far() - before));  // captured, not executed
+  cudaGraphDestroy(g);
+  (void)ok;
+}
+
+// Device time of fn() on the batch stream, best of reps.
+template <class F>
+static float time_best(Batch& b, int reps, F&& fn) {
+  cudaEvent_t e0, e1;
+  MGAR_CUDA(cudaEventCreate(&e0));
+  MGAR_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  for (int r = 0; r < reps; ++r) {
+    MGAR_CUDA(cudaEventRecord(e0, b.stream));
+    fn();
+    MGAR_CUDA(cudaEventRecord(e1, b.stream));
+    MGAR_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    MGAR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    best = std::min(best, ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return best;
+}
+
+// Autotuner: per level, the block size of its node kernels from 64 / 128 /
+// 256 / 512 threads, and the warps per block of the coarsest solve from
+// 2 / 4 / 8, each timed on the batch's own levels (the kernels are
+// node-parallel without reductions, so the choice changes no result).  The
+// device scalars mark every design active while it runs.
+static void autotune(Batch& b) {
+  std::vector<double> ones((size_t)b.nd * kBS, 0.0);
+  for (int d = 0; d < b.nd; ++d) ones[(size_t)d * kBS + BS_ACT] = 1.0;
+  MGAR_CUDA(cudaMemcpy(b.bsc, ones.data(), ones.size() * sizeof(double), cudaMemcpyHostToDevice));
+  const int cand[4] = {64, 128, 256, 512};
+  char line[160];
+  b.report = "batched V-cycle autotuner (best of 5 timed runs per candidate)\n";
+  for (int l = 0; l + 1 < b.lmax; ++l) {
+    Lev* L = b.dlev + (size_t)l * b.nd;
+    float best = 1e30f;
+    int pick = 256;
+    for (int th : cand) {
+      make_level_shapes(b, l, th);
+      const float ms = time_best(b, 5, [&] {
+        if (l == 0) {
+          launch_shape(b, b.s_node[0], kb_jz0, (const Lev*)L);
+          launch_shape(b, b.s_node[0], kb_resid0, (const Lev*)L);
+          launch_shape(b, b.s_next[0], kb_restrict, (const Lev*)L);
+          launch_shape(b, b.s_node[0], kb_prolong0, (const Lev*)L);
+        } else {
+          launch_shape(b, b.s_node[l], kb_resid, (const Lev*)L);
+          launch_shape(b, b.s_next[l], kb_restrict, (const Lev*)L);
+          launch_shape(b, b.s_node[l], kb_post, (const Lev*)L);
+        }
+      });
+      snprintf(line, sizeof(line), "  level %d: %3d threads %8.2f us\n", l, th, ms * 1e3f);
+      b.report += line;
+      if (ms < best) {
+        best = ms;
+        pick = th;
+      }
+    }
+    make_level_shapes(b, l, pick);
+    b.tuned[l] = pick;
+    snprintf(line, sizeof(line), "level %d: %d threads per block\n", l, pick);
+    b.report += line;
+  }
+  const int wc[3] = {2, 4, 8};
+  float best = 1e30f;
+  int pick = 8;
+  for (int w : wc) {
+    make_coarse_shape(b, w);
+    const float ms = time_best(b, 5, [&] { launch_shape(b, b.s_coarse, kb_coarse, (const Coarse*)b.dco); });
+    snprintf(line, sizeof(line), "  coarsest: %d warps %8.2f us\n", w, ms * 1e3f);
+    b.report += line;
+    if (ms < best) {
+      best = ms;
+      pick = w;
+    }
+  }
+  make_coarse_shape(b, pick);
+  b.tuned[b.lmax - 1] = pick;
+  snprintf(line, sizeof(line), "coarsest solve: %d warps per block\n", pick);
+  b.report += line;
+}
+
+}  // namespace bat
+}  // namespace mgar
+
+using namespace mgar;
+using namespace mgar::bat;
+
+namespace {
+thread_local std::string g_batch_create_error = "no error";
+
+template <class F>
+int bguard(mgar_batch_t hb, F&& f) {
+  Batch* b = reinterpret_cast<Batch*>(hb);
+  if (!b) return MGAR_ERR_ARG;
+  try {
+    return f(*b);
+  } catch (const Error& e) {
+    b->err = e.msg;
+    return e.code;
+  } catch (const std::exception& e) {
+    b->err = e.what();
+    return MGAR_ERR_CUDA;
+  }
+}
+
+void free_batch(Batch& b) {
+  if (b.exec) cudaGraphExecDestroy(b.exec);
+  for (auto& s : b.s_node) free_shape(s);
+  for (auto& s : b.s_next) free_shape(s);
+  free_shape(b.s_coarse);
+  free_shape(b.s_red);
+  cudaFree(b.dlev);
+  cudaFree(b.dco);
+  cudaFree(b.ddes);
+  cudaFree(b.bsc);
+  cudaFree(b.consts);
+  cudaFree(b.partials);
+  cudaFree(b.counters);
+  if (b.hconsts) cudaFreeHost(b.hconsts);
+  if (b.hbsc) cudaFreeHost(b.hbsc);
+  if (b.cap) cudaStreamDestroy(b.cap);
+}
+}  // namespace
+
+extern "C" {
+
+int mgar_batch_create(mgar_batch_t* out, const mgar_t* handles, int count, void* stream) {
+  if (!out || !handles || count < 1) {
+    g_batch_create_error = "mgar_batch_create: bad arguments";
+    return MGAR_ERR_ARG;
+  }
+  *out = nullptr;
+  Batch* b = new Batch();
+  try {
+    b->nd = count;
+    b->stream = reinterpret_cast<cudaStream_t>(stream);
+    for (int d = 0; d < count; ++d) {
+      Ctx* c = reinterpret_cast<Ctx*>(handles[d]);
+      require(c != nullptr, MGAR_ERR_ARG, "null handle");
+      require(c->dim == 2 && c->p.precision == MGAR_MIXED, MGAR_ERR_ARG,
+              "batched solves take 2D handles of the mixed precision");
+      for (Ctx* o : b->h) require(o != c, MGAR_ERR_ARG, "a handle appears twice");
+      b->h.push_back(c);
+      b->lmax = std::max(b->lmax, c->nl);
+    }
+    const int nd = b->nd, lmax = b->lmax;
+    b->s_node.resize(lmax);
+    b->s_next.resize(lmax);
+    b->tuned.assign(lmax, 256);
+    MGAR_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+    // tables
+    std::vector<Lev> lev((size_t)lmax * nd);
+    std::vector<Coarse> co(nd);
+    std::vector<Des> des(nd);
+    std::vector<int64_t> n0(nd);
+    for (int d = 0; d < nd; ++d) {
+      Ctx& c = *b->h[d];
+      const Dims& d0 = c.L[0];
+      n0[d] = d0.n;
+      des[d].f = FineOp<double>{c.ke, nullptr, c.fixed, d0.ex, d0.ey, d0.ez, d0.NX, d0.NY, d0.NZ,
+                                (int)d0.n, d0.fNX, d0.fNXY};
+      des[d].q = c.q;
+      des[d].r = c.r;
+      des[d].z = c.z;
+      des[d].p = c.pv;
+      des[d].Ap = c.Ap;
+      des[d].b32 = c.b32;
+      des[d].x32 = c.x32;
+      des[d].x = nullptr;  // the caller's T, set at each solve
+      for (int l = 0; l + 1 < c.nl; ++l) {
+        Lev& v = lev[(size_t)l * nd + d];
+        const Dims& dl = c.L[l];
+        const Dims& dn = c.L[l + 1];
+        v.d = dl;
+        v.dn = dn;
+        v.omega = (float)c.p.omega;
+        v.dinv = c.h32[l].dinv;
+        v.dinv_n = c.h32[l + 1].dinv;
+        v.t = c.h32[l].t;
+        v.r = c.h32[l].r;
+        if (l == 0) {
+          v.f0 = FineOp<float>{c.ke0_f, nullptr, c.fixed, dl.ex, dl.ey, dl.ez, dl.NX, dl.NY, dl.NZ,
+                               (int)dl.n, dl.fNX, dl.fNXY};
+          v.x = c.x32;
+          v.b = c.b32;
+          v.fixed = c.fixed;
+        } else {
+          v.op = StencilOp<float>{c.h32[l].st, c.h32[l].dinv, dl.NX, dl.NY, dl.NZ, (int)dl.n,
+                                  dl.fNX, dl.fNXY};
+          v.x = c.h32[l].x;
+          v.b = c.h32[l].b;
+          v.fixed = nullptr;
+        }
+        const bool next_coarsest = l + 2 == c.nl;
+        v.bn = c.h32[l + 1].b;
+        v.xn = next_coarsest ? nullptr : c.h32[l + 1].x;
+        v.resn = next_coarsest ? c.h32[l + 1].x : c.h32[l + 1].t;
+      }
+      co[d].cinv = c.cinv;
+      co[d].b = c.h32[c.nl - 1].b;
+      co[d].x = c.h32[c.nl - 1].x;
+      co[d].nc = c.nc;
+    }
+    MGAR_CUDA(cudaMalloc(&b->dlev, lev.size() * sizeof(Lev)));
+    MGAR_CUDA(cudaMemcpy(b->dlev, lev.data(), lev.size() * sizeof(Lev), cudaMemcpyHostToDevice));
+    MGAR_CUDA(cudaMalloc(&b->dco, co.size() * sizeof(Coarse)));
+    MGAR_CUDA(cudaMemcpy(b->dco, co.data(), co.size() * sizeof(Coarse), cudaMemcpyHostToDevice));
+    MGAR_CUDA(cudaMalloc(&b->ddes, des.size() * sizeof(Des)));
+    MGAR_CUDA(cudaMemcpy(b->ddes, des.data(), des.size() * sizeof(Des), cudaMemcpyHostToDevice));
+    b->hdes = des;
+    b->s_red = make_shape(n0, kRedThreads, kRedThreads);
+    for (int l = 0; l + 1 < lmax; ++l) make_level_shapes(*b, l, 256);
+    make_coarse_shape(*b, 8);
+    MGAR_CUDA(cudaMalloc(&b->bsc, (size_t)nd * kBS * sizeof(double)));
+    MGAR_CUDA(cudaMemset(b->bsc, 0, (size_t)nd * kBS * sizeof(double)));
+    MGAR_CUDA(cudaMalloc(&b->consts, (size_t)nd * 3 * sizeof(double)));
+    MGAR_CUDA(cudaHostAlloc(&b->hconsts, (size_t)nd * 3 * sizeof(double), cudaHostAllocDefault));
+    MGAR_CUDA(cudaHostAlloc(&b->hbsc, (size_t)nd * kBS * sizeof(double), cudaHostAllocDefault));
+    MGAR_CUDA(cudaMalloc(&b->partials, (size_t)std::max(b->s_red.nblocks, 1) * sizeof(double)));
+    MGAR_CUDA(cudaMalloc(&b->counters, (size_t)nd * sizeof(unsigned int)));
+    MGAR_CUDA(cudaMemset(b->counters, 0, (size_t)nd * sizeof(unsigned int)));
+  } catch (const Error& e) {
+    g_batch_create_error = e.msg;
+    free_batch(*b);
+    delete b;
+    return e.code;
+  }
+  *out = reinterpret_cast<mgar_batch_t>(b);
+  return MGAR_OK;
+}
+
+int mgar_batch_destroy(mgar_batch_t hb) {
+  if (!hb) return MGAR_OK;
+  Batch* b = reinterpret_cast<Batch*>(hb);
+  free_batch(*b);
+  delete b;
+  return MGAR_OK;
+}
+
+const char* mgar_batch_last_error(mgar_batch_t hb) {
+  if (!hb) return g_batch_create_error.c_str();
+  return reinterpret_cast<Batch*>(hb)->err.c_str();
+}
+
+int mgar_batch_solve_mgcg(mgar_batch_t hb, double* const* T, int* iters, double* relres,
+                          int* status) {
+  return bguard(hb, [&](Batch& b) {
+    require(T != nullptr, MGAR_ERR_ARG, "batch_solve_mgcg: null T");
+    for (int d = 0; d < b.nd; ++d) require(T[d] != nullptr, MGAR_ERR_ARG, "batch_solve_mgcg: null T[d]");
+    // each design's hierarchy from its current design (K0 <- K), on the batch
+    // stream; the coarsest factorisations run on the handles' side streams,
+    // all of them at once, and the stream waits for them before the solve
+    for (Ctx* c : b.h) {
+      cudaStream_t saved = c->stream;
+      c->stream = b.stream;
+      try {
+        build_hierarchy(*c);
+      } catch (...) {
+        c->stream = saved;
+        throw;
+      }
+      c->stream = saved;
+    }
+    for (Ctx* c : b.h) {
+      cudaStream_t saved = c->stream;
+      c->stream = b.stream;
+      join_coarse(*c);
+      c->stream = saved;
+    }
+    // the callers' solution vectors and the per-design constants
+    std::vector<Des>& des = b.hdes;
+    bool moved = false;
+    for (int d = 0; d < b.nd; ++d) {
+      moved = moved || des[d].x != T[d];
+      des[d].x = T[d];
+      b.hconsts[3 * d] = b.h[d]->qnorm;
+      b.hconsts[3 * d + 1] = b.h[d]->p.eps2;
+      b.hconsts[3 * d + 2] = (double)b.h[d]->p.cg_max;
+    }
+    if (moved)
+      MGAR_CUDA(cudaMemcpyAsync(b.ddes, des.data(), b.nd * sizeof(Des), cudaMemcpyHostToDevice,
+                                b.stream));
+    MGAR_CUDA(cudaMemcpyAsync(b.consts, b.hconsts, (size_t)b.nd * 3 * sizeof(double),
+                              cudaMemcpyHostToDevice, b.stream));
+    if (!b.exec) {
+      MGAR_CUDA(cudaStreamSynchronize(b.stream));
+      autotune(b);
+      build_graph(b);
+    }
+    MGAR_CUDA(cudaGraphLaunch(b.exec, b.stream));
+    MGAR_CUDA(cudaMemcpyAsync(b.hbsc, b.bsc, (size_t)b.nd * kBS * sizeof(double),
+                              cudaMemcpyDeviceToHost, b.stream));
+    MGAR_CUDA(cudaStreamSynchronize(b.stream));
+    int maxit = 0;
+    int rc = MGAR_OK;
+    for (int d = 0; d < b.nd; ++d) {
+      const double* s = b.hbsc + (size_t)d * kBS;
+      const int it = (int)s[BS_IT];
+      const double rel = std::sqrt(s[BS_RR]) / s[BS_QN];
+      maxit = std::max(maxit, it);
+      int st = MGAR_OK;
+      if (s[BS_BAD] != 0.0 || !std::isfinite(rel)) st = MGAR_ERR_NONFINITE;
+      else if (!(rel <= b.h[d]->p.eps2)) st = MGAR_ERR_MAXIT;
+      if (iters) iters[d] = it;
+      if (relres) relres[d] = rel;
+      if (status) status[d] = st;
+      if (st == MGAR_ERR_NONFINITE) rc = MGAR_ERR_NONFINITE;
+      else if (st == MGAR_ERR_MAXIT && rc == MGAR_OK) rc = MGAR_ERR_MAXIT;
+      // the solution is the handle's new reference
+      b.h[d]->have_ref = true;
+    }
+    count_launches(b.prologue + (int64_t)maxit * b.body);
+    // the factorisations' error flags (published per handle)
+    for (Ctx* c : b.h) {
+      int e = 0;
+      MGAR_CUDA(cudaMemcpy(&e, c->derr, sizeof(int), cudaMemcpyDeviceToHost));
+      if (e) {
+        MGAR_CUDA(cudaMemset(c->derr, 0, sizeof(int)));
+        throw Error{e, "a coarsest factorisation met a non-positive pivot"};
+      }
+    }
+    if (rc == MGAR_ERR_MAXIT) b.err = "a design reached cg_max";
+    if (rc == MGAR_ERR_NONFINITE) b.err = "a design's CG broke down (non-finite residual)";
+    return rc;
+  });
+}
+
+int mgar_batch_report(mgar_batch_t hb, char* buf, int64_t len) {
+  return bguard(hb, [&](Batch& b) {
+    require(buf && len > 0, MGAR_ERR_ARG, "batch_report: bad buffer");
+    const size_t n = std::min<size_t>((size_t)len - 1, b.report.size());
+    std::memcpy(buf, b.report.data(), n);
+    buf[n] = 0;
+    return MGAR_OK;
+  });
+}
+
+}  // extern "C"

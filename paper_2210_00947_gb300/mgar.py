@@ -35,11 +35,13 @@ ERROR_NAMES = {MGAR_ERR_ARG: "MGAR_ERR_ARG", MGAR_ERR_CUDA: "MGAR_ERR_CUDA",
 
 # every entry point of include/mgar.h, in declaration order
 EXPORTS = ("mgar_default_params", "mgar_create", "mgar_destroy", "mgar_set_stream",
-           "mgar_last_error", "mgar_filter", "mgar_set_density", "mgar_apply_K",
+           "mgar_last_error", "mgar_filter", "mgar_set_density", "mgar_set_load", "mgar_apply_K",
            "mgar_build_hierarchy", "mgar_vcycle", "mgar_solve_mgcg", "mgar_solve_mgar",
            "mgar_sensitivity", "mgar_postprocess", "mgar_oc_update", "mgar_step", "mgar_sizes", "mgar_run",
            "mgar_profile_start", "mgar_profile_stop", "mgar_profile_report",
-           "mgar_kernel_launches", "mgar_sensitivity_noalloc")
+           "mgar_kernel_launches", "mgar_batch_create", "mgar_batch_destroy",
+           "mgar_batch_last_error", "mgar_batch_solve_mgcg", "mgar_batch_report",
+           "mgar_sensitivity_noalloc")
 
 # kernel classes of mgar_profile_start
 KC_APPLY64, KC_SMOOTH0, KC_RESID0, KC_OC, KC_GALERKIN0, KC_FILTER, KC_SENS = range(1, 8)
@@ -105,6 +107,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "mgar_last_error": (ctypes.c_char_p, [vp]),
         "mgar_filter": (i32, [vp, vp, vp, i32]),
         "mgar_set_density": (i32, [vp, vp, i32]),
+        "mgar_set_load": (i32, [vp, vp]),
         "mgar_apply_K": (i32, [vp, vp, vp]),
         "mgar_build_hierarchy": (i32, [vp]),
         "mgar_vcycle": (i32, [vp, vp, vp]),
@@ -120,6 +123,11 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "mgar_profile_stop": (i32, [vp, dp, P(ctypes.c_int64)]),
         "mgar_profile_report": (i32, [vp, ctypes.c_char_p, ctypes.c_int64]),
         "mgar_kernel_launches": (ctypes.c_int64, []),
+        "mgar_batch_create": (i32, [P(vp), P(vp), i32, vp]),
+        "mgar_batch_destroy": (i32, [vp]),
+        "mgar_batch_last_error": (ctypes.c_char_p, [vp]),
+        "mgar_batch_solve_mgcg": (i32, [vp, P(vp), P(i32), dp, P(i32)]),
+        "mgar_batch_report": (i32, [vp, ctypes.c_char_p, ctypes.c_int64]),
         "mgar_sensitivity_noalloc": (i32, [P(Params), vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
@@ -219,6 +227,10 @@ class Solver:
     def set_density(self, rho, physical=False):
         self._check(self._lib.mgar_set_density(self._h, _ptr(rho), int(physical)))
 
+    def set_load(self, q):
+        """mgar_set_load: q is a float64 CUDA tensor of n entries."""
+        self._check(self._lib.mgar_set_load(self._h, _ptr(q)))
+
     def apply_K(self, x, y):
         self._check(self._lib.mgar_apply_K(self._h, _ptr(x), _ptr(y)))
         return y
@@ -294,6 +306,65 @@ class Solver:
         self._check(self._lib.mgar_step(self._h, _ptr(rho), _ptr(T), int(cycle),
                                         ctypes.byref(info)))
         return info.as_dict()
+
+
+class BatchSolver:
+    """Batched MGCG over several 2D mixed-precision Solvers (mgar_batch_*):
+    one launch per V-cycle level and operation over all designs."""
+
+    def __init__(self, solvers, stream=None):
+        import torch
+        self._lib = load()
+        self.solvers = list(solvers)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        hs = (ctypes.c_void_p * len(self.solvers))(*[s._h.value for s in self.solvers])
+        b = ctypes.c_void_p()
+        rc = self._lib.mgar_batch_create(ctypes.byref(b), hs, len(self.solvers),
+                                         ctypes.c_void_p(stream.cuda_stream))
+        if rc != MGAR_OK:
+            raise MgarError(rc, self._lib.mgar_batch_last_error(None).decode())
+        self._b = b
+
+    def solve(self, Ts):
+        """mgar_batch_solve_mgcg: Ts are the designs' temperature tensors (warm
+        start in, solution out); returns per design (iters, relres, ok)."""
+        n = len(self.solvers)
+        if len(Ts) != n:
+            raise ValueError("one temperature tensor per design")
+        ptrs = (ctypes.c_void_p * n)(*[_ptr(t).value for t in Ts])
+        it = (ctypes.c_int32 * n)()
+        rr = (ctypes.c_double * n)()
+        st = (ctypes.c_int32 * n)()
+        rc = self._lib.mgar_batch_solve_mgcg(self._b, ptrs, it, rr, st)
+        if rc not in (MGAR_OK, MGAR_ERR_MAXIT):
+            raise MgarError(rc, self._lib.mgar_batch_last_error(self._b).decode())
+        return [(it[d], rr[d], st[d] == MGAR_OK) for d in range(n)]
+
+    def report(self) -> str:
+        buf = ctypes.create_string_buffer(1 << 14)
+        rc = self._lib.mgar_batch_report(self._b, buf, len(buf))
+        if rc != MGAR_OK:
+            raise MgarError(rc, self._lib.mgar_batch_last_error(self._b).decode())
+        return buf.value.decode()
+
+    def close(self):
+        if getattr(self, "_b", None):
+            self._lib.mgar_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def kernel_launches() -> int:
