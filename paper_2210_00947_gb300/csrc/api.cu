@@ -136,6 +136,13 @@ void free_ctx(Ctx& c) {
   if (c.hseq) cudaFreeHost(c.hseq);
 }
 
+// q = load with fixed nodes zeroed (Eq. 3: their rows are eliminated)
+__global__ void k_masked_load(const double* __restrict__ src, const uint8_t* __restrict__ fixed,
+                              double* __restrict__ q, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) q[i] = fixed[i] ? 0.0 : src[i];
+}
+
 // One design cycle of Figure 5 on device arrays rho (design) and T.
 mgar_step_info design_cycle(Ctx& c, double* rho, double* T, int cycle) {
   mgar_step_info inf{};
@@ -466,6 +473,30 @@ int mgar_set_density(mgar_t h, const double* rho, int is_physical) {
   return guarded(h, [&](Ctx& c) {
     require(rho != nullptr, MGAR_ERR_ARG, "set_density: null rho");
     set_density(c, rho, is_physical != 0);
+    return MGAR_OK;
+  });
+}
+
+int mgar_set_load(mgar_t h, const double* q) {
+  return guarded(h, [&](Ctx& c) {
+    require(q != nullptr, MGAR_ERR_ARG, "set_load: null q");
+    k_masked_load<<<blocks_for(c.n), kThreads, 0, c.stream>>>(q, c.fixed, c.q, c.n);
+    MGAR_LAUNCH_CHECK();
+    dot(c, c.q, c.q, c.n, c.dsc + S_TMP);
+    fetch_scalars(c, S_TMP, 1);
+    const double qnorm = std::sqrt(c.hsc[S_TMP]);
+    require(qnorm > 0.0 && std::isfinite(qnorm), MGAR_ERR_ARG, "set_load: load vector is zero");
+    c.qnorm = qnorm;
+    if (c.p.precision == MGAR_MIXED) q_to_df(c);
+    // the CG graphs carry ||q|| in their stopping tests: rebuilt on next use
+    if (c.cg_exec) {
+      MGAR_CUDA(cudaGraphExecDestroy(c.cg_exec));
+      c.cg_exec = nullptr;
+    }
+    if (c.ru_exec) {
+      MGAR_CUDA(cudaGraphExecDestroy(c.ru_exec));
+      c.ru_exec = nullptr;
+    }
     return MGAR_OK;
   });
 }
