@@ -424,6 +424,7 @@ int mgar_create(mgar_t* out, const mgar_params* p, const uint8_t* fixed_mask, co
     if (const char* sc = std::getenv("MGAR_SPLIT_COARSE")) c->split_coarse_nodes = std::atoll(sc);
     if (const char* bn = std::getenv("MGAR_BOTTOM_NODES")) c->bottom_nodes = std::atoll(bn);
     if (const char* nb = std::getenv("MGAR_NO_CLUSTER")) c->bottom_ok = c->bottom_ok && nb[0] != '1';
+    if (const char* fc = std::getenv("MGAR_FP64_COARSE")) c->df_coarse = fc[0] != '1';
     if (c->dim == 3) {
       fine3d_prepare(*c);
       if (P.precision == MGAR_MIXED) df3d_prepare(*c);

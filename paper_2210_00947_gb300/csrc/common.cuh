@@ -264,6 +264,9 @@ struct Ctx {
   bool coarse_pending = false;
   bool derr_fresh = true;  // the last published device error flag follows every factorisation
   cudaStream_t cap_stream2 = nullptr;  // captures the body of a graph's IF node
+  // the FP32 V-cycle's coarsest factor and inverse in df64 on the FP32 pipe
+  // (MGAR_FP64_COARSE=1: in FP64, as the FP64 V-cycle's)
+  bool df_coarse = true;
 
   // instrumentation: CUDA-event timing of one kernel class
   int prof_class = 0;

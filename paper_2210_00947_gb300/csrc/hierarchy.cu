@@ -455,6 +455,135 @@ __global__ void k_band_inverse(const B* __restrict__ gband, const B* __restrict_
     for (int i = lane; i < n; i += 32) inv[(int64_t)i * n + col] = colbuf[i];
 }
 
+// The same factorisation and inverse in double-float arithmetic (df64: two
+// FP32 words, ~48 bits) on the FP32 pipe, for the FP32 V-cycle.  GB300 runs
+// FP64 at 1/58 of the FP32 rate, and the chain of 125 dependent pivots is
+// bound by that rate; a df64 operation costs a handful of FP32 operations.
+// The band arrives in FP64 (gband), is factorised in shared memory, and the
+// factor (band, rdiag) is stored as df64 pairs in the same buffers; the
+// inverse is written in FP64.
+__device__ __forceinline__ df df_ld(const float2* p) {
+  const float2 v = *p;
+  return df{v.x, v.y};
+}
+__device__ __forceinline__ void df_st(float2* p, df v) { *p = make_float2(v.hi, v.lo); }
+
+// 1 / sqrt(a), a > 0: an FP32 seed and two Newton steps y <- y + y (1 - a y^2) / 2
+// with the residual 1 - a y^2 formed in df64 (each step doubles the correct bits)
+__device__ __forceinline__ df df_rsqrt(df a) {
+  df y{rsqrtf(a.hi), 0.f};
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const df e = df_sub(df{1.f, 0.f}, df_mul(df_mul(a, y), y));
+    y = df_add(y, df_mulf(y, 0.5f * e.hi));
+  }
+  return y;
+}
+
+__global__ void __launch_bounds__(kCholThreads) k_band_cholesky_df(double* __restrict__ gband,
+                                                                   double* __restrict__ grdiag,
+                                                                   int n, int bw,
+                                                                   int* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* band = reinterpret_cast<float2*>(smraw);
+  float2* out = reinterpret_cast<float2*>(gband);  // same bytes, df64 pairs
+  float2* rdiag = reinterpret_cast<float2*>(grdiag);
+  __shared__ float2 rpiv;
+  __shared__ int bad;
+  const int ld = bw + 1;
+  const int64_t size = (int64_t)n * ld;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int64_t t = tid; t < size; t += blockDim.x) {
+    const df v = df_from_double(gband[t]);
+    band[t] = make_float2(v.hi, v.lo);
+  }
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (tid == 0) {
+      const df a = df_ld(band + (int64_t)k * ld + bw);
+      if (!(a.hi > 0.f) || !isfinite(a.hi)) bad = 1;
+      const df r = df_rsqrt(a);
+      rpiv = make_float2(r.hi, r.lo);
+      df_st(band + (int64_t)k * ld + bw, df_mul(a, r));  // sqrt(a)
+      df_st(rdiag + k, r);
+    }
+    __syncthreads();
+    if (bad) break;
+    const int last = min(k + bw, n - 1);
+    const int m = last - k;
+    const df rp{rpiv.x, rpiv.y};
+    for (int t = tid; t < m; t += blockDim.x) {
+      const int64_t at = (int64_t)(k + 1 + t) * ld + (bw - 1 - t);  // L(k+1+t, k)
+      if (CK(at, size)) df_st(band + at, df_mul(df_ld(band + at), rp));
+    }
+    __syncthreads();
+    // A(i, j) -= L(i, k) L(j, k) for k < j <= i <= last
+    for (int ii = warp; ii < m; ii += nw) {
+      const int i = k + 1 + ii;
+      const df lik = df_ld(band + (int64_t)i * ld + (k - i + bw));
+      for (int jj = lane; jj <= ii; jj += 32) {
+        const int j = k + 1 + jj;
+        const int64_t at = (int64_t)i * ld + (j - i + bw);
+        const int64_t bt = (int64_t)j * ld + (k - j + bw);
+        if (CK(at, size) && CK(bt, size))
+          df_st(band + at, df_sub(df_ld(band + at), df_mul(lik, df_ld(band + bt))));
+      }
+    }
+    __syncthreads();
+  }
+  for (int64_t t = tid; t < size; t += blockDim.x) out[t] = band[t];
+  if (tid == 0 && bad) *err = MGAR_ERR_NOT_SPD;
+}
+
+// Columns of the inverse from the df64 factor, one warp per column, as
+// k_band_inverse does in FP64; the result is written in FP64.
+__global__ void k_band_inverse_df(const double* __restrict__ gband_d,
+                                  const double* __restrict__ grdiag_d, int n, int bw,
+                                  double* __restrict__ inv) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const float2* gband = reinterpret_cast<const float2*>(gband_d);
+  const float2* rdiag = reinterpret_cast<const float2*>(grdiag_d);
+  float2* sband = reinterpret_cast<float2*>(smraw);
+  const int ld = bw + 1;
+  const int64_t size = (int64_t)n * ld;
+  const int warps = blockDim.x >> 5;
+  const int wid = threadIdx.x >> 5;
+  for (int64_t t = threadIdx.x; t < size; t += blockDim.x) sband[t] = gband[t];
+  __syncthreads();
+  float2* colbuf = sband + size + (int64_t)wid * n;
+  const int col = blockIdx.x * warps + wid;
+  const int lane = threadIdx.x & 31;
+  if (col >= n) return;
+  for (int i = lane; i < n; i += 32) colbuf[i] = make_float2(i == col ? 1.f : 0.f, 0.f);
+  __syncwarp();
+  // forward: L y = e_col (y_p = 0 for p < col)
+  for (int p = col; p < n; ++p) {
+    const df yp = df_mul(df_ld(colbuf + p), df_ld(rdiag + p));
+    __syncwarp();
+    if (lane == 0) df_st(colbuf + p, yp);
+    const int last = min(n - 1, p + bw);
+    for (int i = p + 1 + lane; i <= last; i += 32) {
+      const int64_t at = (int64_t)i * ld + (p - i + bw);  // L(i, p)
+      if (CK(at, size)) df_st(colbuf + i, df_sub(df_ld(colbuf + i), df_mul(df_ld(sband + at), yp)));
+    }
+    __syncwarp();
+  }
+  // backward: L^T x = y
+  for (int i = n - 1; i >= 0; --i) {
+    const df xi = df_mul(df_ld(colbuf + i), df_ld(rdiag + i));
+    __syncwarp();
+    if (lane == 0) df_st(colbuf + i, xi);
+    const int first = max(0, i - bw);
+    for (int p = first + lane; p < i; p += 32) {
+      const int64_t at = (int64_t)i * ld + (p - i + bw);  // L(i, p)
+      if (CK(at, size)) df_st(colbuf + p, df_sub(df_ld(colbuf + p), df_mul(df_ld(sband + at), xi)));
+    }
+    __syncwarp();
+  }
+  for (int i = lane; i < n; i += 32) inv[(int64_t)i * n + col] = df_to_double(df_ld(colbuf + i));
+}
+
 __global__ void k_d2f(const double* a, float* b, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
@@ -510,6 +639,10 @@ void alloc_hierarchy(Ctx& c) {
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandSmemMax));
   MGAR_CUDA(cudaFuncSetAttribute(k_band_inverse<float, true>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandSmemMax));
+  MGAR_CUDA(cudaFuncSetAttribute(k_band_cholesky_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kBandSmemMax));
+  MGAR_CUDA(cudaFuncSetAttribute(k_band_inverse_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kBandSmemMax));
   // constant tables: k0 (nen^2) then G (3^dim * nen^2)
   const int nen = c.nen, ntypes = c.dim == 2 ? 9 : 27;
   std::vector<double> k0(nen * nen), G((size_t)ntypes * nen * nen, 0.0),
@@ -592,6 +725,24 @@ static void coarse_factor(Ctx& c, const Real* st, const Dims& dcst) {
   MGAR_LAUNCH_CHECK();
   const size_t band_bytes = (size_t)c.nc * (c.bw + 1) * sizeof(B);
   const bool smem = band_bytes <= kBandSmemMax;
+  const size_t inv_smem = band_bytes + (size_t)8 * c.nc * sizeof(B);
+  // the FP32 V-cycle's coarsest factor and inverse in df64 on the FP32 pipe
+  // (same band bytes: a df64 pair is the size of a double)
+  if (sizeof(Real) == 4 && sizeof(B) == 8 && smem && inv_smem <= kBandSmemMax && c.df_coarse) {
+    k_band_cholesky_df<<<1, kCholThreads, band_bytes, s>>>((double*)band, (double*)rdiag, c.nc,
+                                                           c.bw, c.derr);
+    MGAR_LAUNCH_CHECK();
+    k_band_inverse_df<<<(c.nc + 7) / 8, 256, inv_smem, s>>>((const double*)band,
+                                                           (const double*)rdiag, c.nc, c.bw,
+                                                           (double*)inv);
+    MGAR_LAUNCH_CHECK();
+    if (c.side_stream) {
+      MGAR_CUDA(cudaEventRecord(c.ev_join, s));
+      c.coarse_pending = true;
+      c.derr_fresh = false;
+    }
+    return;
+  }
   if (smem) {
     k_band_cholesky<B, true><<<1, kCholThreads, band_bytes, s>>>(band, rdiag, c.nc, c.bw, c.derr);
   } else {
@@ -599,7 +750,6 @@ static void coarse_factor(Ctx& c, const Real* st, const Dims& dcst) {
   }
   MGAR_LAUNCH_CHECK();
   MGAR_CUDA(cudaMemsetAsync(inv, 0, (size_t)c.nc * c.nc * sizeof(B), s));
-  const size_t inv_smem = band_bytes + (size_t)8 * c.nc * sizeof(B);
   if (smem && inv_smem <= kBandSmemMax)
     k_band_inverse<B, true><<<(c.nc + 7) / 8, 256, inv_smem, s>>>(band, rdiag, c.nc, c.bw, inv);
   else
