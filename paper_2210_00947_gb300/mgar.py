@@ -31,7 +31,8 @@ MGAR_GUESS_ZERO = 1
 
 ERROR_NAMES = {MGAR_ERR_ARG: "MGAR_ERR_ARG", MGAR_ERR_CUDA: "MGAR_ERR_CUDA",
                MGAR_ERR_NOT_SPD: "MGAR_ERR_NOT_SPD", MGAR_ERR_MAXIT: "MGAR_ERR_MAXIT",
-               MGAR_ERR_NONFINITE: "MGAR_ERR_NONFINITE", MGAR_ERR_STATE: "MGAR_ERR_STATE"}
+               MGAR_ERR_NONFINITE: "MGAR_ERR_NONFINITE", MGAR_ERR_STATE: "MGAR_ERR_STATE",
+               MGAR_ERR_TOO_LARGE: "MGAR_ERR_TOO_LARGE"}
 
 # every entry point of include/mgar.h, in declaration order
 EXPORTS = ("mgar_default_params", "mgar_create", "mgar_destroy", "mgar_set_stream",

@@ -120,15 +120,19 @@ def test_vcycle_matches_oracle(dims, nl, zero_guess):
 
 # The mixed path's FP32 V-cycle (tiled finest-level passes, the restriction
 # that leaves each coarse level's zero-guess sweep, the coarse residual, the
-# cluster kernel for the small levels, the column interpolation) against the
-# oracle's FP64 V-cycle on the same hierarchy.  FP32 storage and arithmetic
-# bound the agreement (the operands carry 2^-24 and each stencil row cancels
-# its 21-27 terms down to the residual); the bar is 1e-4.  (42, 42, 21)
-# selects the 43 x 5 tiles and coarsens z oddly.
+# column interpolation; the small levels as separate launches, or in one
+# cluster launch on request) against the oracle's FP64 V-cycle on the same
+# hierarchy.  FP32 storage and arithmetic bound the agreement (the operands
+# carry 2^-24 and each stencil row cancels its 21-27 terms down to the
+# residual); the bar is 1e-4.  (42, 42, 21) selects the 43 x 5 tiles and
+# coarsens z oddly.
 @pytest.mark.parametrize("dims,nl", [((37, 23, 0), 3), ((100, 100, 0), 4), ((13, 11, 9), 3),
                                      ((20, 18, 16), 4), ((42, 42, 21), 3)])
 @pytest.mark.parametrize("zero_guess", [True, False])
-def test_mixed_vcycle_matches_oracle(dims, nl, zero_guess):
+@pytest.mark.parametrize("cluster", [False, True])
+def test_mixed_vcycle_matches_oracle(dims, nl, zero_guess, cluster, monkeypatch):
+    if cluster:
+        monkeypatch.setenv("MGAR_CLUSTER_BOTTOM", "1")
     g, rho, fixed, q = make_problem(dims, mask="sink")
     A = fem.system_matrix(g, rho, fixed)
     dims_e = dims[:2] if dims[2] == 0 else dims
