@@ -245,7 +245,7 @@ struct Ctx {
   // df64 (MGAR_DF64_CG=1 selects the df64 CG); an update whenever ||r||
   // falls below ru_delta times its value at the previous update
   bool ru_cg = true;
-  double ru_delta = 1e-2;
+  double ru_delta = 1e-3;
   cudaGraphExec_t ru_exec = nullptr;
   int64_t ru_body_kernels = 0, ru_update_kernels = 0;
   // finest post-smoothing as a thin interpolation pass + the tiled sweep
