@@ -427,6 +427,12 @@ def run_gpu(args):
                  "max_rel_err_accepted_mgar": max(acc) if acc else None,
                  "accepted_mgar_cycles": len(acc),
                  "reference": "FP64 MGCG (eps2 1e-10) on the same design each cycle"}
+        print("[check] cycle, solve (mgcg / mgar accepted), CG iterations, Res, compliance, "
+              "FP64 MGCG compliance, relative error:\n" +
+              "\n".join(f"  {k:3d} {'mgar' if i['accepted'] else 'mgcg'} {i['cg_iters']:3d} "
+                        f"{i['res']:9.3e} {i['compliance']:.12e} {c:.12e} {e:.3e}"
+                        for e, (k, i, c) in zip(errs, rows)),
+              file=sys.stderr, flush=True)
 
     # MGAR at the paper's acceptance threshold (Eq. 28, eps1 = 0.5) under both
     # readings of Eq. 17 (timed, with the compliance error of every accepted
