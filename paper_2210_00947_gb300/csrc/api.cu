@@ -638,6 +638,7 @@ int mgar_profile_start(mgar_t h, int kernel_class) {
     }
     c.prof_class = kernel_class;
     c.prof_used = 0;
+    c.prof_open = false;
     c.prof_report.clear();
     if (kernel_class == MGAR_KC_TIMELINE) {
       MGAR_CUDA(cudaEventRecord(c.prof_ev[0], c.stream));

@@ -311,13 +311,15 @@ __global__ void k_cg_reset(double* dsc) {
 // ... and after each update of x and r: count the iteration, flip the
 // parity, and continue while ||r|| / ||q|| > eps2 (the host loop's test,
 // same arithmetic) and fewer than cg_max iterations ran; a non-finite
-// residual stops the loop and the host reports it.
+// residual stops the loop and the host reports it.  shift: the iteration's
+// r . z (RZ1) becomes the next one's old value (RZ0).
 __global__ void k_cg_check(double* dsc, double qnorm, double eps2, int cg_max,
-                           cudaGraphConditionalHandle loop) {
+                           cudaGraphConditionalHandle loop, int shift) {
   const double rel = sqrt(dsc[S_RR]) / qnorm;
   const int it = (int)dsc[S_CGIT] + 1;
   dsc[S_CGIT] = (double)it;
   dsc[S_CGPAR] = (double)(((int)dsc[S_CGPAR]) ^ 1);
+  if (shift) dsc[S_RZ0] = dsc[S_RZ1];
   const bool go = isfinite(rel) && rel > eps2 && it < cg_max;
   cudaGraphSetConditional(loop, go ? 1u : 0u);
 }
@@ -348,7 +350,39 @@ static void cg_iteration(Ctx& c, bool first, cudaGraphConditionalHandle loop) {
              (const double*)(c.dsc + S_PAP), c.partials, c.counter, c.dsc + S_RR, c.b32,
              (const float2*)c.df_p, (const double*)(c.dsc + S_CGPAR));
   MGAR_LAUNCH_CHECK();
-  k_cg_check<<<1, 1, 0, c.stream>>>(c.dsc, c.qnorm, c.p.eps2, c.p.cg_max, loop);
+  k_cg_check<<<1, 1, 0, c.stream>>>(c.dsc, c.qnorm, c.p.eps2, c.p.cg_max, loop, 0);
+  MGAR_LAUNCH_CHECK();
+}
+
+// 2D: one CG iteration of the device-side loop with the generic kernels,
+// the host loop's steps and arithmetic: V-cycle z = M r (r's FP32 copy is
+// written by the update of x and r), r . z into RZ1, p = z (first) or
+// p = z + (RZ1 / RZ0) p, A p with p . A p, the update of x and r with
+// alpha = RZ1 / pAp, the check (which moves RZ1 to RZ0).
+static void cg_iteration_2d(Ctx& c, bool first, cudaGraphConditionalHandle loop) {
+  const int n = (int)c.n;
+  const int rb = c.grid_blocks;
+  const DfOp op = make_op(c);
+  if (first) {
+    k_df_to_f32<<<blocks_for(n), kThreads, 0, c.stream>>>(c.df_r, c.b32, n);
+    MGAR_LAUNCH_CHECK();
+  }
+  vcycle<float>(c, c.b32, c.x32, true);
+  k_df_dot_f<<<rb, kThreads, 0, c.stream>>>(c.df_r, c.x32, n, c.partials, c.counter, c.dsc + S_RZ1);
+  MGAR_LAUNCH_CHECK();
+  if (first)
+    k_f32_to_df<<<blocks_for(n), kThreads, 0, c.stream>>>(c.x32, c.df_p, n);
+  else
+    k_df_cg_p<<<rb, kThreads, 0, c.stream>>>(c.df_p, c.x32, n, c.dsc + S_RZ1, c.dsc + S_RZ0);
+  MGAR_LAUNCH_CHECK();
+  k_df_apply<2, true><<<blocks_for(n), kThreads, 0, c.stream>>>(op, c.df_p, c.df_Ap, c.partials,
+                                                                c.counter, c.dsc + S_PAP);
+  MGAR_LAUNCH_CHECK();
+  k_df_cg_xr<<<rb, kThreads, 0, c.stream>>>(c.df_x, c.df_r, c.df_p, c.df_Ap, n, c.dsc + S_RZ1,
+                                            c.dsc + S_PAP, c.partials, c.counter, c.dsc + S_RR,
+                                            c.b32);
+  MGAR_LAUNCH_CHECK();
+  k_cg_check<<<1, 1, 0, c.stream>>>(c.dsc, c.qnorm, c.p.eps2, c.p.cg_max, loop, 1);
   MGAR_LAUNCH_CHECK();
 }
 
@@ -358,6 +392,7 @@ static void cg_iteration(Ctx& c, bool first, cudaGraphConditionalHandle loop) {
 // per solve instead of once per iteration.  False if the device or driver
 // refuses any part (the host loop is used then).
 static bool build_cg_graph(Ctx& c) {
+  auto iteration = c.dim == 2 ? cg_iteration_2d : cg_iteration;
   cudaGraph_t g = nullptr;
   cudaGraphConditionalHandle loop = 0;
   cudaStream_t saved = c.stream;
@@ -382,7 +417,7 @@ static bool build_cg_graph(Ctx& c) {
     try {
       k_cg_reset<<<1, 1, 0, c.stream>>>(c.dsc);
       MGAR_LAUNCH_CHECK();
-      cg_iteration(c, true, loop);
+      iteration(c, true, loop);
       // the WHILE node after everything captured so far
       cudaStreamCaptureStatus st;
       cudaGraph_t cg = nullptr;
@@ -414,7 +449,7 @@ static bool build_cg_graph(Ctx& c) {
     c.stream = c.cap_stream;
     const int64_t body_before = launches_so_far();
     try {
-      cg_iteration(c, false, loop);
+      iteration(c, false, loop);
     } catch (...) {
       issued = false;
     }
@@ -425,6 +460,7 @@ static bool build_cg_graph(Ctx& c) {
     if (!issued || e != cudaSuccess) { fail(e); break; }
     e = cudaGraphInstantiate(&c.cg_exec, g, 0);
     if (e != cudaSuccess) { c.cg_exec = nullptr; fail(e); break; }
+    c.cg_exec_cgmax = c.p.cg_max;
     ok = true;
   } while (false);
   c.stream = saved;
@@ -433,6 +469,16 @@ static bool build_cg_graph(Ctx& c) {
   c.prologue_kernels = captured - c.body_kernels;
   if (g) cudaGraphDestroy(g);
   return ok;
+}
+
+// The graph holds the iteration cap by value: one built for another cap
+// (the df64 CG finishing a reliable-update solve gets the iterations left)
+// is rebuilt.
+static void drop_stale_cg_graph(Ctx& c) {
+  if (c.cg_exec && c.cg_exec_cgmax != c.p.cg_max) {
+    MGAR_CUDA(cudaGraphExecDestroy(c.cg_exec));
+    c.cg_exec = nullptr;
+  }
 }
 
 static int solve_mgcg_df3(Ctx& c, double* T, int* iters, double* relres) {
@@ -451,6 +497,7 @@ static int solve_mgcg_df3(Ctx& c, double* T, int* iters, double* relres) {
   // (event records cannot sit inside a conditional body)
   if (!(rel <= c.p.eps2) && c.cg_graph && c.prof_class == 0 && c.use_graphs) {
     require(std::isfinite(rel), MGAR_ERR_NONFINITE, "non-finite initial residual");
+    drop_stale_cg_graph(c);
     if (!c.cg_exec && !build_cg_graph(c)) c.cg_graph = false;
   }
   if (!(rel <= c.p.eps2) && c.cg_exec && c.prof_class == 0 && c.use_graphs) {
@@ -855,7 +902,23 @@ int solve_mgcg_df(Ctx& c, double* T, int* iters, double* relres) {
   fetch_scalars(c, S_RR, 1);
   double rel = std::sqrt(c.hsc[S_RR]) / c.qnorm;
   int it = 0;
-  if (!(rel <= c.p.eps2)) {
+  // 2D: the device-side loop while no kernel class is being timed with
+  // events (event records cannot sit inside a conditional body)
+  const bool graph = c.dim == 2 && c.cg_graph && c.prof_class == 0 && c.use_graphs;
+  if (!(rel <= c.p.eps2) && graph) {
+    require(std::isfinite(rel), MGAR_ERR_NONFINITE, "non-finite initial residual");
+    drop_stale_cg_graph(c);
+    if (!c.cg_exec && !build_cg_graph(c)) c.cg_graph = false;
+  }
+  if (!(rel <= c.p.eps2) && graph && c.cg_exec) {
+    join_coarse(c);
+    MGAR_CUDA(cudaGraphLaunch(c.cg_exec, c.stream));
+    fetch_scalars(c, S_RR, S_CGIT - S_RR + 1);
+    it = (int)c.hsc[S_CGIT];
+    count_launches(c.prologue_kernels + (int64_t)std::max(it - 1, 0) * c.body_kernels);
+    rel = std::sqrt(c.hsc[S_RR]) / c.qnorm;
+    require(std::isfinite(rel), MGAR_ERR_NONFINITE, "CG breakdown (non-finite residual)");
+  } else if (!(rel <= c.p.eps2)) {
     require(std::isfinite(rel), MGAR_ERR_NONFINITE, "non-finite initial residual");
     precondition_df(c);
     int a = S_RZ0, b = S_RZ1;

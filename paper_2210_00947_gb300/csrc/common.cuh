@@ -240,6 +240,7 @@ struct Ctx {
   // device-side CG loop (3D mixed path): one graph with a conditional WHILE node
   bool cg_graph = true;
   cudaGraphExec_t cg_exec = nullptr;
+  int cg_exec_cgmax = 0;   // the iteration cap captured in cg_exec
   int64_t prologue_kernels = 0, body_kernels = 0;
   // 3D mixed path: FP32 CG iterations with reliable updates of x and r in
   // df64 (MGAR_DF64_CG=1 selects the df64 CG); an update whenever ||r||
@@ -271,6 +272,7 @@ struct Ctx {
   // instrumentation: CUDA-event timing of one kernel class
   int prof_class = 0;
   int prof_used = 0;
+  bool prof_open = false;  // a scope of the timed class is open (inner ones are not timed)
   cudaEvent_t* prof_ev = nullptr;  // [2 * kProfMax]
   // timeline mode (prof_class == MGAR_KC_TIMELINE): an event after every
   // launch site; device time between consecutive marks goes to the later site
@@ -309,13 +311,18 @@ Ctx*& current_ctx();
 struct ProfScope {
   Ctx& c;
   bool on;
-  ProfScope(Ctx& ctx, int kc) : c(ctx), on(ctx.prof_class == kc && ctx.prof_used < kProfMax) {
-    if (on) cudaEventRecord(c.prof_ev[2 * c.prof_used], c.stream);
+  ProfScope(Ctx& ctx, int kc)
+      : c(ctx), on(ctx.prof_class == kc && ctx.prof_used < kProfMax && !ctx.prof_open) {
+    if (on) {
+      cudaEventRecord(c.prof_ev[2 * c.prof_used], c.stream);
+      c.prof_open = true;  // a nested scope of the same class is part of this one
+    }
   }
   ~ProfScope() {
     if (on) {
       cudaEventRecord(c.prof_ev[2 * c.prof_used + 1], c.stream);
       ++c.prof_used;
+      c.prof_open = false;
     }
   }
 };
