@@ -357,6 +357,7 @@ __global__ void k_oc_init(double* dsc, double lo, double hi) {
   dsc[S_OC_HI] = hi;
   dsc[S_OC_DONE] = 0.0;
   dsc[S_OC_STEPS] = 0.0;
+  dsc[S_OC_FAIL] = 0.0;  // the update by the plain bisection is applied
 }
 
 // ---- OC solve for mu = 1/sqrt(lambda) without 50 FP64 passes ----------
@@ -533,13 +534,34 @@ __global__ void k_oc_finish(const double* __restrict__ s, const double* __restri
   const int lane = threadIdx.x;
   const double C = dsc[S_OC_C], B = dsc[S_OC_B];
   double a = dsc[S_OC_MUA], b = dsc[S_OC_MUB];
+  // up to kCache ambiguous elements are staged in shared memory, so the
+  // bisection steps do not wait on global loads; the same elements in the
+  // same order as the loads below otherwise
+  constexpr int kCache = 256;
+  __shared__ double cs[kCache], cl[kCache], ch[kCache], cd[kCache];
+  const bool cached = namb <= kCache;
+  if (cached) {
+    for (int i = lane; i < namb; i += 32) {
+      const int e = CK(i, kOcAmbMax) ? key[i] : 0;
+      const bool ok = CK(e, ne);
+      cs[i] = ok ? s[e] : 0.0;
+      cl[i] = ok ? lo[e] : 0.0;
+      ch[i] = ok ? hi[e] : 0.0;
+      cd[i] = ok ? dv[e] : 0.0;
+    }
+    __syncwarp();
+  }
   auto g = [&](double mu) {
     double acc = 0.0;
-    for (int i = lane; i < namb; i += 32) {
-      if (!CK(i, kOcAmbMax)) continue;
-      const int e = key[i];
-      if (!CK(e, ne)) continue;
-      acc += dv[e] * fmin(fmax(s[e] * mu, lo[e]), hi[e]);
+    if (cached) {
+      for (int i = lane; i < namb; i += 32) acc += cd[i] * fmin(fmax(cs[i] * mu, cl[i]), ch[i]);
+    } else {
+      for (int i = lane; i < namb; i += 32) {
+        if (!CK(i, kOcAmbMax)) continue;
+        const int e = key[i];
+        if (!CK(e, ne)) continue;
+        acc += dv[e] * fmin(fmax(s[e] * mu, lo[e]), hi[e]);
+      }
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     return C + B * mu + acc;
@@ -559,10 +581,13 @@ __global__ void k_oc_finish(const double* __restrict__ s, const double* __restri
   if (lane == 0) dsc[S_OC_MU] = 0.5 * (a + b);
 }
 
-// rho <- clamp(s mu) for mu = dsc[S_OC_MU]; max |change| into dsc.
+// rho <- clamp(s mu) for mu = dsc[S_OC_MU]; max |change| into dsc.  Skipped
+// (every block) while the fast solve's failure flag is up: the host then
+// runs the plain bisection and this kernel again.
 __global__ void k_oc_apply(double* __restrict__ rho, const double* __restrict__ s,
                            const double* __restrict__ lo, const double* __restrict__ hi, int ne,
                            double* dsc, double* partials, unsigned int* counter) {
+  if (dsc[S_OC_FAIL] != 0.0) return;
   const double mu = dsc[S_OC_MU];
   double ch = 0.0;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
@@ -832,9 +857,13 @@ void oc_update(Ctx& c, double* rho, const double* dc, double volfrac, double mov
     k_oc_finish<<<1, 1024, 0, c.stream>>>(c.oc_s, c.oc_lo, c.oc_hi, c.dv, ne, volfrac, c.dsc,
                                           c.oc_amb, c.oc_namb);
     MGAR_LAUNCH_CHECK();
-    // one fetch from S_COMPL on: a compliance dot launched before the
-    // update arrives with the check
-    fetch_scalars(c, S_COMPL, S_OC_FAIL - S_COMPL + 1);
+    // applied unless the fast solve failed; one fetch from S_OC_LAM on
+    // brings the check, lambda, the change and a compliance dot launched
+    // before the update
+    k_oc_apply<<<rb, kThreads, 0, c.stream>>>(rho, c.oc_s, c.oc_lo, c.oc_hi, ne, c.dsc, c.partials,
+                                              c.counter);
+    MGAR_LAUNCH_CHECK();
+    fetch_scalars(c, S_OC_LAM, S_OC_FAIL - S_OC_LAM + 1);
     fast_ok = c.hsc[S_OC_FAIL] == 0.0;
   }
   if (!fast_ok) {
@@ -853,15 +882,13 @@ void oc_update(Ctx& c, double* rho, const double* dc, double volfrac, double mov
     }
     k_oc_mu_from_bracket<<<1, 1, 0, c.stream>>>(c.dsc);
     MGAR_LAUNCH_CHECK();
-  }
-  k_oc_apply<<<rb, kThreads, 0, c.stream>>>(rho, c.oc_s, c.oc_lo, c.oc_hi, ne, c.dsc, c.partials,
-                                            c.counter);
-  MGAR_LAUNCH_CHECK();
-  if (lambda || change) {
+    k_oc_apply<<<rb, kThreads, 0, c.stream>>>(rho, c.oc_s, c.oc_lo, c.oc_hi, ne, c.dsc, c.partials,
+                                              c.counter);
+    MGAR_LAUNCH_CHECK();
     fetch_scalars(c, S_OC_LAM, 3);
-    if (lambda) *lambda = c.hsc[S_OC_LAM];
-    if (change) *change = c.hsc[S_OC_CHANGE];
   }
+  if (lambda) *lambda = c.hsc[S_OC_LAM];
+  if (change) *change = c.hsc[S_OC_CHANGE];
   c.oc_fallbacks += fast_ok ? 0 : 1;
 }
 
