@@ -768,7 +768,11 @@ __device__ __forceinline__ Real fine_row3(const FineOp<Real>& op, const Real* __
 }
 
 // Assembled (Galerkin) coarse operator: S = 3^d coefficients per node,
-// stored as st[s*n + i] with s = (dx+1) + 3(dy+1) [+ 9(dz+1)].
+// s = (dx+1) + 3(dy+1) [+ 9(dz+1)], of which the operator's symmetry
+// (A = P^T A_f P) leaves the upper half to store: slots s >= SH (the centre
+// SH = S/2 and the neighbours after it in grid order) as st[(s-SH)*n + i];
+// a lower slot's coefficient is the neighbour's mirror one, st[(SH-s)*n + j]
+// with j = i + offset(s).  Half the bytes per pass and per build.
 template <typename Real>
 struct StencilOp {
   const Real* st;
@@ -778,12 +782,27 @@ struct StencilOp {
   FastDiv fNX, fNXY;
 };
 
+// stored slots per node (upper half with the centre)
+constexpr int stencil_slots(int dim) { return dim == 2 ? 5 : 14; }
+
+// Coefficient of full slot s in row idx; nb is the neighbour's index and
+// in_grid whether it lies in the grid (the assembled coefficient of a
+// neighbour outside is zero; a lower slot reads the neighbour's storage, so
+// it needs the test, an upper one holds the zero itself).
+template <int DIM, typename Real>
+__device__ __forceinline__ Real st_coef(const StencilOp<Real>& op, int s, int idx, int nb,
+                                        bool in_grid) {
+  constexpr int SH = DIM == 2 ? 4 : 13;
+  if (s >= SH) return op.st[(s - SH) * op.n + idx];
+  return in_grid ? op.st[(SH - s) * op.n + nb] : Real(0);
+}
+
 template <typename Real, bool CG = false>
 __device__ __forceinline__ Real stencil_row2(const StencilOp<Real>& op, const Real* __restrict__ x,
                                              int i, int j) {
   const int idx = i + op.NX * j;
   // the assembled coefficient of a neighbour outside the grid is zero, so
-  // clamped coordinates give the same sum without branches
+  // clamped coordinates give the same sum
   Real acc = Real(0);
 #pragma unroll
   for (int dy = -1; dy <= 1; ++dy) {
@@ -794,7 +813,8 @@ __device__ __forceinline__ Real stencil_row2(const StencilOp<Real>& op, const Re
       const int s = (dx + 1) + 3 * (dy + 1);
       const int nb = ii + op.NX * jj;
       if (!CK(nb, op.n) || !CK(idx, op.n)) continue;
-      acc += op.st[s * op.n + idx] * (CG ? __ldcg(x + nb) : x[nb]);
+      const bool in = ii == i + dx && jj == j + dy;
+      acc += st_coef<2>(op, s, idx, nb, in) * (CG ? __ldcg(x + nb) : x[nb]);
     }
   }
   return acc;
@@ -821,7 +841,8 @@ __device__ __forceinline__ Real stencil_row3(const StencilOp<Real>& op, const Re
         const int s = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
         const int nb = ii + NX * jj + NXY * kk;
         const bool ok = CK(nb, op.n) && CK(idx, op.n);
-        sv[s] = ok ? op.st[s * op.n + idx] : Real(0);
+        const bool in = ii == i + dx && jj == j + dy && kk == k + dz;
+        sv[s] = ok ? st_coef<3>(op, s, idx, nb, in) : Real(0);
         xv[s] = ok ? (CG ? __ldcg(x + nb) : x[nb]) : Real(0);
       }
     }

@@ -287,8 +287,9 @@ __global__ void k_assemble(const Real* __restrict__ elem, Dims d, Real* __restri
       acc[s] += row[J];
     }
   }
+  // the upper half with the centre (the operator is symmetric)
 #pragma unroll
-  for (int s = 0; s < S; ++s) st[s * (int)d.n + idx] = acc[s];
+  for (int s = S / 2; s < S; ++s) st[(s - S / 2) * (int)d.n + idx] = acc[s];
   dinv[idx] = Real(1) / acc[S / 2];
 }
 
@@ -332,8 +333,11 @@ __global__ void k_band_fill(const Real* __restrict__ st, Dims d, int bw, B* __re
     if (ii < 0 || ii >= d.NX || jj < 0 || jj >= d.NY || kk < 0 || kk >= d.NZ) continue;
     const int col = ii + d.NX * (jj + d.NY * kk);  // no load depends on it before the check
     if (col > idx) continue;
+    // col <= idx: the centre, or a lower slot held by the neighbour col as
+    // its mirror (upper) slot S - 1 - s
+    const int64_t at = s == S / 2 ? (int64_t)idx : (int64_t)(S / 2 - s) * d.n + col;
     if (CK((int64_t)idx * (bw + 1) + (col - idx + bw), d.n * (bw + 1)) && CK(col - idx + bw, bw + 1))
-      band[(int64_t)idx * (bw + 1) + (col - idx + bw)] = (B)st[s * (int)d.n + idx];
+      band[(int64_t)idx * (bw + 1) + (col - idx + bw)] = (B)st[at];
   }
 }
 
@@ -599,7 +603,7 @@ static void alloc_levels(Ctx& c, LevelBuf<Real>* h) {
     MGAR_CUDA(cudaMalloc(&h[l].t, d.n * sizeof(Real)));
     MGAR_CUDA(cudaMalloc(&h[l].r, d.n * sizeof(Real)));
     if (l >= 1) {
-      MGAR_CUDA(cudaMalloc(&h[l].st, (size_t)c.S * d.n * sizeof(Real)));
+      MGAR_CUDA(cudaMalloc(&h[l].st, (size_t)stencil_slots(c.dim) * d.n * sizeof(Real)));
       MGAR_CUDA(cudaMalloc(&h[l].elem, (size_t)d.ne * nen * nen * sizeof(Real)));
       MGAR_CUDA(cudaMalloc(&h[l].x, d.n * sizeof(Real)));
       MGAR_CUDA(cudaMalloc(&h[l].b, d.n * sizeof(Real)));

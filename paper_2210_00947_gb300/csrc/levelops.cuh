@@ -219,7 +219,8 @@ __device__ __forceinline__ void post_node(const StencilOp<Real>& op, const Real*
         if (!CK(nb, op.n)) continue;
         const Real v = ldv<CG>(cur + nb) + pv;
         const int s = tx + 3 * ty + 9 * tz;
-        acc += op.st[s * op.n + idx] * v;
+        const bool in = ii == i - 1 + tx && jj == j - 1 + ty && (DIM == 2 || kk == k - 1 + tz);
+        acc += st_coef<DIM>(op, s, idx, nb, in) * v;
         if (tx == 1 && ty == 1 && tz == (DIM == 3 ? 1 : 0)) vc = v;
       }
     }
