@@ -797,60 +797,84 @@ __device__ __forceinline__ Real st_coef(const StencilOp<Real>& op, int s, int id
   return in_grid ? op.st[(SH - s) * op.n + nb] : Real(0);
 }
 
-template <typename Real, bool CG = false>
-__device__ __forceinline__ Real stencil_row2(const StencilOp<Real>& op, const Real* __restrict__ x,
-                                             int i, int j) {
-  const int idx = i + op.NX * j;
-  // the assembled coefficient of a neighbour outside the grid is zero, so
-  // clamped coordinates give the same sum
-  Real acc = Real(0);
-#pragma unroll
-  for (int dy = -1; dy <= 1; ++dy) {
-    const int jj = min(max(j + dy, 0), op.NY - 1);
-#pragma unroll
-    for (int dx = -1; dx <= 1; ++dx) {
-      const int ii = min(max(i + dx, 0), op.NX - 1);
-      const int s = (dx + 1) + 3 * (dy + 1);
-      const int nb = ii + op.NX * jj;
-      if (!CK(nb, op.n) || !CK(idx, op.n)) continue;
-      const bool in = ii == i + dx && jj == j + dy;
-      acc += st_coef<2>(op, s, idx, nb, in) * (CG ? __ldcg(x + nb) : x[nb]);
-    }
-  }
-  return acc;
-}
+// A row in two halves: the coefficients (hierarchy data, so a kernel may
+// gather them before it waits on its predecessor) and the product with x in
+// slot order s = (dx+1) + 3 (dy+1) [+ 9 (dz+1)].  Clamped coordinates: the
+// coefficient of a neighbour outside the grid is zero, so the clamped
+// operand value it meets does not matter.
+template <int DIM>
+__host__ __device__ constexpr int stencil_size() { return DIM == 2 ? 9 : 27; }
 
-// The 27 coefficients and operand values are loaded before the first
-// product (compile-time slots), so a row costs one memory round trip; the
-// products are summed in the slot order s = (dx+1) + 3 (dy+1) + 9 (dz+1).
-template <typename Real, bool CG = false>
-__device__ __forceinline__ Real stencil_row3(const StencilOp<Real>& op, const Real* __restrict__ x,
-                                             int i, int j, int k) {
+template <int DIM, typename Real>
+__device__ __forceinline__ void stencil_coefs(const StencilOp<Real>& op, int i, int j, int k,
+                                              Real (&sv)[stencil_size<DIM>()]) {
   const int NX = op.NX, NXY = op.NX * op.NY;
-  const int idx = i + NX * j + NXY * k;
-  Real sv[27], xv[27];
+  const int idx = i + NX * j + (DIM == 3 ? NXY * k : 0);
 #pragma unroll
-  for (int dz = -1; dz <= 1; ++dz) {
-    const int kk = min(max(k + dz, 0), op.NZ - 1);
+  for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz) {
+    const int kk = DIM == 3 ? min(max(k + dz, 0), op.NZ - 1) : 0;
 #pragma unroll
     for (int dy = -1; dy <= 1; ++dy) {
       const int jj = min(max(j + dy, 0), op.NY - 1);
 #pragma unroll
       for (int dx = -1; dx <= 1; ++dx) {
         const int ii = min(max(i + dx, 0), op.NX - 1);
-        const int s = (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
-        const int nb = ii + NX * jj + NXY * kk;
+        const int s = (dx + 1) + 3 * (dy + 1) + (DIM == 3 ? 9 * (dz + 1) : 0);
+        const int nb = ii + NX * jj + (DIM == 3 ? NXY * kk : 0);
         const bool ok = CK(nb, op.n) && CK(idx, op.n);
-        const bool in = ii == i + dx && jj == j + dy && kk == k + dz;
-        sv[s] = ok ? st_coef<3>(op, s, idx, nb, in) : Real(0);
+        const bool in = ii == i + dx && jj == j + dy && (DIM == 2 || kk == k + dz);
+        sv[s] = ok ? st_coef<DIM>(op, s, idx, nb, in) : Real(0);
+      }
+    }
+  }
+}
+
+template <int DIM, typename Real, bool CG = false>
+__device__ __forceinline__ Real stencil_apply(const StencilOp<Real>& op, const Real* __restrict__ x,
+                                              int i, int j, int k,
+                                              const Real (&sv)[stencil_size<DIM>()]) {
+  const int NX = op.NX, NXY = op.NX * op.NY;
+  const int idx = i + NX * j + (DIM == 3 ? NXY * k : 0);
+  constexpr int S = stencil_size<DIM>();
+  Real xv[S];
+#pragma unroll
+  for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz) {
+    const int kk = DIM == 3 ? min(max(k + dz, 0), op.NZ - 1) : 0;
+#pragma unroll
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int jj = min(max(j + dy, 0), op.NY - 1);
+#pragma unroll
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int ii = min(max(i + dx, 0), op.NX - 1);
+        const int s = (dx + 1) + 3 * (dy + 1) + (DIM == 3 ? 9 * (dz + 1) : 0);
+        const int nb = ii + NX * jj + (DIM == 3 ? NXY * kk : 0);
+        const bool ok = CK(nb, op.n) && CK(idx, op.n);
         xv[s] = ok ? (CG ? __ldcg(x + nb) : x[nb]) : Real(0);
       }
     }
   }
   Real acc = Real(0);
 #pragma unroll
-  for (int s = 0; s < 27; ++s) acc += sv[s] * xv[s];
+  for (int s = 0; s < S; ++s) acc += sv[s] * xv[s];
   return acc;
+}
+
+// The whole row: coefficients and operand values loaded before the first
+// product, so a row costs one memory round trip.
+template <typename Real, bool CG = false>
+__device__ __forceinline__ Real stencil_row2(const StencilOp<Real>& op, const Real* __restrict__ x,
+                                             int i, int j) {
+  Real sv[9];
+  stencil_coefs<2>(op, i, j, 0, sv);
+  return stencil_apply<2, Real, CG>(op, x, i, j, 0, sv);
+}
+
+template <typename Real, bool CG = false>
+__device__ __forceinline__ Real stencil_row3(const StencilOp<Real>& op, const Real* __restrict__ x,
+                                             int i, int j, int k) {
+  Real sv[27];
+  stencil_coefs<3>(op, i, j, k, sv);
+  return stencil_apply<3, Real, CG>(op, x, i, j, k, sv);
 }
 
 // Coordinates of flat index idx on a row-major (x fastest) box whose rows

@@ -801,8 +801,9 @@ static void build_levels(Ctx& c, const Real* ke0, LevelBuf<Real>* h) {
 
 void build_hierarchy(Ctx& c) {
   cudaStream_t s = c.stream;
-  MGAR_CUDA(cudaMemcpyAsync(c.ke0, c.ke, c.ne * sizeof(double), cudaMemcpyDeviceToDevice, s));
   if (c.p.precision == MGAR_FP64) {
+    // the reference k_e of MGAR's K - K0 (the mixed path keeps only its FP32 copy)
+    MGAR_CUDA(cudaMemcpyAsync(c.ke0, c.ke, c.ne * sizeof(double), cudaMemcpyDeviceToDevice, s));
     if (c.dim == 2) build_levels<double, 2>(c, c.ke0, c.h64);
     else build_levels<double, 3>(c, c.ke0, c.h64);
   } else {

@@ -153,12 +153,13 @@ __device__ __forceinline__ void interp_axis(int f, int nf, int& c0, float (&w)[3
 // v = x + P x_c at the node and its neighbours, x' = v + w D^-1 (b - A v).
 // The 3^d coarse values around the node are read once and interpolated
 // separably onto the 3^d fine positions.
-template <typename Real, int DIM, bool CG>
+// PRE: the row's coefficients were gathered already (sv, slot order).
+template <typename Real, int DIM, bool CG, bool PRE = false>
 __device__ __forceinline__ void post_node(const StencilOp<Real>& op, const Real* __restrict__ xc,
                                           const Real* __restrict__ cur, const Real* __restrict__ b,
                                           const Real* __restrict__ dinv, Real omega,
                                           Real* __restrict__ dst, const Dims& f, const Dims& cd,
-                                          int idx) {
+                                          int idx, const Real* sv = nullptr) {
   int i, j, k;
   coords(idx, op.fNX, op.fNXY, i, j, k);
   constexpr int NZ3 = DIM == 3 ? 3 : 1;
@@ -220,7 +221,7 @@ __device__ __forceinline__ void post_node(const StencilOp<Real>& op, const Real*
         const Real v = ldv<CG>(cur + nb) + pv;
         const int s = tx + 3 * ty + 9 * tz;
         const bool in = ii == i - 1 + tx && jj == j - 1 + ty && (DIM == 2 || kk == k - 1 + tz);
-        acc += st_coef<DIM>(op, s, idx, nb, in) * v;
+        acc += (PRE ? sv[s] : st_coef<DIM>(op, s, idx, nb, in)) * v;
         if (tx == 1 && ty == 1 && tz == (DIM == 3 ? 1 : 0)) vc = v;
       }
     }

@@ -178,12 +178,26 @@ __global__ void k_prolong3(const Real* __restrict__ xc, const Real* cur, Real* d
   }
 }
 
+// The coarse-level kernels gather what the hierarchy build wrote (stencil
+// coefficients, D^-1, the coarsest inverse) before they wait on their
+// predecessor: a kernel may start while its predecessor runs, and every
+// kernel here waits before it lets its own successor start, so everything
+// older than the predecessor is complete and visible by then.  The latency
+// of those loads overlaps the predecessor's tail; the arithmetic and its
+// order are unchanged.
 template <typename Real, int DIM>
 __global__ void k_resid_coarse(StencilOp<Real> op, const Real* __restrict__ b,
                                const Real* __restrict__ x, Real* __restrict__ r) {
-  pdl_wait();
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx < op.n) resid_node<Real, DIM, false>(op, b, x, r, idx);
+  const bool on = idx < op.n;
+  int i = 0, j = 0, k = 0;
+  Real sv[stencil_size<DIM>()];
+  if (on) {
+    coords(idx, op.fNX, op.fNXY, i, j, k);
+    stencil_coefs<DIM>(op, i, j, k, sv);
+  }
+  pdl_wait();
+  if (on) r[idx] = b[idx] - stencil_apply<DIM, Real, false>(op, x, i, j, k, sv);
   pdl_trigger();
 }
 
@@ -192,19 +206,74 @@ __global__ void k_post_coarse(StencilOp<Real> op, const Real* __restrict__ xc,
                               const Real* __restrict__ cur, const Real* __restrict__ b,
                               const Real* __restrict__ dinv, Real omega, Real* __restrict__ dst,
                               Dims f, Dims cd) {
-  pdl_wait();
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx < op.n) post_node<Real, DIM, false>(op, xc, cur, b, dinv, omega, dst, f, cd, idx);
+  const bool on = idx < op.n;
+  Real sv[stencil_size<DIM>()];
+  if (on) {
+    int i, j, k;
+    coords(idx, op.fNX, op.fNXY, i, j, k);
+    stencil_coefs<DIM>(op, i, j, k, sv);
+  }
+  pdl_wait();
+  if (on) post_node<Real, DIM, false, true>(op, xc, cur, b, dinv, omega, dst, f, cd, idx, sv);
   pdl_trigger();
 }
 
+// One damped-Jacobi sweep on an assembled level, x' = x + w D^-1 (b - A x).
+template <typename Real, int DIM>
+__global__ void k_jacobi_st(StencilOp<Real> op, const Real* __restrict__ b,
+                            const Real* __restrict__ xin, Real* __restrict__ xout,
+                            const Real* __restrict__ dinv, Real omega) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool on = idx < op.n;
+  int i = 0, j = 0, k = 0;
+  Real sv[stencil_size<DIM>()];
+  Real dv = Real(0);
+  if (on) {
+    coords(idx, op.fNX, op.fNXY, i, j, k);
+    stencil_coefs<DIM>(op, i, j, k, sv);
+    dv = dinv[idx];
+  }
+  pdl_wait();
+  if (on) {
+    const Real ax = stencil_apply<DIM, Real, false>(op, xin, i, j, k, sv);
+    xout[idx] = xin[idx] + omega * dv * (b[idx] - ax);
+  }
+  pdl_trigger();
+}
+
+// x = C b with the explicit inverse of the coarsest operator: a warp per
+// row, the row's entries loaded before the wait when it has at most 128
+// (four per lane), summed in the same order as coarse_row.
 template <typename Real, typename M>
 __global__ void k_coarse_solve(const M* __restrict__ cinv, const Real* __restrict__ b,
                                Real* __restrict__ x, int n) {
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  const bool pre = n <= 128;
+  M cv[4] = {M(0), M(0), M(0), M(0)};
+  if (pre && row < n) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int jj = lane + 32 * q;
+      if (jj < n && CK((int64_t)row * n + jj, (int64_t)n * n)) cv[q] = cinv[(int64_t)row * n + jj];
+    }
+  }
   pdl_wait();
   pdl_trigger();
-  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (row < n) coarse_row<Real, false, M>(cinv, b, x, n, row, threadIdx.x & 31);
+  if (row >= n) return;
+  if (!pre) {
+    coarse_row<Real, false, M>(cinv, b, x, n, row, lane);
+    return;
+  }
+  M s = M(0);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int jj = lane + 32 * q;
+    if (jj < n) s += cv[q] * (M)b[jj];
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) x[row] = (Real)s;
 }
 
 // ------------------------------------------- bottom of the V-cycle, one cluster
@@ -320,8 +389,8 @@ static void sweep(Ctx& c, int l, const Real* b, const Real* xin, Real* xout) {
     k_jacobi<<<blocks_for(d.n), kThreads, 0, c.stream>>>(fine_row<Real, DIM>(c, ref_ke<Real>(c), nullptr),
                                                          b, xin, xout, h[0].dinv, om);
   else
-    k_jacobi<<<blocks_for(d.n), kThreads, 0, c.stream>>>(stencil_row<Real, DIM>(c, l), b, xin, xout,
-                                                         h[l].dinv, om);
+    launch_pdl(c.stream, c.use_pdl, k_jacobi_st<Real, DIM>, dim3(blocks_for(d.n)), dim3(kThreads),
+               stencil_row<Real, DIM>(c, l).op, b, xin, xout, (const Real*)h[l].dinv, om);
   MGAR_LAUNCH_CHECK_AT(level_site(1, l));
 }
 
