@@ -286,7 +286,11 @@ __global__ void __launch_bounds__(T::NTB, f3d_minb(MODE, T::NT)) k_fine3d(FineAr
   Real cv[4], cb[4], cd[4], mv[4];
   bool cf[4];
   const bool rdot = (MODE == POST || MODE == SWEEP || MODE == DIR) && a.dout != nullptr;
+  // the thread's terms of p . Ap, or of r . x' with r in FP32, are few (one z
+  // run, about 20): summed in FP32 and combined across threads in df64; r in
+  // df64 pairs keeps a df64 sum
   df dacc{0.f, 0.f};
+  float facc = 0.f;
 
   auto issue_plane_to = [&](int p, NodeFetch<Real, MODE>& o, NodeFetch<Real, MODE>& rg, Real& ob,
                             Real& od) {
@@ -384,13 +388,13 @@ __global__ void __launch_bounds__(T::NTB, f3d_minb(MODE, T::NT)) k_fine3d(FineAr
       } else if (MODE == DIR) {                                                            \
         pdst[idx] = xi;                                                                    \
         ((Real*)a.out1)[idx] = ax;                                                         \
-        if (rdot) dacc = df_add(dacc, df_mulf(df{(float)xi, 0.f}, (float)ax));             \
+        if (rdot) facc = fmaf((float)xi, (float)ax, facc);                                  \
       } else {                                                                             \
         const Real xo = xi + om * cd[S1] * (bi - ax);                                      \
         ((Real*)a.out0)[idx] = xo;                                                         \
         if (rdot) {                                                                        \
-          const df rr = a.rdot ? df{rv.x, rv.y} : df{(float)bi, 0.f};                      \
-          dacc = df_add(dacc, df_mulf(rr, (float)xo));                                     \
+          if (a.rdot) dacc = df_add(dacc, df_mulf(df{rv.x, rv.y}, (float)xo));              \
+          else facc = fmaf((float)bi, (float)xo, facc);                                    \
         }                                                                                  \
       }                                                                                    \
     }                                                                                      \
@@ -410,7 +414,8 @@ __global__ void __launch_bounds__(T::NTB, f3d_minb(MODE, T::NT)) k_fine3d(FineAr
     double t;
     const int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     const int nb = gridDim.x * gridDim.y * gridDim.z;
-    if (block_sum_last_df(dacc, a.partials, a.counter, t, tid, T::NTB, bid, nb) && tid == 0) {
+    const df v = df_add(dacc, df{facc, 0.f});
+    if (block_sum_last_df(v, a.partials, a.counter, t, tid, T::NTB, bid, nb) && tid == 0) {
       a.dout[0] = t;
       if (MODE == DIR && a.rz_set) *a.rz_set = *a.rz_new;  // every block has read rz_new
     }
