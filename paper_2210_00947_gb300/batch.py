@@ -119,22 +119,26 @@ def run_designs(designs: list[Design], cycles: int, workers: int = 16,
 
 
 def run_designs_batched(designs: list[Design], cycles: int, workers: int = 16, device: int = 0,
-                        nl: int = 5, **overrides):
+                        nl: int = 5, groups: int = 1, **overrides):
     """Optimise every design for `cycles` design cycles, MGCG in every cycle,
-    with one batched solve per cycle over all designs (mgar_batch_solve_mgcg:
-    one launch per V-cycle level and operation for the whole set).  Per
-    cycle: each design's filter and SIMP (queued on its own stream), the
-    batched solve (its stream waits for them), then each design's
-    sensitivities and OC update, `workers` designs at a time on host threads.
-    Mixed precision (FP32 V-cycle, FP64 CG).  Returns, per design, the final
-    densities and compliances, the seconds of the cycles, and the batched
-    solver's autotuner report."""
+    with batched solves (mgar_batch_solve_mgcg: one launch per V-cycle level
+    and operation for a whole batch).  Per cycle of a batch: each design's
+    filter and SIMP (queued on its own stream), the batched solve (its
+    stream waits for them), then each design's sensitivities and OC update
+    on host threads.  With groups > 1 the designs are dealt round-robin into
+    that many batches, each with its own batched solver, stream and host
+    thread, so that one batch's solve overlaps another's per-design work
+    (results do not depend on the grouping: every reduction has a fixed
+    order per design).  Mixed precision (FP32 V-cycle, FP64 CG).  Returns,
+    per design, the final densities and compliances, the seconds of the
+    cycles, and the first batch's autotuner report."""
     import time
 
     import torch
 
     torch.cuda.set_device(device)
     dev = torch.device("cuda", device)
+    groups = max(1, min(groups, len(designs)))
     streams, solvers, rhos, Ts, dcs = [], [], [], [], []
     for d in designs:
         st = torch.cuda.Stream(dev)
@@ -144,40 +148,55 @@ def run_designs_batched(designs: list[Design], cycles: int, workers: int = 16, d
         rhos.append(torch.tensor(d.density(), device=dev))
         Ts.append(torch.zeros(solvers[-1].n_nodes, dtype=torch.float64, device=dev))
         dcs.append(torch.empty(d.nx * d.ny, dtype=torch.float64, device=dev))
-    bstream = torch.cuda.Stream(dev)
-    bs = mgar.BatchSolver(solvers, stream=bstream)
+    members = [list(range(g, len(designs), groups)) for g in range(groups)]
+    bstreams = [torch.cuda.Stream(dev) for _ in range(groups)]
+    bsolvers = [mgar.BatchSolver([solvers[i] for i in m], stream=bs)
+                for m, bs in zip(members, bstreams)]
     hist = [[] for _ in designs]
-    pool = cf.ThreadPoolExecutor(max_workers=max(1, workers))
+    per = max(1, workers // groups)
+    pools = [cf.ThreadPoolExecutor(max_workers=per) for _ in range(groups)]
 
     def design_update(i):
         c = solvers[i].sensitivity(Ts[i], dcs[i])
         solvers[i].oc_update(rhos[i], dcs[i], designs[i].volfrac, 0.2)
         return c
 
-    def cycle():
-        for i, s in enumerate(solvers):
-            s.set_density(rhos[i])
+    def cycle(g):
+        m, bs, bstream = members[g], bsolvers[g], bstreams[g]
+        for i in m:
+            solvers[i].set_density(rhos[i])
             ev = torch.cuda.Event()
             ev.record(streams[i])
             bstream.wait_event(ev)
-        res = bs.solve(Ts)
-        comps = list(pool.map(design_update, range(len(designs))))
-        for i, (c, r) in enumerate(zip(comps, res)):
+        res = bs.solve([Ts[i] for i in m])
+        comps = list(pools[g].map(design_update, m))
+        for i, c, r in zip(m, comps, res):
             hist[i].append(dict(compliance=c, cg_iters=r[0], converged=r[2]))
+
+    def run_group(g):
+        torch.cuda.set_device(device)
+        for _ in range(cycles):
+            cycle(g)
+        for i in members[g]:
+            streams[i].synchronize()
 
     try:
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        for _ in range(cycles):
-            cycle()
-        for st in streams:
-            st.synchronize()
+        if groups == 1:
+            run_group(0)
+        else:
+            with cf.ThreadPoolExecutor(max_workers=groups) as ex:
+                for f in [ex.submit(run_group, g) for g in range(groups)]:
+                    f.result()
         seconds = time.perf_counter() - t0
         out = [(rhos[i].cpu().numpy(), hist[i]) for i in range(len(designs))]
-        report = bs.report()
+        report = bsolvers[0].report()
     finally:
-        pool.shutdown()
-        bs.close()
+        for pool in pools:
+            pool.shutdown()
+        for bs in bsolvers:
+            bs.close()
         for s in solvers:
             s.close()
     return out, seconds, report

@@ -148,6 +148,12 @@ def test_batched_design_loop_follows_the_per_handle_loop():
     ds = UNEVEN[:3]
     cycles = 5
     bat, _, report = batch.run_designs_batched(ds, cycles=cycles, workers=3, nl=5, eps2=1e-10)
+    # sub-batches with their own solvers and threads give the same results
+    bat2, _, _ = batch.run_designs_batched(ds, cycles=cycles, workers=3, nl=5, groups=2,
+                                           eps2=1e-10)
+    for (r1, h1), (r2, h2) in zip(bat, bat2):
+        np.testing.assert_array_equal(r1, r2)
+        assert [h["compliance"] for h in h1] == [h["compliance"] for h in h2]
     ref, _ = batch.run_designs(ds, cycles=cycles, workers=3, precision=mgar.MGAR_MIXED, nl=5,
                                eps2=1e-10, n_on=cycles + 1)
     assert "coarsest solve" in report
