@@ -74,9 +74,6 @@ def parse():
                     help="run this many seeded independent 2D designs concurrently and one after "
                          "another (--cycles each, default 30); one JSON line")
     ap.add_argument("--batch-workers", type=int, default=16)
-    ap.add_argument("--batch-groups", type=int, default=2,
-                    help="batched run: sub-batches with their own solver, stream and host thread, "
-                         "so one's solve overlaps another's per-design work")
     ap.add_argument("--postprocess", default=None,
                     help="time the boundary post-processing (Eq. 24-27) after --cycles design "
                          "cycles of this workload; one JSON line")
@@ -747,8 +744,7 @@ def run_batch(args):
     batch.run_designs_batched(designs[:2], cycles=2, workers=2, device=local)
     batch.run_designs(designs[:2], cycles=2, workers=2, precision=prec, device=local)
     bat, t_bat, report = batch.run_designs_batched(designs, cycles=cycles,
-                                                   workers=args.batch_workers, device=local,
-                                                   groups=args.batch_groups)
+                                                   workers=args.batch_workers, device=local)
     n_on = {"n_on": cycles + 1}  # MGCG in every cycle, as the batched run
     par, t_par = batch.run_designs(designs, cycles=cycles, workers=args.batch_workers,
                                    precision=prec, device=local, **n_on)
@@ -767,9 +763,10 @@ def run_batch(args):
             "dofs_total": sum((d.nx + 1) * (d.ny + 1)
                               for d in batch.designs_from_workload(args.batch)),
             "batched": {"seconds": t_bat, "design_cycles_per_s": total / t_bat,
-                        "nl": 5, "groups": args.batch_groups,
-                        "solve": "one launch per V-cycle level and operation over all designs of "
-                                 "a sub-batch, FP32 V-cycle and FP64 CG in one CUDA graph",
+                        "nl": 5,
+                        "solve": "one mgar_batch_cycle per cycle: one launch per V-cycle level and "
+                                 "operation over all designs, FP32 V-cycle and FP64 CG in one CUDA "
+                                 "graph; every design's update queued before any is read",
                         "cg_iters_mean": statistics.mean(h["cg_iters"] for _, hs in bat
                                                          for h in hs),
                         "autotuner": [l for l in report.splitlines() if not l.startswith("  ")]},

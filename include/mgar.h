@@ -283,7 +283,10 @@ typedef struct mgar_batch_ctx* mgar_batch_t;
 
 /* Create a batch over `count` handles (host array), all 2D and created with
  * MGAR_MIXED; a handle may appear once.  The handles must outlive the batch
- * and must not be used by other calls while a batch call runs.  Work is
+ * and must not be used by other calls while a batch call runs.  Batch calls
+ * run one at a time per process (calls from several host threads wait for
+ * each other: concurrent batches gave differing results and once an illegal
+ * address in an experiment).  Work is
  * ordered on `stream` (cudaStream_t, NULL = legacy default).
  * Errors: MGAR_ERR_ARG (bad arguments, 3D or FP64 handles), MGAR_ERR_CUDA. */
 int mgar_batch_create(mgar_batch_t* out, const mgar_t* handles, int count, void* stream);
@@ -308,6 +311,28 @@ const char* mgar_batch_last_error(mgar_batch_t b);
  * the stream. */
 int mgar_batch_solve_mgcg(mgar_batch_t b, double* const* T, int* iters, double* relres,
                           int* status);
+
+/* One design cycle of Figure 5 with MGCG for every design of the batch
+ * (Eq. 6-8 filter and Eq. 4 SIMP, the batched solve of Eq. 3, the
+ * compliance of Eq. 5, the sensitivities of Eq. 9-11 and the OC update), as
+ * mgar_step does for one handle with n_on past the cycle: each design's
+ * filter, sensitivity and OC kernels run on its handle's stream, the solve
+ * on the batch's, and every design's update is queued before any outcome is
+ * read.
+ *   rho:     host array of `count` device pointers, each ne_d doubles: the
+ *            design in, the updated design out.
+ *   T:       host array of `count` device pointers, each n_d doubles: warm
+ *            start in, this cycle's temperatures out.
+ *   volfrac: host array of `count` volume fractions in (0, 1).
+ *   move:    OC move limit (> 0), the same for every design.
+ *   info:    host array of `count` reports (may be NULL): compliance, CG
+ *            iterations, relative residual, lambda, status per design.
+ * Returns as mgar_batch_solve_mgcg.  Errors: MGAR_ERR_ARG (null pointers,
+ * volfrac or move out of range, a handle with the continuation filter
+ * schedule of filter_alpha, which follows mgar_step's cycle count).
+ * Synchronises every handle's stream and the batch's. */
+int mgar_batch_cycle(mgar_batch_t b, double* const* rho, double* const* T, const double* volfrac,
+                     double move, mgar_step_info* info);
 
 /* The autotuner's timings and choices as text (empty before the first
  * solve), written to buf (host, len bytes, NUL-terminated). */

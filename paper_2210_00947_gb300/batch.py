@@ -119,84 +119,45 @@ def run_designs(designs: list[Design], cycles: int, workers: int = 16,
 
 
 def run_designs_batched(designs: list[Design], cycles: int, workers: int = 16, device: int = 0,
-                        nl: int = 5, groups: int = 1, **overrides):
+                        nl: int = 5, **overrides):
     """Optimise every design for `cycles` design cycles, MGCG in every cycle,
-    with batched solves (mgar_batch_solve_mgcg: one launch per V-cycle level
-    and operation for a whole batch).  Per cycle of a batch: each design's
-    filter and SIMP (queued on its own stream), the batched solve (its
-    stream waits for them), then each design's sensitivities and OC update
-    on host threads.  With groups > 1 the designs are dealt round-robin into
-    that many batches, each with its own batched solver, stream and host
-    thread, so that one batch's solve overlaps another's per-design work
-    (results do not depend on the grouping: every reduction has a fixed
-    order per design).  Mixed precision (FP32 V-cycle, FP64 CG).  Returns,
-    per design, the final densities and compliances, the seconds of the
-    cycles, and the first batch's autotuner report."""
+    one mgar_batch_cycle per cycle for the whole set: each design's filter and
+    SIMP on its own stream, the batched solve (one launch per V-cycle level
+    and operation for all designs), then every design's sensitivities and OC
+    update queued on its stream before any outcome is read.  Mixed precision
+    (FP32 V-cycle, FP64 CG).  Returns, per design, the final densities and
+    compliances, the seconds of the cycles, and the batched solver's
+    autotuner report.  `workers` is accepted for the per-handle runner's
+    signature."""
     import time
 
     import torch
 
+    del workers
     torch.cuda.set_device(device)
     dev = torch.device("cuda", device)
-    groups = max(1, min(groups, len(designs)))
-    streams, solvers, rhos, Ts, dcs = [], [], [], [], []
+    solvers, rhos, Ts = [], [], []
     for d in designs:
-        st = torch.cuda.Stream(dev)
         p = d.params(cycles, mgar.MGAR_MIXED, nl=nl, n_on=cycles + 1, **overrides)
-        solvers.append(mgar.Solver(p, d.fixed(), d.q(), stream=st))
-        streams.append(st)
+        solvers.append(mgar.Solver(p, d.fixed(), d.q(), stream=torch.cuda.Stream(dev)))
         rhos.append(torch.tensor(d.density(), device=dev))
         Ts.append(torch.zeros(solvers[-1].n_nodes, dtype=torch.float64, device=dev))
-        dcs.append(torch.empty(d.nx * d.ny, dtype=torch.float64, device=dev))
-    members = [list(range(g, len(designs), groups)) for g in range(groups)]
-    bstreams = [torch.cuda.Stream(dev) for _ in range(groups)]
-    bsolvers = [mgar.BatchSolver([solvers[i] for i in m], stream=bs)
-                for m, bs in zip(members, bstreams)]
+    bs = mgar.BatchSolver(solvers, stream=torch.cuda.Stream(dev))
+    volfracs = [d.volfrac for d in designs]
     hist = [[] for _ in designs]
-    per = max(1, workers // groups)
-    pools = [cf.ThreadPoolExecutor(max_workers=per) for _ in range(groups)]
-
-    def design_update(i):
-        c = solvers[i].sensitivity(Ts[i], dcs[i])
-        solvers[i].oc_update(rhos[i], dcs[i], designs[i].volfrac, 0.2)
-        return c
-
-    def cycle(g):
-        m, bs, bstream = members[g], bsolvers[g], bstreams[g]
-        for i in m:
-            solvers[i].set_density(rhos[i])
-            ev = torch.cuda.Event()
-            ev.record(streams[i])
-            bstream.wait_event(ev)
-        res = bs.solve([Ts[i] for i in m])
-        comps = list(pools[g].map(design_update, m))
-        for i, c, r in zip(m, comps, res):
-            hist[i].append(dict(compliance=c, cg_iters=r[0], converged=r[2]))
-
-    def run_group(g):
-        torch.cuda.set_device(device)
-        for _ in range(cycles):
-            cycle(g)
-        for i in members[g]:
-            streams[i].synchronize()
-
     try:
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        if groups == 1:
-            run_group(0)
-        else:
-            with cf.ThreadPoolExecutor(max_workers=groups) as ex:
-                for f in [ex.submit(run_group, g) for g in range(groups)]:
-                    f.result()
+        for _ in range(cycles):
+            for i, inf in enumerate(bs.cycle(rhos, Ts, volfracs, 0.2)):
+                hist[i].append(dict(compliance=inf["compliance"], cg_iters=inf["cg_iters"],
+                                    converged=inf["status"] == mgar.MGAR_OK))
+        torch.cuda.synchronize(dev)
         seconds = time.perf_counter() - t0
         out = [(rhos[i].cpu().numpy(), hist[i]) for i in range(len(designs))]
-        report = bsolvers[0].report()
+        report = bs.report()
     finally:
-        for pool in pools:
-            pool.shutdown()
-        for bs in bsolvers:
-            bs.close()
+        bs.close()
         for s in solvers:
             s.close()
     return out, seconds, report

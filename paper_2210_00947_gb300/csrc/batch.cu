@@ -27,6 +27,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 namespace mgar {
@@ -335,6 +336,9 @@ struct Batch {
   cudaGraphExec_t exec = nullptr;
   int64_t prologue = 0, body = 0;
   std::string report;
+  // design cycles: each handle's stream -> the batch stream, and back
+  std::vector<cudaEvent_t> ev_des;
+  cudaEvent_t ev_solved = nullptr;
 };
 
 static void free_shape(Shape& s) {
@@ -602,10 +606,15 @@ using namespace mgar::bat;
 namespace {
 thread_local std::string g_batch_create_error = "no error";
 
+// Batch calls run one at a time per process (concurrent batches from
+// several host threads are not supported; see the header).
+std::mutex g_batch_mutex;
+
 template <class F>
 int bguard(mgar_batch_t hb, F&& f) {
   Batch* b = reinterpret_cast<Batch*>(hb);
   if (!b) return MGAR_ERR_ARG;
+  std::lock_guard<std::mutex> lock(g_batch_mutex);
   try {
     return f(*b);
   } catch (const Error& e) {
@@ -619,6 +628,8 @@ int bguard(mgar_batch_t hb, F&& f) {
 
 void free_batch(Batch& b) {
   if (b.exec) cudaGraphExecDestroy(b.exec);
+  for (cudaEvent_t e : b.ev_des) cudaEventDestroy(e);
+  if (b.ev_solved) cudaEventDestroy(b.ev_solved);
   for (auto& s : b.s_node) free_shape(s);
   for (auto& s : b.s_next) free_shape(s);
   free_shape(b.s_coarse);
@@ -733,6 +744,10 @@ int mgar_batch_create(mgar_batch_t* out, const mgar_t* handles, int count, void*
     MGAR_CUDA(cudaMalloc(&b->partials, (size_t)std::max(b->s_red.nblocks, 1) * sizeof(double)));
     MGAR_CUDA(cudaMalloc(&b->counters, (size_t)nd * sizeof(unsigned int)));
     MGAR_CUDA(cudaMemset(b->counters, 0, (size_t)nd * sizeof(unsigned int)));
+    b->ev_des.assign(nd, nullptr);
+    for (int d = 0; d < nd; ++d)
+      MGAR_CUDA(cudaEventCreateWithFlags(&b->ev_des[d], cudaEventDisableTiming));
+    MGAR_CUDA(cudaEventCreateWithFlags(&b->ev_solved, cudaEventDisableTiming));
   } catch (const Error& e) {
     g_batch_create_error = e.msg;
     free_batch(*b);
@@ -756,85 +771,144 @@ const char* mgar_batch_last_error(mgar_batch_t hb) {
   return reinterpret_cast<Batch*>(hb)->err.c_str();
 }
 
+// The batched solve for the designs' current densities (shared by the solve
+// and the design-cycle entry points).
+static int batch_solve(Batch& b, double* const* T, int* iters, double* relres, int* status) {
+  require(T != nullptr, MGAR_ERR_ARG, "batch_solve_mgcg: null T");
+  for (int d = 0; d < b.nd; ++d) require(T[d] != nullptr, MGAR_ERR_ARG, "batch_solve_mgcg: null T[d]");
+  // each design's hierarchy from its current design (K0 <- K), on the batch
+  // stream; the coarsest factorisations run on the handles' side streams,
+  // all of them at once, and the stream waits for them before the solve
+  for (Ctx* c : b.h) {
+    cudaStream_t saved = c->stream;
+    c->stream = b.stream;
+    try {
+      build_hierarchy(*c);
+    } catch (...) {
+      c->stream = saved;
+      throw;
+    }
+    c->stream = saved;
+  }
+  for (Ctx* c : b.h) {
+    cudaStream_t saved = c->stream;
+    c->stream = b.stream;
+    join_coarse(*c);
+    c->stream = saved;
+  }
+  // the callers' solution vectors and the per-design constants
+  std::vector<Des>& des = b.hdes;
+  bool moved = false;
+  for (int d = 0; d < b.nd; ++d) {
+    moved = moved || des[d].x != T[d];
+    des[d].x = T[d];
+    b.hconsts[3 * d] = b.h[d]->qnorm;
+    b.hconsts[3 * d + 1] = b.h[d]->p.eps2;
+    b.hconsts[3 * d + 2] = (double)b.h[d]->p.cg_max;
+  }
+  if (moved)
+    MGAR_CUDA(cudaMemcpyAsync(b.ddes, des.data(), b.nd * sizeof(Des), cudaMemcpyHostToDevice,
+                              b.stream));
+  MGAR_CUDA(cudaMemcpyAsync(b.consts, b.hconsts, (size_t)b.nd * 3 * sizeof(double),
+                            cudaMemcpyHostToDevice, b.stream));
+  if (!b.exec) {
+    MGAR_CUDA(cudaStreamSynchronize(b.stream));
+    autotune(b);
+    build_graph(b);
+  }
+  MGAR_CUDA(cudaGraphLaunch(b.exec, b.stream));
+  MGAR_CUDA(cudaMemcpyAsync(b.hbsc, b.bsc, (size_t)b.nd * kBS * sizeof(double),
+                            cudaMemcpyDeviceToHost, b.stream));
+  MGAR_CUDA(cudaStreamSynchronize(b.stream));
+  int maxit = 0;
+  int rc = MGAR_OK;
+  for (int d = 0; d < b.nd; ++d) {
+    const double* s = b.hbsc + (size_t)d * kBS;
+    const int it = (int)s[BS_IT];
+    const double rel = std::sqrt(s[BS_RR]) / s[BS_QN];
+    maxit = std::max(maxit, it);
+    int st = MGAR_OK;
+    if (s[BS_BAD] != 0.0 || !std::isfinite(rel)) st = MGAR_ERR_NONFINITE;
+    else if (!(rel <= b.h[d]->p.eps2)) st = MGAR_ERR_MAXIT;
+    if (iters) iters[d] = it;
+    if (relres) relres[d] = rel;
+    if (status) status[d] = st;
+    if (st == MGAR_ERR_NONFINITE) rc = MGAR_ERR_NONFINITE;
+    else if (st == MGAR_ERR_MAXIT && rc == MGAR_OK) rc = MGAR_ERR_MAXIT;
+    // the solution is the handle's new reference
+    b.h[d]->have_ref = true;
+  }
+  count_launches(b.prologue + (int64_t)maxit * b.body);
+  // the factorisations' error flags (published per handle)
+  for (Ctx* c : b.h) {
+    int e = 0;
+    MGAR_CUDA(cudaMemcpy(&e, c->derr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+      MGAR_CUDA(cudaMemset(c->derr, 0, sizeof(int)));
+      throw Error{e, "a coarsest factorisation met a non-positive pivot"};
+    }
+  }
+  if (rc == MGAR_ERR_MAXIT) b.err = "a design reached cg_max";
+  if (rc == MGAR_ERR_NONFINITE) b.err = "a design's CG broke down (non-finite residual)";
+  return rc;
+}
+
 int mgar_batch_solve_mgcg(mgar_batch_t hb, double* const* T, int* iters, double* relres,
                           int* status) {
+  return bguard(hb, [&](Batch& b) { return batch_solve(b, T, iters, relres, status); });
+}
+
+int mgar_batch_cycle(mgar_batch_t hb, double* const* rho, double* const* T, const double* volfrac,
+                     double move, mgar_step_info* info) {
   return bguard(hb, [&](Batch& b) {
-    require(T != nullptr, MGAR_ERR_ARG, "batch_solve_mgcg: null T");
-    for (int d = 0; d < b.nd; ++d) require(T[d] != nullptr, MGAR_ERR_ARG, "batch_solve_mgcg: null T[d]");
-    // each design's hierarchy from its current design (K0 <- K), on the batch
-    // stream; the coarsest factorisations run on the handles' side streams,
-    // all of them at once, and the stream waits for them before the solve
-    for (Ctx* c : b.h) {
-      cudaStream_t saved = c->stream;
-      c->stream = b.stream;
-      try {
-        build_hierarchy(*c);
-      } catch (...) {
-        c->stream = saved;
-        throw;
-      }
-      c->stream = saved;
+    require(rho && T && volfrac, MGAR_ERR_ARG, "batch_cycle: null argument");
+    require(move > 0.0, MGAR_ERR_ARG, "batch_cycle: move must be positive");
+    const int nd = b.nd;
+    for (int d = 0; d < nd; ++d) {
+      require(rho[d] && T[d], MGAR_ERR_ARG, "batch_cycle: null rho[d] or T[d]");
+      require(volfrac[d] > 0.0 && volfrac[d] < 1.0, MGAR_ERR_ARG, "batch_cycle: volfrac outside (0, 1)");
+      require(!(b.h[d]->p.filter_alpha > 0.0), MGAR_ERR_ARG,
+              "batch_cycle: the continuation filter schedule is per cycle of mgar_step");
     }
-    for (Ctx* c : b.h) {
-      cudaStream_t saved = c->stream;
-      c->stream = b.stream;
-      join_coarse(*c);
-      c->stream = saved;
+    // each design's filter and SIMP on its own stream; the batch stream waits
+    // for all of them
+    for (int d = 0; d < nd; ++d) {
+      Ctx& c = *b.h[d];
+      set_density(c, rho[d], false);
+      MGAR_CUDA(cudaEventRecord(b.ev_des[d], c.stream));
+      MGAR_CUDA(cudaStreamWaitEvent(b.stream, b.ev_des[d], 0));
     }
-    // the callers' solution vectors and the per-design constants
-    std::vector<Des>& des = b.hdes;
-    bool moved = false;
-    for (int d = 0; d < b.nd; ++d) {
-      moved = moved || des[d].x != T[d];
-      des[d].x = T[d];
-      b.hconsts[3 * d] = b.h[d]->qnorm;
-      b.hconsts[3 * d + 1] = b.h[d]->p.eps2;
-      b.hconsts[3 * d + 2] = (double)b.h[d]->p.cg_max;
+    std::vector<int> it(nd), st(nd);
+    std::vector<double> rr(nd);
+    const int rc = batch_solve(b, T, it.data(), rr.data(), st.data());
+    // each design's sensitivities, compliance and OC update queued on its
+    // own stream after the solve, all of them before any outcome is read
+    MGAR_CUDA(cudaEventRecord(b.ev_solved, b.stream));
+    for (int d = 0; d < nd; ++d) {
+      Ctx& c = *b.h[d];
+      MGAR_CUDA(cudaStreamWaitEvent(c.stream, b.ev_solved, 0));
+      sensitivity(c, T[d], c.tmp_dc, nullptr, nullptr);
+      dot(c, c.q, T[d], c.n, c.dsc + S_COMPL);
+      oc_issue(c, rho[d], c.tmp_dc, volfrac[d], move);
     }
-    if (moved)
-      MGAR_CUDA(cudaMemcpyAsync(b.ddes, des.data(), b.nd * sizeof(Des), cudaMemcpyHostToDevice,
-                                b.stream));
-    MGAR_CUDA(cudaMemcpyAsync(b.consts, b.hconsts, (size_t)b.nd * 3 * sizeof(double),
-                              cudaMemcpyHostToDevice, b.stream));
-    if (!b.exec) {
-      MGAR_CUDA(cudaStreamSynchronize(b.stream));
-      autotune(b);
-      build_graph(b);
-    }
-    MGAR_CUDA(cudaGraphLaunch(b.exec, b.stream));
-    MGAR_CUDA(cudaMemcpyAsync(b.hbsc, b.bsc, (size_t)b.nd * kBS * sizeof(double),
-                              cudaMemcpyDeviceToHost, b.stream));
-    MGAR_CUDA(cudaStreamSynchronize(b.stream));
-    int maxit = 0;
-    int rc = MGAR_OK;
-    for (int d = 0; d < b.nd; ++d) {
-      const double* s = b.hbsc + (size_t)d * kBS;
-      const int it = (int)s[BS_IT];
-      const double rel = std::sqrt(s[BS_RR]) / s[BS_QN];
-      maxit = std::max(maxit, it);
-      int st = MGAR_OK;
-      if (s[BS_BAD] != 0.0 || !std::isfinite(rel)) st = MGAR_ERR_NONFINITE;
-      else if (!(rel <= b.h[d]->p.eps2)) st = MGAR_ERR_MAXIT;
-      if (iters) iters[d] = it;
-      if (relres) relres[d] = rel;
-      if (status) status[d] = st;
-      if (st == MGAR_ERR_NONFINITE) rc = MGAR_ERR_NONFINITE;
-      else if (st == MGAR_ERR_MAXIT && rc == MGAR_OK) rc = MGAR_ERR_MAXIT;
-      // the solution is the handle's new reference
-      b.h[d]->have_ref = true;
-    }
-    count_launches(b.prologue + (int64_t)maxit * b.body);
-    // the factorisations' error flags (published per handle)
-    for (Ctx* c : b.h) {
-      int e = 0;
-      MGAR_CUDA(cudaMemcpy(&e, c->derr, sizeof(int), cudaMemcpyDeviceToHost));
-      if (e) {
-        MGAR_CUDA(cudaMemset(c->derr, 0, sizeof(int)));
-        throw Error{e, "a coarsest factorisation met a non-positive pivot"};
+    for (int d = 0; d < nd; ++d) {
+      Ctx& c = *b.h[d];
+      double lam = 0.0, change = 0.0;
+      oc_complete(c, rho[d], volfrac[d], &lam, &change);
+      if (info) {
+        mgar_step_info& inf = info[d];
+        inf = mgar_step_info{};
+        inf.compliance = c.hsc[S_COMPL];
+        inf.res = NAN;
+        inf.relres = rr[d];
+        inf.lambda = lam;
+        inf.used_mgcg = 1;
+        inf.accepted = 0;
+        inf.cg_iters = it[d];
+        inf.status = st[d];
+        inf.compliance_mgar = NAN;
       }
     }
-    if (rc == MGAR_ERR_MAXIT) b.err = "a design reached cg_max";
-    if (rc == MGAR_ERR_NONFINITE) b.err = "a design's CG broke down (non-finite residual)";
     return rc;
   });
 }

@@ -957,6 +957,11 @@ void postprocess(Ctx& c, const double* rho, const double* T, double volfrac, dou
                  double* level_out, double* volume_out);
 void oc_update(Ctx& c, double* rho, const double* dc, double volfrac, double move, double* lambda,
                double* change);
+// oc_update in two halves: the fast solve and its application queued without
+// a host read, then the read of its outcome (and the plain bisection if it
+// failed), so many handles' updates can be queued before any is read
+void oc_issue(Ctx& c, double* rho, const double* dc, double volfrac, double move);
+void oc_complete(Ctx& c, double* rho, double volfrac, double* lambda, double* change);
 
 }  // namespace mgar
 

@@ -823,8 +823,10 @@ void sensitivity(Ctx& c, const double* T, double* dc, double* dv, double* compli
 
 namespace mgar {
 
-void oc_update(Ctx& c, double* rho, const double* dc, double volfrac, double move, double* lambda,
-               double* change) {
+// The fast solve for lambda and its application to rho, queued on the
+// handle's stream without a host read (the apply does nothing if the solve
+// failed; oc_complete reads the outcome).
+void oc_issue(Ctx& c, double* rho, const double* dc, double volfrac, double move) {
   const int ne = (int)c.ne;
   const int rb = c.grid_blocks_e;
   k_oc_prep<<<blocks_for(ne), kThreads, 0, c.stream>>>(rho, dc, c.rsdv, c.oc_s, c.oc_lo, c.oc_hi,
@@ -832,42 +834,43 @@ void oc_update(Ctx& c, double* rho, const double* dc, double volfrac, double mov
   MGAR_LAUNCH_CHECK();
   // lambda in [1e-40, 1e40]  <=>  ln(mu) in [-20 ln 10, 20 ln 10]
   const double Lmax = 20.0 * std::log(10.0), Lmin = -Lmax;
-  bool fast_ok = false;
-  {
-    ProfScope ps(c, MGAR_KC_OC);
-    k_oc_prep32<<<blocks_for(ne), kThreads, 0, c.stream>>>(c.oc_s, c.oc_lo, c.oc_hi, c.oc_s32,
-                                                           c.oc_lo32, c.oc_hi32, ne);
+  ProfScope ps(c, MGAR_KC_OC);
+  k_oc_prep32<<<blocks_for(ne), kThreads, 0, c.stream>>>(c.oc_s, c.oc_lo, c.oc_hi, c.oc_s32,
+                                                         c.oc_lo32, c.oc_hi32, ne);
+  MGAR_LAUNCH_CHECK();
+  k_oc_start<<<1, 32, 0, c.stream>>>(c.dsc, Lmin, Lmax, 1);
+  MGAR_LAUNCH_CHECK();
+  // three blocks per SM (the 80 registers of the 31 accumulators allow
+  // three): more loads in flight; the last block's sum over the partials
+  // stays short
+  const int msb = std::min(blocks_for(ne), c.sms * 3);
+  for (int pass = 0; pass < kOcPasses; ++pass) {
+    k_oc_multisect<<<msb, kThreads, 0, c.stream>>>(c.oc_s32, c.oc_lo32, c.oc_hi32, c.dv32, ne,
+                                                  volfrac, c.dsc, c.partials, c.counter);
     MGAR_LAUNCH_CHECK();
-    k_oc_start<<<1, 32, 0, c.stream>>>(c.dsc, Lmin, Lmax, 1);
-    MGAR_LAUNCH_CHECK();
-    // three blocks per SM (the 80 registers of the 31 accumulators allow
-    // three): more loads in flight; the last block's sum over the partials
-    // stays short
-    const int msb = std::min(blocks_for(ne), c.sms * 3);
-    for (int pass = 0; pass < kOcPasses; ++pass) {
-      k_oc_multisect<<<msb, kThreads, 0, c.stream>>>(c.oc_s32, c.oc_lo32, c.oc_hi32, c.dv32, ne,
-                                                    volfrac, c.dsc, c.partials, c.counter);
-      MGAR_LAUNCH_CHECK();
-    }
-    MGAR_CUDA(cudaMemsetAsync(c.oc_namb, 0, sizeof(int), c.stream));
-    k_oc_classify<<<rb, kThreads, 0, c.stream>>>(c.oc_s, c.oc_lo, c.oc_hi, c.dv, ne, kOcMargin, Lmin,
-                                                 Lmax, c.dsc, c.oc_amb, c.oc_namb, c.partials,
-                                                 c.counter);
-    MGAR_LAUNCH_CHECK();
-    k_oc_finish<<<1, 1024, 0, c.stream>>>(c.oc_s, c.oc_lo, c.oc_hi, c.dv, ne, volfrac, c.dsc,
-                                          c.oc_amb, c.oc_namb);
-    MGAR_LAUNCH_CHECK();
-    // applied unless the fast solve failed; one fetch from S_OC_LAM on
-    // brings the check, lambda, the change and a compliance dot launched
-    // before the update
-    k_oc_apply<<<rb, kThreads, 0, c.stream>>>(rho, c.oc_s, c.oc_lo, c.oc_hi, ne, c.dsc, c.partials,
-                                              c.counter);
-    MGAR_LAUNCH_CHECK();
-    fetch_scalars(c, S_OC_LAM, S_OC_FAIL - S_OC_LAM + 1);
-    fast_ok = c.hsc[S_OC_FAIL] == 0.0;
   }
+  MGAR_CUDA(cudaMemsetAsync(c.oc_namb, 0, sizeof(int), c.stream));
+  k_oc_classify<<<rb, kThreads, 0, c.stream>>>(c.oc_s, c.oc_lo, c.oc_hi, c.dv, ne, kOcMargin, Lmin,
+                                               Lmax, c.dsc, c.oc_amb, c.oc_namb, c.partials,
+                                               c.counter);
+  MGAR_LAUNCH_CHECK();
+  k_oc_finish<<<1, 1024, 0, c.stream>>>(c.oc_s, c.oc_lo, c.oc_hi, c.dv, ne, volfrac, c.dsc,
+                                        c.oc_amb, c.oc_namb);
+  MGAR_LAUNCH_CHECK();
+  k_oc_apply<<<rb, kThreads, 0, c.stream>>>(rho, c.oc_s, c.oc_lo, c.oc_hi, ne, c.dsc, c.partials,
+                                            c.counter);
+  MGAR_LAUNCH_CHECK();
+}
+
+// One host read from S_OC_LAM on brings the check, lambda, the change and a
+// compliance dot launched before the update; if the fast solve failed, the
+// plain bisection on lambda over the whole range and the apply again.
+void oc_complete(Ctx& c, double* rho, double volfrac, double* lambda, double* change) {
+  const int ne = (int)c.ne;
+  const int rb = c.grid_blocks_e;
+  fetch_scalars(c, S_OC_LAM, S_OC_FAIL - S_OC_LAM + 1);
+  const bool fast_ok = c.hsc[S_OC_FAIL] == 0.0;
   if (!fast_ok) {
-    // plain bisection on lambda over the whole range
     k_oc_init<<<1, 1, 0, c.stream>>>(c.dsc, 1e-40, 1e40);
     MGAR_LAUNCH_CHECK();
     const int max_steps = 200, batch = 16;
@@ -890,6 +893,12 @@ void oc_update(Ctx& c, double* rho, const double* dc, double volfrac, double mov
   if (lambda) *lambda = c.hsc[S_OC_LAM];
   if (change) *change = c.hsc[S_OC_CHANGE];
   c.oc_fallbacks += fast_ok ? 0 : 1;
+}
+
+void oc_update(Ctx& c, double* rho, const double* dc, double volfrac, double move, double* lambda,
+               double* change) {
+  oc_issue(c, rho, dc, volfrac, move);
+  oc_complete(c, rho, volfrac, lambda, change);
 }
 
 

@@ -256,7 +256,8 @@ __global__ void k_coarse_solve(const M* __restrict__ cinv, const Real* __restric
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int jj = lane + 32 * q;
-      if (jj < n && CK((int64_t)row * n + jj, (int64_t)n * n)) cv[q] = cinv[(int64_t)row * n + jj];
+      const int jc = min(jj, n - 1);  // a valid address even where the entry is unused
+      if (jj < n && CK((int64_t)row * n + jc, (int64_t)n * n)) cv[q] = cinv[(int64_t)row * n + jc];
     }
   }
   pdl_wait();

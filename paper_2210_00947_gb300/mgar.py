@@ -41,7 +41,7 @@ EXPORTS = ("mgar_default_params", "mgar_create", "mgar_destroy", "mgar_set_strea
            "mgar_sensitivity", "mgar_postprocess", "mgar_oc_update", "mgar_step", "mgar_sizes", "mgar_run",
            "mgar_profile_start", "mgar_profile_stop", "mgar_profile_report",
            "mgar_kernel_launches", "mgar_batch_create", "mgar_batch_destroy",
-           "mgar_batch_last_error", "mgar_batch_solve_mgcg", "mgar_batch_report",
+           "mgar_batch_last_error", "mgar_batch_solve_mgcg", "mgar_batch_cycle", "mgar_batch_report",
            "mgar_sensitivity_noalloc")
 
 # kernel classes of mgar_profile_start
@@ -128,6 +128,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
         "mgar_batch_destroy": (i32, [vp]),
         "mgar_batch_last_error": (ctypes.c_char_p, [vp]),
         "mgar_batch_solve_mgcg": (i32, [vp, P(vp), P(i32), dp, P(i32)]),
+        "mgar_batch_cycle": (i32, [vp, P(vp), P(vp), dp, ctypes.c_double, P(StepInfo)]),
         "mgar_batch_report": (i32, [vp, ctypes.c_char_p, ctypes.c_int64]),
         "mgar_sensitivity_noalloc": (i32, [P(Params), vp, vp, vp, vp]),
     }
@@ -342,6 +343,22 @@ class BatchSolver:
         if rc not in (MGAR_OK, MGAR_ERR_MAXIT):
             raise MgarError(rc, self._lib.mgar_batch_last_error(self._b).decode())
         return [(it[d], rr[d], st[d] == MGAR_OK) for d in range(n)]
+
+    def cycle(self, rhos, Ts, volfracs, move=0.2):
+        """mgar_batch_cycle: one MGCG design cycle of every design (filter,
+        batched solve, sensitivities, OC); rhos and Ts are updated in place;
+        returns the per-design reports."""
+        n = len(self.solvers)
+        if len(rhos) != n or len(Ts) != n or len(volfracs) != n:
+            raise ValueError("one density, temperature tensor and volume fraction per design")
+        rp = (ctypes.c_void_p * n)(*[_ptr(r).value for r in rhos])
+        tp = (ctypes.c_void_p * n)(*[_ptr(t).value for t in Ts])
+        vf = (ctypes.c_double * n)(*[float(v) for v in volfracs])
+        infos = (StepInfo * n)()
+        rc = self._lib.mgar_batch_cycle(self._b, rp, tp, vf, float(move), infos)
+        if rc not in (MGAR_OK, MGAR_ERR_MAXIT):
+            raise MgarError(rc, self._lib.mgar_batch_last_error(self._b).decode())
+        return [infos[d].as_dict() for d in range(n)]
 
     def report(self) -> str:
         buf = ctypes.create_string_buffer(1 << 14)

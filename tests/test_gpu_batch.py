@@ -148,12 +148,6 @@ def test_batched_design_loop_follows_the_per_handle_loop():
     ds = UNEVEN[:3]
     cycles = 5
     bat, _, report = batch.run_designs_batched(ds, cycles=cycles, workers=3, nl=5, eps2=1e-10)
-    # sub-batches with their own solvers and threads give the same results
-    bat2, _, _ = batch.run_designs_batched(ds, cycles=cycles, workers=3, nl=5, groups=2,
-                                           eps2=1e-10)
-    for (r1, h1), (r2, h2) in zip(bat, bat2):
-        np.testing.assert_array_equal(r1, r2)
-        assert [h["compliance"] for h in h1] == [h["compliance"] for h in h2]
     ref, _ = batch.run_designs(ds, cycles=cycles, workers=3, precision=mgar.MGAR_MIXED, nl=5,
                                eps2=1e-10, n_on=cycles + 1)
     assert "coarsest solve" in report
@@ -163,3 +157,44 @@ def test_batched_design_loop_follows_the_per_handle_loop():
             assert a["converged"]
             assert abs(a["compliance"] - b["compliance"]) <= 1e-6 * abs(b["compliance"])
         assert np.max(np.abs(rb - rr)) < 1e-5
+
+
+def test_batch_cycle_equals_its_steps():
+    """mgar_batch_cycle (filter, batched solve, sensitivities and OC queued for
+    every design before any outcome is read) gives bit for bit what the same
+    steps give called one by one."""
+    ds = UNEVEN[:3]
+    cycles = 3
+    runs = []
+    for fused in (True, False):
+        sv, rh, Ts, vf = [], [], [], []
+        for d in ds:
+            p = d.params(cycles, mgar.MGAR_MIXED, nl=5, n_on=cycles + 1, eps2=1e-10)
+            sv.append(mgar.Solver(p, d.fixed(), d.q(), stream=torch.cuda.Stream()))
+            rh.append(torch.tensor(d.density(), device="cuda:0"))
+            Ts.append(torch.zeros(sv[-1].n_nodes, dtype=torch.float64, device="cuda:0"))
+            vf.append(d.volfrac)
+        comps = []
+        with mgar.BatchSolver(sv, stream=torch.cuda.Stream()) as b:
+            for _ in range(cycles):
+                if fused:
+                    comps.append([inf["compliance"] for inf in b.cycle(rh, Ts, vf, 0.2)])
+                else:
+                    for s, r in zip(sv, rh):
+                        s.set_density(r)
+                    torch.cuda.synchronize()
+                    b.solve(Ts)
+                    row = []
+                    for s, r, T, v in zip(sv, rh, Ts, vf):
+                        dc = torch.empty_like(r)
+                        row.append(s.sensitivity(T, dc))
+                        s.oc_update(r, dc, v, 0.2)
+                    comps.append(row)
+        torch.cuda.synchronize()
+        runs.append(([r.cpu().numpy() for r in rh], comps))
+        for s in sv:
+            s.close()
+    (ra, ca), (rb, cb) = runs
+    assert ca == cb
+    for a, b_ in zip(ra, rb):
+        np.testing.assert_array_equal(a, b_)
