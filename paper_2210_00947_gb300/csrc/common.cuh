@@ -45,7 +45,7 @@ constexpr int kMaxFilterOffsets = 3072;
 constexpr int kMaxM = 8;
 constexpr int kOcCand = 31;      // multisection candidates per pass (5 bits)
 constexpr int kOcPasses = 6;     // FP32 passes at most: ln-bracket 92 -> 9e-8
-constexpr double kOcTarget = 1e-6;  // passes stop once the ln-bracket is this narrow
+constexpr double kOcTarget = 2e-5;  // passes stop once the ln-bracket is this narrow (the margin below)
 constexpr int kOcAmbMax = 4096;  // ambiguous elements handled by the FP64 finish
 constexpr double kOcMargin = 2e-5;  // ln-bracket widening that absorbs FP32 volume rounding
 constexpr size_t kBandSmemMax = 160 * 1024;  // band factorised in shared memory up to this size
