@@ -763,7 +763,7 @@ def run_batch(args):
             "dofs_total": sum((d.nx + 1) * (d.ny + 1)
                               for d in batch.designs_from_workload(args.batch)),
             "batched": {"seconds": t_bat, "design_cycles_per_s": total / t_bat,
-                        "nl": 5,
+                        "nl": "each design's own depth (coarsest level of at most 300 nodes)",
                         "solve": "one mgar_batch_cycle per cycle: one launch per V-cycle level and "
                                  "operation over all designs, FP32 V-cycle and FP64 CG in one CUDA "
                                  "graph; every design's update queued before any is read",

@@ -119,7 +119,7 @@ def run_designs(designs: list[Design], cycles: int, workers: int = 16,
 
 
 def run_designs_batched(designs: list[Design], cycles: int, workers: int = 16, device: int = 0,
-                        nl: int = 5, **overrides):
+                        nl: int = 0, **overrides):
     """Optimise every design for `cycles` design cycles, MGCG in every cycle,
     one mgar_batch_cycle per cycle for the whole set: each design's filter and
     SIMP on its own stream, the batched solve (one launch per V-cycle level
@@ -127,8 +127,9 @@ def run_designs_batched(designs: list[Design], cycles: int, workers: int = 16, d
     update queued on its stream before any outcome is read.  Mixed precision
     (FP32 V-cycle, FP64 CG).  Returns, per design, the final densities and
     compliances, the seconds of the cycles, and the batched solver's
-    autotuner report.  `workers` is accepted for the per-handle runner's
-    signature."""
+    autotuner report.  nl = 0: each design's own depth (coarsest level of
+    at most 300 nodes, as the per-handle runner's).  `workers` is accepted
+    for the per-handle runner's signature."""
     import time
 
     import torch
@@ -138,7 +139,8 @@ def run_designs_batched(designs: list[Design], cycles: int, workers: int = 16, d
     dev = torch.device("cuda", device)
     solvers, rhos, Ts = [], [], []
     for d in designs:
-        p = d.params(cycles, mgar.MGAR_MIXED, nl=nl, n_on=cycles + 1, **overrides)
+        depth = {"nl": nl} if nl else {}
+        p = d.params(cycles, mgar.MGAR_MIXED, n_on=cycles + 1, **depth, **overrides)
         solvers.append(mgar.Solver(p, d.fixed(), d.q(), stream=torch.cuda.Stream(dev)))
         rhos.append(torch.tensor(d.density(), device=dev))
         Ts.append(torch.zeros(solvers[-1].n_nodes, dtype=torch.float64, device=dev))

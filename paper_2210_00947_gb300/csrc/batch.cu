@@ -338,7 +338,7 @@ struct Batch {
   std::string report;
   // design cycles: each handle's stream -> the batch stream, and back
   std::vector<cudaEvent_t> ev_des;
-  cudaEvent_t ev_solved = nullptr;
+  cudaEvent_t ev_solved = nullptr, ev_start = nullptr;
 };
 
 static void free_shape(Shape& s) {
@@ -630,6 +630,7 @@ void free_batch(Batch& b) {
   if (b.exec) cudaGraphExecDestroy(b.exec);
   for (cudaEvent_t e : b.ev_des) cudaEventDestroy(e);
   if (b.ev_solved) cudaEventDestroy(b.ev_solved);
+  if (b.ev_start) cudaEventDestroy(b.ev_start);
   for (auto& s : b.s_node) free_shape(s);
   for (auto& s : b.s_next) free_shape(s);
   free_shape(b.s_coarse);
@@ -748,6 +749,7 @@ int mgar_batch_create(mgar_batch_t* out, const mgar_t* handles, int count, void*
     for (int d = 0; d < nd; ++d)
       MGAR_CUDA(cudaEventCreateWithFlags(&b->ev_des[d], cudaEventDisableTiming));
     MGAR_CUDA(cudaEventCreateWithFlags(&b->ev_solved, cudaEventDisableTiming));
+    MGAR_CUDA(cudaEventCreateWithFlags(&b->ev_start, cudaEventDisableTiming));
   } catch (const Error& e) {
     g_batch_create_error = e.msg;
     free_batch(*b);
@@ -776,26 +778,19 @@ const char* mgar_batch_last_error(mgar_batch_t hb) {
 static int batch_solve(Batch& b, double* const* T, int* iters, double* relres, int* status) {
   require(T != nullptr, MGAR_ERR_ARG, "batch_solve_mgcg: null T");
   for (int d = 0; d < b.nd; ++d) require(T[d] != nullptr, MGAR_ERR_ARG, "batch_solve_mgcg: null T[d]");
-  // each design's hierarchy from its current design (K0 <- K), on the batch
-  // stream; the coarsest factorisations run on the handles' side streams,
-  // all of them at once, and the stream waits for them before the solve
-  for (Ctx* c : b.h) {
-    cudaStream_t saved = c->stream;
-    c->stream = b.stream;
-    try {
-      build_hierarchy(*c);
-    } catch (...) {
-      c->stream = saved;
-      throw;
-    }
-    c->stream = saved;
+  // each design's hierarchy from its current design (K0 <- K) on its own
+  // handle's stream, after what the batch stream holds, so the designs'
+  // builds (and their coarsest factorisations on the handles' side streams)
+  // run at once; the batch stream waits for all of them before the solve
+  MGAR_CUDA(cudaEventRecord(b.ev_start, b.stream));
+  for (int d = 0; d < b.nd; ++d) {
+    Ctx& c = *b.h[d];
+    MGAR_CUDA(cudaStreamWaitEvent(c.stream, b.ev_start, 0));
+    build_hierarchy(c);
+    join_coarse(c);
+    MGAR_CUDA(cudaEventRecord(b.ev_des[d], c.stream));
   }
-  for (Ctx* c : b.h) {
-    cudaStream_t saved = c->stream;
-    c->stream = b.stream;
-    join_coarse(*c);
-    c->stream = saved;
-  }
+  for (int d = 0; d < b.nd; ++d) MGAR_CUDA(cudaStreamWaitEvent(b.stream, b.ev_des[d], 0));
   // the callers' solution vectors and the per-design constants
   std::vector<Des>& des = b.hdes;
   bool moved = false;
