@@ -273,7 +273,8 @@ int64_t mgar_kernel_launches(void);
  * (its grid, sink, load, density and parameters).  A batch holds no copy of
  * the designs' data, only device tables of their sizes and buffers: every
  * step of the solve is one launch over all designs (one per V-cycle level
- * and operation), the outer CG runs in FP64 around the FP32 V-cycle, and
+ * and operation), the outer CG runs in double-float arithmetic (FP64
+ * accuracy on the FP32 pipe; FP64 scalars) around the FP32 V-cycle, and
  * the solve after the hierarchy builds is one CUDA graph that iterates while
  * any design is unconverged.  The V-cycle kernels' block sizes come from an
  * autotuner at the first solve (mgar_batch_report lists its timings and

@@ -8,8 +8,10 @@
 // that design's level.  So one launch per V-cycle level and operation serves
 // every design, and the designs' different depths only decide which of them
 // take part in a level (a design's coarsest level is solved by one launch
-// over all designs' coarsest levels).  The outer CG runs in FP64 around the
-// FP32 V-cycle (FP32 preconditioner, FP64 refinement); its per-design scalars
+// over all designs' coarsest levels).  The outer CG runs in double-float
+// (df64) arithmetic on the FP32 pipe around the FP32 V-cycle (FP32
+// preconditioner, FP64-accurate refinement: GB300 runs FP64 at 1/58 of the
+// FP32 rate), with FP64 scalars; its per-design scalars
 // stay on the device, a design stops when its own ||r|| / ||q|| <= eps2 or
 // at cg_max (its blocks then leave at once), and the whole solve after the
 // hierarchy builds is one CUDA graph: a WHILE node repeats the iteration
@@ -23,6 +25,7 @@
 // autotuner run at the first solve, which times the candidates on the
 // batch's own levels and keeps the fastest.
 #include "common.cuh"
+#include "dfop.cuh"
 #include "levelops.cuh"
 
 #include <algorithm>
@@ -60,9 +63,10 @@ struct Coarse {
 };
 
 struct Des {
-  FineOp<double> f;    // current conductivities (FP64, matrix-free)
-  const double* q;
-  double *x, *r, *z, *p, *Ap;
+  DfOp f;              // current conductivities (df64 pairs, matrix-free difference form)
+  const float2* q;     // the load as df64 pairs
+  float2 *x, *r, *p, *Ap;  // CG vectors as df64 pairs (the handle's own buffers)
+  double* T;           // the caller's solution (FP64): warm start in, solution out
   float *b32, *x32;    // FP32 input and output of the V-cycle at level 0
 };
 
@@ -90,7 +94,10 @@ __device__ __forceinline__ void seg_finish(double (&v)[N], double* partials, uns
   }
 }
 
-// ------------------------------------------------------------ FP64 CG kernels
+// ------------------------------------------------------------ df64 CG kernels
+// The outer CG runs in double-float arithmetic on the FP32 pipe (GB300 runs
+// FP64 at 1/58 of the FP32 rate): vectors as df64 pairs, the product in the
+// exact difference form, scalars in FP64.
 // Per design: scalars of this solve, iteration 0, active.
 __global__ void kb_init(double* bsc, const double* consts, int nd) {
   const int d = blockIdx.x * blockDim.x + threadIdx.x;
@@ -104,6 +111,22 @@ __global__ void kb_init(double* bsc, const double* consts, int nd) {
   s[BS_CGMAX] = consts[3 * d + 2];
 }
 
+// x = T as df64 pairs (the start of each design's CG)
+__global__ void kb_t_to_df(const Des* D, const int* bdes, const int* b0) {
+  const int d = bdes[blockIdx.x];
+  const Des& g = D[d];
+  const int idx = (blockIdx.x - b0[d]) * blockDim.x + threadIdx.x;
+  if (idx < g.f.n) g.x[idx] = pack(df_from_double(g.T[idx]));
+}
+
+// T = x (the end of each design's CG)
+__global__ void kb_df_to_t(const Des* D, const int* bdes, const int* b0) {
+  const int d = bdes[blockIdx.x];
+  const Des& g = D[d];
+  const int idx = (blockIdx.x - b0[d]) * blockDim.x + threadIdx.x;
+  if (idx < g.f.n) g.T[idx] = df_to_double(unpack(g.x[idx]));
+}
+
 // r = q - A x, its FP32 copy, ||r||^2 (the start of each design's CG).
 __global__ void kb_resid64(const Des* D, const int* bdes, const int* b0, double* bsc,
                            double* partials, unsigned int* counters) {
@@ -113,13 +136,10 @@ __global__ void kb_resid64(const Des* D, const int* bdes, const int* b0, double*
   const int idx = (blockIdx.x - b0[d]) * blockDim.x + threadIdx.x;
   double v[1] = {0.0};
   if (idx < g.f.n) {
-    int i, j, k;
-    coords(idx, g.f.fNX, g.f.fNXY, i, j, k);
-    double diag;
-    const double ri = g.q[idx] - fine_row2(g.f, g.x, i, j, diag);
-    g.r[idx] = ri;
-    g.b32[idx] = (float)ri;
-    v[0] = ri * ri;
+    const df ri = df_sub(unpack(g.q[idx]), df_row<2>(g.f, g.x, idx));
+    g.r[idx] = pack(ri);
+    g.b32[idx] = __fadd_rn(ri.hi, ri.lo);
+    v[0] = df_to_double(df_mul(ri, ri));
   }
   seg_finish<1>(v, partials, counters, d, b0[d], nb, bsc + d * kBS + BS_RR);
 }
@@ -145,12 +165,9 @@ __global__ void kb_apply_dot(const Des* D, const int* bdes, const int* b0, doubl
   const int idx = (blockIdx.x - b0[d]) * blockDim.x + threadIdx.x;
   double v[1] = {0.0};
   if (idx < g.f.n) {
-    int i, j, k;
-    coords(idx, g.f.fNX, g.f.fNXY, i, j, k);
-    double diag;
-    const double ap = fine_row2(g.f, g.p, i, j, diag);
-    g.Ap[idx] = ap;
-    v[0] = g.p[idx] * ap;
+    const df ap = df_row<2>(g.f, g.p, idx);
+    g.Ap[idx] = pack(ap);
+    v[0] = df_to_double(df_mul(unpack(g.p[idx]), ap));
   }
   seg_finish<1>(v, partials, counters, d, b0[d], nb, bsc + d * kBS + BS_PAP);
 }
@@ -163,16 +180,16 @@ __global__ void kb_cg_xr(const Des* D, const int* bdes, const int* b0, double* b
   const Des& g = D[d];
   const double* s = bsc + d * kBS;
   const int par = ((int)s[BS_IT]) & 1;
-  const double alpha = block_div(s + BS_RZ + par, s + BS_PAP);
+  const df alpha = block_div_df(s + BS_RZ + par, s + BS_PAP);
   const int nb = (g.f.n + blockDim.x - 1) / blockDim.x;
   const int idx = (blockIdx.x - b0[d]) * blockDim.x + threadIdx.x;
   double v[1] = {0.0};
   if (idx < g.f.n) {
-    g.x[idx] += alpha * g.p[idx];
-    const double ri = g.r[idx] - alpha * g.Ap[idx];
-    g.r[idx] = ri;
-    g.b32[idx] = (float)ri;
-    v[0] = ri * ri;
+    g.x[idx] = pack(df_add(unpack(g.x[idx]), df_mul(alpha, unpack(g.p[idx]))));
+    const df ri = df_sub(unpack(g.r[idx]), df_mul(alpha, unpack(g.Ap[idx])));
+    g.r[idx] = pack(ri);
+    g.b32[idx] = __fadd_rn(ri.hi, ri.lo);
+    v[0] = df_to_double(df_mul(ri, ri));
   }
   seg_finish<1>(v, partials, counters, d, b0[d], nb, bsc + d * kBS + BS_RR);
 }
@@ -198,16 +215,21 @@ __global__ void kb_check(double* bsc, int nd, cudaGraphConditionalHandle loop) {
   if (threadIdx.x == 0) cudaGraphSetConditional(loop, any ? 1u : 0u);
 }
 
-// p = z + (r.z_new / r.z_old) p (p = z in the first iteration).
+// p = z + (r.z_new / r.z_old) p (p = z in the first iteration), z the FP32
+// V-cycle output.
 __global__ void kb_cg_p(const Des* D, const int* bdes, const int* b0, const double* bsc) {
   const int d = bdes[blockIdx.x];
   if (!active(bsc, d)) return;
   const Des& g = D[d];
   const double* s = bsc + d * kBS;
   const int it = (int)s[BS_IT];
-  const double beta = it == 0 ? 0.0 : block_div(s + BS_RZ + (it & 1), s + BS_RZ + ((it - 1) & 1));
+  const df beta = it == 0 ? df{0.f, 0.f}
+                          : block_div_df(s + BS_RZ + (it & 1), s + BS_RZ + ((it - 1) & 1));
   const int idx = (blockIdx.x - b0[d]) * blockDim.x + threadIdx.x;
-  if (idx < g.f.n) g.p[idx] = it == 0 ? g.z[idx] : g.z[idx] + beta * g.p[idx];
+  if (idx < g.f.n) {
+    const df z{g.x32[idx], 0.f};
+    g.p[idx] = pack(it == 0 ? z : df_add(z, df_mul(beta, unpack(g.p[idx]))));
+  }
 }
 
 // --------------------------------------------------------- V-cycle kernels
@@ -303,9 +325,7 @@ __global__ void kb_sweep0(const Lev* L, const Des* D, const int* bdes, const int
     const float ti = v.t[idx];
     const float xo = ti + v.omega * v.dinv[idx] * (v.b[idx] - fine_row2(v.f0, v.t, i, j, diag));
     v.x[idx] = xo;
-    const double zi = (double)xo;
-    g.z[idx] = zi;
-    s[0] = g.r[idx] * zi;
+    s[0] = df_to_double(df_mulf(unpack(g.r[idx]), xo));
   }
   const int par = ((int)bsc[d * kBS + BS_IT]) & 1;
   seg_finish<1>(s, partials, counters, d, b0[d], nb, bsc + d * kBS + BS_RZ + par);
@@ -461,6 +481,8 @@ static void build_graph(Batch& b) {
     const int th = 128;
     kb_init<<<(b.nd + th - 1) / th, th, 0, b.stream>>>(b.bsc, b.consts, b.nd);
     MGAR_LAUNCH_CHECK();
+    kb_t_to_df<<<b.s_red.nblocks, kRedThreads, 0, b.stream>>>(b.ddes, b.s_red.bdes, b.s_red.b0);
+    MGAR_LAUNCH_CHECK();
     red_launch_resid(b);
     kb_start<<<(b.nd + th - 1) / th, th, 0, b.stream>>>(b.bsc, b.nd);
     MGAR_LAUNCH_CHECK();
@@ -483,6 +505,9 @@ static void build_graph(Batch& b) {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     MGAR_CUDA(cudaStreamUpdateCaptureDependencies(b.stream, &wnode, nullptr, 1,
                                                   cudaStreamSetCaptureDependencies));
+    // after the loop: the solutions back to the callers' FP64 vectors
+    kb_df_to_t<<<b.s_red.nblocks, kRedThreads, 0, b.stream>>>(b.ddes, b.s_red.bdes, b.s_red.b0);
+    MGAR_LAUNCH_CHECK();
     cudaGraph_t out = nullptr;
     MGAR_CUDA(cudaStreamEndCapture(b.cap, &out));
     b.stream = saved;
@@ -683,16 +708,15 @@ int mgar_batch_create(mgar_batch_t* out, const mgar_t* handles, int count, void*
       Ctx& c = *b->h[d];
       const Dims& d0 = c.L[0];
       n0[d] = d0.n;
-      des[d].f = FineOp<double>{c.ke, nullptr, c.fixed, d0.ex, d0.ey, d0.ez, d0.NX, d0.NY, d0.NZ,
-                                (int)d0.n, d0.fNX, d0.fNXY};
-      des[d].q = c.q;
-      des[d].r = c.r;
-      des[d].z = c.z;
-      des[d].p = c.pv;
-      des[d].Ap = c.Ap;
+      des[d].f = make_op(c);  // k_e pointers only: set_density keeps them current
+      des[d].q = c.df_q;
+      des[d].x = c.df_x;
+      des[d].r = c.df_r;
+      des[d].p = c.df_p;
+      des[d].Ap = c.df_Ap;
       des[d].b32 = c.b32;
       des[d].x32 = c.x32;
-      des[d].x = nullptr;  // the caller's T, set at each solve
+      des[d].T = nullptr;  // the caller's T, set at each solve
       for (int l = 0; l + 1 < c.nl; ++l) {
         Lev& v = lev[(size_t)l * nd + d];
         const Dims& dl = c.L[l];
@@ -795,8 +819,8 @@ static int batch_solve(Batch& b, double* const* T, int* iters, double* relres, i
   std::vector<Des>& des = b.hdes;
   bool moved = false;
   for (int d = 0; d < b.nd; ++d) {
-    moved = moved || des[d].x != T[d];
-    des[d].x = T[d];
+    moved = moved || des[d].T != T[d];
+    des[d].T = T[d];
     b.hconsts[3 * d] = b.h[d]->qnorm;
     b.hconsts[3 * d + 1] = b.h[d]->p.eps2;
     b.hconsts[3 * d + 2] = (double)b.h[d]->p.cg_max;

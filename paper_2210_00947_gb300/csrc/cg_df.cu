@@ -15,115 +15,11 @@
 // term is then rounded relative to its own size, not relative to |x|.
 #include "common.cuh"
 #include "df64.cuh"
+#include "dfop.cuh"
 
 namespace mgar {
 
 namespace {
-
-struct DfOp {
-  const float2* ke;
-  const uint8_t* fixed;
-  int ex, ey, ez, NX, NY, NZ, n;
-  FastDiv fNX, fNXY;
-  df scale;  // 1/6 (2D) or 1/12 (3D)
-};
-
-__device__ __forceinline__ df ld_kdf(const DfOp& op, int e, bool ok) {
-  const int ee = (ok && CK(e, op.ex * op.ey * op.ez)) ? e : 0;
-  const float2 v = op.ke[ee];
-  return ok ? df{v.x, v.y} : df{0.f, 0.f};
-}
-
-// neighbour value x^_j (0 when fixed or off the grid; off-grid terms also
-// have zero weight)
-__device__ __forceinline__ df ld_xdf(const DfOp& op, const float2* __restrict__ x, int idx, bool ok) {
-  const int j = (ok && CK(idx, op.n)) ? idx : 0;
-  const float2 v = x[j];
-  return (ok && !op.fixed[j]) ? df{v.x, v.y} : df{0.f, 0.f};
-}
-
-// acc += w * (xi - xj)
-__device__ __forceinline__ void df_term(df& acc, df w, df xi, df xj) {
-  float s, e;
-  two_sum(xi.hi, -xj.hi, s, e);
-  e = __fadd_rn(e, __fsub_rn(xi.lo, xj.lo));
-  acc = df_add(acc, df_mul(w, df_make(s, e)));
-}
-
-__device__ __forceinline__ df df_row2(const DfOp& op, const float2* __restrict__ x, int i, int j) {
-  const int idx = i + op.NX * j;
-  const float2 xv = x[idx];
-  const df xi{xv.x, xv.y};
-  if (op.fixed[idx]) return xi;
-  const bool xm = i > 0, xp = i < op.ex, ym = j > 0, yp = j < op.ey;
-  const int e00 = (i - 1) + op.ex * (j - 1);
-  const df k00 = ld_kdf(op, e00, xm && ym), k01 = ld_kdf(op, e00 + 1, xp && ym);
-  const df k10 = ld_kdf(op, e00 + op.ex, xm && yp), k11 = ld_kdf(op, e00 + op.ex + 1, xp && yp);
-  const int NX = op.NX;
-  df acc{0.f, 0.f};
-  df_term(acc, df_add(k00, k10), xi, ld_xdf(op, x, idx - 1, xm));
-  df_term(acc, df_add(k01, k11), xi, ld_xdf(op, x, idx + 1, xp));
-  df_term(acc, df_add(k00, k01), xi, ld_xdf(op, x, idx - NX, ym));
-  df_term(acc, df_add(k10, k11), xi, ld_xdf(op, x, idx + NX, yp));
-  df_term(acc, df_add(k00, k00), xi, ld_xdf(op, x, idx - NX - 1, xm && ym));
-  df_term(acc, df_add(k01, k01), xi, ld_xdf(op, x, idx - NX + 1, xp && ym));
-  df_term(acc, df_add(k10, k10), xi, ld_xdf(op, x, idx + NX - 1, xm && yp));
-  df_term(acc, df_add(k11, k11), xi, ld_xdf(op, x, idx + NX + 1, xp && yp));
-  return df_mul(acc, op.scale);
-}
-
-__device__ __forceinline__ df df_row3(const DfOp& op, const float2* __restrict__ x, int i, int j, int k) {
-  const int NX = op.NX, NXY = op.NX * op.NY;
-  const int idx = i + NX * j + NXY * k;
-  const float2 xv = x[idx];
-  const df xi{xv.x, xv.y};
-  if (op.fixed[idx]) return xi;
-  const bool xm = i > 0, xp = i < op.ex, ym = j > 0, yp = j < op.ey, zm = k > 0, zp = k < op.ez;
-  const int EX = op.ex, EXY = op.ex * op.ey;
-  const int e000 = (i - 1) + EX * (j - 1) + EXY * (k - 1);
-  const df k000 = ld_kdf(op, e000, xm && ym && zm);
-  const df k001 = ld_kdf(op, e000 + 1, xp && ym && zm);
-  const df k010 = ld_kdf(op, e000 + EX, xm && yp && zm);
-  const df k011 = ld_kdf(op, e000 + EX + 1, xp && yp && zm);
-  const df k100 = ld_kdf(op, e000 + EXY, xm && ym && zp);
-  const df k101 = ld_kdf(op, e000 + EXY + 1, xp && ym && zp);
-  const df k110 = ld_kdf(op, e000 + EXY + EX, xm && yp && zp);
-  const df k111 = ld_kdf(op, e000 + EXY + EX + 1, xp && yp && zp);
-  df acc{0.f, 0.f};
-  // face diagonals in the xy, xz and yz planes (two elements each)
-  df_term(acc, df_add(k000, k100), xi, ld_xdf(op, x, idx - 1 - NX, xm && ym));
-  df_term(acc, df_add(k001, k101), xi, ld_xdf(op, x, idx + 1 - NX, xp && ym));
-  df_term(acc, df_add(k010, k110), xi, ld_xdf(op, x, idx - 1 + NX, xm && yp));
-  df_term(acc, df_add(k011, k111), xi, ld_xdf(op, x, idx + 1 + NX, xp && yp));
-  df_term(acc, df_add(k000, k010), xi, ld_xdf(op, x, idx - 1 - NXY, xm && zm));
-  df_term(acc, df_add(k001, k011), xi, ld_xdf(op, x, idx + 1 - NXY, xp && zm));
-  df_term(acc, df_add(k100, k110), xi, ld_xdf(op, x, idx - 1 + NXY, xm && zp));
-  df_term(acc, df_add(k101, k111), xi, ld_xdf(op, x, idx + 1 + NXY, xp && zp));
-  df_term(acc, df_add(k000, k001), xi, ld_xdf(op, x, idx - NX - NXY, ym && zm));
-  df_term(acc, df_add(k010, k011), xi, ld_xdf(op, x, idx + NX - NXY, yp && zm));
-  df_term(acc, df_add(k100, k101), xi, ld_xdf(op, x, idx - NX + NXY, ym && zp));
-  df_term(acc, df_add(k110, k111), xi, ld_xdf(op, x, idx + NX + NXY, yp && zp));
-  // body diagonals (one element each)
-  df_term(acc, k000, xi, ld_xdf(op, x, idx - 1 - NX - NXY, xm && ym && zm));
-  df_term(acc, k001, xi, ld_xdf(op, x, idx + 1 - NX - NXY, xp && ym && zm));
-  df_term(acc, k010, xi, ld_xdf(op, x, idx - 1 + NX - NXY, xm && yp && zm));
-  df_term(acc, k011, xi, ld_xdf(op, x, idx + 1 + NX - NXY, xp && yp && zm));
-  df_term(acc, k100, xi, ld_xdf(op, x, idx - 1 - NX + NXY, xm && ym && zp));
-  df_term(acc, k101, xi, ld_xdf(op, x, idx + 1 - NX + NXY, xp && ym && zp));
-  df_term(acc, k110, xi, ld_xdf(op, x, idx - 1 + NX + NXY, xm && yp && zp));
-  df_term(acc, k111, xi, ld_xdf(op, x, idx + 1 + NX + NXY, xp && yp && zp));
-  return df_mul(acc, op.scale);
-}
-
-template <int DIM>
-__device__ __forceinline__ df df_row(const DfOp& op, const float2* __restrict__ x, int idx) {
-  int i, j, k;
-  coords(idx, op.fNX, op.fNXY, i, j, k);
-  return DIM == 2 ? df_row2(op, x, i, j) : df_row3(op, x, i, j, k);
-}
-
-__device__ __forceinline__ float2 pack(df a) { return make_float2(a.hi, a.lo); }
-__device__ __forceinline__ df unpack(float2 v) { return df{v.x, v.y}; }
 
 // y = A x; with DOT, x.y into out (per-thread df sums, FP64 across threads)
 template <int DIM, bool DOT>
@@ -232,24 +128,6 @@ __global__ void k_d_to_df(const double* __restrict__ a, float2* __restrict__ b, 
 __global__ void k_df_to_d(const float2* __restrict__ a, double* __restrict__ b, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = df_to_double(unpack(a[i]));
-}
-
-DfOp make_op(Ctx& c) {
-  const Dims& d = c.L[0];
-  DfOp op;
-  op.ke = c.ke_df;
-  op.fixed = c.fixed;
-  op.ex = d.ex;
-  op.ey = d.ey;
-  op.ez = d.ez;
-  op.NX = d.NX;
-  op.NY = d.NY;
-  op.NZ = d.NZ;
-  op.n = (int)d.n;
-  op.fNX = d.fNX;
-  op.fNXY = d.fNXY;
-  op.scale = df_from_double(c.dim == 2 ? 1.0 / 6.0 : 1.0 / 12.0);
-  return op;
 }
 
 }  // namespace
