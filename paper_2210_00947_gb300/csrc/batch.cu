@@ -39,7 +39,9 @@ namespace bat {
 constexpr int kRedThreads = 256;  // block size of every reducing kernel
 constexpr int kBS = 16;           // device scalars per design
 enum : int { BS_RZ = 0, BS_PAP = 2, BS_RR = 3, BS_IT = 4, BS_ACT = 5, BS_QN = 6, BS_EPS = 7,
-             BS_CGMAX = 8, BS_BAD = 9 };
+             BS_CGMAX = 8, BS_BAD = 9,
+             // gathered from each handle after the solve / the design cycle
+             BS_COMPL = 10, BS_LAM = 11, BS_CHANGE = 12, BS_FAIL = 13, BS_DERR = 14 };
 
 // One design at one level of the V-cycle.
 struct Lev {
@@ -68,6 +70,8 @@ struct Des {
   float2 *x, *r, *p, *Ap;  // CG vectors as df64 pairs (the handle's own buffers)
   double* T;           // the caller's solution (FP64): warm start in, solution out
   float *b32, *x32;    // FP32 input and output of the V-cycle at level 0
+  const double* dsc;   // the handle's device scalars (compliance, OC outcome)
+  const int* derr;     // the handle's factorisation error flag
 };
 
 // Launch shape: which design each block serves.
@@ -125,6 +129,20 @@ __global__ void kb_df_to_t(const Des* D, const int* bdes, const int* b0) {
   const Des& g = D[d];
   const int idx = (blockIdx.x - b0[d]) * blockDim.x + threadIdx.x;
   if (idx < g.f.n) g.T[idx] = df_to_double(unpack(g.x[idx]));
+}
+
+// Each handle's compliance, OC outcome and factorisation flag into the
+// batch scalars, so that one copy brings every design's outcome to the host.
+__global__ void kb_gather(const Des* D, int nd, double* bsc) {
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= nd) return;
+  const Des& g = D[d];
+  double* s = bsc + (size_t)d * kBS;
+  s[BS_COMPL] = g.dsc[S_COMPL];
+  s[BS_LAM] = g.dsc[S_OC_LAM];
+  s[BS_CHANGE] = g.dsc[S_OC_CHANGE];
+  s[BS_FAIL] = g.dsc[S_OC_FAIL];
+  s[BS_DERR] = (double)*g.derr;
 }
 
 // r = q - A x, its FP32 copy, ||r||^2 (the start of each design's CG).
@@ -359,6 +377,14 @@ struct Batch {
   // design cycles: each handle's stream -> the batch stream, and back
   std::vector<cudaEvent_t> ev_des;
   cudaEvent_t ev_solved = nullptr, ev_start = nullptr;
+  // per-design work of every handle as one graph (a branch per design), kept
+  // while the pointers and values captured in it stay the same
+  struct DesignGraph {
+    std::vector<uint64_t> key;
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;
+  };
+  DesignGraph g_hier, g_pre, g_post;  // hierarchy; filter+SIMP+hierarchy; sens+compliance+OC
 };
 
 static void free_shape(Shape& s) {
@@ -653,6 +679,8 @@ int bguard(mgar_batch_t hb, F&& f) {
 
 void free_batch(Batch& b) {
   if (b.exec) cudaGraphExecDestroy(b.exec);
+  for (Batch::DesignGraph* g : {&b.g_hier, &b.g_pre, &b.g_post})
+    if (g->exec) cudaGraphExecDestroy(g->exec);
   for (cudaEvent_t e : b.ev_des) cudaEventDestroy(e);
   if (b.ev_solved) cudaEventDestroy(b.ev_solved);
   if (b.ev_start) cudaEventDestroy(b.ev_start);
@@ -671,6 +699,186 @@ void free_batch(Batch& b) {
   if (b.hbsc) cudaFreeHost(b.hbsc);
   if (b.cap) cudaStreamDestroy(b.cap);
 }
+// Graphs are taken when every handle allows them and none is timing a
+// kernel class (a timed class is measured launch by launch).
+bool graphable(const Batch& b) {
+  for (const Ctx* c : b.h)
+    if (!c->use_graphs || c->prof_class != 0) return false;
+  return true;
+}
+
+// The batch stream after whatever each handle's stream holds, with each
+// handle's pending coarsest factorisation joined first.
+void order_after_handles(Batch& b) {
+  for (int d = 0; d < b.nd; ++d) {
+    Ctx& c = *b.h[d];
+    join_coarse(c);
+    if (c.stream == b.stream) continue;
+    MGAR_CUDA(cudaEventRecord(b.ev_des[d], c.stream));
+    MGAR_CUDA(cudaStreamWaitEvent(b.stream, b.ev_des[d], 0));
+  }
+}
+
+uint64_t key_bits(double v) {
+  uint64_t u;
+  std::memcpy(&u, &v, sizeof u);
+  return u;
+}
+
+// What a design's captured work depends on besides the batch's own buffers:
+// its filter (radius and table size).
+void key_filter(std::vector<uint64_t>& key, const Ctx& c) {
+  key.push_back(key_bits(c.filter_r));
+  key.push_back((uint64_t)c.n_filter);
+}
+
+// Launches g on the batch stream, capturing it first if its key changed:
+// each design's work is captured on the batch's capture stream (the handle's
+// side stream joins it for the coarsest factorisation and is joined back)
+// and added to one graph as a child graph without dependencies, so the
+// designs' branches run at once and the host issues one launch for all.
+template <class F>
+void launch_design_graph(Batch& b, Batch::DesignGraph& g, std::vector<uint64_t>&& key,
+                                F&& chain) {
+  if (!g.exec || g.key != key) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g.exec = nullptr;
+    cudaGraph_t parent = nullptr;
+    MGAR_CUDA(cudaGraphCreate(&parent, 0));
+    const int64_t before = launches_so_far();
+    try {
+      for (int d = 0; d < b.nd; ++d) {
+        Ctx& c = *b.h[d];
+        cudaStream_t saved = c.stream;
+        cudaGraph_t gd = nullptr;
+        MGAR_CUDA(cudaStreamBeginCapture(b.cap, cudaStreamCaptureModeThreadLocal));
+        c.stream = b.cap;
+        try {
+          chain(d, c);
+          join_coarse(c);
+        } catch (...) {
+          c.stream = saved;
+          cudaStreamEndCapture(b.cap, &gd);
+          if (gd) cudaGraphDestroy(gd);
+          throw;
+        }
+        c.stream = saved;
+        MGAR_CUDA(cudaStreamEndCapture(b.cap, &gd));
+        cudaGraphNode_t node;
+        const cudaError_t e = cudaGraphAddChildGraphNode(&node, parent, nullptr, 0, gd);
+        cudaGraphDestroy(gd);
+        MGAR_CUDA(e);
+      }
+      cudaGraphExec_t exec = nullptr;
+      MGAR_CUDA(cudaGraphInstantiate(&exec, parent, 0));
+      g.exec = exec;
+    } catch (...) {
+      cudaGraphDestroy(parent);
+      count_launches(-(launches_so_far() - before));
+      throw;
+    }
+    cudaGraphDestroy(parent);
+    g.kernels = launches_so_far() - before;
+    count_launches(-g.kernels);  // captured, not executed
+    g.key = std::move(key);
+  }
+  MGAR_CUDA(cudaGraphLaunch(g.exec, b.stream));
+  count_launches(g.kernels);
+}
+
+// Each design's hierarchy from its current design (K0 <- K), ordered after
+// what the batch stream and the handle's stream hold; the batch stream
+// waits for all of them.  As one graph of per-design branches, or (timed or
+// graph-less handles) on the handles' own streams, so that the designs'
+// builds (and their coarsest factorisations on the handles' side streams)
+// run at once either way.
+void build_hierarchies(Batch& b) {
+  if (graphable(b)) {
+    order_after_handles(b);
+    launch_design_graph(b, b.g_hier, {}, [](int, Ctx& c) { build_hierarchy(c); });
+    return;
+  }
+  MGAR_CUDA(cudaEventRecord(b.ev_start, b.stream));
+  for (int d = 0; d < b.nd; ++d) {
+    Ctx& c = *b.h[d];
+    MGAR_CUDA(cudaStreamWaitEvent(c.stream, b.ev_start, 0));
+    build_hierarchy(c);
+    join_coarse(c);
+    MGAR_CUDA(cudaEventRecord(b.ev_des[d], c.stream));
+  }
+  for (int d = 0; d < b.nd; ++d) MGAR_CUDA(cudaStreamWaitEvent(b.stream, b.ev_des[d], 0));
+}
+
+// The batched solve queued on the batch stream after the hierarchies: the
+// callers' solution vectors and the per-design constants, the autotuner and
+// the solve graph on the first call, the graph's launch.
+void solve_issue(Batch& b, double* const* T) {
+  std::vector<Des>& des = b.hdes;
+  bool moved = false;
+  for (int d = 0; d < b.nd; ++d) {
+    moved = moved || des[d].T != T[d];
+    des[d].T = T[d];
+    b.hconsts[3 * d] = b.h[d]->qnorm;
+    b.hconsts[3 * d + 1] = b.h[d]->p.eps2;
+    b.hconsts[3 * d + 2] = (double)b.h[d]->p.cg_max;
+  }
+  if (moved)
+    MGAR_CUDA(cudaMemcpyAsync(b.ddes, des.data(), b.nd * sizeof(Des), cudaMemcpyHostToDevice,
+                              b.stream));
+  MGAR_CUDA(cudaMemcpyAsync(b.consts, b.hconsts, (size_t)b.nd * 3 * sizeof(double),
+                            cudaMemcpyHostToDevice, b.stream));
+  if (!b.exec) {
+    MGAR_CUDA(cudaStreamSynchronize(b.stream));
+    autotune(b);
+    build_graph(b);
+  }
+  MGAR_CUDA(cudaGraphLaunch(b.exec, b.stream));
+}
+
+// Every design's outcome to the host once the batch stream holds all the
+// work: one gather kernel, one copy, one wait.
+void gather_outcomes(Batch& b) {
+  kb_gather<<<(b.nd + 127) / 128, 128, 0, b.stream>>>(b.ddes, b.nd, b.bsc);
+  MGAR_LAUNCH_CHECK();
+  MGAR_CUDA(cudaMemcpyAsync(b.hbsc, b.bsc, (size_t)b.nd * kBS * sizeof(double),
+                            cudaMemcpyDeviceToHost, b.stream));
+  MGAR_CUDA(cudaStreamSynchronize(b.stream));
+}
+
+// The solve's outcome per design from the gathered scalars; a coarsest
+// factorisation that met a non-positive pivot is an error of the call.
+int solve_read(Batch& b, int* iters, double* relres, int* status) {
+  int maxit = 0;
+  int rc = MGAR_OK;
+  for (int d = 0; d < b.nd; ++d) {
+    const double* s = b.hbsc + (size_t)d * kBS;
+    const int it = (int)s[BS_IT];
+    const double rel = std::sqrt(s[BS_RR]) / s[BS_QN];
+    maxit = std::max(maxit, it);
+    int st = MGAR_OK;
+    if (s[BS_BAD] != 0.0 || !std::isfinite(rel)) st = MGAR_ERR_NONFINITE;
+    else if (!(rel <= b.h[d]->p.eps2)) st = MGAR_ERR_MAXIT;
+    if (iters) iters[d] = it;
+    if (relres) relres[d] = rel;
+    if (status) status[d] = st;
+    if (st == MGAR_ERR_NONFINITE) rc = MGAR_ERR_NONFINITE;
+    else if (st == MGAR_ERR_MAXIT && rc == MGAR_OK) rc = MGAR_ERR_MAXIT;
+    // the solution is the handle's new reference
+    b.h[d]->have_ref = true;
+  }
+  count_launches(b.prologue + (int64_t)maxit * b.body);
+  for (int d = 0; d < b.nd; ++d) {
+    const int e = (int)b.hbsc[(size_t)d * kBS + BS_DERR];
+    if (e) {
+      MGAR_CUDA(cudaMemset(b.h[d]->derr, 0, sizeof(int)));
+      throw Error{e, "a coarsest factorisation met a non-positive pivot"};
+    }
+  }
+  if (rc == MGAR_ERR_MAXIT) b.err = "a design reached cg_max";
+  if (rc == MGAR_ERR_NONFINITE) b.err = "a design's CG broke down (non-finite residual)";
+  return rc;
+}
+
 }  // namespace
 
 extern "C" {
@@ -717,6 +925,8 @@ int mgar_batch_create(mgar_batch_t* out, const mgar_t* handles, int count, void*
       des[d].b32 = c.b32;
       des[d].x32 = c.x32;
       des[d].T = nullptr;  // the caller's T, set at each solve
+      des[d].dsc = c.dsc;
+      des[d].derr = c.derr;
       for (int l = 0; l + 1 < c.nl; ++l) {
         Lev& v = lev[(size_t)l * nd + d];
         const Dims& dl = c.L[l];
@@ -797,79 +1007,14 @@ const char* mgar_batch_last_error(mgar_batch_t hb) {
   return reinterpret_cast<Batch*>(hb)->err.c_str();
 }
 
-// The batched solve for the designs' current densities (shared by the solve
-// and the design-cycle entry points).
+// The batched solve for the designs' current densities.
 static int batch_solve(Batch& b, double* const* T, int* iters, double* relres, int* status) {
   require(T != nullptr, MGAR_ERR_ARG, "batch_solve_mgcg: null T");
   for (int d = 0; d < b.nd; ++d) require(T[d] != nullptr, MGAR_ERR_ARG, "batch_solve_mgcg: null T[d]");
-  // each design's hierarchy from its current design (K0 <- K) on its own
-  // handle's stream, after what the batch stream holds, so the designs'
-  // builds (and their coarsest factorisations on the handles' side streams)
-  // run at once; the batch stream waits for all of them before the solve
-  MGAR_CUDA(cudaEventRecord(b.ev_start, b.stream));
-  for (int d = 0; d < b.nd; ++d) {
-    Ctx& c = *b.h[d];
-    MGAR_CUDA(cudaStreamWaitEvent(c.stream, b.ev_start, 0));
-    build_hierarchy(c);
-    join_coarse(c);
-    MGAR_CUDA(cudaEventRecord(b.ev_des[d], c.stream));
-  }
-  for (int d = 0; d < b.nd; ++d) MGAR_CUDA(cudaStreamWaitEvent(b.stream, b.ev_des[d], 0));
-  // the callers' solution vectors and the per-design constants
-  std::vector<Des>& des = b.hdes;
-  bool moved = false;
-  for (int d = 0; d < b.nd; ++d) {
-    moved = moved || des[d].T != T[d];
-    des[d].T = T[d];
-    b.hconsts[3 * d] = b.h[d]->qnorm;
-    b.hconsts[3 * d + 1] = b.h[d]->p.eps2;
-    b.hconsts[3 * d + 2] = (double)b.h[d]->p.cg_max;
-  }
-  if (moved)
-    MGAR_CUDA(cudaMemcpyAsync(b.ddes, des.data(), b.nd * sizeof(Des), cudaMemcpyHostToDevice,
-                              b.stream));
-  MGAR_CUDA(cudaMemcpyAsync(b.consts, b.hconsts, (size_t)b.nd * 3 * sizeof(double),
-                            cudaMemcpyHostToDevice, b.stream));
-  if (!b.exec) {
-    MGAR_CUDA(cudaStreamSynchronize(b.stream));
-    autotune(b);
-    build_graph(b);
-  }
-  MGAR_CUDA(cudaGraphLaunch(b.exec, b.stream));
-  MGAR_CUDA(cudaMemcpyAsync(b.hbsc, b.bsc, (size_t)b.nd * kBS * sizeof(double),
-                            cudaMemcpyDeviceToHost, b.stream));
-  MGAR_CUDA(cudaStreamSynchronize(b.stream));
-  int maxit = 0;
-  int rc = MGAR_OK;
-  for (int d = 0; d < b.nd; ++d) {
-    const double* s = b.hbsc + (size_t)d * kBS;
-    const int it = (int)s[BS_IT];
-    const double rel = std::sqrt(s[BS_RR]) / s[BS_QN];
-    maxit = std::max(maxit, it);
-    int st = MGAR_OK;
-    if (s[BS_BAD] != 0.0 || !std::isfinite(rel)) st = MGAR_ERR_NONFINITE;
-    else if (!(rel <= b.h[d]->p.eps2)) st = MGAR_ERR_MAXIT;
-    if (iters) iters[d] = it;
-    if (relres) relres[d] = rel;
-    if (status) status[d] = st;
-    if (st == MGAR_ERR_NONFINITE) rc = MGAR_ERR_NONFINITE;
-    else if (st == MGAR_ERR_MAXIT && rc == MGAR_OK) rc = MGAR_ERR_MAXIT;
-    // the solution is the handle's new reference
-    b.h[d]->have_ref = true;
-  }
-  count_launches(b.prologue + (int64_t)maxit * b.body);
-  // the factorisations' error flags (published per handle)
-  for (Ctx* c : b.h) {
-    int e = 0;
-    MGAR_CUDA(cudaMemcpy(&e, c->derr, sizeof(int), cudaMemcpyDeviceToHost));
-    if (e) {
-      MGAR_CUDA(cudaMemset(c->derr, 0, sizeof(int)));
-      throw Error{e, "a coarsest factorisation met a non-positive pivot"};
-    }
-  }
-  if (rc == MGAR_ERR_MAXIT) b.err = "a design reached cg_max";
-  if (rc == MGAR_ERR_NONFINITE) b.err = "a design's CG broke down (non-finite residual)";
-  return rc;
+  build_hierarchies(b);
+  solve_issue(b, T);
+  gather_outcomes(b);
+  return solve_read(b, iters, relres, status);
 }
 
 int mgar_batch_solve_mgcg(mgar_batch_t hb, double* const* T, int* iters, double* relres,
@@ -889,31 +1034,68 @@ int mgar_batch_cycle(mgar_batch_t hb, double* const* rho, double* const* T, cons
       require(!(b.h[d]->p.filter_alpha > 0.0), MGAR_ERR_ARG,
               "batch_cycle: the continuation filter schedule is per cycle of mgar_step");
     }
-    // each design's filter and SIMP on its own stream; the batch stream waits
-    // for all of them
-    for (int d = 0; d < nd; ++d) {
-      Ctx& c = *b.h[d];
-      set_density(c, rho[d], false);
-      MGAR_CUDA(cudaEventRecord(b.ev_des[d], c.stream));
-      MGAR_CUDA(cudaStreamWaitEvent(b.stream, b.ev_des[d], 0));
-    }
-    std::vector<int> it(nd), st(nd);
-    std::vector<double> rr(nd);
-    const int rc = batch_solve(b, T, it.data(), rr.data(), st.data());
-    // each design's sensitivities, compliance and OC update queued on its
-    // own stream after the solve, all of them before any outcome is read
-    MGAR_CUDA(cudaEventRecord(b.ev_solved, b.stream));
-    for (int d = 0; d < nd; ++d) {
-      Ctx& c = *b.h[d];
-      MGAR_CUDA(cudaStreamWaitEvent(c.stream, b.ev_solved, 0));
+    // each design's sensitivities (Eq. 10 through the filter), compliance
+    // and OC update after the solve
+    auto post = [&](int d, Ctx& c) {
       sensitivity(c, T[d], c.tmp_dc, nullptr, nullptr);
       dot(c, c.q, T[d], c.n, c.dsc + S_COMPL);
       oc_issue(c, rho[d], c.tmp_dc, volfrac[d], move);
+    };
+    if (graphable(b)) {
+      // three launches from the host: every design's filter, SIMP and
+      // hierarchy as one graph, the solve graph, every design's update as
+      // one graph
+      std::vector<uint64_t> kpre, kpost;
+      for (int d = 0; d < nd; ++d) {
+        kpre.push_back((uint64_t)(uintptr_t)rho[d]);
+        key_filter(kpre, *b.h[d]);
+      }
+      kpost = kpre;
+      for (int d = 0; d < nd; ++d) {
+        kpost.push_back((uint64_t)(uintptr_t)T[d]);
+        kpost.push_back(key_bits(volfrac[d]));
+      }
+      kpost.push_back(key_bits(move));
+      order_after_handles(b);
+      launch_design_graph(b, b.g_pre, std::move(kpre), [&](int d, Ctx& c) {
+        set_density(c, rho[d], false);
+        build_hierarchy(c);
+      });
+      solve_issue(b, T);
+      launch_design_graph(b, b.g_post, std::move(kpost), post);
+    } else {
+      // each design's filter and SIMP on its own stream, the hierarchies,
+      // the solve, then the updates on the handles' streams again
+      for (int d = 0; d < nd; ++d) {
+        Ctx& c = *b.h[d];
+        set_density(c, rho[d], false);
+        MGAR_CUDA(cudaEventRecord(b.ev_des[d], c.stream));
+        MGAR_CUDA(cudaStreamWaitEvent(b.stream, b.ev_des[d], 0));
+      }
+      build_hierarchies(b);
+      solve_issue(b, T);
+      MGAR_CUDA(cudaEventRecord(b.ev_solved, b.stream));
+      for (int d = 0; d < nd; ++d) {
+        Ctx& c = *b.h[d];
+        MGAR_CUDA(cudaStreamWaitEvent(c.stream, b.ev_solved, 0));
+        post(d, c);
+        MGAR_CUDA(cudaEventRecord(b.ev_des[d], c.stream));
+        MGAR_CUDA(cudaStreamWaitEvent(b.stream, b.ev_des[d], 0));
+      }
     }
+    gather_outcomes(b);
+    std::vector<int> it(nd), st(nd);
+    std::vector<double> rr(nd);
+    const int rc = solve_read(b, it.data(), rr.data(), st.data());
     for (int d = 0; d < nd; ++d) {
       Ctx& c = *b.h[d];
+      const double* s = b.hbsc + (size_t)d * kBS;
+      c.hsc[S_COMPL] = s[BS_COMPL];
+      c.hsc[S_OC_LAM] = s[BS_LAM];
+      c.hsc[S_OC_CHANGE] = s[BS_CHANGE];
+      c.hsc[S_OC_FAIL] = s[BS_FAIL];
       double lam = 0.0, change = 0.0;
-      oc_complete(c, rho[d], volfrac[d], &lam, &change);
+      oc_finish(c, rho[d], volfrac[d], &lam, &change);
       if (info) {
         mgar_step_info& inf = info[d];
         inf = mgar_step_info{};

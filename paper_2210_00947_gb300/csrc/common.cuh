@@ -962,6 +962,9 @@ void oc_update(Ctx& c, double* rho, const double* dc, double volfrac, double mov
 // failed), so many handles' updates can be queued before any is read
 void oc_issue(Ctx& c, double* rho, const double* dc, double volfrac, double move);
 void oc_complete(Ctx& c, double* rho, double volfrac, double* lambda, double* change);
+// oc_complete without its read: the host mirror already holds S_OC_LAM,
+// S_OC_CHANGE and S_OC_FAIL of the update
+void oc_finish(Ctx& c, double* rho, double volfrac, double* lambda, double* change);
 
 }  // namespace mgar
 

@@ -866,9 +866,16 @@ void oc_issue(Ctx& c, double* rho, const double* dc, double volfrac, double move
 // compliance dot launched before the update; if the fast solve failed, the
 // plain bisection on lambda over the whole range and the apply again.
 void oc_complete(Ctx& c, double* rho, double volfrac, double* lambda, double* change) {
+  fetch_scalars(c, S_OC_LAM, S_OC_FAIL - S_OC_LAM + 1);
+  oc_finish(c, rho, volfrac, lambda, change);
+}
+
+// The rest of oc_complete once the host mirror holds S_OC_LAM, S_OC_CHANGE
+// and S_OC_FAIL of this update (read by oc_complete, or gathered for many
+// designs at once by the batched design cycle).
+void oc_finish(Ctx& c, double* rho, double volfrac, double* lambda, double* change) {
   const int ne = (int)c.ne;
   const int rb = c.grid_blocks_e;
-  fetch_scalars(c, S_OC_LAM, S_OC_FAIL - S_OC_LAM + 1);
   const bool fast_ok = c.hsc[S_OC_FAIL] == 0.0;
   if (!fast_ok) {
     k_oc_init<<<1, 1, 0, c.stream>>>(c.dsc, 1e-40, 1e40);

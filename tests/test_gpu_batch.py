@@ -160,14 +160,21 @@ def test_batched_design_loop_follows_the_per_handle_loop():
         assert np.max(np.abs(rb - rr)) < 1e-5
 
 
-def test_batch_cycle_equals_its_steps():
+def test_batch_cycle_equals_its_steps(monkeypatch):
     """mgar_batch_cycle (filter, batched solve, sensitivities and OC queued for
     every design before any outcome is read) gives bit for bit what the same
-    steps give called one by one."""
+    steps give called one by one: as graphs of per-design branches (captured
+    again when the solution vectors move), and launched eagerly on the
+    handles' streams."""
     ds = UNEVEN[:3]
-    cycles = 3
+    cycles = 4
     runs = []
-    for fused in (True, False):
+    for mode in ("graphs", "eager", "steps"):
+        fused = mode != "steps"
+        if mode == "eager":
+            monkeypatch.setenv("MGAR_NO_GRAPHS", "1")
+        else:
+            monkeypatch.delenv("MGAR_NO_GRAPHS", raising=False)
         sv, rh, Ts, vf = [], [], [], []
         for d in ds:
             p = d.params(cycles, mgar.MGAR_MIXED, nl=5, n_on=cycles + 1, eps2=1e-10)
@@ -177,7 +184,9 @@ def test_batch_cycle_equals_its_steps():
             vf.append(d.volfrac)
         comps = []
         with mgar.BatchSolver(sv, stream=torch.cuda.Stream()) as b:
-            for _ in range(cycles):
+            for k in range(cycles):
+                if k == 2:
+                    Ts = [T.clone() for T in Ts]
                 if fused:
                     comps.append([inf["compliance"] for inf in b.cycle(rh, Ts, vf, 0.2)])
                 else:
@@ -195,7 +204,8 @@ def test_batch_cycle_equals_its_steps():
         runs.append(([r.cpu().numpy() for r in rh], comps))
         for s in sv:
             s.close()
-    (ra, ca), (rb, cb) = runs
-    assert ca == cb
-    for a, b_ in zip(ra, rb):
-        np.testing.assert_array_equal(a, b_)
+    (ra, ca), *others = runs
+    for rb, cb in others:
+        assert ca == cb
+        for a, b_ in zip(ra, rb):
+            np.testing.assert_array_equal(a, b_)
