@@ -316,10 +316,14 @@ int mgar_batch_solve_mgcg(mgar_batch_t b, double* const* T, int* iters, double* 
 /* One design cycle of Figure 5 with MGCG for every design of the batch
  * (Eq. 6-8 filter and Eq. 4 SIMP, the batched solve of Eq. 3, the
  * compliance of Eq. 5, the sensitivities of Eq. 9-11 and the OC update), as
- * mgar_step does for one handle with n_on past the cycle: each design's
- * filter, sensitivity and OC kernels run on its handle's stream, the solve
- * on the batch's, and every design's update is queued before any outcome is
- * read.
+ * mgar_step does for one handle with n_on past the cycle.  All of it runs on
+ * the batch's stream, ordered after what each handle's stream holds: every
+ * design's filter, SIMP and hierarchy as one CUDA graph of per-design
+ * branches, the solve graph, every design's update as one graph, then one
+ * read of all outcomes.  The per-design graphs are kept while the pointers,
+ * volume fractions and move limit passed stay the same, and captured again
+ * otherwise.  When a handle times a kernel class or runs without graphs, the
+ * same launches are issued on the handles' own streams instead.
  *   rho:     host array of `count` device pointers, each ne_d doubles: the
  *            design in, the updated design out.
  *   T:       host array of `count` device pointers, each n_d doubles: warm
@@ -331,7 +335,7 @@ int mgar_batch_solve_mgcg(mgar_batch_t b, double* const* T, int* iters, double* 
  * Returns as mgar_batch_solve_mgcg.  Errors: MGAR_ERR_ARG (null pointers,
  * volfrac or move out of range, a handle with the continuation filter
  * schedule of filter_alpha, which follows mgar_step's cycle count).
- * Synchronises every handle's stream and the batch's. */
+ * Synchronises the batch's stream (and with it all the work of the call). */
 int mgar_batch_cycle(mgar_batch_t b, double* const* rho, double* const* T, const double* volfrac,
                      double move, mgar_step_info* info);
 
