@@ -764,9 +764,11 @@ def run_batch(args):
                               for d in batch.designs_from_workload(args.batch)),
             "batched": {"seconds": t_bat, "design_cycles_per_s": total / t_bat,
                         "nl": "each design's own depth (coarsest level of at most 300 nodes)",
-                        "solve": "one mgar_batch_cycle per cycle: one launch per V-cycle level and "
-                                 "operation over all designs, FP32 V-cycle and FP64 CG in one CUDA "
-                                 "graph; every design's update queued before any is read",
+                        "solve": "one mgar_batch_cycle per cycle: every design's filter, SIMP and "
+                                 "hierarchy as one graph of per-design branches; the solve graph, one "
+                                 "launch per V-cycle level and operation over all designs, FP32 "
+                                 "V-cycle and double-float CG; every design's sensitivities and OC "
+                                 "update as one graph; one read of all outcomes",
                         "cg_iters_mean": statistics.mean(h["cg_iters"] for _, hs in bat
                                                          for h in hs),
                         "autotuner": [l for l in report.splitlines() if not l.startswith("  ")]},
