@@ -84,18 +84,19 @@ struct Shape {
 
 __device__ __forceinline__ bool active(const double* bsc, int d) { return bsc[d * kBS + BS_ACT] != 0.0; }
 
-// Deterministic per-design sum: the design's blocks write partials, its last
-// block adds them in block order into *out.
-template <int N>
-__device__ __forceinline__ void seg_finish(double (&v)[N], double* partials, unsigned int* counters,
-                                           int d, int b0, int nb, double* out) {
-  double t[N];
-  if (block_sum_last_ids<N>(v, partials + (size_t)N * b0, counters + d, t, threadIdx.x, blockDim.x,
-                            blockIdx.x - b0, nb) &&
-      threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < N; ++k) out[k] = t[k];
-  }
+// Deterministic per-design sum of one double-float value per thread: the
+// design's blocks write partials, its last block adds them in block order
+// into *out.  Warp sums in df64 on the FP32 pipe, FP64 only across warps and
+// blocks (GB300 runs FP64 at 1/58
+// of the FP32 rate; an FP64 value per thread through a shuffle tree costs
+// more than the data pass of these kernels).
+__device__ __forceinline__ void seg_finish_df(df v, double* partials, unsigned int* counters, int d,
+                                              int b0, int nb, double* out) {
+  double t = 0.0;
+  if (block_sum_last_df(v, partials + b0, counters + d, t, threadIdx.x, blockDim.x,
+                        blockIdx.x - b0, nb) &&
+      threadIdx.x == 0)
+    *out = t;
 }
 
 // ------------------------------------------------------------ df64 CG kernels
@@ -152,14 +153,14 @@ __global__ void kb_resid64(const Des* D, const int* bdes, const int* b0, double*
   const Des& g = D[d];
   const int nb = (g.f.n + blockDim.x - 1) / blockDim.x;
   const int idx = (blockIdx.x - b0[d]) * blockDim.x + threadIdx.x;
-  double v[1] = {0.0};
+  df v{0.f, 0.f};
   if (idx < g.f.n) {
     const df ri = df_sub(unpack(g.q[idx]), df_row<2>(g.f, g.x, idx));
     g.r[idx] = pack(ri);
     g.b32[idx] = __fadd_rn(ri.hi, ri.lo);
-    v[0] = df_to_double(df_mul(ri, ri));
+    v = df_mul(ri, ri);
   }
-  seg_finish<1>(v, partials, counters, d, b0[d], nb, bsc + d * kBS + BS_RR);
+  seg_finish_df(v, partials, counters, d, b0[d], nb, bsc + d * kBS + BS_RR);
 }
 
 // After the initial residual: a design whose start already meets eps2 (or
@@ -181,13 +182,13 @@ __global__ void kb_apply_dot(const Des* D, const int* bdes, const int* b0, doubl
   const Des& g = D[d];
   const int nb = (g.f.n + blockDim.x - 1) / blockDim.x;
   const int idx = (blockIdx.x - b0[d]) * blockDim.x + threadIdx.x;
-  double v[1] = {0.0};
+  df v{0.f, 0.f};
   if (idx < g.f.n) {
     const df ap = df_row<2>(g.f, g.p, idx);
     g.Ap[idx] = pack(ap);
-    v[0] = df_to_double(df_mul(unpack(g.p[idx]), ap));
+    v = df_mul(unpack(g.p[idx]), ap);
   }
-  seg_finish<1>(v, partials, counters, d, b0[d], nb, bsc + d * kBS + BS_PAP);
+  seg_finish_df(v, partials, counters, d, b0[d], nb, bsc + d * kBS + BS_PAP);
 }
 
 // alpha = r.z / p.Ap; x += alpha p; r -= alpha Ap; ||r||^2; FP32 copy of r.
@@ -201,20 +202,20 @@ __global__ void kb_cg_xr(const Des* D, const int* bdes, const int* b0, double* b
   const df alpha = block_div_df(s + BS_RZ + par, s + BS_PAP);
   const int nb = (g.f.n + blockDim.x - 1) / blockDim.x;
   const int idx = (blockIdx.x - b0[d]) * blockDim.x + threadIdx.x;
-  double v[1] = {0.0};
+  df v{0.f, 0.f};
   if (idx < g.f.n) {
     g.x[idx] = pack(df_add(unpack(g.x[idx]), df_mul(alpha, unpack(g.p[idx]))));
     const df ri = df_sub(unpack(g.r[idx]), df_mul(alpha, unpack(g.Ap[idx])));
     g.r[idx] = pack(ri);
     g.b32[idx] = __fadd_rn(ri.hi, ri.lo);
-    v[0] = df_to_double(df_mul(ri, ri));
+    v = df_mul(ri, ri);
   }
-  seg_finish<1>(v, partials, counters, d, b0[d], nb, bsc + d * kBS + BS_RR);
+  seg_finish_df(v, partials, counters, d, b0[d], nb, bsc + d * kBS + BS_RR);
 }
 
 // One iteration done: count it and decide, per design, whether to go on;
 // the WHILE node repeats while any design is active.
-__global__ void kb_check(double* bsc, int nd, cudaGraphConditionalHandle loop) {
+__global__ void kb_check(double* bsc, int nd, cudaGraphConditionalHandle loop, int* any_out) {
   __shared__ int any;
   if (threadIdx.x == 0) any = 0;
   __syncthreads();
@@ -230,7 +231,10 @@ __global__ void kb_check(double* bsc, int nd, cudaGraphConditionalHandle loop) {
     if (go) atomicOr(&any, 1);
   }
   __syncthreads();
-  if (threadIdx.x == 0) cudaGraphSetConditional(loop, any ? 1u : 0u);
+  if (threadIdx.x == 0) {
+    if (any_out) *any_out = any;  // a loop driven from the host
+    else cudaGraphSetConditional(loop, any ? 1u : 0u);
+  }
 }
 
 // p = z + (r.z_new / r.z_old) p (p = z in the first iteration), z the FP32
@@ -335,7 +339,7 @@ __global__ void kb_sweep0(const Lev* L, const Des* D, const int* bdes, const int
   const Des& g = D[d];
   const int nb = (v.d.n + blockDim.x - 1) / blockDim.x;
   const int idx = (blockIdx.x - b0[d]) * blockDim.x + threadIdx.x;
-  double s[1] = {0.0};
+  df s{0.f, 0.f};
   if (idx < v.d.n) {
     int i, j, k;
     coords(idx, v.f0.fNX, v.f0.fNXY, i, j, k);
@@ -343,10 +347,10 @@ __global__ void kb_sweep0(const Lev* L, const Des* D, const int* bdes, const int
     const float ti = v.t[idx];
     const float xo = ti + v.omega * v.dinv[idx] * (v.b[idx] - fine_row2(v.f0, v.t, i, j, diag));
     v.x[idx] = xo;
-    s[0] = df_to_double(df_mulf(unpack(g.r[idx]), xo));
+    s = df_mulf(unpack(g.r[idx]), xo);
   }
   const int par = ((int)bsc[d * kBS + BS_IT]) & 1;
-  seg_finish<1>(s, partials, counters, d, b0[d], nb, bsc + d * kBS + BS_RZ + par);
+  seg_finish_df(s, partials, counters, d, b0[d], nb, bsc + d * kBS + BS_RZ + par);
 }
 
 // ------------------------------------------------------------------- host
@@ -373,6 +377,9 @@ struct Batch {
   Shape s_coarse;
   cudaGraphExec_t exec = nullptr;
   int64_t prologue = 0, body = 0;
+  int* any = nullptr;   // device: any design active after a host-driven iteration
+  int* hany = nullptr;  // pinned copy
+  bool eager = false;   // the last solve was launched from the host
   std::string report;
   // design cycles: each handle's stream -> the batch stream, and back
   std::vector<cudaEvent_t> ev_des;
@@ -385,6 +392,10 @@ struct Batch {
     int64_t kernels = 0;
   };
   DesignGraph g_hier, g_pre, g_post;  // hierarchy; filter+SIMP+hierarchy; sens+compliance+OC
+  // device time of the last graph-launched design cycle's three parts
+  cudaEvent_t ev_ph[4] = {nullptr, nullptr, nullptr, nullptr};
+  double phase_ms[3] = {0.0, 0.0, 0.0};
+  bool have_phases = false;
 };
 
 static void free_shape(Shape& s) {
@@ -476,18 +487,53 @@ static void red_launch_resid(Batch& b) {
   MGAR_LAUNCH_CHECK();
 }
 
-static void iteration(Batch& b, cudaGraphConditionalHandle loop) {
+static void iteration(Batch& b, cudaGraphConditionalHandle loop, int* any_out = nullptr) {
   kb_apply_dot<<<b.s_red.nblocks, kRedThreads, 0, b.stream>>>(b.ddes, b.s_red.bdes, b.s_red.b0,
                                                               b.bsc, b.partials, b.counters);
   MGAR_LAUNCH_CHECK();
   kb_cg_xr<<<b.s_red.nblocks, kRedThreads, 0, b.stream>>>(b.ddes, b.s_red.bdes, b.s_red.b0, b.bsc,
                                                           b.partials, b.counters);
   MGAR_LAUNCH_CHECK();
-  kb_check<<<1, 256, 0, b.stream>>>(b.bsc, b.nd, loop);
+  kb_check<<<1, 256, 0, b.stream>>>(b.bsc, b.nd, loop, any_out);
   MGAR_LAUNCH_CHECK();
   vcycle(b);
   kb_cg_p<<<b.s_red.nblocks, kRedThreads, 0, b.stream>>>(b.ddes, b.s_red.bdes, b.s_red.b0, b.bsc);
   MGAR_LAUNCH_CHECK();
+}
+
+// Per-design scalars, initial residuals, first V-cycle and direction.
+static void prologue(Batch& b) {
+  const int th = 128;
+  kb_init<<<(b.nd + th - 1) / th, th, 0, b.stream>>>(b.bsc, b.consts, b.nd);
+  MGAR_LAUNCH_CHECK();
+  kb_t_to_df<<<b.s_red.nblocks, kRedThreads, 0, b.stream>>>(b.ddes, b.s_red.bdes, b.s_red.b0);
+  MGAR_LAUNCH_CHECK();
+  red_launch_resid(b);
+  kb_start<<<(b.nd + th - 1) / th, th, 0, b.stream>>>(b.bsc, b.nd);
+  MGAR_LAUNCH_CHECK();
+  vcycle(b);
+  kb_cg_p<<<b.s_red.nblocks, kRedThreads, 0, b.stream>>>(b.ddes, b.s_red.bdes, b.s_red.b0, b.bsc);
+  MGAR_LAUNCH_CHECK();
+}
+
+// After the loop: the solutions back to the callers' FP64 vectors.
+static void epilogue(Batch& b) {
+  kb_df_to_t<<<b.s_red.nblocks, kRedThreads, 0, b.stream>>>(b.ddes, b.s_red.bdes, b.s_red.b0);
+  MGAR_LAUNCH_CHECK();
+}
+
+// The solve launched from the host (handles that time kernel classes or run
+// without graphs): the graph's launches in the graph's order, the loop's
+// condition read after each iteration as the WHILE node reads it.
+static void solve_eager(Batch& b) {
+  prologue(b);
+  for (;;) {
+    iteration(b, 0, b.any);
+    MGAR_CUDA(cudaMemcpyAsync(b.hany, b.any, sizeof(int), cudaMemcpyDeviceToHost, b.stream));
+    MGAR_CUDA(cudaStreamSynchronize(b.stream));
+    if (!*b.hany) break;
+  }
+  epilogue(b);
 }
 
 // The solve after the hierarchy builds as one graph: scalars, initial
@@ -504,17 +550,7 @@ static void build_graph(Batch& b) {
     MGAR_CUDA(cudaStreamBeginCaptureToGraph(b.cap, g, nullptr, nullptr, 0,
                                             cudaStreamCaptureModeThreadLocal));
     b.stream = b.cap;
-    const int th = 128;
-    kb_init<<<(b.nd + th - 1) / th, th, 0, b.stream>>>(b.bsc, b.consts, b.nd);
-    MGAR_LAUNCH_CHECK();
-    kb_t_to_df<<<b.s_red.nblocks, kRedThreads, 0, b.stream>>>(b.ddes, b.s_red.bdes, b.s_red.b0);
-    MGAR_LAUNCH_CHECK();
-    red_launch_resid(b);
-    kb_start<<<(b.nd + th - 1) / th, th, 0, b.stream>>>(b.bsc, b.nd);
-    MGAR_LAUNCH_CHECK();
-    vcycle(b);
-    kb_cg_p<<<b.s_red.nblocks, kRedThreads, 0, b.stream>>>(b.ddes, b.s_red.bdes, b.s_red.b0, b.bsc);
-    MGAR_LAUNCH_CHECK();
+    prologue(b);
     cudaStreamCaptureStatus st;
     cudaGraph_t cg = nullptr;
     const cudaGraphNode_t* deps = nullptr;
@@ -531,9 +567,7 @@ static void build_graph(Batch& b) {
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     MGAR_CUDA(cudaStreamUpdateCaptureDependencies(b.stream, &wnode, nullptr, 1,
                                                   cudaStreamSetCaptureDependencies));
-    // after the loop: the solutions back to the callers' FP64 vectors
-    kb_df_to_t<<<b.s_red.nblocks, kRedThreads, 0, b.stream>>>(b.ddes, b.s_red.bdes, b.s_red.b0);
-    MGAR_LAUNCH_CHECK();
+    epilogue(b);
     cudaGraph_t out = nullptr;
     MGAR_CUDA(cudaStreamEndCapture(b.cap, &out));
     b.stream = saved;
@@ -681,6 +715,8 @@ void free_batch(Batch& b) {
   if (b.exec) cudaGraphExecDestroy(b.exec);
   for (Batch::DesignGraph* g : {&b.g_hier, &b.g_pre, &b.g_post})
     if (g->exec) cudaGraphExecDestroy(g->exec);
+  for (cudaEvent_t e : b.ev_ph)
+    if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : b.ev_des) cudaEventDestroy(e);
   if (b.ev_solved) cudaEventDestroy(b.ev_solved);
   if (b.ev_start) cudaEventDestroy(b.ev_start);
@@ -695,6 +731,8 @@ void free_batch(Batch& b) {
   cudaFree(b.consts);
   cudaFree(b.partials);
   cudaFree(b.counters);
+  cudaFree(b.any);
+  if (b.hany) cudaFreeHost(b.hany);
   if (b.hconsts) cudaFreeHost(b.hconsts);
   if (b.hbsc) cudaFreeHost(b.hbsc);
   if (b.cap) cudaStreamDestroy(b.cap);
@@ -832,7 +870,9 @@ void solve_issue(Batch& b, double* const* T) {
     autotune(b);
     build_graph(b);
   }
-  MGAR_CUDA(cudaGraphLaunch(b.exec, b.stream));
+  b.eager = !graphable(b);
+  if (b.eager) solve_eager(b);
+  else MGAR_CUDA(cudaGraphLaunch(b.exec, b.stream));
 }
 
 // Every design's outcome to the host once the batch stream holds all the
@@ -866,7 +906,7 @@ int solve_read(Batch& b, int* iters, double* relres, int* status) {
     // the solution is the handle's new reference
     b.h[d]->have_ref = true;
   }
-  count_launches(b.prologue + (int64_t)maxit * b.body);
+  if (!b.eager) count_launches(b.prologue + (int64_t)maxit * b.body);
   for (int d = 0; d < b.nd; ++d) {
     const int e = (int)b.hbsc[(size_t)d * kBS + BS_DERR];
     if (e) {
@@ -979,11 +1019,14 @@ int mgar_batch_create(mgar_batch_t* out, const mgar_t* handles, int count, void*
     MGAR_CUDA(cudaMalloc(&b->partials, (size_t)std::max(b->s_red.nblocks, 1) * sizeof(double)));
     MGAR_CUDA(cudaMalloc(&b->counters, (size_t)nd * sizeof(unsigned int)));
     MGAR_CUDA(cudaMemset(b->counters, 0, (size_t)nd * sizeof(unsigned int)));
+    MGAR_CUDA(cudaMalloc(&b->any, sizeof(int)));
+    MGAR_CUDA(cudaHostAlloc(&b->hany, sizeof(int), cudaHostAllocDefault));
     b->ev_des.assign(nd, nullptr);
     for (int d = 0; d < nd; ++d)
       MGAR_CUDA(cudaEventCreateWithFlags(&b->ev_des[d], cudaEventDisableTiming));
     MGAR_CUDA(cudaEventCreateWithFlags(&b->ev_solved, cudaEventDisableTiming));
     MGAR_CUDA(cudaEventCreateWithFlags(&b->ev_start, cudaEventDisableTiming));
+    for (cudaEvent_t& e : b->ev_ph) MGAR_CUDA(cudaEventCreate(&e));
   } catch (const Error& e) {
     g_batch_create_error = e.msg;
     free_batch(*b);
@@ -1057,12 +1100,18 @@ int mgar_batch_cycle(mgar_batch_t hb, double* const* rho, double* const* T, cons
       }
       kpost.push_back(key_bits(move));
       order_after_handles(b);
+      MGAR_CUDA(cudaEventRecord(b.ev_ph[0], b.stream));
       launch_design_graph(b, b.g_pre, std::move(kpre), [&](int d, Ctx& c) {
         set_density(c, rho[d], false);
         build_hierarchy(c);
       });
+      MGAR_CUDA(cudaEventRecord(b.ev_ph[1], b.stream));
+      const bool tuning = !b.exec;
       solve_issue(b, T);
+      MGAR_CUDA(cudaEventRecord(b.ev_ph[2], b.stream));
       launch_design_graph(b, b.g_post, std::move(kpost), post);
+      MGAR_CUDA(cudaEventRecord(b.ev_ph[3], b.stream));
+      b.have_phases = !tuning;
     } else {
       // each design's filter and SIMP on its own stream, the hierarchies,
       // the solve, then the updates on the handles' streams again
@@ -1084,6 +1133,12 @@ int mgar_batch_cycle(mgar_batch_t hb, double* const* rho, double* const* T, cons
       }
     }
     gather_outcomes(b);
+    if (b.have_phases)
+      for (int k = 0; k < 3; ++k) {
+        float ms = 0.f;
+        MGAR_CUDA(cudaEventElapsedTime(&ms, b.ev_ph[k], b.ev_ph[k + 1]));
+        b.phase_ms[k] = ms;
+      }
     std::vector<int> it(nd), st(nd);
     std::vector<double> rr(nd);
     const int rc = solve_read(b, it.data(), rr.data(), st.data());
@@ -1117,8 +1172,17 @@ int mgar_batch_cycle(mgar_batch_t hb, double* const* rho, double* const* T, cons
 int mgar_batch_report(mgar_batch_t hb, char* buf, int64_t len) {
   return bguard(hb, [&](Batch& b) {
     require(buf && len > 0, MGAR_ERR_ARG, "batch_report: bad buffer");
-    const size_t n = std::min<size_t>((size_t)len - 1, b.report.size());
-    std::memcpy(buf, b.report.data(), n);
+    std::string r = b.report;
+    if (b.have_phases) {
+      char line[256];
+      std::snprintf(line, sizeof line,
+                    "last design cycle, device ms: filter+SIMP+hierarchy %.3f, solve %.3f, "
+                    "sensitivities+OC %.3f\n",
+                    b.phase_ms[0], b.phase_ms[1], b.phase_ms[2]);
+      r += line;
+    }
+    const size_t n = std::min<size_t>((size_t)len - 1, r.size());
+    std::memcpy(buf, r.data(), n);
     buf[n] = 0;
     return MGAR_OK;
   });

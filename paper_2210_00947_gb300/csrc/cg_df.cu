@@ -21,18 +21,19 @@ namespace mgar {
 
 namespace {
 
-// y = A x; with DOT, x.y into out (per-thread df sums, FP64 across threads)
+// y = A x; with DOT, x.y into out (warp sums in df64, FP64 across warps and
+// blocks)
 template <int DIM, bool DOT>
 __global__ void k_df_apply(DfOp op, const float2* __restrict__ x, float2* __restrict__ y,
                            double* partials, unsigned int* counter, double* out) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  double v[1] = {0.0};
+  df v{0.f, 0.f};
   if (idx < op.n) {
     const df yv = df_row<DIM>(op, x, idx);
     y[idx] = pack(yv);
-    if (DOT) v[0] = df_to_double(df_mul(unpack(x[idx]), yv));
+    if (DOT) v = df_mul(unpack(x[idx]), yv);
   }
-  if (DOT) block_sum_finish<1>(v, partials, counter, out);
+  if (DOT) block_sum_finish_df(v, partials, counter, out);
 }
 
 // r = q - A x and ||r||^2
@@ -41,13 +42,13 @@ __global__ void k_df_residual(DfOp op, const float2* __restrict__ q, const float
                               float2* __restrict__ r, double* partials, unsigned int* counter,
                               double* out) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  double v[1] = {0.0};
+  df v{0.f, 0.f};
   if (idx < op.n) {
     const df ri = df_sub(unpack(q[idx]), df_row<DIM>(op, x, idx));
     r[idx] = pack(ri);
-    v[0] = df_to_double(df_mul(ri, ri));
+    v = df_mul(ri, ri);
   }
-  block_sum_finish<1>(v, partials, counter, out);
+  block_sum_finish_df(v, partials, counter, out);
 }
 
 // alpha = rz / pAp; x += alpha p; r -= alpha Ap; ||r||^2; optionally the
