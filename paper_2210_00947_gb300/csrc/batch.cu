@@ -84,6 +84,24 @@ struct Shape {
 
 __device__ __forceinline__ bool active(const double* bsc, int d) { return bsc[d * kBS + BS_ACT] != 0.0; }
 
+// Nodes per thread of the level-0 launches: a thread takes nodes base,
+// base + blockDim.x, ... of its design, so each block's lookups (its design,
+// the design's tables and scalars) serve several nodes and each thread has
+// several independent loads in flight.
+constexpr int kNpt0 = 4;  // V-cycle node kernels at level 0
+constexpr int kNptR = 2;  // CG kernels (double-float vectors, reductions)
+
+// The first node of this thread in its design, for npt nodes per thread.
+__device__ __forceinline__ int node_base(const int* b0, int d, int npt) {
+  return (blockIdx.x - b0[d]) * blockDim.x * npt + threadIdx.x;
+}
+
+// The number of blocks of design d's launch over n nodes.
+__device__ __forceinline__ int design_blocks(int n, int npt) {
+  const int per = blockDim.x * npt;
+  return (n + per - 1) / per;
+}
+
 // Deterministic per-design sum of one double-float value per thread: the
 // design's blocks write partials, its last block adds them in block order
 // into *out.  Warp sums in df64 on the FP32 pipe, FP64 only across warps and
@@ -120,16 +138,24 @@ __global__ void kb_init(double* bsc, const double* consts, int nd) {
 __global__ void kb_t_to_df(const Des* D, const int* bdes, const int* b0) {
   const int d = bdes[blockIdx.x];
   const Des& g = D[d];
-  const int idx = (blockIdx.x - b0[d]) * blockDim.x + threadIdx.x;
-  if (idx < g.f.n) g.x[idx] = pack(df_from_double(g.T[idx]));
+  const int base = node_base(b0, d, kNptR);
+#pragma unroll
+  for (int u = 0; u < kNptR; ++u) {
+    const int idx = base + u * blockDim.x;
+    if (idx < g.f.n) g.x[idx] = pack(df_from_double(g.T[idx]));
+  }
 }
 
 // T = x (the end of each design's CG)
 __global__ void kb_df_to_t(const Des* D, const int* bdes, const int* b0) {
   const int d = bdes[blockIdx.x];
   const Des& g = D[d];
-  const int idx = (blockIdx.x - b0[d]) * blockDim.x + threadIdx.x;
-  if (idx < g.f.n) g.T[idx] = df_to_double(unpack(g.x[idx]));
+  const int base = node_base(b0, d, kNptR);
+#pragma unroll
+  for (int u = 0; u < kNptR; ++u) {
+    const int idx = base + u * blockDim.x;
+    if (idx < g.f.n) g.T[idx] = df_to_double(unpack(g.x[idx]));
+  }
 }
 
 // Each handle's compliance, OC outcome and factorisation flag into the
@@ -151,16 +177,20 @@ __global__ void kb_resid64(const Des* D, const int* bdes, const int* b0, double*
                            double* partials, unsigned int* counters) {
   const int d = bdes[blockIdx.x];
   const Des& g = D[d];
-  const int nb = (g.f.n + blockDim.x - 1) / blockDim.x;
-  const int idx = (blockIdx.x - b0[d]) * blockDim.x + threadIdx.x;
+  const int base = node_base(b0, d, kNptR);
   df v{0.f, 0.f};
-  if (idx < g.f.n) {
-    const df ri = df_sub(unpack(g.q[idx]), df_row<2>(g.f, g.x, idx));
-    g.r[idx] = pack(ri);
-    g.b32[idx] = __fadd_rn(ri.hi, ri.lo);
-    v = df_mul(ri, ri);
+#pragma unroll
+  for (int u = 0; u < kNptR; ++u) {
+    const int idx = base + u * blockDim.x;
+    if (idx < g.f.n) {
+      const df ri = df_sub(unpack(g.q[idx]), df_row<2>(g.f, g.x, idx));
+      g.r[idx] = pack(ri);
+      g.b32[idx] = __fadd_rn(ri.hi, ri.lo);
+      v = df_add(v, df_mul(ri, ri));
+    }
   }
-  seg_finish_df(v, partials, counters, d, b0[d], nb, bsc + d * kBS + BS_RR);
+  seg_finish_df(v, partials, counters, d, b0[d], design_blocks(g.f.n, kNptR),
+                bsc + d * kBS + BS_RR);
 }
 
 // After the initial residual: a design whose start already meets eps2 (or
@@ -180,15 +210,19 @@ __global__ void kb_apply_dot(const Des* D, const int* bdes, const int* b0, doubl
   const int d = bdes[blockIdx.x];
   if (!active(bsc, d)) return;
   const Des& g = D[d];
-  const int nb = (g.f.n + blockDim.x - 1) / blockDim.x;
-  const int idx = (blockIdx.x - b0[d]) * blockDim.x + threadIdx.x;
+  const int base = node_base(b0, d, kNptR);
   df v{0.f, 0.f};
-  if (idx < g.f.n) {
-    const df ap = df_row<2>(g.f, g.p, idx);
-    g.Ap[idx] = pack(ap);
-    v = df_mul(unpack(g.p[idx]), ap);
+#pragma unroll
+  for (int u = 0; u < kNptR; ++u) {
+    const int idx = base + u * blockDim.x;
+    if (idx < g.f.n) {
+      const df ap = df_row<2>(g.f, g.p, idx);
+      g.Ap[idx] = pack(ap);
+      v = df_add(v, df_mul(unpack(g.p[idx]), ap));
+    }
   }
-  seg_finish_df(v, partials, counters, d, b0[d], nb, bsc + d * kBS + BS_PAP);
+  seg_finish_df(v, partials, counters, d, b0[d], design_blocks(g.f.n, kNptR),
+                bsc + d * kBS + BS_PAP);
 }
 
 // alpha = r.z / p.Ap; x += alpha p; r -= alpha Ap; ||r||^2; FP32 copy of r.
@@ -200,17 +234,33 @@ __global__ void kb_cg_xr(const Des* D, const int* bdes, const int* b0, double* b
   const double* s = bsc + d * kBS;
   const int par = ((int)s[BS_IT]) & 1;
   const df alpha = block_div_df(s + BS_RZ + par, s + BS_PAP);
-  const int nb = (g.f.n + blockDim.x - 1) / blockDim.x;
-  const int idx = (blockIdx.x - b0[d]) * blockDim.x + threadIdx.x;
-  df v{0.f, 0.f};
-  if (idx < g.f.n) {
-    g.x[idx] = pack(df_add(unpack(g.x[idx]), df_mul(alpha, unpack(g.p[idx]))));
-    const df ri = df_sub(unpack(g.r[idx]), df_mul(alpha, unpack(g.Ap[idx])));
-    g.r[idx] = pack(ri);
-    g.b32[idx] = __fadd_rn(ri.hi, ri.lo);
-    v = df_mul(ri, ri);
+  const int base = node_base(b0, d, kNptR);
+  // every node's four loads first, then the updates
+  float2 xv[kNptR], pv[kNptR], rv[kNptR], qv[kNptR];
+#pragma unroll
+  for (int u = 0; u < kNptR; ++u) {
+    const int idx = base + u * blockDim.x;
+    if (idx < g.f.n) {
+      xv[u] = g.x[idx];
+      pv[u] = g.p[idx];
+      rv[u] = g.r[idx];
+      qv[u] = g.Ap[idx];
+    }
   }
-  seg_finish_df(v, partials, counters, d, b0[d], nb, bsc + d * kBS + BS_RR);
+  df v{0.f, 0.f};
+#pragma unroll
+  for (int u = 0; u < kNptR; ++u) {
+    const int idx = base + u * blockDim.x;
+    if (idx < g.f.n) {
+      g.x[idx] = pack(df_add(unpack(xv[u]), df_mul(alpha, unpack(pv[u]))));
+      const df ri = df_sub(unpack(rv[u]), df_mul(alpha, unpack(qv[u])));
+      g.r[idx] = pack(ri);
+      g.b32[idx] = __fadd_rn(ri.hi, ri.lo);
+      v = df_add(v, df_mul(ri, ri));
+    }
+  }
+  seg_finish_df(v, partials, counters, d, b0[d], design_blocks(g.f.n, kNptR),
+                bsc + d * kBS + BS_RR);
 }
 
 // One iteration done: count it and decide, per design, whether to go on;
@@ -247,10 +297,24 @@ __global__ void kb_cg_p(const Des* D, const int* bdes, const int* b0, const doub
   const int it = (int)s[BS_IT];
   const df beta = it == 0 ? df{0.f, 0.f}
                           : block_div_df(s + BS_RZ + (it & 1), s + BS_RZ + ((it - 1) & 1));
-  const int idx = (blockIdx.x - b0[d]) * blockDim.x + threadIdx.x;
-  if (idx < g.f.n) {
-    const df z{g.x32[idx], 0.f};
-    g.p[idx] = pack(it == 0 ? z : df_add(z, df_mul(beta, unpack(g.p[idx]))));
+  const int base = node_base(b0, d, kNptR);
+  float zv[kNptR];
+  float2 pv[kNptR];
+#pragma unroll
+  for (int u = 0; u < kNptR; ++u) {
+    const int idx = base + u * blockDim.x;
+    if (idx < g.f.n) {
+      zv[u] = g.x32[idx];
+      pv[u] = g.p[idx];
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kNptR; ++u) {
+    const int idx = base + u * blockDim.x;
+    if (idx < g.f.n) {
+      const df z{zv[u], 0.f};
+      g.p[idx] = pack(it == 0 ? z : df_add(z, df_mul(beta, unpack(pv[u]))));
+    }
   }
 }
 
@@ -266,22 +330,42 @@ __device__ __forceinline__ bool lev_node(const int* bdes, const int* b0, const d
 
 // level 0, zero initial guess: t = w D^-1 b
 __global__ void kb_jz0(const Lev* L, const int* bdes, const int* b0, const double* bsc) {
-  int d, idx;
-  if (!lev_node(bdes, b0, bsc, d, idx)) return;
+  const int d = bdes[blockIdx.x];
+  if (!active(bsc, d)) return;
   const Lev& v = L[d];
-  if (idx < v.d.n) v.t[idx] = v.omega * v.dinv[idx] * v.b[idx];
+  const int base = node_base(b0, d, kNpt0);
+  float dv[kNpt0], bv[kNpt0];
+#pragma unroll
+  for (int u = 0; u < kNpt0; ++u) {
+    const int idx = base + u * blockDim.x;
+    if (idx < v.d.n) {
+      dv[u] = v.dinv[idx];
+      bv[u] = v.b[idx];
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kNpt0; ++u) {
+    const int idx = base + u * blockDim.x;
+    if (idx < v.d.n) v.t[idx] = v.omega * dv[u] * bv[u];
+  }
 }
 
 // level 0: r = b - A t (matrix-free FP32 operator)
 __global__ void kb_resid0(const Lev* L, const int* bdes, const int* b0, const double* bsc) {
-  int d, idx;
-  if (!lev_node(bdes, b0, bsc, d, idx)) return;
+  const int d = bdes[blockIdx.x];
+  if (!active(bsc, d)) return;
   const Lev& v = L[d];
-  if (idx >= v.d.n) return;
-  int i, j, k;
-  coords(idx, v.f0.fNX, v.f0.fNXY, i, j, k);
-  float diag;
-  v.r[idx] = v.b[idx] - fine_row2(v.f0, v.t, i, j, diag);
+  const int base = node_base(b0, d, kNpt0);
+#pragma unroll
+  for (int u = 0; u < kNpt0; ++u) {
+    const int idx = base + u * blockDim.x;
+    if (idx < v.d.n) {
+      int i, j, k;
+      coords(idx, v.f0.fNX, v.f0.fNXY, i, j, k);
+      float diag;
+      v.r[idx] = v.b[idx] - fine_row2(v.f0, v.t, i, j, diag);
+    }
+  }
 }
 
 // b_next = P^T r (fixed fine nodes excluded at level 0), and the next level's
@@ -323,10 +407,15 @@ __global__ void kb_post(const Lev* L, const int* bdes, const int* b0, const doub
 
 // level 0: t += P res_1 (fixed nodes keep t)
 __global__ void kb_prolong0(const Lev* L, const int* bdes, const int* b0, const double* bsc) {
-  int d, idx;
-  if (!lev_node(bdes, b0, bsc, d, idx)) return;
+  const int d = bdes[blockIdx.x];
+  if (!active(bsc, d)) return;
   const Lev& v = L[d];
-  if (idx < v.d.n) prolong_node<float, 2>(v.resn, v.t, v.t, v.d, v.dn, v.fixed, idx);
+  const int base = node_base(b0, d, kNpt0);
+#pragma unroll
+  for (int u = 0; u < kNpt0; ++u) {
+    const int idx = base + u * blockDim.x;
+    if (idx < v.d.n) prolong_node<float, 2>(v.resn, v.t, v.t, v.d, v.dn, v.fixed, idx);
+  }
 }
 
 // level 0: x = t + w D^-1 (b - A t), z = x in FP64 and r . z (the CG's new
@@ -337,20 +426,24 @@ __global__ void kb_sweep0(const Lev* L, const Des* D, const int* bdes, const int
   if (!active(bsc, d)) return;
   const Lev& v = L[d];
   const Des& g = D[d];
-  const int nb = (v.d.n + blockDim.x - 1) / blockDim.x;
-  const int idx = (blockIdx.x - b0[d]) * blockDim.x + threadIdx.x;
+  const int base = node_base(b0, d, kNptR);
   df s{0.f, 0.f};
-  if (idx < v.d.n) {
-    int i, j, k;
-    coords(idx, v.f0.fNX, v.f0.fNXY, i, j, k);
-    float diag;
-    const float ti = v.t[idx];
-    const float xo = ti + v.omega * v.dinv[idx] * (v.b[idx] - fine_row2(v.f0, v.t, i, j, diag));
-    v.x[idx] = xo;
-    s = df_mulf(unpack(g.r[idx]), xo);
+#pragma unroll
+  for (int u = 0; u < kNptR; ++u) {
+    const int idx = base + u * blockDim.x;
+    if (idx < v.d.n) {
+      int i, j, k;
+      coords(idx, v.f0.fNX, v.f0.fNXY, i, j, k);
+      float diag;
+      const float ti = v.t[idx];
+      const float xo = ti + v.omega * v.dinv[idx] * (v.b[idx] - fine_row2(v.f0, v.t, i, j, diag));
+      v.x[idx] = xo;
+      s = df_add(s, df_mulf(unpack(g.r[idx]), xo));
+    }
   }
   const int par = ((int)bsc[d * kBS + BS_IT]) & 1;
-  seg_finish_df(s, partials, counters, d, b0[d], nb, bsc + d * kBS + BS_RZ + par);
+  seg_finish_df(s, partials, counters, d, b0[d], design_blocks(v.d.n, kNptR),
+                bsc + d * kBS + BS_RZ + par);
 }
 
 // ------------------------------------------------------------------- host
@@ -439,7 +532,7 @@ static std::vector<int64_t> level_units(const Batch& b, int l, bool next) {
 static void make_level_shapes(Batch& b, int l, int threads) {
   free_shape(b.s_node[l]);
   free_shape(b.s_next[l]);
-  b.s_node[l] = make_shape(level_units(b, l, false), threads, threads);
+  b.s_node[l] = make_shape(level_units(b, l, false), threads * (l == 0 ? kNpt0 : 1), threads);
   b.s_next[l] = make_shape(level_units(b, l, true), threads, threads);
 }
 
@@ -1008,7 +1101,7 @@ int mgar_batch_create(mgar_batch_t* out, const mgar_t* handles, int count, void*
     MGAR_CUDA(cudaMalloc(&b->ddes, des.size() * sizeof(Des)));
     MGAR_CUDA(cudaMemcpy(b->ddes, des.data(), des.size() * sizeof(Des), cudaMemcpyHostToDevice));
     b->hdes = des;
-    b->s_red = make_shape(n0, kRedThreads, kRedThreads);
+    b->s_red = make_shape(n0, kRedThreads * kNptR, kRedThreads);
     for (int l = 0; l + 1 < lmax; ++l) make_level_shapes(*b, l, 256);
     make_coarse_shape(*b, 8);
     MGAR_CUDA(cudaMalloc(&b->bsc, (size_t)nd * kBS * sizeof(double)));
