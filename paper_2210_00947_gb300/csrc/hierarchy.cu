@@ -588,6 +588,155 @@ __global__ void k_band_inverse_df(const double* __restrict__ gband_d,
   for (int i = lane; i < n; i += 32) inv[(int64_t)i * n + col] = df_to_double(df_ld(colbuf + i));
 }
 
+// Band widths below one warp (every coarsest level the V-cycles build here:
+// 5^3 nodes in 3D, up to 17^2 in 2D): the same factorisation and inverse,
+// the same df64 operations on every entry in the same order (bit-identical
+// results), with shorter dependency chains.
+constexpr int kWinBw = 32;
+
+// The pivot of column k: sqrt(A(k,k)) into the band, 1/sqrt into rdiag and
+// *rp; *bad set when A(k,k) is not positive.
+__device__ __forceinline__ void chol_pivot_df(float2* band, float2* rdiag, int k, int ld, int bw,
+                                              float2* rp, int* bad) {
+  const df a = df_ld(band + (int64_t)k * ld + bw);
+  if (!(a.hi > 0.f) || !isfinite(a.hi)) *bad = 1;
+  const df r = df_rsqrt(a);
+  *rp = make_float2(r.hi, r.lo);
+  df_st(band + (int64_t)k * ld + bw, df_mul(a, r));
+  df_st(rdiag + k, r);
+}
+
+// Right-looking band Cholesky for bw < 32, one barrier per column: warp w
+// takes row i = k+1+w of column k's rank-1 update (lane l the entry j =
+// k+1+l <= i), scaling A(i,k) and A(j,k) by the pivot as it reads them; the
+// scaled column is stored after the barrier, when no thread reads the
+// unscaled one any more.  The first lane of warp 0, which updates A(k+1,k+1),
+// computes the next pivot at once (double-buffered pivot and flag), so the
+// pivot's rsqrt chain overlaps the other rows' updates.
+__global__ void __launch_bounds__(kCholThreads) k_band_cholesky_df_win(double* __restrict__ gband,
+                                                                       double* __restrict__ grdiag,
+                                                                       int n, int bw,
+                                                                       int* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* band = reinterpret_cast<float2*>(smraw);
+  float2* out = reinterpret_cast<float2*>(gband);  // same bytes, df64 pairs
+  float2* rdiag = reinterpret_cast<float2*>(grdiag);
+  __shared__ float2 rpiv[2];
+  __shared__ int bad[2];
+  const int ld = bw + 1;
+  const int64_t size = (int64_t)n * ld;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int64_t t = tid; t < size; t += blockDim.x) {
+    const df v = df_from_double(gband[t]);
+    band[t] = make_float2(v.hi, v.lo);
+  }
+  if (tid == 0) bad[0] = bad[1] = 0;
+  __syncthreads();
+  if (tid == 0) chol_pivot_df(band, rdiag, 0, ld, bw, &rpiv[0], &bad[0]);
+  __syncthreads();
+  df lprev{0.f, 0.f};  // lane 0 of warp w: L(i, k-1) of its row in the last column
+  int64_t aprev = -1;
+  for (int k = 0; k < n; ++k) {
+    if (bad[k & 1]) break;
+    const df rp{rpiv[k & 1].x, rpiv[k & 1].y};
+    if (aprev >= 0) {
+      df_st(band + aprev, lprev);
+      aprev = -1;
+    }
+    const int m = min(k + bw, n - 1) - k;
+    if (warp < m) {
+      const int i = k + 1 + warp;
+      const int64_t ai = (int64_t)i * ld + (k - i + bw);  // A(i, k)
+      const df lik = df_mul(df_ld(band + ai), rp);
+      if (lane <= warp) {
+        const int j = k + 1 + lane;
+        const int64_t at = (int64_t)i * ld + (j - i + bw);
+        const df ljk = df_mul(df_ld(band + (int64_t)j * ld + (k - j + bw)), rp);
+        df_st(band + at, df_sub(df_ld(band + at), df_mul(lik, ljk)));
+      }
+      if (lane == 0) {
+        lprev = lik;
+        aprev = ai;
+        if (warp == 0)
+          chol_pivot_df(band, rdiag, k + 1, ld, bw, &rpiv[(k + 1) & 1], &bad[(k + 1) & 1]);
+      }
+    }
+    __syncthreads();
+  }
+  if (aprev >= 0) df_st(band + aprev, lprev);
+  __syncthreads();
+  for (int64_t t = tid; t < size; t += blockDim.x) out[t] = band[t];
+  if (tid == 0 && (bad[0] || bad[1])) *err = MGAR_ERR_NOT_SPD;
+}
+
+// Columns of the inverse for bw < 32, one warp per column, the unknowns of
+// the substitutions in registers: lane l holds the row r = l (mod 32) of the
+// bw + 1 rows the current step touches, receives the step's solved value by
+// shuffle and takes row r + 32 (forward) or r - 32 (backward) once its own
+// row is solved, so no step waits on shared memory.
+__global__ void k_band_inverse_df_win(const double* __restrict__ gband_d,
+                                      const double* __restrict__ grdiag_d, int n, int bw,
+                                      double* __restrict__ inv) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const float2* gband = reinterpret_cast<const float2*>(gband_d);
+  const float2* rdiag = reinterpret_cast<const float2*>(grdiag_d);
+  float2* sband = reinterpret_cast<float2*>(smraw);
+  const int ld = bw + 1;
+  const int64_t size = (int64_t)n * ld;
+  const int warps = blockDim.x >> 5;
+  const int wid = threadIdx.x >> 5;
+  for (int64_t t = threadIdx.x; t < size; t += blockDim.x) sband[t] = gband[t];
+  __syncthreads();
+  float2* colbuf = sband + size + (int64_t)wid * n;  // the forward solution y
+  const int col = blockIdx.x * warps + wid;
+  const int lane = threadIdx.x & 31;
+  if (col >= n) return;
+  for (int i = lane; i < col; i += 32) colbuf[i] = make_float2(0.f, 0.f);
+  // forward: L y = e_col (y_p = 0 for p < col)
+  int r = col + ((lane - col) & 31);
+  df y = r == col ? df{1.f, 0.f} : df{0.f, 0.f};
+  for (int p = col; p < n; ++p) {
+    const int owner = p & 31;
+    const bool upd = r > p && r <= p + bw && r < n;
+    df lrp{0.f, 0.f};
+    if (upd) lrp = df_ld(sband + (int64_t)r * ld + (p - r + bw));  // L(r, p)
+    df yp{0.f, 0.f};
+    if (lane == owner) {
+      yp = df_mul(y, df_ld(rdiag + p));
+      df_st(colbuf + p, yp);
+    }
+    yp.hi = __shfl_sync(0xffffffffu, yp.hi, owner);
+    yp.lo = __shfl_sync(0xffffffffu, yp.lo, owner);
+    if (upd) y = df_sub(y, df_mul(lrp, yp));
+    if (lane == owner) {
+      r = p + 32;
+      y = df{0.f, 0.f};
+    }
+  }
+  __syncwarp();
+  // backward: L^T x = y
+  r = (n - 1) - ((n - 1 - lane) & 31);
+  y = r >= 0 ? df_ld(colbuf + r) : df{0.f, 0.f};
+  for (int i = n - 1; i >= 0; --i) {
+    const int owner = i & 31;
+    const bool upd = r >= 0 && r < i && r >= i - bw;
+    df lir{0.f, 0.f};
+    if (upd) lir = df_ld(sband + (int64_t)i * ld + (r - i + bw));  // L(i, r)
+    df xi{0.f, 0.f};
+    if (lane == owner) {
+      xi = df_mul(y, df_ld(rdiag + i));
+      inv[(int64_t)i * n + col] = df_to_double(xi);
+    }
+    xi.hi = __shfl_sync(0xffffffffu, xi.hi, owner);
+    xi.lo = __shfl_sync(0xffffffffu, xi.lo, owner);
+    if (upd) y = df_sub(y, df_mul(lir, xi));
+    if (lane == owner) {
+      r = i - 32;
+      y = r >= 0 ? df_ld(colbuf + r) : df{0.f, 0.f};
+    }
+  }
+}
+
 __global__ void k_d2f(const double* a, float* b, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
@@ -646,6 +795,10 @@ void alloc_hierarchy(Ctx& c) {
   MGAR_CUDA(cudaFuncSetAttribute(k_band_cholesky_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kBandSmemMax));
   MGAR_CUDA(cudaFuncSetAttribute(k_band_inverse_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kBandSmemMax));
+  MGAR_CUDA(cudaFuncSetAttribute(k_band_cholesky_df_win, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kBandSmemMax));
+  MGAR_CUDA(cudaFuncSetAttribute(k_band_inverse_df_win, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kBandSmemMax));
   // constant tables: k0 (nen^2) then G (3^dim * nen^2)
   const int nen = c.nen, ntypes = c.dim == 2 ? 9 : 27;
@@ -733,13 +886,22 @@ static void coarse_factor(Ctx& c, const Real* st, const Dims& dcst) {
   // the FP32 V-cycle's coarsest factor and inverse in df64 on the FP32 pipe
   // (same band bytes: a df64 pair is the size of a double)
   if (sizeof(Real) == 4 && sizeof(B) == 8 && smem && inv_smem <= kBandSmemMax && c.df_coarse) {
-    k_band_cholesky_df<<<1, kCholThreads, band_bytes, s>>>((double*)band, (double*)rdiag, c.nc,
-                                                           c.bw, c.derr);
-    MGAR_LAUNCH_CHECK();
-    k_band_inverse_df<<<(c.nc + 7) / 8, 256, inv_smem, s>>>((const double*)band,
-                                                           (const double*)rdiag, c.nc, c.bw,
-                                                           (double*)inv);
-    MGAR_LAUNCH_CHECK();
+    if (c.bw < kWinBw) {
+      k_band_cholesky_df_win<<<1, 32 * std::max(c.bw, 1), band_bytes, s>>>(
+          (double*)band, (double*)rdiag, c.nc, c.bw, c.derr);
+      MGAR_LAUNCH_CHECK();
+      k_band_inverse_df_win<<<(c.nc + 7) / 8, 256, inv_smem, s>>>(
+          (const double*)band, (const double*)rdiag, c.nc, c.bw, (double*)inv);
+      MGAR_LAUNCH_CHECK();
+    } else {
+      k_band_cholesky_df<<<1, kCholThreads, band_bytes, s>>>((double*)band, (double*)rdiag, c.nc,
+                                                             c.bw, c.derr);
+      MGAR_LAUNCH_CHECK();
+      k_band_inverse_df<<<(c.nc + 7) / 8, 256, inv_smem, s>>>((const double*)band,
+                                                             (const double*)rdiag, c.nc, c.bw,
+                                                             (double*)inv);
+      MGAR_LAUNCH_CHECK();
+    }
     if (c.side_stream) {
       MGAR_CUDA(cudaEventRecord(c.ev_join, s));
       c.coarse_pending = true;
