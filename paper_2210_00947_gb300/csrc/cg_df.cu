@@ -22,18 +22,32 @@ namespace mgar {
 namespace {
 
 // y = A x; with DOT, x.y into out (warp sums in df64, FP64 across warps and
-// blocks)
-template <int DIM, bool DOT>
+// blocks).  NPT nodes per thread: base, base + blockDim.x, ...
+template <int DIM, bool DOT, int NPT = 1>
 __global__ void k_df_apply(DfOp op, const float2* __restrict__ x, float2* __restrict__ y,
                            double* partials, unsigned int* counter, double* out) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int base = blockIdx.x * blockDim.x * NPT + threadIdx.x;
   df v{0.f, 0.f};
-  if (idx < op.n) {
-    const df yv = df_row<DIM>(op, x, idx);
-    y[idx] = pack(yv);
-    if (DOT) v = df_mul(unpack(x[idx]), yv);
+#pragma unroll
+  for (int u = 0; u < NPT; ++u) {
+    const int idx = base + u * blockDim.x;
+    if (idx < op.n) {
+      const df yv = df_row<DIM>(op, x, idx);
+      y[idx] = pack(yv);
+      if (DOT) v = df_add(v, df_mul(unpack(x[idx]), yv));
+    }
   }
   if (DOT) block_sum_finish_df(v, partials, counter, out);
+}
+
+// The 2D product with p . Ap, two nodes per thread.
+constexpr int kNptApply2 = 2;
+
+void df_apply2_dot(const DfOp& op, const float2* x, float2* y, double* partials,
+                   unsigned int* counter, double* out, cudaStream_t s) {
+  const int per = kThreads * kNptApply2;
+  k_df_apply<2, true, kNptApply2><<<(op.n + per - 1) / per, kThreads, 0, s>>>(op, x, y, partials,
+                                                                             counter, out);
 }
 
 // r = q - A x and ||r||^2
@@ -246,16 +260,21 @@ static void cg_iteration_2d(Ctx& c, bool first, cudaGraphConditionalHandle loop)
     k_df_to_f32<<<blocks_for(n), kThreads, 0, c.stream>>>(c.df_r, c.b32, n);
     MGAR_LAUNCH_CHECK();
   }
-  vcycle<float>(c, c.b32, c.x32, true);
-  k_df_dot_f<<<rb, kThreads, 0, c.stream>>>(c.df_r, c.x32, n, c.partials, c.counter, c.dsc + S_RZ1);
-  MGAR_LAUNCH_CHECK();
+  if (vcycle_dot_ok(c)) {
+    // r . z fused into the V-cycle's last sweep
+    vcycle_dot(c, c.b32, c.x32, c.df_r, c.dsc + S_RZ1);
+  } else {
+    vcycle<float>(c, c.b32, c.x32, true);
+    k_df_dot_f<<<rb, kThreads, 0, c.stream>>>(c.df_r, c.x32, n, c.partials, c.counter,
+                                              c.dsc + S_RZ1);
+    MGAR_LAUNCH_CHECK();
+  }
   if (first)
     k_f32_to_df<<<blocks_for(n), kThreads, 0, c.stream>>>(c.x32, c.df_p, n);
   else
     k_df_cg_p<<<rb, kThreads, 0, c.stream>>>(c.df_p, c.x32, n, c.dsc + S_RZ1, c.dsc + S_RZ0);
   MGAR_LAUNCH_CHECK();
-  k_df_apply<2, true><<<blocks_for(n), kThreads, 0, c.stream>>>(op, c.df_p, c.df_Ap, c.partials,
-                                                                c.counter, c.dsc + S_PAP);
+  df_apply2_dot(op, c.df_p, c.df_Ap, c.partials, c.counter, c.dsc + S_PAP, c.stream);
   MGAR_LAUNCH_CHECK();
   k_df_cg_xr<<<rb, kThreads, 0, c.stream>>>(c.df_x, c.df_r, c.df_p, c.df_Ap, n, c.dsc + S_RZ1,
                                             c.dsc + S_PAP, c.partials, c.counter, c.dsc + S_RR,
@@ -799,18 +818,26 @@ int solve_mgcg_df(Ctx& c, double* T, int* iters, double* relres) {
     require(std::isfinite(rel), MGAR_ERR_NONFINITE, "CG breakdown (non-finite residual)");
   } else if (!(rel <= c.p.eps2)) {
     require(std::isfinite(rel), MGAR_ERR_NONFINITE, "non-finite initial residual");
-    precondition_df(c);
+    // 2D with the fused V-cycle: the FP32 copy of r comes from the update of x
+    // and r, and r . z from the V-cycle's last sweep (the graph's arithmetic)
+    const bool fused = c.dim == 2 && vcycle_dot_ok(c);
     int a = S_RZ0, b = S_RZ1;
-    k_df_dot_f<<<rb, kThreads, 0, c.stream>>>(c.df_r, c.x32, n, c.partials, c.counter, c.dsc + a);
-    MGAR_LAUNCH_CHECK();
+    if (fused) {
+      k_df_to_f32<<<blocks_for(n), kThreads, 0, c.stream>>>(c.df_r, c.b32, n);
+      MGAR_LAUNCH_CHECK();
+      precondition_f32(c, a);
+    } else {
+      precondition_df(c);
+      k_df_dot_f<<<rb, kThreads, 0, c.stream>>>(c.df_r, c.x32, n, c.partials, c.counter, c.dsc + a);
+      MGAR_LAUNCH_CHECK();
+    }
     k_f32_to_df<<<blocks_for(n), kThreads, 0, c.stream>>>(c.x32, c.df_p, n);
     MGAR_LAUNCH_CHECK();
     while (it < c.p.cg_max) {
       {
         ProfScope ps(c, MGAR_KC_APPLY64);
         if (c.dim == 2)
-          k_df_apply<2, true><<<blocks_for(n), kThreads, 0, c.stream>>>(
-              op, c.df_p, c.df_Ap, c.partials, c.counter, c.dsc + S_PAP);
+          df_apply2_dot(op, c.df_p, c.df_Ap, c.partials, c.counter, c.dsc + S_PAP, c.stream);
         else
           k_df_apply<3, true><<<blocks_for(n), kThreads, 0, c.stream>>>(
               op, c.df_p, c.df_Ap, c.partials, c.counter, c.dsc + S_PAP);
@@ -818,16 +845,21 @@ int solve_mgcg_df(Ctx& c, double* T, int* iters, double* relres) {
       }
       k_df_cg_xr<<<rb, kThreads, 0, c.stream>>>(c.df_x, c.df_r, c.df_p, c.df_Ap, n, c.dsc + a,
                                                 c.dsc + S_PAP, c.partials, c.counter, c.dsc + S_RR,
-                                                nullptr);
+                                                fused ? c.b32 : nullptr);
       MGAR_LAUNCH_CHECK();
       ++it;
       fetch_scalars(c, S_RR, 1);
       rel = std::sqrt(c.hsc[S_RR]) / c.qnorm;
       require(std::isfinite(rel), MGAR_ERR_NONFINITE, "CG breakdown (non-finite residual)");
       if (rel <= c.p.eps2) break;
-      precondition_df(c);
-      k_df_dot_f<<<rb, kThreads, 0, c.stream>>>(c.df_r, c.x32, n, c.partials, c.counter, c.dsc + b);
-      MGAR_LAUNCH_CHECK();
+      if (fused) {
+        precondition_f32(c, b);
+      } else {
+        precondition_df(c);
+        k_df_dot_f<<<rb, kThreads, 0, c.stream>>>(c.df_r, c.x32, n, c.partials, c.counter,
+                                                  c.dsc + b);
+        MGAR_LAUNCH_CHECK();
+      }
       k_df_cg_p<<<rb, kThreads, 0, c.stream>>>(c.df_p, c.x32, n, c.dsc + b, c.dsc + a);
       MGAR_LAUNCH_CHECK();
       std::swap(a, b);

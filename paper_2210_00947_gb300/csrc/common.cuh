@@ -907,6 +907,11 @@ void fine3d_dir(Ctx& c, const float* z, const float* p_old, float* p, const doub
                 double* dot, double* rz_set);
 // zero-guess FP32 V-cycle x = M b that also leaves r . x in *dout (r in
 // double-float pairs, or r = b when r is null; 3D tiled path)
+// vcycle_dot applies: one pre- and one post-sweep, two levels or more, and
+// (3D) the tiled finest kernels
+inline bool vcycle_dot_ok(const Ctx& c) {
+  return c.p.nu_pre == 1 && c.p.nu_post == 1 && c.nl >= 2 && !c.untiled;
+}
 void vcycle_dot(Ctx& c, const float* b, float* x, const float2* r, double* dout);
 // launch shapes of the tiled kernels (occupancy query; call outside stream capture)
 void fine3d_prepare(Ctx& c);

@@ -91,6 +91,87 @@ __global__ void k_apply(Row row, const Real* __restrict__ x, Real* __restrict__ 
   if (DOT) block_sum_finish<1>(v, partials, counter, out);
 }
 
+// The 2D finest-level passes with kNptFine nodes per thread (nodes base,
+// base + blockDim.x, ...): each thread has several nodes' loads in flight and
+// the launch a quarter of the blocks; the arithmetic per node is that of the
+// one-node kernels above.
+constexpr int kNptFine = 4;
+
+inline int blocks_npt(int64_t n) {
+  const int64_t per = (int64_t)kThreads * kNptFine;
+  return (int)((n + per - 1) / per);
+}
+
+template <typename Real>
+__global__ void k_jacobi_zero_n(const Real* __restrict__ b, Real* __restrict__ x,
+                                const Real* __restrict__ dinv, Real omega, int n) {
+  const int base = blockIdx.x * blockDim.x * kNptFine + threadIdx.x;
+  Real bv[kNptFine], dv[kNptFine];
+#pragma unroll
+  for (int u = 0; u < kNptFine; ++u) {
+    const int idx = base + u * blockDim.x;
+    if (idx < n) {
+      bv[u] = b[idx];
+      dv[u] = dinv[idx];
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kNptFine; ++u) {
+    const int idx = base + u * blockDim.x;
+    if (idx < n) x[idx] = omega * dv[u] * bv[u];
+  }
+}
+
+template <class Row, typename Real>
+__global__ void k_residual_n(Row row, const Real* __restrict__ b, const Real* __restrict__ x,
+                             Real* __restrict__ r) {
+  const int base = blockIdx.x * blockDim.x * kNptFine + threadIdx.x;
+#pragma unroll
+  for (int u = 0; u < kNptFine; ++u) {
+    const int idx = base + u * blockDim.x;
+    if (idx < row.size()) r[idx] = b[idx] - row(x, idx);
+  }
+}
+
+template <typename Real, int DIM>
+__global__ void k_prolong_n(const Real* __restrict__ xc, const Real* cur, Real* dst, Dims f, Dims cd,
+                            const uint8_t* __restrict__ fixed) {
+  pdl_wait();
+  pdl_trigger();
+  const int base = blockIdx.x * blockDim.x * kNptFine + threadIdx.x;
+#pragma unroll
+  for (int u = 0; u < kNptFine; ++u) {
+    const int idx = base + u * blockDim.x;
+    if (idx < f.n) prolong_node<Real, DIM>(xc, cur, dst, f, cd, fixed, idx);
+  }
+}
+
+// One damped-Jacobi sweep; with DOT also r . xout (r as df64 pairs: the CG's
+// r . z) into *dout, double-float warp sums, FP64 across warps and blocks.
+template <class Row, typename Real, bool DOT>
+__global__ void k_jacobi_n(Row row, const Real* __restrict__ b, const Real* __restrict__ xin,
+                           Real* __restrict__ xout, const Real* __restrict__ dinv, Real omega,
+                           const float2* __restrict__ rdot, double* partials,
+                           unsigned int* counter, double* dout) {
+  const int base = blockIdx.x * blockDim.x * kNptFine + threadIdx.x;
+  df acc{0.f, 0.f};
+#pragma unroll
+  for (int u = 0; u < kNptFine; ++u) {
+    const int idx = base + u * blockDim.x;
+    if (idx < row.size()) {
+      const Real ax = row(xin, idx);
+      const Real xo = xin[idx] + omega * dinv[idx] * (b[idx] - ax);
+      xout[idx] = xo;
+      if (DOT) {
+        // r . z, or b . z when no r is given
+        const float2 rv = rdot ? rdot[idx] : make_float2((float)b[idx], 0.f);
+        acc = df_add(acc, df_mulf(df{rv.x, rv.y}, (float)xo));
+      }
+    }
+  }
+  if (DOT) block_sum_finish_df(acc, partials, counter, dout);
+}
+
 template <typename Real, int DIM>
 __global__ void k_restrict(const Real* __restrict__ r, Real* __restrict__ bc, Dims f, Dims cd,
                            const uint8_t* __restrict__ fixed, const Real* __restrict__ dinvc = nullptr,
@@ -529,14 +610,17 @@ static void vcycle_fused(Ctx& c, const float* b0, float* x0, bool zero_guess,
       cur0 = h[0].t;
     } else {
       if (zero_guess) {
-        k_jacobi_zero<<<blocks_for(d0.n), kThreads, 0, c.stream>>>(b0, h[0].t, h[0].dinv, om,
-                                                                   (int)d0.n);
+        k_jacobi_zero_n<<<blocks_npt(d0.n), kThreads, 0, c.stream>>>(b0, h[0].t, h[0].dinv, om,
+                                                                     (int)d0.n);
         MGAR_LAUNCH_CHECK_AT(level_site(0, 0));
       } else {
         sweep<Real, DIM>(c, 0, b0, x0, h[0].t);
       }
       cur0 = h[0].t;
-      residual<Real, DIM>(c, 0, b0, cur0, h[0].r);
+      ProfScope pr(c, MGAR_KC_RESID0);
+      k_residual_n<<<blocks_npt(d0.n), kThreads, 0, c.stream>>>(
+          fine_row<Real, DIM>(c, ref_ke<Real>(c), nullptr), b0, (const Real*)cur0, h[0].r);
+      MGAR_LAUNCH_CHECK_AT(level_site(2, 0));
     }
   }
   // the tiled 3D kernels leave r = 0 on fixed nodes, which P^T = (Z P)^T ignores
@@ -604,11 +688,21 @@ static void vcycle_fused(Ctx& c, const float* b0, float* x0, bool zero_guess,
     fine3d(c, 3, ref_ke<Real>(c), b0, h[0].dinv, cur0, nullptr, x0, nullptr, rdot, dout);
   } else {
     ProfScope ps(c, MGAR_KC_SMOOTH0);
-    // interpolation in place on the pre-smoothed iterate, then the sweep into x0
-    k_prolong<Real, DIM><<<blocks_for(d0.n), kThreads, 0, c.stream>>>(res[1], cur0, cur0, d0, c.L[1],
-                                                                       c.fixed);
+    // interpolation in place on the pre-smoothed iterate, then the sweep into
+    // x0 (with r . x0 into *dout when asked)
+    k_prolong_n<Real, DIM><<<blocks_npt(d0.n), kThreads, 0, c.stream>>>(res[1], cur0, cur0, d0,
+                                                                         c.L[1], c.fixed);
     MGAR_LAUNCH_CHECK_AT(level_site(4, 0));
-    sweep<Real, DIM>(c, 0, b0, cur0, x0);
+    const FineRow<Real, DIM> row = fine_row<Real, DIM>(c, ref_ke<Real>(c), nullptr);
+    if (dout)
+      k_jacobi_n<FineRow<Real, DIM>, Real, true><<<blocks_npt(d0.n), kThreads, 0, c.stream>>>(
+          row, b0, (const Real*)cur0, x0, (const Real*)h[0].dinv, om, rdot, c.partials, c.counter,
+          dout);
+    else
+      k_jacobi_n<FineRow<Real, DIM>, Real, false><<<blocks_npt(d0.n), kThreads, 0, c.stream>>>(
+          row, b0, (const Real*)cur0, x0, (const Real*)h[0].dinv, om, nullptr, nullptr, nullptr,
+          nullptr);
+    MGAR_LAUNCH_CHECK_AT(level_site(1, 0));
   }
 }
 
@@ -696,9 +790,10 @@ template void vcycle<double>(Ctx&, const double*, double*, bool);
 template void vcycle<float>(Ctx&, const float*, float*, bool);
 
 void vcycle_dot(Ctx& c, const float* b, float* x, const float2* r, double* dout) {
-  require(c.dim == 3 && c.p.nu_pre == 1 && c.p.nu_post == 1 && c.nl >= 2 && !c.untiled, MGAR_ERR_ARG,
-          "fused r.z V-cycle needs the tiled 3D path");
-  vcycle_fused<3>(c, b, x, true, r, dout);
+  require(vcycle_dot_ok(c), MGAR_ERR_ARG,
+          "fused r.z V-cycle needs one pre- and one post-sweep, two levels and the tiled 3D kernels");
+  if (c.dim == 2) vcycle_fused<2>(c, b, x, true, r, dout);
+  else vcycle_fused<3>(c, b, x, true, r, dout);
 }
 
 template <typename Real, int DIM>
