@@ -5,8 +5,10 @@
 // of an H8 node (c = 1/12), w_ij = k_a + k_b along the edges and 2 k_e across
 // the diagonals of a Q4 node (c = 1/6); a fixed row is the identity.  Each
 // term's difference is exact (TwoSum) and each product exact (TwoProd), so a
-// term is rounded relative to its own size, not relative to |x|.  Shared by
-// the single-design CG and the batched CG.
+// term is rounded relative to its own size, not relative to |x|; the terms
+// are summed with their rounding errors gathered apart and one
+// renormalisation at the end.  Shared by the single-design CG and the
+// batched CG.
 #pragma once
 
 #include "common.cuh"
@@ -36,13 +38,35 @@ __device__ __forceinline__ df ld_xdf(const DfOp& op, const float2* __restrict__ 
   return (ok && !op.fixed[j]) ? df{v.x, v.y} : df{0.f, 0.f};
 }
 
-// acc += w * (xi - xj)
-__device__ __forceinline__ void df_term(df& acc, df w, df xi, df xj) {
+// (ah, al) += w * (xi - xj) with the pair left unnormalised: the difference
+// formed exactly (TwoSum), the product's high part added by TwoSum and every
+// rounding error gathered in al (the compensated dot product of Ogita, Rump
+// and Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 26, 2005:
+// as accurate as twice the working precision, with one renormalisation at
+// the end instead of one per term).
+__device__ __forceinline__ void df_acc_term(float& ah, float& al, df w, df xi, df xj) {
   float s, e;
   two_sum(xi.hi, -xj.hi, s, e);
   e = __fadd_rn(e, __fsub_rn(xi.lo, xj.lo));
-  acc = df_add(acc, df_mul(w, df_make(s, e)));
+  float p, pe;
+  two_prod(w.hi, s, p, pe);
+  pe = __fmaf_rn(w.hi, e, pe);
+  pe = __fmaf_rn(w.lo, s, pe);
+  float t, te;
+  two_sum(ah, p, t, te);
+  ah = t;
+  al = __fadd_rn(al, __fadd_rn(te, pe));
 }
+
+// k_a + k_b as an unnormalised pair (df_acc_term multiplies both halves)
+__device__ __forceinline__ df df_wsum(df a, df b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  return df{s, __fadd_rn(e, __fadd_rn(a.lo, b.lo))};
+}
+
+// 2 k, exactly
+__device__ __forceinline__ df df_twice(df a) { return df{2.f * a.hi, 2.f * a.lo}; }
 
 __device__ __forceinline__ df df_row2(const DfOp& op, const float2* __restrict__ x, int i, int j) {
   const int idx = i + op.NX * j;
@@ -54,16 +78,16 @@ __device__ __forceinline__ df df_row2(const DfOp& op, const float2* __restrict__
   const df k00 = ld_kdf(op, e00, xm && ym), k01 = ld_kdf(op, e00 + 1, xp && ym);
   const df k10 = ld_kdf(op, e00 + op.ex, xm && yp), k11 = ld_kdf(op, e00 + op.ex + 1, xp && yp);
   const int NX = op.NX;
-  df acc{0.f, 0.f};
-  df_term(acc, df_add(k00, k10), xi, ld_xdf(op, x, idx - 1, xm));
-  df_term(acc, df_add(k01, k11), xi, ld_xdf(op, x, idx + 1, xp));
-  df_term(acc, df_add(k00, k01), xi, ld_xdf(op, x, idx - NX, ym));
-  df_term(acc, df_add(k10, k11), xi, ld_xdf(op, x, idx + NX, yp));
-  df_term(acc, df_add(k00, k00), xi, ld_xdf(op, x, idx - NX - 1, xm && ym));
-  df_term(acc, df_add(k01, k01), xi, ld_xdf(op, x, idx - NX + 1, xp && ym));
-  df_term(acc, df_add(k10, k10), xi, ld_xdf(op, x, idx + NX - 1, xm && yp));
-  df_term(acc, df_add(k11, k11), xi, ld_xdf(op, x, idx + NX + 1, xp && yp));
-  return df_mul(acc, op.scale);
+  float ah = 0.f, al = 0.f;
+  df_acc_term(ah, al, df_wsum(k00, k10), xi, ld_xdf(op, x, idx - 1, xm));
+  df_acc_term(ah, al, df_wsum(k01, k11), xi, ld_xdf(op, x, idx + 1, xp));
+  df_acc_term(ah, al, df_wsum(k00, k01), xi, ld_xdf(op, x, idx - NX, ym));
+  df_acc_term(ah, al, df_wsum(k10, k11), xi, ld_xdf(op, x, idx + NX, yp));
+  df_acc_term(ah, al, df_twice(k00), xi, ld_xdf(op, x, idx - NX - 1, xm && ym));
+  df_acc_term(ah, al, df_twice(k01), xi, ld_xdf(op, x, idx - NX + 1, xp && ym));
+  df_acc_term(ah, al, df_twice(k10), xi, ld_xdf(op, x, idx + NX - 1, xm && yp));
+  df_acc_term(ah, al, df_twice(k11), xi, ld_xdf(op, x, idx + NX + 1, xp && yp));
+  return df_mul(df_make(ah, al), op.scale);
 }
 
 __device__ __forceinline__ df df_row3(const DfOp& op, const float2* __restrict__ x, int i, int j, int k) {
@@ -83,30 +107,30 @@ __device__ __forceinline__ df df_row3(const DfOp& op, const float2* __restrict__
   const df k101 = ld_kdf(op, e000 + EXY + 1, xp && ym && zp);
   const df k110 = ld_kdf(op, e000 + EXY + EX, xm && yp && zp);
   const df k111 = ld_kdf(op, e000 + EXY + EX + 1, xp && yp && zp);
-  df acc{0.f, 0.f};
+  float ah = 0.f, al = 0.f;
   // face diagonals in the xy, xz and yz planes (two elements each)
-  df_term(acc, df_add(k000, k100), xi, ld_xdf(op, x, idx - 1 - NX, xm && ym));
-  df_term(acc, df_add(k001, k101), xi, ld_xdf(op, x, idx + 1 - NX, xp && ym));
-  df_term(acc, df_add(k010, k110), xi, ld_xdf(op, x, idx - 1 + NX, xm && yp));
-  df_term(acc, df_add(k011, k111), xi, ld_xdf(op, x, idx + 1 + NX, xp && yp));
-  df_term(acc, df_add(k000, k010), xi, ld_xdf(op, x, idx - 1 - NXY, xm && zm));
-  df_term(acc, df_add(k001, k011), xi, ld_xdf(op, x, idx + 1 - NXY, xp && zm));
-  df_term(acc, df_add(k100, k110), xi, ld_xdf(op, x, idx - 1 + NXY, xm && zp));
-  df_term(acc, df_add(k101, k111), xi, ld_xdf(op, x, idx + 1 + NXY, xp && zp));
-  df_term(acc, df_add(k000, k001), xi, ld_xdf(op, x, idx - NX - NXY, ym && zm));
-  df_term(acc, df_add(k010, k011), xi, ld_xdf(op, x, idx + NX - NXY, yp && zm));
-  df_term(acc, df_add(k100, k101), xi, ld_xdf(op, x, idx - NX + NXY, ym && zp));
-  df_term(acc, df_add(k110, k111), xi, ld_xdf(op, x, idx + NX + NXY, yp && zp));
+  df_acc_term(ah, al, df_wsum(k000, k100), xi, ld_xdf(op, x, idx - 1 - NX, xm && ym));
+  df_acc_term(ah, al, df_wsum(k001, k101), xi, ld_xdf(op, x, idx + 1 - NX, xp && ym));
+  df_acc_term(ah, al, df_wsum(k010, k110), xi, ld_xdf(op, x, idx - 1 + NX, xm && yp));
+  df_acc_term(ah, al, df_wsum(k011, k111), xi, ld_xdf(op, x, idx + 1 + NX, xp && yp));
+  df_acc_term(ah, al, df_wsum(k000, k010), xi, ld_xdf(op, x, idx - 1 - NXY, xm && zm));
+  df_acc_term(ah, al, df_wsum(k001, k011), xi, ld_xdf(op, x, idx + 1 - NXY, xp && zm));
+  df_acc_term(ah, al, df_wsum(k100, k110), xi, ld_xdf(op, x, idx - 1 + NXY, xm && zp));
+  df_acc_term(ah, al, df_wsum(k101, k111), xi, ld_xdf(op, x, idx + 1 + NXY, xp && zp));
+  df_acc_term(ah, al, df_wsum(k000, k001), xi, ld_xdf(op, x, idx - NX - NXY, ym && zm));
+  df_acc_term(ah, al, df_wsum(k010, k011), xi, ld_xdf(op, x, idx + NX - NXY, yp && zm));
+  df_acc_term(ah, al, df_wsum(k100, k101), xi, ld_xdf(op, x, idx - NX + NXY, ym && zp));
+  df_acc_term(ah, al, df_wsum(k110, k111), xi, ld_xdf(op, x, idx + NX + NXY, yp && zp));
   // body diagonals (one element each)
-  df_term(acc, k000, xi, ld_xdf(op, x, idx - 1 - NX - NXY, xm && ym && zm));
-  df_term(acc, k001, xi, ld_xdf(op, x, idx + 1 - NX - NXY, xp && ym && zm));
-  df_term(acc, k010, xi, ld_xdf(op, x, idx - 1 + NX - NXY, xm && yp && zm));
-  df_term(acc, k011, xi, ld_xdf(op, x, idx + 1 + NX - NXY, xp && yp && zm));
-  df_term(acc, k100, xi, ld_xdf(op, x, idx - 1 - NX + NXY, xm && ym && zp));
-  df_term(acc, k101, xi, ld_xdf(op, x, idx + 1 - NX + NXY, xp && ym && zp));
-  df_term(acc, k110, xi, ld_xdf(op, x, idx - 1 + NX + NXY, xm && yp && zp));
-  df_term(acc, k111, xi, ld_xdf(op, x, idx + 1 + NX + NXY, xp && yp && zp));
-  return df_mul(acc, op.scale);
+  df_acc_term(ah, al, k000, xi, ld_xdf(op, x, idx - 1 - NX - NXY, xm && ym && zm));
+  df_acc_term(ah, al, k001, xi, ld_xdf(op, x, idx + 1 - NX - NXY, xp && ym && zm));
+  df_acc_term(ah, al, k010, xi, ld_xdf(op, x, idx - 1 + NX - NXY, xm && yp && zm));
+  df_acc_term(ah, al, k011, xi, ld_xdf(op, x, idx + 1 + NX - NXY, xp && yp && zm));
+  df_acc_term(ah, al, k100, xi, ld_xdf(op, x, idx - 1 - NX + NXY, xm && ym && zp));
+  df_acc_term(ah, al, k101, xi, ld_xdf(op, x, idx + 1 - NX + NXY, xp && ym && zp));
+  df_acc_term(ah, al, k110, xi, ld_xdf(op, x, idx - 1 + NX + NXY, xm && yp && zp));
+  df_acc_term(ah, al, k111, xi, ld_xdf(op, x, idx + 1 + NX + NXY, xp && yp && zp));
+  return df_mul(df_make(ah, al), op.scale);
 }
 
 template <int DIM>
