@@ -673,21 +673,26 @@ __global__ void __launch_bounds__(kCholThreads) k_band_cholesky_df_win(double* _
 // the substitutions in registers: lane l holds the row r = l (mod 32) of the
 // bw + 1 rows the current step touches, receives the step's solved value by
 // shuffle and takes row r + 32 (forward) or r - 32 (backward) once its own
-// row is solved, so no step waits on shared memory.
+// row is solved, so no step waits on shared memory.  The band and the
+// reciprocal pivots are staged in shared memory; a step's coefficient and
+// pivot loads do not depend on the chain, and the solved value is stored
+// after it has been passed on.
 __global__ void k_band_inverse_df_win(const double* __restrict__ gband_d,
                                       const double* __restrict__ grdiag_d, int n, int bw,
                                       double* __restrict__ inv) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const float2* gband = reinterpret_cast<const float2*>(gband_d);
-  const float2* rdiag = reinterpret_cast<const float2*>(grdiag_d);
+  const float2* grdiag = reinterpret_cast<const float2*>(grdiag_d);
   float2* sband = reinterpret_cast<float2*>(smraw);
   const int ld = bw + 1;
   const int64_t size = (int64_t)n * ld;
+  float2* srdiag = sband + size;
   const int warps = blockDim.x >> 5;
   const int wid = threadIdx.x >> 5;
   for (int64_t t = threadIdx.x; t < size; t += blockDim.x) sband[t] = gband[t];
+  for (int t = threadIdx.x; t < n; t += blockDim.x) srdiag[t] = grdiag[t];
   __syncthreads();
-  float2* colbuf = sband + size + (int64_t)wid * n;  // the forward solution y
+  float2* colbuf = srdiag + n + (int64_t)wid * n;  // the forward solution y
   const int col = blockIdx.x * warps + wid;
   const int lane = threadIdx.x & 31;
   if (col >= n) return;
@@ -698,17 +703,14 @@ __global__ void k_band_inverse_df_win(const double* __restrict__ gband_d,
   for (int p = col; p < n; ++p) {
     const int owner = p & 31;
     const bool upd = r > p && r <= p + bw && r < n;
-    df lrp{0.f, 0.f};
-    if (upd) lrp = df_ld(sband + (int64_t)r * ld + (p - r + bw));  // L(r, p)
-    df yp{0.f, 0.f};
-    if (lane == owner) {
-      yp = df_mul(y, df_ld(rdiag + p));
-      df_st(colbuf + p, yp);
-    }
+    const df lrp = upd ? df_ld(sband + (int64_t)r * ld + (p - r + bw)) : df{0.f, 0.f};  // L(r, p)
+    const df rd = df_ld(srdiag + p);
+    df yp = df_mul(y, rd);  // the owner's solved value (others discard theirs)
     yp.hi = __shfl_sync(0xffffffffu, yp.hi, owner);
     yp.lo = __shfl_sync(0xffffffffu, yp.lo, owner);
     if (upd) y = df_sub(y, df_mul(lrp, yp));
     if (lane == owner) {
+      df_st(colbuf + p, yp);
       r = p + 32;
       y = df{0.f, 0.f};
     }
@@ -720,17 +722,14 @@ __global__ void k_band_inverse_df_win(const double* __restrict__ gband_d,
   for (int i = n - 1; i >= 0; --i) {
     const int owner = i & 31;
     const bool upd = r >= 0 && r < i && r >= i - bw;
-    df lir{0.f, 0.f};
-    if (upd) lir = df_ld(sband + (int64_t)i * ld + (r - i + bw));  // L(i, r)
-    df xi{0.f, 0.f};
-    if (lane == owner) {
-      xi = df_mul(y, df_ld(rdiag + i));
-      inv[(int64_t)i * n + col] = df_to_double(xi);
-    }
+    const df lir = upd ? df_ld(sband + (int64_t)i * ld + (r - i + bw)) : df{0.f, 0.f};  // L(i, r)
+    const df rd = df_ld(srdiag + i);
+    df xi = df_mul(y, rd);
     xi.hi = __shfl_sync(0xffffffffu, xi.hi, owner);
     xi.lo = __shfl_sync(0xffffffffu, xi.lo, owner);
     if (upd) y = df_sub(y, df_mul(lir, xi));
     if (lane == owner) {
+      inv[(int64_t)i * n + col] = df_to_double(xi);
       r = i - 32;
       y = r >= 0 ? df_ld(colbuf + r) : df{0.f, 0.f};
     }
@@ -886,22 +885,23 @@ static void coarse_factor(Ctx& c, const Real* st, const Dims& dcst) {
   // the FP32 V-cycle's coarsest factor and inverse in df64 on the FP32 pipe
   // (same band bytes: a df64 pair is the size of a double)
   if (sizeof(Real) == 4 && sizeof(B) == 8 && smem && inv_smem <= kBandSmemMax && c.df_coarse) {
-    if (c.bw < kWinBw) {
+    // the windowed inverse also stages the n reciprocal pivots
+    const size_t win_smem = inv_smem + (size_t)c.nc * sizeof(B);
+    if (c.bw < kWinBw)
       k_band_cholesky_df_win<<<1, 32 * std::max(c.bw, 1), band_bytes, s>>>(
           (double*)band, (double*)rdiag, c.nc, c.bw, c.derr);
-      MGAR_LAUNCH_CHECK();
-      k_band_inverse_df_win<<<(c.nc + 7) / 8, 256, inv_smem, s>>>(
-          (const double*)band, (const double*)rdiag, c.nc, c.bw, (double*)inv);
-      MGAR_LAUNCH_CHECK();
-    } else {
+    else
       k_band_cholesky_df<<<1, kCholThreads, band_bytes, s>>>((double*)band, (double*)rdiag, c.nc,
                                                              c.bw, c.derr);
-      MGAR_LAUNCH_CHECK();
+    MGAR_LAUNCH_CHECK();
+    if (c.bw < kWinBw && win_smem <= kBandSmemMax)
+      k_band_inverse_df_win<<<(c.nc + 7) / 8, 256, win_smem, s>>>(
+          (const double*)band, (const double*)rdiag, c.nc, c.bw, (double*)inv);
+    else
       k_band_inverse_df<<<(c.nc + 7) / 8, 256, inv_smem, s>>>((const double*)band,
                                                              (const double*)rdiag, c.nc, c.bw,
                                                              (double*)inv);
-      MGAR_LAUNCH_CHECK();
-    }
+    MGAR_LAUNCH_CHECK();
     if (c.side_stream) {
       MGAR_CUDA(cudaEventRecord(c.ev_join, s));
       c.coarse_pending = true;
