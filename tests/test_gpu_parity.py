@@ -125,9 +125,13 @@ def test_vcycle_matches_oracle(dims, nl, zero_guess):
 # hierarchy.  FP32 storage and arithmetic bound the agreement (the operands
 # carry 2^-24 and each stencil row cancels its 21-27 terms down to the
 # residual); the bar is 1e-4.  (42, 42, 21) selects the 43 x 5 tiles and
-# coarsens z oddly.
+# coarsens z oddly.  The coarsest factor and inverse: band widths below 32
+# take the windowed kernels (all but the last three cases; (16, 16, 12) at
+# nl 3 is width 31), (10, 10, 8) and (60, 20, 0) at nl 2 (widths 43 and 32)
+# the shared-memory df64 kernels, (42, 42, 21) the global-memory FP64 ones.
 @pytest.mark.parametrize("dims,nl", [((37, 23, 0), 3), ((100, 100, 0), 4), ((13, 11, 9), 3),
-                                     ((20, 18, 16), 4), ((42, 42, 21), 3)])
+                                     ((20, 18, 16), 4), ((16, 16, 12), 3), ((10, 10, 8), 2),
+                                     ((60, 20, 0), 2), ((42, 42, 21), 3)])
 @pytest.mark.parametrize("zero_guess", [True, False])
 @pytest.mark.parametrize("cluster", [False, True])
 def test_mixed_vcycle_matches_oracle(dims, nl, zero_guess, cluster, monkeypatch):
