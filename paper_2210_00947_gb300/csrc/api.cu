@@ -127,8 +127,8 @@ void free_ctx(Ctx& c) {
   cudaFree(c.run_rho);
   cudaFree(c.run_T);
   void* ptrs[] = {c.fixed, c.efix, c.gfix, c.q, c.rho_phys, c.ke, c.ke0, c.ke_f, c.ke0_f, c.inv_hs, c.inv_hs_df, c.rho_phys_df, c.f_offs, c.f_w,
-                  c.dv, c.rsdv, c.r, c.z, c.pv, c.Ap, c.tm, c.tmp_dc, c.R, c.W, c.b32, c.x32, c.ke_df, c.df_q, c.df_x, c.df_r, c.df_p, c.df_Ap, c.df_p2, c.df_e, c.kd_df, c.xc32, c.p32, c.p32b, c.y32, c.tmp_e, c.oc_s, c.oc_lo,
-                  c.oc_hi, c.oc_s32, c.oc_lo32, c.oc_hi32, c.dv32, c.oc_amb, c.oc_namb, c.partials, c.counter, c.dsc, c.derr};
+                  c.dv, c.rsdv, c.dv_df, c.r, c.z, c.pv, c.Ap, c.tm, c.tmp_dc, c.R, c.W, c.b32, c.x32, c.ke_df, c.df_q, c.df_x, c.df_r, c.df_p, c.df_Ap, c.df_p2, c.df_e, c.kd_df, c.xc32, c.p32, c.p32b, c.y32, c.tmp_e, c.oc_s, c.oc_lo,
+                  c.oc_hi, c.oc_rho, c.oc_s32, c.oc_lo32, c.oc_hi32, c.dv32, c.oc_amb, c.oc_namb, c.partials, c.counter, c.dsc, c.derr};
   for (void* p : ptrs) cudaFree(p);
   if (c.hsc) cudaFreeHost(c.hsc);
   if (c.f_offs_h) cudaFreeHost(c.f_offs_h);
@@ -300,11 +300,13 @@ int mgar_create(mgar_t* out, const mgar_params* p, const uint8_t* fixed_mask, co
     MGAR_CUDA(cudaMalloc(&c->inv_hs_df, ne * sizeof(float2)));
     MGAR_CUDA(cudaMalloc(&c->rho_phys_df, ne * sizeof(float2)));
     MGAR_CUDA(cudaMalloc(&c->dv, ne * sizeof(double)));
-    MGAR_CUDA(cudaMalloc(&c->rsdv, ne * sizeof(double)));
+    MGAR_CUDA(cudaMalloc(&c->rsdv, ne * sizeof(float2)));
+    MGAR_CUDA(cudaMalloc(&c->dv_df, ne * sizeof(float2)));
     MGAR_CUDA(cudaMalloc(&c->tmp_e, ne * sizeof(double)));
-    MGAR_CUDA(cudaMalloc(&c->oc_s, ne * sizeof(double)));
-    MGAR_CUDA(cudaMalloc(&c->oc_lo, ne * sizeof(double)));
-    MGAR_CUDA(cudaMalloc(&c->oc_hi, ne * sizeof(double)));
+    MGAR_CUDA(cudaMalloc(&c->oc_s, ne * sizeof(float2)));
+    MGAR_CUDA(cudaMalloc(&c->oc_lo, ne * sizeof(float2)));
+    MGAR_CUDA(cudaMalloc(&c->oc_hi, ne * sizeof(float2)));
+    MGAR_CUDA(cudaMalloc(&c->oc_rho, ne * sizeof(float2)));
     MGAR_CUDA(cudaMalloc(&c->oc_s32, ne * sizeof(float)));
     MGAR_CUDA(cudaMalloc(&c->oc_lo32, ne * sizeof(float)));
     MGAR_CUDA(cudaMalloc(&c->oc_hi32, ne * sizeof(float)));

@@ -164,7 +164,8 @@ struct Ctx {
   int4* f_offs = nullptr;   // filter offsets (dx, dy, dz)
   double* f_w = nullptr;    // filter weights max(0, r - |d|)
   double* dv = nullptr;     // F^T (1/E)
-  double* rsdv = nullptr;   // 1 / sqrt(dv)
+  float2* rsdv = nullptr;   // 1 / sqrt(dv), double-float
+  float2* dv_df = nullptr;  // dv, double-float
   int n_filter = 0;
   double filter_r = 0.0;    // radius of the current tables
   int filter_cap = 0;       // offsets the tables have room for
@@ -195,7 +196,9 @@ struct Ctx {
          *df_Ap = nullptr, *df_p2 = nullptr;
   float2* df_e = nullptr;  // mixed mode: df64 scratch over elements (filter input)
   float2* kd_df = nullptr; // mixed mode: 4 sum_e k_e per node (df64), the 3D operator's diagonal x 12
-  double *tmp_e = nullptr, *oc_s = nullptr, *oc_lo = nullptr, *oc_hi = nullptr;
+  double* tmp_e = nullptr;
+  // OC update: s_e, the move limits and rho as double-float pairs, FP32 copies
+  float2 *oc_s = nullptr, *oc_lo = nullptr, *oc_hi = nullptr, *oc_rho = nullptr;
   float *oc_s32 = nullptr, *oc_lo32 = nullptr, *oc_hi32 = nullptr, *dv32 = nullptr;
   int *oc_amb = nullptr, *oc_namb = nullptr;
   int64_t oc_fallbacks = 0;

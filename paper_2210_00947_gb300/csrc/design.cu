@@ -283,29 +283,55 @@ __global__ void k_elem_sens(const double* __restrict__ T, const double* __restri
   out[e] = -coef * rp * energy;
 }
 
-// OC preparation: s_e = rho_e sqrt(max(-dc_e, 0) / dv_e) and the move box;
-// rsdv = 1 / sqrt(dv) is fixed by the filter and computed once.
+// The OC update's per-element values are kept as double-float pairs (df64,
+// about 48 bits) and its per-element arithmetic runs on the FP32 pipe: GB300
+// runs FP64 arithmetic and FP32<->FP64 conversions at about 1.6 per SM and
+// clock against 110 FP32 operations, and each FP64 operation per element
+// costs about 4 us on 2.1 M elements.  The design's rho and dc arrive in
+// FP64 and the new rho leaves in FP64 (one conversion each); the scalars
+// (lambda, the bracket, the volume sums across blocks) stay FP64.
+__device__ __forceinline__ df ld2(const float2* p, int64_t i) {
+  const float2 v = p[i];
+  return df{v.x, v.y};
+}
+__device__ __forceinline__ void st2(float2* p, int64_t i, df v) { p[i] = make_float2(v.hi, v.lo); }
+
+// OC preparation: s_e = rho_e sqrt(max(-dc_e, 0) / dv_e) and the move box
+// [max(0, rho - move), min(1, rho + move)], with their FP32 copies for the
+// multisection and rho itself for the apply; rsdv = 1 / sqrt(dv) is fixed by
+// the filter and computed once.
 __global__ void k_oc_prep(const double* __restrict__ rho, const double* __restrict__ dc,
-                          const double* __restrict__ rsdv, double* __restrict__ s,
-                          double* __restrict__ lo, double* __restrict__ hi, int64_t ne,
-                          double move) {
+                          const float2* __restrict__ rsdv, float2* __restrict__ s,
+                          float2* __restrict__ lo, float2* __restrict__ hi,
+                          float2* __restrict__ rdf, float* __restrict__ s32,
+                          float* __restrict__ lo32, float* __restrict__ hi32, int64_t ne,
+                          df move) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= ne) return;
-  const double r = rho[e];
-  // sqrt(x) = x / sqrt(x) with the Newton-refined reciprocal square root:
-  // a few FP64 multiplies instead of GB300's long FP64 square-root sequence
-  const double x = fmax(-dc[e], 0.0);
-  const double sq = x > 0.0 ? x * rsqrt_nr(x) : 0.0;
-  s[e] = r * sq * rsdv[e];
-  lo[e] = fmax(0.0, r - move);
-  hi[e] = fmin(1.0, r + move);
+  const df r = df_from_double(rho[e]);
+  const df x = df_from_double(-dc[e]);
+  // sqrt(x) = x / sqrt(x); x <= 0 (or NaN) gives 0
+  const df sq = x.hi > 0.f ? df_mul(x, df_rsqrt(x)) : df{0.f, 0.f};
+  const df sv = df_mul(df_mul(r, sq), ld2(rsdv, e));
+  df l = df_sub(r, move);
+  if (l.hi < 0.f) l = df{0.f, 0.f};
+  df h = df_add(r, move);
+  if (df_le(df{1.f, 0.f}, h)) h = df{1.f, 0.f};
+  st2(s, e, sv);
+  st2(lo, e, l);
+  st2(hi, e, h);
+  st2(rdf, e, r);
+  s32[e] = sv.hi;
+  lo32[e] = l.hi;
+  hi32[e] = h.hi;
 }
 
 // One bisection step on lambda: volume sum_e dv_e clamp(s_e / sqrt(lambda))
 // at the geometric midpoint of the bracket; the last block moves the
-// bracket and raises the done flag once (hi - lo) / (hi + lo) <= tol.
-__global__ void k_oc_pass(const double* __restrict__ s, const double* __restrict__ lo,
-                          const double* __restrict__ hi, const double* __restrict__ dv, int64_t ne,
+// bracket and raises the done flag once (hi - lo) / (hi + lo) <= tol.  The
+// fallback of the fast solve: FP64 arithmetic on the pairs' values.
+__global__ void k_oc_pass(const float2* __restrict__ s, const float2* __restrict__ lo,
+                          const float2* __restrict__ hi, const float2* __restrict__ dv, int64_t ne,
                           double volfrac, double tol, double* dsc, double* partials,
                           unsigned int* counter) {
   if (dsc[S_OC_DONE] != 0.0) return;
@@ -315,7 +341,9 @@ __global__ void k_oc_pass(const double* __restrict__ s, const double* __restrict
   double v[1] = {0.0};
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne;
        e += (int64_t)gridDim.x * blockDim.x)
-    v[0] += dv[e] * fmin(fmax(s[e] * mu, lo[e]), hi[e]);
+    v[0] += df_to_double(ld2(dv, e)) *
+            fmin(fmax(df_to_double(ld2(s, e)) * mu, df_to_double(ld2(lo, e))),
+                 df_to_double(ld2(hi, e)));
   double vol[1];
   if (block_sum_last<1>(v, partials, counter, vol) && threadIdx.x == 0) {
     double nlo = blo, nhi = bhi;
@@ -327,24 +355,6 @@ __global__ void k_oc_pass(const double* __restrict__ s, const double* __restrict
     dsc[S_OC_STEPS] += 1.0;
     if ((nhi - nlo) / (nhi + nlo) <= tol) dsc[S_OC_DONE] = 1.0;
   }
-}
-
-// rho <- clamp(s / sqrt(lambda)) with lambda the bracket's geometric
-// midpoint; max |change| into dsc.
-__global__ void k_oc_final(double* __restrict__ rho, const double* __restrict__ s,
-                           const double* __restrict__ lo, const double* __restrict__ hi, int64_t ne,
-                           double* dsc, double* partials, unsigned int* counter) {
-  const double lam = sqrt(dsc[S_OC_LO] * dsc[S_OC_HI]);
-  const double mu = 1.0 / sqrt(lam);
-  double ch = 0.0;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const double rn = fmin(fmax(s[e] * mu, lo[e]), hi[e]);
-    ch = fmax(ch, fabs(rn - rho[e]));
-    rho[e] = rn;
-  }
-  block_max_finish(ch, partials, counter, dsc + S_OC_CHANGE);
-  if (blockIdx.x == 0 && threadIdx.x == 0) dsc[S_OC_LAM] = lam;
 }
 
 __global__ void k_oc_mu_from_bracket(double* dsc) {
@@ -463,37 +473,55 @@ __global__ void k_oc_multisect(const float* __restrict__ s, const float* __restr
 }
 
 // Split elements for the bracket [mu_a, mu_b] (ln bracket widened by
-// margin): constant part C, slope B, and the ambiguous list.
-__global__ void k_oc_classify(const double* __restrict__ s, const double* __restrict__ lo,
-                              const double* __restrict__ hi, const double* __restrict__ dv, int ne,
+// margin): constant part C, slope B, and the ambiguous list.  The tests and
+// sums run in df64; an element whose breakpoint lies within rounding of a
+// bracket end is either listed as ambiguous or contributes an error of that
+// rounding's size (the root lies well inside the bracket).
+__global__ void k_oc_classify(const float2* __restrict__ s, const float2* __restrict__ lo,
+                              const float2* __restrict__ hi, const float2* __restrict__ dv, int ne,
                               double margin, double Lmin, double Lmax, double* dsc, int* amb,
                               int* namb, double* partials, unsigned int* counter) {
-  __shared__ double mua, mub;
+  __shared__ float2 mua, mub;
   if (threadIdx.x == 0) {
     const double La = fmax(dsc[S_OC_LA] - margin, Lmin), Lb = fmin(dsc[S_OC_LB] + margin, Lmax);
-    mua = exp(La);
-    mub = exp(Lb);
+    const double ea = exp(La), eb = exp(Lb);
     if (blockIdx.x == 0) {
-      dsc[S_OC_MUA] = mua;
-      dsc[S_OC_MUB] = mub;
+      dsc[S_OC_MUA] = ea;
+      dsc[S_OC_MUB] = eb;
     }
+    const df da = df_from_double(ea), db = df_from_double(eb);
+    mua = make_float2(da.hi, da.lo);
+    mub = make_float2(db.hi, db.lo);
   }
   __syncthreads();
-  const double a = mua, b = mub;
-  double v[2] = {0.0, 0.0};
+  const df A{mua.x, mua.y}, Bv{mub.x, mub.y};
+  df v0{0.f, 0.f}, v1{0.f, 0.f};
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
-    const double se = s[e], l = lo[e], h = hi[e];
-    const double ta = se * a, tb = se * b;
-    if (tb <= l) v[0] += dv[e] * l;
-    else if (ta >= h) v[0] += dv[e] * h;
-    else if (ta >= l && tb <= h) v[1] += dv[e] * se;
+    const df se = ld2(s, e), l = ld2(lo, e), h = ld2(hi, e);
+    const df ta = df_mul(se, A), tb = df_mul(se, Bv);
+    if (df_le(tb, l)) v0 = df_add(v0, df_mul(ld2(dv, e), l));
+    else if (df_le(h, ta)) v0 = df_add(v0, df_mul(ld2(dv, e), h));
+    else if (df_le(l, ta) && df_le(tb, h)) v1 = df_add(v1, df_mul(ld2(dv, e), se));
     else {
       const int slot = atomicAdd(namb, 1);
       if (slot < kOcAmbMax && CK(slot, kOcAmbMax)) amb[slot] = e;
     }
   }
+  // warp sums in df64, FP64 across warps and blocks
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v0 = df_add(v0, df{__shfl_down_sync(0xffffffffu, v0.hi, o), __shfl_down_sync(0xffffffffu, v0.lo, o)});
+    v1 = df_add(v1, df{__shfl_down_sync(0xffffffffu, v1.hi, o), __shfl_down_sync(0xffffffffu, v1.lo, o)});
+  }
+  double w[2] = {0.0, 0.0};
+  if ((threadIdx.x & 31) == 0) {
+    w[0] = df_to_double(v0);
+    w[1] = df_to_double(v1);
+  }
   double tot[2];
-  if (block_sum_last<2>(v, partials, counter, tot) && threadIdx.x == 0) {
+  if (block_sum_last_core<2>(w, partials, counter, tot, threadIdx.x, blockDim.x, blockIdx.x,
+                             gridDim.x) &&
+      threadIdx.x == 0) {
     dsc[S_OC_C] = tot[0];
     dsc[S_OC_B] = tot[1];
   }
@@ -501,8 +529,8 @@ __global__ void k_oc_classify(const double* __restrict__ s, const double* __rest
 
 // Sort the ambiguous list (bitonic, shared memory), then one warp bisects
 // g(mu) = C + B mu + sum_amb dv clamp(s mu, lo, hi) = volfrac on [mu_a, mu_b].
-__global__ void k_oc_finish(const double* __restrict__ s, const double* __restrict__ lo,
-                            const double* __restrict__ hi, const double* __restrict__ dv, int ne,
+__global__ void k_oc_finish(const float2* __restrict__ s, const float2* __restrict__ lo,
+                            const float2* __restrict__ hi, const float2* __restrict__ dv, int ne,
                             double volfrac, double* dsc, int* amb, int* namb_p) {
   __shared__ int key[kOcAmbMax];
   const int namb = *namb_p;
@@ -544,10 +572,10 @@ __global__ void k_oc_finish(const double* __restrict__ s, const double* __restri
     for (int i = lane; i < namb; i += 32) {
       const int e = CK(i, kOcAmbMax) ? key[i] : 0;
       const bool ok = CK(e, ne);
-      cs[i] = ok ? s[e] : 0.0;
-      cl[i] = ok ? lo[e] : 0.0;
-      ch[i] = ok ? hi[e] : 0.0;
-      cd[i] = ok ? dv[e] : 0.0;
+      cs[i] = ok ? df_to_double(ld2(s, e)) : 0.0;
+      cl[i] = ok ? df_to_double(ld2(lo, e)) : 0.0;
+      ch[i] = ok ? df_to_double(ld2(hi, e)) : 0.0;
+      cd[i] = ok ? df_to_double(ld2(dv, e)) : 0.0;
     }
     __syncwarp();
   }
@@ -560,7 +588,9 @@ __global__ void k_oc_finish(const double* __restrict__ s, const double* __restri
         if (!CK(i, kOcAmbMax)) continue;
         const int e = key[i];
         if (!CK(e, ne)) continue;
-        acc += dv[e] * fmin(fmax(s[e] * mu, lo[e]), hi[e]);
+        acc += df_to_double(ld2(dv, e)) *
+               fmin(fmax(df_to_double(ld2(s, e)) * mu, df_to_double(ld2(lo, e))),
+                    df_to_double(ld2(hi, e)));
       }
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -583,19 +613,22 @@ __global__ void k_oc_finish(const double* __restrict__ s, const double* __restri
 
 // rho <- clamp(s mu) for mu = dsc[S_OC_MU]; max |change| into dsc.  Skipped
 // (every block) while the fast solve's failure flag is up: the host then
-// runs the plain bisection and this kernel again.
-__global__ void k_oc_apply(double* __restrict__ rho, const double* __restrict__ s,
-                           const double* __restrict__ lo, const double* __restrict__ hi, int ne,
-                           double* dsc, double* partials, unsigned int* counter) {
+// runs the plain bisection and this kernel again.  rho_old is the pair the
+// preparation kept; the clamp and the change are formed in df64.
+__global__ void k_oc_apply(double* __restrict__ rho, const float2* __restrict__ s,
+                           const float2* __restrict__ lo, const float2* __restrict__ hi,
+                           const float2* __restrict__ rdf, int ne, double* dsc, double* partials,
+                           unsigned int* counter) {
   if (dsc[S_OC_FAIL] != 0.0) return;
   const double mu = dsc[S_OC_MU];
-  double ch = 0.0;
+  const df M = df_from_double(mu);
+  df chd{0.f, 0.f};
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += gridDim.x * blockDim.x) {
-    const double rn = fmin(fmax(s[e] * mu, lo[e]), hi[e]);
-    ch = fmax(ch, fabs(rn - rho[e]));
-    rho[e] = rn;
+    const df rn = df_min(df_max(df_mul(ld2(s, e), M), ld2(lo, e)), ld2(hi, e));
+    chd = df_max(chd, df_abs(df_sub(rn, ld2(rdf, e))));
+    rho[e] = df_to_double(rn);
   }
-  block_max_finish(ch, partials, counter, dsc + S_OC_CHANGE);
+  block_max_finish(df_to_double(chd), partials, counter, dsc + S_OC_CHANGE);
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     dsc[S_OC_LAM] = 1.0 / (mu * mu);
     // ln mu for the next update's warm start
@@ -606,25 +639,18 @@ __global__ void k_oc_apply(double* __restrict__ rho, const double* __restrict__ 
   }
 }
 
-__global__ void k_rsqrt_e(const double* __restrict__ a, double* __restrict__ b, int n) {
+// dv and 1 / sqrt(dv) as double-float pairs for the OC update
+__global__ void k_dv_df(const double* __restrict__ dv, float2* __restrict__ dvdf,
+                        float2* __restrict__ rsdv, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) b[i] = 1.0 / sqrt(a[i]);
+  if (i >= n) return;
+  st2(dvdf, i, df_from_double(dv[i]));
+  st2(rsdv, i, df_from_double(1.0 / sqrt(dv[i])));
 }
 
 __global__ void k_d2f_e(const double* __restrict__ a, float* __restrict__ b, int n) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
-}
-
-// FP32 copies of the OC inputs for the multisection.
-__global__ void k_oc_prep32(const double* __restrict__ s, const double* __restrict__ lo,
-                            const double* __restrict__ hi, float* __restrict__ s32,
-                            float* __restrict__ lo32, float* __restrict__ hi32, int ne) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= ne) return;
-  s32[e] = (float)s[e];
-  lo32[e] = (float)lo[e];
-  hi32[e] = (float)hi[e];
 }
 
 // ------------------------------------------------------------------- host
@@ -681,7 +707,7 @@ static void filter_derived(Ctx& c) {
   filter(c, c.tmp_e, c.dv, true);
   k_d2f_e<<<blocks_for(c.ne), kThreads, 0, c.stream>>>(c.dv, c.dv32, (int)c.ne);
   MGAR_LAUNCH_CHECK();
-  k_rsqrt_e<<<blocks_for(c.ne), kThreads, 0, c.stream>>>(c.dv, c.rsdv, (int)c.ne);
+  k_dv_df<<<blocks_for(c.ne), kThreads, 0, c.stream>>>(c.dv, c.dv_df, c.rsdv, (int)c.ne);
   MGAR_LAUNCH_CHECK();
 }
 
@@ -830,14 +856,12 @@ void oc_issue(Ctx& c, double* rho, const double* dc, double volfrac, double move
   const int ne = (int)c.ne;
   const int rb = c.grid_blocks_e;
   k_oc_prep<<<blocks_for(ne), kThreads, 0, c.stream>>>(rho, dc, c.rsdv, c.oc_s, c.oc_lo, c.oc_hi,
-                                                       ne, move);
+                                                       c.oc_rho, c.oc_s32, c.oc_lo32, c.oc_hi32,
+                                                       ne, df_from_double(move));
   MGAR_LAUNCH_CHECK();
   // lambda in [1e-40, 1e40]  <=>  ln(mu) in [-20 ln 10, 20 ln 10]
   const double Lmax = 20.0 * std::log(10.0), Lmin = -Lmax;
   ProfScope ps(c, MGAR_KC_OC);
-  k_oc_prep32<<<blocks_for(ne), kThreads, 0, c.stream>>>(c.oc_s, c.oc_lo, c.oc_hi, c.oc_s32,
-                                                         c.oc_lo32, c.oc_hi32, ne);
-  MGAR_LAUNCH_CHECK();
   k_oc_start<<<1, 32, 0, c.stream>>>(c.dsc, Lmin, Lmax, 1);
   MGAR_LAUNCH_CHECK();
   // three blocks per SM (the 80 registers of the 31 accumulators allow
@@ -850,15 +874,15 @@ void oc_issue(Ctx& c, double* rho, const double* dc, double volfrac, double move
     MGAR_LAUNCH_CHECK();
   }
   MGAR_CUDA(cudaMemsetAsync(c.oc_namb, 0, sizeof(int), c.stream));
-  k_oc_classify<<<rb, kThreads, 0, c.stream>>>(c.oc_s, c.oc_lo, c.oc_hi, c.dv, ne, kOcMargin, Lmin,
+  k_oc_classify<<<rb, kThreads, 0, c.stream>>>(c.oc_s, c.oc_lo, c.oc_hi, c.dv_df, ne, kOcMargin, Lmin,
                                                Lmax, c.dsc, c.oc_amb, c.oc_namb, c.partials,
                                                c.counter);
   MGAR_LAUNCH_CHECK();
-  k_oc_finish<<<1, 1024, 0, c.stream>>>(c.oc_s, c.oc_lo, c.oc_hi, c.dv, ne, volfrac, c.dsc,
+  k_oc_finish<<<1, 1024, 0, c.stream>>>(c.oc_s, c.oc_lo, c.oc_hi, c.dv_df, ne, volfrac, c.dsc,
                                         c.oc_amb, c.oc_namb);
   MGAR_LAUNCH_CHECK();
-  k_oc_apply<<<rb, kThreads, 0, c.stream>>>(rho, c.oc_s, c.oc_lo, c.oc_hi, ne, c.dsc, c.partials,
-                                            c.counter);
+  k_oc_apply<<<rb, kThreads, 0, c.stream>>>(rho, c.oc_s, c.oc_lo, c.oc_hi, c.oc_rho, ne, c.dsc,
+                                            c.partials, c.counter);
   MGAR_LAUNCH_CHECK();
 }
 
@@ -883,7 +907,7 @@ void oc_finish(Ctx& c, double* rho, double volfrac, double* lambda, double* chan
     const int max_steps = 200, batch = 16;
     for (int done = 0; done < max_steps; done += batch) {
       for (int b = 0; b < batch; ++b) {
-        k_oc_pass<<<rb, kThreads, 0, c.stream>>>(c.oc_s, c.oc_lo, c.oc_hi, c.dv, ne, volfrac, 1e-13,
+        k_oc_pass<<<rb, kThreads, 0, c.stream>>>(c.oc_s, c.oc_lo, c.oc_hi, c.dv_df, ne, volfrac, 1e-13,
                                                  c.dsc, c.partials, c.counter);
         MGAR_LAUNCH_CHECK();
       }
@@ -892,8 +916,8 @@ void oc_finish(Ctx& c, double* rho, double volfrac, double* lambda, double* chan
     }
     k_oc_mu_from_bracket<<<1, 1, 0, c.stream>>>(c.dsc);
     MGAR_LAUNCH_CHECK();
-    k_oc_apply<<<rb, kThreads, 0, c.stream>>>(rho, c.oc_s, c.oc_lo, c.oc_hi, ne, c.dsc, c.partials,
-                                              c.counter);
+    k_oc_apply<<<rb, kThreads, 0, c.stream>>>(rho, c.oc_s, c.oc_lo, c.oc_hi, c.oc_rho, ne, c.dsc,
+                                              c.partials, c.counter);
     MGAR_LAUNCH_CHECK();
     fetch_scalars(c, S_OC_LAM, 3);
   }

@@ -70,6 +70,27 @@ __device__ __forceinline__ df df_mulf(df a, float b) {
   return df_make(p, e);
 }
 
+// 1 / sqrt(a), a > 0: an FP32 seed and two Newton steps y <- y + y (1 - a y^2) / 2
+// with the residual 1 - a y^2 formed in df64 (each step doubles the correct bits)
+__device__ __forceinline__ df df_rsqrt(df a) {
+  df y{rsqrtf(a.hi), 0.f};
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const df e = df_sub(df{1.f, 0.f}, df_mul(df_mul(a, y), y));
+    y = df_add(y, df_mulf(y, 0.5f * e.hi));
+  }
+  return y;
+}
+
+// Order of normalised pairs (|lo| <= ulp(hi)/2): by the high words, then the
+// low words.
+__device__ __forceinline__ bool df_le(df a, df b) {
+  return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo);
+}
+__device__ __forceinline__ df df_max(df a, df b) { return df_le(a, b) ? b : a; }
+__device__ __forceinline__ df df_min(df a, df b) { return df_le(a, b) ? a : b; }
+__device__ __forceinline__ df df_abs(df a) { return a.hi < 0.f ? df_neg(a) : a; }
+
 // conversions (the FP64 side costs one FP64 subtraction per value)
 __host__ __device__ __forceinline__ df df_from_double(double x) {
   df r;

@@ -472,18 +472,6 @@ __device__ __forceinline__ df df_ld(const float2* p) {
 }
 __device__ __forceinline__ void df_st(float2* p, df v) { *p = make_float2(v.hi, v.lo); }
 
-// 1 / sqrt(a), a > 0: an FP32 seed and two Newton steps y <- y + y (1 - a y^2) / 2
-// with the residual 1 - a y^2 formed in df64 (each step doubles the correct bits)
-__device__ __forceinline__ df df_rsqrt(df a) {
-  df y{rsqrtf(a.hi), 0.f};
-#pragma unroll
-  for (int it = 0; it < 2; ++it) {
-    const df e = df_sub(df{1.f, 0.f}, df_mul(df_mul(a, y), y));
-    y = df_add(y, df_mulf(y, 0.5f * e.hi));
-  }
-  return y;
-}
-
 __global__ void __launch_bounds__(kCholThreads) k_band_cholesky_df(double* __restrict__ gband,
                                                                    double* __restrict__ grdiag,
                                                                    int n, int bw,
