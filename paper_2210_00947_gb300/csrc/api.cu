@@ -177,13 +177,17 @@ mgar_step_info design_cycle(Ctx& c, double* rho, double* T, int cycle) {
     inf.relres = rr;
   }
   double comp = 0.0;
-  // after a mixed 3D MGCG solve the double-float pairs of T are still in df_x
-  const bool t_df = need_mgcg && c.p.precision == MGAR_MIXED && c.dim == 3 && !c.untiled;
-  sensitivity(c, T, c.tmp_dc, nullptr, nullptr, t_df ? c.df_x : nullptr);
+  // after a mixed MGCG solve the double-float pairs of T are still in df_x
+  // (the 2D df64 CG and the tiled 3D path both end by converting df_x to T);
+  // the mixed path hands dc to the OC update as double-float pairs
+  const bool mixed = c.p.precision == MGAR_MIXED;
+  const bool t_df = need_mgcg && mixed && (c.dim == 2 || !c.untiled);
+  sensitivity(c, T, mixed ? nullptr : c.tmp_dc, nullptr, nullptr, t_df ? c.df_x : nullptr,
+              mixed ? dc_pairs(c) : nullptr);
   // f = q^T T (Eq. 5), read with the OC update's first scalar fetch
   dot(c, c.q, T, c.n, c.dsc + S_COMPL);
   double lam = 0.0, change = 0.0;
-  oc_update(c, rho, c.tmp_dc, c.p.volfrac, c.p.move, &lam, &change);
+  oc_update(c, rho, c.tmp_dc, c.p.volfrac, c.p.move, &lam, &change, mixed ? dc_pairs(c) : nullptr);
   comp = c.hsc[S_COMPL];
   inf.compliance = comp;
   inf.lambda = lam;

@@ -1173,9 +1173,9 @@ int mgar_batch_cycle(mgar_batch_t hb, double* const* rho, double* const* T, cons
     // each design's sensitivities (Eq. 10 through the filter), compliance
     // and OC update after the solve
     auto post = [&](int d, Ctx& c) {
-      sensitivity(c, T[d], c.tmp_dc, nullptr, nullptr);
+      sensitivity(c, T[d], nullptr, nullptr, nullptr, nullptr, dc_pairs(c));
       dot(c, c.q, T[d], c.n, c.dsc + S_COMPL);
-      oc_issue(c, rho[d], c.tmp_dc, volfrac[d], move);
+      oc_issue(c, rho[d], nullptr, volfrac[d], move, dc_pairs(c));
     };
     if (graphable(b)) {
       // three launches from the host: every design's filter, SIMP and

@@ -958,17 +958,24 @@ void set_filter_radius(Ctx& c, double r);
 void filter(Ctx& c, const double* in, double* out, bool transpose);
 void set_density(Ctx& c, const double* rho, bool physical);
 // T_df: the same temperatures as double-float pairs when the caller has them
-// (mixed path), else null
+// (mixed path), else null.  dc_df (mixed path only): dc as double-float pairs
+// instead of FP64 (dc may then be null)
 void sensitivity(Ctx& c, const double* T, double* dc, double* dv, double* compliance,
-                 const float2* T_df = nullptr);
+                 const float2* T_df = nullptr, float2* dc_df = nullptr);
 void postprocess(Ctx& c, const double* rho, const double* T, double volfrac, double* rho_out,
                  double* level_out, double* volume_out);
+// dc_df: dc as double-float pairs (then dc is not read)
 void oc_update(Ctx& c, double* rho, const double* dc, double volfrac, double move, double* lambda,
-               double* change);
+               double* change, const float2* dc_df = nullptr);
 // oc_update in two halves: the fast solve and its application queued without
 // a host read, then the read of its outcome (and the plain bisection if it
 // failed), so many handles' updates can be queued before any is read
-void oc_issue(Ctx& c, double* rho, const double* dc, double volfrac, double move);
+void oc_issue(Ctx& c, double* rho, const double* dc, double volfrac, double move,
+              const float2* dc_df = nullptr);
+// The internal dc buffer as double-float pairs (the same bytes as its ne
+// doubles): the mixed design cycle keeps dc in that form between the
+// sensitivities and the OC update
+inline float2* dc_pairs(Ctx& c) { return reinterpret_cast<float2*>(c.tmp_dc); }
 void oc_complete(Ctx& c, double* rho, double volfrac, double* lambda, double* change);
 // oc_complete without its read: the host mirror already holds S_OC_LAM,
 // S_OC_CHANGE and S_OC_FAIL of the update

@@ -185,7 +185,7 @@ __global__ void k_sens_df(const float2* __restrict__ T, const double* __restrict
 // Transpose filter (Eq. 9/11) of a df64 input already scaled by inv_hs.
 __global__ void k_filter_t_df(const float2* __restrict__ in, const int4* __restrict__ offs,
                               const double* __restrict__ w, int noff, Dims d, int reach, int reach_z,
-                              double* __restrict__ out) {
+                              double* __restrict__ out, float2* __restrict__ out_df) {
   // offsets staged as bytes: |d| <= 127 for any radius the tables allow
   __shared__ df ws[kMaxFilterOffsets];
   __shared__ char4 os[kMaxFilterOffsets];
@@ -202,7 +202,15 @@ __global__ void k_filter_t_df(const float2* __restrict__ in, const int4* __restr
   int i, j, k;
   coords(e, d.fEX, d.fEXY, i, j, k);
   const df v = filter_sum_df(in, ws, os, noff, e, i, j, k, d, reach, reach_z);
-  if (valid) out[e] = df_to_double(v);
+  if (!valid) return;
+  if (out_df) {
+    // renormalised by TwoSum: the pair an FP64 round trip of hi + lo gives
+    float sh, se;
+    two_sum(v.hi, v.lo, sh, se);
+    out_df[e] = make_float2(sh, se);
+  } else {
+    out[e] = df_to_double(v);
+  }
 }
 
 __global__ void k_to_df(const double* __restrict__ a, float2* __restrict__ b, int n) {
@@ -301,7 +309,7 @@ __device__ __forceinline__ void st2(float2* p, int64_t i, df v) { p[i] = make_fl
 // multisection and rho itself for the apply; rsdv = 1 / sqrt(dv) is fixed by
 // the filter and computed once.
 __global__ void k_oc_prep(const double* __restrict__ rho, const double* __restrict__ dc,
-                          const float2* __restrict__ rsdv, float2* __restrict__ s,
+                          const float2* __restrict__ dc_df, const float2* __restrict__ rsdv, float2* __restrict__ s,
                           float2* __restrict__ lo, float2* __restrict__ hi,
                           float2* __restrict__ rdf, float* __restrict__ s32,
                           float* __restrict__ lo32, float* __restrict__ hi32, int64_t ne,
@@ -309,7 +317,7 @@ __global__ void k_oc_prep(const double* __restrict__ rho, const double* __restri
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= ne) return;
   const df r = df_from_double(rho[e]);
-  const df x = df_from_double(-dc[e]);
+  const df x = dc_df ? df_neg(ld2(dc_df, e)) : df_from_double(-dc[e]);
   // sqrt(x) = x / sqrt(x); x <= 0 (or NaN) gives 0
   const df sq = x.hi > 0.f ? df_mul(x, df_rsqrt(x)) : df{0.f, 0.f};
   const df sv = df_mul(df_mul(r, sq), ld2(rsdv, e));
@@ -801,10 +809,11 @@ void set_density(Ctx& c, const double* rho, bool physical) {
 }
 
 void sensitivity(Ctx& c, const double* T, double* dc, double* dv, double* compliance,
-                 const float2* T_df) {
+                 const float2* T_df, float2* dc_df) {
   const Dims& d = c.L[0];
   const double coef = c.p.penal * (c.p.k0 - c.p.kmin);
-  if (dc && c.p.precision == MGAR_MIXED) {
+  require(!dc_df || c.p.precision == MGAR_MIXED, MGAR_ERR_ARG, "dc pairs need the mixed path");
+  if ((dc || dc_df) && c.p.precision == MGAR_MIXED) {
     ProfScope ps(c, MGAR_KC_SENS);
     if (!T_df) {
       k_to_df<<<blocks_for(c.n), kThreads, 0, c.stream>>>(T, c.df_p2, (int)c.n);
@@ -823,7 +832,8 @@ void sensitivity(Ctx& c, const double* T, double* dc, double* dv, double* compli
                                                                 c.p.penal);
     MGAR_LAUNCH_CHECK();
     k_filter_t_df<<<blocks_for(c.ne), kThreads, 0, c.stream>>>(
-        c.df_e, c.f_offs, c.f_w, c.n_filter, d, filter_reach(c), c.dim == 3 ? filter_reach(c) : 0, dc);
+        c.df_e, c.f_offs, c.f_w, c.n_filter, d, filter_reach(c), c.dim == 3 ? filter_reach(c) : 0,
+        dc_df ? nullptr : dc, dc_df);
     MGAR_LAUNCH_CHECK();
   } else if (dc) {
     ProfScope ps(c, MGAR_KC_SENS);
@@ -852,10 +862,11 @@ namespace mgar {
 // The fast solve for lambda and its application to rho, queued on the
 // handle's stream without a host read (the apply does nothing if the solve
 // failed; oc_complete reads the outcome).
-void oc_issue(Ctx& c, double* rho, const double* dc, double volfrac, double move) {
+void oc_issue(Ctx& c, double* rho, const double* dc, double volfrac, double move,
+              const float2* dc_df) {
   const int ne = (int)c.ne;
   const int rb = c.grid_blocks_e;
-  k_oc_prep<<<blocks_for(ne), kThreads, 0, c.stream>>>(rho, dc, c.rsdv, c.oc_s, c.oc_lo, c.oc_hi,
+  k_oc_prep<<<blocks_for(ne), kThreads, 0, c.stream>>>(rho, dc, dc_df, c.rsdv, c.oc_s, c.oc_lo, c.oc_hi,
                                                        c.oc_rho, c.oc_s32, c.oc_lo32, c.oc_hi32,
                                                        ne, df_from_double(move));
   MGAR_LAUNCH_CHECK();
@@ -927,8 +938,8 @@ void oc_finish(Ctx& c, double* rho, double volfrac, double* lambda, double* chan
 }
 
 void oc_update(Ctx& c, double* rho, const double* dc, double volfrac, double move, double* lambda,
-               double* change) {
-  oc_issue(c, rho, dc, volfrac, move);
+               double* change, const float2* dc_df) {
+  oc_issue(c, rho, dc, volfrac, move, dc_df);
   oc_complete(c, rho, volfrac, lambda, change);
 }
 
