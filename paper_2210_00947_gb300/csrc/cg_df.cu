@@ -717,7 +717,8 @@ static int solve_mgcg_ru3(Ctx& c, double* T, int* iters, double* relres) {
   int it = 0;
   if (!(rel <= c.p.eps2)) {
     require(std::isfinite(rel), MGAR_ERR_NONFINITE, "non-finite initial residual");
-    MGAR_CUDA(cudaMemsetAsync(c.xc32, 0, (size_t)n * sizeof(float), c.stream));
+    zero_async(c.xc32, n, c.stream);
+    MGAR_LAUNCH_CHECK();
     k_ru_start<<<1, 1, 0, c.stream>>>(c.dsc);
     MGAR_LAUNCH_CHECK();
     // the graph while no kernel class is being timed with events

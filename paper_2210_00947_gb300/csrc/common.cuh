@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -375,6 +376,31 @@ inline void require(bool ok, int code, const std::string& msg) {
 inline int blocks_for(int64_t n, int threads = kThreads) {
   int64_t b = (n + threads - 1) / threads;
   return (int)(b < 1 ? 1 : b);
+}
+
+// Zero fill and device-to-device copy as kernels: in a graph they run on the
+// SMs beside the other branches' kernels instead of queueing for a copy
+// engine, and in a stream they follow a kernel without a switch of engine.
+template <typename T>
+__global__ void k_zero(T* __restrict__ a, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = T(0);
+}
+template <typename T>
+__global__ void k_copy(const T* __restrict__ src, T* __restrict__ dst, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+constexpr int kFillBlocksMax = 4096;
+template <typename T>
+inline void zero_async(T* a, int64_t n, cudaStream_t s) {
+  k_zero<T><<<std::min(blocks_for(n), kFillBlocksMax), kThreads, 0, s>>>(a, n);
+}
+template <typename T>
+inline void copy_async(const T* src, T* dst, int64_t n, cudaStream_t s) {
+  k_copy<T><<<std::min(blocks_for(n), kFillBlocksMax), kThreads, 0, s>>>(src, dst, n);
 }
 
 // ------------------------------------------------------------ reductions

@@ -402,10 +402,11 @@ __device__ __forceinline__ void oc_candidates(double* dsc) {
 // previous update known): a two-sided geometric ladder L0 +- 1e-3 * 2^(j-1),
 // j = 1..14, around it, with the range ends as outermost candidates, so the
 // first pass brackets the root anywhere in the range and finely near L0.
-__global__ void k_oc_start(double* dsc, double La, double Lb, int warm) {
+__global__ void k_oc_start(double* dsc, double La, double Lb, int warm, int* namb) {
   const bool w = warm && dsc[S_OC_HAVEPREV] != 0.0;
   const double L0 = fmin(fmax(dsc[S_OC_LPREV], La), Lb);
   if (threadIdx.x == 0) {
+    *namb = 0;  // the classification's ambiguous count
     dsc[S_OC_LA] = La;
     dsc[S_OC_LB] = Lb;
     dsc[S_OC_FAIL] = 0.0;
@@ -873,7 +874,7 @@ void oc_issue(Ctx& c, double* rho, const double* dc, double volfrac, double move
   // lambda in [1e-40, 1e40]  <=>  ln(mu) in [-20 ln 10, 20 ln 10]
   const double Lmax = 20.0 * std::log(10.0), Lmin = -Lmax;
   ProfScope ps(c, MGAR_KC_OC);
-  k_oc_start<<<1, 32, 0, c.stream>>>(c.dsc, Lmin, Lmax, 1);
+  k_oc_start<<<1, 32, 0, c.stream>>>(c.dsc, Lmin, Lmax, 1, c.oc_namb);
   MGAR_LAUNCH_CHECK();
   // three blocks per SM (the 80 registers of the 31 accumulators allow
   // three): more loads in flight; the last block's sum over the partials
@@ -884,7 +885,6 @@ void oc_issue(Ctx& c, double* rho, const double* dc, double volfrac, double move
                                                   volfrac, c.dsc, c.partials, c.counter);
     MGAR_LAUNCH_CHECK();
   }
-  MGAR_CUDA(cudaMemsetAsync(c.oc_namb, 0, sizeof(int), c.stream));
   k_oc_classify<<<rb, kThreads, 0, c.stream>>>(c.oc_s, c.oc_lo, c.oc_hi, c.dv_df, ne, kOcMargin, Lmin,
                                                Lmax, c.dsc, c.oc_amb, c.oc_namb, c.partials,
                                                c.counter);

@@ -864,7 +864,8 @@ static void coarse_factor(Ctx& c, const Real* st, const Dims& dcst) {
   B* band = CoarseT<Real>::band(c);
   B* rdiag = CoarseT<Real>::rdiag(c);
   B* inv = CoarseT<Real>::inv(c);
-  MGAR_CUDA(cudaMemsetAsync(band, 0, (size_t)c.nc * (c.bw + 1) * sizeof(B), s));
+  zero_async(band, (int64_t)c.nc * (c.bw + 1), s);
+  MGAR_LAUNCH_CHECK();
   k_band_fill<Real, DIM, B><<<blocks_for(dcst.n), kThreads, 0, s>>>(st, dcst, c.bw, band);
   MGAR_LAUNCH_CHECK();
   const size_t band_bytes = (size_t)c.nc * (c.bw + 1) * sizeof(B);
@@ -953,12 +954,14 @@ void build_hierarchy(Ctx& c) {
   cudaStream_t s = c.stream;
   if (c.p.precision == MGAR_FP64) {
     // the reference k_e of MGAR's K - K0 (the mixed path keeps only its FP32 copy)
-    MGAR_CUDA(cudaMemcpyAsync(c.ke0, c.ke, c.ne * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    copy_async((const double*)c.ke, c.ke0, c.ne, s);
+    MGAR_LAUNCH_CHECK();
     if (c.dim == 2) build_levels<double, 2>(c, c.ke0, c.h64);
     else build_levels<double, 3>(c, c.ke0, c.h64);
   } else {
     // the FP32 copy of k_e is already fl32(k_e) (set_density writes both)
-    MGAR_CUDA(cudaMemcpyAsync(c.ke0_f, c.ke_f, c.ne * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    copy_async((const float*)c.ke_f, c.ke0_f, c.ne, s);
+    MGAR_LAUNCH_CHECK();
     if (c.dim == 2) build_levels<float, 2>(c, c.ke0_f, c.h32);
     else build_levels<float, 3>(c, c.ke0_f, c.h32);
   }
